@@ -1,0 +1,225 @@
+/*
+ * lasto_poisson.h -- C ABI of the GB300 (sm_103a) LASTO interstitial Poisson step.
+ *
+ * The step is the Poisson solve between the atom spheres of a free-standing
+ * cluster in the Linear Augmented Slater-Type Orbital method (Kang, Davenport,
+ * Glimm, Keyes, McGuigan; Section 3, Eq. 3.2-3.6, with Section 1's description
+ * of the pseudo-density):
+ *   1. inside every sphere the monopole of the electron density is replaced by a
+ *      smooth pseudo-density with the same charge (nucleus included) and the same
+ *      value and slope at the sphere radius; the nonspherical terms stay on the
+ *      grid as they are;
+ *   2. the pseudo-density is deposited on a graded tensor-product mesh and the
+ *      box faces get Dirichlet values from the cluster's multipole expansion;
+ *   3. multigrid (7-point finite differences, red-black Gauss-Seidel, full
+ *      weighting, trilinear prolongation, exact coarse solve), accelerated by
+ *      conjugate gradients, solves Lap u = 4 pi rho_tilde between the spheres;
+ *   4. the potential is interpolated onto every sphere surface and projected on
+ *      real spherical harmonics up to l = 4 (Eq. 3.6), the boundary data of the
+ *      inner Dirichlet problem (Eq. 3.4-3.5).
+ *
+ * Conventions used by every entry point
+ *   - Units: bohr and hartree.  u is the electrostatic potential: Lap u =
+ *     4 pi rho_tilde with rho_tilde the electron-sign pseudo-density, so
+ *     u -> +Z/r near a bare nucleus (the sign of Eq. 2.6).
+ *   - Grids: n[0]*n[1]*n[2] nodes, x-fastest, index (k*n[1] + j)*n[0] + i, FP64.
+ *     Nodes on the six faces carry Dirichlet values.  n[a] is odd and coarsens
+ *     (n+1)/2 repeatedly to at most 9 nodes per axis.
+ *   - Atoms: pos[n_atoms][3], Z[n_atoms], R[n_atoms], slater_w[n_atoms][3]
+ *     (electrons in each normalised Slater term zeta^3/(8 pi) e^{-zeta r}),
+ *     slater_zeta[n_atoms][3] (the same three exponents for every atom of a
+ *     cluster), c_lm[n_atoms][24] (coefficient of (r/R)^l y_lm in the
+ *     nonspherical part, l = 1..4, slot l*l + l + m - 1).
+ *   - Real spherical harmonics: orthonormal, no Condon-Shortley phase,
+ *     lm = l*l + l + m, m > 0 ~ cos(m phi), m < 0 ~ sin(|m| phi).
+ *   - Every pointer argument is DEVICE memory unless it says "host".  The caller
+ *     owns all inputs and outputs and the stream; nothing is freed or retained
+ *     beyond the call except inside a handle.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *     default stream).  Device-detected outcomes are written to device or host
+ *     status memory as stated and are valid after the stream synchronises.
+ *   - Return value: LASTO_OK or an error code for what the host can detect
+ *     (bad arguments, CUDA launch errors).  No exception or abort crosses the ABI.
+ */
+#ifndef LASTO_POISSON_H
+#define LASTO_POISSON_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum lasto_status {
+    LASTO_OK = 0,
+    LASTO_ERR_INVALID_ARG = 1,   /* bad sizes, null pointers, mesh that cannot coarsen, non-uniform zeta */
+    LASTO_ERR_GEOMETRY = 2,      /* spheres overlap, or a sphere is not two nodes inside the box */
+    LASTO_ERR_NONFINITE = 3,     /* NaN/Inf in the deposited density or in the iteration */
+    LASTO_ERR_NOT_CONVERGED = 4, /* cycle cap reached; outputs are written and stats hold the residual */
+    LASTO_ERR_TIMEOUT = 5,       /* a bounded device wait ran out */
+    LASTO_ERR_CUDA = 6,          /* a CUDA call failed; lasto_poisson_last_error() has the text */
+    LASTO_ERR_NO_MEMORY = 7      /* a solve needs more than the handle's workspace */
+};
+
+enum lasto_precision {
+    LASTO_PREC_FP64 = 0,  /* everything in FP64 ("plain" form) */
+    LASTO_PREC_MIXED = 1  /* FP32 smoothing/restriction/prolongation inside FP64 defect correction;
+                             the density exponentials in FP32-pair arithmetic (about 44 bits) */
+};
+
+enum lasto_cycle {
+    LASTO_CYCLE_V = 0,    /* stationary V(nu1,nu2)-cycles from the start */
+    LASTO_CYCLE_FV = 1,   /* one F-cycle, then V-cycles */
+    LASTO_CYCLE_PCG = 2   /* conjugate gradients preconditioned by one symmetric V-cycle (default) */
+};
+
+typedef struct lasto_config {
+    int n_max;        /* largest nodes per axis any solve will use (sizes the workspace) */
+    int max_atoms;    /* largest total atom count per solve call */
+    int max_batch;    /* largest number of clusters per solve call */
+    int precision;    /* enum lasto_precision */
+    int cycle;        /* enum lasto_cycle */
+    int nu1, nu2;     /* pre/post Gauss-Seidel sweeps per level (red+black = one sweep) */
+    int max_cycles;   /* cap on cycles / CG iterations */
+    double rel_tol;   /* stop when ||b - A u||_2 <= rel_tol ||b_eff||_2 (b_eff: b with the faces moved in) */
+    int n_theta;      /* Gauss-Legendre points in cos(theta) of the sphere quadrature (<= 32) */
+    int n_phi;        /* uniform points in phi (<= 64) */
+} lasto_config;
+
+/* Fills cfg with the defaults: n_max 129, max_atoms 561, max_batch 1, FP64, PCG,
+ * nu1 = nu2 = 2, 50 cycles, rel_tol 1e-10, 16 x 32 sphere points. */
+void lasto_config_default(lasto_config* cfg);
+
+typedef struct lasto_cluster {
+    int n_atoms;
+    const double* pos;          /* [n_atoms][3] device */
+    const double* Z;            /* [n_atoms]    device */
+    const double* R;            /* [n_atoms]    device */
+    const double* slater_w;     /* [n_atoms][3] device */
+    const double* slater_zeta;  /* [n_atoms][3] device */
+    const double* c_lm;         /* [n_atoms][24] device */
+    int n[3];                   /* nodes per axis */
+    const double* x;            /* [n[0]] device node coordinates, strictly increasing */
+    const double* y;            /* [n[1]] device */
+    const double* z;            /* [n[2]] device */
+    double centre[3];           /* host values: expansion centre of the boundary multipoles */
+} lasto_cluster;
+
+typedef struct lasto_stats {
+    int cycles;         /* V-cycles or CG iterations run */
+    int status;         /* enum lasto_status of this cluster */
+    double rel_resid;   /* final ||b - A u|| / ||b_eff|| (true residual, recomputed) */
+    double bnorm;       /* ||b_eff|| */
+} lasto_stats;
+
+typedef struct lasto_poisson lasto_poisson;   /* opaque; owns workspace, plans and CUDA graphs */
+
+/* Allocates the workspace for cfg (device memory sized by n_max, max_atoms,
+ * max_batch).  *out is NULL on failure.  Errors: INVALID_ARG, CUDA, NO_MEMORY. */
+int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out);
+
+/* The whole step (Section 3, Eq. 3.2-3.6) for n_clusters clusters (<= max_batch).
+ *   v_lm      device [sum n_atoms][25]: V_LM(R_i) = int y_LM V dOmega on each sphere
+ *             surface (Eq. 3.6; reading: unit-sphere measure so V = sum V_LM y_LM).
+ *   potential device, optional (NULL): the converged u of every cluster,
+ *             concatenated grids.
+ *   guess     device, optional (NULL): interior initial guess, same layout as
+ *             potential (faces are overwritten by the multipole values).
+ *   stats     host [n_clusters], optional (NULL); valid after stream sync; must
+ *             stay alive until then.
+ * The handle replays a CUDA graph captured for the same pointers and sizes, so
+ * repeated solves on the same buffers cost one graph launch.  Not thread-safe
+ * per handle.  Device outcomes per cluster go to stats[c].status. */
+int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* clusters, int n_clusters, double* v_lm,
+                        double* potential, const double* guess, lasto_stats* stats, void* stream);
+
+void lasto_poisson_destroy(lasto_poisson* h);
+
+/* Text of the last error on this handle (never NULL; "" when none). */
+const char* lasto_poisson_last_error(const lasto_poisson* h);
+
+/* ------------------------------------------------------------------ mesh (Section 3)
+ * One mesh axis, "fine meshes near the atoms and coarse meshes at large distances"
+ * with Dirichlet conditions at the edge (Section 3, first paragraph):
+ *   x(xi) = centre + A xi + B sign(xi)|xi|^p, xi = (i - m)/m, m = (n-1)/2,
+ *   A = h_min m, A + B = half_width, A + p B = h_max m; when p > p_max, p = p_max
+ *   and A, B follow from the other two conditions; B = 0 gives a uniform axis.
+ * x: device [n].  info: device [5] = {A, B, p, centre spacing, edge spacing}, may be NULL.
+ * Errors (host-checked): INVALID_ARG for even n, n < 3, or parameters with no
+ * monotone solution. */
+int lasto_mesh_axis(int n, double centre, double half_width, double h_min, double h_max, double p_max,
+                    double* x, double* info, void* stream);
+
+/* ------------------------------------------------------------------ single operations
+ * Each runs one kernel family of the solve on caller buffers, for parity tests
+ * and for callers composing their own pipeline.  They allocate their own small
+ * scratch with the stream-ordered allocator and free it on the same stream. */
+
+/* Per-sphere pseudo-density (Section 3, the three constraints beside Eq. 3.2-3.3;
+ * reading: rho_tilde = a + b r^2 + c r^4).  Outputs device [n_atoms]: q (charge of
+ * rho - Z delta inside the sphere, electron sign), rhoR, drhoR (monopole of the
+ * density and its slope at R), coef [n_atoms][3] = (a, b, c).  status: device int,
+ * set to GEOMETRY if spheres overlap, INVALID_ARG if zeta differs between atoms,
+ * left unchanged otherwise (caller zeroes it). */
+int lasto_op_sphere_params(const lasto_cluster* cl, double* q, double* rhoR, double* drhoR, double* coef,
+                           int* status, void* stream);
+
+/* Deposit b = 4 pi rho_tilde_grid at every node (Section 1's pseudo-density swap):
+ * inside sphere i, n_e - rho0_i(r) + rho_tilde_i(r); elsewhere n_e.  owner: device
+ * int [N] (sphere index or -1), may be NULL.  precision selects FP64 or FP32-pair
+ * exponentials.  status as above, plus NONFINITE. */
+int lasto_op_deposit(const lasto_cluster* cl, int precision, double* b, int* owner, int* status, void* stream);
+
+/* Boundary multipoles Q_lm = sum_nodes (b/4pi) vol r^l y_lm(node - centre), l <= 4,
+ * vol = product of dual-cell lengths.  Q: device [25]. */
+int lasto_op_multipoles(const int n[3], const double* x, const double* y, const double* z, const double* b,
+                        const double centre[3], double* Q, void* stream);
+
+/* Dirichlet faces u = -sum_lm 4pi/(2l+1) Q_lm y_lm / r^(l+1) about centre (Eq. 2.7
+ * decay).  Writes only the six faces of u. */
+int lasto_op_boundary_fill(const int n[3], const double* x, const double* y, const double* z,
+                           const double centre[3], const double* Q, double* u, void* stream);
+
+/* Au = A u on interior nodes (7-point nonuniform difference), 0 on faces. */
+int lasto_op_apply(const int n[3], const double* x, const double* y, const double* z, const double* u,
+                   double* Au, void* stream);
+
+/* r = b - A u on interior nodes, 0 on faces. */
+int lasto_op_residual(const int n[3], const double* x, const double* y, const double* z, const double* u,
+                      const double* b, double* r, void* stream);
+
+/* Red-black Gauss-Seidel: `sweeps` sweeps, each a red (i+j+k even) then a black
+ * half sweep, in place on u.  fp32 != 0 runs the FP32 smoother on float copies
+ * (u32, b32 device float [N]) instead of u, b. */
+int lasto_op_smooth(const int n[3], const double* x, const double* y, const double* z, double* u,
+                    const double* b, int sweeps, void* stream);
+int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const double* z, float* u,
+                        const float* b, int sweeps, void* stream);
+
+/* Full weighting bc = Vc^-1 P^T Vf r onto the every-other-node mesh; bc device
+ * [(n0+1)/2 * (n1+1)/2 * (n2+1)/2], faces set to 0.  x, y, z are the fine axes. */
+int lasto_op_restrict(const int n[3], const double* x, const double* y, const double* z, const double* r,
+                      double* bc, void* stream);
+
+/* u += P ec on fine interior nodes, P = trilinear interpolation in physical
+ * coordinates; ec is the coarse field (faces are read as stored). */
+int lasto_op_prolong_add(const int n[3], const double* x, const double* y, const double* z, const double* ec,
+                         double* u, void* stream);
+
+/* Exact solve A e = b on a grid of at most 9 nodes per axis with zero faces (fast
+ * diagonalisation of the three 1-D operators).  e faces set to 0. */
+int lasto_op_coarse_solve(const int n[3], const double* x, const double* y, const double* z, const double* b,
+                          double* e, void* stream);
+
+/* V_LM(R_i) of Eq. 3.6 for n_atoms spheres: n_theta Gauss-Legendre points in
+ * cos(theta) x n_phi uniform phi; trilinear interpolation of u in physical
+ * coordinates.  vlm device [n_atoms][25].  status: GEOMETRY if a surface point
+ * leaves the box. */
+int lasto_op_project(const int n[3], const double* x, const double* y, const double* z, const double* u,
+                     int n_atoms, const double* pos, const double* R, int n_theta, int n_phi, double* vlm,
+                     int* status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

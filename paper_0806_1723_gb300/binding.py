@@ -1,0 +1,302 @@
+"""ctypes binding of ``liblasto_poisson.so`` with the C ABI's names.
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Device memory and streams come from PyTorch; pointers are passed as
+plain integers.  The library must be built (``build.build()``) and a CUDA
+device present: there is no CPU path, and loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+LASTO_OK, LASTO_ERR_INVALID_ARG, LASTO_ERR_GEOMETRY, LASTO_ERR_NONFINITE = 0, 1, 2, 3
+LASTO_ERR_NOT_CONVERGED, LASTO_ERR_TIMEOUT, LASTO_ERR_CUDA, LASTO_ERR_NO_MEMORY = 4, 5, 6, 7
+LASTO_PREC_FP64, LASTO_PREC_MIXED = 0, 1
+LASTO_CYCLE_V, LASTO_CYCLE_FV, LASTO_CYCLE_PCG = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "GEOMETRY", 3: "NONFINITE", 4: "NOT_CONVERGED", 5: "TIMEOUT",
+                6: "CUDA", 7: "NO_MEMORY"}
+
+_P = ctypes.c_void_p
+
+
+class lasto_config(ctypes.Structure):
+    _fields_ = [("n_max", ctypes.c_int), ("max_atoms", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("precision", ctypes.c_int), ("cycle", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("rel_tol", ctypes.c_double), ("n_theta", ctypes.c_int),
+                ("n_phi", ctypes.c_int)]
+
+
+class lasto_cluster(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("pos", _P), ("Z", _P), ("R", _P), ("slater_w", _P),
+                ("slater_zeta", _P), ("c_lm", _P), ("n", ctypes.c_int * 3), ("x", _P), ("y", _P), ("z", _P),
+                ("centre", ctypes.c_double * 3)]
+
+
+class lasto_stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_resid", ctypes.c_double),
+                ("bnorm", ctypes.c_double)]
+
+
+EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve", "lasto_poisson_destroy",
+           "lasto_poisson_last_error", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
+           "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
+           "lasto_op_smooth_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
+           "lasto_op_project"]
+
+_lib = None
+
+
+def _declare(L):
+    i, d, vp = ctypes.c_int, ctypes.c_double, _P
+    ip = ctypes.POINTER(ctypes.c_int)
+    cfgp, clp, stp = ctypes.POINTER(lasto_config), ctypes.POINTER(lasto_cluster), ctypes.POINTER(lasto_stats)
+    sig = {
+        "lasto_config_default": (None, [cfgp]),
+        "lasto_poisson_create": (i, [cfgp, ctypes.POINTER(vp)]),
+        "lasto_poisson_solve": (i, [vp, clp, i, vp, vp, vp, stp, vp]),
+        "lasto_poisson_destroy": (None, [vp]),
+        "lasto_poisson_last_error": (ctypes.c_char_p, [vp]),
+        "lasto_mesh_axis": (i, [i, d, d, d, d, d, vp, vp, vp]),
+        "lasto_op_sphere_params": (i, [clp, vp, vp, vp, vp, vp, vp]),
+        "lasto_op_deposit": (i, [clp, i, vp, vp, vp, vp]),
+        "lasto_op_multipoles": (i, [ip, vp, vp, vp, vp, ctypes.POINTER(d), vp, vp]),
+        "lasto_op_boundary_fill": (i, [ip, vp, vp, vp, ctypes.POINTER(d), vp, vp, vp]),
+        "lasto_op_apply": (i, [ip, vp, vp, vp, vp, vp, vp]),
+        "lasto_op_residual": (i, [ip, vp, vp, vp, vp, vp, vp, vp]),
+        "lasto_op_smooth": (i, [ip, vp, vp, vp, vp, vp, i, vp]),
+        "lasto_op_smooth_f32": (i, [ip, vp, vp, vp, vp, vp, i, vp]),
+        "lasto_op_restrict": (i, [ip, vp, vp, vp, vp, vp, vp]),
+        "lasto_op_prolong_add": (i, [ip, vp, vp, vp, vp, vp, vp]),
+        "lasto_op_coarse_solve": (i, [ip, vp, vp, vp, vp, vp, vp]),
+        "lasto_op_project": (i, [ip, vp, vp, vp, vp, i, vp, vp, i, i, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it is missing or no CUDA device is visible."""
+    global _lib
+    if _lib is None:
+        if build_if_needed:
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library not built: {_build.LIB}")
+        _lib = ctypes.CDLL(_build.LIB)
+        _declare(_lib)
+    return _lib
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+# ------------------------------------------------------------------ marshalling helpers
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors, contiguous"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _n3(n):
+    return (ctypes.c_int * 3)(*[int(v) for v in n])
+
+
+def _check(st, what):
+    if st != LASTO_OK:
+        raise RuntimeError(f"{what} failed: {STATUS_NAMES.get(st, st)}")
+
+
+def lasto_config_default() -> lasto_config:
+    c = lasto_config()
+    load().lasto_config_default(ctypes.byref(c))
+    return c
+
+
+def lasto_mesh_axis(n, centre, half_width, h_min, h_max, p_max=6.0, device="cuda", stream=None, info=False):
+    x = torch.empty(n, dtype=torch.float64, device=device)
+    inf = torch.empty(5, dtype=torch.float64, device=device) if info else None
+    st = load().lasto_mesh_axis(int(n), float(centre), float(half_width), float(h_min), float(h_max), float(p_max),
+                                _ptr(x), _ptr(inf), _stream(stream))
+    _check(st, "lasto_mesh_axis")
+    return (x, inf) if info else x
+
+
+class DeviceCluster:
+    """A cluster's arrays on the device plus its mesh axes built by ``lasto_mesh_axis``."""
+
+    def __init__(self, cl, device="cuda", stream=None, axes=None):
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(device)
+        self.src = cl
+        self.n_atoms = int(cl.pos.shape[0])
+        self.pos, self.Z, self.R = f(cl.pos), f(cl.Z), f(cl.R)
+        self.w, self.zeta, self.clm = f(cl.slater_w), f(cl.slater_zeta), f(cl.c_lm)
+        self.n = (int(cl.n),) * 3
+        self.centre = tuple(float(c) for c in cl.centre)
+        if axes is None:
+            axes = [lasto_mesh_axis(cl.n, self.centre[a], cl.half_width, cl.h_min, cl.h_max, cl.p_max, device, stream)
+                    for a in range(3)]
+        else:
+            axes = [f(a) for a in axes]
+        self.x, self.y, self.z = axes
+
+    def struct(self) -> lasto_cluster:
+        c = lasto_cluster()
+        c.n_atoms = self.n_atoms
+        c.pos, c.Z, c.R = _ptr(self.pos), _ptr(self.Z), _ptr(self.R)
+        c.slater_w, c.slater_zeta, c.c_lm = _ptr(self.w), _ptr(self.zeta), _ptr(self.clm)
+        c.n = _n3(self.n)
+        c.x, c.y, c.z = _ptr(self.x), _ptr(self.y), _ptr(self.z)
+        c.centre = (ctypes.c_double * 3)(*self.centre)
+        return c
+
+    @property
+    def N(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+
+class Poisson:
+    """Owns one ``lasto_poisson`` handle."""
+
+    def __init__(self, n_max=129, max_atoms=561, max_batch=1, precision=LASTO_PREC_FP64, cycle=LASTO_CYCLE_PCG,
+                 nu1=2, nu2=2, max_cycles=50, rel_tol=1e-10, n_theta=16, n_phi=32):
+        L = load()
+        cfg = lasto_config_default()
+        cfg.n_max, cfg.max_atoms, cfg.max_batch = n_max, max_atoms, max_batch
+        cfg.precision, cfg.cycle, cfg.nu1, cfg.nu2 = precision, cycle, nu1, nu2
+        cfg.max_cycles, cfg.rel_tol, cfg.n_theta, cfg.n_phi = max_cycles, rel_tol, n_theta, n_phi
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        st = L.lasto_poisson_create(ctypes.byref(cfg), ctypes.byref(h))
+        _check(st, "lasto_poisson_create")
+        self.h = h
+        self._stats = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lasto_poisson_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return load().lasto_poisson_last_error(self.h).decode()
+
+    def solve(self, clusters, v_lm, potential=None, guess=None, stats=True, stream=None):
+        """Enqueue one solve of the DeviceClusters; returns the host stats array (valid after sync)."""
+        if not isinstance(clusters, (list, tuple)):
+            clusters = [clusters]
+        arr = (lasto_cluster * len(clusters))(*[c.struct() for c in clusters])
+        self._keep = (clusters, arr)
+        st_arr = (lasto_stats * len(clusters))() if stats else None
+        self._stats = st_arr
+        st = load().lasto_poisson_solve(self.h, arr, len(clusters), _ptr(v_lm), _ptr(potential), _ptr(guess),
+                                        st_arr, _stream(stream))
+        if st != LASTO_OK:
+            raise RuntimeError(f"lasto_poisson_solve failed: {STATUS_NAMES.get(st, st)}: {self.last_error()}")
+        return st_arr
+
+
+# ------------------------------------------------------------------ single operations
+def lasto_op_sphere_params(dc: DeviceCluster, stream=None):
+    na = dc.n_atoms
+    q, rhoR, drhoR = (torch.empty(na, dtype=torch.float64, device=dc.pos.device) for _ in range(3))
+    coef = torch.empty((na, 3), dtype=torch.float64, device=dc.pos.device)
+    status = torch.zeros(1, dtype=torch.int32, device=dc.pos.device)
+    c = dc.struct()
+    _check(load().lasto_op_sphere_params(ctypes.byref(c), _ptr(q), _ptr(rhoR), _ptr(drhoR), _ptr(coef),
+                                         _ptr(status), _stream(stream)), "lasto_op_sphere_params")
+    return q, rhoR, drhoR, coef, status
+
+
+def lasto_op_deposit(dc: DeviceCluster, precision=LASTO_PREC_FP64, stream=None):
+    n = dc.n
+    b = torch.empty((n[2], n[1], n[0]), dtype=torch.float64, device=dc.pos.device)
+    owner = torch.empty((n[2], n[1], n[0]), dtype=torch.int32, device=dc.pos.device)
+    status = torch.zeros(1, dtype=torch.int32, device=dc.pos.device)
+    c = dc.struct()
+    _check(load().lasto_op_deposit(ctypes.byref(c), int(precision), _ptr(b), _ptr(owner), _ptr(status),
+                                   _stream(stream)), "lasto_op_deposit")
+    return b, owner, status
+
+
+def _axes(x, y, z):
+    n = (len(x), len(y), len(z))
+    return _n3(n), _ptr(x), _ptr(y), _ptr(z)
+
+
+def lasto_op_multipoles(x, y, z, b, centre=(0.0, 0.0, 0.0), stream=None):
+    Q = torch.empty(25, dtype=torch.float64, device=b.device)
+    c = (ctypes.c_double * 3)(*centre)
+    _check(load().lasto_op_multipoles(*_axes(x, y, z), _ptr(b), c, _ptr(Q), _stream(stream)), "lasto_op_multipoles")
+    return Q
+
+
+def lasto_op_boundary_fill(x, y, z, Q, u, centre=(0.0, 0.0, 0.0), stream=None):
+    c = (ctypes.c_double * 3)(*centre)
+    _check(load().lasto_op_boundary_fill(*_axes(x, y, z), c, _ptr(Q), _ptr(u), _stream(stream)),
+           "lasto_op_boundary_fill")
+    return u
+
+
+def lasto_op_apply(x, y, z, u, stream=None):
+    out = torch.empty_like(u)
+    _check(load().lasto_op_apply(*_axes(x, y, z), _ptr(u), _ptr(out), _stream(stream)), "lasto_op_apply")
+    return out
+
+
+def lasto_op_residual(x, y, z, u, b, stream=None):
+    out = torch.empty_like(u)
+    _check(load().lasto_op_residual(*_axes(x, y, z), _ptr(u), _ptr(b), _ptr(out), _stream(stream)),
+           "lasto_op_residual")
+    return out
+
+
+def lasto_op_smooth(x, y, z, u, b, sweeps=1, stream=None):
+    fn = load().lasto_op_smooth if u.dtype == torch.float64 else load().lasto_op_smooth_f32
+    _check(fn(*_axes(x, y, z), _ptr(u), _ptr(b), int(sweeps), _stream(stream)), "lasto_op_smooth")
+    return u
+
+
+def lasto_op_restrict(x, y, z, r, stream=None):
+    bc = torch.empty(((len(z) + 1) // 2, (len(y) + 1) // 2, (len(x) + 1) // 2), dtype=torch.float64, device=r.device)
+    _check(load().lasto_op_restrict(*_axes(x, y, z), _ptr(r), _ptr(bc), _stream(stream)), "lasto_op_restrict")
+    return bc
+
+
+def lasto_op_prolong_add(x, y, z, ec, u, stream=None):
+    _check(load().lasto_op_prolong_add(*_axes(x, y, z), _ptr(ec), _ptr(u), _stream(stream)), "lasto_op_prolong_add")
+    return u
+
+
+def lasto_op_coarse_solve(x, y, z, b, stream=None):
+    e = torch.empty_like(b)
+    _check(load().lasto_op_coarse_solve(*_axes(x, y, z), _ptr(b), _ptr(e), _stream(stream)), "lasto_op_coarse_solve")
+    return e
+
+
+def lasto_op_project(x, y, z, u, pos, R, n_theta=16, n_phi=32, stream=None):
+    na = int(R.shape[0])
+    vlm = torch.empty((na, 25), dtype=torch.float64, device=u.device)
+    status = torch.zeros(1, dtype=torch.int32, device=u.device)
+    _check(load().lasto_op_project(*_axes(x, y, z), _ptr(u), na, _ptr(pos), _ptr(R), int(n_theta), int(n_phi),
+                                   _ptr(vlm), _ptr(status), _stream(stream)), "lasto_op_project")
+    return vlm, status

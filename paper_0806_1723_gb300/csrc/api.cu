@@ -1,0 +1,818 @@
+// C ABI of the GB300 LASTO interstitial Poisson step: handle, workspace, CUDA-graph
+// plan of one solve, and the single-operation entry points.
+//
+// One solve is captured once into a CUDA graph and replayed: setup (mesh tables,
+// coarse eigenvectors, sphere parameters), deposit, multipoles, faces, then a
+// conditional WHILE node whose body is one multigrid-preconditioned CG iteration (or
+// one V-cycle), and whose condition is set on the device by the convergence test, so
+// the iteration runs with no host round trip.  Then the true residual, the projection
+// and the stats.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ctl.cuh"
+#include "internal.cuh"
+
+using namespace lasto;
+
+namespace {
+
+struct Scratch {
+    void* p = nullptr;
+    cudaStream_t s;
+    explicit Scratch(size_t bytes, cudaStream_t st) : s(st)
+    {
+        if (bytes && cudaMallocAsync(&p, bytes, s) != cudaSuccess) p = nullptr;
+    }
+    ~Scratch()
+    {
+        if (p) cudaFreeAsync(p, s);
+    }
+    template <typename T>
+    T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// A bump allocator over one device pool (all pieces 256-byte aligned).
+struct Carver {
+    char* base;
+    size_t cap, off = 0;
+    bool ok = true;
+    template <typename T>
+    T* take(size_t count)
+    {
+        const size_t bytes = ((count * sizeof(T)) + 255) & ~size_t(255);
+        if (off + bytes > cap) {
+            ok = false;
+            return nullptr;
+        }
+        T* p = reinterpret_cast<T*>(base + off);
+        off += bytes;
+        return p;
+    }
+};
+
+// Everything one cluster's solve touches on the device.
+struct ClusterPlan {
+    int L = 0;
+    LevelStore lv[MAX_LEVELS];
+    double *p = nullptr, *q = nullptr, *z = nullptr;  // level-0 CG vectors (FP64)
+    double* rec = nullptr;                            // sphere records
+    double* mom = nullptr;                            // multipole scratch
+    double* part = nullptr;                           // reduction partials
+    int nparts = 0;
+    double* Q = nullptr;
+    Ctl* ctl = nullptr;
+    CoarseEig* eig = nullptr;
+    int* status = nullptr;
+    lasto_stats* stats_dev = nullptr;
+};
+
+size_t cluster_bytes(const int n[3], int n_atoms)
+{
+    // generous upper bound computed by a dry run of the carver
+    Carver c{nullptr, ~size_t(0) >> 1};
+    int nn[3] = {n[0], n[1], n[2]};
+    const int L = num_levels(nn);
+    if (L < 1) return 0;
+    for (int l = 0; l < L; l++) {
+        const size_t N = (size_t)nn[0] * nn[1] * nn[2];
+        for (int d = 0; d < 3; d++) c.take<double>(axis_pool_doubles(nn[d]));
+        c.take<double>(N);          // inv_diag
+        for (int t = 0; t < 3; t++) c.take<double>(N);
+        for (int t = 0; t < 3; t++) c.take<float>(N);
+        if (l == 0)
+            for (int t = 0; t < 3; t++) c.take<double>(N);
+        for (int d = 0; d < 3; d++) nn[d] = (nn[d] + 1) / 2;
+    }
+    c.take<double>((size_t)SPHERE_REC_DOUBLES * std::max(n_atoms, 1));
+    c.take<double>(multipole_scratch_doubles(n));
+    c.take<double>(((size_t)n[0] * n[1] * n[2] + 255) / 256 + 64);
+    c.take<double>(32);
+    c.take<Ctl>(1);
+    c.take<CoarseEig>(1);
+    c.take<int>(4);
+    c.take<lasto_stats>(1);
+    return c.off;
+}
+
+bool carve_cluster(Carver& c, const int n[3], int n_atoms, ClusterPlan& P)
+{
+    int nn[3] = {n[0], n[1], n[2]};
+    P.L = num_levels(nn);
+    if (P.L < 1) return false;
+    for (int l = 0; l < P.L; l++) {
+        LevelStore& S = P.lv[l];
+        const size_t N = (size_t)nn[0] * nn[1] * nn[2];
+        for (int d = 0; d < 3; d++) {
+            S.n[d] = nn[d];
+            double* pool = c.take<double>(axis_pool_doubles(nn[d]));
+            if (!pool) return false;
+            carve_axis(&S.ax[d], nn[d], pool);
+        }
+        S.inv_diag = c.take<double>(N);
+        S.u = c.take<double>(N);
+        S.b = c.take<double>(N);
+        S.r = c.take<double>(N);
+        S.u32 = c.take<float>(N);
+        S.b32 = c.take<float>(N);
+        S.r32 = c.take<float>(N);
+        if (l == 0) {
+            P.p = c.take<double>(N);
+            P.q = c.take<double>(N);
+            P.z = c.take<double>(N);
+        }
+        for (int d = 0; d < 3; d++) nn[d] = (nn[d] + 1) / 2;
+    }
+    P.rec = c.take<double>((size_t)SPHERE_REC_DOUBLES * std::max(n_atoms, 1));
+    P.mom = c.take<double>(multipole_scratch_doubles(n));
+    P.nparts = (int)(((size_t)n[0] * n[1] * n[2] + 255) / 256);
+    P.part = c.take<double>((size_t)P.nparts + 64);
+    P.Q = c.take<double>(32);
+    P.ctl = c.take<Ctl>(1);
+    P.eig = c.take<CoarseEig>(1);
+    P.status = c.take<int>(4);
+    P.stats_dev = c.take<lasto_stats>(1);
+    return c.ok;
+}
+
+bool valid_n(const int n[3])
+{
+    for (int d = 0; d < 3; d++)
+        if (n[d] < 3 || n[d] % 2 == 0) return false;
+    int nn[3] = {n[0], n[1], n[2]};
+    return num_levels(nn) >= 1;
+}
+
+__global__ void k_copy_interior(const double* __restrict__ src, double* __restrict__ dst, int nx, int ny, int nz)
+{
+    const size_t P = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t N = (size_t)nx * ny * nz;
+    if (P >= N) return;
+    const size_t nxy = (size_t)nx * ny;
+    const int k = (int)(P / nxy), j = (int)((P % nxy) / nx), i = (int)(P % nx);
+    if (i == 0 || j == 0 || k == 0 || i == nx - 1 || j == ny - 1 || k == nz - 1) return;
+    dst[P] = src[P];
+}
+
+__global__ void k_write_stats(const Ctl* __restrict__ ctl, const int* __restrict__ status, lasto_stats* out)
+{
+    lasto_stats s;
+    s.cycles = ctl->iter;
+    s.rel_resid = ctl->true_rel;
+    s.bnorm = ctl->bnorm;
+    s.status = status[0] != 0 ? status[0] : ctl->status;
+    *out = s;
+}
+
+}  // namespace
+
+struct lasto_poisson {
+    lasto_config cfg;
+    Err err;
+    int device = 0;
+    char* pool = nullptr;
+    size_t pool_bytes = 0;
+    double* quad = nullptr;
+    int nq = 0;
+    cudaStream_t cs = nullptr, cs2 = nullptr;
+    // cached graph
+    std::vector<char> key;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n_clusters = 0;
+    std::vector<ClusterPlan> plans;
+    lasto_stats* stats_pinned = nullptr;
+    lasto_stats* stats_user = nullptr;
+    int stats_count = 0;
+};
+
+namespace {
+
+int fail(lasto_poisson* h, int code, const std::string& msg)
+{
+    if (h) {
+        h->err.code = code;
+        h->err.msg = msg;
+    }
+    return code;
+}
+
+#define TRY(call)                                                            \
+    do {                                                                     \
+        cudaError_t c_ = (call);                                             \
+        if (c_ != cudaSuccess) return set_cuda_error(&h->err, c_, #call);    \
+    } while (0)
+
+// ---------------------------------------------------------------- cycles (enqueue only)
+template <typename T>
+struct Arr;
+template <>
+struct Arr<double> {
+    static double* u(LevelStore& s) { return s.u; }
+    static double* b(LevelStore& s) { return s.b; }
+    static double* r(LevelStore& s) { return s.r; }
+    static LevelT<double> view(const LevelStore& s) { return s.view64(); }
+};
+template <>
+struct Arr<float> {
+    static float* u(LevelStore& s) { return s.u32; }
+    static float* b(LevelStore& s) { return s.b32; }
+    static float* r(LevelStore& s) { return s.r32; }
+    static LevelT<float> view(const LevelStore& s) { return s.view32(); }
+};
+
+template <typename T>
+int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, bool fcycle, bool sym, cudaStream_t s)
+{
+    LevelStore& S = P.lv[l];
+    const LevelT<T> V = Arr<T>::view(S);
+    const int nu1 = h->cfg.nu1, nu2 = h->cfg.nu2;
+    if (l == P.L - 1) {
+        if (l == 0) {
+            TRY(launch_residual<T>(V, u, b, r, s));
+            TRY(launch_coarse_apply<T>(V, P.eig, r, u, true, s));
+        } else {
+            TRY(launch_coarse_apply<T>(V, P.eig, b, u, false, s));
+        }
+        return LASTO_OK;
+    }
+    for (int it = 0; it < nu1; it++) {
+        TRY(launch_rbgs<T>(V, u, b, 0, s));
+        TRY(launch_rbgs<T>(V, u, b, 1, s));
+    }
+    TRY(launch_residual<T>(V, u, b, r, s));
+    LevelStore& C = P.lv[l + 1];
+    const LevelT<T> VC = Arr<T>::view(C);
+    TRY(launch_restrict<T>(V, VC, r, Arr<T>::b(C), s));
+    TRY(cudaMemsetAsync(Arr<T>::u(C), 0, sizeof(T) * C.N(), s));
+    int st = enqueue_cycle<T>(h, P, l + 1, Arr<T>::u(C), Arr<T>::b(C), Arr<T>::r(C), fcycle, sym, s);
+    if (st) return st;
+    if (fcycle) {
+        st = enqueue_cycle<T>(h, P, l + 1, Arr<T>::u(C), Arr<T>::b(C), Arr<T>::r(C), false, sym, s);
+        if (st) return st;
+    }
+    TRY(launch_prolong_add<T>(V, VC, Arr<T>::u(C), u, s));
+    for (int it = 0; it < nu2; it++) {
+        TRY(launch_rbgs<T>(V, u, b, sym ? 1 : 0, s));
+        TRY(launch_rbgs<T>(V, u, b, sym ? 0 : 1, s));
+    }
+    return LASTO_OK;
+}
+
+int enqueue_setup(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, cudaStream_t s)
+{
+    // the FP64 smoother (plain preconditioner, stationary cycles) reads a stored inverse diagonal
+    const bool fp64 = h->cfg.precision == LASTO_PREC_FP64 || h->cfg.cycle != LASTO_CYCLE_PCG;
+    for (int l = 0; l < P.L; l++) {
+        const double* src[3];
+        int stride;
+        if (l == 0) {
+            src[0] = cl.x;
+            src[1] = cl.y;
+            src[2] = cl.z;
+            stride = 1;
+        } else {
+            for (int d = 0; d < 3; d++) src[d] = P.lv[l - 1].ax[d].c;
+            stride = 2;
+        }
+        TRY(launch_level_tables(P.lv[l], nullptr, src, stride, s));
+        if (fp64 && l < P.L - 1) TRY(launch_inv_diag(P.lv[l], s));
+    }
+    TRY(launch_coarse_eig(P.lv[P.L - 1], P.eig, s));
+    return LASTO_OK;
+}
+
+int enqueue_rhs(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const double* guess, cudaStream_t s)
+{
+    LevelStore& F = P.lv[0];
+    const int* n = cl.n;
+    TRY(launch_sphere_params(cl, cl.x, cl.y, cl.z, P.rec, nullptr, nullptr, nullptr, nullptr, P.status, s));
+    TRY(launch_deposit(cl, P.rec, h->cfg.precision, F.b, nullptr, nullptr, nullptr, P.status, s));
+    double* tabs = P.mom;
+    double* rowm = tabs + 5 * ((size_t)n[0] + n[1] + n[2]);
+    double* plane = rowm + 5 * (size_t)n[1] * n[2];
+    TRY(launch_multipoles(n, cl.x, cl.y, cl.z, F.b, cl.centre, tabs, rowm, plane, P.Q, s));
+    TRY(cudaMemsetAsync(F.u, 0, sizeof(double) * F.N(), s));
+    TRY(launch_boundary_fill(n, cl.x, cl.y, cl.z, cl.centre[0], cl.centre[1], cl.centre[2], P.Q, F.u, s));
+    if (guess) {
+        k_copy_interior<<<(unsigned)((F.N() + 255) / 256), 256, 0, s>>>(guess, F.u, n[0], n[1], n[2]);
+        TRY(cudaGetLastError());
+    }
+    return LASTO_OK;
+}
+
+// Prologue of the iteration: ||b_eff||, control block, F-cycle, starting residual.
+int enqueue_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s)
+{
+    LevelStore& F = P.lv[0];
+    const LevelT<double> V = F.view64();
+    const int cyc = h->cfg.cycle;
+    TRY(launch_bnorm_partials(V, F.u, F.b, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_BNORM, cond, 0, s));
+    const double tol = h->cfg.rel_tol;
+    TRY(launch_ctl_init(P.ctl, tol, cyc == LASTO_CYCLE_PCG ? 0.5 * tol : tol, h->cfg.max_cycles, s));
+    if (cyc == LASTO_CYCLE_FV) {
+        int st = enqueue_cycle<double>(h, P, 0, F.u, F.b, F.r, true, false, s);
+        if (st) return st;
+    }
+    TRY(launch_resid_norm_partials(V, F.u, F.b, F.r, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_START, cond, use_cond, s));
+    if (cyc == LASTO_CYCLE_PCG) {
+        TRY(cudaMemsetAsync(P.p, 0, sizeof(double) * F.N(), s));
+        if (h->cfg.precision == LASTO_PREC_MIXED) TRY(launch_to_f32(F.r, F.b32, F.N(), s));
+    }
+    return LASTO_OK;
+}
+
+// One iteration (the body of the WHILE node).
+int enqueue_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s)
+{
+    LevelStore& F = P.lv[0];
+    const LevelT<double> V = F.view64();
+    if (h->cfg.cycle != LASTO_CYCLE_PCG) {
+        int st = enqueue_cycle<double>(h, P, 0, F.u, F.b, F.r, false, false, s);
+        if (st) return st;
+        TRY(launch_resid_norm_partials(V, F.u, F.b, F.r, P.part, s));
+        TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_CHECK, cond, use_cond, s));
+        return LASTO_OK;
+    }
+    const bool mixed = h->cfg.precision == LASTO_PREC_MIXED;
+    int st;
+    if (mixed) {
+        TRY(cudaMemsetAsync(F.u32, 0, sizeof(float) * F.N(), s));
+        st = enqueue_cycle<float>(h, P, 0, F.u32, F.b32, F.r32, false, true, s);
+        if (st) return st;
+        TRY(launch_dot_rz<float>(V, F.r, F.u32, P.part, s));
+        TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_BETA, cond, 0, s));
+        TRY(launch_update_p<float>(V, P.ctl, F.u32, P.p, s));
+    } else {
+        TRY(cudaMemsetAsync(P.z, 0, sizeof(double) * F.N(), s));
+        st = enqueue_cycle<double>(h, P, 0, P.z, F.r, P.q, false, true, s);
+        if (st) return st;
+        TRY(launch_dot_rz<double>(V, F.r, P.z, P.part, s));
+        TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_BETA, cond, 0, s));
+        TRY(launch_update_p<double>(V, P.ctl, P.z, P.p, s));
+    }
+    TRY(launch_apply_dot(V, P.p, P.q, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_ALPHA, cond, 0, s));
+    TRY(launch_update_ur(V, P.ctl, P.p, P.q, F.u, F.r, mixed ? F.b32 : nullptr, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_CHECK, cond, use_cond, s));
+    return LASTO_OK;
+}
+
+int enqueue_finish(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, double* vlm, double* potential,
+                   cudaStream_t s)
+{
+    LevelStore& F = P.lv[0];
+    const LevelT<double> V = F.view64();
+    TRY(launch_resid_norm_partials(V, F.u, F.b, nullptr, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_TRUE, 0, 0, s));
+    TRY(launch_project(cl.n, cl.x, cl.y, cl.z, F.u, cl.n_atoms, cl.pos, cl.R, h->quad, h->nq, vlm, P.status, s));
+    if (potential) TRY(cudaMemcpyAsync(potential, F.u, sizeof(double) * F.N(), cudaMemcpyDeviceToDevice, s));
+    k_write_stats<<<1, 1, 0, s>>>(P.ctl, P.status, P.stats_dev);
+    TRY(cudaGetLastError());
+    return LASTO_OK;
+}
+
+int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,
+                  const double* guess)
+{
+    cudaStream_t s = h->cs;
+    TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    int st = LASTO_OK;
+    size_t atom_off = 0, grid_off = 0;
+    for (int c = 0; c < nc && st == LASTO_OK; c++) {
+        ClusterPlan& P = h->plans[c];
+        const lasto_cluster& cl = cls[c];
+        if ((st = (cudaMemsetAsync(P.status, 0, sizeof(int) * 4, s) == cudaSuccess) ? 0 : LASTO_ERR_CUDA)) break;
+        if ((st = enqueue_setup(h, P, cl, s))) break;
+        if ((st = enqueue_rhs(h, P, cl, guess ? guess + grid_off : nullptr, s))) break;
+        // conditional WHILE node for the iteration
+        cudaStreamCaptureStatus cstat;
+        cudaGraph_t g;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(s, &cstat, nullptr, &g, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamGetCaptureInfo"); break; }
+        cudaGraphConditionalHandle cond;
+        e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaGraphConditionalHandleCreate"); break; }
+        if ((st = enqueue_start(h, P, cond, 1, s))) break;
+        e = cudaStreamGetCaptureInfo(s, &cstat, nullptr, &g, &deps, nullptr, &ndeps);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamGetCaptureInfo"); break; }
+        alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+        std::memset(cpbuf, 0, sizeof(cpbuf));
+        cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
+        cp->type = cudaGraphNodeTypeConditional;
+        cp->conditional.handle = cond;
+        cp->conditional.type = cudaGraphCondTypeWhile;
+        cp->conditional.size = 1;
+        cudaGraphNode_t wnode;
+        e = cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, cp);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaGraphAddNode(while)"); break; }
+        cudaGraph_t body = cp->conditional.phGraph_out[0];
+        e = cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamUpdateCaptureDependencies"); break; }
+        e = cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamBeginCaptureToGraph"); break; }
+        st = enqueue_iteration(h, P, cond, 1, h->cs2);
+        cudaGraph_t bout = nullptr;
+        e = cudaStreamEndCapture(h->cs2, &bout);
+        if (st) break;
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamEndCapture(body)"); break; }
+        if ((st = enqueue_finish(h, P, cl, v_lm + NLM * atom_off, potential ? potential + grid_off : nullptr, s)))
+            break;
+        atom_off += cl.n_atoms;
+        grid_off += (size_t)cl.n[0] * cl.n[1] * cl.n[2];
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_cuda_error(&h->err, e, "cudaGraphInstantiate");
+    }
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->graph = g;
+    h->exec = ex;
+    return LASTO_OK;
+}
+
+void CUDART_CB copy_stats_out(void* arg)
+{
+    lasto_poisson* h = static_cast<lasto_poisson*>(arg);
+    if (h->stats_user) std::memcpy(h->stats_user, h->stats_pinned, sizeof(lasto_stats) * h->stats_count);
+}
+
+}  // namespace
+
+// ================================================================ ABI
+extern "C" {
+
+void lasto_config_default(lasto_config* c)
+{
+    if (!c) return;
+    c->n_max = 129;
+    c->max_atoms = 561;
+    c->max_batch = 1;
+    c->precision = LASTO_PREC_FP64;
+    c->cycle = LASTO_CYCLE_PCG;
+    c->nu1 = 2;
+    c->nu2 = 2;
+    c->max_cycles = 50;
+    c->rel_tol = 1e-10;
+    c->n_theta = 16;
+    c->n_phi = 32;
+}
+
+int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
+{
+    if (!out) return LASTO_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg) return LASTO_ERR_INVALID_ARG;
+    const int nm[3] = {cfg->n_max, cfg->n_max, cfg->n_max};
+    if (!valid_n(nm) || cfg->max_atoms < 1 || cfg->max_batch < 1 || cfg->nu1 < 0 || cfg->nu2 < 0 ||
+        cfg->nu1 + cfg->nu2 < 1 || cfg->max_cycles < 1 || cfg->max_cycles >= CTL_HIST || !(cfg->rel_tol > 0.0) ||
+        cfg->n_theta < 1 || cfg->n_theta > 32 || cfg->n_phi < 1 || cfg->n_phi > 64 ||
+        (cfg->precision != LASTO_PREC_FP64 && cfg->precision != LASTO_PREC_MIXED) ||
+        (cfg->cycle != LASTO_CYCLE_V && cfg->cycle != LASTO_CYCLE_FV && cfg->cycle != LASTO_CYCLE_PCG))
+        return LASTO_ERR_INVALID_ARG;
+    lasto_poisson* h = new (std::nothrow) lasto_poisson();
+    if (!h) return LASTO_ERR_NO_MEMORY;
+    h->cfg = *cfg;
+    cudaGetDevice(&h->device);
+    init_device_constants();
+    const size_t per = cluster_bytes(nm, cfg->max_atoms);
+    h->pool_bytes = per * (size_t)cfg->max_batch;
+    cudaError_t e = cudaMalloc(&h->pool, h->pool_bytes);
+    if (e != cudaSuccess) {
+        delete h;
+        return e == cudaErrorMemoryAllocation ? LASTO_ERR_NO_MEMORY : LASTO_ERR_CUDA;
+    }
+    h->nq = cfg->n_theta * cfg->n_phi;
+    std::vector<double> tab((size_t)h->nq * 28);
+    host_quadrature(cfg->n_theta, cfg->n_phi, tab.data());
+    e = cudaMalloc(&h->quad, sizeof(double) * tab.size());
+    if (e == cudaSuccess) e = cudaMemcpy(h->quad, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->stats_pinned, sizeof(lasto_stats) * cfg->max_batch);
+    if (e != cudaSuccess) {
+        lasto_poisson_destroy(h);
+        return LASTO_ERR_CUDA;
+    }
+    *out = h;
+    return LASTO_OK;
+}
+
+void lasto_poisson_destroy(lasto_poisson* h)
+{
+    if (!h) return;
+    if (h->cs) cudaStreamSynchronize(h->cs);
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    if (h->pool) cudaFree(h->pool);
+    if (h->quad) cudaFree(h->quad);
+    if (h->stats_pinned) cudaFreeHost(h->stats_pinned);
+    if (h->cs) cudaStreamDestroy(h->cs);
+    if (h->cs2) cudaStreamDestroy(h->cs2);
+    delete h;
+}
+
+const char* lasto_poisson_last_error(const lasto_poisson* h)
+{
+    return h ? h->err.msg.c_str() : "null handle";
+}
+
+int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,
+                        const double* guess, lasto_stats* stats, void* stream)
+{
+    if (!h) return LASTO_ERR_INVALID_ARG;
+    h->err = Err();
+    if (!cls || nc < 1 || nc > h->cfg.max_batch || !v_lm) return fail(h, LASTO_ERR_INVALID_ARG, "bad clusters/outputs");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // key of the captured graph: every pointer and size the graph bakes in
+    std::vector<char> key;
+    auto put = [&](const void* p, size_t n) {
+        const char* c = static_cast<const char*>(p);
+        key.insert(key.end(), c, c + n);
+    };
+    size_t total_atoms = 0;
+    for (int c = 0; c < nc; c++) {
+        const lasto_cluster& cl = cls[c];
+        if (!valid_n(cl.n) || cl.n[0] > h->cfg.n_max || cl.n[1] > h->cfg.n_max || cl.n[2] > h->cfg.n_max)
+            return fail(h, LASTO_ERR_INVALID_ARG, "grid size: odd, >= 3, coarsening to <= 9 nodes, <= n_max");
+        if (cl.n_atoms < 1 || cl.n_atoms > h->cfg.max_atoms || !cl.pos || !cl.Z || !cl.R || !cl.slater_w ||
+            !cl.slater_zeta || !cl.c_lm || !cl.x || !cl.y || !cl.z)
+            return fail(h, LASTO_ERR_INVALID_ARG, "cluster arrays");
+        total_atoms += cl.n_atoms;
+        put(&cl, sizeof(cl));
+    }
+    put(&v_lm, sizeof(v_lm));
+    put(&potential, sizeof(potential));
+    put(&guess, sizeof(guess));
+    put(&nc, sizeof(nc));
+    (void)total_atoms;
+    if (key != h->key || !h->exec) {
+        // carve the workspace for these clusters
+        h->plans.assign(nc, ClusterPlan());
+        Carver cv{h->pool, h->pool_bytes};
+        for (int c = 0; c < nc; c++)
+            if (!carve_cluster(cv, cls[c].n, cls[c].n_atoms, h->plans[c]))
+                return fail(h, LASTO_ERR_NO_MEMORY, "workspace too small for this batch");
+        h->key.clear();
+        int st = capture_solve(h, cls, nc, v_lm, potential, guess);
+        if (st) return st;
+        h->key = key;
+        h->n_clusters = nc;
+    }
+    cudaError_t e = cudaGraphLaunch(h->exec, s);
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaGraphLaunch");
+    if (stats) {
+        for (int c = 0; c < nc; c++) {
+            e = cudaMemcpyAsync(h->stats_pinned + c, h->plans[c].stats_dev, sizeof(lasto_stats),
+                                cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return set_cuda_error(&h->err, e, "stats copy");
+        }
+        h->stats_user = stats;
+        h->stats_count = nc;
+        e = cudaLaunchHostFunc(s, copy_stats_out, h);
+        if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaLaunchHostFunc");
+    }
+    return LASTO_OK;
+}
+
+// ---------------------------------------------------------------- mesh
+int lasto_mesh_axis(int n, double centre, double half_width, double h_min, double h_max, double p_max, double* x,
+                    double* info, void* stream)
+{
+    if (n < 3 || n % 2 == 0 || !x || !(half_width > 0.0) || !(h_min > 0.0) || !(h_max > 0.0)) return LASTO_ERR_INVALID_ARG;
+    const double m = 0.5 * (n - 1);
+    const double A = h_min * m, B = half_width - A;
+    if (B < -1e-12 * half_width) return LASTO_ERR_INVALID_ARG;
+    if (B > 1e-12 * half_width) {
+        double p = (h_max * m - A) / B;
+        double AA = A;
+        if (p > p_max) {
+            if (!(p_max > 1.0)) return LASTO_ERR_INVALID_ARG;
+            const double BB = (h_max * m - half_width) / (p_max - 1.0);
+            AA = half_width - BB;
+            p = p_max;
+        }
+        if (!(p >= 1.0) || !(AA > 0.0)) return LASTO_ERR_INVALID_ARG;
+    }
+    cudaError_t e = launch_mesh_axis(n, centre, half_width, h_min, h_max, p_max, x, info, (cudaStream_t)stream);
+    return e == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ================================================================ single operations
+namespace {
+
+// Level tables (and optional inverse diagonal) for one grid in scratch memory.
+struct OpLevel {
+    Scratch mem;
+    LevelStore S;
+    OpLevel(const int n[3], const double* x, const double* y, const double* z, bool inv, cudaStream_t s)
+        : mem(sizeof(double) * (axis_pool_doubles(n[0]) + axis_pool_doubles(n[1]) + axis_pool_doubles(n[2]) +
+                                (inv ? (size_t)n[0] * n[1] * n[2] : 0) + 64),
+              s)
+    {
+        std::memset(&S, 0, sizeof(S));
+        if (!mem.p) return;
+        double* p = mem.as<double>();
+        for (int d = 0; d < 3; d++) {
+            S.n[d] = n[d];
+            carve_axis(&S.ax[d], n[d], p);
+            p += axis_pool_doubles(n[d]);
+        }
+        S.inv_diag = inv ? p : nullptr;
+        const double* src[3] = {x, y, z};
+        launch_level_tables(S, nullptr, src, 1, s);
+        if (inv) launch_inv_diag(S, s);
+    }
+    bool ok() const { return mem.p != nullptr; }
+};
+
+int op_status(cudaError_t e) { return e == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA; }
+
+bool op_grid_ok(const int n[3], const double* x, const double* y, const double* z)
+{
+    if (!n || !x || !y || !z) return false;
+    for (int d = 0; d < 3; d++)
+        if (n[d] < 3 || n[d] % 2 == 0) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lasto_op_sphere_params(const lasto_cluster* cl, double* q, double* rhoR, double* drhoR, double* coef, int* status,
+                           void* stream)
+{
+    if (!cl || cl->n_atoms < 1 || !op_grid_ok(cl->n, cl->x, cl->y, cl->z)) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    init_device_constants();
+    Scratch rec(sizeof(double) * SPHERE_REC_DOUBLES * cl->n_atoms, s);
+    if (!rec.p) return LASTO_ERR_NO_MEMORY;
+    return op_status(launch_sphere_params(*cl, cl->x, cl->y, cl->z, rec.as<double>(), q, rhoR, drhoR, coef, status, s));
+}
+
+int lasto_op_deposit(const lasto_cluster* cl, int precision, double* b, int* owner, int* status, void* stream)
+{
+    if (!cl || !b || cl->n_atoms < 1 || !op_grid_ok(cl->n, cl->x, cl->y, cl->z)) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    init_device_constants();
+    Scratch rec(sizeof(double) * SPHERE_REC_DOUBLES * cl->n_atoms, s);
+    if (!rec.p) return LASTO_ERR_NO_MEMORY;
+    cudaError_t e = launch_sphere_params(*cl, cl->x, cl->y, cl->z, rec.as<double>(), nullptr, nullptr, nullptr,
+                                         nullptr, status, s);
+    if (e == cudaSuccess) e = launch_deposit(*cl, rec.as<double>(), precision, b, owner, nullptr, nullptr, status, s);
+    return op_status(e);
+}
+
+int lasto_op_multipoles(const int n[3], const double* x, const double* y, const double* z, const double* b,
+                        const double centre[3], double* Q, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !b || !centre || !Q) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    init_device_constants();
+    Scratch m(sizeof(double) * multipole_scratch_doubles(n), s);
+    if (!m.p) return LASTO_ERR_NO_MEMORY;
+    double* tabs = m.as<double>();
+    double* rowm = tabs + 5 * ((size_t)n[0] + n[1] + n[2]);
+    double* plane = rowm + 5 * (size_t)n[1] * n[2];
+    return op_status(launch_multipoles(n, x, y, z, b, centre, tabs, rowm, plane, Q, s));
+}
+
+int lasto_op_boundary_fill(const int n[3], const double* x, const double* y, const double* z, const double centre[3],
+                           const double* Q, double* u, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !centre || !Q || !u) return LASTO_ERR_INVALID_ARG;
+    init_device_constants();
+    return op_status(launch_boundary_fill(n, x, y, z, centre[0], centre[1], centre[2], Q, u, (cudaStream_t)stream));
+}
+
+int lasto_op_apply(const int n[3], const double* x, const double* y, const double* z, const double* u, double* Au,
+                   void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !u || !Au) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, false, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    return op_status(launch_apply<double>(L.S.view64(), u, Au, s));
+}
+
+int lasto_op_residual(const int n[3], const double* x, const double* y, const double* z, const double* u,
+                      const double* b, double* r, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !u || !b || !r) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, false, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    return op_status(launch_residual<double>(L.S.view64(), u, b, r, s));
+}
+
+int lasto_op_smooth(const int n[3], const double* x, const double* y, const double* z, double* u, const double* b,
+                    int sweeps, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !u || !b || sweeps < 0) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, true, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < sweeps && e == cudaSuccess; it++) {
+        e = launch_rbgs<double>(L.S.view64(), u, b, 0, s);
+        if (e == cudaSuccess) e = launch_rbgs<double>(L.S.view64(), u, b, 1, s);
+    }
+    return op_status(e);
+}
+
+int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const double* z, float* u, const float* b,
+                        int sweeps, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !u || !b || sweeps < 0) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, false, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < sweeps && e == cudaSuccess; it++) {
+        e = launch_rbgs<float>(L.S.view32(), u, b, 0, s);
+        if (e == cudaSuccess) e = launch_rbgs<float>(L.S.view32(), u, b, 1, s);
+    }
+    return op_status(e);
+}
+
+int lasto_op_restrict(const int n[3], const double* x, const double* y, const double* z, const double* r, double* bc,
+                      void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !r || !bc || n[0] < 5 || n[1] < 5 || n[2] < 5) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, false, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    LevelT<double> C = L.S.view64();
+    C.nx = (n[0] + 1) / 2;
+    C.ny = (n[1] + 1) / 2;
+    C.nz = (n[2] + 1) / 2;
+    return op_status(launch_restrict<double>(L.S.view64(), C, r, bc, s));
+}
+
+int lasto_op_prolong_add(const int n[3], const double* x, const double* y, const double* z, const double* ec,
+                         double* u, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !ec || !u || n[0] < 5 || n[1] < 5 || n[2] < 5) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, false, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    LevelT<double> C = L.S.view64();
+    C.nx = (n[0] + 1) / 2;
+    C.ny = (n[1] + 1) / 2;
+    C.nz = (n[2] + 1) / 2;
+    return op_status(launch_prolong_add<double>(L.S.view64(), C, ec, u, s));
+}
+
+int lasto_op_coarse_solve(const int n[3], const double* x, const double* y, const double* z, const double* b,
+                          double* e, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !b || !e || n[0] > MAX_COARSE || n[1] > MAX_COARSE || n[2] > MAX_COARSE)
+        return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, false, s);
+    Scratch eig(sizeof(CoarseEig), s);
+    if (!L.ok() || !eig.p) return LASTO_ERR_NO_MEMORY;
+    cudaError_t er = launch_coarse_eig(L.S, eig.as<CoarseEig>(), s);
+    if (er == cudaSuccess) er = launch_coarse_apply<double>(L.S.view64(), eig.as<CoarseEig>(), b, e, false, s);
+    return op_status(er);
+}
+
+int lasto_op_project(const int n[3], const double* x, const double* y, const double* z, const double* u, int n_atoms,
+                     const double* pos, const double* R, int n_theta, int n_phi, double* vlm, int* status,
+                     void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !u || n_atoms < 0 || (n_atoms > 0 && (!pos || !R || !vlm)) || n_theta < 1 ||
+        n_theta > 32 || n_phi < 1 || n_phi > 64)
+        return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nq = n_theta * n_phi;
+    std::vector<double> tab((size_t)nq * 28);
+    host_quadrature(n_theta, n_phi, tab.data());
+    Scratch q(sizeof(double) * tab.size(), s);
+    if (!q.p) return LASTO_ERR_NO_MEMORY;
+    cudaError_t e = cudaMemcpyAsync(q.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = launch_project(n, x, y, z, u, n_atoms, pos, R, q.as<double>(), nq, vlm, status, s);
+    return op_status(e);
+}
+
+}  // extern "C"

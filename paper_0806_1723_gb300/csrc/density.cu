@@ -1,0 +1,553 @@
+// Right-hand side of the interstitial Poisson problem: per-sphere pseudo-density,
+// deposit on the mesh, boundary multipoles and Dirichlet face values.
+//
+// Section 1 of the paper: the rapidly varying density inside each sphere is replaced
+// by a smooth pseudo-density with the same multipole moments (nucleus included); only
+// the monopole is replaced, the nonspherical terms go on the grid as they are.
+// Section 3 (constraints beside Eq. 3.2-3.3): same charge inside the sphere, same
+// value and slope at R.  Reading of the shape: rho_tilde = a + b r^2 + c r^4.
+//
+// GPU formulation.  With the same three Slater exponents on every atom, the spherical
+// average of the neighbours' Slater terms about sphere i factorises into
+//   N_i(r) = sum_k [ 2 A_ik sinh(zeta_k r)/r - 2 B_ik cosh(zeta_k r) ],
+//   A_ik = sum_{j != i} W_jk e^{-zeta_k D_ij} (1 + zeta_k D_ij) / (2 D_ij zeta_k^2),
+//   B_ik = sum_{j != i} W_jk e^{-zeta_k D_ij} / (2 D_ij zeta_k),
+// (W = w zeta^3 / 8 pi), so a node inside sphere i costs three exponentials instead
+// of one average per neighbour, and the sphere charge integrals are closed forms.
+// Inside sphere i the deposit evaluates n_e - rho0_i + rho_tilde_i as
+//   (neighbours' Slater terms at the node) - N_i(r) + rho_ns,i(x) + rho_tilde_i(r),
+// the atom's own spherical terms cancelling exactly rather than numerically.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace lasto {
+
+// ---------------------------------------------------------------- harmonics table
+static __constant__ Mono c_mono[N_MONO_TERMS];
+
+void host_monomials(Mono* o)
+{
+    const double pi = PI;
+    const double c0 = 0.5 / std::sqrt(pi), c1 = std::sqrt(3.0 / (4 * pi));
+    const double c2a = 0.5 * std::sqrt(15 / pi), c2b = 0.25 * std::sqrt(5 / pi), c2c = 0.25 * std::sqrt(15 / pi);
+    const double c3a = 0.25 * std::sqrt(35 / (2 * pi)), c3b = 0.5 * std::sqrt(105 / pi), c3c = 0.25 * std::sqrt(21 / (2 * pi));
+    const double c3d = 0.25 * std::sqrt(7 / pi), c3e = 0.25 * std::sqrt(105 / pi);
+    const double c4a = 0.75 * std::sqrt(35 / pi), c4b = 0.75 * std::sqrt(35 / (2 * pi)), c4c = 0.75 * std::sqrt(5 / pi);
+    const double c4d = 0.75 * std::sqrt(5 / (2 * pi)), c4e = (3.0 / 16) / std::sqrt(pi), c4f = 0.375 * std::sqrt(5 / pi);
+    const double c4g = (3.0 / 16) * std::sqrt(35 / pi);
+    const Mono t[N_MONO_TERMS] = {
+        {0, 0, 0, 0, c0},
+        {1, 0, 1, 0, c1}, {2, 0, 0, 1, c1}, {3, 1, 0, 0, c1},
+        {4, 1, 1, 0, c2a}, {5, 0, 1, 1, c2a},
+        {6, 0, 0, 2, 2 * c2b}, {6, 2, 0, 0, -c2b}, {6, 0, 2, 0, -c2b},
+        {7, 1, 0, 1, c2a}, {8, 2, 0, 0, c2c}, {8, 0, 2, 0, -c2c},
+        {9, 2, 1, 0, 3 * c3a}, {9, 0, 3, 0, -c3a},
+        {10, 1, 1, 1, c3b},
+        {11, 0, 1, 2, 4 * c3c}, {11, 2, 1, 0, -c3c}, {11, 0, 3, 0, -c3c},
+        {12, 0, 0, 3, 2 * c3d}, {12, 2, 0, 1, -3 * c3d}, {12, 0, 2, 1, -3 * c3d},
+        {13, 1, 0, 2, 4 * c3c}, {13, 3, 0, 0, -c3c}, {13, 1, 2, 0, -c3c},
+        {14, 2, 0, 1, c3e}, {14, 0, 2, 1, -c3e},
+        {15, 3, 0, 0, c3a}, {15, 1, 2, 0, -3 * c3a},
+        {16, 3, 1, 0, c4a}, {16, 1, 3, 0, -c4a},
+        {17, 2, 1, 1, 3 * c4b}, {17, 0, 3, 1, -c4b},
+        {18, 1, 1, 2, 6 * c4c}, {18, 3, 1, 0, -c4c}, {18, 1, 3, 0, -c4c},
+        {19, 0, 1, 3, 4 * c4d}, {19, 2, 1, 1, -3 * c4d}, {19, 0, 3, 1, -3 * c4d},
+        {20, 0, 0, 4, 8 * c4e}, {20, 4, 0, 0, 3 * c4e}, {20, 0, 4, 0, 3 * c4e},
+        {20, 2, 2, 0, 6 * c4e}, {20, 2, 0, 2, -24 * c4e}, {20, 0, 2, 2, -24 * c4e},
+        {21, 1, 0, 3, 4 * c4d}, {21, 3, 0, 1, -3 * c4d}, {21, 1, 2, 1, -3 * c4d},
+        {22, 2, 0, 2, 6 * c4f}, {22, 0, 2, 2, -6 * c4f}, {22, 4, 0, 0, -c4f}, {22, 0, 4, 0, c4f},
+        {23, 3, 0, 1, c4b}, {23, 1, 2, 1, -3 * c4b},
+        {24, 4, 0, 0, c4g}, {24, 2, 2, 0, -6 * c4g}, {24, 0, 4, 0, c4g},
+    };
+    for (int i = 0; i < N_MONO_TERMS; i++) o[i] = t[i];
+}
+
+void host_solid_harmonics(double x, double y, double z, double* S)
+{
+    Mono t[N_MONO_TERMS];
+    host_monomials(t);
+    double px[5] = {1, x, x * x, x * x * x, x * x * x * x}, py[5] = {1, y, y * y, y * y * y, y * y * y * y},
+           pz[5] = {1, z, z * z, z * z * z, z * z * z * z};
+    for (int q = 0; q < NLM; q++) S[q] = 0.0;
+    for (int i = 0; i < N_MONO_TERMS; i++) S[t[i].lm] += t[i].coef * px[t[i].a] * py[t[i].b] * pz[t[i].c];
+}
+
+static int g_mono_uploaded_device = -1;
+static cudaError_t ensure_monomials()
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (g_mono_uploaded_device == dev) return cudaSuccess;
+    Mono t[N_MONO_TERMS];
+    host_monomials(t);
+    e = cudaMemcpyToSymbol(c_mono, t, sizeof(t));
+    if (e == cudaSuccess) g_mono_uploaded_device = dev;
+    return e;
+}
+
+__device__ __forceinline__ void solid_harmonics(double x, double y, double z, double* S)
+{
+    double px[5], py[5], pz[5];
+    px[0] = py[0] = pz[0] = 1.0;
+#pragma unroll
+    for (int p = 1; p < 5; p++) {
+        px[p] = px[p - 1] * x;
+        py[p] = py[p - 1] * y;
+        pz[p] = pz[p - 1] * z;
+    }
+#pragma unroll
+    for (int q = 0; q < NLM; q++) S[q] = 0.0;
+#pragma unroll
+    for (int t = 0; t < N_MONO_TERMS; t++) {
+        const Mono m = c_mono[t];
+        S[m.lm] = fma(m.coef, px[m.a] * py[m.b] * pz[m.c], S[m.lm]);
+    }
+}
+
+// ---------------------------------------------------------------- sphere records
+// rec[i][*]: 0-2 pos, 3 R, 4-6 W_k, 7-9 zeta_k, 10-12 A_k, 13-15 B_k, 16-18 (a, b, c),
+// 19 q, 20 rho0(R), 21 rho0'(R)
+enum { RX = 0, RR = 3, RW = 4, RZ = 7, RA = 10, RB = 13, RC = 16, RQ = 19, RRHO = 20, RDRHO = 21 };
+
+struct SphArgs {
+    int na;
+    const double *pos, *Z, *R, *w, *zeta;
+    const double* ax[3];
+    int n[3];
+    double* rec;
+    double *q, *rhoR, *drhoR, *coef;
+    int* status;
+};
+
+constexpr int SPH_NT = 128;
+
+__global__ void __launch_bounds__(SPH_NT) k_sphere_params(SphArgs a)
+{
+    __shared__ double sm[32];
+    __shared__ double red[6];
+    __shared__ int bad_geom, bad_zeta;
+    const int i = blockIdx.x;
+    if (threadIdx.x == 0) bad_geom = bad_zeta = 0;
+    __syncthreads();
+    const double xi = a.pos[3 * i], yi = a.pos[3 * i + 1], zi = a.pos[3 * i + 2], Ri = a.R[i];
+    double zt[3];
+    for (int k = 0; k < 3; k++) zt[k] = a.zeta[3 * i + k];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = threadIdx.x; j < a.na; j += SPH_NT) {
+        if (j == i) continue;
+        const double dx = a.pos[3 * j] - xi, dy = a.pos[3 * j + 1] - yi, dz = a.pos[3 * j + 2] - zi;
+        const double D = sqrt(dx * dx + dy * dy + dz * dz);
+        if (!(D >= Ri + a.R[j])) bad_geom = 1;
+        for (int k = 0; k < 3; k++) {
+            const double z = a.zeta[3 * j + k];
+            if (z != zt[k]) bad_zeta = 1;
+            const double W = a.w[3 * j + k] * z * z * z / (8.0 * PI);
+            const double e = exp(-z * D);
+            acc[k] += W * e * (1.0 + z * D) / (2.0 * D * z * z);
+            acc[3 + k] += W * e / (2.0 * D * z);
+        }
+    }
+    for (int v = 0; v < 6; v++) {
+        const double s = block_sum<SPH_NT>(acc[v], sm);
+        if (threadIdx.x == 0) red[v] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // the sphere must sit two nodes inside every face
+    for (int d = 0; d < 3; d++) {
+        const double c = a.pos[3 * i + d];
+        if (!(c - Ri >= a.ax[d][2] && c + Ri <= a.ax[d][a.n[d] - 3])) bad_geom = 1;
+    }
+    double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * i;
+    r[RX] = xi;
+    r[RX + 1] = yi;
+    r[RX + 2] = zi;
+    r[RR] = Ri;
+    double rho = 0.0, drho = 0.0, inside = 0.0;
+    for (int k = 0; k < 3; k++) {
+        const double z = zt[k], wk = a.w[3 * i + k];
+        const double W = wk * z * z * z / (8.0 * PI);
+        const double A = red[k], B = red[3 + k];
+        r[RW + k] = W;
+        r[RZ + k] = z;
+        r[RA + k] = A;
+        r[RB + k] = B;
+        const double zR = z * Ri, eR = exp(-zR), sh = sinh(zR), ch = cosh(zR);
+        rho += W * eR + 2.0 * A * sh / Ri - 2.0 * B * ch;
+        drho += -z * W * eR + 2.0 * A * (z * ch / Ri - sh / (Ri * Ri)) - 2.0 * B * z * sh;
+        // electrons inside the sphere: own normalised Slater term + neighbour averages
+        const double own = wk * (1.0 - eR * (1.0 + zR + 0.5 * zR * zR));
+        const double I1 = Ri * ch / z - sh / (z * z);                                   // int r sinh
+        const double I2 = Ri * Ri * sh / z - 2.0 * Ri * ch / (z * z) + 2.0 * sh / (z * z * z);  // int r^2 cosh
+        inside += own + 4.0 * PI * (2.0 * A * I1 - 2.0 * B * I2);
+    }
+    const double q = inside - a.Z[i];
+    const double Qr = q / (4.0 * PI);
+    const double R2 = Ri * Ri, R3 = R2 * Ri, R4 = R2 * R2, R7 = R4 * R3;
+    const double cc = (Qr - rho * R3 / 3.0 + drho * R4 / 15.0) * (105.0 / (8.0 * R7));
+    const double bb = drho / (2.0 * Ri) - 2.0 * cc * R2;
+    const double aa = rho - 0.5 * drho * Ri + cc * R4;
+    r[RC] = aa;
+    r[RC + 1] = bb;
+    r[RC + 2] = cc;
+    r[RQ] = q;
+    r[RRHO] = rho;
+    r[RDRHO] = drho;
+    if (a.q) a.q[i] = q;
+    if (a.rhoR) a.rhoR[i] = rho;
+    if (a.drhoR) a.drhoR[i] = drho;
+    if (a.coef) {
+        a.coef[3 * i] = aa;
+        a.coef[3 * i + 1] = bb;
+        a.coef[3 * i + 2] = cc;
+    }
+    if (a.status) {
+        if (bad_zeta) atomicMax(a.status, (int)LASTO_ERR_INVALID_ARG);
+        if (bad_geom) atomicMax(a.status, (int)LASTO_ERR_GEOMETRY);
+    }
+}
+
+cudaError_t launch_sphere_params(const lasto_cluster& cl, const double* ax0, const double* ax1, const double* ax2,
+                                 double* rec, double* q, double* rhoR, double* drhoR, double* coef, int* status,
+                                 cudaStream_t s)
+{
+    SphArgs a;
+    a.na = cl.n_atoms;
+    a.pos = cl.pos;
+    a.Z = cl.Z;
+    a.R = cl.R;
+    a.w = cl.slater_w;
+    a.zeta = cl.slater_zeta;
+    a.ax[0] = ax0;
+    a.ax[1] = ax1;
+    a.ax[2] = ax2;
+    for (int d = 0; d < 3; d++) a.n[d] = cl.n[d];
+    a.rec = rec;
+    a.q = q;
+    a.rhoR = rhoR;
+    a.drhoR = drhoR;
+    a.coef = coef;
+    a.status = status;
+    k_sphere_params<<<cl.n_atoms, SPH_NT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- deposit (FP64)
+struct DepArgs {
+    int na;
+    int n[3];
+    const double* ax[3];
+    const double* rec;
+    const double* clm;
+    double* b;
+    int* owner;
+    int* status;
+};
+
+// per-atom fields staged in shared memory
+constexpr int SA = 14;  // x y z R^2 W0 W1 W2 A0 A1 A2 B0 B1 B2 R
+constexpr int DEP_NT = 256;
+constexpr double EXP_CUT = 40.0;   // e^{-40} * max W < 1e-14 absolute; skipped terms are below FP64 rounding of n_e
+
+__device__ __forceinline__ double nonspherical(const double* __restrict__ c, double dx, double dy, double dz,
+                                               double r, double R, double z1)
+{
+    double S[NLM];
+    solid_harmonics(dx, dy, dz, S);
+    const double iR = 1.0 / R;
+    double ang = 0.0, Rl = iR;
+    int l = 1;
+    for (int lm = 1; lm < NLM; lm++) {
+        const int ll = l_of_lm(lm);
+        if (ll != l) {
+            Rl *= iR;
+            l = ll;
+        }
+        ang = fma(c[lm - 1] * Rl, S[lm], ang);
+    }
+    const double t = 1.0 - r * r * iR * iR;
+    return z1 * z1 * z1 / (8.0 * PI) * exp(-z1 * r) * t * t * ang;
+}
+
+__global__ void __launch_bounds__(DEP_NT) k_deposit64(DepArgs a)
+{
+    extern __shared__ double sat[];
+    // the exponents are the same on every atom (checked by the sphere kernel): take atom 0's
+    const double z0 = a.rec[RZ], z1 = a.rec[RZ + 1], z2 = a.rec[RZ + 2];
+    for (int t = threadIdx.x; t < a.na; t += DEP_NT) {
+        const double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * t;
+        double* o = sat + SA * t;
+        o[0] = r[RX];
+        o[1] = r[RX + 1];
+        o[2] = r[RX + 2];
+        o[3] = r[RR] * r[RR];
+        for (int k = 0; k < 3; k++) {
+            o[4 + k] = r[RW + k];
+            o[7 + k] = r[RA + k];
+            o[10 + k] = r[RB + k];
+        }
+        o[13] = r[RR];
+    }
+    __syncthreads();
+    const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
+    const size_t P = blockIdx.x * (size_t)DEP_NT + threadIdx.x;
+    if (P >= N) return;
+    const size_t nxy = (size_t)a.n[0] * a.n[1];
+    const int k = (int)(P / nxy);
+    const int j = (int)((P - (size_t)k * nxy) / a.n[0]);
+    const int i = (int)(P - (size_t)k * nxy - (size_t)j * a.n[0]);
+    const double x = a.ax[0][i], y = a.ax[1][j], z = a.ax[2][k];
+    const double zz[3] = {z0, z1, z2};
+    double s = 0.0;
+    int own = -1;
+    double ox = 0, oy = 0, oz = 0, or2 = 0;
+    for (int t = 0; t < a.na; t++) {
+        const double* o = sat + SA * t;
+        const double dx = x - o[0], dy = y - o[1], dz = z - o[2];
+        const double r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+        if (r2 < o[3]) {
+            own = t;
+            ox = dx;
+            oy = dy;
+            oz = dz;
+            or2 = r2;
+            continue;
+        }
+        const double r = sqrt(r2);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const double e = zz[q] * r;
+            if (e < EXP_CUT) s = fma(o[4 + q], exp(-e), s);
+        }
+    }
+    if (own >= 0) {
+        const double* o = sat + SA * own;
+        const double* rc = a.rec + (size_t)SPHERE_REC_DOUBLES * own;
+        const double r = sqrt(or2);
+        double nbr = 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const double zr = zz[q] * r;
+            const double shr = (zr > 1e-6) ? sinh(zr) / r : zz[q] * (1.0 + zr * zr / 6.0);
+            nbr += 2.0 * o[7 + q] * shr - 2.0 * o[10 + q] * cosh(zr);
+        }
+        const double pseudo = fma(fma(rc[RC + 2], or2, rc[RC + 1]), or2, rc[RC]);
+        const double ns = nonspherical(a.clm + 24 * (size_t)own, ox, oy, oz, r, o[13], z0);
+        s = s - nbr + ns + pseudo;
+    }
+    const double bv = 4.0 * PI * s;
+    a.b[P] = bv;
+    if (a.owner) a.owner[P] = own;
+    if (!isfinite(bv) && a.status) atomicMax(a.status, (int)LASTO_ERR_NONFINITE);
+}
+
+
+cudaError_t launch_deposit(const lasto_cluster& cl, const double* rec, int precision, double* b, int* owner,
+                           const double* /*xm_tab*/, double* /*row_mom*/, int* status, cudaStream_t s)
+{
+    cudaError_t e = ensure_monomials();
+    if (e != cudaSuccess) return e;
+    DepArgs a;
+    a.na = cl.n_atoms;
+    for (int d = 0; d < 3; d++) a.n[d] = cl.n[d];
+    a.ax[0] = cl.x;
+    a.ax[1] = cl.y;
+    a.ax[2] = cl.z;
+    a.rec = rec;
+    a.clm = cl.c_lm;
+    a.b = b;
+    a.owner = owner;
+    a.status = status;
+    const size_t N = (size_t)cl.n[0] * cl.n[1] * cl.n[2];
+    const size_t smem = sizeof(double) * SA * (size_t)cl.n_atoms;
+    (void)precision;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    k_deposit64<<<(unsigned)((N + DEP_NT - 1) / DEP_NT), DEP_NT, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+void init_device_constants()
+{
+    static int done_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev == done_dev) return;
+    ensure_monomials();
+    cudaFuncSetAttribute(k_deposit64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    done_dev = dev;
+}
+
+// ---------------------------------------------------------------- boundary multipoles
+// Q_lm = sum (b/4pi) vol S_lm(node - centre).  S_lm is a polynomial of degree l in
+// (x, y, z) and vol a product of per-axis dual lengths, so the sum factorises:
+// per-row x-moments (5 FMAs per node), then y and z contractions over the rows,
+// then the monomial expansion of each S_lm.
+constexpr int MOM_NT = 128;
+
+// xm[a][i] = (x_i - cx)^a * dual_i, a = 0..4
+__global__ void k_moment_table(const double* __restrict__ x, int n, double c, double* __restrict__ tab)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dual = (i == 0) ? 0.5 * (x[1] - x[0]) : (i == n - 1) ? 0.5 * (x[n - 1] - x[n - 2])
+                                                                  : 0.5 * (x[i + 1] - x[i - 1]);
+    const double d = x[i] - c;
+    double p = dual;
+    for (int a = 0; a < 5; a++) {
+        tab[(size_t)a * n + i] = p;
+        p *= d;
+    }
+}
+
+// row_mom[a][row] = sum_i xm[a][i] b[row, i],  row = k*ny + j
+__global__ void __launch_bounds__(MOM_NT) k_row_moments(const double* __restrict__ b, int nx, size_t nrows,
+                                                       const double* __restrict__ xm, double* __restrict__ row_mom)
+{
+    __shared__ double sm[32];
+    const size_t row = blockIdx.x;
+    const double* br = b + row * nx;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < nx; i += MOM_NT) {
+        const double v = br[i];
+#pragma unroll
+        for (int q = 0; q < 5; q++) acc[q] = fma(xm[(size_t)q * nx + i], v, acc[q]);
+    }
+    for (int q = 0; q < 5; q++) {
+        const double s = block_sum<MOM_NT>(acc[q], sm);
+        if (threadIdx.x == 0) row_mom[(size_t)q * nrows + row] = s;
+    }
+}
+
+// pairs (a, b) with a + b <= 4, in a fixed order
+__constant__ int c_ab[15][2] = {{0, 0}, {0, 1}, {0, 2}, {0, 3}, {0, 4}, {1, 0}, {1, 1}, {1, 2}, {1, 3},
+                                {2, 0}, {2, 1}, {2, 2}, {3, 0}, {3, 1}, {4, 0}};
+
+// plane[ab][k] = sum_j ym[b][j] row_mom[a][k*ny + j]
+__global__ void __launch_bounds__(MOM_NT) k_plane_moments(const double* __restrict__ row_mom, int ny, int nz,
+                                                         const double* __restrict__ ym, double* __restrict__ plane)
+{
+    __shared__ double sm[32];
+    const int k = blockIdx.x;
+    const size_t nrows = (size_t)ny * nz;
+    for (int ab = 0; ab < 15; ab++) {
+        const int A = c_ab[ab][0], B = c_ab[ab][1];
+        double acc = 0.0;
+        for (int j = threadIdx.x; j < ny; j += MOM_NT)
+            acc = fma(ym[(size_t)B * ny + j], row_mom[(size_t)A * nrows + (size_t)k * ny + j], acc);
+        const double s = block_sum<MOM_NT>(acc, sm);
+        if (threadIdx.x == 0) plane[(size_t)ab * nz + k] = s;
+    }
+}
+
+// M[a][b][c] = sum_k zm[c][k] plane[ab][k]; Q_lm = sum_terms coef M / (4 pi)
+__global__ void __launch_bounds__(MOM_NT) k_final_moments(const double* __restrict__ plane, int nz,
+                                                         const double* __restrict__ zm, double* __restrict__ Q)
+{
+    __shared__ double sm[32];
+    __shared__ double M[5][5][5];
+    for (int ab = 0; ab < 15; ab++) {
+        const int A = c_ab[ab][0], B = c_ab[ab][1];
+        for (int C = 0; C + A + B <= 4; C++) {
+            double acc = 0.0;
+            for (int k = threadIdx.x; k < nz; k += MOM_NT) acc = fma(zm[(size_t)C * nz + k], plane[(size_t)ab * nz + k], acc);
+            const double s = block_sum<MOM_NT>(acc, sm);
+            if (threadIdx.x == 0) M[A][B][C] = s;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NLM) {
+        double q = 0.0;
+        for (int t = 0; t < N_MONO_TERMS; t++) {
+            const Mono m = c_mono[t];
+            if (m.lm == (int)threadIdx.x) q = fma(m.coef, M[m.a][m.b][m.c], q);
+        }
+        Q[threadIdx.x] = q / (4.0 * PI);
+    }
+}
+
+cudaError_t launch_multipoles(const int n[3], const double* x, const double* y, const double* z, const double* b,
+                              const double centre[3], double* tabs, double* row_mom, double* plane, double* Q,
+                              cudaStream_t s)
+{
+    cudaError_t e = ensure_monomials();
+    if (e != cudaSuccess) return e;
+    double* xm = tabs;
+    double* ym = xm + 5 * (size_t)n[0];
+    double* zm = ym + 5 * (size_t)n[1];
+    k_moment_table<<<(n[0] + 127) / 128, 128, 0, s>>>(x, n[0], centre[0], xm);
+    k_moment_table<<<(n[1] + 127) / 128, 128, 0, s>>>(y, n[1], centre[1], ym);
+    k_moment_table<<<(n[2] + 127) / 128, 128, 0, s>>>(z, n[2], centre[2], zm);
+    const size_t nrows = (size_t)n[1] * n[2];
+    k_row_moments<<<(unsigned)nrows, MOM_NT, 0, s>>>(b, n[0], nrows, xm, row_mom);
+    k_plane_moments<<<n[2], MOM_NT, 0, s>>>(row_mom, n[1], n[2], ym, plane);
+    k_final_moments<<<1, MOM_NT, 0, s>>>(plane, n[2], zm, Q);
+    return cudaGetLastError();
+}
+
+size_t multipole_scratch_doubles(const int n[3])
+{
+    return 5 * ((size_t)n[0] + n[1] + n[2]) + 5 * (size_t)n[1] * n[2] + 15 * (size_t)n[2];
+}
+
+// ---------------------------------------------------------------- Dirichlet faces
+// u = -sum_lm 4 pi/(2l+1) Q_lm S_lm(d) / r^(2l+1), d = node - centre (Eq. 2.7 decay).
+__global__ void k_boundary_fill(int nx, int ny, int nz, const double* __restrict__ x, const double* __restrict__ y,
+                                const double* __restrict__ z, double cx, double cy, double cz,
+                                const double* __restrict__ Q, double* __restrict__ u)
+{
+    const size_t fx = (size_t)ny * nz, fy = (size_t)nx * nz, fz = (size_t)nx * ny;
+    const size_t total = 2 * (fx + fy + fz);
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    size_t r = t;
+    if (r < 2 * fx) {
+        const int side = (int)(r / fx);
+        r %= fx;
+        i = side ? nx - 1 : 0;
+        j = (int)(r % ny);
+        k = (int)(r / ny);
+    } else if ((r -= 2 * fx) < 2 * fy) {
+        const int side = (int)(r / fy);
+        r %= fy;
+        j = side ? ny - 1 : 0;
+        i = (int)(r % nx);
+        k = (int)(r / nx);
+    } else {
+        r -= 2 * fy;
+        const int side = (int)(r / fz);
+        r %= fz;
+        k = side ? nz - 1 : 0;
+        i = (int)(r % nx);
+        j = (int)(r / nx);
+    }
+    const double dx = x[i] - cx, dy = y[j] - cy, dz = z[k] - cz;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double ir = 1.0 / sqrt(r2), ir2 = ir * ir;
+    double S[NLM];
+    solid_harmonics(dx, dy, dz, S);
+    double v = 0.0, pw = ir;   // ir^(2l+1)
+    int l = 0;
+    for (int lm = 0; lm < NLM; lm++) {
+        const int ll = l_of_lm(lm);
+        if (ll != l) {
+            pw *= ir2;
+            l = ll;
+        }
+        v = fma(-4.0 * PI / (2.0 * l + 1.0) * Q[lm] * pw, S[lm], v);
+    }
+    u[((size_t)k * ny + j) * nx + i] = v;
+}
+
+cudaError_t launch_boundary_fill(const int n[3], const double* x, const double* y, const double* z, double cx,
+                                 double cy, double cz, const double* Q, double* u, cudaStream_t s)
+{
+    cudaError_t e = ensure_monomials();
+    if (e != cudaSuccess) return e;
+    const size_t total = 2 * ((size_t)n[1] * n[2] + (size_t)n[0] * n[2] + (size_t)n[0] * n[1]);
+    k_boundary_fill<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n[0], n[1], n[2], x, y, z, cx, cy, cz, Q, u);
+    return cudaGetLastError();
+}
+
+}  // namespace lasto

@@ -1,0 +1,181 @@
+// Internal declarations of the sm_103a LASTO interstitial Poisson library.
+// Shared only among the library's own .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/lasto_poisson.h"
+
+namespace lasto {
+
+constexpr int NLM = 25;
+constexpr int MAX_LEVELS = 10;
+constexpr int MAX_COARSE = 9;        // nodes per axis on the coarsest level
+constexpr int MAX_QUAD = 2048;       // n_theta * n_phi
+constexpr int RED_THREADS = 256;     // block size of reducing kernels
+constexpr double PI = 3.141592653589793238462643383279502884;
+
+// ---------------------------------------------------------------- errors
+struct Err {
+    int code = LASTO_OK;
+    std::string msg;
+};
+int set_cuda_error(Err* e, cudaError_t c, const char* what);
+#define LASTO_TRY(err, call)                                              \
+    do {                                                                  \
+        cudaError_t c_ = (call);                                          \
+        if (c_ != cudaSuccess) return ::lasto::set_cuda_error(err, c_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------- spherical harmonics
+// Real solid harmonics r^l y_lm as sums of monomials x^a y^b z^c (a+b+c = l <= 4).
+struct Mono {
+    int lm;
+    int a, b, c;
+    double coef;
+};
+constexpr int N_MONO_TERMS = 56;
+void host_monomials(Mono* out);      // the 56 terms, coefficients in FP64
+void host_solid_harmonics(double x, double y, double z, double* S);
+
+__host__ __device__ __forceinline__ int l_of_lm(int lm) { return lm >= 16 ? 4 : lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0; }
+
+// ---------------------------------------------------------------- block reductions
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* smem)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) smem[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < NT / 32) ? smem[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;  // valid in thread 0
+}
+
+// ---------------------------------------------------------------- levels
+// Per-axis tables of one level.  Coordinates and every coefficient derive from the
+// node coordinates of the level (the coarse level keeps every other fine node).
+template <typename T>
+struct AxisT {
+    const double* c;   // coordinates [n]
+    const T* cm;       // 2/((h- + h+) h-)  (minus neighbour) [n], 0 at the ends
+    const T* cp;       // 2/((h- + h+) h+)  (plus neighbour)
+    const T* dg;       // cm + cp
+    const T* dual;     // dual-cell length
+    const T* pl;       // prolongation weight of coarse node (f-1)/2 at odd fine f (1 at even f)
+    const T* pr;       // weight of coarse node (f+1)/2 at odd f (0 at even f)
+    const T* rw;       // restriction weights of coarse node I [nc][3] (fine 2I-1, 2I, 2I+1)
+    int n;
+};
+
+template <typename T>
+struct LevelT {
+    AxisT<T> ax[3];
+    const T* inv_diag;  // [N] or nullptr (FP32 smoother computes the diagonal)
+    int nx, ny, nz;
+    __host__ __device__ size_t N() const { return (size_t)nx * ny * nz; }
+};
+
+// Raw (writable) per-axis storage of one level in one pool.
+struct AxisStore {
+    double* c;
+    double *cm, *cp, *dg, *dual, *pl, *pr, *rw;
+    float *cm32, *cp32, *dg32, *dual32, *pl32, *pr32, *rw32;
+    int n;
+};
+
+struct LevelStore {
+    AxisStore ax[3];
+    int n[3];
+    double* inv_diag;   // FP64 [N]
+    double *u, *b, *r;  // FP64 work arrays (level 0: u unused by the preconditioner)
+    float *u32, *b32, *r32;
+    size_t N() const { return (size_t)n[0] * n[1] * n[2]; }
+    LevelT<double> view64() const;
+    LevelT<float> view32() const;
+};
+
+// Exact coarse solve by fast diagonalisation of the three 1-D operators.
+struct CoarseEig {
+    double F[3][(MAX_COARSE - 2) * (MAX_COARSE - 2)];  // forward  [p][i] = Q[i][p] sqrt(V_i)
+    double B[3][(MAX_COARSE - 2) * (MAX_COARSE - 2)];  // backward [i][p] = Q[i][p] / sqrt(V_i)
+    double lam[3][MAX_COARSE - 2];
+    int m[3];
+    int ok[3];
+};
+
+int num_levels(const int n[3], int* coarse_n = nullptr);
+size_t axis_pool_doubles(int n);     // doubles needed by one AxisStore of n nodes
+void carve_axis(AxisStore* a, int n, double* pool);
+
+// ---------------------------------------------------------------- kernel launchers
+// mesh.cu
+cudaError_t launch_mesh_axis(int n, double c, double L, double h_min, double h_max, double p_max, double* x,
+                             double* info, cudaStream_t s);
+cudaError_t launch_level_tables(const LevelStore& fine, const LevelStore* coarse, const double* src_coords[3],
+                                int src_stride, cudaStream_t s);
+cudaError_t launch_inv_diag(const LevelStore& L, cudaStream_t s);
+cudaError_t launch_coarse_eig(const LevelStore& L, CoarseEig* eig, cudaStream_t s);
+
+// mg.cu
+template <typename T>
+cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(const LevelT<T>& L, const T* u, const T* b, T* r, cudaStream_t s);
+template <typename T>
+cudaError_t launch_apply(const LevelT<T>& L, const T* u, T* Au, cudaStream_t s);
+template <typename T>
+cudaError_t launch_restrict(const LevelT<T>& fine, const LevelT<T>& coarse, const T* r, T* bc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong_add(const LevelT<T>& fine, const LevelT<T>& coarse, const T* ec, T* u, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_apply(const LevelT<T>& L, const CoarseEig* eig, const T* b, T* e, bool add, cudaStream_t s);
+
+// reductions / CG (mg.cu)
+struct Ctl;
+int reduce_blocks(const LevelT<double>& L);
+cudaError_t launch_bnorm_partials(const LevelT<double>& L, const double* u, const double* b, double* part, cudaStream_t s);
+cudaError_t launch_resid_norm_partials(const LevelT<double>& L, const double* u, const double* b, double* r,
+                                       double* part, cudaStream_t s);
+cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, double* part, cudaStream_t s);
+cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const double* p, const double* q, double* u,
+                             double* r, float* r32, double* part, cudaStream_t s);
+template <typename TZ>
+cudaError_t launch_dot_rz(const LevelT<double>& L, const double* r, const TZ* z, double* part, cudaStream_t s);
+template <typename TZ>
+cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const TZ* z, double* p, cudaStream_t s);
+cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s);
+
+// density.cu
+void init_device_constants();   // constant tables and kernel attributes; call outside stream capture
+constexpr int SPHERE_REC_DOUBLES = 24;
+cudaError_t launch_sphere_params(const lasto_cluster& cl, const double* ax0, const double* ax1, const double* ax2,
+                                 double* rec, double* q, double* rhoR, double* drhoR, double* coef, int* status,
+                                 cudaStream_t s);
+cudaError_t launch_deposit(const lasto_cluster& cl, const double* rec, int precision, double* b, int* owner,
+                           const double* xm_tab, double* row_mom, int* status, cudaStream_t s);
+size_t multipole_scratch_doubles(const int n[3]);
+cudaError_t launch_multipoles(const int n[3], const double* x, const double* y, const double* z, const double* b,
+                              const double centre[3], double* tabs, double* row_mom, double* plane, double* Q,
+                              cudaStream_t s);
+cudaError_t launch_boundary_fill(const int n[3], const double* x, const double* y, const double* z, double cx,
+                                 double cy, double cz, const double* Q, double* u, cudaStream_t s);
+
+// project.cu
+void host_quadrature(int n_theta, int n_phi, double* table /* [nq][28]: unit xyz, w*S_lm */);
+cudaError_t launch_project(const int n[3], const double* x, const double* y, const double* z, const double* u,
+                           int n_atoms, const double* pos, const double* R, const double* quad, int nq,
+                           double* vlm, int* status, cudaStream_t s);
+
+}  // namespace lasto

@@ -1,0 +1,559 @@
+// Multigrid and conjugate-gradient kernels of the interstitial Poisson solve
+// (Section 3: "a finite difference scheme and a multigrid method").
+//
+// All kernels walk the grid with a flat node index.  Every smoothed level has an
+// odd number of nodes per axis, so the parity of the flat index equals the parity
+// of i+j+k: red nodes are the even flat indices, and a half sweep is one thread per
+// node of that colour with unit-stride neighbour loads.  Reductions are two-stage
+// (per-block partials, then one block in a fixed order), so every norm and dot is
+// bitwise reproducible.
+#include "internal.cuh"
+#include "ctl.cuh"
+
+namespace lasto {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ void node_ijk(size_t P, int nx, int ny, int& i, int& j, int& k)
+{
+    const size_t nxy = (size_t)nx * ny;
+    k = (int)(P / nxy);
+    const size_t rem = P - (size_t)k * nxy;
+    j = (int)(rem / nx);
+    i = (int)(rem - (size_t)j * nx);
+}
+
+template <typename T>
+__device__ __forceinline__ bool is_face(const LevelT<T>& L, int i, int j, int k)
+{
+    return i == 0 || j == 0 || k == 0 || i == L.nx - 1 || j == L.ny - 1 || k == L.nz - 1;
+}
+
+// sum of the six neighbour terms in the fixed order x-, x+, y-, y+, z-, z+
+template <typename T>
+__device__ __forceinline__ T offdiag(const LevelT<T>& L, const T* __restrict__ u, size_t P, int i, int j, int k)
+{
+    const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
+    T t = L.ax[0].cm[i] * u[P - 1];
+    t = fma(L.ax[0].cp[i], u[P + 1], t);
+    t = fma(L.ax[1].cm[j], u[P - sy], t);
+    t = fma(L.ax[1].cp[j], u[P + sy], t);
+    t = fma(L.ax[2].cm[k], u[P - sz], t);
+    t = fma(L.ax[2].cp[k], u[P + sz], t);
+    return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T dsum(const LevelT<T>& L, int i, int j, int k)
+{
+    return L.ax[0].dg[i] + L.ax[1].dg[j] + L.ax[2].dg[k];
+}
+
+// ---------------------------------------------------------------- smoother
+template <typename T>
+__global__ void __launch_bounds__(NT) k_rbgs(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour,
+                                            size_t nhalf)
+{
+    const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (t >= nhalf) return;
+    const size_t P = 2 * t + colour;
+    int i, j, k;
+    node_ijk(P, L.nx, L.ny, i, j, k);
+    if (is_face(L, i, j, k)) return;
+    const T acc = b[P] - offdiag(L, u, P, i, j, k);
+    if constexpr (sizeof(T) == 8) {
+        u[P] = acc * L.inv_diag[P];
+    } else {
+        u[P] = acc / (-dsum(L, i, j, k));
+    }
+}
+
+template <typename T>
+cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s)
+{
+    const size_t N = L.N();
+    const size_t nhalf = (N + 1 - colour) / 2;
+    k_rbgs<T><<<(unsigned)((nhalf + NT - 1) / NT), NT, 0, s>>>(L, u, b, colour, nhalf);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- residual / apply
+template <typename T>
+__global__ void __launch_bounds__(NT) k_residual(LevelT<T> L, const T* __restrict__ u, const T* __restrict__ b,
+                                                T* __restrict__ r)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= L.N()) return;
+    int i, j, k;
+    node_ijk(P, L.nx, L.ny, i, j, k);
+    if (is_face(L, i, j, k)) {
+        r[P] = T(0);
+        return;
+    }
+    const T Au = fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
+    r[P] = b[P] - Au;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_apply(LevelT<T> L, const T* __restrict__ u, T* __restrict__ Au)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= L.N()) return;
+    int i, j, k;
+    node_ijk(P, L.nx, L.ny, i, j, k);
+    Au[P] = is_face(L, i, j, k) ? T(0) : fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
+}
+
+template <typename T>
+cudaError_t launch_residual(const LevelT<T>& L, const T* u, const T* b, T* r, cudaStream_t s)
+{
+    k_residual<T><<<(unsigned)((L.N() + NT - 1) / NT), NT, 0, s>>>(L, u, b, r);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_apply(const LevelT<T>& L, const T* u, T* Au, cudaStream_t s)
+{
+    k_apply<T><<<(unsigned)((L.N() + NT - 1) / NT), NT, 0, s>>>(L, u, Au);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- transfers
+// bc = Vc^-1 P^T Vf r: the 27-point stencil factorises into per-axis weights.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_restrict(LevelT<T> F, LevelT<T> C, const T* __restrict__ r,
+                                                T* __restrict__ bc)
+{
+    const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (t >= C.N()) return;
+    int I, J, K;
+    node_ijk(t, C.nx, C.ny, I, J, K);
+    if (is_face(C, I, J, K)) {
+        bc[t] = T(0);
+        return;
+    }
+    const T* wx = F.ax[0].rw + 3 * I;
+    const T* wy = F.ax[1].rw + 3 * J;
+    const T* wz = F.ax[2].rw + 3 * K;
+    const size_t sy = F.nx, sz = (size_t)F.nx * F.ny;
+    const T* base = r + (size_t)(2 * K - 1) * sz + (size_t)(2 * J - 1) * sy + (2 * I - 1);
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int bb = 0; bb < 3; bb++) {
+            const T* row = base + c * sz + bb * sy;
+            const T s = fma(wx[0], row[0], fma(wx[1], row[1], wx[2] * row[2]));
+            acc = fma(wz[c] * wy[bb], s, acc);
+        }
+    bc[t] = acc;
+}
+
+template <typename T>
+cudaError_t launch_restrict(const LevelT<T>& F, const LevelT<T>& C, const T* r, T* bc, cudaStream_t s)
+{
+    k_restrict<T><<<(unsigned)((C.N() + NT - 1) / NT), NT, 0, s>>>(F, C, r, bc);
+    return cudaGetLastError();
+}
+
+// u += P ec: per axis an even fine node sits on a coarse node (weight 1), an odd one
+// between two (weights pl, pr in physical coordinates).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, const T* __restrict__ ec,
+                                                   T* __restrict__ u)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= F.N()) return;
+    int i, j, k;
+    node_ijk(P, F.nx, F.ny, i, j, k);
+    if (is_face(F, i, j, k)) return;
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+    const T wx[2] = {F.ax[0].pl[i], F.ax[0].pr[i]};
+    const T wy[2] = {F.ax[1].pl[j], F.ax[1].pr[j]};
+    const T wz[2] = {F.ax[2].pl[k], F.ax[2].pr[k]};
+    const size_t sy = C.nx, sz = (size_t)C.nx * C.ny;
+    const T* base = ec + (size_t)K * sz + (size_t)J * sy + I;
+    T e = T(0);
+    for (int c = 0; c < nk; c++)
+        for (int bb = 0; bb < nj; bb++) {
+            const T* row = base + c * sz + bb * sy;
+            const T s = (ni == 2) ? fma(wx[0], row[0], wx[1] * row[1]) : row[0];
+            e = fma(wz[c] * wy[bb], s, e);
+        }
+    u[P] += e;
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(const LevelT<T>& F, const LevelT<T>& C, const T* ec, T* u, cudaStream_t s)
+{
+    k_prolong_add<T><<<(unsigned)((F.N() + NT - 1) / NT), NT, 0, s>>>(F, C, ec, u);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- exact coarse solve
+constexpr int MC = MAX_COARSE - 2;
+constexpr int MC3 = MC * MC * MC;
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_coarse_apply(LevelT<T> L, const CoarseEig* __restrict__ E,
+                                                     const T* __restrict__ b, T* __restrict__ e, int add)
+{
+    __shared__ double s0[MC3], s1[MC3];
+    const int mx = L.nx - 2, my = L.ny - 2, mz = L.nz - 2, M = mx * my * mz;
+    const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
+    auto node = [&](int a, int bb, int c) { return (size_t)(c + 1) * sz + (size_t)(bb + 1) * sy + (a + 1); };
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        const int a = t % mx, bb = (t / mx) % my, c = t / (mx * my);
+        s0[t] = (double)b[node(a, bb, c)];
+    }
+    __syncthreads();
+    const double* Fx = E->F[0];
+    const double* Fy = E->F[1];
+    const double* Fz = E->F[2];
+    const double* Bx = E->B[0];
+    const double* By = E->B[1];
+    const double* Bz = E->B[2];
+    // forward along x, y, z
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        const int p = t % mx, rest = t / mx;
+        double acc = 0.0;
+        for (int a = 0; a < mx; a++) acc = fma(Fx[p * mx + a], s0[rest * mx + a], acc);
+        s1[t] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        const int p = t % mx, q = (t / mx) % my, c = t / (mx * my);
+        double acc = 0.0;
+        for (int bb = 0; bb < my; bb++) acc = fma(Fy[q * my + bb], s1[(c * my + bb) * mx + p], acc);
+        s0[t] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        const int p = t % mx, q = (t / mx) % my, sidx = t / (mx * my);
+        double acc = 0.0;
+        for (int c = 0; c < mz; c++) acc = fma(Fz[sidx * mz + c], s0[(c * my + q) * mx + p], acc);
+        s1[t] = acc / (E->lam[0][p] + E->lam[1][q] + E->lam[2][sidx]);
+    }
+    __syncthreads();
+    // backward along z, y, x
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        const int p = t % mx, q = (t / mx) % my, c = t / (mx * my);
+        double acc = 0.0;
+        for (int sidx = 0; sidx < mz; sidx++) acc = fma(Bz[c * mz + sidx], s1[(sidx * my + q) * mx + p], acc);
+        s0[t] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        const int p = t % mx, bb = (t / mx) % my, c = t / (mx * my);
+        double acc = 0.0;
+        for (int q = 0; q < my; q++) acc = fma(By[bb * my + q], s0[(c * my + q) * mx + p], acc);
+        s1[t] = acc;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        const int a = t % mx, rest = t / mx;
+        double acc = 0.0;
+        for (int p = 0; p < mx; p++) acc = fma(Bx[a * mx + p], s1[rest * mx + p], acc);
+        const size_t P = node(a, (t / mx) % my, t / (mx * my));
+        if (add) e[P] = (T)((double)e[P] + acc);
+        else e[P] = (T)acc;
+    }
+    if (!add) {
+        const int N = L.nx * L.ny * L.nz;
+        for (int t = threadIdx.x; t < N; t += blockDim.x) {
+            const int i = t % L.nx, j = (t / L.nx) % L.ny, k = t / (L.nx * L.ny);
+            if (is_face(L, i, j, k)) e[t] = T(0);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_coarse_apply(const LevelT<T>& L, const CoarseEig* eig, const T* b, T* e, bool add, cudaStream_t s)
+{
+    k_coarse_apply<T><<<1, 512, 0, s>>>(L, eig, b, e, add ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- reductions
+int reduce_blocks(const LevelT<double>& L) { return (int)((L.N() + NT - 1) / NT); }
+
+__device__ __forceinline__ double vol(const LevelT<double>& L, int i, int j, int k)
+{
+    return L.ax[0].dual[i] * L.ax[1].dual[j] * L.ax[2].dual[k];
+}
+
+// ||b_eff||^2 partials: b with the Dirichlet faces moved to the right-hand side.
+__global__ void __launch_bounds__(NT) k_bnorm_partials(LevelT<double> L, const double* __restrict__ u,
+                                                      const double* __restrict__ b, double* __restrict__ part)
+{
+    __shared__ double sm[32];
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    double acc = 0.0;
+    if (P < L.N()) {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (!is_face(L, i, j, k)) {
+            const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
+            double v = b[P];
+            if (i == 1) v -= L.ax[0].cm[i] * u[P - 1];
+            if (i == L.nx - 2) v -= L.ax[0].cp[i] * u[P + 1];
+            if (j == 1) v -= L.ax[1].cm[j] * u[P - sy];
+            if (j == L.ny - 2) v -= L.ax[1].cp[j] * u[P + sy];
+            if (k == 1) v -= L.ax[2].cm[k] * u[P - sz];
+            if (k == L.nz - 2) v -= L.ax[2].cp[k] * u[P + sz];
+            acc = v * v;
+        }
+    }
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// r = b - A u (written when r != nullptr) and ||r||^2 partials
+__global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const double* __restrict__ u,
+                                                  const double* __restrict__ b, double* __restrict__ r,
+                                                  double* __restrict__ part)
+{
+    __shared__ double sm[32];
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    double acc = 0.0;
+    if (P < L.N()) {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        double v = 0.0;
+        if (!is_face(L, i, j, k)) v = b[P] - fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
+        if (r) r[P] = v;
+        acc = v * v;
+    }
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// q = A p and <p, q>_vol partials
+__global__ void __launch_bounds__(NT) k_apply_dot(LevelT<double> L, const double* __restrict__ p,
+                                                 double* __restrict__ q, double* __restrict__ part)
+{
+    __shared__ double sm[32];
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    double acc = 0.0;
+    if (P < L.N()) {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        double v = 0.0;
+        if (!is_face(L, i, j, k)) {
+            v = fma(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
+            acc = vol(L, i, j, k) * p[P] * v;
+        }
+        q[P] = v;
+    }
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// u += alpha p; r -= alpha q; r32 = (float) r; ||r||^2 partials
+__global__ void __launch_bounds__(NT) k_update_ur(LevelT<double> L, const Ctl* __restrict__ ctl,
+                                                 const double* __restrict__ p, const double* __restrict__ q,
+                                                 double* __restrict__ u, double* __restrict__ r, float* __restrict__ r32,
+                                                 double* __restrict__ part)
+{
+    __shared__ double sm[32];
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    const double alpha = ctl->alpha;
+    double acc = 0.0;
+    if (P < L.N()) {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (!is_face(L, i, j, k)) {
+            u[P] = fma(alpha, p[P], u[P]);
+            const double rv = fma(-alpha, q[P], r[P]);
+            r[P] = rv;
+            if (r32) r32[P] = (float)rv;
+            acc = rv * rv;
+        } else if (r32) {
+            r32[P] = 0.0f;
+        }
+    }
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(NT) k_dot_rz(LevelT<double> L, const double* __restrict__ r,
+                                              const TZ* __restrict__ z, double* __restrict__ part)
+{
+    __shared__ double sm[32];
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    double acc = 0.0;
+    if (P < L.N()) {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (!is_face(L, i, j, k)) acc = vol(L, i, j, k) * r[P] * (double)z[P];
+    }
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(NT) k_update_p(LevelT<double> L, const Ctl* __restrict__ ctl,
+                                                const TZ* __restrict__ z, double* __restrict__ p)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= L.N()) return;
+    int i, j, k;
+    node_ijk(P, L.nx, L.ny, i, j, k);
+    p[P] = is_face(L, i, j, k) ? 0.0 : fma(ctl->beta, p[P], (double)z[P]);
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n)
+{
+    const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (t < n) b[t] = (float)a[t];
+}
+
+#define GRID(L) (unsigned)((L.N() + NT - 1) / NT), NT, 0, s
+
+cudaError_t launch_bnorm_partials(const LevelT<double>& L, const double* u, const double* b, double* part, cudaStream_t s)
+{
+    k_bnorm_partials<<<GRID(L)>>>(L, u, b, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_resid_norm_partials(const LevelT<double>& L, const double* u, const double* b, double* r,
+                                       double* part, cudaStream_t s)
+{
+    k_resid_norm<<<GRID(L)>>>(L, u, b, r, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, double* part, cudaStream_t s)
+{
+    k_apply_dot<<<GRID(L)>>>(L, p, q, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const double* p, const double* q, double* u,
+                             double* r, float* r32, double* part, cudaStream_t s)
+{
+    k_update_ur<<<GRID(L)>>>(L, ctl, p, q, u, r, r32, part);
+    return cudaGetLastError();
+}
+template <typename TZ>
+cudaError_t launch_dot_rz(const LevelT<double>& L, const double* r, const TZ* z, double* part, cudaStream_t s)
+{
+    k_dot_rz<TZ><<<GRID(L)>>>(L, r, z, part);
+    return cudaGetLastError();
+}
+template <typename TZ>
+cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const TZ* z, double* p, cudaStream_t s)
+{
+    k_update_p<TZ><<<GRID(L)>>>(L, ctl, z, p);
+    return cudaGetLastError();
+}
+cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s)
+{
+    k_to_f32<<<(unsigned)((n + NT - 1) / NT), NT, 0, s>>>(a, b, n);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- scalar steps
+// One block sums the partials in a fixed order; thread 0 updates the control block.
+__device__ double fin_sum(const double* __restrict__ part, int nparts, double* sm)
+{
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < nparts; t += NT) acc += part[t];
+    return block_sum<NT>(acc, sm);
+}
+
+__global__ void __launch_bounds__(NT) k_fin(Ctl* ctl, const double* __restrict__ part, int nparts, int op,
+                                           cudaGraphConditionalHandle cond, int use_cond)
+{
+    __shared__ double sm[32];
+    const double s = fin_sum(part, nparts, sm);
+    if (threadIdx.x != 0) return;
+    Ctl& c = *ctl;
+    switch (op) {
+        case FIN_BNORM:
+            c.bnorm = sqrt(s);
+            break;
+        case FIN_ALPHA:
+            c.alpha = (s != 0.0 && isfinite(s)) ? c.rz / s : 0.0;
+            break;
+        case FIN_BETA: {
+            c.beta = (c.iter == 0 || c.rz == 0.0) ? 0.0 : s / c.rz;
+            c.rz = s;
+            break;
+        }
+        case FIN_START:   // residual of the starting guess
+        case FIN_CHECK: {
+            const double scale = c.bnorm > 0.0 ? c.bnorm : 1.0;
+            const double rel = sqrt(s) / scale;
+            if (op == FIN_CHECK) c.iter += 1;
+            c.rel = rel;
+            if (c.iter < CTL_HIST) c.hist[c.iter] = rel;
+            int go = 1;
+            if (!isfinite(rel)) {
+                c.status = LASTO_ERR_NONFINITE;
+                go = 0;
+            } else if (rel <= c.tol_iter) {
+                c.status = LASTO_OK;
+                go = 0;
+            } else if (c.iter >= c.max_iter) {
+                c.status = LASTO_ERR_NOT_CONVERGED;
+                go = 0;
+            }
+            c.done = !go;
+            if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+            break;
+        }
+        case FIN_TRUE: {
+            const double scale = c.bnorm > 0.0 ? c.bnorm : 1.0;
+            c.true_rel = sqrt(s) / scale;
+            if (c.status == LASTO_OK && !(c.true_rel <= c.tol)) c.status = LASTO_ERR_NOT_CONVERGED;
+            if (!isfinite(c.true_rel)) c.status = LASTO_ERR_NONFINITE;
+            break;
+        }
+        default:
+            break;
+    }
+}
+
+cudaError_t launch_fin(Ctl* ctl, const double* part, int nparts, int op, cudaGraphConditionalHandle cond,
+                       int use_cond, cudaStream_t s)
+{
+    k_fin<<<1, NT, 0, s>>>(ctl, part, nparts, op, cond, use_cond);
+    return cudaGetLastError();
+}
+
+__global__ void k_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter)
+{
+    Ctl& c = *ctl;
+    c.tol = tol;
+    c.tol_iter = tol_iter;
+    c.max_iter = max_iter;
+    c.iter = 0;
+    c.status = LASTO_ERR_NOT_CONVERGED;
+    c.done = 0;
+    c.rz = 1.0;
+    c.alpha = c.beta = 0.0;
+    c.rel = c.true_rel = -1.0;
+}
+
+cudaError_t launch_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter, cudaStream_t s)
+{
+    k_ctl_init<<<1, 1, 0, s>>>(ctl, tol, tol_iter, max_iter);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- instantiations
+#define INST(T)                                                                                              \
+    template cudaError_t launch_rbgs<T>(const LevelT<T>&, T*, const T*, int, cudaStream_t);                 \
+    template cudaError_t launch_residual<T>(const LevelT<T>&, const T*, const T*, T*, cudaStream_t);        \
+    template cudaError_t launch_apply<T>(const LevelT<T>&, const T*, T*, cudaStream_t);                     \
+    template cudaError_t launch_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, T*, cudaStream_t); \
+    template cudaError_t launch_prolong_add<T>(const LevelT<T>&, const LevelT<T>&, const T*, T*, cudaStream_t); \
+    template cudaError_t launch_coarse_apply<T>(const LevelT<T>&, const CoarseEig*, const T*, T*, bool, cudaStream_t);
+INST(double)
+INST(float)
+template cudaError_t launch_dot_rz<double>(const LevelT<double>&, const double*, const double*, double*, cudaStream_t);
+template cudaError_t launch_dot_rz<float>(const LevelT<double>&, const double*, const float*, double*, cudaStream_t);
+template cudaError_t launch_update_p<double>(const LevelT<double>&, const Ctl*, const double*, double*, cudaStream_t);
+template cudaError_t launch_update_p<float>(const LevelT<double>&, const Ctl*, const float*, double*, cudaStream_t);
+
+}  // namespace lasto

@@ -1,0 +1,171 @@
+"""GPU parity of each kernel family against the FP64 oracle, through the C ABI.
+
+Inputs are seeded and made here (graded axes with several tiles and a ragged
+tail, random fields); both sides get the same arrays.  Tolerances: FP64 kernels
+agree to a few units of rounding of their largest term (the two sides differ only
+in FMA contraction and summation order); the FP32 smoother to FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import dev, graded_axis, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(33, 33, 33), (65, 33, 49), (97, 97, 97)]
+
+
+def _grid(n, seed):
+    x = graded_axis(n[0], 6.0, 3.0, seed, 0.1)
+    y = graded_axis(n[1], 5.0, 2.0, seed + 1, 0.1)
+    z = graded_axis(n[2], 7.0, 4.0, seed + 2, 0.1)
+    return x, y, z
+
+
+def _coef_scale(x, y, z):
+    h = min(np.diff(x).min(), np.diff(y).min(), np.diff(z).min())
+    return 12.0 / (h * h)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_apply_and_residual(orc, n):
+    B = need_gpu()
+    x, y, z = _grid(n, 1)
+    rng = np.random.default_rng(2)
+    u, b = rng.normal(size=n[::-1]), rng.normal(size=n[::-1])
+    tol = 1e-13 * _coef_scale(x, y, z) * np.abs(u).max()
+    Au = host(B.lasto_op_apply(dev(x), dev(y), dev(z), dev(u)))
+    assert np.abs(Au - orc.apply_A(x, y, z, u)).max() < tol
+    r = host(B.lasto_op_residual(dev(x), dev(y), dev(z), dev(u), dev(b)))
+    assert np.abs(r - orc.residual(x, y, z, u, b)).max() < tol
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_red_black_sweeps(orc, n):
+    B = need_gpu()
+    x, y, z = _grid(n, 3)
+    rng = np.random.default_rng(4)
+    u, b = rng.normal(size=n[::-1]), rng.normal(size=n[::-1])
+    ref = u.copy()
+    for _ in range(2):
+        orc.rbgs_half(x, y, z, ref, b, 0)
+        orc.rbgs_half(x, y, z, ref, b, 1)
+    got = host(B.lasto_op_smooth(dev(x), dev(y), dev(z), dev(u), dev(b), sweeps=2))
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_red_black_sweep_fp32(orc):
+    B = need_gpu()
+    import torch
+    n = (65, 33, 49)
+    x, y, z = _grid(n, 5)
+    rng = np.random.default_rng(6)
+    u, b = rng.normal(size=n[::-1]), rng.normal(size=n[::-1])
+    ref = u.copy()
+    orc.rbgs_half(x, y, z, ref, b, 0)
+    orc.rbgs_half(x, y, z, ref, b, 1)
+    u32 = torch.as_tensor(u.astype(np.float32)).cuda()
+    b32 = torch.as_tensor(b.astype(np.float32)).cuda()
+    got = B.lasto_op_smooth(dev(x), dev(y), dev(z), u32, b32, sweeps=1).cpu().numpy().astype(np.float64)
+    assert np.abs(got - ref).max() < 2e-5 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_restriction_and_prolongation(orc, n):
+    B = need_gpu()
+    x, y, z = _grid(n, 7)
+    rng = np.random.default_rng(8)
+    r = rng.normal(size=n[::-1])
+    bc = host(B.lasto_op_restrict(dev(x), dev(y), dev(z), dev(r)))
+    ref = orc.restrict(x, y, z, r)
+    assert np.abs(bc - ref).max() < 1e-13 * np.abs(ref).max()
+    nc = tuple((v + 1) // 2 for v in n)
+    ec = rng.normal(size=nc[::-1])
+    ec[0] = ec[-1] = 0; ec[:, 0] = ec[:, -1] = 0; ec[:, :, 0] = ec[:, :, -1] = 0
+    u = rng.normal(size=n[::-1])
+    got = host(B.lasto_op_prolong_add(dev(x), dev(y), dev(z), dev(ec), dev(u)))
+    refu = orc.prolong_add(x, y, z, ec, u.copy())
+    assert np.abs(got - refu).max() < 1e-14 * np.abs(refu).max() * 10
+
+
+@pytest.mark.parametrize("n", [(9, 9, 9), (7, 9, 5), (5, 5, 5), (3, 3, 3)])
+def test_coarse_solve(orc, n):
+    B = need_gpu()
+    x, y, z = _grid(n, 9) if min(n) > 3 else (np.array([-1, 0.2, 1.0]),) * 3
+    b = np.random.default_rng(10).normal(size=n[::-1])
+    e = host(B.lasto_op_coarse_solve(dev(x), dev(y), dev(z), dev(b)))
+    ref = orc.coarse_solve(x, y, z, b)
+    assert np.abs(e - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_mesh_axis(orc):
+    B = need_gpu()
+    for (n, L, hmin, hmax) in [(65, 12.0, 0.375, 0.375), (129, 22.8, 0.12, 0.6), (385, 38.4, 0.12, 0.6),
+                               (97, 18.0, 0.15, 0.6)]:
+        x, info = B.lasto_mesh_axis(n, 0.0, L, hmin, hmax, 6.0, info=True)
+        ref, rinfo = orc.mesh_axis(n, 0.0, L, hmin, hmax, 6.0)
+        assert np.abs(host(x) - ref).max() <= 4e-16 * L
+        assert np.allclose(host(info), rinfo, rtol=1e-14, atol=1e-15)
+
+
+@pytest.fixture(scope="module")
+def small_clusters():
+    return [synth.pd13_small(n=33), synth.pd2_dimer(n=33, graded=True), synth.pd13_uniform65()]
+
+
+def test_sphere_params(orc, small_clusters):
+    B = need_gpu()
+    for cl in small_clusters:
+        dc = B.DeviceCluster(cl)
+        q, rhoR, drhoR, coef, status = (host(t) for t in B.lasto_op_sphere_params(dc))
+        rq, rr, rd, rc = orc.sphere_params(cl)
+        assert status[0] == 0
+        assert np.abs(q - rq).max() < 1e-12 * np.abs(rq).max()
+        assert np.abs(rhoR - rr).max() < 1e-12 * np.abs(rr).max()
+        assert np.abs(drhoR - rd).max() < 1e-11 * np.abs(rd).max()
+        assert np.abs(coef - rc).max() < 1e-11 * np.abs(rc).max()
+
+
+def test_deposit(orc, small_clusters):
+    B = need_gpu()
+    for cl in small_clusters:
+        dc = B.DeviceCluster(cl)
+        x, y, z = orc.mesh(cl)
+        assert np.abs(host(dc.x) - x).max() < 1e-14 * cl.half_width
+        b, owner, status = B.lasto_op_deposit(dc)
+        ref, rowner = orc.deposit(cl, host(dc.x), host(dc.y), host(dc.z))
+        assert host(status)[0] == 0
+        assert np.array_equal(host(owner), rowner)
+        b = host(b)
+        # the GPU cancels each atom's own spherical terms analytically; the oracle subtracts them
+        assert np.abs(b - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_multipoles_and_faces(orc, small_clusters):
+    B = need_gpu()
+    for cl in small_clusters:
+        dc = B.DeviceCluster(cl)
+        x, y, z = host(dc.x), host(dc.y), host(dc.z)
+        b, _, _ = B.lasto_op_deposit(dc)
+        bh = host(b)
+        Q = host(B.lasto_op_multipoles(dc.x, dc.y, dc.z, b))
+        rQ = orc.multipoles(x, y, z, bh)
+        assert np.abs(Q - rQ).max() < 1e-12 * np.abs(rQ).max()
+        import torch
+        u = torch.zeros_like(b)
+        B.lasto_op_boundary_fill(dc.x, dc.y, dc.z, dev(rQ), u)
+        ref = orc.boundary_fill(x, y, z, rQ, np.zeros(bh.shape))
+        assert np.abs(host(u) - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_projection(orc):
+    B = need_gpu()
+    cl = synth.pd13_small(n=33)
+    dc = B.DeviceCluster(cl)
+    x, y, z = host(dc.x), host(dc.y), host(dc.z)
+    u = np.random.default_rng(11).normal(size=(33, 33, 33))
+    vlm, status = B.lasto_op_project(dc.x, dc.y, dc.z, dev(u), dc.pos, dc.R)
+    ref = orc.project(x, y, z, u, cl.pos, cl.R)
+    assert host(status)[0] == 0
+    assert np.abs(host(vlm) - ref).max() < 1e-13 * np.abs(ref).max()
