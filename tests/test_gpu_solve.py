@@ -17,7 +17,11 @@ _ORACLE_CACHE = {}
 
 
 def oracle_vlm(orc, cl):
-    key = cl.name + str(cl.slater_w.sum()) + str(cl.pos.sum())
+    import hashlib
+    h = hashlib.sha1()
+    for a in (cl.pos, cl.slater_w, cl.slater_zeta, cl.c_lm, cl.R, cl.Z):
+        h.update(np.ascontiguousarray(a).tobytes())
+    key = (cl.name, cl.n, cl.half_width, cl.h_min, cl.h_max, h.hexdigest())
     if key not in _ORACLE_CACHE:
         out = orc.poisson_solve(cl, tol=1e-13, max_cycles=200)
         assert out["status"] == 0, out["status"]
