@@ -135,6 +135,13 @@ int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* clusters, int n_c
 
 void lasto_poisson_destroy(lasto_poisson* h);
 
+/* Kernel launches of the graph captured by the last lasto_poisson_solve on h:
+ * *fixed = kernels that run once per solve (setup, deposit, multipoles, faces,
+ * projection, ...), *per_iteration = kernels in one body of the iteration loop,
+ * so one solve launches fixed + cycles * per_iteration kernels.  Host pointers.
+ * Errors: INVALID_ARG if no solve has been captured yet. */
+int lasto_poisson_kernel_counts(const lasto_poisson* h, int* fixed, int* per_iteration);
+
 /* Text of the last error on this handle (never NULL; "" when none). */
 const char* lasto_poisson_last_error(const lasto_poisson* h);
 

@@ -44,7 +44,7 @@ class lasto_stats(ctypes.Structure):
 
 
 EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve", "lasto_poisson_destroy",
-           "lasto_poisson_last_error", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
+           "lasto_poisson_last_error", "lasto_poisson_kernel_counts", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
            "lasto_op_smooth_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
            "lasto_op_project"]
@@ -62,6 +62,7 @@ def _declare(L):
         "lasto_poisson_solve": (i, [vp, clp, i, vp, vp, vp, stp, vp]),
         "lasto_poisson_destroy": (None, [vp]),
         "lasto_poisson_last_error": (ctypes.c_char_p, [vp]),
+        "lasto_poisson_kernel_counts": (i, [vp, ip, ip]),
         "lasto_mesh_axis": (i, [i, d, d, d, d, d, vp, vp, vp]),
         "lasto_op_sphere_params": (i, [clp, vp, vp, vp, vp, vp, vp]),
         "lasto_op_deposit": (i, [clp, i, vp, vp, vp, vp]),
@@ -196,6 +197,13 @@ class Poisson:
             self.close()
         except Exception:
             pass
+
+    def kernel_counts(self):
+        """(kernels per solve outside the loop, kernels per loop iteration) of the captured graph."""
+        f, it = ctypes.c_int(), ctypes.c_int()
+        _check(load().lasto_poisson_kernel_counts(self.h, ctypes.byref(f), ctypes.byref(it)),
+               "lasto_poisson_kernel_counts")
+        return f.value, it.value
 
     def last_error(self) -> str:
         return load().lasto_poisson_last_error(self.h).decode()

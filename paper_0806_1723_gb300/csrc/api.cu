@@ -186,6 +186,8 @@ struct lasto_poisson {
     lasto_stats* stats_pinned = nullptr;
     lasto_stats* stats_user = nullptr;
     int stats_count = 0;
+    int kernels_fixed = -1, kernels_iter = -1;
+    std::vector<cudaGraph_t> bodies;
 };
 
 namespace {
@@ -380,6 +382,7 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
                   const double* guess)
 {
     cudaStream_t s = h->cs;
+    h->bodies.clear();
     TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int st = LASTO_OK;
     size_t atom_off = 0, grid_off = 0;
@@ -413,6 +416,7 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
         e = cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, cp);
         if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaGraphAddNode(while)"); break; }
         cudaGraph_t body = cp->conditional.phGraph_out[0];
+        h->bodies.push_back(body);
         e = cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
         if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamUpdateCaptureDependencies"); break; }
         e = cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
@@ -434,6 +438,32 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
         return st;
     }
     if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaStreamEndCapture");
+    {
+        // kernel nodes of the top-level graph and of the WHILE bodies
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        int fixed = 0, iter = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            cudaGraphNodeGetType(nd, &t);
+            if (t == cudaGraphNodeTypeKernel) fixed++;
+        }
+        for (cudaGraph_t bg : h->bodies) {
+            size_t bn = 0;
+            cudaGraphGetNodes(bg, nullptr, &bn);
+            std::vector<cudaGraphNode_t> bnodes(bn);
+            cudaGraphGetNodes(bg, bnodes.data(), &bn);
+            for (auto nd : bnodes) {
+                cudaGraphNodeType t;
+                cudaGraphNodeGetType(nd, &t);
+                if (t == cudaGraphNodeTypeKernel) iter++;
+            }
+        }
+        h->kernels_fixed = fixed;
+        h->kernels_iter = h->bodies.empty() ? 0 : iter / (int)h->bodies.size();
+    }
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
     if (e != cudaSuccess) {
@@ -526,6 +556,14 @@ void lasto_poisson_destroy(lasto_poisson* h)
     if (h->cs) cudaStreamDestroy(h->cs);
     if (h->cs2) cudaStreamDestroy(h->cs2);
     delete h;
+}
+
+int lasto_poisson_kernel_counts(const lasto_poisson* h, int* fixed, int* per_iteration)
+{
+    if (!h || !fixed || !per_iteration || h->kernels_fixed < 0) return LASTO_ERR_INVALID_ARG;
+    *fixed = h->kernels_fixed;
+    *per_iteration = h->kernels_iter;
+    return LASTO_OK;
 }
 
 const char* lasto_poisson_last_error(const lasto_poisson* h)
