@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
+    p.add_argument("--direct", action="store_true",
+                   help="launch the kernels directly instead of one CUDA graph per solve (for ncu)")
     return p.parse_args()
 
 
@@ -200,7 +202,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def make(precision):
-        return B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, precision=precision)
+        return B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, precision=precision, launch=1 if args.direct else 0)
 
     dc = B.DeviceCluster(cl)
     vlm = torch.empty((cl.n_atoms, 25), dtype=torch.float64, device=dev)
@@ -211,7 +213,7 @@ def main():
             st = solver.solve(dc, vlm)
         torch.cuda.synchronize()
         assert st[0].status == 0 and st[0].rel_resid <= 1e-10, (st[0].status, st[0].rel_resid)
-        fixed, per_it = solver.kernel_counts()
+        fixed, per_it = solver.kernel_counts() if not args.direct else (0, 0)
         ms, launches, cycles = [], 0, []
         for _ in range(steps):
             flush.fill_(1.0)                       # evict the working set from L2

@@ -84,10 +84,14 @@ typedef struct lasto_config {
     double rel_tol;   /* stop when ||b - A u||_2 <= rel_tol ||b_eff||_2 (b_eff: b with the faces moved in) */
     int n_theta;      /* Gauss-Legendre points in cos(theta) of the sphere quadrature (<= 32) */
     int n_phi;        /* uniform points in phi (<= 64) */
+    int launch;       /* 0: one CUDA graph per solve, iteration loop on the device (default);
+                         1: the same kernels launched directly with a host-side loop that
+                         synchronises once per iteration (for profilers that cannot see
+                         kernels inside conditional graph nodes) */
 } lasto_config;
 
 /* Fills cfg with the defaults: n_max 129, max_atoms 561, max_batch 1, FP64, PCG,
- * nu1 = nu2 = 2, 50 cycles, rel_tol 1e-10, 16 x 32 sphere points. */
+ * nu1 = nu2 = 2, 50 cycles, rel_tol 1e-10, 16 x 32 sphere points, graph launch. */
 void lasto_config_default(lasto_config* cfg);
 
 typedef struct lasto_cluster {

@@ -485,6 +485,59 @@ void CUDART_CB copy_stats_out(void* arg)
 
 }  // namespace
 
+static int copy_stats(lasto_poisson* h, int nc, lasto_stats* stats, cudaStream_t s)
+{
+    cudaError_t e;
+    if (stats) {
+        for (int c = 0; c < nc; c++) {
+            e = cudaMemcpyAsync(h->stats_pinned + c, h->plans[c].stats_dev, sizeof(lasto_stats),
+                                cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return set_cuda_error(&h->err, e, "stats copy");
+        }
+        h->stats_user = stats;
+        h->stats_count = nc;
+        e = cudaLaunchHostFunc(s, copy_stats_out, h);
+        if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaLaunchHostFunc");
+    }
+    return LASTO_OK;
+}
+
+// The same kernels as the captured graph, launched directly; the iteration loop runs
+// on the host and reads the device control block once per iteration.
+static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,
+                        const double* guess, cudaStream_t s)
+{
+    h->plans.assign(nc, ClusterPlan());
+    h->key.clear();
+    Carver cv{h->pool, h->pool_bytes};
+    for (int c = 0; c < nc; c++)
+        if (!carve_cluster(cv, cls[c].n, cls[c].n_atoms, h->plans[c]))
+            return fail(h, LASTO_ERR_NO_MEMORY, "workspace too small for this batch");
+    size_t atom_off = 0, grid_off = 0;
+    for (int c = 0; c < nc; c++) {
+        ClusterPlan& P = h->plans[c];
+        const lasto_cluster& cl = cls[c];
+        int st;
+        TRY(cudaMemsetAsync(P.status, 0, sizeof(int) * 4, s));
+        if ((st = enqueue_setup(h, P, cl, s))) return st;
+        if ((st = enqueue_rhs(h, P, cl, guess ? guess + grid_off : nullptr, s))) return st;
+        if ((st = enqueue_start(h, P, 0, 0, s))) return st;
+        int done = 0;
+        TRY(cudaMemcpyAsync(&done, &P.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        TRY(cudaStreamSynchronize(s));
+        for (int it = 0; it < h->cfg.max_cycles && !done; it++) {
+            if ((st = enqueue_iteration(h, P, 0, 0, s))) return st;
+            TRY(cudaMemcpyAsync(&done, &P.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+            TRY(cudaStreamSynchronize(s));
+        }
+        if ((st = enqueue_finish(h, P, cl, v_lm + NLM * atom_off, potential ? potential + grid_off : nullptr, s)))
+            return st;
+        atom_off += cl.n_atoms;
+        grid_off += (size_t)cl.n[0] * cl.n[1] * cl.n[2];
+    }
+    return LASTO_OK;
+}
+
 // ================================================================ ABI
 extern "C" {
 
@@ -502,6 +555,7 @@ void lasto_config_default(lasto_config* c)
     c->rel_tol = 1e-10;
     c->n_theta = 16;
     c->n_phi = 32;
+    c->launch = 0;
 }
 
 int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
@@ -514,7 +568,8 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
         cfg->nu1 + cfg->nu2 < 1 || cfg->max_cycles < 1 || cfg->max_cycles >= CTL_HIST || !(cfg->rel_tol > 0.0) ||
         cfg->n_theta < 1 || cfg->n_theta > 32 || cfg->n_phi < 1 || cfg->n_phi > 64 ||
         (cfg->precision != LASTO_PREC_FP64 && cfg->precision != LASTO_PREC_MIXED) ||
-        (cfg->cycle != LASTO_CYCLE_V && cfg->cycle != LASTO_CYCLE_FV && cfg->cycle != LASTO_CYCLE_PCG))
+        (cfg->cycle != LASTO_CYCLE_V && cfg->cycle != LASTO_CYCLE_FV && cfg->cycle != LASTO_CYCLE_PCG) ||
+        (cfg->launch != 0 && cfg->launch != 1))
         return LASTO_ERR_INVALID_ARG;
     lasto_poisson* h = new (std::nothrow) lasto_poisson();
     if (!h) return LASTO_ERR_NO_MEMORY;
@@ -600,6 +655,11 @@ int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
     put(&guess, sizeof(guess));
     put(&nc, sizeof(nc));
     (void)total_atoms;
+    if (h->cfg.launch == 1) {
+        int st = direct_solve(h, cls, nc, v_lm, potential, guess, s);
+        if (st) return st;
+        return copy_stats(h, nc, stats, s);
+    }
     if (key != h->key || !h->exec) {
         // carve the workspace for these clusters
         h->plans.assign(nc, ClusterPlan());
@@ -615,19 +675,9 @@ int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
     }
     cudaError_t e = cudaGraphLaunch(h->exec, s);
     if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaGraphLaunch");
-    if (stats) {
-        for (int c = 0; c < nc; c++) {
-            e = cudaMemcpyAsync(h->stats_pinned + c, h->plans[c].stats_dev, sizeof(lasto_stats),
-                                cudaMemcpyDeviceToHost, s);
-            if (e != cudaSuccess) return set_cuda_error(&h->err, e, "stats copy");
-        }
-        h->stats_user = stats;
-        h->stats_count = nc;
-        e = cudaLaunchHostFunc(s, copy_stats_out, h);
-        if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaLaunchHostFunc");
-    }
-    return LASTO_OK;
+    return copy_stats(h, nc, stats, s);
 }
+
 
 // ---------------------------------------------------------------- mesh
 int lasto_mesh_axis(int n, double centre, double half_width, double h_min, double h_max, double p_max, double* x,

@@ -19,12 +19,21 @@
 // the atom's own spherical terms cancelling exactly rather than numerically.
 #include <cmath>
 
+#include "df.cuh"
 #include "internal.cuh"
 
 namespace lasto {
 
 // ---------------------------------------------------------------- harmonics table
 static __constant__ Mono c_mono[N_MONO_TERMS];
+
+// double-float copies for the FP32-pair deposit
+struct MonoF {
+    int lm, a, b, c;
+    float h, l;
+};
+static __constant__ MonoF c_mono_f[N_MONO_TERMS];
+static __constant__ float c_exp_h[64], c_exp_l[64];   // 2^(-j/64) as double-floats
 
 void host_monomials(Mono* o)
 {
@@ -83,6 +92,26 @@ static cudaError_t ensure_monomials()
     Mono t[N_MONO_TERMS];
     host_monomials(t);
     e = cudaMemcpyToSymbol(c_mono, t, sizeof(t));
+    if (e != cudaSuccess) return e;
+    MonoF tf[N_MONO_TERMS];
+    for (int i = 0; i < N_MONO_TERMS; i++) {
+        tf[i].lm = t[i].lm;
+        tf[i].a = t[i].a;
+        tf[i].b = t[i].b;
+        tf[i].c = t[i].c;
+        tf[i].h = (float)t[i].coef;
+        tf[i].l = (float)(t[i].coef - (double)tf[i].h);
+    }
+    e = cudaMemcpyToSymbol(c_mono_f, tf, sizeof(tf));
+    if (e != cudaSuccess) return e;
+    float eh[64], el[64];
+    for (int j = 0; j < 64; j++) {
+        const double v = std::exp2(-j / 64.0);
+        eh[j] = (float)v;
+        el[j] = (float)(v - (double)eh[j]);
+    }
+    e = cudaMemcpyToSymbol(c_exp_h, eh, sizeof(eh));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_exp_l, el, sizeof(el));
     if (e == cudaSuccess) g_mono_uploaded_device = dev;
     return e;
 }
@@ -108,12 +137,12 @@ __device__ __forceinline__ void solid_harmonics(double x, double y, double z, do
 
 // ---------------------------------------------------------------- sphere records
 // rec[i][*]: 0-2 pos, 3 R, 4-6 W_k, 7-9 zeta_k, 10-12 A_k, 13-15 B_k, 16-18 (a, b, c),
-// 19 q, 20 rho0(R), 21 rho0'(R)
-enum { RX = 0, RR = 3, RW = 4, RZ = 7, RA = 10, RB = 13, RC = 16, RQ = 19, RRHO = 20, RDRHO = 21 };
+// 19 q, 20 rho0(R), 21 rho0'(R), 24-47: c_lm / R^l as 24 double-floats (float pairs)
+enum { RX = 0, RR = 3, RW = 4, RZ = 7, RA = 10, RB = 13, RC = 16, RQ = 19, RRHO = 20, RDRHO = 21, RNS = 24 };
 
 struct SphArgs {
     int na;
-    const double *pos, *Z, *R, *w, *zeta;
+    const double *pos, *Z, *R, *w, *zeta, *clm;
     const double* ax[3];
     int n[3];
     double* rec;
@@ -195,6 +224,21 @@ __global__ void __launch_bounds__(SPH_NT) k_sphere_params(SphArgs a)
     r[RQ] = q;
     r[RRHO] = rho;
     r[RDRHO] = drho;
+    {
+        float* ns = reinterpret_cast<float*>(r + RNS);
+        double iRl = 1.0;
+        int l = 0;
+        for (int lm = 1; lm < NLM; lm++) {
+            const int ll = l_of_lm(lm);
+            while (l < ll) {
+                iRl /= Ri;
+                l++;
+            }
+            const double v = a.clm[24 * (size_t)i + lm - 1] * iRl;
+            ns[2 * (lm - 1)] = (float)v;
+            ns[2 * (lm - 1) + 1] = (float)(v - (double)(float)v);
+        }
+    }
     if (a.q) a.q[i] = q;
     if (a.rhoR) a.rhoR[i] = rho;
     if (a.drhoR) a.drhoR[i] = drho;
@@ -220,6 +264,7 @@ cudaError_t launch_sphere_params(const lasto_cluster& cl, const double* ax0, con
     a.R = cl.R;
     a.w = cl.slater_w;
     a.zeta = cl.slater_zeta;
+    a.clm = cl.c_lm;
     a.ax[0] = ax0;
     a.ax[1] = ax1;
     a.ax[2] = ax2;
@@ -245,6 +290,9 @@ struct DepArgs {
     int* owner;
     int* status;
 };
+
+constexpr int SAF = 16;   // FP32-pair deposit, per atom floats: D(x,y,z) pairs, W_k pairs, R^2, pad
+__global__ void k_deposit_df(DepArgs a);
 
 // per-atom fields staged in shared memory
 constexpr int SA = 14;  // x y z R^2 W0 W1 W2 A0 A1 A2 B0 B1 B2 R
@@ -362,10 +410,156 @@ cudaError_t launch_deposit(const lasto_cluster& cl, const double* rec, int preci
     a.status = status;
     const size_t N = (size_t)cl.n[0] * cl.n[1] * cl.n[2];
     const size_t smem = sizeof(double) * SA * (size_t)cl.n_atoms;
-    (void)precision;
+    if (precision == LASTO_PREC_MIXED) {
+        const size_t smf = sizeof(float) * (128 + SAF * (size_t)cl.n_atoms);
+        if (smf > 200 * 1024) return cudaErrorInvalidValue;
+        k_deposit_df<<<(unsigned)((N + DEP_NT - 1) / DEP_NT), DEP_NT, smf, s>>>(a);
+        return cudaGetLastError();
+    }
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     k_deposit64<<<(unsigned)((N + DEP_NT - 1) / DEP_NT), DEP_NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- deposit (FP32 pairs)
+using dfa::df;
+
+__device__ __forceinline__ bool inside_fp64(const DepArgs& a, double x, double y, double z, int t)
+{
+    const double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * t;
+    const double dx = x - r[RX], dy = y - r[RX + 1], dz = z - r[RX + 2];
+    return fma(dx, dx, fma(dy, dy, dz * dz)) < r[RR] * r[RR];
+}
+
+__global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
+{
+    extern __shared__ float sf[];
+    float* th = sf;
+    float* tl = sf + 64;
+    float* sat = sf + 128;
+    const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
+    const size_t nxy = (size_t)a.n[0] * a.n[1];
+    // block origin: the block's first node; offsets from it keep the pairs' magnitudes small
+    const size_t P0 = blockIdx.x * (size_t)DEP_NT;
+    const int k0 = (int)(P0 / nxy), j0 = (int)((P0 - (size_t)k0 * nxy) / a.n[0]);
+    const int i0 = (int)(P0 - (size_t)k0 * nxy - (size_t)j0 * a.n[0]);
+    const double ox = a.ax[0][i0], oy = a.ax[1][j0], oz = a.ax[2][k0];
+    for (int t = threadIdx.x; t < 64; t += DEP_NT) {
+        th[t] = c_exp_h[t];
+        tl[t] = c_exp_l[t];
+    }
+    for (int t = threadIdx.x; t < a.na; t += DEP_NT) {
+        const double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * t;
+        float* o = sat + SAF * t;
+        const df Dx = dfa::from_double(r[RX] - ox), Dy = dfa::from_double(r[RX + 1] - oy),
+                 Dz = dfa::from_double(r[RX + 2] - oz);
+        o[0] = Dx.h; o[1] = Dx.l; o[2] = Dy.h; o[3] = Dy.l; o[4] = Dz.h; o[5] = Dz.l;
+        for (int q = 0; q < 3; q++) {
+            const df W = dfa::from_double(r[RW + q]);
+            o[6 + 2 * q] = W.h;
+            o[7 + 2 * q] = W.l;
+        }
+        o[12] = (float)(r[RR] * r[RR]);
+    }
+    __syncthreads();
+    const size_t P = P0 + threadIdx.x;
+    if (P >= N) return;
+    const int k = (int)(P / nxy);
+    const int j = (int)((P - (size_t)k * nxy) / a.n[0]);
+    const int i = (int)(P - (size_t)k * nxy - (size_t)j * a.n[0]);
+    const double x = a.ax[0][i], y = a.ax[1][j], z = a.ax[2][k];
+    const df px = dfa::from_double(x - ox), py = dfa::from_double(y - oy), pz = dfa::from_double(z - oz);
+    df zt[3];
+    float zmin = 1e30f;
+    for (int q = 0; q < 3; q++) {
+        zt[q] = dfa::from_double(a.rec[RZ + q]);
+        zmin = fminf(zmin, zt[q].h);
+    }
+    const float cut = EXP_CUT / zmin;
+    const float cut2 = cut * cut * (1.0f + 1e-5f);
+    df s = {0.0f, 0.0f};
+    int own = -1;
+    df orr2 = {0.0f, 0.0f}, odx = s, ody = s, odz = s;
+    for (int t = 0; t < a.na; t++) {
+        const float* o = sat + SAF * t;
+        const df dx = dfa::add(px, df{-o[0], -o[1]});
+        const df dy = dfa::add(py, df{-o[2], -o[3]});
+        const df dz = dfa::add(pz, df{-o[4], -o[5]});
+        const df r2 = dfa::add(dfa::add(dfa::sqr(dx), dfa::sqr(dy)), dfa::sqr(dz));
+        if (r2.h > cut2) continue;
+        if (r2.h < o[12] * (1.0f + 2e-6f)) {
+            const bool in = (r2.h < o[12] * (1.0f - 2e-6f)) ? true : inside_fp64(a, x, y, z, t);
+            if (in) {
+                own = t;
+                orr2 = r2;
+                odx = dx;
+                ody = dy;
+                odz = dz;
+                continue;
+            }
+        }
+        const df r = dfa::sqrt_df(r2);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const df tq = dfa::mul(r, zt[q]);
+            if (tq.h < EXP_CUT) s = dfa::add(s, dfa::mul(df{o[6 + 2 * q], o[7 + 2 * q]}, dfa::exp_neg(tq, th, tl)));
+        }
+    }
+    if (own >= 0) {
+        const double* rc = a.rec + (size_t)SPHERE_REC_DOUBLES * own;
+        const df r = dfa::sqrt_df(orr2);
+        df nbr = {0.0f, 0.0f}, e1 = {1.0f, 0.0f};
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const df zr = dfa::mul(r, zt[q]);
+            const df em = dfa::exp_neg(zr, th, tl), ep = dfa::exp_neg(dfa::neg(zr), th, tl);
+            if (q == 0) e1 = em;
+            df shr;   // sinh(zeta r) / r
+            if (zr.h > 1e-3f) {
+                df sh = dfa::add(ep, dfa::neg(em));
+                sh.h *= 0.5f;
+                sh.l *= 0.5f;
+                shr = dfa::div(sh, r);
+            } else {
+                shr = dfa::mul(zt[q], dfa::add_f(df{1.0f, 0.0f}, zr.h * zr.h * (1.0f / 6.0f)));
+            }
+            df ch = dfa::add(ep, em);
+            ch.h *= 0.5f;
+            ch.l *= 0.5f;
+            const df A2 = dfa::from_double(2.0 * rc[RA + q]), B2 = dfa::from_double(2.0 * rc[RB + q]);
+            nbr = dfa::add(nbr, dfa::add(dfa::mul(A2, shr), dfa::neg(dfa::mul(B2, ch))));
+        }
+        const df ca = dfa::from_double(rc[RC]), cb = dfa::from_double(rc[RC + 1]), cc = dfa::from_double(rc[RC + 2]);
+        const df pseudo = dfa::add(ca, dfa::mul(orr2, dfa::add(cb, dfa::mul(orr2, cc))));
+        // nonspherical part: slater(zeta_1, r) (1 - r^2/R^2)^2 sum c_lm (r/R)^l y_lm
+        const float* ns = reinterpret_cast<const float*>(rc + RNS);
+        df pxs[5], pys[5], pzs[5];
+        pxs[0] = pys[0] = pzs[0] = df{1.0f, 0.0f};
+        for (int p = 1; p < 5; p++) {
+            pxs[p] = dfa::mul(pxs[p - 1], odx);
+            pys[p] = dfa::mul(pys[p - 1], ody);
+            pzs[p] = dfa::mul(pzs[p - 1], odz);
+        }
+        df ang = {0.0f, 0.0f};
+        for (int t = 1; t < N_MONO_TERMS; t++) {
+            const MonoF m = c_mono_f[t];
+            const df term = dfa::mul(dfa::mul(df{m.h, m.l}, df{ns[2 * (m.lm - 1)], ns[2 * (m.lm - 1) + 1]}),
+                                     dfa::mul(dfa::mul(pxs[m.a], pys[m.b]), pzs[m.c]));
+            ang = dfa::add(ang, term);
+        }
+        const double R = rc[RR];
+        const df invR2 = dfa::from_double(1.0 / (R * R));
+        const df tt = dfa::add_f(dfa::neg(dfa::mul(orr2, invR2)), 1.0f);
+        const double z1 = rc[RZ];
+        const df radial = dfa::mul(dfa::mul(dfa::from_double(z1 * z1 * z1 / (8.0 * PI)), e1), dfa::sqr(tt));
+        const df nsv = dfa::mul(radial, ang);
+        s = dfa::add(dfa::add(s, dfa::neg(nbr)), dfa::add(pseudo, nsv));
+    }
+    const df fourpi = dfa::from_double(4.0 * PI);
+    const double bv = dfa::to_double(dfa::mul(fourpi, s));
+    a.b[P] = bv;
+    if (a.owner) a.owner[P] = own;
+    if (!isfinite(bv) && a.status) atomicMax(a.status, (int)LASTO_ERR_NONFINITE);
 }
 
 void init_device_constants()
@@ -375,6 +569,7 @@ void init_device_constants()
     if (cudaGetDevice(&dev) != cudaSuccess || dev == done_dev) return;
     ensure_monomials();
     cudaFuncSetAttribute(k_deposit64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_deposit_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     done_dev = dev;
 }
 

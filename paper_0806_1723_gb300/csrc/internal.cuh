@@ -159,7 +159,7 @@ cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s);
 
 // density.cu
 void init_device_constants();   // constant tables and kernel attributes; call outside stream capture
-constexpr int SPHERE_REC_DOUBLES = 24;
+constexpr int SPHERE_REC_DOUBLES = 48;
 cudaError_t launch_sphere_params(const lasto_cluster& cl, const double* ax0, const double* ax1, const double* ax2,
                                  double* rec, double* q, double* rhoR, double* drhoR, double* coef, int* status,
                                  cudaStream_t s);

@@ -80,6 +80,17 @@ def test_pd55_graded_129(orc, precision):
     assert orc.norm2_interior(r) <= 2e-10 * orc.norm2_interior(orc.residual(x, y, z, ub, b))
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_direct_launch_matches_graph(orc, precision):
+    """The profiling launch mode runs the same kernels: same answer bit for bit."""
+    B = need_gpu()
+    cl = synth.pd13_small(n=33)
+    _, _, v_graph, _, st_g = gpu_solve(B, cl, precision=precision)
+    _, _, v_direct, _, st_d = gpu_solve(B, cl, precision=precision, launch=1)
+    assert st_g.status == 0 and st_d.status == 0 and st_g.cycles == st_d.cycles
+    assert np.array_equal(v_graph, v_direct)
+
+
 def test_replay_is_deterministic_and_tracks_new_density(orc):
     import torch
     B = need_gpu()
