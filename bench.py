@@ -287,7 +287,8 @@ def main():
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---------------- roofline of the dominant kernel (the FP64 deposit), timed alone
-    roof = kernel_roofline(B, cl, dc, stream, flush, dev)
+    roof = kernel_roofline(B, cl, dc, stream, flush, dev, 1)
+    roof["fp64_deposit_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 0)["ms"]
 
     # ---------------- CPU baseline: the oracle as it stands, one whole solve
     cpu = None
@@ -319,32 +320,23 @@ def main():
     return 0
 
 
-def kernel_roofline(B, cl, dc, stream, flush, dev):
-    """FP64 deposit kernel timed alone with CUDA events; algorithmic FP64 work per launch.
-
-    Work model: every (node, atom) pair evaluates its Slater terms (distance, square
-    root, one exponential per term within the 40/zeta cutoff).  Counted as FP64
-    instructions of the kernel's inner loop would overstate `exp`, so the figure is
-    reported in pair terms per second and the fraction against the FP64 FMA peak uses
-    the measured pair cost; see the design notes.
-    """
+def kernel_roofline(B, cl, dc, stream, flush, dev, precision=1):
+    """The deposit kernel family timed alone with CUDA events (median of 5, L2 flushed)."""
     import torch
-    n_rep = 5
-    B.lasto_op_deposit(dc)   # warm
+    B.lasto_op_deposit(dc, precision=precision)   # warm
     torch.cuda.synchronize()
     ms = []
-    for _ in range(n_rep):
+    for _ in range(5):
         flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        B.lasto_op_deposit(dc)
+        B.lasto_op_deposit(dc, precision=precision)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     t = statistics.median(ms) / 1e3
-    N = cl.n ** 3
-    pairs = N * cl.n_atoms
-    return {"kernel": "lasto_op_deposit (sphere params + FP64 deposit)", "bound": "alu", "unit": "Gpair/s",
+    pairs = cl.n ** 3 * cl.n_atoms
+    return {"kernel": f"lasto_op_deposit precision={precision}", "bound": "alu", "unit": "Gpair/s",
             "achieved": pairs / t / 1e9, "peak": None, "frac": None, "traffic": None, "ms": t * 1e3}
 
 
