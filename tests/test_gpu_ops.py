@@ -143,8 +143,10 @@ def test_deposit(orc, small_clusters, precision, tol):
         assert np.array_equal(host(owner), rowner)
         b = host(b)
         assert np.abs(b - ref).max() < tol * np.abs(ref).max()
-        big = np.abs(ref) > 1e-6 * np.abs(ref).max()
-        assert np.abs((b - ref)[big] / ref[big]).max() < 100 * tol
+        # node by node where the density matters; far out the GPU drops Slater terms below
+        # e^-40 of their weight (about 1e-14 absolute), which the oracle keeps
+        big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+        assert np.abs((b - ref)[big] / ref[big]).max() < 1e-10
 
 
 def test_multipoles_and_faces(orc, small_clusters):
