@@ -181,6 +181,23 @@ int lasto_op_sphere_params(const lasto_cluster* cl, double* q, double* rhoR, dou
  * exponentials.  status as above, plus NONFINITE. */
 int lasto_op_deposit(const lasto_cluster* cl, int precision, double* b, int* owner, int* status, void* stream);
 
+/* Allocation-free variant of lasto_op_deposit, for callers that cannot allocate device
+ * memory when they deposit (a fixed device-memory budget set at start-up, a device heap
+ * owned by another framework's allocator, a real-time loop that forbids allocation).
+ * The paper has no counterpart: this is a property of the library, not of the method.
+ * Same arguments, kernels and results as lasto_op_deposit; the per-sphere records live
+ * in one file-scope device array sized for 1024 atoms (384 KiB, held by every device
+ * that loads the library until exit) instead of allocator scratch.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ * Errors: INVALID_ARG when n_atoms > 1024 (or as lasto_op_deposit), CUDA when the
+ * array's device address cannot be found.
+ * The first call on each device looks up that address (and uploads the constant tables)
+ * with the device current; make that first call before any stream capture.  Every call
+ * shares the one array: calls that overlap on the GPU (two streams, or two host threads)
+ * race and must be ordered by the caller. */
+int lasto_op_deposit_noalloc(const lasto_cluster* cl, int precision, double* b, int* owner, int* status,
+                             void* stream);
+
 /* Boundary multipoles Q_lm = sum_nodes (b/4pi) vol r^l y_lm(node - centre), l <= 4,
  * vol = product of dual-cell lengths.  Q: device [25]. */
 int lasto_op_multipoles(const int n[3], const double* x, const double* y, const double* z, const double* b,

@@ -45,6 +45,7 @@ class lasto_stats(ctypes.Structure):
 
 EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve", "lasto_poisson_destroy",
            "lasto_poisson_last_error", "lasto_poisson_kernel_counts", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
+           "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
            "lasto_op_smooth_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
            "lasto_op_project"]
@@ -66,6 +67,7 @@ def _declare(L):
         "lasto_mesh_axis": (i, [i, d, d, d, d, d, vp, vp, vp]),
         "lasto_op_sphere_params": (i, [clp, vp, vp, vp, vp, vp, vp]),
         "lasto_op_deposit": (i, [clp, i, vp, vp, vp, vp]),
+        "lasto_op_deposit_noalloc": (i, [clp, i, vp, vp, vp, vp]),
         "lasto_op_multipoles": (i, [ip, vp, vp, vp, vp, ctypes.POINTER(d), vp, vp]),
         "lasto_op_boundary_fill": (i, [ip, vp, vp, vp, ctypes.POINTER(d), vp, vp, vp]),
         "lasto_op_apply": (i, [ip, vp, vp, vp, vp, vp, vp]),
@@ -245,6 +247,14 @@ def lasto_op_deposit(dc: DeviceCluster, precision=LASTO_PREC_FP64, stream=None):
     _check(load().lasto_op_deposit(ctypes.byref(c), int(precision), _ptr(b), _ptr(owner), _ptr(status),
                                    _stream(stream)), "lasto_op_deposit")
     return b, owner, status
+
+
+def lasto_op_deposit_noalloc(dc: DeviceCluster, b, owner=None, status=None, precision=LASTO_PREC_FP64, stream=None):
+    """Allocation-free deposit into caller buffers b (float64 [N]) and optional owner / status."""
+    c = dc.struct()
+    _check(load().lasto_op_deposit_noalloc(ctypes.byref(c), int(precision), _ptr(b), _ptr(owner), _ptr(status),
+                                           _stream(stream)), "lasto_op_deposit_noalloc")
+    return b
 
 
 def _axes(x, y, z):
