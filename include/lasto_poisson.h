@@ -63,8 +63,10 @@ enum lasto_status {
 
 enum lasto_precision {
     LASTO_PREC_FP64 = 0,  /* everything in FP64 ("plain" form) */
-    LASTO_PREC_MIXED = 1  /* FP32 smoothing/restriction/prolongation inside FP64 defect correction;
-                             the density exponentials in FP32-pair arithmetic (about 44 bits) */
+    LASTO_PREC_MIXED = 1  /* defect correction: FP64 residual and correction accumulation around
+                             an FP32 multigrid-preconditioned CG (FP32 smoothing, restriction,
+                             prolongation and CG vectors); the density exponentials in FP32-pair
+                             arithmetic (about 44 bits); moments and projection stay FP64 */
 };
 
 enum lasto_cycle {
@@ -110,10 +112,12 @@ typedef struct lasto_cluster {
 } lasto_cluster;
 
 typedef struct lasto_stats {
-    int cycles;         /* V-cycles or CG iterations run */
+    int cycles;         /* V-cycles or CG iterations run (all inner iterations for MIXED) */
     int status;         /* enum lasto_status of this cluster */
-    double rel_resid;   /* final ||b - A u|| / ||b_eff|| (true residual, recomputed) */
+    double rel_resid;   /* final ||b - A u|| / ||b_eff|| (true residual, recomputed in FP64) */
     double bnorm;       /* ||b_eff|| */
+    int outer;          /* FP64 defect-correction steps (MIXED with CG), else 0 */
+    int reserved;
 } lasto_stats;
 
 typedef struct lasto_poisson lasto_poisson;   /* opaque; owns workspace, plans and CUDA graphs */
@@ -141,10 +145,12 @@ void lasto_poisson_destroy(lasto_poisson* h);
 
 /* Kernel launches of the graph captured by the last lasto_poisson_solve on h:
  * *fixed = kernels that run once per solve (setup, deposit, multipoles, faces,
- * projection, ...), *per_iteration = kernels in one body of the iteration loop,
- * so one solve launches fixed + cycles * per_iteration kernels.  Host pointers.
- * Errors: INVALID_ARG if no solve has been captured yet. */
-int lasto_poisson_kernel_counts(const lasto_poisson* h, int* fixed, int* per_iteration);
+ * projection, ...), *per_iteration = kernels in one CG iteration or V-cycle,
+ * *per_outer = kernels of one defect-correction step outside its inner iterations
+ * (0 unless MIXED with CG); one solve launches
+ * fixed + cycles * per_iteration + outer * per_outer kernels (stats.cycles,
+ * stats.outer).  Host pointers.  Errors: INVALID_ARG if no graph was captured yet. */
+int lasto_poisson_kernel_counts(const lasto_poisson* h, int* fixed, int* per_iteration, int* per_outer);
 
 /* Text of the last error on this handle (never NULL; "" when none). */
 const char* lasto_poisson_last_error(const lasto_poisson* h);

@@ -40,7 +40,7 @@ class lasto_cluster(ctypes.Structure):
 
 class lasto_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_resid", ctypes.c_double),
-                ("bnorm", ctypes.c_double)]
+                ("bnorm", ctypes.c_double), ("outer", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve", "lasto_poisson_destroy",
@@ -63,7 +63,7 @@ def _declare(L):
         "lasto_poisson_solve": (i, [vp, clp, i, vp, vp, vp, stp, vp]),
         "lasto_poisson_destroy": (None, [vp]),
         "lasto_poisson_last_error": (ctypes.c_char_p, [vp]),
-        "lasto_poisson_kernel_counts": (i, [vp, ip, ip]),
+        "lasto_poisson_kernel_counts": (i, [vp, ip, ip, ip]),
         "lasto_mesh_axis": (i, [i, d, d, d, d, d, vp, vp, vp]),
         "lasto_op_sphere_params": (i, [clp, vp, vp, vp, vp, vp, vp]),
         "lasto_op_deposit": (i, [clp, i, vp, vp, vp, vp]),
@@ -202,11 +202,11 @@ class Poisson:
             pass
 
     def kernel_counts(self):
-        """(kernels per solve outside the loop, kernels per loop iteration) of the captured graph."""
-        f, it = ctypes.c_int(), ctypes.c_int()
-        _check(load().lasto_poisson_kernel_counts(self.h, ctypes.byref(f), ctypes.byref(it)),
+        """(once per solve, per CG iteration / V-cycle, per defect-correction step) kernel launches."""
+        f, it, ou = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().lasto_poisson_kernel_counts(self.h, ctypes.byref(f), ctypes.byref(it), ctypes.byref(ou)),
                "lasto_poisson_kernel_counts")
-        return f.value, it.value
+        return f.value, it.value, ou.value
 
     def last_error(self) -> str:
         return load().lasto_poisson_last_error(self.h).decode()

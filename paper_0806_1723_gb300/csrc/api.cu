@@ -58,6 +58,7 @@ struct ClusterPlan {
     int L = 0;
     LevelStore lv[MAX_LEVELS];
     double *p = nullptr, *q = nullptr, *z = nullptr;  // level-0 CG vectors (FP64)
+    float *e32 = nullptr, *p32 = nullptr, *q32 = nullptr;  // level-0 inner CG vectors (FP32)
     double* rec = nullptr;                            // sphere records
     double* mom = nullptr;                            // multipole scratch
     double* part = nullptr;                           // reduction partials
@@ -82,8 +83,10 @@ size_t cluster_bytes(const int n[3], int n_atoms)
         c.take<double>(N);          // inv_diag
         for (int t = 0; t < 3; t++) c.take<double>(N);
         for (int t = 0; t < 3; t++) c.take<float>(N);
-        if (l == 0)
+        if (l == 0) {
             for (int t = 0; t < 3; t++) c.take<double>(N);
+            for (int t = 0; t < 3; t++) c.take<float>(N);
+        }
         for (int d = 0; d < 3; d++) nn[d] = (nn[d] + 1) / 2;
     }
     c.take<double>((size_t)SPHERE_REC_DOUBLES * std::max(n_atoms, 1));
@@ -122,6 +125,9 @@ bool carve_cluster(Carver& c, const int n[3], int n_atoms, ClusterPlan& P)
             P.p = c.take<double>(N);
             P.q = c.take<double>(N);
             P.z = c.take<double>(N);
+            P.e32 = c.take<float>(N);
+            P.p32 = c.take<float>(N);
+            P.q32 = c.take<float>(N);
         }
         for (int d = 0; d < 3; d++) nn[d] = (nn[d] + 1) / 2;
     }
@@ -163,6 +169,7 @@ __global__ void k_write_stats(const Ctl* __restrict__ ctl, const int* __restrict
     s.rel_resid = ctl->true_rel;
     s.bnorm = ctl->bnorm;
     s.status = status[0] != 0 ? status[0] : ctl->status;
+    s.outer = ctl->outer;
     *out = s;
 }
 
@@ -176,7 +183,8 @@ struct lasto_poisson {
     size_t pool_bytes = 0;
     double* quad = nullptr;
     int nq = 0;
-    cudaStream_t cs = nullptr, cs2 = nullptr;
+    cudaStream_t cs = nullptr, cs2 = nullptr, cs3 = nullptr, cs4 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // cached graph
     std::vector<char> key;
     cudaGraph_t graph = nullptr;
@@ -186,8 +194,8 @@ struct lasto_poisson {
     lasto_stats* stats_pinned = nullptr;
     lasto_stats* stats_user = nullptr;
     int stats_count = 0;
-    int kernels_fixed = -1, kernels_iter = -1;
-    std::vector<cudaGraph_t> bodies;
+    int kernels_fixed = -1, kernels_iter = -1, kernels_outer = 0;
+    std::vector<cudaGraph_t> bodies, outer_bodies;
 };
 
 namespace {
@@ -305,6 +313,29 @@ int enqueue_rhs(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const
     return LASTO_OK;
 }
 
+// Setup and right-hand side of one cluster.  The mesh tables and the coarse eigenvectors
+// depend only on the mesh and run on a second stream beside the sphere parameters,
+// deposit, multipoles and faces; the two branches join before the iteration.
+int enqueue_prologue(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const double* guess, cudaStream_t s)
+{
+    TRY(cudaEventRecord(h->ev_fork, s));
+    TRY(cudaStreamWaitEvent(h->cs4, h->ev_fork, 0));
+    int st = enqueue_setup(h, P, cl, h->cs4);
+    if (st) return st;
+    TRY(cudaEventRecord(h->ev_join, h->cs4));
+    TRY(cudaMemsetAsync(P.status, 0, sizeof(int) * 4, s));
+    if ((st = enqueue_rhs(h, P, cl, guess, s))) return st;
+    TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+    return LASTO_OK;
+}
+
+// The mixed form with CG runs as defect correction: FP64 residual and correction
+// accumulation outside, FP32 multigrid-preconditioned CG inside.
+bool is_defect_correction(const lasto_poisson* h)
+{
+    return h->cfg.precision == LASTO_PREC_MIXED && h->cfg.cycle == LASTO_CYCLE_PCG;
+}
+
 // Prologue of the iteration: ||b_eff||, control block, F-cycle, starting residual.
 int enqueue_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s)
 {
@@ -314,17 +345,16 @@ int enqueue_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle c
     TRY(launch_bnorm_partials(V, F.u, F.b, P.part, s));
     TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_BNORM, cond, 0, s));
     const double tol = h->cfg.rel_tol;
-    TRY(launch_ctl_init(P.ctl, tol, cyc == LASTO_CYCLE_PCG ? 0.5 * tol : tol, h->cfg.max_cycles, s));
+    const bool dc = is_defect_correction(h);
+    TRY(launch_ctl_init(P.ctl, tol, (cyc == LASTO_CYCLE_PCG && !dc) ? 0.5 * tol : tol, h->cfg.max_cycles, s));
     if (cyc == LASTO_CYCLE_FV) {
         int st = enqueue_cycle<double>(h, P, 0, F.u, F.b, F.r, true, false, s);
         if (st) return st;
     }
-    TRY(launch_resid_norm_partials(V, F.u, F.b, F.r, P.part, s));
+    TRY(launch_resid_norm_partials(V, F.u, F.b, F.r, P.part, s, dc ? F.b32 : nullptr));
     TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_START, cond, use_cond, s));
-    if (cyc == LASTO_CYCLE_PCG) {
-        TRY(cudaMemsetAsync(P.p, 0, sizeof(double) * F.N(), s));
-        if (h->cfg.precision == LASTO_PREC_MIXED) TRY(launch_to_f32(F.r, F.b32, F.N(), s));
-    }
+    if (cyc == LASTO_CYCLE_PCG) TRY(cudaMemsetAsync(P.p, 0, sizeof(double) * F.N(), s));
+    if (dc) TRY(cudaMemsetAsync(P.e32, 0, sizeof(float) * F.N(), s));
     return LASTO_OK;
 }
 
@@ -364,6 +394,46 @@ int enqueue_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHand
     return LASTO_OK;
 }
 
+// One FP32 CG iteration of the inner solve A e = r32 (body of the inner WHILE node).
+int enqueue_inner_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle cond, int use_cond,
+                            cudaStream_t s)
+{
+    LevelStore& F = P.lv[0];
+    const LevelT<float> V = F.view32();
+    TRY(cudaMemsetAsync(F.u32, 0, sizeof(float) * F.N(), s));
+    int st = enqueue_cycle<float>(h, P, 0, F.u32, F.b32, F.r32, false, true, s);
+    if (st) return st;
+    TRY(launch_dot32(V, F.b32, F.u32, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_IN_BETA, cond, 0, s));
+    TRY(launch_update_p32(V, P.ctl, F.u32, P.p32, s));
+    TRY(launch_apply_dot32(V, P.p32, P.q32, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_IN_ALPHA, cond, 0, s));
+    TRY(launch_update_er32(V, P.ctl, P.p32, P.q32, P.e32, F.b32, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_IN_CHECK, cond, use_cond, s));
+    return LASTO_OK;
+}
+
+// Start of one defect-correction step: ||r32|| and a fresh inner CG.
+int enqueue_inner_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s)
+{
+    LevelStore& F = P.lv[0];
+    TRY(launch_dot32(F.view32(), F.b32, nullptr, P.part, s));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_IN_START, cond, use_cond, s));
+    TRY(cudaMemsetAsync(P.p32, 0, sizeof(float) * F.N(), s));
+    return LASTO_OK;
+}
+
+// End of one defect-correction step: u += e in FP64, true FP64 residual (and its FP32 copy).
+int enqueue_outer_finish(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle cond, int use_cond,
+                         cudaStream_t s)
+{
+    LevelStore& F = P.lv[0];
+    TRY(launch_add_correction(F.N(), F.u, P.e32, s));
+    TRY(launch_resid_norm_partials(F.view64(), F.u, F.b, F.r, P.part, s, F.b32));
+    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_OUTER, cond, use_cond, s));
+    return LASTO_OK;
+}
+
 int enqueue_finish(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, double* vlm, double* potential,
                    cudaStream_t s)
 {
@@ -378,50 +448,103 @@ int enqueue_finish(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, do
     return LASTO_OK;
 }
 
+// A conditional handle on the graph that stream s is capturing into.
+int new_handle(lasto_poisson* h, cudaStream_t s, cudaGraphConditionalHandle* cond)
+{
+    cudaStreamCaptureStatus cstat;
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cstat, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaStreamGetCaptureInfo");
+    e = cudaGraphConditionalHandleCreate(cond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaGraphConditionalHandleCreate");
+    return LASTO_OK;
+}
+
+// A WHILE node on `cond` after everything stream s has captured so far; s continues after it.
+int add_while(lasto_poisson* h, cudaStream_t s, cudaGraphConditionalHandle cond, cudaGraph_t* body)
+{
+    cudaStreamCaptureStatus cstat;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cstat, nullptr, &g, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaStreamGetCaptureInfo");
+    alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(cpbuf, 0, sizeof(cpbuf));
+    cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
+    cp->type = cudaGraphNodeTypeConditional;
+    cp->conditional.handle = cond;
+    cp->conditional.type = cudaGraphCondTypeWhile;
+    cp->conditional.size = 1;
+    cudaGraphNode_t wnode;
+    e = cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, cp);
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaGraphAddNode(while)");
+    *body = cp->conditional.phGraph_out[0];
+    e = cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaStreamUpdateCaptureDependencies");
+    return LASTO_OK;
+}
+
+int count_kernels(cudaGraph_t g)
+{
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(nd, &t);
+        if (t == cudaGraphNodeTypeKernel) k++;
+    }
+    return k;
+}
+
 int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,
                   const double* guess)
 {
     cudaStream_t s = h->cs;
     h->bodies.clear();
+    h->outer_bodies.clear();
     TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int st = LASTO_OK;
     size_t atom_off = 0, grid_off = 0;
     for (int c = 0; c < nc && st == LASTO_OK; c++) {
         ClusterPlan& P = h->plans[c];
         const lasto_cluster& cl = cls[c];
-        if ((st = (cudaMemsetAsync(P.status, 0, sizeof(int) * 4, s) == cudaSuccess) ? 0 : LASTO_ERR_CUDA)) break;
-        if ((st = enqueue_setup(h, P, cl, s))) break;
-        if ((st = enqueue_rhs(h, P, cl, guess ? guess + grid_off : nullptr, s))) break;
-        // conditional WHILE node for the iteration
-        cudaStreamCaptureStatus cstat;
-        cudaGraph_t g;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        cudaError_t e = cudaStreamGetCaptureInfo(s, &cstat, nullptr, &g, &deps, nullptr, &ndeps);
-        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamGetCaptureInfo"); break; }
+        if ((st = enqueue_prologue(h, P, cl, guess ? guess + grid_off : nullptr, s))) break;
+        // conditional WHILE node(s) for the iteration
         cudaGraphConditionalHandle cond;
-        e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
-        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaGraphConditionalHandleCreate"); break; }
+        if ((st = new_handle(h, s, &cond))) break;
         if ((st = enqueue_start(h, P, cond, 1, s))) break;
-        e = cudaStreamGetCaptureInfo(s, &cstat, nullptr, &g, &deps, nullptr, &ndeps);
-        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamGetCaptureInfo"); break; }
-        alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
-        std::memset(cpbuf, 0, sizeof(cpbuf));
-        cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
-        cp->type = cudaGraphNodeTypeConditional;
-        cp->conditional.handle = cond;
-        cp->conditional.type = cudaGraphCondTypeWhile;
-        cp->conditional.size = 1;
-        cudaGraphNode_t wnode;
-        e = cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, cp);
-        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaGraphAddNode(while)"); break; }
-        cudaGraph_t body = cp->conditional.phGraph_out[0];
-        h->bodies.push_back(body);
-        e = cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
-        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamUpdateCaptureDependencies"); break; }
-        e = cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        cudaGraph_t body;
+        if ((st = add_while(h, s, cond, &body))) break;
+        cudaError_t e = cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamBeginCaptureToGraph"); break; }
-        st = enqueue_iteration(h, P, cond, 1, h->cs2);
+        if (is_defect_correction(h)) {
+            // outer body: inner start, inner WHILE (FP32 CG), FP64 correction + residual
+            h->outer_bodies.push_back(body);
+            cudaGraphConditionalHandle cin;
+            cudaGraph_t ibody;
+            st = new_handle(h, h->cs2, &cin);
+            if (!st) st = enqueue_inner_start(h, P, cin, 1, h->cs2);
+            if (!st) st = add_while(h, h->cs2, cin, &ibody);
+            if (!st) {
+                h->bodies.push_back(ibody);
+                e = cudaStreamBeginCaptureToGraph(h->cs3, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+                if (e != cudaSuccess) st = set_cuda_error(&h->err, e, "cudaStreamBeginCaptureToGraph(inner)");
+                else {
+                    st = enqueue_inner_iteration(h, P, cin, 1, h->cs3);
+                    cudaGraph_t iout = nullptr;
+                    e = cudaStreamEndCapture(h->cs3, &iout);
+                    if (!st && e != cudaSuccess) st = set_cuda_error(&h->err, e, "cudaStreamEndCapture(inner)");
+                }
+            }
+            if (!st) st = enqueue_outer_finish(h, P, cond, 1, h->cs2);
+        } else {
+            h->bodies.push_back(body);
+            st = enqueue_iteration(h, P, cond, 1, h->cs2);
+        }
         cudaGraph_t bout = nullptr;
         e = cudaStreamEndCapture(h->cs2, &bout);
         if (st) break;
@@ -440,29 +563,12 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
     if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaStreamEndCapture");
     {
         // kernel nodes of the top-level graph and of the WHILE bodies
-        size_t nn = 0;
-        cudaGraphGetNodes(g, nullptr, &nn);
-        std::vector<cudaGraphNode_t> nodes(nn);
-        cudaGraphGetNodes(g, nodes.data(), &nn);
-        int fixed = 0, iter = 0;
-        for (auto nd : nodes) {
-            cudaGraphNodeType t;
-            cudaGraphNodeGetType(nd, &t);
-            if (t == cudaGraphNodeTypeKernel) fixed++;
-        }
-        for (cudaGraph_t bg : h->bodies) {
-            size_t bn = 0;
-            cudaGraphGetNodes(bg, nullptr, &bn);
-            std::vector<cudaGraphNode_t> bnodes(bn);
-            cudaGraphGetNodes(bg, bnodes.data(), &bn);
-            for (auto nd : bnodes) {
-                cudaGraphNodeType t;
-                cudaGraphNodeGetType(nd, &t);
-                if (t == cudaGraphNodeTypeKernel) iter++;
-            }
-        }
-        h->kernels_fixed = fixed;
-        h->kernels_iter = h->bodies.empty() ? 0 : iter / (int)h->bodies.size();
+        h->kernels_fixed = count_kernels(g);
+        int it = 0, ou = 0;
+        for (cudaGraph_t bg : h->bodies) it += count_kernels(bg);
+        for (cudaGraph_t bg : h->outer_bodies) ou += count_kernels(bg);
+        h->kernels_iter = h->bodies.empty() ? 0 : it / (int)h->bodies.size();
+        h->kernels_outer = h->outer_bodies.empty() ? 0 : ou / (int)h->outer_bodies.size();
     }
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
@@ -518,17 +624,32 @@ static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
         ClusterPlan& P = h->plans[c];
         const lasto_cluster& cl = cls[c];
         int st;
-        TRY(cudaMemsetAsync(P.status, 0, sizeof(int) * 4, s));
-        if ((st = enqueue_setup(h, P, cl, s))) return st;
-        if ((st = enqueue_rhs(h, P, cl, guess ? guess + grid_off : nullptr, s))) return st;
+        if ((st = enqueue_prologue(h, P, cl, guess ? guess + grid_off : nullptr, s))) return st;
         if ((st = enqueue_start(h, P, 0, 0, s))) return st;
         int done = 0;
         TRY(cudaMemcpyAsync(&done, &P.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
         TRY(cudaStreamSynchronize(s));
-        for (int it = 0; it < h->cfg.max_cycles && !done; it++) {
-            if ((st = enqueue_iteration(h, P, 0, 0, s))) return st;
-            TRY(cudaMemcpyAsync(&done, &P.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-            TRY(cudaStreamSynchronize(s));
+        if (is_defect_correction(h)) {
+            for (int outer = 0; outer < h->cfg.max_cycles && !done; outer++) {
+                if ((st = enqueue_inner_start(h, P, 0, 0, s))) return st;
+                int go = 0;
+                TRY(cudaMemcpyAsync(&go, &P.ctl->go_in, sizeof(int), cudaMemcpyDeviceToHost, s));
+                TRY(cudaStreamSynchronize(s));
+                while (go) {
+                    if ((st = enqueue_inner_iteration(h, P, 0, 0, s))) return st;
+                    TRY(cudaMemcpyAsync(&go, &P.ctl->go_in, sizeof(int), cudaMemcpyDeviceToHost, s));
+                    TRY(cudaStreamSynchronize(s));
+                }
+                if ((st = enqueue_outer_finish(h, P, 0, 0, s))) return st;
+                TRY(cudaMemcpyAsync(&done, &P.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+                TRY(cudaStreamSynchronize(s));
+            }
+        } else {
+            for (int it = 0; it < h->cfg.max_cycles && !done; it++) {
+                if ((st = enqueue_iteration(h, P, 0, 0, s))) return st;
+                TRY(cudaMemcpyAsync(&done, &P.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+                TRY(cudaStreamSynchronize(s));
+            }
         }
         if ((st = enqueue_finish(h, P, cl, v_lm + NLM * atom_off, potential ? potential + grid_off : nullptr, s)))
             return st;
@@ -590,6 +711,10 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
     if (e == cudaSuccess) e = cudaMemcpy(h->quad, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs3, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs4, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMallocHost(&h->stats_pinned, sizeof(lasto_stats) * cfg->max_batch);
     if (e != cudaSuccess) {
         lasto_poisson_destroy(h);
@@ -610,14 +735,19 @@ void lasto_poisson_destroy(lasto_poisson* h)
     if (h->stats_pinned) cudaFreeHost(h->stats_pinned);
     if (h->cs) cudaStreamDestroy(h->cs);
     if (h->cs2) cudaStreamDestroy(h->cs2);
+    if (h->cs3) cudaStreamDestroy(h->cs3);
+    if (h->cs4) cudaStreamDestroy(h->cs4);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
 }
 
-int lasto_poisson_kernel_counts(const lasto_poisson* h, int* fixed, int* per_iteration)
+int lasto_poisson_kernel_counts(const lasto_poisson* h, int* fixed, int* per_iteration, int* per_outer)
 {
-    if (!h || !fixed || !per_iteration || h->kernels_fixed < 0) return LASTO_ERR_INVALID_ARG;
+    if (!h || !fixed || !per_iteration || !per_outer || h->kernels_fixed < 0) return LASTO_ERR_INVALID_ARG;
     *fixed = h->kernels_fixed;
     *per_iteration = h->kernels_iter;
+    *per_outer = h->kernels_outer;
     return LASTO_OK;
 }
 

@@ -17,10 +17,16 @@ struct Ctl {
     double tol;        // requested relative tolerance
     double tol_iter;   // tolerance the loop checks (CG: half of tol, so the true residual meets tol)
     int iter, max_iter, status, done;
+    // inner FP32 CG of the mixed form (defect correction): scalars of the current inner solve
+    double rz_in, alpha_in, beta_in, rr0_in, tol_in;
+    int iter_in, max_in, outer, go_in;
     double hist[CTL_HIST];
 };
 
-enum FinOp { FIN_BNORM = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_START = 3, FIN_CHECK = 4, FIN_TRUE = 5 };
+enum FinOp {
+    FIN_BNORM = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_START = 3, FIN_CHECK = 4, FIN_TRUE = 5,
+    FIN_IN_START = 6, FIN_IN_ALPHA = 7, FIN_IN_BETA = 8, FIN_IN_CHECK = 9, FIN_OUTER = 10
+};
 
 cudaError_t launch_fin(Ctl* ctl, const double* part, int nparts, int op, cudaGraphConditionalHandle cond,
                        int use_cond, cudaStream_t s);

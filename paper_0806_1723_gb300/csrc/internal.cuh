@@ -147,7 +147,13 @@ struct Ctl;
 int reduce_blocks(const LevelT<double>& L);
 cudaError_t launch_bnorm_partials(const LevelT<double>& L, const double* u, const double* b, double* part, cudaStream_t s);
 cudaError_t launch_resid_norm_partials(const LevelT<double>& L, const double* u, const double* b, double* r,
-                                       double* part, cudaStream_t s);
+                                       double* part, cudaStream_t s, float* r32 = nullptr);
+cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, double* part, cudaStream_t s);
+cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
+                               float* r, double* part, cudaStream_t s);
+cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, double* part, cudaStream_t s);
+cudaError_t launch_update_p32(const LevelT<float>& L, const Ctl* ctl, const float* z, float* p, cudaStream_t s);
+cudaError_t launch_add_correction(size_t N, double* u, float* e, cudaStream_t s);
 cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, double* part, cudaStream_t s);
 cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const double* p, const double* q, double* u,
                              double* r, float* r32, double* part, cudaStream_t s);

@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(NT) k_bnorm_partials(LevelT<double> L, const d
 // r = b - A u (written when r != nullptr) and ||r||^2 partials
 __global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const double* __restrict__ u,
                                                   const double* __restrict__ b, double* __restrict__ r,
-                                                  double* __restrict__ part)
+                                                  float* __restrict__ r32, double* __restrict__ part)
 {
     __shared__ double sm[32];
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const doubl
         double v = 0.0;
         if (!is_face(L, i, j, k)) v = b[P] - fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
         if (r) r[P] = v;
+        if (r32) r32[P] = (float)v;
         acc = v * v;
     }
     const double s = block_sum<NT>(acc, sm);
@@ -404,6 +405,120 @@ __global__ void __launch_bounds__(NT) k_update_p(LevelT<double> L, const Ctl* __
     p[P] = is_face(L, i, j, k) ? 0.0 : fma(ctl->beta, p[P], (double)z[P]);
 }
 
+// ---------------------------------------------------------------- inner FP32 CG (defect correction)
+__device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int k)
+{
+    return L.ax[0].dual[i] * L.ax[1].dual[j] * L.ax[2].dual[k];
+}
+
+// q = A p and <p, q>_vol partials, FP32 vectors, FP64 block sums
+__global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p,
+                                                   float* __restrict__ q, double* __restrict__ part)
+{
+    __shared__ double sm[32];
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    double acc = 0.0;
+    if (P < L.N()) {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        float v = 0.0f;
+        if (!is_face(L, i, j, k)) {
+            v = fmaf(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
+            acc = (double)(vol32(L, i, j, k) * p[P] * v);
+        }
+        q[P] = v;
+    }
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// e += alpha p; r -= alpha q; ||r||^2 partials
+__global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* __restrict__ ctl,
+                                                   const float* __restrict__ p, const float* __restrict__ q,
+                                                   float* __restrict__ e, float* __restrict__ r,
+                                                   double* __restrict__ part)
+{
+    __shared__ double sm[32];
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    const float alpha = (float)ctl->alpha_in;
+    double acc = 0.0;
+    if (P < L.N()) {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (!is_face(L, i, j, k)) {
+            e[P] = fmaf(alpha, p[P], e[P]);
+            const float rv = fmaf(-alpha, q[P], r[P]);
+            r[P] = rv;
+            acc = (double)rv * (double)rv;
+        }
+    }
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// <r, z>_vol partials (FP32) or ||r||^2 partials (z == nullptr)
+__global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __restrict__ r,
+                                             const float* __restrict__ z, double* __restrict__ part)
+{
+    __shared__ double sm[32];
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    double acc = 0.0;
+    if (P < L.N()) {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (!is_face(L, i, j, k)) acc = z ? (double)(vol32(L, i, j, k) * r[P] * z[P]) : (double)r[P] * (double)r[P];
+    }
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* __restrict__ ctl,
+                                                  const float* __restrict__ z, float* __restrict__ p)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= L.N()) return;
+    int i, j, k;
+    node_ijk(P, L.nx, L.ny, i, j, k);
+    p[P] = is_face(L, i, j, k) ? 0.0f : fmaf((float)ctl->beta_in, p[P], z[P]);
+}
+
+// u += e (FP64 accumulation of the FP32 correction); e = 0 for the next inner solve
+__global__ void __launch_bounds__(NT) k_add_correction(size_t N, double* __restrict__ u, float* __restrict__ e)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= N) return;
+    u[P] += (double)e[P];
+    e[P] = 0.0f;
+}
+
+#define GRID32(L) (unsigned)((L.N() + NT - 1) / NT), NT, 0, s
+cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, double* part, cudaStream_t s)
+{
+    k_apply_dot32<<<GRID32(L)>>>(L, p, q, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
+                               float* r, double* part, cudaStream_t s)
+{
+    k_update_er32<<<GRID32(L)>>>(L, ctl, p, q, e, r, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, double* part, cudaStream_t s)
+{
+    k_dot32<<<GRID32(L)>>>(L, r, z, part);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_p32(const LevelT<float>& L, const Ctl* ctl, const float* z, float* p, cudaStream_t s)
+{
+    k_update_p32<<<GRID32(L)>>>(L, ctl, z, p);
+    return cudaGetLastError();
+}
+cudaError_t launch_add_correction(size_t N, double* u, float* e, cudaStream_t s)
+{
+    k_add_correction<<<(unsigned)((N + NT - 1) / NT), NT, 0, s>>>(N, u, e);
+    return cudaGetLastError();
+}
+
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n)
 {
     const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
@@ -418,9 +533,9 @@ cudaError_t launch_bnorm_partials(const LevelT<double>& L, const double* u, cons
     return cudaGetLastError();
 }
 cudaError_t launch_resid_norm_partials(const LevelT<double>& L, const double* u, const double* b, double* r,
-                                       double* part, cudaStream_t s)
+                                       double* part, cudaStream_t s, float* r32)
 {
-    k_resid_norm<<<GRID(L)>>>(L, u, b, r, part);
+    k_resid_norm<<<GRID(L)>>>(L, u, b, r, r32, part);
     return cudaGetLastError();
 }
 cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, double* part, cudaStream_t s)
@@ -502,6 +617,53 @@ __global__ void __launch_bounds__(NT) k_fin(Ctl* ctl, const double* __restrict__
             if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
             break;
         }
+        case FIN_IN_START: {   // ||r||^2 of the new inner right-hand side; reset the inner CG
+            c.rr0_in = s;
+            c.rz_in = 1.0;
+            c.alpha_in = c.beta_in = 0.0;
+            c.iter_in = 0;
+            const int go = (s > 0.0 && isfinite(s) && c.iter < c.max_iter) ? 1 : 0;
+            c.go_in = go;
+            if (use_cond) cudaGraphSetConditional(cond, (unsigned)go);
+            break;
+        }
+        case FIN_IN_ALPHA:
+            c.alpha_in = (s != 0.0 && isfinite(s)) ? c.rz_in / s : 0.0;
+            break;
+        case FIN_IN_BETA:
+            c.beta_in = (c.iter_in == 0 || c.rz_in == 0.0) ? 0.0 : s / c.rz_in;
+            c.rz_in = s;
+            break;
+        case FIN_IN_CHECK: {
+            c.iter += 1;
+            c.iter_in += 1;
+            const double rel_in = c.rr0_in > 0.0 ? sqrt(s / c.rr0_in) : 0.0;
+            const int go = (isfinite(rel_in) && rel_in > c.tol_in && c.iter_in < c.max_in && c.iter < c.max_iter) ? 1 : 0;
+            c.go_in = go;
+            if (use_cond) cudaGraphSetConditional(cond, (unsigned)go);
+            break;
+        }
+        case FIN_OUTER: {   // true FP64 residual after a correction step
+            const double scale = c.bnorm > 0.0 ? c.bnorm : 1.0;
+            const double rel = sqrt(s) / scale;
+            c.outer += 1;
+            c.rel = rel;
+            if (c.iter < CTL_HIST) c.hist[c.iter] = rel;
+            int go = 1;
+            if (!isfinite(rel)) {
+                c.status = LASTO_ERR_NONFINITE;
+                go = 0;
+            } else if (rel <= c.tol) {
+                c.status = LASTO_OK;
+                go = 0;
+            } else if (c.iter >= c.max_iter) {
+                c.status = LASTO_ERR_NOT_CONVERGED;
+                go = 0;
+            }
+            c.done = !go;
+            if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+            break;
+        }
         case FIN_TRUE: {
             const double scale = c.bnorm > 0.0 ? c.bnorm : 1.0;
             c.true_rel = sqrt(s) / scale;
@@ -533,6 +695,12 @@ __global__ void k_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter)
     c.rz = 1.0;
     c.alpha = c.beta = 0.0;
     c.rel = c.true_rel = -1.0;
+    c.rz_in = 1.0;
+    c.alpha_in = c.beta_in = c.rr0_in = 0.0;
+    c.tol_in = 2e-5;
+    c.iter_in = 0;
+    c.max_in = 40;
+    c.outer = 0;
 }
 
 cudaError_t launch_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter, cudaStream_t s)
