@@ -233,12 +233,36 @@ struct Arr<float> {
     static LevelT<float> view(const LevelStore& s) { return s.view32(); }
 };
 
+// First level run by the one-block bottom kernel (its correction starts at zero, so not
+// level 0), or -1 when every level is launched separately.
+int bottom_level(const ClusterPlan& P)
+{
+    for (int l = 1; l < P.L - 1; l++)
+        if (P.lv[l].N() <= BOTTOM_MAX_NODES && P.L - l <= BOTTOM_MAX_LEVELS) return l;
+    return -1;
+}
+
 template <typename T>
 int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, bool fcycle, bool sym, cudaStream_t s)
 {
     LevelStore& S = P.lv[l];
     const LevelT<T> V = Arr<T>::view(S);
     const int nu1 = h->cfg.nu1, nu2 = h->cfg.nu2;
+    if (!fcycle && l > 0 && l == bottom_level(P)) {
+        BottomArgs<T> a;
+        a.nlev = P.L - l;
+        for (int q = 0; q < a.nlev; q++) {
+            a.lv[q] = Arr<T>::view(P.lv[l + q]);
+            a.u[q] = Arr<T>::u(P.lv[l + q]);
+            a.b[q] = Arr<T>::b(P.lv[l + q]);
+        }
+        a.eig = P.eig;
+        a.nu1 = nu1;
+        a.nu2 = nu2;
+        a.sym = sym ? 1 : 0;
+        TRY(launch_bottom<T>(a, s));
+        return LASTO_OK;
+    }
     if (l == P.L - 1) {
         if (l == 0) {
             TRY(launch_residual<T>(V, u, b, r, s));
@@ -252,11 +276,10 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
         TRY(launch_rbgs<T>(V, u, b, 0, s));
         TRY(launch_rbgs<T>(V, u, b, 1, s));
     }
-    TRY(launch_residual<T>(V, u, b, r, s));
     LevelStore& C = P.lv[l + 1];
     const LevelT<T> VC = Arr<T>::view(C);
-    TRY(launch_restrict<T>(V, VC, r, Arr<T>::b(C), s));
-    TRY(cudaMemsetAsync(Arr<T>::u(C), 0, sizeof(T) * C.N(), s));
+    (void)r;
+    TRY(launch_resid_restrict<T>(V, VC, u, b, Arr<T>::b(C), Arr<T>::u(C), s));
     int st = enqueue_cycle<T>(h, P, l + 1, Arr<T>::u(C), Arr<T>::b(C), Arr<T>::r(C), fcycle, sym, s);
     if (st) return st;
     if (fcycle) {

@@ -18,7 +18,7 @@ struct Ctl {
     double tol_iter;   // tolerance the loop checks (CG: half of tol, so the true residual meets tol)
     int iter, max_iter, status, done;
     // inner FP32 CG of the mixed form (defect correction): scalars of the current inner solve
-    double rz_in, alpha_in, beta_in, rr0_in, tol_in;
+    double rz_in, alpha_in, beta_in, rr0_in, tol_in, tol_in_eff;
     int iter_in, max_in, outer, go_in;
     double hist[CTL_HIST];
 };

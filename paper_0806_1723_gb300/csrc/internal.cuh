@@ -142,6 +142,24 @@ cudaError_t launch_prolong_add(const LevelT<T>& fine, const LevelT<T>& coarse, c
 template <typename T>
 cudaError_t launch_coarse_apply(const LevelT<T>& L, const CoarseEig* eig, const T* b, T* e, bool add, cudaStream_t s);
 
+template <typename T>
+cudaError_t launch_resid_restrict(const LevelT<T>& fine, const LevelT<T>& coarse, const T* u, const T* b, T* bc, T* uc,
+                                  cudaStream_t s);
+
+// Levels lb..L-1 of a V-cycle in one thread block (u[0] = 0 on entry).
+constexpr int BOTTOM_MAX_LEVELS = 4;
+constexpr size_t BOTTOM_MAX_NODES = 40000;   // the top bottom level has at most this many nodes
+template <typename T>
+struct BottomArgs {
+    LevelT<T> lv[BOTTOM_MAX_LEVELS];
+    T* u[BOTTOM_MAX_LEVELS];
+    T* b[BOTTOM_MAX_LEVELS];
+    const CoarseEig* eig;
+    int nlev, nu1, nu2, sym;
+};
+template <typename T>
+cudaError_t launch_bottom(const BottomArgs<T>& a, cudaStream_t s);
+
 // reductions / CG (mg.cu)
 struct Ctl;
 int reduce_blocks(const LevelT<double>& L);

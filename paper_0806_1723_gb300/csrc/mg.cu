@@ -195,11 +195,12 @@ cudaError_t launch_prolong_add(const LevelT<T>& F, const LevelT<T>& C, const T* 
 constexpr int MC = MAX_COARSE - 2;
 constexpr int MC3 = MC * MC * MC;
 
+// Exact solve on the coarsest grid by fast diagonalisation; one thread block, s0/s1 are
+// shared buffers of MC3 doubles.  add = 1: e += A^-1 b; add = 0: e = A^-1 b with zero faces.
 template <typename T>
-__global__ void __launch_bounds__(512) k_coarse_apply(LevelT<T> L, const CoarseEig* __restrict__ E,
-                                                     const T* __restrict__ b, T* __restrict__ e, int add)
+__device__ void coarse_apply_block(const LevelT<T>& L, const CoarseEig* __restrict__ E, const T* __restrict__ b,
+                                   T* __restrict__ e, int add, double* s0, double* s1)
 {
-    __shared__ double s0[MC3], s1[MC3];
     const int mx = L.nx - 2, my = L.ny - 2, mz = L.nz - 2, M = mx * my * mz;
     const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
     auto node = [&](int a, int bb, int c) { return (size_t)(c + 1) * sz + (size_t)(bb + 1) * sy + (a + 1); };
@@ -214,7 +215,6 @@ __global__ void __launch_bounds__(512) k_coarse_apply(LevelT<T> L, const CoarseE
     const double* Bx = E->B[0];
     const double* By = E->B[1];
     const double* Bz = E->B[2];
-    // forward along x, y, z
     for (int t = threadIdx.x; t < M; t += blockDim.x) {
         const int p = t % mx, rest = t / mx;
         double acc = 0.0;
@@ -236,7 +236,6 @@ __global__ void __launch_bounds__(512) k_coarse_apply(LevelT<T> L, const CoarseE
         s1[t] = acc / (E->lam[0][p] + E->lam[1][q] + E->lam[2][sidx]);
     }
     __syncthreads();
-    // backward along z, y, x
     for (int t = threadIdx.x; t < M; t += blockDim.x) {
         const int p = t % mx, q = (t / mx) % my, c = t / (mx * my);
         double acc = 0.0;
@@ -266,12 +265,172 @@ __global__ void __launch_bounds__(512) k_coarse_apply(LevelT<T> L, const CoarseE
             if (is_face(L, i, j, k)) e[t] = T(0);
         }
     }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_coarse_apply(LevelT<T> L, const CoarseEig* __restrict__ E,
+                                                     const T* __restrict__ b, T* __restrict__ e, int add)
+{
+    __shared__ double s0[MC3], s1[MC3];
+    coarse_apply_block<T>(L, E, b, e, add, s0, s1);
 }
 
 template <typename T>
 cudaError_t launch_coarse_apply(const LevelT<T>& L, const CoarseEig* eig, const T* b, T* e, bool add, cudaStream_t s)
 {
     k_coarse_apply<T><<<1, 512, 0, s>>>(L, eig, b, e, add ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- fused residual + restriction
+// bc = Vc^-1 P^T Vf (b - A u) with the 27 fine residuals formed on the fly, and the coarse
+// correction uc zeroed for the recursion: one pass instead of residual, restriction, memset.
+template <typename T>
+__device__ __forceinline__ T resid_at(const LevelT<T>& F, const T* __restrict__ u, const T* __restrict__ b, size_t P,
+                                      int i, int j, int k)
+{
+    return b[P] - fma(-dsum(F, i, j, k), u[P], offdiag(F, u, P, i, j, k));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_resid_restrict(LevelT<T> F, LevelT<T> C, const T* __restrict__ u,
+                                                      const T* __restrict__ b, T* __restrict__ bc, T* __restrict__ uc)
+{
+    const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (t >= C.N()) return;
+    int I, J, K;
+    node_ijk(t, C.nx, C.ny, I, J, K);
+    uc[t] = T(0);
+    if (is_face(C, I, J, K)) {
+        bc[t] = T(0);
+        return;
+    }
+    const T* wx = F.ax[0].rw + 3 * I;
+    const T* wy = F.ax[1].rw + 3 * J;
+    const T* wz = F.ax[2].rw + 3 * K;
+    const size_t sy = F.nx, sz = (size_t)F.nx * F.ny;
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+#pragma unroll
+        for (int bb = 0; bb < 3; bb++) {
+            const int fk = 2 * K - 1 + c, fj = 2 * J - 1 + bb, fi = 2 * I - 1;
+            const size_t P = (size_t)fk * sz + (size_t)fj * sy + fi;
+            const T r0 = resid_at(F, u, b, P, fi, fj, fk);
+            const T r1 = resid_at(F, u, b, P + 1, fi + 1, fj, fk);
+            const T r2 = resid_at(F, u, b, P + 2, fi + 2, fj, fk);
+            acc = fma(wz[c] * wy[bb], fma(wx[0], r0, fma(wx[1], r1, wx[2] * r2)), acc);
+        }
+    bc[t] = acc;
+}
+
+template <typename T>
+cudaError_t launch_resid_restrict(const LevelT<T>& F, const LevelT<T>& C, const T* u, const T* b, T* bc, T* uc,
+                                  cudaStream_t s)
+{
+    k_resid_restrict<T><<<(unsigned)((C.N() + NT - 1) / NT), NT, 0, s>>>(F, C, u, b, bc, uc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- bottom V-cycle (one block)
+// Levels lb..L-1 of a V-cycle in one thread block: the small levels cost far more in launch
+// latency than in work, so smoothing, residual, restriction, the exact coarsest solve and
+// prolongation run as phases separated by __syncthreads.  u[lb] must be zero on entry.
+constexpr int BOT_NT = 1024;
+
+template <typename T>
+__device__ void bot_rbgs(const LevelT<T>& L, T* __restrict__ u, const T* __restrict__ b, int colour)
+{
+    const size_t N = L.N(), nhalf = (N + 1 - colour) / 2;
+    for (size_t t = threadIdx.x; t < nhalf; t += BOT_NT) {
+        const size_t P = 2 * t + colour;
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (is_face(L, i, j, k)) continue;
+        const T acc = b[P] - offdiag(L, u, P, i, j, k);
+        if constexpr (sizeof(T) == 8) u[P] = acc * L.inv_diag[P];
+        else u[P] = acc / (-dsum(L, i, j, k));
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
+{
+    __shared__ double s0[MC3], s1[MC3];
+    const int nl = a.nlev;
+    for (int l = 0; l < nl - 1; l++) {
+        const LevelT<T>& F = a.lv[l];
+        for (int it = 0; it < a.nu1; it++) {
+            bot_rbgs(F, a.u[l], a.b[l], 0);
+            bot_rbgs(F, a.u[l], a.b[l], 1);
+        }
+        const LevelT<T>& C = a.lv[l + 1];
+        for (size_t t = threadIdx.x; t < C.N(); t += BOT_NT) {
+            int I, J, K;
+            node_ijk(t, C.nx, C.ny, I, J, K);
+            a.u[l + 1][t] = T(0);
+            if (is_face(C, I, J, K)) {
+                a.b[l + 1][t] = T(0);
+                continue;
+            }
+            const T* wx = F.ax[0].rw + 3 * I;
+            const T* wy = F.ax[1].rw + 3 * J;
+            const T* wz = F.ax[2].rw + 3 * K;
+            const size_t sy = F.nx, sz = (size_t)F.nx * F.ny;
+            T acc = T(0);
+            for (int c = 0; c < 3; c++)
+                for (int bb = 0; bb < 3; bb++) {
+                    const int fk = 2 * K - 1 + c, fj = 2 * J - 1 + bb, fi = 2 * I - 1;
+                    const size_t P = (size_t)fk * sz + (size_t)fj * sy + fi;
+                    const T r0 = resid_at(F, a.u[l], a.b[l], P, fi, fj, fk);
+                    const T r1 = resid_at(F, a.u[l], a.b[l], P + 1, fi + 1, fj, fk);
+                    const T r2 = resid_at(F, a.u[l], a.b[l], P + 2, fi + 2, fj, fk);
+                    acc = fma(wz[c] * wy[bb], fma(wx[0], r0, fma(wx[1], r1, wx[2] * r2)), acc);
+                }
+            a.b[l + 1][t] = acc;
+        }
+        __syncthreads();
+    }
+    coarse_apply_block<T>(a.lv[nl - 1], a.eig, a.b[nl - 1], a.u[nl - 1], 0, s0, s1);
+    for (int l = nl - 2; l >= 0; l--) {
+        const LevelT<T>& F = a.lv[l];
+        const LevelT<T>& C = a.lv[l + 1];
+        const T* ec = a.u[l + 1];
+        T* u = a.u[l];
+        for (size_t P = threadIdx.x; P < F.N(); P += BOT_NT) {
+            int i, j, k;
+            node_ijk(P, F.nx, F.ny, i, j, k);
+            if (is_face(F, i, j, k)) continue;
+            const int I = i >> 1, J = j >> 1, K = k >> 1;
+            const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+            const T wx[2] = {F.ax[0].pl[i], F.ax[0].pr[i]};
+            const T wy[2] = {F.ax[1].pl[j], F.ax[1].pr[j]};
+            const T wz[2] = {F.ax[2].pl[k], F.ax[2].pr[k]};
+            const size_t sy = C.nx, sz = (size_t)C.nx * C.ny;
+            const T* base = ec + (size_t)K * sz + (size_t)J * sy + I;
+            T e = T(0);
+            for (int c = 0; c < nk; c++)
+                for (int bb = 0; bb < nj; bb++) {
+                    const T* row = base + c * sz + bb * sy;
+                    const T sv = (ni == 2) ? fma(wx[0], row[0], wx[1] * row[1]) : row[0];
+                    e = fma(wz[c] * wy[bb], sv, e);
+                }
+            u[P] += e;
+        }
+        __syncthreads();
+        for (int it = 0; it < a.nu2; it++) {
+            bot_rbgs(F, u, a.b[l], a.sym ? 1 : 0);
+            bot_rbgs(F, u, a.b[l], a.sym ? 0 : 1);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_bottom(const BottomArgs<T>& a, cudaStream_t s)
+{
+    k_bottom<T><<<1, BOT_NT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -618,6 +777,8 @@ __global__ void __launch_bounds__(NT) k_fin(Ctl* ctl, const double* __restrict__
             break;
         }
         case FIN_IN_START: {   // ||r||^2 of the new inner right-hand side; reset the inner CG
+            // reduce only as far as the outer tolerance needs on the last step (0.3 safety)
+            c.tol_in_eff = (c.rel > 0.0) ? fmax(c.tol_in, 0.3 * c.tol / c.rel) : c.tol_in;
             c.rr0_in = s;
             c.rz_in = 1.0;
             c.alpha_in = c.beta_in = 0.0;
@@ -638,7 +799,7 @@ __global__ void __launch_bounds__(NT) k_fin(Ctl* ctl, const double* __restrict__
             c.iter += 1;
             c.iter_in += 1;
             const double rel_in = c.rr0_in > 0.0 ? sqrt(s / c.rr0_in) : 0.0;
-            const int go = (isfinite(rel_in) && rel_in > c.tol_in && c.iter_in < c.max_in && c.iter < c.max_iter) ? 1 : 0;
+            const int go = (isfinite(rel_in) && rel_in > c.tol_in_eff && c.iter_in < c.max_in && c.iter < c.max_iter) ? 1 : 0;
             c.go_in = go;
             if (use_cond) cudaGraphSetConditional(cond, (unsigned)go);
             break;
@@ -711,6 +872,9 @@ cudaError_t launch_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter,
 
 // ---------------------------------------------------------------- instantiations
 #define INST(T)                                                                                              \
+    template cudaError_t launch_resid_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, const T*, T*, T*, \
+                                                  cudaStream_t);                                             \
+    template cudaError_t launch_bottom<T>(const BottomArgs<T>&, cudaStream_t);                              \
     template cudaError_t launch_rbgs<T>(const LevelT<T>&, T*, const T*, int, cudaStream_t);                 \
     template cudaError_t launch_residual<T>(const LevelT<T>&, const T*, const T*, T*, cudaStream_t);        \
     template cudaError_t launch_apply<T>(const LevelT<T>&, const T*, T*, cudaStream_t);                     \
