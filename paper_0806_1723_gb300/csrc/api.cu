@@ -234,7 +234,8 @@ struct Arr<float> {
 };
 
 // First level run by the one-block bottom kernel (its correction starts at zero, so not
-// level 0), or -1 when every level is launched separately.
+// level 0), or -1 when every level is launched separately.  FP32 only: one SM's FP64 units
+// are far too slow for even a 17^3 level, while FP32 work this small is pure launch latency.
 int bottom_level(const ClusterPlan& P)
 {
     for (int l = 1; l < P.L - 1; l++)
@@ -248,7 +249,7 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
     LevelStore& S = P.lv[l];
     const LevelT<T> V = Arr<T>::view(S);
     const int nu1 = h->cfg.nu1, nu2 = h->cfg.nu2;
-    if (!fcycle && l > 0 && l == bottom_level(P)) {
+    if (sizeof(T) == 4 && !fcycle && l > 0 && l == bottom_level(P)) {
         BottomArgs<T> a;
         a.nlev = P.L - l;
         for (int q = 0; q < a.nlev; q++) {

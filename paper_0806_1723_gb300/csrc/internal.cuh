@@ -148,7 +148,7 @@ cudaError_t launch_resid_restrict(const LevelT<T>& fine, const LevelT<T>& coarse
 
 // Levels lb..L-1 of a V-cycle in one thread block (u[0] = 0 on entry).
 constexpr int BOTTOM_MAX_LEVELS = 4;
-constexpr size_t BOTTOM_MAX_NODES = 40000;   // the top bottom level has at most this many nodes
+constexpr size_t BOTTOM_MAX_NODES = 5000;    // the top bottom level has at most this many nodes (17^3)
 template <typename T>
 struct BottomArgs {
     LevelT<T> lv[BOTTOM_MAX_LEVELS];
