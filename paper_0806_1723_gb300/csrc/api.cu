@@ -279,8 +279,15 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
     }
     LevelStore& C = P.lv[l + 1];
     const LevelT<T> VC = Arr<T>::view(C);
-    (void)r;
-    TRY(launch_resid_restrict<T>(V, VC, u, b, Arr<T>::b(C), Arr<T>::u(C), s));
+    if (sizeof(T) == 4) {
+        // FP32: form the 27 fine residuals inside the restriction (cheaper than a pass)
+        TRY(launch_resid_restrict<T>(V, VC, u, b, Arr<T>::b(C), Arr<T>::u(C), s));
+    } else {
+        // FP64: each residual once (FP64 arithmetic, not bandwidth, bounds this chip)
+        TRY(launch_residual<T>(V, u, b, r, s));
+        TRY(launch_restrict<T>(V, VC, r, Arr<T>::b(C), s));
+        TRY(cudaMemsetAsync(Arr<T>::u(C), 0, sizeof(T) * C.N(), s));
+    }
     int st = enqueue_cycle<T>(h, P, l + 1, Arr<T>::u(C), Arr<T>::b(C), Arr<T>::r(C), fcycle, sym, s);
     if (st) return st;
     if (fcycle) {
