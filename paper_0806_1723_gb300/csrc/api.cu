@@ -66,8 +66,12 @@ struct ClusterPlan {
     double* Q = nullptr;
     Ctl* ctl = nullptr;
     CoarseEig* eig = nullptr;
-    int* status = nullptr;
+    int* status = nullptr;              // [0] status, [1] reduction ticket counter
     lasto_stats* stats_dev = nullptr;
+    Red red(int op, cudaGraphConditionalHandle cond = 0, int use_cond = 0) const
+    {
+        return Red{part, reinterpret_cast<unsigned int*>(status + 1), ctl, op, cond, use_cond};
+    }
 };
 
 size_t cluster_bytes(const int n[3], int n_atoms)
@@ -373,8 +377,7 @@ int enqueue_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle c
     LevelStore& F = P.lv[0];
     const LevelT<double> V = F.view64();
     const int cyc = h->cfg.cycle;
-    TRY(launch_bnorm_partials(V, F.u, F.b, P.part, s));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_BNORM, cond, 0, s));
+    TRY(launch_bnorm(V, F.u, F.b, P.red(FIN_BNORM), s));
     const double tol = h->cfg.rel_tol;
     const bool dc = is_defect_correction(h);
     TRY(launch_ctl_init(P.ctl, tol, (cyc == LASTO_CYCLE_PCG && !dc) ? 0.5 * tol : tol, h->cfg.max_cycles, s));
@@ -382,8 +385,7 @@ int enqueue_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle c
         int st = enqueue_cycle<double>(h, P, 0, F.u, F.b, F.r, true, false, s);
         if (st) return st;
     }
-    TRY(launch_resid_norm_partials(V, F.u, F.b, F.r, P.part, s, dc ? F.b32 : nullptr));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_START, cond, use_cond, s));
+    TRY(launch_resid_norm(V, F.u, F.b, F.r, dc ? F.b32 : nullptr, P.red(FIN_START, cond, use_cond), s));
     if (cyc == LASTO_CYCLE_PCG) TRY(cudaMemsetAsync(P.p, 0, sizeof(double) * F.N(), s));
     if (dc) TRY(cudaMemsetAsync(P.e32, 0, sizeof(float) * F.N(), s));
     return LASTO_OK;
@@ -397,31 +399,16 @@ int enqueue_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHand
     if (h->cfg.cycle != LASTO_CYCLE_PCG) {
         int st = enqueue_cycle<double>(h, P, 0, F.u, F.b, F.r, false, false, s);
         if (st) return st;
-        TRY(launch_resid_norm_partials(V, F.u, F.b, F.r, P.part, s));
-        TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_CHECK, cond, use_cond, s));
+        TRY(launch_resid_norm(V, F.u, F.b, F.r, nullptr, P.red(FIN_CHECK, cond, use_cond), s));
         return LASTO_OK;
     }
-    const bool mixed = h->cfg.precision == LASTO_PREC_MIXED;
-    int st;
-    if (mixed) {
-        TRY(cudaMemsetAsync(F.u32, 0, sizeof(float) * F.N(), s));
-        st = enqueue_cycle<float>(h, P, 0, F.u32, F.b32, F.r32, false, true, s);
-        if (st) return st;
-        TRY(launch_dot_rz<float>(V, F.r, F.u32, P.part, s));
-        TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_BETA, cond, 0, s));
-        TRY(launch_update_p<float>(V, P.ctl, F.u32, P.p, s));
-    } else {
-        TRY(cudaMemsetAsync(P.z, 0, sizeof(double) * F.N(), s));
-        st = enqueue_cycle<double>(h, P, 0, P.z, F.r, P.q, false, true, s);
-        if (st) return st;
-        TRY(launch_dot_rz<double>(V, F.r, P.z, P.part, s));
-        TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_BETA, cond, 0, s));
-        TRY(launch_update_p<double>(V, P.ctl, P.z, P.p, s));
-    }
-    TRY(launch_apply_dot(V, P.p, P.q, P.part, s));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_ALPHA, cond, 0, s));
-    TRY(launch_update_ur(V, P.ctl, P.p, P.q, F.u, F.r, mixed ? F.b32 : nullptr, P.part, s));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_CHECK, cond, use_cond, s));
+    TRY(cudaMemsetAsync(P.z, 0, sizeof(double) * F.N(), s));
+    int st = enqueue_cycle<double>(h, P, 0, P.z, F.r, P.q, false, true, s);
+    if (st) return st;
+    TRY(launch_dot_rz(V, F.r, P.z, P.red(FIN_BETA), s));
+    TRY(launch_update_p(V, P.ctl, P.z, P.p, s));
+    TRY(launch_apply_dot(V, P.p, P.q, P.red(FIN_ALPHA), s));
+    TRY(launch_update_ur(V, P.ctl, P.p, P.q, F.u, F.r, P.red(FIN_CHECK, cond, use_cond), s));
     return LASTO_OK;
 }
 
@@ -434,13 +421,10 @@ int enqueue_inner_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphCondition
     TRY(cudaMemsetAsync(F.u32, 0, sizeof(float) * F.N(), s));
     int st = enqueue_cycle<float>(h, P, 0, F.u32, F.b32, F.r32, false, true, s);
     if (st) return st;
-    TRY(launch_dot32(V, F.b32, F.u32, P.part, s));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_IN_BETA, cond, 0, s));
+    TRY(launch_dot32(V, F.b32, F.u32, P.red(FIN_IN_BETA), s));
     TRY(launch_update_p32(V, P.ctl, F.u32, P.p32, s));
-    TRY(launch_apply_dot32(V, P.p32, P.q32, P.part, s));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_IN_ALPHA, cond, 0, s));
-    TRY(launch_update_er32(V, P.ctl, P.p32, P.q32, P.e32, F.b32, P.part, s));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_IN_CHECK, cond, use_cond, s));
+    TRY(launch_apply_dot32(V, P.p32, P.q32, P.red(FIN_IN_ALPHA), s));
+    TRY(launch_update_er32(V, P.ctl, P.p32, P.q32, P.e32, F.b32, P.red(FIN_IN_CHECK, cond, use_cond), s));
     return LASTO_OK;
 }
 
@@ -448,8 +432,7 @@ int enqueue_inner_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphCondition
 int enqueue_inner_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s)
 {
     LevelStore& F = P.lv[0];
-    TRY(launch_dot32(F.view32(), F.b32, nullptr, P.part, s));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_IN_START, cond, use_cond, s));
+    TRY(launch_dot32(F.view32(), F.b32, nullptr, P.red(FIN_IN_START, cond, use_cond), s));
     TRY(cudaMemsetAsync(P.p32, 0, sizeof(float) * F.N(), s));
     return LASTO_OK;
 }
@@ -460,8 +443,7 @@ int enqueue_outer_finish(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalH
 {
     LevelStore& F = P.lv[0];
     TRY(launch_add_correction(F.N(), F.u, P.e32, s));
-    TRY(launch_resid_norm_partials(F.view64(), F.u, F.b, F.r, P.part, s, F.b32));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_OUTER, cond, use_cond, s));
+    TRY(launch_resid_norm(F.view64(), F.u, F.b, F.r, F.b32, P.red(FIN_OUTER, cond, use_cond), s));
     return LASTO_OK;
 }
 
@@ -470,8 +452,7 @@ int enqueue_finish(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, do
 {
     LevelStore& F = P.lv[0];
     const LevelT<double> V = F.view64();
-    TRY(launch_resid_norm_partials(V, F.u, F.b, nullptr, P.part, s));
-    TRY(launch_fin(P.ctl, P.part, P.nparts, FIN_TRUE, 0, 0, s));
+    TRY(launch_resid_norm(V, F.u, F.b, nullptr, nullptr, P.red(FIN_TRUE), s));
     TRY(launch_project(cl.n, cl.x, cl.y, cl.z, F.u, cl.n_atoms, cl.pos, cl.R, h->quad, h->nq, vlm, P.status, s));
     if (potential) TRY(cudaMemcpyAsync(potential, F.u, sizeof(double) * F.N(), cudaMemcpyDeviceToDevice, s));
     k_write_stats<<<1, 1, 0, s>>>(P.ctl, P.status, P.stats_dev);

@@ -28,8 +28,6 @@ enum FinOp {
     FIN_IN_START = 6, FIN_IN_ALPHA = 7, FIN_IN_BETA = 8, FIN_IN_CHECK = 9, FIN_OUTER = 10
 };
 
-cudaError_t launch_fin(Ctl* ctl, const double* part, int nparts, int op, cudaGraphConditionalHandle cond,
-                       int use_cond, cudaStream_t s);
 cudaError_t launch_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter, cudaStream_t s);
 
 }  // namespace lasto

@@ -160,25 +160,32 @@ struct BottomArgs {
 template <typename T>
 cudaError_t launch_bottom(const BottomArgs<T>& a, cudaStream_t s);
 
-// reductions / CG (mg.cu)
+// reductions / CG (mg.cu).  A reducing kernel sums one quantity over the grid and its last
+// block applies the scalar step `op` (enum FinOp) to the control block.
 struct Ctl;
+struct Red {
+    double* part;            // one partial per block (at most 1216 blocks)
+    unsigned int* counter;   // zero between launches
+    Ctl* ctl;
+    int op;
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+};
 int reduce_blocks(const LevelT<double>& L);
-cudaError_t launch_bnorm_partials(const LevelT<double>& L, const double* u, const double* b, double* part, cudaStream_t s);
-cudaError_t launch_resid_norm_partials(const LevelT<double>& L, const double* u, const double* b, double* r,
-                                       double* part, cudaStream_t s, float* r32 = nullptr);
-cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, double* part, cudaStream_t s);
+cudaError_t launch_bnorm(const LevelT<double>& L, const double* u, const double* b, const Red& red, cudaStream_t s);
+cudaError_t launch_resid_norm(const LevelT<double>& L, const double* u, const double* b, double* r, float* r32,
+                              const Red& red, cudaStream_t s);
+cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, const Red& red, cudaStream_t s);
+cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const double* p, const double* q, double* u,
+                             double* r, const Red& red, cudaStream_t s);
+cudaError_t launch_dot_rz(const LevelT<double>& L, const double* r, const double* z, const Red& red, cudaStream_t s);
+cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const double* z, double* p, cudaStream_t s);
+cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s);
 cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
-                               float* r, double* part, cudaStream_t s);
-cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, double* part, cudaStream_t s);
+                               float* r, const Red& red, cudaStream_t s);
+cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, const Red& red, cudaStream_t s);
 cudaError_t launch_update_p32(const LevelT<float>& L, const Ctl* ctl, const float* z, float* p, cudaStream_t s);
 cudaError_t launch_add_correction(size_t N, double* u, float* e, cudaStream_t s);
-cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, double* part, cudaStream_t s);
-cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const double* p, const double* q, double* u,
-                             double* r, float* r32, double* part, cudaStream_t s);
-template <typename TZ>
-cudaError_t launch_dot_rz(const LevelT<double>& L, const double* r, const TZ* z, double* part, cudaStream_t s);
-template <typename TZ>
-cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const TZ* z, double* p, cudaStream_t s);
 cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s);
 
 // density.cu

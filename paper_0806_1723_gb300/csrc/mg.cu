@@ -7,6 +7,8 @@
 // node of that colour with unit-stride neighbour loads.  Reductions are two-stage
 // (per-block partials, then one block in a fixed order), so every norm and dot is
 // bitwise reproducible.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "ctl.cuh"
 
@@ -435,313 +437,41 @@ cudaError_t launch_bottom(const BottomArgs<T>& a, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------- reductions
-int reduce_blocks(const LevelT<double>& L) { return (int)((L.N() + NT - 1) / NT); }
+// Reducing kernels run a grid-stride loop over at most RED_BLOCKS blocks, accumulate in the
+// kernel's own precision (FP32 shuffles for FP32 vectors: FP64 is 1/58 of FP32 here),
+// write one FP64 partial per block, and the last block to finish (atomic ticket) sums the
+// partials in block order and applies the scalar step of the iteration -- so no separate
+// finalising launch, and every result is bitwise reproducible.
+constexpr int RED_BLOCKS = 1216;   // 152 SMs x 8
+
+int reduce_blocks(const LevelT<double>& L) { return (int)std::min<size_t>((L.N() + NT - 1) / NT, RED_BLOCKS); }
+static unsigned red_grid(size_t N) { return (unsigned)std::min<size_t>((N + NT - 1) / NT, RED_BLOCKS); }
 
 __device__ __forceinline__ double vol(const LevelT<double>& L, int i, int j, int k)
 {
     return L.ax[0].dual[i] * L.ax[1].dual[j] * L.ax[2].dual[k];
 }
 
-// ||b_eff||^2 partials: b with the Dirichlet faces moved to the right-hand side.
-__global__ void __launch_bounds__(NT) k_bnorm_partials(LevelT<double> L, const double* __restrict__ u,
-                                                      const double* __restrict__ b, double* __restrict__ part)
+// FP32 warp sums, one FP64 value per warp, FP64 across the block's warps
+__device__ __forceinline__ double block_sum_f32(float v, double* sm)
 {
-    __shared__ double sm[32];
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    double acc = 0.0;
-    if (P < L.N()) {
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        if (!is_face(L, i, j, k)) {
-            const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
-            double v = b[P];
-            if (i == 1) v -= L.ax[0].cm[i] * u[P - 1];
-            if (i == L.nx - 2) v -= L.ax[0].cp[i] * u[P + 1];
-            if (j == 1) v -= L.ax[1].cm[j] * u[P - sy];
-            if (j == L.ny - 2) v -= L.ax[1].cp[j] * u[P + sy];
-            if (k == 1) v -= L.ax[2].cm[k] * u[P - sz];
-            if (k == L.nz - 2) v -= L.ax[2].cp[k] * u[P + sz];
-            acc = v * v;
-        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sm[w] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = (threadIdx.x < NT / 32) ? sm[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     }
-    const double s = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
+    return s;
 }
 
-// r = b - A u (written when r != nullptr) and ||r||^2 partials
-__global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const double* __restrict__ u,
-                                                  const double* __restrict__ b, double* __restrict__ r,
-                                                  float* __restrict__ r32, double* __restrict__ part)
+__device__ void fin_apply(Ctl& c, double s, int op, cudaGraphConditionalHandle cond, int use_cond)
 {
-    __shared__ double sm[32];
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    double acc = 0.0;
-    if (P < L.N()) {
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        double v = 0.0;
-        if (!is_face(L, i, j, k)) v = b[P] - fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
-        if (r) r[P] = v;
-        if (r32) r32[P] = (float)v;
-        acc = v * v;
-    }
-    const double s = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// q = A p and <p, q>_vol partials
-__global__ void __launch_bounds__(NT) k_apply_dot(LevelT<double> L, const double* __restrict__ p,
-                                                 double* __restrict__ q, double* __restrict__ part)
-{
-    __shared__ double sm[32];
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    double acc = 0.0;
-    if (P < L.N()) {
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        double v = 0.0;
-        if (!is_face(L, i, j, k)) {
-            v = fma(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
-            acc = vol(L, i, j, k) * p[P] * v;
-        }
-        q[P] = v;
-    }
-    const double s = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// u += alpha p; r -= alpha q; r32 = (float) r; ||r||^2 partials
-__global__ void __launch_bounds__(NT) k_update_ur(LevelT<double> L, const Ctl* __restrict__ ctl,
-                                                 const double* __restrict__ p, const double* __restrict__ q,
-                                                 double* __restrict__ u, double* __restrict__ r, float* __restrict__ r32,
-                                                 double* __restrict__ part)
-{
-    __shared__ double sm[32];
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    const double alpha = ctl->alpha;
-    double acc = 0.0;
-    if (P < L.N()) {
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        if (!is_face(L, i, j, k)) {
-            u[P] = fma(alpha, p[P], u[P]);
-            const double rv = fma(-alpha, q[P], r[P]);
-            r[P] = rv;
-            if (r32) r32[P] = (float)rv;
-            acc = rv * rv;
-        } else if (r32) {
-            r32[P] = 0.0f;
-        }
-    }
-    const double s = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-template <typename TZ>
-__global__ void __launch_bounds__(NT) k_dot_rz(LevelT<double> L, const double* __restrict__ r,
-                                              const TZ* __restrict__ z, double* __restrict__ part)
-{
-    __shared__ double sm[32];
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    double acc = 0.0;
-    if (P < L.N()) {
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        if (!is_face(L, i, j, k)) acc = vol(L, i, j, k) * r[P] * (double)z[P];
-    }
-    const double s = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-template <typename TZ>
-__global__ void __launch_bounds__(NT) k_update_p(LevelT<double> L, const Ctl* __restrict__ ctl,
-                                                const TZ* __restrict__ z, double* __restrict__ p)
-{
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    if (P >= L.N()) return;
-    int i, j, k;
-    node_ijk(P, L.nx, L.ny, i, j, k);
-    p[P] = is_face(L, i, j, k) ? 0.0 : fma(ctl->beta, p[P], (double)z[P]);
-}
-
-// ---------------------------------------------------------------- inner FP32 CG (defect correction)
-__device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int k)
-{
-    return L.ax[0].dual[i] * L.ax[1].dual[j] * L.ax[2].dual[k];
-}
-
-// q = A p and <p, q>_vol partials, FP32 vectors, FP64 block sums
-__global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p,
-                                                   float* __restrict__ q, double* __restrict__ part)
-{
-    __shared__ double sm[32];
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    double acc = 0.0;
-    if (P < L.N()) {
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        float v = 0.0f;
-        if (!is_face(L, i, j, k)) {
-            v = fmaf(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
-            acc = (double)(vol32(L, i, j, k) * p[P] * v);
-        }
-        q[P] = v;
-    }
-    const double s = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// e += alpha p; r -= alpha q; ||r||^2 partials
-__global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* __restrict__ ctl,
-                                                   const float* __restrict__ p, const float* __restrict__ q,
-                                                   float* __restrict__ e, float* __restrict__ r,
-                                                   double* __restrict__ part)
-{
-    __shared__ double sm[32];
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    const float alpha = (float)ctl->alpha_in;
-    double acc = 0.0;
-    if (P < L.N()) {
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        if (!is_face(L, i, j, k)) {
-            e[P] = fmaf(alpha, p[P], e[P]);
-            const float rv = fmaf(-alpha, q[P], r[P]);
-            r[P] = rv;
-            acc = (double)rv * (double)rv;
-        }
-    }
-    const double s = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-// <r, z>_vol partials (FP32) or ||r||^2 partials (z == nullptr)
-__global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __restrict__ r,
-                                             const float* __restrict__ z, double* __restrict__ part)
-{
-    __shared__ double sm[32];
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    double acc = 0.0;
-    if (P < L.N()) {
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        if (!is_face(L, i, j, k)) acc = z ? (double)(vol32(L, i, j, k) * r[P] * z[P]) : (double)r[P] * (double)r[P];
-    }
-    const double s = block_sum<NT>(acc, sm);
-    if (threadIdx.x == 0) part[blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* __restrict__ ctl,
-                                                  const float* __restrict__ z, float* __restrict__ p)
-{
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    if (P >= L.N()) return;
-    int i, j, k;
-    node_ijk(P, L.nx, L.ny, i, j, k);
-    p[P] = is_face(L, i, j, k) ? 0.0f : fmaf((float)ctl->beta_in, p[P], z[P]);
-}
-
-// u += e (FP64 accumulation of the FP32 correction); e = 0 for the next inner solve
-__global__ void __launch_bounds__(NT) k_add_correction(size_t N, double* __restrict__ u, float* __restrict__ e)
-{
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    if (P >= N) return;
-    u[P] += (double)e[P];
-    e[P] = 0.0f;
-}
-
-#define GRID32(L) (unsigned)((L.N() + NT - 1) / NT), NT, 0, s
-cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, double* part, cudaStream_t s)
-{
-    k_apply_dot32<<<GRID32(L)>>>(L, p, q, part);
-    return cudaGetLastError();
-}
-cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
-                               float* r, double* part, cudaStream_t s)
-{
-    k_update_er32<<<GRID32(L)>>>(L, ctl, p, q, e, r, part);
-    return cudaGetLastError();
-}
-cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, double* part, cudaStream_t s)
-{
-    k_dot32<<<GRID32(L)>>>(L, r, z, part);
-    return cudaGetLastError();
-}
-cudaError_t launch_update_p32(const LevelT<float>& L, const Ctl* ctl, const float* z, float* p, cudaStream_t s)
-{
-    k_update_p32<<<GRID32(L)>>>(L, ctl, z, p);
-    return cudaGetLastError();
-}
-cudaError_t launch_add_correction(size_t N, double* u, float* e, cudaStream_t s)
-{
-    k_add_correction<<<(unsigned)((N + NT - 1) / NT), NT, 0, s>>>(N, u, e);
-    return cudaGetLastError();
-}
-
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n)
-{
-    const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
-    if (t < n) b[t] = (float)a[t];
-}
-
-#define GRID(L) (unsigned)((L.N() + NT - 1) / NT), NT, 0, s
-
-cudaError_t launch_bnorm_partials(const LevelT<double>& L, const double* u, const double* b, double* part, cudaStream_t s)
-{
-    k_bnorm_partials<<<GRID(L)>>>(L, u, b, part);
-    return cudaGetLastError();
-}
-cudaError_t launch_resid_norm_partials(const LevelT<double>& L, const double* u, const double* b, double* r,
-                                       double* part, cudaStream_t s, float* r32)
-{
-    k_resid_norm<<<GRID(L)>>>(L, u, b, r, r32, part);
-    return cudaGetLastError();
-}
-cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, double* part, cudaStream_t s)
-{
-    k_apply_dot<<<GRID(L)>>>(L, p, q, part);
-    return cudaGetLastError();
-}
-cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const double* p, const double* q, double* u,
-                             double* r, float* r32, double* part, cudaStream_t s)
-{
-    k_update_ur<<<GRID(L)>>>(L, ctl, p, q, u, r, r32, part);
-    return cudaGetLastError();
-}
-template <typename TZ>
-cudaError_t launch_dot_rz(const LevelT<double>& L, const double* r, const TZ* z, double* part, cudaStream_t s)
-{
-    k_dot_rz<TZ><<<GRID(L)>>>(L, r, z, part);
-    return cudaGetLastError();
-}
-template <typename TZ>
-cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const TZ* z, double* p, cudaStream_t s)
-{
-    k_update_p<TZ><<<GRID(L)>>>(L, ctl, z, p);
-    return cudaGetLastError();
-}
-cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s)
-{
-    k_to_f32<<<(unsigned)((n + NT - 1) / NT), NT, 0, s>>>(a, b, n);
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- scalar steps
-// One block sums the partials in a fixed order; thread 0 updates the control block.
-__device__ double fin_sum(const double* __restrict__ part, int nparts, double* sm)
-{
-    double acc = 0.0;
-    for (int t = threadIdx.x; t < nparts; t += NT) acc += part[t];
-    return block_sum<NT>(acc, sm);
-}
-
-__global__ void __launch_bounds__(NT) k_fin(Ctl* ctl, const double* __restrict__ part, int nparts, int op,
-                                           cudaGraphConditionalHandle cond, int use_cond)
-{
-    __shared__ double sm[32];
-    const double s = fin_sum(part, nparts, sm);
-    if (threadIdx.x != 0) return;
-    Ctl& c = *ctl;
     switch (op) {
         case FIN_BNORM:
             c.bnorm = sqrt(s);
@@ -749,11 +479,10 @@ __global__ void __launch_bounds__(NT) k_fin(Ctl* ctl, const double* __restrict__
         case FIN_ALPHA:
             c.alpha = (s != 0.0 && isfinite(s)) ? c.rz / s : 0.0;
             break;
-        case FIN_BETA: {
+        case FIN_BETA:
             c.beta = (c.iter == 0 || c.rz == 0.0) ? 0.0 : s / c.rz;
             c.rz = s;
             break;
-        }
         case FIN_START:   // residual of the starting guess
         case FIN_CHECK: {
             const double scale = c.bnorm > 0.0 ? c.bnorm : 1.0;
@@ -837,10 +566,289 @@ __global__ void __launch_bounds__(NT) k_fin(Ctl* ctl, const double* __restrict__
     }
 }
 
-cudaError_t launch_fin(Ctl* ctl, const double* part, int nparts, int op, cudaGraphConditionalHandle cond,
-                       int use_cond, cudaStream_t s)
+// Block partial -> last block sums the partials in order and applies the scalar step.
+__device__ void reduce_finish(double block_total, const Red& r, double* sm)
 {
-    k_fin<<<1, NT, 0, s>>>(ctl, part, nparts, op, cond, use_cond);
+    __shared__ int is_last;
+    if (threadIdx.x == 0) {
+        r.part[blockIdx.x] = block_total;
+        __threadfence();
+        const unsigned prev = atomicAdd(r.counter, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (unsigned t = threadIdx.x; t < gridDim.x; t += NT) acc += __ldcg(r.part + t);
+    const double s = block_sum<NT>(acc, sm);
+    if (threadIdx.x == 0) {
+        *r.counter = 0u;
+        fin_apply(*r.ctl, s, r.op, r.cond, r.use_cond);
+    }
+}
+
+#define GRID_STRIDE(P, N) for (size_t P = blockIdx.x * (size_t)NT + threadIdx.x; P < (N); P += (size_t)gridDim.x * NT)
+
+// ||b_eff||^2: b with the Dirichlet faces moved to the right-hand side.
+__global__ void __launch_bounds__(NT) k_bnorm(LevelT<double> L, const double* __restrict__ u,
+                                             const double* __restrict__ b, Red red)
+{
+    __shared__ double sm[32];
+    double acc = 0.0;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (is_face(L, i, j, k)) continue;
+        const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
+        double v = b[P];
+        if (i == 1) v -= L.ax[0].cm[i] * u[P - 1];
+        if (i == L.nx - 2) v -= L.ax[0].cp[i] * u[P + 1];
+        if (j == 1) v -= L.ax[1].cm[j] * u[P - sy];
+        if (j == L.ny - 2) v -= L.ax[1].cp[j] * u[P + sy];
+        if (k == 1) v -= L.ax[2].cm[k] * u[P - sz];
+        if (k == L.nz - 2) v -= L.ax[2].cp[k] * u[P + sz];
+        acc = fma(v, v, acc);
+    }
+    reduce_finish(block_sum<NT>(acc, sm), red, sm);
+}
+
+// r = b - A u (written when r != nullptr, FP32 copy when r32 != nullptr) and ||r||^2
+__global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const double* __restrict__ u,
+                                                  const double* __restrict__ b, double* __restrict__ r,
+                                                  float* __restrict__ r32, Red red)
+{
+    __shared__ double sm[32];
+    double acc = 0.0;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        double v = 0.0;
+        if (!is_face(L, i, j, k)) v = b[P] - fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
+        if (r) r[P] = v;
+        if (r32) r32[P] = (float)v;
+        acc = fma(v, v, acc);
+    }
+    reduce_finish(block_sum<NT>(acc, sm), red, sm);
+}
+
+// q = A p and <p, q>_vol
+__global__ void __launch_bounds__(NT) k_apply_dot(LevelT<double> L, const double* __restrict__ p,
+                                                 double* __restrict__ q, Red red)
+{
+    __shared__ double sm[32];
+    double acc = 0.0;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        double v = 0.0;
+        if (!is_face(L, i, j, k)) {
+            v = fma(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
+            acc = fma(vol(L, i, j, k) * p[P], v, acc);
+        }
+        q[P] = v;
+    }
+    reduce_finish(block_sum<NT>(acc, sm), red, sm);
+}
+
+// u += alpha p; r -= alpha q; ||r||^2
+__global__ void __launch_bounds__(NT) k_update_ur(LevelT<double> L, const Ctl* __restrict__ ctl,
+                                                 const double* __restrict__ p, const double* __restrict__ q,
+                                                 double* __restrict__ u, double* __restrict__ r, Red red)
+{
+    __shared__ double sm[32];
+    const double alpha = ctl->alpha;
+    double acc = 0.0;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (is_face(L, i, j, k)) continue;
+        u[P] = fma(alpha, p[P], u[P]);
+        const double rv = fma(-alpha, q[P], r[P]);
+        r[P] = rv;
+        acc = fma(rv, rv, acc);
+    }
+    reduce_finish(block_sum<NT>(acc, sm), red, sm);
+}
+
+__global__ void __launch_bounds__(NT) k_dot_rz(LevelT<double> L, const double* __restrict__ r,
+                                              const double* __restrict__ z, Red red)
+{
+    __shared__ double sm[32];
+    double acc = 0.0;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (!is_face(L, i, j, k)) acc = fma(vol(L, i, j, k) * r[P], z[P], acc);
+    }
+    reduce_finish(block_sum<NT>(acc, sm), red, sm);
+}
+
+__global__ void __launch_bounds__(NT) k_update_p(LevelT<double> L, const Ctl* __restrict__ ctl,
+                                                const double* __restrict__ z, double* __restrict__ p)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= L.N()) return;
+    int i, j, k;
+    node_ijk(P, L.nx, L.ny, i, j, k);
+    p[P] = is_face(L, i, j, k) ? 0.0 : fma(ctl->beta, p[P], z[P]);
+}
+
+// ---------------------------------------------------------------- inner FP32 CG (defect correction)
+__device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int k)
+{
+    return L.ax[0].dual[i] * L.ax[1].dual[j] * L.ax[2].dual[k];
+}
+
+__global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p,
+                                                   float* __restrict__ q, Red red)
+{
+    __shared__ double sm[32];
+    float acc = 0.0f;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        float v = 0.0f;
+        if (!is_face(L, i, j, k)) {
+            v = fmaf(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
+            acc = fmaf(vol32(L, i, j, k) * p[P], v, acc);
+        }
+        q[P] = v;
+    }
+    reduce_finish(block_sum_f32(acc, sm), red, sm);
+}
+
+__global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* __restrict__ ctl,
+                                                   const float* __restrict__ p, const float* __restrict__ q,
+                                                   float* __restrict__ e, float* __restrict__ r, Red red)
+{
+    __shared__ double sm[32];
+    const float alpha = (float)ctl->alpha_in;
+    float acc = 0.0f;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (is_face(L, i, j, k)) continue;
+        e[P] = fmaf(alpha, p[P], e[P]);
+        const float rv = fmaf(-alpha, q[P], r[P]);
+        r[P] = rv;
+        acc = fmaf(rv, rv, acc);
+    }
+    reduce_finish(block_sum_f32(acc, sm), red, sm);
+}
+
+// <r, z>_vol, or ||r||^2 when z == nullptr
+__global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __restrict__ r,
+                                             const float* __restrict__ z, Red red)
+{
+    __shared__ double sm[32];
+    float acc = 0.0f;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L.nx, L.ny, i, j, k);
+        if (is_face(L, i, j, k)) continue;
+        acc = z ? fmaf(vol32(L, i, j, k) * r[P], z[P], acc) : fmaf(r[P], r[P], acc);
+    }
+    reduce_finish(block_sum_f32(acc, sm), red, sm);
+}
+
+__global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* __restrict__ ctl,
+                                                  const float* __restrict__ z, float* __restrict__ p)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= L.N()) return;
+    int i, j, k;
+    node_ijk(P, L.nx, L.ny, i, j, k);
+    p[P] = is_face(L, i, j, k) ? 0.0f : fmaf((float)ctl->beta_in, p[P], z[P]);
+}
+
+// u += e (FP64 accumulation of the FP32 correction); e = 0 for the next inner solve
+__global__ void __launch_bounds__(NT) k_add_correction(size_t N, double* __restrict__ u, float* __restrict__ e)
+{
+    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (P >= N) return;
+    u[P] += (double)e[P];
+    e[P] = 0.0f;
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n)
+{
+    const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
+    if (t < n) b[t] = (float)a[t];
+}
+
+#define RGRID(L) red_grid(L.N()), NT, 0, s
+#define GRID(L) (unsigned)((L.N() + NT - 1) / NT), NT, 0, s
+
+cudaError_t launch_bnorm(const LevelT<double>& L, const double* u, const double* b, const Red& red, cudaStream_t s)
+{
+    k_bnorm<<<RGRID(L)>>>(L, u, b, red);
+    return cudaGetLastError();
+}
+cudaError_t launch_resid_norm(const LevelT<double>& L, const double* u, const double* b, double* r, float* r32,
+                              const Red& red, cudaStream_t s)
+{
+    k_resid_norm<<<RGRID(L)>>>(L, u, b, r, r32, red);
+    return cudaGetLastError();
+}
+cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, const Red& red, cudaStream_t s)
+{
+    k_apply_dot<<<RGRID(L)>>>(L, p, q, red);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const double* p, const double* q, double* u,
+                             double* r, const Red& red, cudaStream_t s)
+{
+    k_update_ur<<<RGRID(L)>>>(L, ctl, p, q, u, r, red);
+    return cudaGetLastError();
+}
+cudaError_t launch_dot_rz(const LevelT<double>& L, const double* r, const double* z, const Red& red, cudaStream_t s)
+{
+    k_dot_rz<<<RGRID(L)>>>(L, r, z, red);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const double* z, double* p, cudaStream_t s)
+{
+    k_update_p<<<GRID(L)>>>(L, ctl, z, p);
+    return cudaGetLastError();
+}
+cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s)
+{
+    k_apply_dot32<<<RGRID(L)>>>(L, p, q, red);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
+                               float* r, const Red& red, cudaStream_t s)
+{
+    k_update_er32<<<RGRID(L)>>>(L, ctl, p, q, e, r, red);
+    return cudaGetLastError();
+}
+cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, const Red& red, cudaStream_t s)
+{
+    k_dot32<<<RGRID(L)>>>(L, r, z, red);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_p32(const LevelT<float>& L, const Ctl* ctl, const float* z, float* p, cudaStream_t s)
+{
+    k_update_p32<<<GRID(L)>>>(L, ctl, z, p);
+    return cudaGetLastError();
+}
+cudaError_t launch_add_correction(size_t N, double* u, float* e, cudaStream_t s)
+{
+    k_add_correction<<<(unsigned)((N + NT - 1) / NT), NT, 0, s>>>(N, u, e);
+    return cudaGetLastError();
+}
+cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s)
+{
+    k_to_f32<<<(unsigned)((n + NT - 1) / NT), NT, 0, s>>>(a, b, n);
     return cudaGetLastError();
 }
 
@@ -883,9 +891,5 @@ cudaError_t launch_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter,
     template cudaError_t launch_coarse_apply<T>(const LevelT<T>&, const CoarseEig*, const T*, T*, bool, cudaStream_t);
 INST(double)
 INST(float)
-template cudaError_t launch_dot_rz<double>(const LevelT<double>&, const double*, const double*, double*, cudaStream_t);
-template cudaError_t launch_dot_rz<float>(const LevelT<double>&, const double*, const float*, double*, cudaStream_t);
-template cudaError_t launch_update_p<double>(const LevelT<double>&, const Ctl*, const double*, double*, cudaStream_t);
-template cudaError_t launch_update_p<float>(const LevelT<double>&, const Ctl*, const float*, double*, cudaStream_t);
 
 }  // namespace lasto
