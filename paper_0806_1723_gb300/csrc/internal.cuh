@@ -159,6 +159,7 @@ struct BottomArgs {
 };
 template <typename T>
 cudaError_t launch_bottom(const BottomArgs<T>& a, cudaStream_t s);
+void init_mg_attributes();   // shared-memory opt-in of the bottom kernel; call outside capture
 
 // reductions / CG (mg.cu).  A reducing kernel sums one quantity over the grid and its last
 // block applies the scalar step `op` (enum FinOp) to the control block.

@@ -357,24 +357,76 @@ __device__ void bot_rbgs(const LevelT<T>& L, T* __restrict__ u, const T* __restr
     __syncthreads();
 }
 
+// Shared-memory layout of the bottom levels: per level u, b and the eight axis tables of
+// each axis; the kernel copies the tables and b in, works in shared memory only, and writes
+// the top bottom level's u back for the prolongation above it.
+template <typename T>
+__device__ void bot_stage_axis(const AxisT<T>& g, AxisT<T>& s, T*& cur)
+{
+    const int n = g.n;
+    T* base = cur;
+    T* arr[6] = {base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n};
+    for (int i = threadIdx.x; i < n; i += BOT_NT) {
+        arr[0][i] = g.cm[i];
+        arr[1][i] = g.cp[i];
+        arr[2][i] = g.dg[i];
+        arr[3][i] = g.dual[i];
+        arr[4][i] = g.pl[i];
+        arr[5][i] = g.pr[i];
+    }
+    T* rw = base + 6 * n;
+    for (int i = threadIdx.x; i < 3 * n; i += BOT_NT) rw[i] = g.rw[i];
+    s.c = g.c;
+    s.cm = arr[0];
+    s.cp = arr[1];
+    s.dg = arr[2];
+    s.dual = arr[3];
+    s.pl = arr[4];
+    s.pr = arr[5];
+    s.rw = rw;
+    s.n = n;
+    cur = base + 9 * n;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
 {
-    __shared__ double s0[MC3], s1[MC3];
+    extern __shared__ __align__(16) unsigned char bot_smem[];
+    double* s0 = reinterpret_cast<double*>(bot_smem);
+    double* s1 = s0 + MC3;
+    T* cur = reinterpret_cast<T*>(s1 + MC3);
     const int nl = a.nlev;
+    LevelT<T> lv[BOTTOM_MAX_LEVELS];
+    T* u[BOTTOM_MAX_LEVELS];
+    T* b[BOTTOM_MAX_LEVELS];
+    for (int l = 0; l < nl; l++) {
+        lv[l] = a.lv[l];
+        for (int d = 0; d < 3; d++) bot_stage_axis(a.lv[l].ax[d], lv[l].ax[d], cur);
+        const size_t N = lv[l].N();
+        u[l] = cur;
+        cur += N;
+        b[l] = cur;
+        cur += N;
+    }
+    // top level: b from global, u = 0 (the caller's correction starts at zero)
+    for (size_t t = threadIdx.x; t < lv[0].N(); t += BOT_NT) {
+        b[0][t] = a.b[0][t];
+        u[0][t] = T(0);
+    }
+    __syncthreads();
     for (int l = 0; l < nl - 1; l++) {
-        const LevelT<T>& F = a.lv[l];
+        const LevelT<T>& F = lv[l];
         for (int it = 0; it < a.nu1; it++) {
-            bot_rbgs(F, a.u[l], a.b[l], 0);
-            bot_rbgs(F, a.u[l], a.b[l], 1);
+            bot_rbgs(F, u[l], b[l], 0);
+            bot_rbgs(F, u[l], b[l], 1);
         }
-        const LevelT<T>& C = a.lv[l + 1];
+        const LevelT<T>& C = lv[l + 1];
         for (size_t t = threadIdx.x; t < C.N(); t += BOT_NT) {
             int I, J, K;
             node_ijk(t, C.nx, C.ny, I, J, K);
-            a.u[l + 1][t] = T(0);
+            u[l + 1][t] = T(0);
             if (is_face(C, I, J, K)) {
-                a.b[l + 1][t] = T(0);
+                b[l + 1][t] = T(0);
                 continue;
             }
             const T* wx = F.ax[0].rw + 3 * I;
@@ -386,21 +438,20 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
                 for (int bb = 0; bb < 3; bb++) {
                     const int fk = 2 * K - 1 + c, fj = 2 * J - 1 + bb, fi = 2 * I - 1;
                     const size_t P = (size_t)fk * sz + (size_t)fj * sy + fi;
-                    const T r0 = resid_at(F, a.u[l], a.b[l], P, fi, fj, fk);
-                    const T r1 = resid_at(F, a.u[l], a.b[l], P + 1, fi + 1, fj, fk);
-                    const T r2 = resid_at(F, a.u[l], a.b[l], P + 2, fi + 2, fj, fk);
+                    const T r0 = resid_at(F, u[l], b[l], P, fi, fj, fk);
+                    const T r1 = resid_at(F, u[l], b[l], P + 1, fi + 1, fj, fk);
+                    const T r2 = resid_at(F, u[l], b[l], P + 2, fi + 2, fj, fk);
                     acc = fma(wz[c] * wy[bb], fma(wx[0], r0, fma(wx[1], r1, wx[2] * r2)), acc);
                 }
-            a.b[l + 1][t] = acc;
+            b[l + 1][t] = acc;
         }
         __syncthreads();
     }
-    coarse_apply_block<T>(a.lv[nl - 1], a.eig, a.b[nl - 1], a.u[nl - 1], 0, s0, s1);
+    coarse_apply_block<T>(lv[nl - 1], a.eig, b[nl - 1], u[nl - 1], 0, s0, s1);
     for (int l = nl - 2; l >= 0; l--) {
-        const LevelT<T>& F = a.lv[l];
-        const LevelT<T>& C = a.lv[l + 1];
-        const T* ec = a.u[l + 1];
-        T* u = a.u[l];
+        const LevelT<T>& F = lv[l];
+        const LevelT<T>& C = lv[l + 1];
+        const T* ec = u[l + 1];
         for (size_t P = threadIdx.x; P < F.N(); P += BOT_NT) {
             int i, j, k;
             node_ijk(P, F.nx, F.ny, i, j, k);
@@ -419,21 +470,41 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
                     const T sv = (ni == 2) ? fma(wx[0], row[0], wx[1] * row[1]) : row[0];
                     e = fma(wz[c] * wy[bb], sv, e);
                 }
-            u[P] += e;
+            u[l][P] += e;
         }
         __syncthreads();
         for (int it = 0; it < a.nu2; it++) {
-            bot_rbgs(F, u, a.b[l], a.sym ? 1 : 0);
-            bot_rbgs(F, u, a.b[l], a.sym ? 0 : 1);
+            bot_rbgs(F, u[l], b[l], a.sym ? 1 : 0);
+            bot_rbgs(F, u[l], b[l], a.sym ? 0 : 1);
         }
     }
+    for (size_t t = threadIdx.x; t < lv[0].N(); t += BOT_NT) a.u[0][t] = u[0][t];
+}
+
+template <typename T>
+size_t bottom_smem_bytes(const BottomArgs<T>& a)
+{
+    size_t bytes = 2 * sizeof(double) * MC3;
+    for (int l = 0; l < a.nlev; l++) {
+        for (int d = 0; d < 3; d++) bytes += sizeof(T) * 9 * (size_t)a.lv[l].ax[d].n;
+        bytes += 2 * sizeof(T) * a.lv[l].N();
+    }
+    return bytes;
 }
 
 template <typename T>
 cudaError_t launch_bottom(const BottomArgs<T>& a, cudaStream_t s)
 {
-    k_bottom<T><<<1, BOT_NT, 0, s>>>(a);
+    const size_t smem = bottom_smem_bytes(a);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    k_bottom<T><<<1, BOT_NT, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+void init_mg_attributes()
+{
+    cudaFuncSetAttribute(k_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_bottom<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 // ---------------------------------------------------------------- reductions
