@@ -151,6 +151,7 @@ bool valid_n(const int n[3])
 {
     for (int d = 0; d < 3; d++)
         if (n[d] < 3 || n[d] % 2 == 0) return false;
+    if ((size_t)n[0] * n[1] * n[2] >= (size_t(1) << 32)) return false;   // kernels index with 32 bits
     int nn[3] = {n[0], n[1], n[2]};
     return num_levels(nn) >= 1;
 }

@@ -16,13 +16,16 @@ namespace lasto {
 
 constexpr int NT = 256;
 
+// Flat index -> (i, j, k).  Grids hold fewer than 2^32 nodes (checked at planning), so the
+// decomposition uses 32-bit unsigned division: a 64-bit division is a long subroutine and
+// would cost more than the stencil update it indexes.
 __device__ __forceinline__ void node_ijk(size_t P, int nx, int ny, int& i, int& j, int& k)
 {
-    const size_t nxy = (size_t)nx * ny;
-    k = (int)(P / nxy);
-    const size_t rem = P - (size_t)k * nxy;
-    j = (int)(rem / nx);
-    i = (int)(rem - (size_t)j * nx);
+    const unsigned p = (unsigned)P, nxy = (unsigned)nx * (unsigned)ny;
+    const unsigned kk = p / nxy, rem = p - kk * nxy, jj = rem / (unsigned)nx;
+    k = (int)kk;
+    j = (int)jj;
+    i = (int)(rem - jj * (unsigned)nx);
 }
 
 template <typename T>
