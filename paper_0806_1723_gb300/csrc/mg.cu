@@ -364,55 +364,51 @@ __device__ void bot_rbgs(const LevelT<T>& L, T* __restrict__ u, const T* __restr
 // each axis; the kernel copies the tables and b in, works in shared memory only, and writes
 // the top bottom level's u back for the prolongation above it.
 template <typename T>
-__device__ void bot_stage_axis(const AxisT<T>& g, AxisT<T>& s, T*& cur)
-{
-    const int n = g.n;
-    T* base = cur;
-    T* arr[6] = {base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n};
-    for (int i = threadIdx.x; i < n; i += BOT_NT) {
-        arr[0][i] = g.cm[i];
-        arr[1][i] = g.cp[i];
-        arr[2][i] = g.dg[i];
-        arr[3][i] = g.dual[i];
-        arr[4][i] = g.pl[i];
-        arr[5][i] = g.pr[i];
-    }
-    T* rw = base + 6 * n;
-    for (int i = threadIdx.x; i < 3 * n; i += BOT_NT) rw[i] = g.rw[i];
-    s.c = g.c;
-    s.cm = arr[0];
-    s.cp = arr[1];
-    s.dg = arr[2];
-    s.dual = arr[3];
-    s.pl = arr[4];
-    s.pr = arr[5];
-    s.rw = rw;
-    s.n = n;
-    cur = base + 9 * n;
-}
-
-template <typename T>
 __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char bot_smem[];
+    // one block-wide copy of the level descriptors (pointing into shared memory)
+    __shared__ LevelT<T> lv[BOTTOM_MAX_LEVELS];
+    __shared__ T* u[BOTTOM_MAX_LEVELS];
+    __shared__ T* b[BOTTOM_MAX_LEVELS];
     double* s0 = reinterpret_cast<double*>(bot_smem);
     double* s1 = s0 + MC3;
-    T* cur = reinterpret_cast<T*>(s1 + MC3);
     const int nl = a.nlev;
-    LevelT<T> lv[BOTTOM_MAX_LEVELS];
-    T* u[BOTTOM_MAX_LEVELS];
-    T* b[BOTTOM_MAX_LEVELS];
-    for (int l = 0; l < nl; l++) {
-        lv[l] = a.lv[l];
-        for (int d = 0; d < 3; d++) bot_stage_axis(a.lv[l].ax[d], lv[l].ax[d], cur);
-        const size_t N = lv[l].N();
-        u[l] = cur;
-        cur += N;
-        b[l] = cur;
-        cur += N;
+    if (threadIdx.x == 0) {
+        T* cur = reinterpret_cast<T*>(s1 + MC3);
+        for (int l = 0; l < nl; l++) {
+            lv[l] = a.lv[l];
+            for (int d = 0; d < 3; d++) {
+                const int n = a.lv[l].ax[d].n;
+                AxisT<T>& A = lv[l].ax[d];
+                A.cm = cur; A.cp = cur + n; A.dg = cur + 2 * n; A.dual = cur + 3 * n;
+                A.pl = cur + 4 * n; A.pr = cur + 5 * n; A.rw = cur + 6 * n;
+                cur += 9 * n;
+            }
+            u[l] = cur;
+            cur += lv[l].N();
+            b[l] = cur;
+            cur += lv[l].N();
+        }
     }
+    __syncthreads();
+    for (int l = 0; l < nl; l++)
+        for (int d = 0; d < 3; d++) {
+            const AxisT<T>& g = a.lv[l].ax[d];
+            T* dst = const_cast<T*>(lv[l].ax[d].cm);
+            const int n = g.n;
+            for (int i = threadIdx.x; i < n; i += BOT_NT) {
+                dst[i] = g.cm[i];
+                dst[n + i] = g.cp[i];
+                dst[2 * n + i] = g.dg[i];
+                dst[3 * n + i] = g.dual[i];
+                dst[4 * n + i] = g.pl[i];
+                dst[5 * n + i] = g.pr[i];
+            }
+            for (int i = threadIdx.x; i < 3 * n; i += BOT_NT) dst[6 * n + i] = g.rw[i];
+        }
     // top level: b from global, u = 0 (the caller's correction starts at zero)
-    for (size_t t = threadIdx.x; t < lv[0].N(); t += BOT_NT) {
+    for (unsigned t = threadIdx.x; t < lv[0].N(); t += BOT_NT) {
         b[0][t] = a.b[0][t];
         u[0][t] = T(0);
     }
@@ -424,7 +420,7 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
             bot_rbgs(F, u[l], b[l], 1);
         }
         const LevelT<T>& C = lv[l + 1];
-        for (size_t t = threadIdx.x; t < C.N(); t += BOT_NT) {
+        for (unsigned t = threadIdx.x; t < C.N(); t += BOT_NT) {
             int I, J, K;
             node_ijk(t, C.nx, C.ny, I, J, K);
             u[l + 1][t] = T(0);
@@ -435,12 +431,12 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
             const T* wx = F.ax[0].rw + 3 * I;
             const T* wy = F.ax[1].rw + 3 * J;
             const T* wz = F.ax[2].rw + 3 * K;
-            const size_t sy = F.nx, sz = (size_t)F.nx * F.ny;
+            const unsigned sy = F.nx, sz = (unsigned)F.nx * F.ny;
             T acc = T(0);
             for (int c = 0; c < 3; c++)
                 for (int bb = 0; bb < 3; bb++) {
                     const int fk = 2 * K - 1 + c, fj = 2 * J - 1 + bb, fi = 2 * I - 1;
-                    const size_t P = (size_t)fk * sz + (size_t)fj * sy + fi;
+                    const unsigned P = (unsigned)fk * sz + (unsigned)fj * sy + fi;
                     const T r0 = resid_at(F, u[l], b[l], P, fi, fj, fk);
                     const T r1 = resid_at(F, u[l], b[l], P + 1, fi + 1, fj, fk);
                     const T r2 = resid_at(F, u[l], b[l], P + 2, fi + 2, fj, fk);
@@ -455,7 +451,8 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
         const LevelT<T>& F = lv[l];
         const LevelT<T>& C = lv[l + 1];
         const T* ec = u[l + 1];
-        for (size_t P = threadIdx.x; P < F.N(); P += BOT_NT) {
+        T* ul = u[l];
+        for (unsigned P = threadIdx.x; P < F.N(); P += BOT_NT) {
             int i, j, k;
             node_ijk(P, F.nx, F.ny, i, j, k);
             if (is_face(F, i, j, k)) continue;
@@ -464,8 +461,8 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
             const T wx[2] = {F.ax[0].pl[i], F.ax[0].pr[i]};
             const T wy[2] = {F.ax[1].pl[j], F.ax[1].pr[j]};
             const T wz[2] = {F.ax[2].pl[k], F.ax[2].pr[k]};
-            const size_t sy = C.nx, sz = (size_t)C.nx * C.ny;
-            const T* base = ec + (size_t)K * sz + (size_t)J * sy + I;
+            const unsigned sy = C.nx, sz = (unsigned)C.nx * C.ny;
+            const T* base = ec + (unsigned)K * sz + (unsigned)J * sy + I;
             T e = T(0);
             for (int c = 0; c < nk; c++)
                 for (int bb = 0; bb < nj; bb++) {
@@ -473,15 +470,15 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
                     const T sv = (ni == 2) ? fma(wx[0], row[0], wx[1] * row[1]) : row[0];
                     e = fma(wz[c] * wy[bb], sv, e);
                 }
-            u[l][P] += e;
+            ul[P] += e;
         }
         __syncthreads();
         for (int it = 0; it < a.nu2; it++) {
-            bot_rbgs(F, u[l], b[l], a.sym ? 1 : 0);
-            bot_rbgs(F, u[l], b[l], a.sym ? 0 : 1);
+            bot_rbgs(F, ul, b[l], a.sym ? 1 : 0);
+            bot_rbgs(F, ul, b[l], a.sym ? 0 : 1);
         }
     }
-    for (size_t t = threadIdx.x; t < lv[0].N(); t += BOT_NT) a.u[0][t] = u[0][t];
+    for (unsigned t = threadIdx.x; t < lv[0].N(); t += BOT_NT) a.u[0][t] = u[0][t];
 }
 
 template <typename T>
