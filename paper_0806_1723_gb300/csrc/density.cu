@@ -596,69 +596,76 @@ __global__ void k_moment_table(const double* __restrict__ x, int n, double c, do
     }
 }
 
-// row_mom[a][row] = sum_i xm[a][i] b[row, i],  row = k*ny + j
+// row_mom[a][row] = sum_i xm[a][i] b[row, i],  row = k*ny + j: one thread per row, sequential
+// FP64 sums (no shuffle trees: FP64 adds are scarce on this GPU).
 __global__ void __launch_bounds__(MOM_NT) k_row_moments(const double* __restrict__ b, int nx, size_t nrows,
                                                        const double* __restrict__ xm, double* __restrict__ row_mom)
 {
-    __shared__ double sm[32];
-    const size_t row = blockIdx.x;
+    const size_t row = blockIdx.x * (size_t)MOM_NT + threadIdx.x;
+    if (row >= nrows) return;
     const double* br = b + row * nx;
     double acc[5] = {0, 0, 0, 0, 0};
-    for (int i = threadIdx.x; i < nx; i += MOM_NT) {
+    for (int i = 0; i < nx; i++) {
         const double v = br[i];
 #pragma unroll
         for (int q = 0; q < 5; q++) acc[q] = fma(xm[(size_t)q * nx + i], v, acc[q]);
     }
-    for (int q = 0; q < 5; q++) {
-        const double s = block_sum<MOM_NT>(acc[q], sm);
-        if (threadIdx.x == 0) row_mom[(size_t)q * nrows + row] = s;
-    }
+#pragma unroll
+    for (int q = 0; q < 5; q++) row_mom[(size_t)q * nrows + row] = acc[q];
 }
 
 // pairs (a, b) with a + b <= 4, in a fixed order
 __constant__ int c_ab[15][2] = {{0, 0}, {0, 1}, {0, 2}, {0, 3}, {0, 4}, {1, 0}, {1, 1}, {1, 2}, {1, 3},
                                 {2, 0}, {2, 1}, {2, 2}, {3, 0}, {3, 1}, {4, 0}};
 
-// plane[ab][k] = sum_j ym[b][j] row_mom[a][k*ny + j]
+// plane[ab][k] = sum_j ym[b][j] row_mom[a][k*ny + j]: one thread per (ab, k)
 __global__ void __launch_bounds__(MOM_NT) k_plane_moments(const double* __restrict__ row_mom, int ny, int nz,
                                                          const double* __restrict__ ym, double* __restrict__ plane)
 {
-    __shared__ double sm[32];
-    const int k = blockIdx.x;
+    const int t = blockIdx.x * MOM_NT + threadIdx.x;
+    if (t >= 15 * nz) return;
+    const int ab = t / nz, k = t - ab * nz;
+    const int A = c_ab[ab][0], B = c_ab[ab][1];
     const size_t nrows = (size_t)ny * nz;
-    for (int ab = 0; ab < 15; ab++) {
-        const int A = c_ab[ab][0], B = c_ab[ab][1];
-        double acc = 0.0;
-        for (int j = threadIdx.x; j < ny; j += MOM_NT)
-            acc = fma(ym[(size_t)B * ny + j], row_mom[(size_t)A * nrows + (size_t)k * ny + j], acc);
-        const double s = block_sum<MOM_NT>(acc, sm);
-        if (threadIdx.x == 0) plane[(size_t)ab * nz + k] = s;
-    }
+    const double* rm = row_mom + (size_t)A * nrows + (size_t)k * ny;
+    const double* yb = ym + (size_t)B * ny;
+    double acc = 0.0;
+    for (int j = 0; j < ny; j++) acc = fma(yb[j], rm[j], acc);
+    plane[(size_t)ab * nz + k] = acc;
 }
 
-// M[a][b][c] = sum_k zm[c][k] plane[ab][k]; Q_lm = sum_terms coef M / (4 pi)
-__global__ void __launch_bounds__(MOM_NT) k_final_moments(const double* __restrict__ plane, int nz,
-                                                         const double* __restrict__ zm, double* __restrict__ Q)
+// M[a][b][c] = sum_k zm[c][k] plane[ab][k] (one thread per monomial); Q_lm = sum_terms coef M / (4 pi)
+__global__ void __launch_bounds__(64) k_final_moments(const double* __restrict__ plane, int nz,
+                                                     const double* __restrict__ zm, double* __restrict__ Q)
 {
-    __shared__ double sm[32];
     __shared__ double M[5][5][5];
-    for (int ab = 0; ab < 15; ab++) {
-        const int A = c_ab[ab][0], B = c_ab[ab][1];
-        for (int C = 0; C + A + B <= 4; C++) {
-            double acc = 0.0;
-            for (int k = threadIdx.x; k < nz; k += MOM_NT) acc = fma(zm[(size_t)C * nz + k], plane[(size_t)ab * nz + k], acc);
-            const double s = block_sum<MOM_NT>(acc, sm);
-            if (threadIdx.x == 0) M[A][B][C] = s;
+    const int t = threadIdx.x;
+    if (t < 35) {
+        // monomial t -> (ab, c) in the order of c_ab with c = 0 .. 4 - a - b
+        int idx = 0, ab = 0, C = 0;
+        for (int q = 0; q < 15; q++) {
+            const int room = 5 - c_ab[q][0] - c_ab[q][1];
+            if (t < idx + room) {
+                ab = q;
+                C = t - idx;
+                break;
+            }
+            idx += room;
         }
+        double acc = 0.0;
+        const double* pl = plane + (size_t)ab * nz;
+        const double* zc = zm + (size_t)C * nz;
+        for (int k = 0; k < nz; k++) acc = fma(zc[k], pl[k], acc);
+        M[c_ab[ab][0]][c_ab[ab][1]][C] = acc;
     }
     __syncthreads();
-    if (threadIdx.x < NLM) {
+    if (t < NLM) {
         double q = 0.0;
-        for (int t = 0; t < N_MONO_TERMS; t++) {
-            const Mono m = c_mono[t];
-            if (m.lm == (int)threadIdx.x) q = fma(m.coef, M[m.a][m.b][m.c], q);
+        for (int m = 0; m < N_MONO_TERMS; m++) {
+            const Mono mo = c_mono[m];
+            if (mo.lm == t) q = fma(mo.coef, M[mo.a][mo.b][mo.c], q);
         }
-        Q[threadIdx.x] = q / (4.0 * PI);
+        Q[t] = q / (4.0 * PI);
     }
 }
 
@@ -675,9 +682,9 @@ cudaError_t launch_multipoles(const int n[3], const double* x, const double* y, 
     k_moment_table<<<(n[1] + 127) / 128, 128, 0, s>>>(y, n[1], centre[1], ym);
     k_moment_table<<<(n[2] + 127) / 128, 128, 0, s>>>(z, n[2], centre[2], zm);
     const size_t nrows = (size_t)n[1] * n[2];
-    k_row_moments<<<(unsigned)nrows, MOM_NT, 0, s>>>(b, n[0], nrows, xm, row_mom);
-    k_plane_moments<<<n[2], MOM_NT, 0, s>>>(row_mom, n[1], n[2], ym, plane);
-    k_final_moments<<<1, MOM_NT, 0, s>>>(plane, n[2], zm, Q);
+    k_row_moments<<<(unsigned)((nrows + MOM_NT - 1) / MOM_NT), MOM_NT, 0, s>>>(b, n[0], nrows, xm, row_mom);
+    k_plane_moments<<<(15 * n[2] + MOM_NT - 1) / MOM_NT, MOM_NT, 0, s>>>(row_mom, n[1], n[2], ym, plane);
+    k_final_moments<<<1, 64, 0, s>>>(plane, n[2], zm, Q);
     return cudaGetLastError();
 }
 
