@@ -188,8 +188,11 @@ struct lasto_poisson {
     size_t pool_bytes = 0;
     double* quad = nullptr;
     int nq = 0;
-    cudaStream_t cs = nullptr, cs2 = nullptr, cs3 = nullptr, cs4 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t cs = nullptr, cs2 = nullptr, cs3 = nullptr;
+    cudaEvent_t ev_origin = nullptr;
+    // per batch slot: the cluster's branch stream, its setup stream and fork/join/done events
+    std::vector<cudaStream_t> bs, ss;
+    std::vector<cudaEvent_t> ef, ej, ed;
     // cached graph
     std::vector<char> key;
     cudaGraph_t graph = nullptr;
@@ -352,16 +355,18 @@ int enqueue_rhs(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const
 // Setup and right-hand side of one cluster.  The mesh tables and the coarse eigenvectors
 // depend only on the mesh and run on a second stream beside the sphere parameters,
 // deposit, multipoles and faces; the two branches join before the iteration.
-int enqueue_prologue(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const double* guess, cudaStream_t s)
+int enqueue_prologue(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const double* guess, cudaStream_t s,
+                     int slot)
 {
-    TRY(cudaEventRecord(h->ev_fork, s));
-    TRY(cudaStreamWaitEvent(h->cs4, h->ev_fork, 0));
-    int st = enqueue_setup(h, P, cl, h->cs4);
+    cudaStream_t side = h->ss[slot];
+    TRY(cudaEventRecord(h->ef[slot], s));
+    TRY(cudaStreamWaitEvent(side, h->ef[slot], 0));
+    int st = enqueue_setup(h, P, cl, side);
     if (st) return st;
-    TRY(cudaEventRecord(h->ev_join, h->cs4));
+    TRY(cudaEventRecord(h->ej[slot], side));
     TRY(cudaMemsetAsync(P.status, 0, sizeof(int) * 4, s));
     if ((st = enqueue_rhs(h, P, cl, guess, s))) return st;
-    TRY(cudaStreamWaitEvent(s, h->ev_join, 0));
+    TRY(cudaStreamWaitEvent(s, h->ej[slot], 0));
     return LASTO_OK;
 }
 
@@ -522,17 +527,23 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
     TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int st = LASTO_OK;
     size_t atom_off = 0, grid_off = 0;
+    // every cluster is an independent branch of the graph: small clusters' latency-bound
+    // kernels run side by side instead of one after another
+    if (cudaEventRecord(h->ev_origin, s) != cudaSuccess) st = LASTO_ERR_CUDA;
     for (int c = 0; c < nc && st == LASTO_OK; c++) {
         ClusterPlan& P = h->plans[c];
         const lasto_cluster& cl = cls[c];
-        if ((st = enqueue_prologue(h, P, cl, guess ? guess + grid_off : nullptr, s))) break;
+        cudaStream_t bsc = h->bs[c];
+        cudaError_t e = cudaStreamWaitEvent(bsc, h->ev_origin, 0);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamWaitEvent(origin)"); break; }
+        if ((st = enqueue_prologue(h, P, cl, guess ? guess + grid_off : nullptr, bsc, c))) break;
         // conditional WHILE node(s) for the iteration
         cudaGraphConditionalHandle cond;
-        if ((st = new_handle(h, s, &cond))) break;
-        if ((st = enqueue_start(h, P, cond, 1, s))) break;
+        if ((st = new_handle(h, bsc, &cond))) break;
+        if ((st = enqueue_start(h, P, cond, 1, bsc))) break;
         cudaGraph_t body;
-        if ((st = add_while(h, s, cond, &body))) break;
-        cudaError_t e = cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if ((st = add_while(h, bsc, cond, &body))) break;
+        e = cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamBeginCaptureToGraph"); break; }
         if (is_defect_correction(h)) {
             // outer body: inner start, inner WHILE (FP32 CG), FP64 correction + residual
@@ -562,8 +573,11 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
         e = cudaStreamEndCapture(h->cs2, &bout);
         if (st) break;
         if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamEndCapture(body)"); break; }
-        if ((st = enqueue_finish(h, P, cl, v_lm + NLM * atom_off, potential ? potential + grid_off : nullptr, s)))
+        if ((st = enqueue_finish(h, P, cl, v_lm + NLM * atom_off, potential ? potential + grid_off : nullptr, bsc)))
             break;
+        e = cudaEventRecord(h->ed[c], bsc);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ed[c], 0);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "join"); break; }
         atom_off += cl.n_atoms;
         grid_off += (size_t)cl.n[0] * cl.n[1] * cl.n[2];
     }
@@ -637,7 +651,7 @@ static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
         ClusterPlan& P = h->plans[c];
         const lasto_cluster& cl = cls[c];
         int st;
-        if ((st = enqueue_prologue(h, P, cl, guess ? guess + grid_off : nullptr, s))) return st;
+        if ((st = enqueue_prologue(h, P, cl, guess ? guess + grid_off : nullptr, s, 0))) return st;
         if ((st = enqueue_start(h, P, 0, 0, s))) return st;
         int done = 0;
         TRY(cudaMemcpyAsync(&done, &P.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -725,9 +739,19 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs3, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs4, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_origin, cudaEventDisableTiming);
+    h->bs.assign(cfg->max_batch, nullptr);
+    h->ss.assign(cfg->max_batch, nullptr);
+    h->ef.assign(cfg->max_batch, nullptr);
+    h->ej.assign(cfg->max_batch, nullptr);
+    h->ed.assign(cfg->max_batch, nullptr);
+    for (int c = 0; c < cfg->max_batch && e == cudaSuccess; c++) {
+        e = cudaStreamCreateWithFlags(&h->bs[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ss[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ef[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ej[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ed[c], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaMallocHost(&h->stats_pinned, sizeof(lasto_stats) * cfg->max_batch);
     if (e != cudaSuccess) {
         lasto_poisson_destroy(h);
@@ -749,9 +773,12 @@ void lasto_poisson_destroy(lasto_poisson* h)
     if (h->cs) cudaStreamDestroy(h->cs);
     if (h->cs2) cudaStreamDestroy(h->cs2);
     if (h->cs3) cudaStreamDestroy(h->cs3);
-    if (h->cs4) cudaStreamDestroy(h->cs4);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_origin) cudaEventDestroy(h->ev_origin);
+    for (auto x : h->bs) if (x) cudaStreamDestroy(x);
+    for (auto x : h->ss) if (x) cudaStreamDestroy(x);
+    for (auto x : h->ef) if (x) cudaEventDestroy(x);
+    for (auto x : h->ej) if (x) cudaEventDestroy(x);
+    for (auto x : h->ed) if (x) cudaEventDestroy(x);
     delete h;
 }
 

@@ -159,3 +159,30 @@ def test_error_statuses(orc):
     dc = B.DeviceCluster(big)
     with pytest.raises(RuntimeError):
         solver.solve(dc, torch.empty((13, 25), dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_of_uneven_clusters(orc, precision):
+    """Several clusters with different grids and atom counts in one solve call (one graph
+    launch, each cluster an independent branch): every cluster matches its own oracle solve."""
+    import torch
+    B = need_gpu()
+    batch = [synth.pd13_small(n=33), synth.pd2_dimer(n=65, half_width=12.0, graded=True), synth.pd13_uniform65(),
+             synth.pd13_small(n=65, seed=21), synth.pd2_dimer(n=33, seed=22)]
+    n_max = max(c.n for c in batch)
+    atoms = sum(c.n_atoms for c in batch)
+    solver = B.Poisson(n_max=n_max, max_atoms=max(c.n_atoms for c in batch), max_batch=len(batch),
+                       precision=precision)
+    dcs = [B.DeviceCluster(c) for c in batch]
+    vlm = torch.empty((atoms, 25), dtype=torch.float64, device="cuda")
+    pot = torch.empty(sum(d.N for d in dcs), dtype=torch.float64, device="cuda")
+    for rep in range(2):                       # capture, then replay
+        st = solver.solve(dcs, vlm, potential=pot)
+        torch.cuda.synchronize()
+        got = host(vlm)
+        off = 0
+        for c, s in zip(batch, st):
+            ref = oracle_vlm(orc, c)
+            assert s.status == 0 and s.rel_resid <= 1e-10, (c.name, s.status, s.rel_resid)
+            assert np.abs(got[off:off + c.n_atoms] - ref).max() <= 1e-8 * np.abs(ref).max(), c.name
+            off += c.n_atoms
