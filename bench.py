@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
+    p.add_argument("--no-batch64", action="store_true")
     p.add_argument("--direct", action="store_true",
                    help="launch the kernels directly instead of one CUDA graph per solve (for ncu)")
     return p.parse_args()
@@ -286,9 +287,18 @@ def main():
         e2e_val = (args.steps * ws) / (max_over_ranks(sum(ms_e2e), ws, dev) / 1e3)
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # ---------------- roofline of the dominant kernel (the FP64 deposit), timed alone
-    roof = kernel_roofline(B, cl, dc, stream, flush, dev, 1)
-    roof["fp64_deposit_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 0)["ms"]
+    # ---------------- batched forms (one graph launch per batch, clusters as concurrent branches)
+    batch8 = batch_throughput(B, [synth.pd55_graded129(seed=1 + k) for k in range(8)], B.LASTO_PREC_MIXED,
+                              max(2, args.steps // 4), flush, stream, dev)
+    b64 = None
+    if not args.no_batch64:
+        b64 = batch_throughput(B, synth.batch64(), B.LASTO_PREC_MIXED, 2, flush, stream, dev, warmup=1)
+
+    # ---------------- roofline of the dominant kernel (FP32 red-black half sweep)
+    roof = smoother_roofline(B, stream, flush, dev)
+    dep = kernel_roofline(B, cl, dc, stream, flush, dev, 1)
+    roof["deposit_fp32pair_ms"] = dep["ms"]
+    roof["deposit_fp64_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 0)["ms"]
 
     # ---------------- CPU baseline: the oracle as it stands, one whole solve
     cpu = None
@@ -307,6 +317,8 @@ def main():
                        "rel_resid": st_mixed.rel_resid, "parallelism": f"replicas x{ws}"},
             "plain_fp64": {"value": plain_value, "unit": UNIT, "ms_per_step": sum(ms_plain) / args.steps,
                            "cycles": cyc_plain[-1][0], "rel_resid": st_plain.rel_resid},
+            "batched_pd55x8": batch8,
+            "batch64_uneven": b64,
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": launches,
@@ -318,6 +330,80 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def batch_throughput(B, clusters, precision, steps, flush, stream, dev, warmup=2):
+    """Solves/s of a batch of clusters solved in one call (one graph launch)."""
+    import torch
+    n_max = max(c.n for c in clusters)
+    solver = B.Poisson(n_max=n_max, max_atoms=max(c.n_atoms for c in clusters), max_batch=len(clusters),
+                       precision=precision)
+    dcs = [B.DeviceCluster(c) for c in clusters]
+    vlm = torch.empty((sum(c.n_atoms for c in clusters), 25), dtype=torch.float64, device=dev)
+    for _ in range(warmup):
+        st = solver.solve(dcs, vlm)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = solver.solve(dcs, vlm)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ok = all(s.status == 0 and s.rel_resid <= 1e-10 for s in st)
+    solver.close()
+    del dcs, vlm
+    torch.cuda.empty_cache()
+    return {"value": len(clusters) * steps / (sum(ms) / 1e3), "unit": UNIT, "clusters": len(clusters),
+            "ms_per_batch": sum(ms) / steps, "all_converged": ok,
+            "max_cycles": max(s.cycles for s in st), "nodes": sum(c.n ** 3 for c in clusters)}
+
+
+def smoother_roofline(B, stream, flush, dev):
+    """FP32 red-black half sweep on the 385^3 graded Pd561 mesh (456 MB of u and b, far beyond
+    L2).  Algorithmic bytes per half sweep: every node's u read once (4 B), the colour's b read
+    and u written (8 B per updated node) = 8 B per node.  Time per launch from a 1-sweep and a
+    3-sweep call (the difference is 4 launches), L2 flushed before each call."""
+    import json as _json
+    import torch
+
+    import synth
+    cl = synth.pd561_graded385(n_densities=1)[0]
+    n = cl.n
+    axes = [B.lasto_mesh_axis(n, 0.0, cl.half_width, cl.h_min, cl.h_max, cl.p_max) for _ in range(3)]
+    u = torch.zeros(n ** 3, dtype=torch.float32, device=dev)
+    b = torch.rand(n ** 3, dtype=torch.float32, device=dev)
+
+    def timed(sweeps):
+        ts = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            B.lasto_op_smooth(*axes, u, b, sweeps=sweeps)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    timed(1)
+    t_launch = (timed(3) - timed(1)) / 4 / 1e3
+    bytes_per_launch = 8.0 * n ** 3
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = bytes_per_launch / t_launch / 1e9
+    del u, b
+    torch.cuda.empty_cache()
+    return {"kernel": "k_rbgs<float> (red-black half sweep, 385^3 graded)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
 
 def kernel_roofline(B, cl, dc, stream, flush, dev, precision=1):
