@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batch64", action="store_true")
+    p.add_argument("--profile", choices=["smoother", "solve"], default=None,
+                   help="run one kernel family for a profiler and exit: 'smoother' = one FP32 red-black sweep "
+                        "on an n^3 graded mesh, 'solve' = one mixed solve of the workload with direct launches")
+    p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
     p.add_argument("--direct", action="store_true",
                    help="launch the kernels directly instead of one CUDA graph per solve (for ncu)")
     return p.parse_args()
@@ -191,6 +195,8 @@ def main():
     ws, rank, local = dist_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
+    if args.profile:
+        return run_profile(args, B)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if ws > 1:
@@ -329,6 +335,30 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def run_profile(args, B):
+    """One kernel family for ncu (no timing of its own)."""
+    import torch
+
+    import synth
+    if args.profile == "smoother":
+        n = args.n
+        axes = [B.lasto_mesh_axis(n, 0.0, 30.0, 0.12, 0.6, 6.0) for _ in range(3)]
+        u = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
+        b = torch.rand(n ** 3, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        B.lasto_op_smooth(*axes, u, b, sweeps=1)
+    else:
+        cl = synth.pd55_graded129()
+        solver = B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, precision=B.LASTO_PREC_MIXED, launch=1)
+        dc = B.DeviceCluster(cl)
+        v = torch.empty((cl.n_atoms, 25), dtype=torch.float64, device="cuda")
+        st = solver.solve(dc, v)
+        torch.cuda.synchronize()
+        assert st[0].status == 0
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "ok": True}))
     return 0
 
 
