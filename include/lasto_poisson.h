@@ -253,6 +253,59 @@ int lasto_op_project(const int n[3], const double* x, const double* y, const dou
                      int n_atoms, const double* pos, const double* R, int n_theta, int n_phi, double* vlm,
                      int* status, void* stream);
 
+/* ------------------------------------------------------------------ learned initial guess
+ * Operations of the small 3-D U-Net that predicts the coarse-grid (33^3) potential used as the
+ * multigrid initial guess.  The paper has no counterpart (it solves from scratch each SCF
+ * step); the network is an accelerator: multigrid always runs to the same residual, so the
+ * guess changes only the iteration count, never the answer.
+ * Layout: channels-last, [node][channel], node = ((b*D + z)*H + y)*W + x over nb grids of
+ * dims = {W, H, D} nodes.  Weights: [27 taps][cin][cout], tap = (dz+1)*9 + (dy+1)*3 + (dx+1),
+ * zero padding.  BF16 arrays are passed as void* (2 bytes per element); cin, cout multiples
+ * of 16 (cout <= 128; wgrad cout <= 64).  All pointers device; all calls asynchronous;
+ * INVALID_ARG for unsupported sizes, CUDA for launch failures. */
+
+/* y = act(conv(x, w) + bias), act = ReLU if relu != 0.  Tensor-core BF16 products, FP32
+ * accumulation.  y32 (FP32, row stride ldy32, channel offset off32) and y16 (BF16, ldy16,
+ * off16) are each optional: writing into a channel slice makes concatenation free. */
+int lasto_nn_conv3d_fwd(int nb, const int dims[3], int cin, int cout, const void* x, const void* w, const float* bias,
+                        int relu, float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, void* stream);
+/* dx32 = data gradient of the convolution for output gradient dy (BF16 [node][cout]);
+ * w_flip is caller scratch of 27*cin*cout BF16 (the flipped, transposed weights). */
+int lasto_nn_conv3d_dgrad(int nb, const int dims[3], int cin, int cout, const void* dy, const void* w, void* w_flip,
+                          float* dx32, void* stream);
+/* dw (FP32 [27][cin][cout]) += weight gradient; db (FP32 [cout], optional) += bias gradient
+ * from dy32 (FP32 copy of dy).  dw accumulates with atomics (order not fixed). */
+int lasto_nn_conv3d_wgrad(int nb, const int dims[3], int cin, int cout, const void* x, const void* dy16,
+                          const float* dy32, float* dw, float* db, void* stream);
+/* dx = dy where y > 0 else 0 (FP32 and / or BF16 output). */
+int lasto_nn_relu_grad(size_t n, const float* y, const float* dy, float* dx, void* dx16, void* stream);
+int lasto_nn_to_bf16(size_t n, const float* a, void* b, void* stream);
+/* dst[node][doff + c] = (or +=) src[node][soff + c], c < C. */
+int lasto_nn_copy_channels(size_t nodes, int C, const float* src, int lds, int soff, float* dst, int ldd, int doff,
+                           int accumulate, void* stream);
+/* Full-weighting average from a fine node grid (odd dims) onto every other node, boundary
+ * planes renormalised; adjoint != 0 applies the transpose (coarse -> fine). */
+int lasto_nn_down(int nb, const int fine[3], int C, const float* x, float* y, int adjoint, void* stream);
+/* Trilinear interpolation from the every-other-node grid onto the fine grid, written into
+ * channels [off, off + C) of rows of stride ldy; adjoint != 0: fine (ldy, off) -> coarse. */
+int lasto_nn_up(int nb, const int fine[3], int C, const float* x, float* y, int ldy, int off, int adjoint, void* stream);
+/* Masked mean-square error: loss (FP64, accumulated) += sum mask (p - t)^2 * inv_count and
+ * dp = 2 mask (p - t) inv_count.  mask may be NULL. */
+int lasto_nn_mse(size_t n, const float* p, const float* t, const float* mask, float inv_count, float* dp, double* loss,
+                 void* stream);
+/* Network input on the coarse (33^3) grid n[3] with coordinates x, y, z: out [N][16] FP32,
+ * channel 0 = b h^2 s0 (interior), channel 1 = faces s1 (faces only), channel 2 = log(h/h_ref),
+ * h the local dual-cell size; b and faces FP64 grids (faces: Dirichlet values, any interior). */
+int lasto_nn_guess_features(const int n[3], const double* b, const double* faces, const double* x, const double* y,
+                            const double* z, float s0, float s1, float h_ref, float* out, void* stream);
+/* Coarse-grid guess u (FP64) = pred[node * ld] / scale inside, faces copied from `faces`. */
+int lasto_nn_guess_grid(const int n[3], const float* pred, int ld, float scale, const double* faces, double* u,
+                        void* stream);
+/* One Adam step (Kingma & Ba) on FP32 master weights, step counted from 1; w16 (BF16 copy)
+ * optional. */
+int lasto_nn_adam(size_t n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
+                  int step, void* w16, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -147,6 +147,25 @@ def pd561_graded385(seed: int = 4, n_densities: int = 8, n: int = 385) -> list[C
     return seq
 
 
+def guess_training_set(count: int, seed: int = 3, n: int = 129) -> list[Cluster]:
+    """Training clusters of the learned initial guess: perturbed Pd13 / Pd55 / Pd147 on graded
+    n^3 meshes (same recipe as the 64-cluster batch, one mesh size)."""
+    rng = np.random.default_rng(seed)
+    shapes = {13: clusters.cuboctahedron13(), 55: clusters.mackay_icosahedron(2), 147: clusters.mackay_icosahedron(3)}
+    out = []
+    for c in range(count):
+        kind = int(rng.choice([13, 55, 147]))
+        pos = shapes[kind] + rng.normal(0.0, 0.1, size=shapes[kind].shape)
+        for _ in range(10000):
+            bad = clusters.close_atoms(pos, 2 * R_SPHERE + 0.24)
+            if len(bad) == 0:
+                break
+            pos[bad] = shapes[kind][bad] + rng.normal(0.0, 0.1, size=(len(bad), 3))
+        out.append(make_cluster(f"guess{c}-Pd{kind}", pos, rng, n=n, half_width=graded_box(pos), h_min=0.12,
+                                h_max=0.6))
+    return out
+
+
 # ---------------------------------------------------------------- small test cases
 def pd2_dimer(seed: int = 10, n: int = 33, half_width: float = 9.0, graded: bool = False) -> Cluster:
     """Pd2 at the paper's GGA bond length 4.802 au (Table 2), in a small box."""
