@@ -92,7 +92,8 @@ def train(net, X, Y, epochs=4, lr=1e-3, log=print, seed=0):
     steps = 0
     for ep in range(epochs):
         perm = torch.randperm(X.shape[0], generator=g)
-        tot, cnt = 0.0, 0
+        tot = torch.zeros((), dtype=torch.float64, device="cuda")
+        cnt = 0
         for s0 in range(0, X.shape[0] - nb + 1, nb):
             idx = perm[s0:s0 + nb].cuda()
             x32.view(nb, N, 16)[:, :, :3] = X[idx]
@@ -102,11 +103,9 @@ def train(net, X, Y, epochs=4, lr=1e-3, log=print, seed=0):
             net.backward(net.dpred)
             net.adam(lr * (0.5 ** (ep // 2)))
             steps += 1
-            if steps % 50 == 0:
-                l = float(loss.item())
-                tot += l
-                cnt += 1
-        hist.append(tot / max(cnt, 1))
+            tot += loss.reshape(())        # summed on the device: no host sync per step
+            cnt += 1
+        hist.append(float(tot.item()) / max(cnt, 1))
         if log:
             log(f"epoch {ep}: mean loss {hist[-1]:.4e}  ({time.time() - t0:.1f}s, {steps} steps)")
     return hist
