@@ -230,6 +230,22 @@ int lasto_op_smooth(const int n[3], const double* x, const double* y, const doub
 int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const double* z, float* u,
                         const float* b, int sweeps, void* stream);
 
+/* Red-black Gauss-Seidel on z-slabs staged in shared memory (the Section 3 smoother):
+ * `sweeps` full sweeps, each colour `first` (0 = red, i+j+k even) then the other, from
+ * u_in into u_out, fused ns (1 or 2) sweeps per pass over the grid.  u_in, u_out, b:
+ * distinct device arrays [n0*n1*n2] (x fastest); u_in is not modified; every node of
+ * u_out is written, faces copied from u_in.  The result is bitwise that of `sweeps`
+ * in-place sweeps.  tile = {tx, ty, kz}: the (x, y) tile and the number of z planes one
+ * thread block owns (any tile gives the same result).  More than one pass takes one
+ * device scratch grid from the stream-ordered allocator.  INVALID_ARG for sweeps < 1, ns
+ * outside {1, 2}, a tile needing more than 200 KiB of shared memory, or u_in == u_out. */
+int lasto_op_smooth_slab(const int n[3], const double* x, const double* y, const double* z, const double* u_in,
+                         double* u_out, const double* b, int sweeps, int ns, int first, const int tile[3],
+                         void* stream);
+int lasto_op_smooth_slab_f32(const int n[3], const double* x, const double* y, const double* z, const float* u_in,
+                             float* u_out, const float* b, int sweeps, int ns, int first, const int tile[3],
+                             void* stream);
+
 /* Full weighting bc = Vc^-1 P^T Vf r onto the every-other-node mesh; bc device
  * [(n0+1)/2 * (n1+1)/2 * (n2+1)/2], faces set to 0.  x, y, z are the fine axes. */
 int lasto_op_restrict(const int n[3], const double* x, const double* y, const double* z, const double* r,

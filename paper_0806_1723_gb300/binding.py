@@ -47,7 +47,7 @@ EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve"
            "lasto_poisson_last_error", "lasto_poisson_kernel_counts", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
            "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
-           "lasto_op_smooth_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
+           "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
            "lasto_op_project", "lasto_nn_conv3d_fwd", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
            "lasto_nn_relu_grad", "lasto_nn_to_bf16", "lasto_nn_copy_channels", "lasto_nn_down", "lasto_nn_up",
            "lasto_nn_mse", "lasto_nn_adam", "lasto_nn_guess_features", "lasto_nn_guess_grid"]
@@ -76,6 +76,8 @@ def _declare(L):
         "lasto_op_residual": (i, [ip, vp, vp, vp, vp, vp, vp, vp]),
         "lasto_op_smooth": (i, [ip, vp, vp, vp, vp, vp, i, vp]),
         "lasto_op_smooth_f32": (i, [ip, vp, vp, vp, vp, vp, i, vp]),
+        "lasto_op_smooth_slab": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, ip, vp]),
+        "lasto_op_smooth_slab_f32": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, ip, vp]),
         "lasto_op_restrict": (i, [ip, vp, vp, vp, vp, vp, vp]),
         "lasto_op_prolong_add": (i, [ip, vp, vp, vp, vp, vp, vp]),
         "lasto_op_coarse_solve": (i, [ip, vp, vp, vp, vp, vp, vp]),
@@ -309,6 +311,15 @@ def lasto_op_smooth(x, y, z, u, b, sweeps=1, stream=None):
     fn = load().lasto_op_smooth if u.dtype == torch.float64 else load().lasto_op_smooth_f32
     _check(fn(*_axes(x, y, z), _ptr(u), _ptr(b), int(sweeps), _stream(stream)), "lasto_op_smooth")
     return u
+
+
+def lasto_op_smooth_slab(x, y, z, u_in, u_out, b, sweeps=None, ns=1, first=0, tile=(32, 8, 16), stream=None):
+    """`sweeps` (default ns) red-black sweeps from u_in into u_out, ns fused per pass (FP64 or FP32)."""
+    fn = load().lasto_op_smooth_slab if u_in.dtype == torch.float64 else load().lasto_op_smooth_slab_f32
+    sweeps = ns if sweeps is None else sweeps
+    _check(fn(*_axes(x, y, z), _ptr(u_in), _ptr(u_out), _ptr(b), int(sweeps), int(ns), int(first), _n3(tile),
+              _stream(stream)), "lasto_op_smooth_slab")
+    return u_out
 
 
 def lasto_op_restrict(x, y, z, r, stream=None):

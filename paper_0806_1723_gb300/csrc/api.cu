@@ -914,6 +914,33 @@ bool op_grid_ok(const int n[3], const double* x, const double* y, const double* 
 
 }  // namespace
 
+template <typename T>
+int op_smooth_slab(const int n[3], const double* x, const double* y, const double* z, const T* u_in, T* u_out,
+                   const T* b, int sweeps, int ns, int first, const int tile[3], void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !u_in || !u_out || !b || !tile || u_in == u_out || sweeps < 1)
+        return LASTO_ERR_INVALID_ARG;
+    const SlabShape sh{tile[0], tile[1], tile[2], ns};
+    if (!slab_shape_ok(sh, sizeof(T))) return LASTO_ERR_INVALID_ARG;
+    init_device_constants();
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, sizeof(T) == 8, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    const int full = sweeps / ns, rest = sweeps % ns, passes = full + (rest ? 1 : 0);
+    Scratch tmp(passes > 1 ? sizeof(T) * (size_t)n[0] * n[1] * n[2] : 0, s);
+    if (passes > 1 && !tmp.p) return LASTO_ERR_NO_MEMORY;
+    const T* src = u_in;
+    cudaError_t e = cudaSuccess;
+    for (int m = 1; m <= passes && e == cudaSuccess; m++) {
+        T* dst = ((passes - m) % 2 == 0) ? u_out : tmp.as<T>();   // the last pass lands in u_out
+        SlabShape shm = sh;
+        if (m == passes && rest) shm.ns = rest;
+        e = launch_rb_slab<T>(Arr<T>::view(L.S), src, dst, b, first & 1, 0, shm, s);
+        src = dst;
+    }
+    return op_status(e);
+}
+
 extern "C" {
 
 int lasto_op_sphere_params(const lasto_cluster* cl, double* q, double* rhoR, double* drhoR, double* coef, int* status,
@@ -1010,6 +1037,20 @@ int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const 
         if (e == cudaSuccess) e = launch_rbgs<float>(L.S.view32(), u, b, 1, s);
     }
     return op_status(e);
+}
+
+int lasto_op_smooth_slab(const int n[3], const double* x, const double* y, const double* z, const double* u_in,
+                         double* u_out, const double* b, int sweeps, int ns, int first, const int tile[3],
+                         void* stream)
+{
+    return op_smooth_slab<double>(n, x, y, z, u_in, u_out, b, sweeps, ns, first, tile, stream);
+}
+
+int lasto_op_smooth_slab_f32(const int n[3], const double* x, const double* y, const double* z, const float* u_in,
+                             float* u_out, const float* b, int sweeps, int ns, int first, const int tile[3],
+                             void* stream)
+{
+    return op_smooth_slab<float>(n, x, y, z, u_in, u_out, b, sweeps, ns, first, tile, stream);
 }
 
 int lasto_op_restrict(const int n[3], const double* x, const double* y, const double* z, const double* r, double* bc,

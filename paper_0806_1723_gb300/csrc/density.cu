@@ -571,6 +571,7 @@ void init_device_constants()
     cudaFuncSetAttribute(k_deposit64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_deposit_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     init_mg_attributes();
+    init_slab_attributes();
     done_dev = dev;
 }
 

@@ -146,6 +146,21 @@ template <typename T>
 cudaError_t launch_resid_restrict(const LevelT<T>& fine, const LevelT<T>& coarse, const T* u, const T* b, T* bc, T* uc,
                                   cudaStream_t s);
 
+// slab.cu: fused red-black smoother.  One pass = ns full sweeps (colour `first`, then the
+// other), u_in -> u_out (distinct arrays; every node of u_out written).  A CTA owns a
+// tx x ty tile of the (x, y) plane and kz planes of z.
+struct SlabShape {
+    int tx, ty, kz, ns;
+};
+constexpr size_t SLAB_MAX_SMEM = 200 * 1024;
+size_t slab_smem_bytes(const SlabShape& sh, size_t elem);
+bool slab_shape_ok(const SlabShape& sh, size_t elem);
+void init_slab_attributes();   // shared-memory opt-in; call outside capture
+// zero_in != 0: u_in is taken as zero everywhere (it is not read)
+template <typename T>
+cudaError_t launch_rb_slab(const LevelT<T>& L, const T* uin, T* uout, const T* b, int first, int zero_in,
+                           const SlabShape& sh, cudaStream_t s);
+
 // Levels lb..L-1 of a V-cycle in one thread block (u[0] = 0 on entry).
 constexpr int BOTTOM_MAX_LEVELS = 4;
 constexpr size_t BOTTOM_MAX_NODES = 5000;    // the top bottom level has at most this many nodes (17^3)

@@ -71,6 +71,79 @@ def test_red_black_sweep_fp32(orc):
     assert np.abs(got - ref).max() < 2e-5 * np.abs(ref).max()
 
 
+SLAB_CASES = [((33, 33, 33), 1, 0, (32, 8, 16)), ((65, 33, 49), 2, 0, (16, 4, 8)), ((65, 33, 49), 2, 1, (64, 16, 16)),
+              ((97, 97, 97), 2, 1, (40, 6, 11)), ((37, 7, 5), 1, 1, (2, 2, 1)), ((35, 9, 33), 1, 0, (62, 6, 16)), ((5, 5, 5), 2, 0, (2, 1, 1)),
+              ((3, 3, 3), 1, 0, (8, 8, 8))]
+
+
+def _sweeps_ref(orc, x, y, z, u, b, ns, first):
+    ref = u.copy()
+    for _ in range(ns):
+        orc.rbgs_half(x, y, z, ref, b, first)
+        orc.rbgs_half(x, y, z, ref, b, 1 - first)
+    return ref
+
+
+@pytest.mark.parametrize("n,ns,first,tile", SLAB_CASES)
+def test_slab_smoother_fp64(orc, n, ns, first, tile):
+    """Fused z-slab passes (ragged tiles, tiles wider than the grid, one-node tiles) equal
+    the oracle's in-place half sweeps; faces are copied unchanged."""
+    B = need_gpu()
+    import torch
+    x, y, z = _grid(n, 11)
+    rng = np.random.default_rng(12)
+    u, b = rng.normal(size=n[::-1]), rng.normal(size=n[::-1])
+    ref = _sweeps_ref(orc, x, y, z, u, b, ns, first)
+    out = torch.full(n[::-1], float("nan"), dtype=torch.float64, device="cuda")
+    B.lasto_op_smooth_slab(dev(x), dev(y), dev(z), dev(u), out, dev(b), ns=ns, first=first, tile=tile)
+    got = host(out)
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+    for face in (np.s_[0], np.s_[-1], np.s_[:, 0], np.s_[:, -1], np.s_[:, :, 0], np.s_[:, :, -1]):
+        assert np.array_equal(got[face], u[face])
+
+
+def test_slab_smoother_fp32(orc):
+    """FP32 passes: within FP32 rounding of the oracle, and bitwise the same for two tilings
+    and for the in-place half-sweep kernel."""
+    B = need_gpu()
+    import torch
+    n = (65, 33, 49)
+    x, y, z = _grid(n, 13)
+    rng = np.random.default_rng(14)
+    u, b = rng.normal(size=n[::-1]), rng.normal(size=n[::-1])
+    u32 = torch.as_tensor(u.astype(np.float32)).cuda()
+    b32 = torch.as_tensor(b.astype(np.float32)).cuda()
+    outs = []
+    for ns, tile in ((2, (32, 8, 16)), (2, (24, 5, 7)), (1, (30, 14, 8))):
+        o = torch.empty_like(u32)
+        B.lasto_op_smooth_slab(dev(x), dev(y), dev(z), u32, o, b32, sweeps=2, ns=ns, first=0, tile=tile)
+        outs.append(o)
+    ref = _sweeps_ref(orc, x, y, z, u, b, 2, 0)
+    assert np.abs(outs[0].cpu().numpy().astype(np.float64) - ref).max() < 4e-5 * np.abs(ref).max()
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    inplace = B.lasto_op_smooth(dev(x), dev(y), dev(z), u32.clone(), b32, sweeps=2)
+    assert torch.equal(outs[0], inplace)
+    # five sweeps as 2 + 2 + 1 fused passes through the op's scratch grid
+    o5 = torch.empty_like(u32)
+    B.lasto_op_smooth_slab(dev(x), dev(y), dev(z), u32, o5, b32, sweeps=5, ns=2, first=0, tile=(32, 8, 16))
+    assert torch.equal(o5, B.lasto_op_smooth(dev(x), dev(y), dev(z), u32.clone(), b32, sweeps=5))
+
+
+def test_slab_smoother_rejects_bad_arguments():
+    B = need_gpu()
+    import torch
+    n = (9, 9, 9)
+    x, y, z = _grid(n, 15)
+    u = torch.zeros(n, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(u)
+    for kw in (dict(u_out=u), dict(ns=3), dict(tile=(400, 400, 4)), dict(sweeps=0), dict(tile=(7, 4, 4))):
+        args = dict(u_in=u, u_out=torch.empty_like(u), b=b, ns=1, first=0, tile=(8, 8, 8))
+        args.update(kw)
+        with pytest.raises(RuntimeError, match="INVALID_ARG"):
+            B.lasto_op_smooth_slab(dev(x), dev(y), dev(z), **args)
+
+
 @pytest.mark.parametrize("n", SIZES)
 def test_restriction_and_prolongation(orc, n):
     B = need_gpu()
