@@ -236,7 +236,10 @@ int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const 
  * distinct device arrays [n0*n1*n2] (x fastest); u_in is not modified; every node of
  * u_out is written, faces copied from u_in.  The result is bitwise that of `sweeps`
  * in-place sweeps.  tile = {tx, ty, kz}: the (x, y) tile and the number of z planes one
- * thread block owns (any tile gives the same result).  More than one pass takes one
+ * thread block owns (any tile gives the same result).  ns = 1 passes need tx = 62 and
+ * 32 (ty + 2) threads <= 512 (FP32) or 256 (FP64); ns = 2 passes take any tile within the
+ * shared-memory limit; a remainder pass (sweeps not a multiple of ns) runs the one-sweep
+ * kernel on its own tile with the given kz.  More than one pass takes one
  * device scratch grid from the stream-ordered allocator.  INVALID_ARG for sweeps < 1, ns
  * outside {1, 2}, a tile needing more than 200 KiB of shared memory, or u_in == u_out. */
 int lasto_op_smooth_slab(const int n[3], const double* x, const double* y, const double* z, const double* u_in,

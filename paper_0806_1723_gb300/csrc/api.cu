@@ -934,7 +934,10 @@ int op_smooth_slab(const int n[3], const double* x, const double* y, const doubl
     for (int m = 1; m <= passes && e == cudaSuccess; m++) {
         T* dst = ((passes - m) % 2 == 0) ? u_out : tmp.as<T>();   // the last pass lands in u_out
         SlabShape shm = sh;
-        if (m == passes && rest) shm.ns = rest;
+        if (m == passes && rest) {   // the remainder pass (fewer sweeps) takes that kernel's own shape
+            shm = slab_default_shape(rest, sizeof(T));
+            shm.kz = sh.kz;
+        }
         e = launch_rb_slab<T>(Arr<T>::view(L.S), src, dst, b, first & 1, 0, shm, s);
         src = dst;
     }

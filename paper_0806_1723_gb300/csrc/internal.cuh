@@ -155,6 +155,7 @@ struct SlabShape {
 constexpr size_t SLAB_MAX_SMEM = 200 * 1024;
 size_t slab_smem_bytes(const SlabShape& sh, size_t elem);
 bool slab_shape_ok(const SlabShape& sh, size_t elem);
+SlabShape slab_default_shape(int ns, size_t elem);   // a valid shape for ns sweeps per pass
 void init_slab_attributes();   // shared-memory opt-in; call outside capture
 // zero_in != 0: u_in is taken as zero everywhere (it is not read)
 template <typename T>

@@ -135,112 +135,100 @@ __global__ void __launch_bounds__(SLAB_NT) k_rb_slab(LevelT<T> L, const T* __res
     }
 }
 
-// One full sweep per pass with the z column in registers.  Thread (px, py) owns the node
-// pair (i0 - 1 + 2 px, i0 + 2 px) of row j0 - 1 + py: one red and one black node in every
-// plane.  The block covers the tile widened by one node (tx = 2 (PX - 1), ty = RY - 2).  At
-// step p it updates the red node of plane p-1 (x/y neighbours from shared plane A: the old
-// values; the edge threads bring one more node of halo), the black node of plane p-2 (x/y
-// neighbours from shared plane B: the red values published a step earlier), and writes
-// plane p-2.  Its pair's u and b for planes p-3 .. p+CD are a register ring that the loop,
-// unrolled over the ring length, indexes with constants, so the loads of plane p+CD are in
-// flight for CD steps; the halo arrives by cp.async into a ring of A planes.  B is
-// double-buffered by step parity, so one barrier per step orders every shared read after
-// its write.
-constexpr int CD = 2;            // planes of prefetch
-constexpr int CR = CD + 4;       // register ring: planes p-3 .. p+CD
-constexpr int CWA = CD + 3;      // shared A ring
+// One full sweep per pass with the z column in registers.  A warp is one row of the
+// block: lane px owns the node pair (i0 - 1 + 2 px, i0 + 2 px) of row j0 - 1 + py, one red
+// and one black node in every plane; 32 lanes cover the 62-node tile plus one node each
+// side, and the block's RY rows the tile's ty = RY - 2 rows plus one each side.  At step p
+// a lane updates its red node of plane p-1 (x/y neighbours from shared plane A: the old
+// values, plus one node of halo that the edge lanes bring), its black node of plane p-2
+// (x/y neighbours from shared plane B: the red values published a step earlier), and
+// writes plane p-2.  The pair's u and b (and the FP64 inverse diagonal) for planes
+// p-3 .. p+2 form a register ring; the loop is unrolled over the ring length, so ring
+// slots, shared slots and the colour of each node of the pair are constants of the
+// unrolled step (the colour pattern also depends on RB = parity(i0 - 1 + j + k0) xor
+// first, a template parameter).  Loads of plane p+2 are in flight for two steps; the halo
+// arrives by cp.async.  One barrier per step orders every shared read after its write.
+constexpr int COL_PX = 32;       // lanes per row (one warp)
+constexpr int COL_TX = 2 * (COL_PX - 1);
+constexpr int CR = 6;            // register ring and shared A ring: planes p-3 .. p+2
 
-template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512)
-    k_rb_col(LevelT<T> L, const T* __restrict__ uin, T* __restrict__ uout, const T* __restrict__ b, int first,
-             int zero_in, int kz)
+template <typename T, int RB>
+__device__ __forceinline__ void col_sweep(const LevelT<T>& L, const T* __restrict__ uin, T* __restrict__ uout,
+                                          const T* __restrict__ b, int zero_in, int k0, int k1, T* SA, T* SB,
+                                          const T* ZC)
 {
-    extern __shared__ __align__(16) unsigned char col_smem[];
-    const int PX = blockDim.x, RY = blockDim.y;
-    const int TX = 2 * (PX - 1), TY = RY - 2;
-    const int AX = TX + 4, AY = TY + 4, BX = TX + 2, AP = AX * AY;
-    T* SA = reinterpret_cast<T*>(col_smem);           // [CWA][AY][AX]
-    T* SB = SA + CWA * AP;                             // [2][RY][BX]
-    T* ZC = SB + 2 * RY * BX;                          // [kz + 4][3]: cm, cp, dg of planes k0-2 ..
+    const int RY = blockDim.y;
+    const int TY = RY - 2;
+    constexpr int AX = COL_TX + 4, BX = COL_TX + 2;
+    const int AY = TY + 4, AP = AX * AY, BP = RY * BX;
     const int nx = L.nx, ny = L.ny, nz = L.nz;
-    const int px = threadIdx.x, py = threadIdx.y, tid = py * PX + px, nth = PX * RY;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * kz;
-    const int k1 = min(k0 + kz, nz);
+    const int px = threadIdx.x, py = threadIdx.y;
+    const int i0 = blockIdx.x * COL_TX, j0 = blockIdx.y * TY;
     const int ia = i0 - 1 + 2 * px, j = j0 - 1 + py;
     const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
     const bool row_in = j >= 0 && j < ny;
-    const bool in_a = row_in && ia >= 0 && ia < nx, in_b = row_in && ia + 1 >= 0 && ia + 1 < nx;
+    const bool in_a = row_in && ia >= 0 && ia < nx, in_b = row_in && ia + 1 < nx;
     const bool row_int = j >= 1 && j <= ny - 2;
     const bool int_a = row_int && ia >= 1 && ia <= nx - 2, int_b = row_int && ia + 1 >= 1 && ia + 1 <= nx - 2;
     const bool row_tile = py >= 1 && py <= TY;
-    const bool tile_a = row_tile && px >= 1, tile_b = row_tile && px <= PX - 2;
+    const bool wa = row_tile && px >= 1 && in_a, wb = row_tile && px <= COL_PX - 2 && in_b;
+    const bool ua_ok = in_a && !zero_in, ub_ok = in_b && !zero_in;
     const int oA = (py + 1) * AX + 2 * px + 1, oB = py * BX + 2 * px;
-
-    for (int e = tid; e < kz + 4; e += nth) {
-        const int qc = min(max(k0 - 2 + e, 0), nz - 1);
-        ZC[3 * e] = L.ax[2].cm[qc];
-        ZC[3 * e + 1] = L.ax[2].cp[qc];
-        ZC[3 * e + 2] = L.ax[2].dg[qc];
-    }
+    // per-thread offset of node a within a plane (ia may be -1: node b = rowoff + 1 is then
+    // column 0; node a itself is never accessed when it lies outside the grid)
+    const long long rowoff = (long long)min(max(j, 0), ny - 1) * nx + ia;
     const int ca = min(max(ia, 0), nx - 1), cb = min(max(ia + 1, 0), nx - 1), cj = min(max(j, 0), ny - 1);
     const T cmxa = L.ax[0].cm[ca], cpxa = L.ax[0].cp[ca], cmxb = L.ax[0].cm[cb], cpxb = L.ax[0].cp[cb];
     const T dga = L.ax[0].dg[ca], dgb = L.ax[0].dg[cb];
     const T cmy = L.ax[1].cm[cj], cpy = L.ax[1].cp[cj], dgy = L.ax[1].dg[cj];
+    // halo roles
+    const bool hl = px == 0 && row_in && i0 - 2 >= 0, hr = px == COL_PX - 1 && row_in && i0 + COL_TX + 1 < nx;
+    const bool hd = py == 0 && j0 - 2 >= 0, hu = py == RY - 1 && j0 + TY + 1 < ny;
+    const bool hd_a = hd && ia >= 0 && ia < nx, hd_b = hd && ia + 1 < nx;
+    const bool hu_a = hu && ia >= 0 && ia < nx, hu_b = hu && ia + 1 < nx;
+    const size_t hoff_l = (size_t)min(max(j, 0), ny - 1) * sy + (size_t)max(i0 - 2, 0);
+    const size_t hoff_r = (size_t)min(max(j, 0), ny - 1) * sy + (size_t)min(i0 + COL_TX + 1, nx - 1);
+    const long long hoff_d = (long long)max(j0 - 2, 0) * nx + ia;
+    const long long hoff_u = (long long)min(j0 + TY + 1, ny - 1) * nx + ia;
 
-    // halo of plane q into its A slot: the edge threads' nodes one step outside the block
-    auto halo = [&](int q) {
+    auto halo = [&](T* A, int q) {
         if (q < 0 || q >= nz) return;
-        T* A = SA + ((q % CWA) + CWA) % CWA * AP;
-        const size_t base = (size_t)q * sz;
-        auto put = [&](int o, int jj, int ii) {
-            if (jj < 0 || jj >= ny || ii < 0 || ii >= nx) return;
+        const long long off = (long long)q * (long long)sz;
+        auto put = [&](bool ok, int o, long long g) {
+            if (!ok) return;
             if (zero_in)
                 A[o] = T(0);
             else
-                cp_async(A + o, uin + base + (size_t)jj * sy + ii);
+                cp_async(A + o, uin + off + g);
         };
-        if (px == 0) put((py + 1) * AX, j, i0 - 2);
-        if (px == PX - 1) put((py + 1) * AX + AX - 1, j, i0 + TX + 1);
-        if (py == 0) {
-            put(2 * px + 1, j0 - 2, ia);
-            put(2 * px + 2, j0 - 2, ia + 1);
-        }
-        if (py == RY - 1) {
-            put((AY - 1) * AX + 2 * px + 1, j0 + TY + 1, ia);
-            put((AY - 1) * AX + 2 * px + 2, j0 + TY + 1, ia + 1);
-        }
-    };
-    auto ldu = [&](bool ok, int q, int ii) -> T {
-        return (ok && !zero_in && q >= 0 && q < nz) ? uin[(size_t)q * sz + (size_t)j * sy + ii] : T(0);
-    };
-    auto ldb = [&](bool ok, int q, int ii) -> T {
-        return (ok && q >= 1 && q <= nz - 2) ? b[(size_t)q * sz + (size_t)j * sy + ii] : T(0);
-    };
-    auto ldi = [&](bool ok, int q, int ii) -> T {
-        if constexpr (sizeof(T) == 8)
-            return (ok && q >= 1 && q <= nz - 2) ? L.inv_diag[(size_t)q * sz + (size_t)j * sy + ii] : T(0);
-        return T(0);
+        put(hl, (py + 1) * AX, (long long)hoff_l);
+        put(hr, (py + 1) * AX + AX - 1, (long long)hoff_r);
+        put(hd_a, 2 * px + 1, hoff_d);
+        put(hd_b, 2 * px + 2, hoff_d + 1);
+        put(hu_a, (AY - 1) * AX + 2 * px + 1, hoff_u);
+        put(hu_b, (AY - 1) * AX + 2 * px + 2, hoff_u + 1);
     };
 
-    // ring slot r holds plane p - 3 + ((r - s) mod CR) at unrolled step s
     T ua[CR], ub[CR], ba[CR], bb[CR], va[CR], vb[CR];
 #pragma unroll
-    for (int r = 0; r < CR; r++) {
-        ua[r] = ub[r] = ba[r] = bb[r] = va[r] = vb[r] = T(0);
-    }
-    // prologue: planes k0-3 .. k0+CD-1 (ring slots 0 .. CR-2); halo of planes k0-1 .. k0+CD-1
+    for (int r = 0; r < CR; r++) ua[r] = ub[r] = ba[r] = bb[r] = va[r] = vb[r] = T(0);
+    auto load = [&](int r, int q) {
+        const bool qu = q >= 0 && q < nz, qb = q >= 1 && q <= nz - 2;
+        const long long off = (long long)q * (long long)sz + rowoff;
+        ua[r] = (ua_ok && qu) ? uin[off] : T(0);
+        ub[r] = (ub_ok && qu) ? uin[off + 1] : T(0);
+        ba[r] = (int_a && qb) ? b[off] : T(0);
+        bb[r] = (int_b && qb) ? b[off + 1] : T(0);
+        if constexpr (sizeof(T) == 8) {
+            va[r] = (int_a && qb) ? L.inv_diag[off] : T(0);
+            vb[r] = (int_b && qb) ? L.inv_diag[off + 1] : T(0);
+        }
+    };
+    // prologue: ring slot r <-> plane k0-3+r at step p = k0; A slot of plane q = (q-k0+3) mod CR
 #pragma unroll
-    for (int r = 0; r < CR - 1; r++) {
-        const int q = k0 - 3 + r;
-        ua[r] = ldu(in_a, q, ia);
-        ub[r] = ldu(in_b, q, ia + 1);
-        ba[r] = ldb(int_a, q, ia);
-        bb[r] = ldb(int_b, q, ia + 1);
-        va[r] = ldi(int_a, q, ia);
-        vb[r] = ldi(int_b, q, ia + 1);
-    }
-    for (int q = k0 - 1; q <= k0 + CD - 1; q++) {
-        halo(q);
+    for (int r = 0; r < CR - 1; r++) load(r, k0 - 3 + r);
+    for (int q = k0 - 1; q <= k0 + 1; q++) {
+        halo(SA + (q - k0 + 3) * AP, q);
         cp_async_commit();
     }
 
@@ -249,90 +237,120 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512)
         for (int s = 0; s < CR; s++) {
             const int p = p0 + s;
             if (p > k1 + 1) break;
-            // ring slots of planes p-3 .. p+CD at this unrolled step
-            const int r3 = (s + 0) % CR, r2 = (s + 1) % CR, r1 = (s + 2) % CR, r0 = (s + 3) % CR,
-                      rn = (s + CR - 1) % CR;
-            // loads of plane p + CD
-            ua[rn] = ldu(in_a, p + CD, ia);
-            ub[rn] = ldu(in_b, p + CD, ia + 1);
-            ba[rn] = ldb(int_a, p + CD, ia);
-            bb[rn] = ldb(int_b, p + CD, ia + 1);
-            va[rn] = ldi(int_a, p + CD, ia);
-            vb[rn] = ldi(int_b, p + CD, ia + 1);
-            halo(p + CD);
+            const int r3 = s % CR, r2 = (s + 1) % CR, r1 = (s + 2) % CR, r0 = (s + 3) % CR, rn = (s + 5) % CR;
+            load(rn, p + 2);
+            halo(SA + ((s + 5) % CR) * AP, p + 2);
             cp_async_commit();
-            // publish plane p-1 (old values; the halo is already on its way into the slot)
-            T* A = SA + (((p - 1) % CWA) + CWA) % CWA * AP;
+            T* A = SA + ((s + 2) % CR) * AP;    // plane p-1
             A[oA] = ua[r1];
             A[oA + 1] = ub[r1];
-            asm volatile("cp.async.wait_group %0;\n" ::"n"(CD + 1) : "memory");
+            asm volatile("cp.async.wait_group 3;\n" ::: "memory");
             __syncthreads();
-            const T* Bp = SB + ((p - 1) & 1) * RY * BX;
-            T* Bn = SB + (p & 1) * RY * BX;
-            // red node of plane q = p - 1
+            const T* Bp = SB + ((s + 1) & 1) * BP;
+            T* Bn = SB + (s & 1) * BP;
+            // red node of plane p-1: node a when RB + s + 1 is even
+            const bool red_a = ((RB + s + 1) & 1) == 0;
             const int q = p - 1;
-            if (q >= max(1, k0 - 1) && q <= min(nz - 2, k1)) {
+            if (q >= max(1, k0 - 1) && q <= min(nz - 2, k1) && (red_a ? int_a : int_b)) {
                 const T* zc = ZC + 3 * (q - k0 + 2);
-                const bool red_a = ((ia + j + q) & 1) == first;
-                if (red_a ? int_a : int_b) {
-                    const int o = red_a ? oA : oA + 1;
-                    const T xm = red_a ? A[o - 1] : ua[r1];
-                    const T xp = red_a ? ub[r1] : A[o + 1];
-                    T t = (red_a ? cmxa : cmxb) * xm;
-                    t = fma(red_a ? cpxa : cpxb, xp, t);
-                    t = fma(cmy, A[o - AX], t);
-                    t = fma(cpy, A[o + AX], t);
-                    t = fma(zc[0], red_a ? ua[r2] : ub[r2], t);
-                    t = fma(zc[1], red_a ? ua[r0] : ub[r0], t);
-                    const T acc = (red_a ? ba[r1] : bb[r1]) - t;
-                    T v;
+                T t;
+                if (red_a) {
+                    t = cmxa * A[oA - 1];
+                    t = fma(cpxa, ub[r1], t);
+                    t = fma(cmy, A[oA - AX], t);
+                    t = fma(cpy, A[oA + AX], t);
+                    t = fma(zc[0], ua[r2], t);
+                    t = fma(zc[1], ua[r0], t);
+                    const T acc = ba[r1] - t;
                     if constexpr (sizeof(T) == 8)
-                        v = acc * (red_a ? va[r1] : vb[r1]);
+                        ua[r1] = acc * va[r1];
                     else
-                        v = acc / (-((red_a ? dga : dgb) + dgy + zc[2]));
-                    if (red_a)
-                        ua[r1] = v;
+                        ua[r1] = acc / (-(dga + dgy + zc[2]));
+                } else {
+                    t = cmxb * ua[r1];
+                    t = fma(cpxb, A[oA + 2], t);
+                    t = fma(cmy, A[oA + 1 - AX], t);
+                    t = fma(cpy, A[oA + 1 + AX], t);
+                    t = fma(zc[0], ub[r2], t);
+                    t = fma(zc[1], ub[r0], t);
+                    const T acc = bb[r1] - t;
+                    if constexpr (sizeof(T) == 8)
+                        ub[r1] = acc * vb[r1];
                     else
-                        ub[r1] = v;
+                        ub[r1] = acc / (-(dgb + dgy + zc[2]));
                 }
             }
-            // black node of plane q2 = p - 2 (tile nodes only)
+            // black node of plane p-2 (tile nodes only): node a when RB + s is odd
+            const bool blk_a = ((RB + s) & 1) == 1;
             const int q2 = p - 2;
-            if (q2 >= max(1, k0) && q2 <= min(nz - 2, k1 - 1)) {
+            if (q2 >= max(1, k0) && q2 <= min(nz - 2, k1 - 1) && (blk_a ? (int_a && wa) : (int_b && wb))) {
                 const T* zc = ZC + 3 * (q2 - k0 + 2);
-                const bool blk_a = ((ia + j + q2) & 1) != first;
-                if (blk_a ? (int_a && tile_a) : (int_b && tile_b)) {
-                    const int o = blk_a ? oB : oB + 1;
-                    const T xm = blk_a ? Bp[o - 1] : ua[r2];
-                    const T xp = blk_a ? ub[r2] : Bp[o + 1];
-                    T t = (blk_a ? cmxa : cmxb) * xm;
-                    t = fma(blk_a ? cpxa : cpxb, xp, t);
-                    t = fma(cmy, Bp[o - BX], t);
-                    t = fma(cpy, Bp[o + BX], t);
-                    t = fma(zc[0], blk_a ? ua[r3] : ub[r3], t);
-                    t = fma(zc[1], blk_a ? ua[r1] : ub[r1], t);
-                    const T acc = (blk_a ? ba[r2] : bb[r2]) - t;
-                    T v;
+                T t;
+                if (blk_a) {
+                    t = cmxa * Bp[oB - 1];
+                    t = fma(cpxa, ub[r2], t);
+                    t = fma(cmy, Bp[oB - BX], t);
+                    t = fma(cpy, Bp[oB + BX], t);
+                    t = fma(zc[0], ua[r3], t);
+                    t = fma(zc[1], ua[r1], t);
+                    const T acc = ba[r2] - t;
                     if constexpr (sizeof(T) == 8)
-                        v = acc * (blk_a ? va[r2] : vb[r2]);
+                        ua[r2] = acc * va[r2];
                     else
-                        v = acc / (-((blk_a ? dga : dgb) + dgy + zc[2]));
-                    if (blk_a)
-                        ua[r2] = v;
+                        ua[r2] = acc / (-(dga + dgy + zc[2]));
+                } else {
+                    t = cmxb * ua[r2];
+                    t = fma(cpxb, Bp[oB + 2], t);
+                    t = fma(cmy, Bp[oB + 1 - BX], t);
+                    t = fma(cpy, Bp[oB + 1 + BX], t);
+                    t = fma(zc[0], ub[r3], t);
+                    t = fma(zc[1], ub[r1], t);
+                    const T acc = bb[r2] - t;
+                    if constexpr (sizeof(T) == 8)
+                        ub[r2] = acc * vb[r2];
                     else
-                        ub[r2] = v;
+                        ub[r2] = acc / (-(dgb + dgy + zc[2]));
                 }
             }
             if (q2 >= k0 && q2 < k1) {
-                const size_t P = (size_t)q2 * sz + (size_t)j * sy + ia;
-                if (in_a && tile_a) uout[P] = ua[r2];
-                if (in_b && tile_b) uout[P + 1] = ub[r2];
+                const long long off = (long long)q2 * (long long)sz + rowoff;
+                if (wa) uout[off] = ua[r2];
+                if (wb) uout[off + 1] = ub[r2];
             }
-            // publish the red values of plane p-1 for the next step's black update
             Bn[oB] = ua[r1];
             Bn[oB + 1] = ub[r1];
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512)
+    k_rb_col(LevelT<T> L, const T* __restrict__ uin, T* __restrict__ uout, const T* __restrict__ b, int first,
+             int zero_in, int kz)
+{
+    extern __shared__ __align__(16) unsigned char col_smem[];
+    const int RY = blockDim.y, TY = RY - 2;
+    constexpr int AX = COL_TX + 4, BX = COL_TX + 2;
+    const int AY = TY + 4;
+    T* SA = reinterpret_cast<T*>(col_smem);   // [CR][AY][AX]
+    T* SB = SA + CR * AX * AY;                 // [2][RY][BX]
+    T* ZC = SB + 2 * RY * BX;                  // [kz + 4][3]: cm, cp, dg of planes k0-2 ..
+    const int nz = L.nz;
+    const int k0 = blockIdx.z * kz, k1 = min(k0 + kz, nz);
+    const int tid = threadIdx.y * COL_PX + threadIdx.x;
+    for (int e = tid; e < kz + 4; e += COL_PX * RY) {
+        const int qc = min(max(k0 - 2 + e, 0), nz - 1);
+        ZC[3 * e] = L.ax[2].cm[qc];
+        ZC[3 * e + 1] = L.ax[2].cp[qc];
+        ZC[3 * e + 2] = L.ax[2].dg[qc];
+    }
+    // colour pattern of the warp's pairs (uniform over the warp: one row, one parity of i)
+    const int j = blockIdx.y * TY - 1 + (int)threadIdx.y;
+    const int rb = ((blockIdx.x * COL_TX - 1 + j + k0) & 1) ^ (first & 1);
+    if (rb)
+        col_sweep<T, 1>(L, uin, uout, b, zero_in, k0, k1, SA, SB, ZC);
+    else
+        col_sweep<T, 0>(L, uin, uout, b, zero_in, k0, k1, SA, SB, ZC);
 }
 
 template <typename T, int NS>
@@ -349,13 +367,13 @@ void* col_kernel()
 
 }  // namespace
 
-// ns = 1 runs the column kernel (block (tx/2 + 1) x (ty + 2) threads); ns = 2 the z-slab
+// ns = 1 runs the column kernel (tx = 62; block 32 x (ty + 2) threads); ns = 2 the z-slab
 // window kernel (256 threads).
 size_t slab_smem_bytes(const SlabShape& sh, size_t elem)
 {
     if (sh.ns == 1) {
-        const size_t AX = sh.tx + 4, AY = sh.ty + 4, BX = sh.tx + 2, RY = sh.ty + 2;
-        return (CWA * AX * AY + 2 * RY * BX + 3 * ((size_t)sh.kz + 4)) * elem;
+        const size_t AX = COL_TX + 4, AY = sh.ty + 4, BX = COL_TX + 2, RY = sh.ty + 2;
+        return (CR * AX * AY + 2 * RY * BX + 3 * ((size_t)sh.kz + 4)) * elem;
     }
     const size_t H = 2 * (size_t)sh.ns;
     return (2 * (size_t)sh.ns + 3) * ((size_t)sh.tx + 2 * H) * ((size_t)sh.ty + 2 * H) * elem;
@@ -364,10 +382,16 @@ size_t slab_smem_bytes(const SlabShape& sh, size_t elem)
 bool slab_shape_ok(const SlabShape& sh, size_t elem)
 {
     if (sh.ns == 1)
-        return sh.tx >= 2 && sh.tx % 2 == 0 && sh.ty >= 1 && sh.kz >= 1 && sh.kz <= 4096 &&
-               (sh.tx / 2 + 1) * (sh.ty + 2) <= (elem == 8 ? 256 : 512) && slab_smem_bytes(sh, elem) <= SLAB_MAX_SMEM;
+        return sh.tx == COL_TX && sh.ty >= 1 && sh.kz >= 1 && sh.kz <= 4096 && COL_PX * (sh.ty + 2) <= (elem == 8 ? 256 : 512) &&
+               slab_smem_bytes(sh, elem) <= SLAB_MAX_SMEM;
     return sh.ns == 2 && sh.tx >= 2 && sh.ty >= 1 && sh.kz >= 1 && sh.tx <= 512 && sh.ty <= 512 &&
            slab_smem_bytes(sh, elem) <= SLAB_MAX_SMEM;
+}
+
+SlabShape slab_default_shape(int ns, size_t elem)
+{
+    if (ns == 1) return SlabShape{COL_TX, elem == 8 ? 6 : 14, 32, 1};
+    return SlabShape{64, 16, 32, 2};
 }
 
 void init_slab_attributes()
@@ -387,7 +411,7 @@ cudaError_t launch_rb_slab(const LevelT<T>& L, const T* uin, T* uout, const T* b
                     (unsigned)((L.nz + sh.kz - 1) / sh.kz));
     const size_t smem = slab_smem_bytes(sh, sizeof(T));
     if (sh.ns == 1)
-        k_rb_col<T><<<grid, dim3(sh.tx / 2 + 1, sh.ty + 2), smem, s>>>(L, uin, uout, b, first & 1, zero_in, sh.kz);
+        k_rb_col<T><<<grid, dim3(COL_PX, sh.ty + 2), smem, s>>>(L, uin, uout, b, first & 1, zero_in, sh.kz);
     else
         k_rb_slab<T, 2><<<grid, SLAB_NT, smem, s>>>(L, uin, uout, b, first & 1, zero_in, sh.tx, sh.ty, sh.kz);
     return cudaGetLastError();

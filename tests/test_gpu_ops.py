@@ -71,9 +71,9 @@ def test_red_black_sweep_fp32(orc):
     assert np.abs(got - ref).max() < 2e-5 * np.abs(ref).max()
 
 
-SLAB_CASES = [((33, 33, 33), 1, 0, (32, 8, 16)), ((65, 33, 49), 2, 0, (16, 4, 8)), ((65, 33, 49), 2, 1, (64, 16, 16)),
-              ((97, 97, 97), 2, 1, (40, 6, 11)), ((37, 7, 5), 1, 1, (2, 2, 1)), ((35, 9, 33), 1, 0, (62, 6, 16)), ((5, 5, 5), 2, 0, (2, 1, 1)),
-              ((3, 3, 3), 1, 0, (8, 8, 8))]
+SLAB_CASES = [((33, 33, 33), 1, 0, (62, 6, 16)), ((65, 33, 49), 2, 0, (16, 4, 8)), ((65, 33, 49), 2, 1, (64, 16, 16)),
+              ((97, 97, 97), 2, 1, (40, 6, 11)), ((37, 7, 5), 1, 1, (62, 1, 1)), ((135, 9, 33), 1, 0, (62, 6, 16)), ((5, 5, 5), 2, 0, (2, 1, 1)),
+              ((3, 3, 3), 1, 0, (62, 4, 8)), ((65, 65, 17), 1, 1, (62, 2, 5))]
 
 
 def _sweeps_ref(orc, x, y, z, u, b, ns, first):
@@ -115,7 +115,7 @@ def test_slab_smoother_fp32(orc):
     u32 = torch.as_tensor(u.astype(np.float32)).cuda()
     b32 = torch.as_tensor(b.astype(np.float32)).cuda()
     outs = []
-    for ns, tile in ((2, (32, 8, 16)), (2, (24, 5, 7)), (1, (30, 14, 8))):
+    for ns, tile in ((2, (32, 8, 16)), (2, (24, 5, 7)), (1, (62, 14, 8))):
         o = torch.empty_like(u32)
         B.lasto_op_smooth_slab(dev(x), dev(y), dev(z), u32, o, b32, sweeps=2, ns=ns, first=0, tile=tile)
         outs.append(o)
