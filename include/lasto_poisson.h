@@ -117,10 +117,30 @@ typedef struct lasto_stats {
     double rel_resid;   /* final ||b - A u|| / ||b_eff|| (true residual, recomputed in FP64) */
     double bnorm;       /* ||b_eff|| */
     int outer;          /* FP64 defect-correction steps (MIXED with CG), else 0 */
-    int reserved;
+    int guess;          /* 1: the solve started from the learned guess (lasto_poisson_set_guess) */
 } lasto_stats;
 
 typedef struct lasto_poisson lasto_poisson;   /* opaque; owns workspace, plans and CUDA graphs */
+
+/* Learned initial guess.  The paper has no counterpart: it solves every SCF step from
+ * scratch.  A small 3-D U-Net (four levels, 16-32-64-64 channels, 3x3x3 convolutions with
+ * BF16 tensor-core products and FP32 accumulation) maps the right-hand side restricted to a
+ * 33^3 subgrid of the mesh (every m-th node, m = (n - 1) / 32), the subgrid's Dirichlet
+ * faces and its local mesh size to the subgrid potential; carried up the multigrid
+ * hierarchy by trilinear prolongation it is the first iterate.  The iteration then runs to
+ * the same tolerance, so the network changes how many iterations a solve takes, never what
+ * it converges to.
+ * params: host FP32, the 15 convolutions in the order e1a e1b e2a e2b e3a e3b bta btb d3a d3b
+ * d2a d2b d1a d1b out (cin->cout: 16-16, 16-16, 16-32, 32-32, 32-64, 64-64, 64-64, 64-64,
+ * 128-64, 64-64, 96-32, 32-32, 48-16, 16-16, 16-16), each as weights [27][cin][cout]
+ * (tap = (dz+1)*9 + (dy+1)*3 + (dx+1)) followed by its bias [cout];
+ * n_params = lasto_guess_param_count().  scales = {s0, s1, h_ref, out}: input channel 0 is
+ * b h^2 s0, channel 1 the face value s1, channel 2 log(h / h_ref); the potential is the
+ * prediction / out.  Copied to the device (synchronously); later solves use the network for
+ * every cluster whose axes all have 32 m + 1 nodes, when the caller passes no guess.
+ * params == NULL removes the network.  INVALID_ARG for a wrong count or a zero scale. */
+size_t lasto_guess_param_count(void);
+int lasto_poisson_set_guess(lasto_poisson* h, const float* params, size_t n_params, const double scales[4]);
 
 /* Allocates the workspace for cfg (device memory sized by n_max, max_atoms,
  * max_batch).  *out is NULL on failure.  Errors: INVALID_ARG, CUDA, NO_MEMORY. */

@@ -40,7 +40,7 @@ class lasto_cluster(ctypes.Structure):
 
 class lasto_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_resid", ctypes.c_double),
-                ("bnorm", ctypes.c_double), ("outer", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("bnorm", ctypes.c_double), ("outer", ctypes.c_int), ("guess", ctypes.c_int)]
 
 
 EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve", "lasto_poisson_destroy",
@@ -48,11 +48,15 @@ EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve"
            "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
            "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
-           "lasto_op_project", "lasto_nn_conv3d_fwd", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
+           "lasto_op_project", "lasto_guess_param_count", "lasto_poisson_set_guess", "lasto_nn_conv3d_fwd", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
            "lasto_nn_relu_grad", "lasto_nn_to_bf16", "lasto_nn_copy_channels", "lasto_nn_down", "lasto_nn_up",
            "lasto_nn_mse", "lasto_nn_adam", "lasto_nn_guess_features", "lasto_nn_guess_grid"]
 
 _lib = None
+
+# the learned guess network's convolutions, in the order of lasto_poisson_set_guess's parameters
+GUESS_LAYERS = ["e1a", "e1b", "e2a", "e2b", "e3a", "e3b", "bta", "btb", "d3a", "d3b", "d2a", "d2b", "d1a", "d1b", "out"]
+GUESS_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_pd_33.npz")
 
 
 def _declare(L):
@@ -66,6 +70,8 @@ def _declare(L):
         "lasto_poisson_destroy": (None, [vp]),
         "lasto_poisson_last_error": (ctypes.c_char_p, [vp]),
         "lasto_poisson_kernel_counts": (i, [vp, ip, ip, ip]),
+        "lasto_guess_param_count": (ctypes.c_size_t, []),
+        "lasto_poisson_set_guess": (i, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t, ctypes.POINTER(d)]),
         "lasto_mesh_axis": (i, [i, d, d, d, d, d, vp, vp, vp]),
         "lasto_op_sphere_params": (i, [clp, vp, vp, vp, vp, vp, vp]),
         "lasto_op_deposit": (i, [clp, i, vp, vp, vp, vp]),
@@ -228,6 +234,27 @@ class Poisson:
 
     def last_error(self) -> str:
         return load().lasto_poisson_last_error(self.h).decode()
+
+    def set_guess(self, weights=GUESS_WEIGHTS):
+        """Load the learned initial-guess network (an .npz of per-layer weights [27][cin][cout],
+        biases and the JSON input/output scales); None removes it."""
+        L = load()
+        if weights is None:
+            _check(L.lasto_poisson_set_guess(self.h, None, 0, None), "lasto_poisson_set_guess")
+            return
+        import json
+        z = np.load(weights)
+        flat = np.concatenate([np.concatenate([np.asarray(z[k + ".w"], dtype=np.float32).ravel(),
+                                               np.asarray(z[k + ".b"], dtype=np.float32).ravel()])
+                               for k in GUESS_LAYERS])
+        if flat.size != L.lasto_guess_param_count():
+            raise ValueError(f"guess network: {flat.size} parameters, expected {L.lasto_guess_param_count()}")
+        sc = json.loads(str(z["scales"]))
+        scales = (ctypes.c_double * 4)(sc["s0"], sc["s1"], sc["h_ref"], sc["out"])
+        flat = np.ascontiguousarray(flat)
+        st = L.lasto_poisson_set_guess(self.h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), flat.size, scales)
+        if st != LASTO_OK:
+            raise RuntimeError(f"lasto_poisson_set_guess failed: {STATUS_NAMES.get(st, st)}: {self.last_error()}")
 
     def solve(self, clusters, v_lm, potential=None, guess=None, stats=True, stream=None):
         """Enqueue one solve of the DeviceClusters; returns the host stats array (valid after sync)."""

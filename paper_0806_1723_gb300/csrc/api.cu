@@ -68,6 +68,12 @@ struct ClusterPlan {
     CoarseEig* eig = nullptr;
     int* status = nullptr;              // [0] status, [1] reduction ticket counter
     lasto_stats* stats_dev = nullptr;
+    // learned guess: the 33^3 subgrid (every gm-th node) and the level gl it is resampled from
+    double *gax[3] = {nullptr, nullptr, nullptr};
+    double *bG = nullptr, *fG = nullptr, *uG = nullptr;
+    int gm[3] = {0, 0, 0};
+    int gl = -1;      // -1: no learned guess for this cluster
+    int gslot = -1;   // its grid in the network's batch
     Red red(int op, cudaGraphConditionalHandle cond = 0, int use_cond = 0) const
     {
         return Red{part, reinterpret_cast<unsigned int*>(status + 1), ctl, op, cond, use_cond};
@@ -101,6 +107,8 @@ size_t cluster_bytes(const int n[3], int n_atoms)
     c.take<CoarseEig>(1);
     c.take<int>(4);
     c.take<lasto_stats>(1);
+    for (int d = 0; d < 3; d++) c.take<double>(GUESS_N);
+    for (int t = 0; t < 3; t++) c.take<double>((size_t)GUESS_N * GUESS_N * GUESS_N);
     return c.off;
 }
 
@@ -144,6 +152,10 @@ bool carve_cluster(Carver& c, const int n[3], int n_atoms, ClusterPlan& P)
     P.eig = c.take<CoarseEig>(1);
     P.status = c.take<int>(4);
     P.stats_dev = c.take<lasto_stats>(1);
+    for (int d = 0; d < 3; d++) P.gax[d] = c.take<double>(GUESS_N);
+    P.bG = c.take<double>((size_t)GUESS_N * GUESS_N * GUESS_N);
+    P.fG = c.take<double>((size_t)GUESS_N * GUESS_N * GUESS_N);
+    P.uG = c.take<double>((size_t)GUESS_N * GUESS_N * GUESS_N);
     return c.ok;
 }
 
@@ -167,9 +179,11 @@ __global__ void k_copy_interior(const double* __restrict__ src, double* __restri
     dst[P] = src[P];
 }
 
-__global__ void k_write_stats(const Ctl* __restrict__ ctl, const int* __restrict__ status, lasto_stats* out)
+__global__ void k_write_stats(const Ctl* __restrict__ ctl, const int* __restrict__ status, int guess,
+                              lasto_stats* out)
 {
     lasto_stats s;
+    s.guess = guess;
     s.cycles = ctl->iter;
     s.rel_resid = ctl->true_rel;
     s.bnorm = ctl->bnorm;
@@ -204,6 +218,9 @@ struct lasto_poisson {
     int stats_count = 0;
     int kernels_fixed = -1, kernels_iter = -1, kernels_outer = 0;
     std::vector<cudaGraph_t> bodies, outer_bodies;
+    GuessNet* net = nullptr;             // learned initial guess (optional)
+    std::vector<cudaEvent_t> eg;         // per slot: features written
+    cudaEvent_t ev_net = nullptr;        // network forward done
 };
 
 namespace {
@@ -370,6 +387,84 @@ int enqueue_prologue(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, 
     return LASTO_OK;
 }
 
+// ---------------------------------------------------------------- learned guess stages
+// Which clusters get the learned guess: every axis n = 32 m + 1 (the 33^3 subgrid takes every
+// m-th node), a network loaded and no caller guess.  gl = the deepest level with at least 33
+// nodes per axis (the subgrid itself for 33, 65, 129, 257, ... nodes).
+int plan_guesses(lasto_poisson* h, const lasto_cluster* cls, int nc, const double* guess)
+{
+    int k = 0;
+    for (int c = 0; c < nc; c++) {
+        ClusterPlan& P = h->plans[c];
+        P.gl = -1;
+        P.gslot = -1;
+        if (!h->net || guess) continue;
+        bool ok = true;
+        for (int d = 0; d < 3; d++) {
+            const int n = cls[c].n[d];
+            ok = ok && n >= GUESS_N && (n - 1) % (GUESS_N - 1) == 0;
+            P.gm[d] = (n - 1) / (GUESS_N - 1);
+        }
+        if (!ok || k >= guess_net_capacity(h->net)) continue;
+        int gl = 0;
+        while (gl + 1 < P.L && P.lv[gl + 1].n[0] >= GUESS_N && P.lv[gl + 1].n[1] >= GUESS_N &&
+               P.lv[gl + 1].n[2] >= GUESS_N)
+            gl++;
+        P.gl = gl;
+        P.gslot = k++;
+    }
+    return k;
+}
+
+// network input of one cluster (after its right-hand side and mesh tables)
+int enqueue_guess_in(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, cudaStream_t s)
+{
+    if (P.gl < 0) return LASTO_OK;
+    const double* ax[3] = {cl.x, cl.y, cl.z};
+    const int G[3] = {GUESS_N, GUESS_N, GUESS_N};
+    for (int d = 0; d < 3; d++) TRY(launch_axis_stride(ax[d], P.gm[d], GUESS_N, P.gax[d], s));
+    for (int l = 0; l < P.gl; l++)
+        TRY(launch_restrict<double>(P.lv[l].view64(), P.lv[l + 1].view64(), P.lv[l].b, P.lv[l + 1].b, s));
+    const LevelStore& S = P.lv[P.gl];
+    TRY(launch_resample(S.n, S.ax[0].c, S.ax[1].c, S.ax[2].c, S.b, G, P.gax[0], P.gax[1], P.gax[2], P.bG, 0, s));
+    TRY(cudaMemsetAsync(P.fG, 0, sizeof(double) * GUESS_N * GUESS_N * GUESS_N, s));
+    TRY(launch_boundary_fill(G, P.gax[0], P.gax[1], P.gax[2], cl.centre[0], cl.centre[1], cl.centre[2], P.Q, P.fG, s));
+    const float* sc = guess_net_scales(h->net);
+    if (lasto_nn_guess_features(G, P.bG, P.fG, P.gax[0], P.gax[1], P.gax[2], sc[0], sc[1], sc[2],
+                                guess_net_features(h->net, P.gslot), s) != LASTO_OK)
+        return fail(h, LASTO_ERR_CUDA, "guess features");
+    return LASTO_OK;
+}
+
+// prediction -> first iterate on the fine grid (interior; faces are already set)
+int enqueue_guess_out(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, cudaStream_t s)
+{
+    if (P.gl < 0) return LASTO_OK;
+    const int G[3] = {GUESS_N, GUESS_N, GUESS_N};
+    const float* sc = guess_net_scales(h->net);
+    if (lasto_nn_guess_grid(G, guess_net_prediction(h->net, P.gslot), 16, sc[3], P.fG, P.uG, s) != LASTO_OK)
+        return fail(h, LASTO_ERR_CUDA, "guess grid");
+    const int gl = P.gl;
+    LevelStore& S = P.lv[gl];
+    double* tgt = gl == 0 ? P.lv[0].u : S.u;
+    if (gl > 0) {
+        TRY(cudaMemsetAsync(tgt, 0, sizeof(double) * S.N(), s));
+        TRY(launch_boundary_fill(S.n, S.ax[0].c, S.ax[1].c, S.ax[2].c, cl.centre[0], cl.centre[1], cl.centre[2], P.Q,
+                                 tgt, s));
+    }
+    TRY(launch_resample(G, P.gax[0], P.gax[1], P.gax[2], P.uG, S.n, S.ax[0].c, S.ax[1].c, S.ax[2].c, tgt, 1, s));
+    for (int l = gl - 1; l >= 0; l--) {
+        LevelStore& Fl = P.lv[l];
+        if (l > 0) {
+            TRY(cudaMemsetAsync(Fl.u, 0, sizeof(double) * Fl.N(), s));
+            TRY(launch_boundary_fill(Fl.n, Fl.ax[0].c, Fl.ax[1].c, Fl.ax[2].c, cl.centre[0], cl.centre[1],
+                                     cl.centre[2], P.Q, Fl.u, s));
+        }
+        TRY(launch_prolong_add<double>(Fl.view64(), P.lv[l + 1].view64(), P.lv[l + 1].u, Fl.u, s));
+    }
+    return LASTO_OK;
+}
+
 // The mixed form with CG runs as defect correction: FP64 residual and correction
 // accumulation outside, FP32 multigrid-preconditioned CG inside.
 bool is_defect_correction(const lasto_poisson* h)
@@ -461,7 +556,7 @@ int enqueue_finish(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, do
     TRY(launch_resid_norm(V, F.u, F.b, nullptr, nullptr, P.red(FIN_TRUE), s));
     TRY(launch_project(cl.n, cl.x, cl.y, cl.z, F.u, cl.n_atoms, cl.pos, cl.R, h->quad, h->nq, vlm, P.status, s));
     if (potential) TRY(cudaMemcpyAsync(potential, F.u, sizeof(double) * F.N(), cudaMemcpyDeviceToDevice, s));
-    k_write_stats<<<1, 1, 0, s>>>(P.ctl, P.status, P.stats_dev);
+    k_write_stats<<<1, 1, 0, s>>>(P.ctl, P.status, P.gl >= 0 ? 1 : 0, P.stats_dev);
     TRY(cudaGetLastError());
     return LASTO_OK;
 }
@@ -528,15 +623,40 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
     int st = LASTO_OK;
     size_t atom_off = 0, grid_off = 0;
     // every cluster is an independent branch of the graph: small clusters' latency-bound
-    // kernels run side by side instead of one after another
+    // kernels run side by side instead of one after another.  With the learned guess the
+    // branches join once, after every right-hand side, for one batched network pass.
+    const int nguess = plan_guesses(h, cls, nc, guess);
     if (cudaEventRecord(h->ev_origin, s) != cudaSuccess) st = LASTO_ERR_CUDA;
+    for (int c = 0; c < nc && st == LASTO_OK; c++) {
+        ClusterPlan& P = h->plans[c];
+        cudaStream_t bsc = h->bs[c];
+        cudaError_t e = cudaStreamWaitEvent(bsc, h->ev_origin, 0);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamWaitEvent(origin)"); break; }
+        if ((st = enqueue_prologue(h, P, cls[c], guess ? guess + grid_off : nullptr, bsc, c))) break;
+        grid_off += (size_t)cls[c].n[0] * cls[c].n[1] * cls[c].n[2];
+        if (nguess > 0) {
+            if ((st = enqueue_guess_in(h, P, cls[c], bsc))) break;
+            e = cudaEventRecord(h->eg[c], bsc);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->eg[c], 0);
+            if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "guess join"); break; }
+        }
+    }
+    if (st == LASTO_OK && nguess > 0) {
+        st = guess_net_forward(h->net, nguess, s);
+        if (st) fail(h, st, "guess network forward");
+        else if (cudaEventRecord(h->ev_net, s) != cudaSuccess) st = fail(h, LASTO_ERR_CUDA, "guess fork");
+    }
+    grid_off = 0;
     for (int c = 0; c < nc && st == LASTO_OK; c++) {
         ClusterPlan& P = h->plans[c];
         const lasto_cluster& cl = cls[c];
         cudaStream_t bsc = h->bs[c];
-        cudaError_t e = cudaStreamWaitEvent(bsc, h->ev_origin, 0);
-        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "cudaStreamWaitEvent(origin)"); break; }
-        if ((st = enqueue_prologue(h, P, cl, guess ? guess + grid_off : nullptr, bsc, c))) break;
+        cudaError_t e;
+        if (nguess > 0) {
+            e = cudaStreamWaitEvent(bsc, h->ev_net, 0);
+            if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "guess fork"); break; }
+            if ((st = enqueue_guess_out(h, P, cl, bsc))) break;
+        }
         // conditional WHILE node(s) for the iteration
         cudaGraphConditionalHandle cond;
         if ((st = new_handle(h, bsc, &cond))) break;
@@ -647,11 +767,23 @@ static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
         if (!carve_cluster(cv, cls[c].n, cls[c].n_atoms, h->plans[c]))
             return fail(h, LASTO_ERR_NO_MEMORY, "workspace too small for this batch");
     size_t atom_off = 0, grid_off = 0;
+    const int nguess = plan_guesses(h, cls, nc, guess);
+    for (int c = 0; c < nc; c++) {
+        int st;
+        if ((st = enqueue_prologue(h, h->plans[c], cls[c], guess ? guess + grid_off : nullptr, s, 0))) return st;
+        if ((st = enqueue_guess_in(h, h->plans[c], cls[c], s))) return st;
+        grid_off += (size_t)cls[c].n[0] * cls[c].n[1] * cls[c].n[2];
+    }
+    if (nguess > 0) {
+        const int st = guess_net_forward(h->net, nguess, s);
+        if (st) return fail(h, st, "guess network forward");
+    }
+    grid_off = 0;
     for (int c = 0; c < nc; c++) {
         ClusterPlan& P = h->plans[c];
         const lasto_cluster& cl = cls[c];
         int st;
-        if ((st = enqueue_prologue(h, P, cl, guess ? guess + grid_off : nullptr, s, 0))) return st;
+        if ((st = enqueue_guess_out(h, P, cl, s))) return st;
         if ((st = enqueue_start(h, P, 0, 0, s))) return st;
         int done = 0;
         TRY(cudaMemcpyAsync(&done, &P.ctl->done, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -740,17 +872,20 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs2, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs3, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_origin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_net, cudaEventDisableTiming);
     h->bs.assign(cfg->max_batch, nullptr);
     h->ss.assign(cfg->max_batch, nullptr);
     h->ef.assign(cfg->max_batch, nullptr);
     h->ej.assign(cfg->max_batch, nullptr);
     h->ed.assign(cfg->max_batch, nullptr);
+    h->eg.assign(cfg->max_batch, nullptr);
     for (int c = 0; c < cfg->max_batch && e == cudaSuccess; c++) {
         e = cudaStreamCreateWithFlags(&h->bs[c], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ss[c], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ef[c], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ej[c], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ed[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->eg[c], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaMallocHost(&h->stats_pinned, sizeof(lasto_stats) * cfg->max_batch);
     if (e != cudaSuccess) {
@@ -779,6 +914,9 @@ void lasto_poisson_destroy(lasto_poisson* h)
     for (auto x : h->ef) if (x) cudaEventDestroy(x);
     for (auto x : h->ej) if (x) cudaEventDestroy(x);
     for (auto x : h->ed) if (x) cudaEventDestroy(x);
+    for (auto x : h->eg) if (x) cudaEventDestroy(x);
+    if (h->ev_net) cudaEventDestroy(h->ev_net);
+    guess_net_free(h->net);
     delete h;
 }
 
@@ -788,6 +926,23 @@ int lasto_poisson_kernel_counts(const lasto_poisson* h, int* fixed, int* per_ite
     *fixed = h->kernels_fixed;
     *per_iteration = h->kernels_iter;
     *per_outer = h->kernels_outer;
+    return LASTO_OK;
+}
+
+size_t lasto_guess_param_count(void) { return guess_param_count(); }
+
+int lasto_poisson_set_guess(lasto_poisson* h, const float* params, size_t n_params, const double scales[4])
+{
+    if (!h) return LASTO_ERR_INVALID_ARG;
+    if (h->cs) cudaStreamSynchronize(h->cs);
+    GuessNet* g = nullptr;
+    if (params) {
+        const int st = guess_net_create(params, n_params, scales, h->cfg.max_batch, &g, h->cs);
+        if (st) return fail(h, st, "guess network");
+    }
+    guess_net_free(h->net);
+    h->net = g;
+    h->key.clear();   // the cached graph was captured without (or with another) network
     return LASTO_OK;
 }
 

@@ -220,6 +220,23 @@ cudaError_t launch_multipoles(const int n[3], const double* x, const double* y, 
 cudaError_t launch_boundary_fill(const int n[3], const double* x, const double* y, const double* z, double cx,
                                  double cy, double cz, const double* Q, double* u, cudaStream_t s);
 
+// guess.cu: the learned initial guess (a 3-D U-Net on a 33^3 subgrid)
+constexpr int GUESS_N = 33;
+struct GuessNet;
+size_t guess_param_count();
+int guess_net_create(const float* params, size_t n_params, const double scales[4], int nbmax, GuessNet** out,
+                     cudaStream_t s);
+void guess_net_free(GuessNet* g);
+int guess_net_forward(GuessNet* g, int nb, cudaStream_t s);
+float* guess_net_features(GuessNet* g, int k);          // FP32 [33^3][16] input of grid k
+const float* guess_net_prediction(GuessNet* g, int k);  // FP32 [33^3][16], channel 0 = prediction
+int guess_net_capacity(const GuessNet* g);
+const float* guess_net_scales(const GuessNet* g);       // s0, s1, h_ref, out
+cudaError_t launch_axis_stride(const double* src, int m, int n, double* dst, cudaStream_t s);
+cudaError_t launch_resample(const int na[3], const double* ax, const double* ay, const double* az, const double* src,
+                            const int nb[3], const double* bx, const double* by, const double* bz, double* dst,
+                            int interior_only, cudaStream_t s);
+
 // project.cu
 void host_quadrature(int n_theta, int n_phi, double* table /* [nq][28]: unit xyz, w*S_lm */);
 cudaError_t launch_project(const int n[3], const double* x, const double* y, const double* z, const double* u,
