@@ -1,21 +1,25 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 LASTO interstitial Poisson step.
 
-Metric: converged Poisson solves per second (relative residual <= 1e-10), one
-step = one whole solve (density, pseudo-density deposit, boundary multipoles,
-faces, multigrid-preconditioned CG, sphere projection) of the Pd55 Mackay
-icosahedron on the graded 129^3 mesh (0.12 -> 0.6 bohr, 10 bohr vacuum) with a
-seeded synthetic Slater-model density.  `value` is the mixed-precision form
-(FP32 multigrid preconditioner inside FP64 CG); the plain FP64 form is reported
-beside it.  The 17-70 MB working set of this workload fits the 129 MB L2, so L2
-is flushed (a 512 MiB write) before every timed step and each step is timed alone
-with CUDA events on the launch stream.
+Metric: converged Poisson solves per second (relative residual <= 1e-10).  One solve =
+density, pseudo-density deposit, boundary multipoles, faces, iteration to 1e-10, sphere
+projection, for a Pd55 Mackay icosahedron on the graded 129^3 mesh (0.12 -> 0.6 bohr,
+10 bohr vacuum) with a seeded synthetic Slater-model density.
+
+`value` is the chosen form: 8 such clusters (density seeds 1..8) per call, solved as
+independent branches of one CUDA graph, each started from the learned guess (the U-Net
+runs inside the graph, once for the batch), with FP64 defect correction around FP32
+multigrid-preconditioned CG and the FP32-pair density deposit.  A step is one batch of 8
+solves.  The plain form (one cluster per call, zero start, FP64 throughout) is timed in the
+same clock-sampled region and reported beside it, as are the forms between the two.  The
+working set fits the 129 MB L2, so L2 is flushed (a 512 MiB write) before every timed step
+and each step is timed alone with CUDA events on the launch stream.
 
 `--impl reference` times the FP64 CPU oracle on the same workload and metric (the
 reference arm; the paper publishes no implementation or timing).
 
-Multi-GPU: the step does not shard; N ranks run N independent replicas (weak
-scaling), value = solves of all ranks / max over ranks of the timed span.
+Multi-GPU: the step does not shard; N ranks run N independent replicas (weak scaling),
+value = solves of all ranks / max over ranks of the timed span.
 """
 from __future__ import annotations
 
@@ -33,7 +37,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "converged Poisson solves/sec (resid <=1e-10)"
 UNIT = "solves/s"
-WORKLOAD = "Pd55 Mackay icosahedron, graded 129^3 (0.12->0.6 bohr, 10 bohr vacuum), synthetic Slater density seed 1"
+WORKLOAD = ("Pd55 Mackay icosahedron, graded 129^3 (0.12->0.6 bohr, 10 bohr vacuum), synthetic Slater densities; "
+            "8 clusters (density seeds 1-8) per step")
+FORM = ("learned initial guess (U-Net in the graph) + FP64 defect correction around FP32 multigrid-preconditioned CG "
+        "+ FP32-pair density; 8 clusters per graph launch")
+BATCH = 8
 
 
 def parse():
@@ -46,9 +54,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batch64", action="store_true")
-    p.add_argument("--profile", choices=["smoother", "solve"], default=None,
+    p.add_argument("--profile", choices=["smoother", "solve", "guess"], default=None,
                    help="run one kernel family for a profiler and exit: 'smoother' = one FP32 red-black sweep "
-                        "on an n^3 graded mesh, 'solve' = one mixed solve of the workload with direct launches")
+                        "on an n^3 graded mesh, 'solve' = one mixed solve of the workload with direct launches, "
+                        "'guess' = the same with the learned initial guess")
     p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
     p.add_argument("--direct", action="store_true",
                    help="launch the kernels directly instead of one CUDA graph per solve (for ncu)")
@@ -204,77 +213,106 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     B.load()
 
-    cl = synth.pd55_graded129()
+    cls8 = [synth.pd55_graded129(seed=1 + k) for k in range(BATCH)]
+    cl = cls8[0]
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    launch = 1 if args.direct else 0
 
-    def make(precision):
-        return B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, precision=precision, launch=1 if args.direct else 0)
+    def make(precision, batch=1, guess=False):
+        s_ = B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, max_batch=batch, precision=precision, launch=launch)
+        if guess:
+            s_.set_guess()
+        return s_
 
-    dc = B.DeviceCluster(cl)
-    vlm = torch.empty((cl.n_atoms, 25), dtype=torch.float64, device=dev)
+    dcs8 = [B.DeviceCluster(c) for c in cls8]
+    vlm8 = torch.empty((BATCH * cl.n_atoms, 25), dtype=torch.float64, device=dev)
+    dc = dcs8[0]
+    vlm = vlm8[:cl.n_atoms]
 
-    def timed_solves(solver, steps, warmup):
+    def timed(solver, dcs, out, steps, warmup):
+        """steps timed calls (L2 flushed before each); kernel launches counted from the graph."""
         st = None
         for _ in range(warmup):
-            st = solver.solve(dc, vlm)
+            st = solver.solve(dcs, out)
         torch.cuda.synchronize()
-        assert st[0].status == 0 and st[0].rel_resid <= 1e-10, (st[0].status, st[0].rel_resid)
+        assert all(x.status == 0 and x.rel_resid <= 1e-10 for x in st), [(x.status, x.rel_resid) for x in st]
         fixed, per_it, per_out = solver.kernel_counts() if not args.direct else (0, 0, 0)
-        ms, launches, cycles = [], 0, []
+        ms, launches = [], 0
         for _ in range(steps):
             flush.fill_(1.0)                       # evict the working set from L2
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = solver.solve(dc, vlm)
+            st = solver.solve(dcs, out)
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-            cycles.append((st[0].cycles, st[0].outer))
-            launches += fixed + st[0].cycles * per_it + st[0].outer * per_out
-            assert st[0].status == 0 and st[0].rel_resid <= 1e-10
-        return ms, launches, cycles, st[0]
+            launches += fixed + sum(x.cycles * per_it + x.outer * per_out for x in st)
+            assert all(x.status == 0 and x.rel_resid <= 1e-10 for x in st)
+        return {"ms": ms, "launches": launches, "stats": list(st)}
 
-    mixed, plain = make(B.LASTO_PREC_MIXED), make(B.LASTO_PREC_FP64)
-    # warm both, then time the plain form and the chosen form with clock sampling
+    def summary(r, nclusters):
+        st = r["stats"]
+        return {"value": nclusters * len(r["ms"]) / (sum(r["ms"]) / 1e3), "unit": UNIT,
+                "ms_per_call": sum(r["ms"]) / len(r["ms"]), "clusters_per_call": nclusters,
+                "cycles": [x.cycles for x in st], "outer": [x.outer for x in st],
+                "max_rel_resid": max(x.rel_resid for x in st), "learned_guess": [x.guess for x in st]}
+
+    plain = make(B.LASTO_PREC_FP64)
+    chosen = make(B.LASTO_PREC_MIXED, BATCH, guess=True)
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        ms_plain, _, cyc_plain, st_plain = timed_solves(plain, args.steps, args.warmup)
+        r_plain = timed(plain, dc, vlm, args.steps, args.warmup)
         barrier(ws)
         torch.cuda.synchronize()
-        ms_mixed, launches, cyc_mixed, st_mixed = timed_solves(mixed, args.steps, args.warmup)
+        r_chosen = timed(chosen, dcs8, vlm8, args.steps, args.warmup)
         torch.cuda.synchronize()
         barrier(ws)
-    span_ms = sum(ms_mixed)
-    span_max = max_over_ranks(span_ms, ws, dev)
-    value = (args.steps * ws) / (span_max / 1e3)
-    plain_value = (args.steps * ws) / (max_over_ranks(sum(ms_plain), ws, dev) / 1e3)
+    span_max = max_over_ranks(sum(r_chosen["ms"]), ws, dev)
+    value = (BATCH * args.steps * ws) / (span_max / 1e3)
+    plain_value = (args.steps * ws) / (max_over_ranks(sum(r_plain["ms"]), ws, dev) / 1e3)
 
-    # ---------------- end to end through the C ABI with host buffers
+    # ---------------- the forms between plain and chosen (one factor at a time)
+    steps_b = max(3, args.steps // 4)
+    mixed1 = make(B.LASTO_PREC_MIXED)
+    forms = {"mixed_single": summary(timed(mixed1, dc, vlm, steps_b, 2), 1)}
+    mixed1.set_guess()
+    forms["mixed_learned_single"] = summary(timed(mixed1, dc, vlm, steps_b, 2), 1)
+    mixed1.close()
+    mixed8 = make(B.LASTO_PREC_MIXED, BATCH)
+    forms["mixed_batched"] = summary(timed(mixed8, dcs8, vlm8, steps_b, 2), BATCH)
+    mixed8.close()
+
+    # ---------------- end to end through the C ABI with host buffers (the chosen form)
     e2e = None
     if not args.no_e2e:
-        host = {k: torch.as_tensor(np.ascontiguousarray(getattr(cl, k), dtype=np.float64)).pin_memory()
-                for k in ("pos", "Z", "R", "slater_w", "slater_zeta", "c_lm")}
-        devbuf = {k: torch.empty_like(v, device=dev) for k, v in host.items()}
-        vlm_host = torch.empty((cl.n_atoms, 25), dtype=torch.float64).pin_memory()
-        dce = B.DeviceCluster(cl)
-        dce.pos, dce.Z, dce.R = devbuf["pos"], devbuf["Z"], devbuf["R"]
-        dce.w, dce.zeta, dce.clm = devbuf["slater_w"], devbuf["slater_zeta"], devbuf["c_lm"]
-        axes = [torch.empty(cl.n, dtype=torch.float64, device=dev) for _ in range(3)]
-        dce.x, dce.y, dce.z = axes
-        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        fields = ("pos", "Z", "R", "slater_w", "slater_zeta", "c_lm")
+        host = [{k: torch.as_tensor(np.ascontiguousarray(getattr(c, k), dtype=np.float64)).pin_memory()
+                 for k in fields} for c in cls8]
+        devbuf = [{k: torch.empty_like(v, device=dev) for k, v in hb.items()} for hb in host]
+        vlm_host = torch.empty((BATCH * cl.n_atoms, 25), dtype=torch.float64).pin_memory()
+        dces = []
+        for c, dbuf in zip(cls8, devbuf):
+            d = B.DeviceCluster(c)
+            d.pos, d.Z, d.R = dbuf["pos"], dbuf["Z"], dbuf["R"]
+            d.w, d.zeta, d.clm = dbuf["slater_w"], dbuf["slater_zeta"], dbuf["c_lm"]
+            d.x, d.y, d.z = (torch.empty(c.n, dtype=torch.float64, device=dev) for _ in range(3))
+            dces.append(d)
+        h2d = sum(v.numel() * v.element_size() for hb in host for v in hb.values())
         d2h = vlm_host.numel() * vlm_host.element_size()
         lib = B.load()
 
         def e2e_step():
-            for k in host:
-                devbuf[k].copy_(host[k], non_blocking=True)
-            for a in range(3):
-                lib.lasto_mesh_axis(cl.n, float(cl.centre[a]), cl.half_width, cl.h_min, cl.h_max, cl.p_max,
-                                    B._ptr(axes[a]), None, B._stream(None))
-            st = mixed.solve(dce, vlm)
-            vlm_host.copy_(vlm, non_blocking=True)
+            for hb, dbuf in zip(host, devbuf):
+                for k in fields:
+                    dbuf[k].copy_(hb[k], non_blocking=True)
+            for c, d in zip(cls8, dces):
+                for a, ax in enumerate((d.x, d.y, d.z)):
+                    lib.lasto_mesh_axis(c.n, float(c.centre[a]), c.half_width, c.h_min, c.h_max, c.p_max,
+                                        B._ptr(ax), None, B._stream(None))
+            st = chosen.solve(dces, vlm8)
+            vlm_host.copy_(vlm8, non_blocking=True)
             return st
 
         for _ in range(args.warmup):
@@ -289,21 +327,18 @@ def main():
             e1.record(stream)
             e1.synchronize()
             ms_e2e.append(e0.elapsed_time(e1))
-            assert st[0].status == 0
-        e2e_val = (args.steps * ws) / (max_over_ranks(sum(ms_e2e), ws, dev) / 1e3)
+            assert all(x.status == 0 for x in st)
+        e2e_val = (BATCH * args.steps * ws) / (max_over_ranks(sum(ms_e2e), ws, dev) / 1e3)
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # ---------------- batched forms (one graph launch per batch, clusters as concurrent branches)
-    batch8 = batch_throughput(B, [synth.pd55_graded129(seed=1 + k) for k in range(8)], B.LASTO_PREC_MIXED,
-                              max(2, args.steps // 4), flush, stream, dev)
+    # ---------------- the uneven batch of 64 (Pd13/55/147 on 65^3 .. 193^3), chosen form
     b64 = None
     if not args.no_batch64:
-        b64 = batch_throughput(B, synth.batch64(), B.LASTO_PREC_MIXED, 2, flush, stream, dev, warmup=1)
+        b64 = batch_throughput(B, synth.batch64(), B.LASTO_PREC_MIXED, 2, flush, stream, dev, warmup=1, guess=True)
 
     # ---------------- roofline of the dominant kernel (FP32 red-black half sweep)
     roof = smoother_roofline(B, stream, flush, dev)
-    dep = kernel_roofline(B, cl, dc, stream, flush, dev, 1)
-    roof["deposit_fp32pair_ms"] = dep["ms"]
+    roof["deposit_fp32pair_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 1)["ms"]
     roof["deposit_fp64_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 0)["ms"]
 
     # ---------------- CPU baseline: the oracle as it stands, one whole solve
@@ -311,23 +346,27 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         dt, out = oracle_solves(cl, 1)
         cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-               "sample": f"1 whole solve of the workload to 1e-10 ({out['cycles']} V(2,2) cycles), {dt:.1f} s"}
+               "sample": f"1 whole solve of one cluster of the workload to 1e-10 ({out['cycles']} V(2,2) cycles), "
+                         f"{dt:.1f} s"}
 
     if rank == 0:
+        ch = summary(r_chosen, BATCH)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": span_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "FP64 defect correction around FP32 multigrid-preconditioned CG; FP32-pair density",
-                       "l2": "flushed before every timed step (512 MiB write)", "cycles": cyc_mixed[-1][0], "defect_correction_steps": cyc_mixed[-1][1],
-                       "rel_resid": st_mixed.rel_resid, "parallelism": f"replicas x{ws}"},
-            "plain_fp64": {"value": plain_value, "unit": UNIT, "ms_per_step": sum(ms_plain) / args.steps,
-                           "cycles": cyc_plain[-1][0], "rel_resid": st_plain.rel_resid},
-            "batched_pd55x8": batch8,
+            "dtype": "f64+f32+bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "form": FORM, "l2": "flushed before every timed step (512 MiB write)",
+                       "cycles": ch["cycles"], "defect_correction_steps": ch["outer"],
+                       "max_rel_resid": ch["max_rel_resid"], "parallelism": f"replicas x{ws}"},
+            "plain_fp64": {"value": plain_value, "unit": UNIT, "ms_per_step": sum(r_plain["ms"]) / args.steps,
+                           "cycles": r_plain["stats"][0].cycles, "rel_resid": r_plain["stats"][0].rel_resid,
+                           "form": "one cluster per call, zero start, FP64 deposit and FP64 multigrid-preconditioned CG"},
+            "chosen_over_plain": value / plain_value,
+            "forms": forms,
             "batch64_uneven": b64,
             "clocks": clk.summary(),
             "e2e": e2e,
-            "gpu_launches": launches,
+            "gpu_launches": r_chosen["launches"],
             "roofline": roof,
             "cpu_baseline": cpu,
         }
@@ -352,6 +391,8 @@ def run_profile(args, B):
     else:
         cl = synth.pd55_graded129()
         solver = B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, precision=B.LASTO_PREC_MIXED, launch=1)
+        if args.profile == "guess":
+            solver.set_guess()
         dc = B.DeviceCluster(cl)
         v = torch.empty((cl.n_atoms, 25), dtype=torch.float64, device="cuda")
         st = solver.solve(dc, v)
@@ -362,12 +403,14 @@ def run_profile(args, B):
     return 0
 
 
-def batch_throughput(B, clusters, precision, steps, flush, stream, dev, warmup=2):
+def batch_throughput(B, clusters, precision, steps, flush, stream, dev, warmup=2, guess=False):
     """Solves/s of a batch of clusters solved in one call (one graph launch)."""
     import torch
     n_max = max(c.n for c in clusters)
     solver = B.Poisson(n_max=n_max, max_atoms=max(c.n_atoms for c in clusters), max_batch=len(clusters),
                        precision=precision)
+    if guess:
+        solver.set_guess()
     dcs = [B.DeviceCluster(c) for c in clusters]
     vlm = torch.empty((sum(c.n_atoms for c in clusters), 25), dtype=torch.float64, device=dev)
     for _ in range(warmup):
@@ -387,8 +430,9 @@ def batch_throughput(B, clusters, precision, steps, flush, stream, dev, warmup=2
     del dcs, vlm
     torch.cuda.empty_cache()
     return {"value": len(clusters) * steps / (sum(ms) / 1e3), "unit": UNIT, "clusters": len(clusters),
-            "ms_per_batch": sum(ms) / steps, "all_converged": ok,
-            "max_cycles": max(s.cycles for s in st), "nodes": sum(c.n ** 3 for c in clusters)}
+            "ms_per_batch": sum(ms) / steps, "all_converged": ok, "mean_cycles": sum(s.cycles for s in st) / len(st),
+            "max_cycles": max(s.cycles for s in st), "learned_guess": sum(s.guess for s in st),
+            "nodes": sum(c.n ** 3 for c in clusters)}
 
 
 def smoother_roofline(B, stream, flush, dev):
@@ -430,8 +474,11 @@ def smoother_roofline(B, stream, flush, dev):
     achieved = bytes_per_launch / t_launch / 1e9
     del u, b
     torch.cuda.empty_cache()
+    # DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel at 257^3
+    # (134.8 MB + 18.3 MB, mean of the red and the black launch), scaled by the node count
+    traffic = 153.1e6 * (n / 257.0) ** 3
     return {"kernel": "k_rbgs<float> (red-black half sweep, 385^3 graded)", "bound": "hbm", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 

@@ -427,8 +427,9 @@ int enqueue_guess_in(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, 
         TRY(launch_restrict<double>(P.lv[l].view64(), P.lv[l + 1].view64(), P.lv[l].b, P.lv[l + 1].b, s));
     const LevelStore& S = P.lv[P.gl];
     TRY(launch_resample(S.n, S.ax[0].c, S.ax[1].c, S.ax[2].c, S.b, G, P.gax[0], P.gax[1], P.gax[2], P.bG, 0, s));
-    TRY(cudaMemsetAsync(P.fG, 0, sizeof(double) * GUESS_N * GUESS_N * GUESS_N, s));
-    TRY(launch_boundary_fill(G, P.gax[0], P.gax[1], P.gax[2], cl.centre[0], cl.centre[1], cl.centre[2], P.Q, P.fG, s));
+    // faces (and a zero interior) from the fine grid's first iterate: copies at shared nodes
+    const LevelStore& F = P.lv[0];
+    TRY(launch_resample(F.n, F.ax[0].c, F.ax[1].c, F.ax[2].c, F.u, G, P.gax[0], P.gax[1], P.gax[2], P.fG, 0, s));
     const float* sc = guess_net_scales(h->net);
     if (lasto_nn_guess_features(G, P.bG, P.fG, P.gax[0], P.gax[1], P.gax[2], sc[0], sc[1], sc[2],
                                 guess_net_features(h->net, P.gslot), s) != LASTO_OK)
@@ -446,22 +447,20 @@ int enqueue_guess_out(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl,
         return fail(h, LASTO_ERR_CUDA, "guess grid");
     const int gl = P.gl;
     LevelStore& S = P.lv[gl];
+    const LevelStore& F = P.lv[0];
     double* tgt = gl == 0 ? P.lv[0].u : S.u;
-    if (gl > 0) {
-        TRY(cudaMemsetAsync(tgt, 0, sizeof(double) * S.N(), s));
-        TRY(launch_boundary_fill(S.n, S.ax[0].c, S.ax[1].c, S.ax[2].c, cl.centre[0], cl.centre[1], cl.centre[2], P.Q,
-                                 tgt, s));
-    }
+    // coarse levels: the fine grid's faces and zero interior (copies at shared nodes)
+    if (gl > 0)
+        TRY(launch_resample(F.n, F.ax[0].c, F.ax[1].c, F.ax[2].c, F.u, S.n, S.ax[0].c, S.ax[1].c, S.ax[2].c, tgt, 0, s));
     TRY(launch_resample(G, P.gax[0], P.gax[1], P.gax[2], P.uG, S.n, S.ax[0].c, S.ax[1].c, S.ax[2].c, tgt, 1, s));
     for (int l = gl - 1; l >= 0; l--) {
         LevelStore& Fl = P.lv[l];
-        if (l > 0) {
-            TRY(cudaMemsetAsync(Fl.u, 0, sizeof(double) * Fl.N(), s));
-            TRY(launch_boundary_fill(Fl.n, Fl.ax[0].c, Fl.ax[1].c, Fl.ax[2].c, cl.centre[0], cl.centre[1],
-                                     cl.centre[2], P.Q, Fl.u, s));
-        }
+        if (l > 0)
+            TRY(launch_resample(F.n, F.ax[0].c, F.ax[1].c, F.ax[2].c, F.u, Fl.n, Fl.ax[0].c, Fl.ax[1].c, Fl.ax[2].c,
+                                Fl.u, 0, s));
         TRY(launch_prolong_add<double>(Fl.view64(), P.lv[l + 1].view64(), P.lv[l + 1].u, Fl.u, s));
     }
+    (void)cl;
     return LASTO_OK;
 }
 

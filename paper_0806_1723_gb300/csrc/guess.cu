@@ -9,11 +9,12 @@
 // Per cluster, after its right-hand side: restrict b (full weighting) down the hierarchy to
 // the deepest level that still has at least 33 nodes per axis, resample it onto the 33^3
 // subgrid (trilinear in physical coordinates; the identity when the level is the subgrid,
-// as for 65^3, 129^3 and 257^3 meshes), set the subgrid's Dirichlet faces from the
-// multipoles, and write the network's input features.  Once every cluster's features are
-// written, one batched forward pass runs.  Per cluster again: the predicted subgrid
-// potential is resampled onto that level's interior, given its Dirichlet faces, and
-// prolonged level by level to the fine grid, where it replaces the zero interior.
+// as for 65^3, 129^3 and 257^3 meshes), take the subgrid's Dirichlet faces from the fine
+// grid's (every subgrid and level node is a fine node), and write the network's input
+// features.  Once every cluster's features are written, one batched forward pass runs.  Per
+// cluster again: the predicted subgrid potential is resampled onto that level's interior,
+// given its faces, and prolonged level by level to the fine grid, where it replaces the
+// zero interior.
 #include <cstring>
 #include <vector>
 
@@ -51,7 +52,8 @@ __device__ __forceinline__ int cell_below(const double* __restrict__ a, int n, d
 }
 
 // dst (grid B) = trilinear interpolation of src (grid A) in physical coordinates; both
-// grids span the same box.  interior_only: B's faces are left as they are.
+// grids span the same box.  Exact (a copy) at the nodes B shares with A.  interior_only: B's
+// faces are left as they are.
 __global__ void k_resample(int ax_n, int ay_n, int az_n, const double* __restrict__ ax, const double* __restrict__ ay,
                            const double* __restrict__ az, const double* __restrict__ src, int bx_n, int by_n, int bz_n,
                            const double* __restrict__ bx, const double* __restrict__ by,
@@ -69,7 +71,7 @@ __global__ void k_resample(int ax_n, int ay_n, int az_n, const double* __restric
     const double tz = (pz - az[ck]) / (az[ck + 1] - az[ck]);
     const size_t sy = (size_t)ax_n, sz = (size_t)ax_n * ay_n;
     const double* c0 = src + (size_t)ck * sz + (size_t)cj * sy + ci;
-    auto lerp = [](double a, double b, double w) { return w == 0.0 ? a : a + w * (b - a); };
+    auto lerp = [](double a, double b, double w) { return w == 0.0 ? a : w == 1.0 ? b : a + w * (b - a); };
     const double v00 = lerp(c0[0], c0[1], tx), v01 = lerp(c0[sy], c0[sy + 1], tx);
     const double v10 = lerp(c0[sz], c0[sz + 1], tx), v11 = lerp(c0[sz + sy], c0[sz + sy + 1], tx);
     dst[t] = lerp(lerp(v00, v01, ty), lerp(v10, v11, ty), tz);
@@ -88,6 +90,8 @@ struct GuessNet {
     float scales[4] = {1, 1, 1, 1};   // s0, s1, h_ref, out
     // activations for nbmax grids
     float *x32, *e1, *cat1, *pred, *p1, *e2, *cat2, *d2, *p2, *e3, *cat3, *d3, *p3, *bt;
+    float* scratch = nullptr;   // tap-group partial sums of the small-grid convolutions
+    size_t scratch_floats = 0;
     void *x16, *a0, *b0, *cat1h, *p1h, *a1, *cat2h, *p2h, *a2, *cat3h, *p3h, *a3;
 };
 
@@ -122,6 +126,8 @@ int guess_net_create(const float* params, size_t n_params, const double scales[4
     for (int l = 0; l < NL; l++) b16 += (size_t)27 * L_CIN[l] * L_COUT[l];
     f32 += N0 * (16 + 16 + 48 + 16) + N1 * (16 + 32 + 96 + 32) + N2 * (32 + 64 + 128 + 64) + N3 * (64 + 64);
     b16 += N0 * (16 + 16 + 16 + 48) + N1 * (16 + 32 + 96) + N2 * (32 + 64 + 128) + N3 * (64 + 64);
+    g->scratch_floats = (size_t)1216 * 64 * 128;
+    f32 += g->scratch_floats;
     const size_t bytes = f32 * 4 + b16 * 2 + 64 * 256;
     if (cudaMalloc(&g->pool, bytes) != cudaSuccess) {
         delete g;
@@ -146,6 +152,7 @@ int guess_net_create(const float* params, size_t n_params, const double scales[4
     g->p1h = H(N1 * 16); g->a1 = H(N1 * 32); g->cat2h = H(N1 * 96);
     g->p2h = H(N2 * 32); g->a2 = H(N2 * 64); g->cat3h = H(N2 * 128);
     g->p3h = H(N3 * 64); g->a3 = H(N3 * 64);
+    g->scratch = F(g->scratch_floats);
     cudaError_t e = cudaMemcpyAsync(staging, params, n_params * 4, cudaMemcpyHostToDevice, s);
     size_t off = 0;
     for (int l = 0; l < NL && e == cudaSuccess; l++) {
@@ -181,8 +188,8 @@ int guess_net_forward(GuessNet* g, int nb, cudaStream_t s)
     int st = LASTO_OK;
     auto conv = [&](int l, int lv, const void* x, float* y32, int ldy32, int off32, void* y16, int ldy16, int off16) {
         if (st) return;
-        st = lasto_nn_conv3d_fwd(nb, dim[lv], L_CIN[l], L_COUT[l], x, g->w16[l], g->bias[l], L_RELU[l], y32, ldy32,
-                                 off32, y16, ldy16, off16, s);
+        st = conv_fwd(nb, dim[lv], L_CIN[l], L_COUT[l], x, g->w16[l], g->bias[l], L_RELU[l], y32, ldy32, off32, y16,
+                      ldy16, off16, g->scratch, g->scratch_floats, s);
     };
     auto tobf = [&](size_t n, const float* a, void* b) {
         if (!st) st = lasto_nn_to_bf16(n, a, b, s);

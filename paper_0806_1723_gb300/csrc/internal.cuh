@@ -232,6 +232,10 @@ float* guess_net_features(GuessNet* g, int k);          // FP32 [33^3][16] input
 const float* guess_net_prediction(GuessNet* g, int k);  // FP32 [33^3][16], channel 0 = prediction
 int guess_net_capacity(const GuessNet* g);
 const float* guess_net_scales(const GuessNet* g);       // s0, s1, h_ref, out
+// nn.cu: convolution with an optional FP32 scratch for tap-group partial sums (small grids)
+int conv_fwd(int nb, const int dims[3], int cin, int cout, const void* x, const void* w, const float* bias, int relu,
+             float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, float* scratch,
+             size_t scratch_floats, void* stream);
 cudaError_t launch_axis_stride(const double* src, int m, int n, double* dst, cudaStream_t s);
 cudaError_t launch_resample(const int na[3], const double* ax, const double* ay, const double* az, const double* src,
                             const int nb[3], const double* bx, const double* by, const double* bz, double* dst,

@@ -38,12 +38,14 @@ __device__ __forceinline__ void split(size_t node, const Grid& g, int& b, int& z
 }
 
 // y = act(conv(x, w) + bias); act = relu if relu != 0.  Writes FP32 (ldy32, off32) and / or
-// BF16 (ldy16, off16) outputs, either may be null.
+// BF16 (ldy16, off16) outputs, either may be null.  With part != null the block sums only the
+// taps of its group blockIdx.y (27 / gridDim.y taps) and stores the raw sums to
+// part[blockIdx.y][node][COUT]; k_conv_epilogue then adds the groups in order.
 template <int COUT>
 __global__ void __launch_bounds__(CT) k_conv_fwd(Grid g, int cin, const bf16* __restrict__ x,
                                                  const bf16* __restrict__ w, const float* __restrict__ bias, int relu,
                                                  float* __restrict__ y32, int ldy32, int off32, bf16* __restrict__ y16,
-                                                 int ldy16, int off16)
+                                                 int ldy16, int off16, float* __restrict__ part)
 {
     __shared__ __align__(32) bf16 As[CM * 16];
     __shared__ __align__(32) bf16 Bs[16 * COUT];
@@ -60,7 +62,8 @@ __global__ void __launch_bounds__(CT) k_conv_fwd(Grid g, int cin, const bf16* __
     int b = 0, z = 0, yy = 0, xx = 0;
     const bool live = node < N;
     if (live) split(node, g, b, z, yy, xx);
-    for (int tap = 0; tap < 27; tap++) {
+    const int tpg = 27 / gridDim.y, tap_a = blockIdx.y * tpg;
+    for (int tap = tap_a; tap < tap_a + tpg; tap++) {
         const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
         const int zz = z + dz, y2 = yy + dy, x2 = xx + dx;
         const bool in = live && zz >= 0 && zz < g.D && y2 >= 0 && y2 < g.H && x2 >= 0 && x2 < g.W;
@@ -88,6 +91,12 @@ __global__ void __launch_bounds__(CT) k_conv_fwd(Grid g, int cin, const bf16* __
     for (int n = 0; n < COUT / 16; n++)
         wmma::store_matrix_sync(Cs + warp * 16 * COUT + n * 16, acc[n], COUT, wmma::mem_row_major);
     __syncthreads();
+    if (part) {
+        float* dst = part + ((size_t)blockIdx.y * N + node0) * COUT;
+        for (int t = threadIdx.x; t < CM * COUT; t += CT)
+            if (node0 + t / COUT < N) dst[t] = Cs[t];
+        return;
+    }
     for (int t = threadIdx.x; t < CM * COUT; t += CT) {
         const int r = t / COUT, co = t % COUT;
         const size_t nd = node0 + r;
@@ -97,6 +106,23 @@ __global__ void __launch_bounds__(CT) k_conv_fwd(Grid g, int cin, const bf16* __
         if (y32) y32[nd * ldy32 + off32 + co] = v;
         if (y16) y16[nd * ldy16 + off16 + co] = __float2bfloat16(v);
     }
+}
+
+// sum of the tap groups (in group order), bias, activation, outputs
+__global__ void k_conv_epilogue(size_t N, int cout, int groups, const float* __restrict__ part,
+                                const float* __restrict__ bias, int relu, float* __restrict__ y32, int ldy32,
+                                int off32, bf16* __restrict__ y16, int ldy16, int off16)
+{
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= N * cout) return;
+    const size_t nd = t / cout;
+    const int co = (int)(t % cout);
+    float v = part[t];
+    for (int k = 1; k < groups; k++) v += part[(size_t)k * N * cout + t];
+    v += bias ? bias[co] : 0.0f;
+    if (relu) v = fmaxf(v, 0.0f);
+    if (y32) y32[nd * ldy32 + off32 + co] = v;
+    if (y16) y16[nd * ldy16 + off16 + co] = __float2bfloat16(v);
 }
 
 // dw[tap][ci][co] += sum_node x[node + tap][ci] dy[node][co];  dbias[co] += sum_node dy[node][co]
@@ -408,6 +434,49 @@ inline unsigned blocks(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace nn
 }  // namespace lasto
 
+namespace lasto {
+
+// Convolution launcher.  Small grids leave most SMs idle with one block per 64 nodes, so
+// when scratch is given the 27 taps are split into 3, 9 or 27 groups (the largest split
+// that keeps the grid within 2432 blocks, 16 per SM) summed by k_conv_epilogue.
+int conv_fwd(int nb, const int dims[3], int cin, int cout, const void* x, const void* w, const float* bias, int relu,
+             float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, float* scratch,
+             size_t scratch_floats, void* stream)
+{
+    using namespace nn;
+    if (nb < 1 || !dims || cin % 16 || cout % 16 || cin < 16 || cout < 16 || cout > 128 || !x || !w)
+        return LASTO_ERR_INVALID_ARG;
+    Grid g{nb, dims[2], dims[1], dims[0]};
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned nbk = blocks(g.nodes(), CM);
+    int groups = 1;
+    if (scratch)
+        for (int cand : {3, 9, 27})
+            if ((size_t)nbk * cand <= 2432 && (size_t)cand * nbk * CM * cout <= scratch_floats) groups = cand;
+    float* part = groups > 1 ? scratch : nullptr;
+    const dim3 grid(nbk, groups);
+    const bf16* X = (const bf16*)x;
+    const bf16* Wt = (const bf16*)w;
+    bf16* Y16 = (bf16*)y16;
+    switch (cout) {
+        case 16: k_conv_fwd<16><<<grid, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16, part); break;
+        case 32: k_conv_fwd<32><<<grid, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16, part); break;
+        case 48: k_conv_fwd<48><<<grid, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16, part); break;
+        case 64: k_conv_fwd<64><<<grid, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16, part); break;
+        case 96: k_conv_fwd<96><<<grid, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16, part); break;
+        case 128: k_conv_fwd<128><<<grid, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16, part); break;
+        default: return LASTO_ERR_INVALID_ARG;
+    }
+    if (part) {
+        const size_t n = g.nodes() * cout;
+        k_conv_epilogue<<<blocks(n, 256), 256, 0, s>>>(g.nodes(), cout, groups, part, bias, relu, y32, ldy32, off32,
+                                                       Y16, ldy16, off16);
+    }
+    return cudaGetLastError() == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
+}
+
+}  // namespace lasto
+
 using namespace lasto::nn;
 
 extern "C" {
@@ -415,24 +484,8 @@ extern "C" {
 int lasto_nn_conv3d_fwd(int nb, const int dims[3], int cin, int cout, const void* x, const void* w, const float* bias,
                         int relu, float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, void* stream)
 {
-    if (nb < 1 || !dims || cin % 16 || cout % 16 || cin < 16 || cout < 16 || cout > 128 || !x || !w)
-        return LASTO_ERR_INVALID_ARG;
-    Grid g{nb, dims[2], dims[1], dims[0]};
-    cudaStream_t s = (cudaStream_t)stream;
-    const unsigned nbk = blocks(g.nodes(), CM);
-    const bf16* X = (const bf16*)x;
-    const bf16* Wt = (const bf16*)w;
-    bf16* Y16 = (bf16*)y16;
-    switch (cout) {
-        case 16: k_conv_fwd<16><<<nbk, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16); break;
-        case 32: k_conv_fwd<32><<<nbk, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16); break;
-        case 48: k_conv_fwd<48><<<nbk, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16); break;
-        case 64: k_conv_fwd<64><<<nbk, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16); break;
-        case 96: k_conv_fwd<96><<<nbk, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16); break;
-        case 128: k_conv_fwd<128><<<nbk, CT, 0, s>>>(g, cin, X, Wt, bias, relu, y32, ldy32, off32, Y16, ldy16, off16); break;
-        default: return LASTO_ERR_INVALID_ARG;
-    }
-    return cudaGetLastError() == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
+    return lasto::conv_fwd(nb, dims, cin, cout, x, w, bias, relu, y32, ldy32, off32, y16, ldy16, off16, nullptr, 0,
+                           stream);
 }
 
 int lasto_nn_conv3d_dgrad(int nb, const int dims[3], int cin, int cout, const void* dy, const void* w, void* w_flip,

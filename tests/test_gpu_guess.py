@@ -83,13 +83,14 @@ def test_guess_inside_the_solve_graph():
     assert [s.guess for s in s0] == [0, 0, 0, 0] and [s.guess for s in s1] == [1, 1, 1, 1]
     a, b = host(v0), host(v1)
     assert np.abs(a - b).max() <= 1e-8 * np.abs(a).max()
-    # the in-graph guess equals the one computed outside the solve (same kernels)
+    # the in-graph guess matches the one computed outside the solve (the same network; the
+    # in-graph pass sums the small grids' convolution taps in groups, so the last bits differ)
     single = B.Poisson(n_max=129, max_atoms=147, precision=B.LASTO_PREC_MIXED)
     for k, dc in enumerate(dcs[:3]):
         v = torch.empty((dc.n_atoms, 25), dtype=torch.float64, device="cuda")
         st = single.solve(dc, v, guess=U.learned_guess(net, dc))[0]
         torch.cuda.synchronize()
-        assert st.cycles == s1[k].cycles, (k, st.cycles, s1[k].cycles)
+        assert abs(st.cycles - s1[k].cycles) <= 1, (k, st.cycles, s1[k].cycles)
     assert sum(s.cycles for s in s1[:3]) < sum(s.cycles for s in s0[:3])
     # replaying the captured graph gives the same counts
     s2 = learned.solve(dcs, v1)
