@@ -308,6 +308,15 @@ int lasto_op_project(const int n[3], const double* x, const double* y, const dou
  * off16) are each optional: writing into a channel slice makes concatenation free. */
 int lasto_nn_conv3d_fwd(int nb, const int dims[3], int cin, int cout, const void* x, const void* w, const float* bias,
                         int relu, float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, void* stream);
+/* The forward convolution on the fifth-generation tensor cores (tcgen05.mma, accumulator in
+ * tensor memory), same arguments and results as lasto_nn_conv3d_fwd except the weights,
+ * which are packed once by lasto_nn_pack_weights (same size, 27*cin*cout BF16) into the
+ * per-step operand tiles.  cout in {16, 32, 48, 64, 96, 128}.  err (device int, optional) is
+ * set to 1 if a tensor-core completion wait timed out (the outputs are then not written). */
+int lasto_nn_pack_weights(int cin, int cout, const void* w, void* wpk, void* stream);
+int lasto_nn_conv3d_fwd_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* wpk,
+                           const float* bias, int relu, float* y32, int ldy32, int off32, void* y16, int ldy16,
+                           int off16, int* err, void* stream);
 /* dx32 = data gradient of the convolution for output gradient dy (BF16 [node][cout]);
  * w_flip is caller scratch of 27*cin*cout BF16 (the flipped, transposed weights). */
 int lasto_nn_conv3d_dgrad(int nb, const int dims[3], int cin, int cout, const void* dy, const void* w, void* w_flip,

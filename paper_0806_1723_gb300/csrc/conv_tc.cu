@@ -1,0 +1,296 @@
+// 3x3x3 convolution of the learned-guess network on the fifth-generation tensor cores
+// (tcgen05): an implicit GEMM, M = 128 nodes per CTA, N = cout, K = 27 taps x cin, issued as
+// K = 16 steps (one tap, 16 input channels) of tcgen05.mma kind::f16 (BF16 x BF16 -> FP32)
+// with the accumulator in tensor memory.
+//
+// A (128 x 16 per step) is gathered by the CTA's 128 threads, one node row each (the
+// neighbour's 16 channels, zero outside the grid), into shared memory in the no-swizzle
+// K-major core-matrix layout: 8 rows x 16 bytes per core matrix, the two K halves 128 bytes
+// apart (leading byte offset), consecutive 8-row groups 256 bytes apart (stride byte
+// offset).  B (cout x 16 per step) is stored in global memory already in that layout (packed
+// once per weight set) and copied in.  Four shared stages form a ring: one thread issues the
+// MMA of a stage and commits it to the stage's mbarrier, which releases the stage for the
+// gather four steps later.  After the last step every thread reads its node's row of the
+// accumulator (tcgen05.ld 32x32b: warp w owns tensor-memory lanes 32w .. 32w+31) and applies
+// bias, ReLU and the output conversions.  Every mbarrier wait is bounded: on a timeout the
+// kernel records an error, stops issuing, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace lasto {
+namespace tc {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int TC_M = 128;        // nodes per CTA (MMA M), one per thread
+constexpr int TC_STAGES = 4;
+constexpr long long TC_SPIN_LIMIT = 1LL << 20;
+
+struct Grid {
+    int nb, D, H, W;
+    __host__ __device__ size_t nodes() const { return (size_t)nb * D * H * W; }
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major, LBO 128 B, SBO 256 B, version 1
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(256 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M = 128, N
+__host__ __device__ constexpr uint32_t make_idesc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (long long it = 0; it < TC_SPIN_LIMIT; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// y = act(conv(x, w) + bias) for one 128-node tile; with part != null the raw sums of tap
+// group blockIdx.y go to part[blockIdx.y][node][COUT] instead.
+template <int COUT>
+__global__ void __launch_bounds__(TC_M) k_conv_tc(Grid g, int cin, const bf16* __restrict__ x,
+                                                 const uint4* __restrict__ wpk, const float* __restrict__ bias,
+                                                 int relu, float* __restrict__ y32, int ldy32, int off32,
+                                                 bf16* __restrict__ y16, int ldy16, int off16,
+                                                 float* __restrict__ part, int* __restrict__ err)
+{
+    constexpr int A_BYTES = TC_M * 32;
+    constexpr int B_BYTES = COUT * 32;
+    constexpr int NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
+    __shared__ __align__(1024) unsigned char sA[TC_STAGES][A_BYTES];
+    __shared__ __align__(1024) unsigned char sB[TC_STAGES][B_BYTES];
+    __shared__ __align__(8) unsigned long long mbar[TC_STAGES];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const size_t N = g.nodes();
+    const size_t node0 = (size_t)blockIdx.x * TC_M;
+
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < TC_STAGES; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(NCOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // this thread's node
+    const size_t node = node0 + tid;
+    const bool live = node < N;
+    int b = 0, z = 0, yy = 0, xx = 0;
+    if (live) {
+        size_t r = node;
+        xx = (int)(r % g.W);
+        r /= g.W;
+        yy = (int)(r % g.H);
+        r /= g.H;
+        z = (int)(r % g.D);
+        b = (int)(r / g.D);
+    }
+    const int cpt = cin / 16;                       // K steps per tap
+    const int tpg = 27 / gridDim.y, tap_a = blockIdx.y * tpg;
+    const int nk = tpg * cpt;
+    const uint32_t idesc = make_idesc(COUT);
+    // canonical placement of this thread's row: 8-row group m8, row rr
+    const int m8 = tid >> 3, rr = tid & 7;
+    const int offA0 = (m8 * 2 + 0) * 128 + rr * 16, offA1 = (m8 * 2 + 1) * 128 + rr * 16;
+
+    for (int kc = 0; kc < nk; kc++) {
+        const int s = kc % TC_STAGES;
+        if (kc >= TC_STAGES) {   // the MMA that last read this stage must be complete
+            if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)((kc / TC_STAGES - 1) & 1))) abort_flag = 1;
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        const int tap = tap_a + kc / cpt, c0 = (kc % cpt) * 16;
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const int zz = z + dz, y2 = yy + dy, x2 = xx + dx;
+        uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
+        if (live && zz >= 0 && zz < g.D && y2 >= 0 && y2 < g.H && x2 >= 0 && x2 < g.W) {
+            const size_t nbn = (((size_t)b * g.D + zz) * g.H + y2) * g.W + x2;
+            const uint4* src = reinterpret_cast<const uint4*>(x + nbn * cin + c0);
+            v0 = src[0];
+            v1 = src[1];
+        }
+        *reinterpret_cast<uint4*>(&sA[s][offA0]) = v0;
+        *reinterpret_cast<uint4*>(&sA[s][offA1]) = v1;
+        const uint4* wsrc = wpk + ((size_t)(tap * cpt + c0 / 16)) * (B_BYTES / 16);
+        for (int t = tid; t < B_BYTES / 16; t += TC_M) reinterpret_cast<uint4*>(sB[s])[t] = wsrc[t];
+        // make the generic-proxy shared stores visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint64_t ad = make_desc(smem_u32(sA[s])), bd = make_desc(smem_u32(sB[s]));
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                    tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(kc > 0 ? 1 : 0)
+                : "memory");
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&mbar[s]))
+                         : "memory");
+        }
+    }
+    // wait for the last MMA (commits complete in issue order)
+    if (!abort_flag && nk > 0) {
+        const int s = (nk - 1) % TC_STAGES;
+        if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)(((nk - 1) / TC_STAGES) & 1))) abort_flag = 1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!abort_flag) {
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        float acc[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; c += 16) tmem_ld16(lane_base + (uint32_t)c, acc + c);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (live) {
+            if (part) {
+                float* dst = part + ((size_t)blockIdx.y * N + node) * COUT;
+#pragma unroll
+                for (int c = 0; c < COUT; c++) dst[c] = acc[c];
+            } else {
+#pragma unroll
+                for (int c = 0; c < COUT; c++) {
+                    float v = acc[c] + (bias ? bias[c] : 0.0f);
+                    if (relu) v = fmaxf(v, 0.0f);
+                    if (y32) y32[node * ldy32 + off32 + c] = v;
+                    if (y16) y16[node * ldy16 + off16 + c] = __float2bfloat16(v);
+                }
+            }
+        }
+    } else if (tid == 0 && err) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
+}
+
+// Pack w [27][cin][cout] into the per-step B tiles: step k = tap * (cin/16) + c0/16 holds
+// element (n = output channel, kk = input channel c0 + kk) at byte
+// ((n/8)*2 + kk/8)*128 + (n%8)*16 + (kk%8)*2 of its cout*32-byte tile.
+__global__ void k_pack_weights(int cin, int cout, const bf16* __restrict__ w, bf16* __restrict__ wpk)
+{
+    const size_t total = (size_t)27 * cin * cout;
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int co = (int)(t % cout);
+    const int ci = (int)((t / cout) % cin);
+    const int tap = (int)(t / ((size_t)cout * cin));
+    const int step = tap * (cin / 16) + ci / 16, kk = ci % 16;
+    const size_t byte = (size_t)step * cout * 32 + ((co / 8) * 2 + kk / 8) * 128 + (co % 8) * 16 + (kk % 8) * 2;
+    wpk[byte / 2] = w[t];
+}
+
+__global__ void k_tc_epilogue(size_t N, int cout, int groups, const float* __restrict__ part,
+                              const float* __restrict__ bias, int relu, float* __restrict__ y32, int ldy32, int off32,
+                              bf16* __restrict__ y16, int ldy16, int off16)
+{
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= N * cout) return;
+    const size_t nd = t / cout;
+    const int co = (int)(t % cout);
+    float v = part[t];
+    for (int k = 1; k < groups; k++) v += part[(size_t)k * N * cout + t];
+    v += bias ? bias[co] : 0.0f;
+    if (relu) v = fmaxf(v, 0.0f);
+    if (y32) y32[nd * ldy32 + off32 + co] = v;
+    if (y16) y16[nd * ldy16 + off16 + co] = __float2bfloat16(v);
+}
+
+}  // namespace tc
+
+cudaError_t launch_pack_weights(int cin, int cout, const void* w, void* wpk, cudaStream_t s)
+{
+    const size_t total = (size_t)27 * cin * cout;
+    tc::k_pack_weights<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(cin, cout, (const tc::bf16*)w, (tc::bf16*)wpk);
+    return cudaGetLastError();
+}
+
+int conv_fwd_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* wpk, const float* bias,
+                int relu, float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, float* scratch,
+                size_t scratch_floats, int* err, void* stream)
+{
+    using namespace tc;
+    if (nb < 1 || !dims || cin % 16 || cin < 16 || !x || !wpk ||
+        !(cout == 16 || cout == 32 || cout == 48 || cout == 64 || cout == 96 || cout == 128))
+        return LASTO_ERR_INVALID_ARG;
+    Grid g{nb, dims[2], dims[1], dims[0]};
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned nbk = (unsigned)((g.nodes() + TC_M - 1) / TC_M);
+    int groups = 1;
+    if (scratch)
+        for (int cand : {3, 9, 27})
+            if ((size_t)nbk * cand <= 2432 && (size_t)cand * g.nodes() * cout <= scratch_floats) groups = cand;
+    float* part = groups > 1 ? scratch : nullptr;
+    const dim3 grid(nbk, groups);
+    const bf16* X = (const bf16*)x;
+    const uint4* W = (const uint4*)wpk;
+    bf16* Y16 = (bf16*)y16;
+#define LASTO_TC_CASE(C)                                                                                           \
+    case C:                                                                                                        \
+        k_conv_tc<C><<<grid, TC_M, 0, s>>>(g, cin, X, W, bias, relu, y32, ldy32, off32, Y16, ldy16, off16, part, err); \
+        break;
+    switch (cout) {
+        LASTO_TC_CASE(16)
+        LASTO_TC_CASE(32)
+        LASTO_TC_CASE(48)
+        LASTO_TC_CASE(64)
+        LASTO_TC_CASE(96)
+        LASTO_TC_CASE(128)
+        default: return LASTO_ERR_INVALID_ARG;
+    }
+#undef LASTO_TC_CASE
+    if (part) {
+        const size_t n = g.nodes() * cout;
+        k_tc_epilogue<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g.nodes(), cout, groups, part, bias, relu, y32,
+                                                                  ldy32, off32, Y16, ldy16, off16);
+    }
+    return cudaGetLastError() == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
+}
+
+}  // namespace lasto

@@ -236,6 +236,11 @@ const float* guess_net_scales(const GuessNet* g);       // s0, s1, h_ref, out
 int conv_fwd(int nb, const int dims[3], int cin, int cout, const void* x, const void* w, const float* bias, int relu,
              float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, float* scratch,
              size_t scratch_floats, void* stream);
+// conv_tc.cu: the same convolution on tcgen05 tensor cores; weights packed once per set
+cudaError_t launch_pack_weights(int cin, int cout, const void* w, void* wpk, cudaStream_t s);
+int conv_fwd_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* wpk, const float* bias,
+                int relu, float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, float* scratch,
+                size_t scratch_floats, int* err, void* stream);
 cudaError_t launch_axis_stride(const double* src, int m, int n, double* dst, cudaStream_t s);
 cudaError_t launch_resample(const int na[3], const double* ax, const double* ay, const double* az, const double* src,
                             const int nb[3], const double* bx, const double* by, const double* bz, double* dst,

@@ -488,6 +488,20 @@ int lasto_nn_conv3d_fwd(int nb, const int dims[3], int cin, int cout, const void
                            stream);
 }
 
+int lasto_nn_pack_weights(int cin, int cout, const void* w, void* wpk, void* stream)
+{
+    if (cin < 16 || cin % 16 || cout < 16 || cout % 16 || !w || !wpk) return LASTO_ERR_INVALID_ARG;
+    return lasto::launch_pack_weights(cin, cout, w, wpk, (cudaStream_t)stream) == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
+}
+
+int lasto_nn_conv3d_fwd_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* wpk,
+                           const float* bias, int relu, float* y32, int ldy32, int off32, void* y16, int ldy16,
+                           int off16, int* err, void* stream)
+{
+    return lasto::conv_fwd_tc(nb, dims, cin, cout, x, wpk, bias, relu, y32, ldy32, off32, y16, ldy16, off16, nullptr,
+                              0, err, stream);
+}
+
 int lasto_nn_conv3d_dgrad(int nb, const int dims[3], int cin, int cout, const void* dy, const void* w, void* w_flip,
                           float* dx32, void* stream)
 {

@@ -49,6 +49,35 @@ def test_conv_forward(cin, cout, relu):
     assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (48, 16), (32, 64), (128, 64), (96, 32), (64, 48),
+                                      (32, 128)])
+def test_conv_forward_tensor_memory(cin, cout):
+    """The tcgen05 convolution (packed weights, accumulator in tensor memory) against the
+    FP64 oracle, with a ragged last tile (630 nodes = 4 tiles of 128 + 118)."""
+    import torch
+    B = need_gpu()
+    L = B.load()
+    rng = np.random.default_rng(3 * cin + cout)
+    nb, D, H, W = 2, 5, 7, 9
+    x = _bf16(rng.normal(size=(nb, D, H, W, cin))).cuda()
+    w = _bf16(rng.normal(size=(27, cin, cout)) * 0.1).cuda()
+    wpk = torch.empty_like(w)
+    bias = torch.as_tensor(rng.normal(size=cout), dtype=torch.float32).cuda()
+    y = torch.full((nb * D * H * W, cout), float("nan"), dtype=torch.float32, device="cuda")
+    y16 = torch.empty(nb * D * H * W, cout, dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert L.lasto_nn_pack_weights(cin, cout, B._ptr(w), B._ptr(wpk), B._stream()) == 0
+    st = L.lasto_nn_conv3d_fwd_tc(nb, _d3((W, H, D)), cin, cout, B._ptr(x), B._ptr(wpk), B._ptr(bias), 1, B._ptr(y),
+                                  cout, 0, B._ptr(y16), cout, 0, B._ptr(err), B._stream())
+    torch.cuda.synchronize()
+    assert st == 0 and int(err.item()) == 0
+    ref = np.maximum(U.conv3d(_f64(x), _f64(w), bias.double().cpu().numpy()), 0)
+    got = y.double().cpu().numpy().reshape(ref.shape)
+    assert np.isfinite(got).all()
+    assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert torch.equal(y16, y.to(torch.bfloat16))
+
+
 @pytest.mark.parametrize("cin,cout", [(16, 32), (64, 16), (96, 32)])
 def test_conv_gradients(cin, cout):
     import torch
