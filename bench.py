@@ -269,6 +269,11 @@ def main():
         r_chosen = timed(chosen, dcs8, vlm8, args.steps, args.warmup)
         torch.cuda.synchronize()
         barrier(ws)
+    tuned = [line.split() for line in chosen.tune_table().strip().splitlines()]
+    smoother_choice = {f"{r[0]}x{r[1]}x{r[2]}/{'f32' if r[3] == '4' else 'f64'}":
+                       (f"in-place half sweeps, {r[5]} threads" if r[4] == "0" else
+                        f"fused {r[9]}-sweep passes, tile {r[6]}x{r[7]}x{r[8]}") + f" ({float(r[10]):.1f} us)"
+                       for r in tuned}
     span_max = max_over_ranks(sum(r_chosen["ms"]), ws, dev)
     value = (BATCH * args.steps * ws) / (span_max / 1e3)
     plain_value = (args.steps * ws) / (max_over_ranks(sum(r_plain["ms"]), ws, dev) / 1e3)
@@ -357,7 +362,8 @@ def main():
             "dtype": "f64+f32+bf16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "form": FORM, "l2": "flushed before every timed step (512 MiB write)",
                        "cycles": ch["cycles"], "defect_correction_steps": ch["outer"],
-                       "max_rel_resid": ch["max_rel_resid"], "parallelism": f"replicas x{ws}"},
+                       "max_rel_resid": ch["max_rel_resid"], "parallelism": f"replicas x{ws}",
+                       "smoother_tuned": smoother_choice},
             "plain_fp64": {"value": plain_value, "unit": UNIT, "ms_per_step": sum(r_plain["ms"]) / args.steps,
                            "cycles": r_plain["stats"][0].cycles, "rel_resid": r_plain["stats"][0].rel_resid,
                            "form": "one cluster per call, zero start, FP64 deposit and FP64 multigrid-preconditioned CG"},

@@ -122,6 +122,19 @@ typedef struct lasto_stats {
 
 typedef struct lasto_poisson lasto_poisson;   /* opaque; owns workspace, plans and CUDA graphs */
 
+/* Smoother tuning (no counterpart in the paper, which gives no implementation).  The first
+ * solve of each new batch layout times, per level shape and precision, the red-black
+ * smoother as in-place half sweeps (128, 256 or 512 threads per block) and as fused passes
+ * of the z-slab and register-column kernels (several tile shapes), and the cycle uses the
+ * fastest; all give bitwise the same iterates.  lasto_poisson_tune_table writes the table as
+ * text, one line per shape: "nx ny nz elem_bytes fused threads tx ty kz sweeps_per_pass us"
+ * (NUL-terminated into buf when cap > 0) and returns its length, -1 for a null handle.
+ * lasto_poisson_set_tune_table adds such lines (shapes it lists are then not timed);
+ * INVALID_ARG for a malformed line or an unusable choice (the fused passes of the pre- and
+ * post-smoothing must together be even in number). */
+int lasto_poisson_tune_table(const lasto_poisson* h, char* buf, size_t cap);
+int lasto_poisson_set_tune_table(lasto_poisson* h, const char* text);
+
 /* Learned initial guess.  The paper has no counterpart: it solves every SCF step from
  * scratch.  A small 3-D U-Net (four levels, 16-32-64-64 channels, 3x3x3 convolutions with
  * BF16 tensor-core products and FP32 accumulation) maps the right-hand side restricted to a

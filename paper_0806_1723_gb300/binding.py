@@ -48,7 +48,8 @@ EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve"
            "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
            "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
-           "lasto_op_project", "lasto_guess_param_count", "lasto_poisson_set_guess", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
+           "lasto_op_project", "lasto_guess_param_count", "lasto_poisson_set_guess",
+           "lasto_poisson_tune_table", "lasto_poisson_set_tune_table", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
            "lasto_nn_relu_grad", "lasto_nn_to_bf16", "lasto_nn_copy_channels", "lasto_nn_down", "lasto_nn_up",
            "lasto_nn_mse", "lasto_nn_adam", "lasto_nn_guess_features", "lasto_nn_guess_grid"]
 
@@ -71,6 +72,8 @@ def _declare(L):
         "lasto_poisson_last_error": (ctypes.c_char_p, [vp]),
         "lasto_poisson_kernel_counts": (i, [vp, ip, ip, ip]),
         "lasto_guess_param_count": (ctypes.c_size_t, []),
+        "lasto_poisson_tune_table": (i, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+        "lasto_poisson_set_tune_table": (i, [vp, ctypes.c_char_p]),
         "lasto_poisson_set_guess": (i, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_size_t, ctypes.POINTER(d)]),
         "lasto_mesh_axis": (i, [i, d, d, d, d, d, vp, vp, vp]),
         "lasto_op_sphere_params": (i, [clp, vp, vp, vp, vp, vp, vp]),
@@ -236,6 +239,19 @@ class Poisson:
 
     def last_error(self) -> str:
         return load().lasto_poisson_last_error(self.h).decode()
+
+    def tune_table(self) -> str:
+        """The smoother choices measured so far, one line per level shape."""
+        L = load()
+        n = L.lasto_poisson_tune_table(self.h, None, 0)
+        buf = ctypes.create_string_buffer(n + 1)
+        L.lasto_poisson_tune_table(self.h, buf, n + 1)
+        return buf.value.decode()
+
+    def set_tune_table(self, text: str):
+        st = load().lasto_poisson_set_tune_table(self.h, text.encode())
+        if st != LASTO_OK:
+            raise RuntimeError(f"lasto_poisson_set_tune_table failed: {STATUS_NAMES.get(st, st)}: {self.last_error()}")
 
     def set_guess(self, weights=GUESS_WEIGHTS):
         """Load the learned initial-guess network (an .npz of per-layer weights [27][cin][cout],

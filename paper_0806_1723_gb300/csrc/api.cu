@@ -9,6 +9,10 @@
 // and the stats.
 #include <algorithm>
 #include <cstring>
+#include <cstdio>
+#include <map>
+#include <array>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -53,6 +57,15 @@ struct Carver {
     }
 };
 
+// How one level is smoothed: in-place half sweeps (block size nt) or fused passes of the
+// z-slab / register-column kernels (shape sh) ping-ponging with a partner array.
+struct SmoothChoice {
+    int fused = 0;
+    int nt = 256;
+    SlabShape sh{0, 0, 0, 0};
+    float us = 0.0f;   // measured time of one pre-smoothing phase
+};
+
 // Everything one cluster's solve touches on the device.
 struct ClusterPlan {
     int L = 0;
@@ -91,7 +104,7 @@ size_t cluster_bytes(const int n[3], int n_atoms)
         const size_t N = (size_t)nn[0] * nn[1] * nn[2];
         for (int d = 0; d < 3; d++) c.take<double>(axis_pool_doubles(nn[d]));
         c.take<double>(N);          // inv_diag
-        for (int t = 0; t < 3; t++) c.take<double>(N);
+        for (int t = 0; t < 4; t++) c.take<double>(N);
         for (int t = 0; t < 3; t++) c.take<float>(N);
         if (l == 0) {
             for (int t = 0; t < 3; t++) c.take<double>(N);
@@ -130,6 +143,7 @@ bool carve_cluster(Carver& c, const int n[3], int n_atoms, ClusterPlan& P)
         S.u = c.take<double>(N);
         S.b = c.take<double>(N);
         S.r = c.take<double>(N);
+        S.u2 = c.take<double>(N);
         S.u32 = c.take<float>(N);
         S.b32 = c.take<float>(N);
         S.r32 = c.take<float>(N);
@@ -218,6 +232,8 @@ struct lasto_poisson {
     int stats_count = 0;
     int kernels_fixed = -1, kernels_iter = -1, kernels_outer = 0;
     std::vector<cudaGraph_t> bodies, outer_bodies;
+    // smoother choice per level shape {nx, ny, nz, element bytes}: measured once, reused
+    std::map<std::array<int, 4>, SmoothChoice> tune;
     GuessNet* net = nullptr;             // learned initial guess (optional)
     std::vector<cudaEvent_t> eg;         // per slot: features written
     cudaEvent_t ev_net = nullptr;        // network forward done
@@ -245,6 +261,7 @@ template <typename T>
 struct Arr;
 template <>
 struct Arr<double> {
+    static double* partner(LevelStore& s) { return s.u2; }
     static double* u(LevelStore& s) { return s.u; }
     static double* b(LevelStore& s) { return s.b; }
     static double* r(LevelStore& s) { return s.r; }
@@ -252,11 +269,124 @@ struct Arr<double> {
 };
 template <>
 struct Arr<float> {
+    static float* partner(LevelStore& s) { return s.r32; }   // r32 is free in the FP32 cycle
     static float* u(LevelStore& s) { return s.u32; }
     static float* b(LevelStore& s) { return s.b32; }
     static float* r(LevelStore& s) { return s.r32; }
     static LevelT<float> view(const LevelStore& s) { return s.view32(); }
 };
+
+// ---------------------------------------------------------------- smoothing and its tuner
+// `nu` red-black sweeps starting with colour `first`.  In place, or as fused passes from
+// `cur` into the other of {home, partner}; cur follows the data.
+template <typename T>
+cudaError_t smooth(const LevelT<T>& V, T*& cur, T* partner, T* home, const T* b, int nu, int first,
+                   const SmoothChoice& ch, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (!ch.fused) {
+        for (int it = 0; it < nu && e == cudaSuccess; it++) {
+            e = launch_rbgs<T>(V, cur, b, first, s, ch.nt);
+            if (e == cudaSuccess) e = launch_rbgs<T>(V, cur, b, 1 - first, s, ch.nt);
+        }
+        return e;
+    }
+    const int ns = ch.sh.ns, full = nu / ns, rest = nu % ns;
+    for (int m = 0; m < full + (rest ? 1 : 0) && e == cudaSuccess; m++) {
+        SlabShape sh = ch.sh;
+        if (m == full) {
+            sh = slab_default_shape(rest, sizeof(T));
+            sh.kz = ch.sh.kz;
+        }
+        T* dst = cur == home ? partner : home;
+        e = launch_rb_slab<T>(V, cur, dst, b, first, 0, sh, s);
+        cur = dst;
+    }
+    return e;
+}
+
+int fused_passes(int nu, int ns) { return nu / ns + (nu % ns ? 1 : 0); }
+
+bool choice_usable(const lasto_poisson* h, const SmoothChoice& c, size_t elem)
+{
+    if (!c.fused) return c.nt >= 32 && c.nt <= 512 && c.nt % 32 == 0;
+    // the pre- and post-smoothing passes together must return the data to its home array
+    return slab_shape_ok(c.sh, elem) && (fused_passes(h->cfg.nu1, c.sh.ns) + fused_passes(h->cfg.nu2, c.sh.ns)) % 2 == 0;
+}
+
+template <typename T>
+SmoothChoice smooth_choice(const lasto_poisson* h, const LevelStore& S)
+{
+    auto it = h->tune.find({S.n[0], S.n[1], S.n[2], (int)sizeof(T)});
+    if (it != h->tune.end() && choice_usable(h, it->second, sizeof(T))) return it->second;
+    return SmoothChoice{};
+}
+
+// Time the candidates on this level's own arrays (zeroed; the stream is idle and not being
+// captured) and keep the fastest pre-smoothing phase.
+template <typename T>
+int tune_level(lasto_poisson* h, LevelStore& S, cudaStream_t st)
+{
+    const std::array<int, 4> key{S.n[0], S.n[1], S.n[2], (int)sizeof(T)};
+    if (h->tune.count(key)) return LASTO_OK;
+    const LevelT<T> V = Arr<T>::view(S);
+    T* u = Arr<T>::u(S);
+    T* partner = Arr<T>::partner(S);
+    T* b = Arr<T>::b(S);
+    TRY(cudaMemsetAsync(u, 0, sizeof(T) * S.N(), st));
+    TRY(cudaMemsetAsync(partner, 0, sizeof(T) * S.N(), st));
+    TRY(cudaMemsetAsync(b, 0, sizeof(T) * S.N(), st));
+    std::vector<SmoothChoice> cand;
+    for (int nt : {128, 256, 512}) {
+        SmoothChoice c;
+        c.nt = nt;
+        cand.push_back(c);
+    }
+    const bool f32 = sizeof(T) == 4;
+    for (int ty : f32 ? std::vector<int>{6, 14} : std::vector<int>{2, 6})
+        for (int kz : {16, 32}) {
+            SmoothChoice c;
+            c.fused = 1;
+            c.sh = SlabShape{62, ty, kz, 1};
+            cand.push_back(c);
+        }
+    for (SlabShape sh : {SlabShape{64, 16, 32, 2}, SlabShape{32, 8, 16, 2}}) {
+        SmoothChoice c;
+        c.fused = 1;
+        c.sh = sh;
+        cand.push_back(c);
+    }
+    cudaEvent_t e0, e1;
+    TRY(cudaEventCreate(&e0));
+    TRY(cudaEventCreate(&e1));
+    SmoothChoice best;
+    best.us = 1e30f;
+    for (const SmoothChoice& c : cand) {
+        if (!choice_usable(h, c, sizeof(T))) continue;
+        T* cur = u;
+        cudaError_t e = smooth<T>(V, cur, partner, u, b, h->cfg.nu1, 0, c, st);   // warm
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; r++) e = smooth<T>(V, cur, partner, u, b, h->cfg.nu1, 0, c, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return set_cuda_error(&h->err, e, "smoother tuning");
+        }
+        const float us = ms * 1000.0f / 3.0f;
+        if (us < best.us) {
+            best = c;
+            best.us = us;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tune[key] = best;
+    return LASTO_OK;
+}
 
 // First level run by the one-block bottom kernel (its correction starts at zero, so not
 // level 0), or -1 when every level is launched separately.  FP32 only: one SM's FP64 units
@@ -298,18 +428,17 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
         }
         return LASTO_OK;
     }
-    for (int it = 0; it < nu1; it++) {
-        TRY(launch_rbgs<T>(V, u, b, 0, s));
-        TRY(launch_rbgs<T>(V, u, b, 1, s));
-    }
+    const SmoothChoice ch = smooth_choice<T>(h, S);
+    T* cur = u;   // fused passes move the iterate between u and the partner array
+    TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu1, 0, ch, s));
     LevelStore& C = P.lv[l + 1];
     const LevelT<T> VC = Arr<T>::view(C);
     if (sizeof(T) == 4) {
         // FP32: form the 27 fine residuals inside the restriction (cheaper than a pass)
-        TRY(launch_resid_restrict<T>(V, VC, u, b, Arr<T>::b(C), Arr<T>::u(C), s));
+        TRY(launch_resid_restrict<T>(V, VC, cur, b, Arr<T>::b(C), Arr<T>::u(C), s));
     } else {
         // FP64: each residual once (FP64 arithmetic, not bandwidth, bounds this chip)
-        TRY(launch_residual<T>(V, u, b, r, s));
+        TRY(launch_residual<T>(V, cur, b, r, s));
         TRY(launch_restrict<T>(V, VC, r, Arr<T>::b(C), s));
         TRY(cudaMemsetAsync(Arr<T>::u(C), 0, sizeof(T) * C.N(), s));
     }
@@ -319,11 +448,9 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
         st = enqueue_cycle<T>(h, P, l + 1, Arr<T>::u(C), Arr<T>::b(C), Arr<T>::r(C), false, sym, s);
         if (st) return st;
     }
-    TRY(launch_prolong_add<T>(V, VC, Arr<T>::u(C), u, s));
-    for (int it = 0; it < nu2; it++) {
-        TRY(launch_rbgs<T>(V, u, b, sym ? 1 : 0, s));
-        TRY(launch_rbgs<T>(V, u, b, sym ? 0 : 1, s));
-    }
+    TRY(launch_prolong_add<T>(V, VC, Arr<T>::u(C), cur, s));
+    TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu2, sym ? 1 : 0, ch, s));
+    if (cur != u) return fail(h, LASTO_ERR_INVALID_ARG, "smoother passes do not return to the level array");
     return LASTO_OK;
 }
 
@@ -469,6 +596,30 @@ int enqueue_guess_out(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl,
 bool is_defect_correction(const lasto_poisson* h)
 {
     return h->cfg.precision == LASTO_PREC_MIXED && h->cfg.cycle == LASTO_CYCLE_PCG;
+}
+
+// Measure the smoother choices of every level the cycle smooths with separate launches
+// (outside any capture, once per level shape and precision; the table is kept in the handle).
+int tune_plans(lasto_poisson* h, const lasto_cluster* cls, int nc, cudaStream_t s)
+{
+    const bool f32 = is_defect_correction(h);   // FP32 cycles run only inside defect correction
+    for (int c = 0; c < nc; c++) {
+        ClusterPlan& P = h->plans[c];
+        int last = P.L - 2;
+        if (f32) {
+            const int bl = bottom_level(P);
+            if (bl > 0) last = bl - 1;
+        }
+        bool need = false;
+        for (int l = 0; l <= last; l++)
+            need = need || !h->tune.count({P.lv[l].n[0], P.lv[l].n[1], P.lv[l].n[2], f32 ? 4 : 8});
+        if (!need) continue;
+        int st = enqueue_setup(h, P, cls[c], s);   // the level's own coefficients
+        if (st) return st;
+        for (int l = 0; l <= last && !st; l++) st = f32 ? tune_level<float>(h, P.lv[l], s) : tune_level<double>(h, P.lv[l], s);
+        if (st) return st;
+    }
+    return LASTO_OK;
 }
 
 // Prologue of the iteration: ||b_eff||, control block, F-cycle, starting residual.
@@ -765,6 +916,7 @@ static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
     for (int c = 0; c < nc; c++)
         if (!carve_cluster(cv, cls[c].n, cls[c].n_atoms, h->plans[c]))
             return fail(h, LASTO_ERR_NO_MEMORY, "workspace too small for this batch");
+    if (int st = tune_plans(h, cls, nc, s)) return st;
     size_t atom_off = 0, grid_off = 0;
     const int nguess = plan_guesses(h, cls, nc, guess);
     for (int c = 0; c < nc; c++) {
@@ -928,6 +1080,51 @@ int lasto_poisson_kernel_counts(const lasto_poisson* h, int* fixed, int* per_ite
     return LASTO_OK;
 }
 
+int lasto_poisson_tune_table(const lasto_poisson* h, char* buf, size_t cap)
+{
+    if (!h) return -1;
+    std::string out;
+    char line[160];
+    for (const auto& kv : h->tune) {
+        const SmoothChoice& c = kv.second;
+        std::snprintf(line, sizeof(line), "%d %d %d %d %d %d %d %d %d %d %.3f\n", kv.first[0], kv.first[1], kv.first[2],
+                      kv.first[3], c.fused, c.nt, c.sh.tx, c.sh.ty, c.sh.kz, c.sh.ns, (double)c.us);
+        out += line;
+    }
+    if (buf && cap > 0) {
+        const size_t n = std::min(cap - 1, out.size());
+        std::memcpy(buf, out.data(), n);
+        buf[n] = '\0';
+    }
+    return (int)out.size();
+}
+
+int lasto_poisson_set_tune_table(lasto_poisson* h, const char* text)
+{
+    if (!h || !text) return LASTO_ERR_INVALID_ARG;
+    std::map<std::array<int, 4>, SmoothChoice> add;
+    const char* p = text;
+    for (;;) {
+        while (*p == ' ' || *p == '\n' || *p == '\r' || *p == '\t') p++;
+        if (!*p) break;
+        std::array<int, 4> k{};
+        SmoothChoice c;
+        double us = 0.0;
+        int used = 0;
+        const int got = std::sscanf(p, "%d %d %d %d %d %d %d %d %d %d %lf%n", &k[0], &k[1], &k[2], &k[3], &c.fused,
+                                    &c.nt, &c.sh.tx, &c.sh.ty, &c.sh.kz, &c.sh.ns, &us, &used);
+        if (got < 11 || used <= 0) return fail(h, LASTO_ERR_INVALID_ARG, "tune table line");
+        c.us = (float)us;
+        if ((k[3] != 4 && k[3] != 8) || !choice_usable(h, c, (size_t)k[3]))
+            return fail(h, LASTO_ERR_INVALID_ARG, "tune table entry");
+        add[k] = c;
+        p += used;
+    }
+    for (const auto& kv : add) h->tune[kv.first] = kv.second;
+    h->key.clear();   // recapture with the new choices
+    return LASTO_OK;
+}
+
 size_t lasto_guess_param_count(void) { return guess_param_count(); }
 
 int lasto_poisson_set_guess(lasto_poisson* h, const float* params, size_t n_params, const double scales[4])
@@ -992,7 +1189,9 @@ int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
             if (!carve_cluster(cv, cls[c].n, cls[c].n_atoms, h->plans[c]))
                 return fail(h, LASTO_ERR_NO_MEMORY, "workspace too small for this batch");
         h->key.clear();
-        int st = capture_solve(h, cls, nc, v_lm, potential, guess);
+        int st = tune_plans(h, cls, nc, s);
+        if (st) return st;
+        st = capture_solve(h, cls, nc, v_lm, potential, guess);
         if (st) return st;
         h->key = key;
         h->n_clusters = nc;

@@ -8,9 +8,10 @@
 // K-major core-matrix layout: 8 rows x 16 bytes per core matrix, the two K halves 128 bytes
 // apart (leading byte offset), consecutive 8-row groups 256 bytes apart (stride byte
 // offset).  B (cout x 16 per step) is stored in global memory already in that layout (packed
-// once per weight set) and copied in.  Four shared stages form a ring: one thread issues the
-// MMA of a stage and commits it to the stage's mbarrier, which releases the stage for the
-// gather four steps later.  After the last step every thread reads its node's row of the
+// once per weight set) and copied in.  Both arrive by cp.async (16-byte copies, zero-filled
+// outside the grid) three steps ahead of their MMA, in a ring of five shared stages: one
+// thread issues the MMA of a stage and commits it to the stage's mbarrier, which releases the
+// stage for the copies of the step five later.  After the last step every thread reads its node's row of the
 // accumulator (tcgen05.ld 32x32b: warp w owns tensor-memory lanes 32w .. 32w+31) and applies
 // bias, ReLU and the output conversions.  Every mbarrier wait is bounded: on a timeout the
 // kernel records an error, stops issuing, frees its tensor memory and returns.
@@ -24,7 +25,8 @@ namespace tc {
 typedef __nv_bfloat16 bf16;
 
 constexpr int TC_M = 128;        // nodes per CTA (MMA M), one per thread
-constexpr int TC_STAGES = 4;
+constexpr int TC_STAGES = 5;
+constexpr int TC_AHEAD = 3;      // steps whose operand copies are in flight
 constexpr long long TC_SPIN_LIMIT = 1LL << 20;
 
 struct Grid {
@@ -137,30 +139,43 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(Grid g, int cin, const bf16* _
     const int m8 = tid >> 3, rr = tid & 7;
     const int offA0 = (m8 * 2 + 0) * 128 + rr * 16, offA1 = (m8 * 2 + 1) * 128 + rr * 16;
 
-    for (int kc = 0; kc < nk; kc++) {
-        const int s = kc % TC_STAGES;
-        if (kc >= TC_STAGES) {   // the MMA that last read this stage must be complete
-            if (!mbar_wait(smem_u32(&mbar[s]), (uint32_t)((kc / TC_STAGES - 1) & 1))) abort_flag = 1;
+    // issue the copies of step k into its stage (after the MMA that last read the stage)
+    auto prefetch = [&](int k) {
+        const int st = k % TC_STAGES;
+        if (k >= TC_STAGES) {
+            if (!mbar_wait(smem_u32(&mbar[st]), (uint32_t)((k / TC_STAGES - 1) & 1))) abort_flag = 1;
         }
-        __syncthreads();
-        if (abort_flag) break;
-        const int tap = tap_a + kc / cpt, c0 = (kc % cpt) * 16;
+        const int tap = tap_a + k / cpt, c0 = (k % cpt) * 16;
         const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
         const int zz = z + dz, y2 = yy + dy, x2 = xx + dx;
-        uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
-        if (live && zz >= 0 && zz < g.D && y2 >= 0 && y2 < g.H && x2 >= 0 && x2 < g.W) {
-            const size_t nbn = (((size_t)b * g.D + zz) * g.H + y2) * g.W + x2;
-            const uint4* src = reinterpret_cast<const uint4*>(x + nbn * cin + c0);
-            v0 = src[0];
-            v1 = src[1];
-        }
-        *reinterpret_cast<uint4*>(&sA[s][offA0]) = v0;
-        *reinterpret_cast<uint4*>(&sA[s][offA1]) = v1;
+        const bool in = live && zz >= 0 && zz < g.D && y2 >= 0 && y2 < g.H && x2 >= 0 && x2 < g.W;
+        const size_t nbn = in ? (((size_t)b * g.D + zz) * g.H + y2) * g.W + x2 : 0;
+        const bf16* src = x + nbn * cin + c0;
+        const uint32_t n = in ? 16u : 0u;   // 0: the 16 bytes are zero-filled, nothing is read
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(&sA[st][offA0])), "l"(src),
+                     "r"(n)
+                     : "memory");
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(&sA[st][offA1])), "l"(src + 8),
+                     "r"(n)
+                     : "memory");
         const uint4* wsrc = wpk + ((size_t)(tap * cpt + c0 / 16)) * (B_BYTES / 16);
-        for (int t = tid; t < B_BYTES / 16; t += TC_M) reinterpret_cast<uint4*>(sB[s])[t] = wsrc[t];
-        // make the generic-proxy shared stores visible to the tensor core (async proxy)
+        for (int t = tid; t < B_BYTES / 16; t += TC_M)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sB[st] + 16 * t)), "l"(wsrc + t)
+                         : "memory");
+    };
+    for (int k = 0; k < TC_AHEAD; k++) {
+        if (k < nk) prefetch(k);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int kc = 0; kc < nk; kc++) {
+        const int s = kc % TC_STAGES;
+        if (kc + TC_AHEAD < nk) prefetch(kc + TC_AHEAD);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_AHEAD) : "memory");   // step kc's copies have landed
+        // make the shared-memory writes visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
+        if (abort_flag) break;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint64_t ad = make_desc(smem_u32(sA[s])), bd = make_desc(smem_u32(sB[s]));
@@ -174,6 +189,7 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(Grid g, int cin, const bf16* _
                          : "memory");
         }
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     // wait for the last MMA (commits complete in issue order)
     if (!abort_flag && nk > 0) {
         const int s = (nk - 1) % TC_STAGES;

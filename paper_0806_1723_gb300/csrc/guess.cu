@@ -92,6 +92,8 @@ struct GuessNet {
     float *x32, *e1, *cat1, *pred, *p1, *e2, *cat2, *d2, *p2, *e3, *cat3, *d3, *p3, *bt;
     float* scratch = nullptr;   // tap-group partial sums of the small-grid convolutions
     size_t scratch_floats = 0;
+    void* wtmp = nullptr;       // BF16 weights of one layer before packing
+    int* err = nullptr;         // tensor-core wait timeouts
     void *x16, *a0, *b0, *cat1h, *p1h, *a1, *cat2h, *p2h, *a2, *cat3h, *p3h, *a3;
 };
 
@@ -122,7 +124,7 @@ int guess_net_create(const float* params, size_t n_params, const double scales[4
     for (int q = 0; q < 4; q++) g->scales[q] = (float)scales[q];
     // one pool: FP32 weights staging, BF16 weights, biases, activations
     const size_t nb = (size_t)nbmax, N0 = nb * g->Ng[0], N1 = nb * g->Ng[1], N2 = nb * g->Ng[2], N3 = nb * g->Ng[3];
-    size_t f32 = n_params, b16 = 0;
+    size_t f32 = n_params + 64, b16 = (size_t)27 * 128 * 64;
     for (int l = 0; l < NL; l++) b16 += (size_t)27 * L_CIN[l] * L_COUT[l];
     f32 += N0 * (16 + 16 + 48 + 16) + N1 * (16 + 32 + 96 + 32) + N2 * (32 + 64 + 128 + 64) + N3 * (64 + 64);
     b16 += N0 * (16 + 16 + 16 + 48) + N1 * (16 + 32 + 96) + N2 * (32 + 64 + 128) + N3 * (64 + 64);
@@ -153,11 +155,17 @@ int guess_net_create(const float* params, size_t n_params, const double scales[4
     g->p2h = H(N2 * 32); g->a2 = H(N2 * 64); g->cat3h = H(N2 * 128);
     g->p3h = H(N3 * 64); g->a3 = H(N3 * 64);
     g->scratch = F(g->scratch_floats);
+    g->wtmp = H((size_t)27 * 128 * 64);
+    g->err = (int*)take(256);
     cudaError_t e = cudaMemcpyAsync(staging, params, n_params * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->err, 0, sizeof(int), s);
     size_t off = 0;
     for (int l = 0; l < NL && e == cudaSuccess; l++) {
         const size_t nw = (size_t)27 * L_CIN[l] * L_COUT[l];
-        if (lasto_nn_to_bf16(nw, staging + off, g->w16[l], s) != LASTO_OK) e = cudaErrorLaunchFailure;
+        // BF16 weights of the layer, packed into the per-step operand tiles the tensor-core
+        // convolution reads
+        if (lasto_nn_to_bf16(nw, staging + off, g->wtmp, s) != LASTO_OK) e = cudaErrorLaunchFailure;
+        if (e == cudaSuccess) e = launch_pack_weights(L_CIN[l], L_COUT[l], g->wtmp, g->w16[l], s);
         off += nw;
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(g->bias[l], staging + off, (size_t)L_COUT[l] * 4, cudaMemcpyDeviceToDevice, s);
@@ -177,8 +185,8 @@ const float* guess_net_prediction(GuessNet* g, int k) { return g->pred + (size_t
 int guess_net_capacity(const GuessNet* g) { return g ? g->nbmax : 0; }
 const float* guess_net_scales(const GuessNet* g) { return g->scales; }
 
-// Forward pass over grids 0 .. nb-1 of the feature buffer; the prediction is channel 0 of
-// pred ([node][16]).  31 launches.
+// Forward pass over grids 0 .. nb-1 of the feature buffer on the tcgen05 convolution; the
+// prediction is channel 0 of pred ([node][16]).
 int guess_net_forward(GuessNet* g, int nb, cudaStream_t s)
 {
     if (nb < 1 || nb > g->nbmax) return LASTO_ERR_INVALID_ARG;
@@ -188,8 +196,8 @@ int guess_net_forward(GuessNet* g, int nb, cudaStream_t s)
     int st = LASTO_OK;
     auto conv = [&](int l, int lv, const void* x, float* y32, int ldy32, int off32, void* y16, int ldy16, int off16) {
         if (st) return;
-        st = conv_fwd(nb, dim[lv], L_CIN[l], L_COUT[l], x, g->w16[l], g->bias[l], L_RELU[l], y32, ldy32, off32, y16,
-                      ldy16, off16, g->scratch, g->scratch_floats, s);
+        st = conv_fwd_tc(nb, dim[lv], L_CIN[l], L_COUT[l], x, g->w16[l], g->bias[l], L_RELU[l], y32, ldy32, off32, y16,
+                         ldy16, off16, g->scratch, g->scratch_floats, g->err, s);
     };
     auto tobf = [&](size_t n, const float* a, void* b) {
         if (!st) st = lasto_nn_to_bf16(n, a, b, s);

@@ -100,6 +100,7 @@ struct LevelStore {
     int n[3];
     double* inv_diag;   // FP64 [N]
     double *u, *b, *r;  // FP64 work arrays (level 0: u unused by the preconditioner)
+    double* u2;         // FP64 partner of the fused smoother passes (FP32 levels use r32)
     float *u32, *b32, *r32;
     size_t N() const { return (size_t)n[0] * n[1] * n[2]; }
     LevelT<double> view64() const;
@@ -130,7 +131,7 @@ cudaError_t launch_coarse_eig(const LevelStore& L, CoarseEig* eig, cudaStream_t 
 
 // mg.cu
 template <typename T>
-cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s);
+cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt = 256);
 template <typename T>
 cudaError_t launch_residual(const LevelT<T>& L, const T* u, const T* b, T* r, cudaStream_t s);
 template <typename T>

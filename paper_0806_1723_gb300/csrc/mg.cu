@@ -56,10 +56,10 @@ __device__ __forceinline__ T dsum(const LevelT<T>& L, int i, int j, int k)
 
 // ---------------------------------------------------------------- smoother
 template <typename T>
-__global__ void __launch_bounds__(NT) k_rbgs(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour,
-                                            size_t nhalf)
+__global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour,
+                                             size_t nhalf)
 {
-    const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (t >= nhalf) return;
     const size_t P = 2 * t + colour;
     int i, j, k;
@@ -74,11 +74,12 @@ __global__ void __launch_bounds__(NT) k_rbgs(LevelT<T> L, T* __restrict__ u, con
 }
 
 template <typename T>
-cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s)
+cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt)
 {
+    if (nt < 32 || nt > 512 || nt % 32) return cudaErrorInvalidValue;
     const size_t N = L.N();
     const size_t nhalf = (N + 1 - colour) / 2;
-    k_rbgs<T><<<(unsigned)((nhalf + NT - 1) / NT), NT, 0, s>>>(L, u, b, colour, nhalf);
+    k_rbgs<T><<<(unsigned)((nhalf + nt - 1) / nt), nt, 0, s>>>(L, u, b, colour, nhalf);
     return cudaGetLastError();
 }
 
@@ -954,7 +955,7 @@ cudaError_t launch_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter,
     template cudaError_t launch_resid_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, const T*, T*, T*, \
                                                   cudaStream_t);                                             \
     template cudaError_t launch_bottom<T>(const BottomArgs<T>&, cudaStream_t);                              \
-    template cudaError_t launch_rbgs<T>(const LevelT<T>&, T*, const T*, int, cudaStream_t);                 \
+    template cudaError_t launch_rbgs<T>(const LevelT<T>&, T*, const T*, int, cudaStream_t, int);               \
     template cudaError_t launch_residual<T>(const LevelT<T>&, const T*, const T*, T*, cudaStream_t);        \
     template cudaError_t launch_apply<T>(const LevelT<T>&, const T*, T*, cudaStream_t);                     \
     template cudaError_t launch_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, T*, cudaStream_t); \

@@ -186,3 +186,50 @@ def test_batch_of_uneven_clusters(orc, precision):
             assert s.status == 0 and s.rel_resid <= 1e-10, (c.name, s.status, s.rel_resid)
             assert np.abs(got[off:off + c.n_atoms] - ref).max() <= 1e-8 * np.abs(ref).max(), c.name
             off += c.n_atoms
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_smoother_tuning_and_forced_choices(precision):
+    """The first solve measures the smoother of every level the cycle smooths with separate
+    launches; whatever the table says (in-place half sweeps, fused register-column passes,
+    fused two-sweep z-slab passes) the converged solution is bitwise the same."""
+    B = need_gpu()
+    import torch
+    prec = B.LASTO_PREC_MIXED if precision == "mixed" else B.LASTO_PREC_FP64
+    cl = synth.pd13_small(n=65)
+    dc = B.DeviceCluster(cl)
+    auto = B.Poisson(n_max=65, max_atoms=13, precision=prec)
+    v_auto = torch.empty((13, 25), dtype=torch.float64, device="cuda")
+    st = auto.solve(dc, v_auto)[0]
+    torch.cuda.synchronize()
+    assert st.status == 0
+    rows = [line.split() for line in auto.tune_table().strip().splitlines()]
+    elem = 4 if precision == "mixed" else 8
+    shapes = sorted({tuple(int(v) for v in r[:3]) for r in rows if int(r[3]) == elem})
+    assert (65, 65, 65) in shapes and (33, 33, 33) in shapes
+    col_ty = 14 if elem == 4 else 6
+    forms = {"inplace": "0 256 0 0 0 0", "column": f"1 256 62 {col_ty} 32 1", "slab": "1 256 64 16 32 2"}
+    out = {}
+    for name, choice in forms.items():
+        solver = B.Poisson(n_max=65, max_atoms=13, precision=prec)
+        solver.set_tune_table("\n".join(f"{a} {b} {c} {elem} {choice} 0" for a, b, c in shapes) + "\n")
+        v = torch.empty((13, 25), dtype=torch.float64, device="cuda")
+        s = solver.solve(dc, v)[0]
+        torch.cuda.synchronize()
+        assert s.status == 0 and s.rel_resid <= 1e-10
+        out[name] = (v.clone(), s.cycles)
+        assert all(line.split()[4:10] == choice.split() for line in solver.tune_table().strip().splitlines()
+                   if int(line.split()[3]) == elem and tuple(int(x) for x in line.split()[:3]) in shapes)
+    assert torch.equal(out["inplace"][0], out["column"][0]) and torch.equal(out["inplace"][0], out["slab"][0])
+    assert out["inplace"][1] == out["column"][1] == out["slab"][1]
+    assert torch.equal(out["inplace"][0], v_auto)
+
+
+def test_tune_table_rejects_bad_lines():
+    B = need_gpu()
+    solver = B.Poisson(n_max=65, max_atoms=13, precision=B.LASTO_PREC_MIXED)
+    for bad in ("65 65 65 4 1 256 62 14 32 3 0\n", "not a table\n", "65 65 65 2 0 256 0 0 0 0 0\n",
+                "65 65 65 4 0 100 0 0 0 0 0\n"):
+        with pytest.raises(RuntimeError, match="INVALID_ARG"):
+            solver.set_tune_table(bad)
+    solver.set_tune_table("\n  \n")   # empty is fine
