@@ -203,18 +203,27 @@ __global__ void __launch_bounds__(TC_M) k_conv_tc(Grid g, int cin, const bf16* _
 #pragma unroll
         for (int c = 0; c < COUT; c += 16) tmem_ld16(lane_base + (uint32_t)c, acc + c);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-        if (live) {
-            if (part) {
-                float* dst = part + ((size_t)blockIdx.y * N + node) * COUT;
+        // the accumulator rows leave through shared memory, 16 channels at a time, so that
+        // consecutive threads store consecutive addresses (the A ring is idle now)
+        float* stage = reinterpret_cast<float*>(&sA[0][0]);   // [TC_M][17]
 #pragma unroll
-                for (int c = 0; c < COUT; c++) dst[c] = acc[c];
-            } else {
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            __syncthreads();
 #pragma unroll
-                for (int c = 0; c < COUT; c++) {
-                    float v = acc[c] + (bias ? bias[c] : 0.0f);
+            for (int j = 0; j < 16; j++) stage[tid * 17 + j] = acc[c0 + j];
+            __syncthreads();
+            for (int e = tid; e < TC_M * 16; e += TC_M) {
+                const int r = e >> 4, j = e & 15, c = c0 + j;
+                const size_t nd = node0 + r;
+                if (nd >= N) continue;
+                const float a = stage[r * 17 + j];
+                if (part) {
+                    part[((size_t)blockIdx.y * N + nd) * COUT + c] = a;
+                } else {
+                    float v = a + (bias ? bias[c] : 0.0f);
                     if (relu) v = fmaxf(v, 0.0f);
-                    if (y32) y32[node * ldy32 + off32 + c] = v;
-                    if (y16) y16[node * ldy16 + off16 + c] = __float2bfloat16(v);
+                    if (y32) y32[nd * ldy32 + off32 + c] = v;
+                    if (y16) y16[nd * ldy16 + off16 + c] = __float2bfloat16(v);
                 }
             }
         }

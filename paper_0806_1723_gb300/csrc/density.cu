@@ -298,6 +298,7 @@ __global__ void k_deposit_df(DepArgs a);
 constexpr int SA = 14;  // x y z R^2 W0 W1 W2 A0 A1 A2 B0 B1 B2 R
 constexpr int DEP_NT = 256;
 constexpr double EXP_CUT = 40.0;   // e^{-40} * max W < 1e-14 absolute; skipped terms are below FP64 rounding of n_e
+constexpr float FAR_T = 20.0f;     // FP32-pair deposit: Slater terms with zeta r > 20 in plain FP32
 
 __device__ __forceinline__ double nonspherical(const double* __restrict__ c, double dx, double dy, double dz,
                                                double r, double R, double z1)
@@ -477,11 +478,28 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     }
     const float cut = EXP_CUT / zmin;
     const float cut2 = cut * cut * (1.0f + 1e-5f);
+    // beyond zeta_min r = FAR_T every Slater term is below e^-20 of its weight: plain FP32
+    // (relative error ~1e-7 of terms that small is ~1e-16 of the node's density scale)
+    const float far = FAR_T / zmin;
+    const float far2 = far * far * (1.0f + 1e-4f);
     df s = {0.0f, 0.0f};
     int own = -1;
     df orr2 = {0.0f, 0.0f}, odx = s, ody = s, odz = s;
     for (int t = 0; t < a.na; t++) {
         const float* o = sat + SAF * t;
+        const float fx = (px.h - o[0]) + (px.l - o[1]), fy = (py.h - o[2]) + (py.l - o[3]);
+        const float fz = (pz.h - o[4]) + (pz.l - o[5]);
+        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+        if (r2f > cut2) continue;
+        if (r2f > far2) {
+            const float rf = sqrtf(r2f);
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                const float e = zt[q].h * rf;
+                if (e < EXP_CUT) s = dfa::add_f(s, o[6 + 2 * q] * expf(-e));
+            }
+            continue;
+        }
         const df dx = dfa::add(px, df{-o[0], -o[1]});
         const df dy = dfa::add(py, df{-o[2], -o[3]});
         const df dz = dfa::add(pz, df{-o[4], -o[5]});
@@ -502,7 +520,11 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
 #pragma unroll
         for (int q = 0; q < 3; q++) {
             const df tq = dfa::mul(r, zt[q]);
-            if (tq.h < EXP_CUT) s = dfa::add(s, dfa::mul(df{o[6 + 2 * q], o[7 + 2 * q]}, dfa::exp_neg(tq, th, tl)));
+            if (tq.h >= EXP_CUT) continue;
+            if (tq.h > FAR_T)
+                s = dfa::add_f(s, o[6 + 2 * q] * expf(-tq.h));
+            else
+                s = dfa::add(s, dfa::mul(df{o[6 + 2 * q], o[7 + 2 * q]}, dfa::exp_neg(tq, th, tl)));
         }
     }
     if (own >= 0) {
