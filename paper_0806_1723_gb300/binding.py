@@ -205,7 +205,7 @@ class Poisson:
     """Owns one ``lasto_poisson`` handle."""
 
     def __init__(self, n_max=129, max_atoms=561, max_batch=1, precision=LASTO_PREC_FP64, cycle=LASTO_CYCLE_PCG,
-                 nu1=2, nu2=2, max_cycles=50, rel_tol=1e-10, n_theta=16, n_phi=32, launch=0):
+                 nu1=4, nu2=4, max_cycles=50, rel_tol=1e-10, n_theta=16, n_phi=32, launch=0):
         L = load()
         cfg = lasto_config_default()
         cfg.n_max, cfg.max_atoms, cfg.max_batch = n_max, max_atoms, max_batch

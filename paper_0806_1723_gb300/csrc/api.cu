@@ -980,8 +980,8 @@ void lasto_config_default(lasto_config* c)
     c->max_batch = 1;
     c->precision = LASTO_PREC_FP64;
     c->cycle = LASTO_CYCLE_PCG;
-    c->nu1 = 2;
-    c->nu2 = 2;
+    c->nu1 = 4;
+    c->nu2 = 4;
     c->max_cycles = 50;
     c->rel_tol = 1e-10;
     c->n_theta = 16;
