@@ -69,6 +69,9 @@ def _declare(L):
         "or_mg_solve": (i, [i, i, i, _D, _D, _D, _D, _D, i, i, i, d, i, _D, _I]),
         "or_project": (i, [i, i, i, _D, _D, _D, _D, i, _D, _D, i, i, _D]),
         "or_poisson_solve": (i, [i, _D, _D, _D, _D, _D, _D, _D, _I, d, _D, _D, _D, _D]),
+        "or_radial_mesh": (None, [i, d, d, _D]),
+        "or_sphere_density": (i, [i, _D, _D, _D, _D, _D, i, d, i, i, _D]),
+        "or_inner_solve": (i, [i, _D, _D, i, d, _D, _D, _D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -248,6 +251,33 @@ def project(x, y, z, u, pos, R, n_theta=16, n_phi=32):
     if st != OK:
         raise ValueError(f"project status {st}")
     return vlm
+
+
+def radial_mesh(n, r_min, R):
+    """Logarithmic radial mesh of a sphere (Section 4: 429 points; last point on the sphere)."""
+    r = np.zeros(n)
+    lib().or_radial_mesh(n, r_min, R, _p(r))
+    return r
+
+
+def sphere_density(cl, n_rad=429, r_min=1e-5, n_theta=16, n_phi=32):
+    """rho_LM(r_j) [na][25][n_rad] by the surface projection of Eq. 3.7 at each radius."""
+    out = np.zeros((cl.n_atoms, 25, n_rad))
+    st = lib().or_sphere_density(cl.n_atoms, _p(_f64(cl.pos)), _p(_f64(cl.R)), _p(_f64(cl.slater_w)),
+                                 _p(_f64(cl.slater_zeta)), _p(_f64(cl.c_lm)), n_rad, r_min, n_theta, n_phi, _p(out))
+    if st != OK:
+        raise ValueError(f"sphere_density status {st}")
+    return out
+
+
+def inner_solve(R, Z, rho_lm, v_R, r_min=1e-5):
+    """V_LM(r_j) [na][25][n_rad] inside each sphere (Eq. 3.4 with the Green's form of Eq. 3.5)."""
+    R, Z, rho_lm, v_R = _f64(R), _f64(Z), _f64(rho_lm), _f64(v_R)
+    v = np.zeros_like(rho_lm)
+    st = lib().or_inner_solve(len(R), _p(R), _p(Z), rho_lm.shape[2], r_min, _p(rho_lm), _p(v_R), _p(v))
+    if st != OK:
+        raise ValueError(f"inner_solve status {st}")
+    return v
 
 
 def poisson_solve(cl, nu1=2, nu2=2, n_f=1, tol=1e-13, max_cycles=60, n_theta=16, n_phi=32, want_u=False):

@@ -864,3 +864,109 @@ int or_poisson_solve(int na, const double* pos, const double* Z, const double* R
     for (int a = 0; a < 3; a++) free(ax[a]);
     return st;
 }
+
+/* ------------------------------------------------------------------ inside the spheres */
+/* Logarithmic radial mesh of a sphere (the paper: "logarithmic, 429 points"; reading: the
+ * last point on the sphere, the first at r_min):  r_j = R exp((j - (n-1)) dx),
+ * dx = ln(R / r_min) / (n - 1). */
+void or_radial_mesh(int n, double r_min, double R, double* r)
+{
+    const double dx = log(R / r_min) / (n - 1);
+    for (int j = 0; j < n; j++) r[j] = R * exp((j - (n - 1)) * dx);
+    r[n - 1] = R;
+}
+
+/* rho_LM(r_j) of atom a: Eq. 3.7's surface projection taken on the sphere of radius r_j about
+ * the atom, sum_q w_q n_e(X_a + r_j u_q) y_LM(u_q), with the projection's n_theta-point
+ * Gauss-Legendre x n_phi uniform rule.  out [na][25][n_rad]. */
+int or_sphere_density(int na, const double* pos, const double* R, const double* w, const double* zeta,
+                      const double* clm, int n_rad, double r_min, int n_theta, int n_phi, double* out)
+{
+    if (n_rad < 4 || !(r_min > 0.0)) return OR_INVALID_ARG;
+    double* t = malloc(sizeof(double) * n_theta);
+    double* wt = malloc(sizeof(double) * n_theta);
+    or_gauss_legendre(n_theta, t, wt);
+#pragma omp parallel for schedule(dynamic)
+    for (int a = 0; a < na; a++) {
+        double* rr = malloc(sizeof(double) * n_rad);
+        or_radial_mesh(n_rad, r_min, R[a], rr);
+        for (int j = 0; j < n_rad; j++) {
+            double acc[25] = {0};
+            for (int it = 0; it < n_theta; it++) {
+                const double ct = t[it], stt = sqrt(1.0 - ct * ct);
+                for (int ip = 0; ip < n_phi; ip++) {
+                    const double ph = 2.0 * PI * ip / n_phi;
+                    const double ux = stt * cos(ph), uy = stt * sin(ph), uz = ct;
+                    const double rho = or_density(na, pos, R, w, zeta, clm, pos[3 * a] + rr[j] * ux,
+                                                  pos[3 * a + 1] + rr[j] * uy, pos[3 * a + 2] + rr[j] * uz);
+                    double S[25];
+                    or_solid_harmonics(ux, uy, uz, S);
+                    const double wq = wt[it] * 2.0 * PI / n_phi;
+                    for (int lm = 0; lm < 25; lm++) acc[lm] += wq * rho * S[lm];
+                }
+            }
+            for (int lm = 0; lm < 25; lm++) out[((size_t)a * 25 + lm) * n_rad + j] = acc[lm];
+        }
+        free(rr);
+    }
+    free(t); free(wt);
+    return OR_OK;
+}
+
+/* integral of g over [x_j, x_{j+1}] on a uniform grid (step h, n >= 4 points): the cubic
+ * through the four nearest samples */
+static double seg_integral(const double* g, int n, int j, double h)
+{
+    if (j == 0) return h / 24.0 * (9.0 * g[0] + 19.0 * g[1] - 5.0 * g[2] + g[3]);
+    if (j == n - 2) return h / 24.0 * (g[n - 4] - 5.0 * g[n - 3] + 19.0 * g[n - 2] + 9.0 * g[n - 1]);
+    return h / 24.0 * (-g[j - 1] + 13.0 * g[j] + 13.0 * g[j + 1] - g[j + 2]);
+}
+
+/* Inner Dirichlet problem of sphere a (Eq. 3.4 with the boundary values of Eq. 3.6), in the
+ * Green's-function form of Eq. 3.5:
+ *   V_LM(r) = V_LM(R) (r/R)^L
+ *           - 4pi/(2L+1) [ r^-(L+1) int_0^r rho_LM r'^(L+2) dr' + r^L int_r^R rho_LM r'^(1-L) dr'
+ *                          - r^L R^-(2L+1) int_0^R rho_LM r'^(L+2) dr' ]
+ *           + delta_L0 sqrt(4pi) Z (1/r - 1/R),
+ * which solves (d2/dr2 + (2/r) d/dr - L(L+1)/r^2) V_LM = 4pi (rho_LM - delta_L0 Z delta) with
+ * V_LM(R) given (reading of Eq. 3.5: its printed integrands are rho r^(L+2) and rho r^(1-L),
+ * and its overall sign is the one that satisfies Eq. 3.4).  Integrals in x = ln r
+ * (dr = r dx) with the cubic rule; on [0, r_0] rho is taken constant.  rho_lm, v: [na][25][n_rad];
+ * v_R: [na][25]. */
+int or_inner_solve(int na, const double* R, const double* Z, int n_rad, double r_min, const double* rho_lm,
+                   const double* v_R, double* v)
+{
+    if (n_rad < 4 || !(r_min > 0.0)) return OR_INVALID_ARG;
+    double* r = malloc(sizeof(double) * n_rad);
+    double* g1 = malloc(sizeof(double) * n_rad);
+    double* g2 = malloc(sizeof(double) * n_rad);
+    double* I1 = malloc(sizeof(double) * n_rad);
+    double* I2 = malloc(sizeof(double) * n_rad);
+    for (int a = 0; a < na; a++) {
+        or_radial_mesh(n_rad, r_min, R[a], r);
+        const double h = log(R[a] / r_min) / (n_rad - 1);
+        for (int lm = 0; lm < 25; lm++) {
+            const int L = l_of(lm);
+            const double* rho = rho_lm + ((size_t)a * 25 + lm) * n_rad;
+            for (int j = 0; j < n_rad; j++) {
+                g1[j] = rho[j] * pow(r[j], L + 2) * r[j];
+                g2[j] = rho[j] * pow(r[j], 1 - L) * r[j];
+            }
+            I1[0] = rho[0] * pow(r[0], L + 3) / (L + 3);
+            for (int j = 0; j + 1 < n_rad; j++) I1[j + 1] = I1[j] + seg_integral(g1, n_rad, j, h);
+            I2[n_rad - 1] = 0.0;
+            for (int j = n_rad - 2; j >= 0; j--) I2[j] = I2[j + 1] + seg_integral(g2, n_rad, j, h);
+            const double Ra = R[a], vr = v_R[25 * a + lm];
+            for (int j = 0; j < n_rad; j++) {
+                const double x = r[j] / Ra, rl = pow(r[j], L);
+                double val = vr * pow(x, L) - 4.0 * PI / (2 * L + 1) *
+                                                  (I1[j] / pow(r[j], L + 1) + rl * I2[j] -
+                                                   rl * I1[n_rad - 1] / pow(Ra, 2 * L + 1));
+                if (L == 0) val += sqrt(4.0 * PI) * Z[a] * (1.0 / r[j] - 1.0 / Ra);
+                v[((size_t)a * 25 + lm) * n_rad + j] = val;
+            }
+        }
+    }
+    free(r); free(g1); free(g2); free(I1); free(I2);
+    return OR_OK;
+}

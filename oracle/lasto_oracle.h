@@ -129,6 +129,15 @@ int or_poisson_solve(int na, const double* pos, const double* Z, const double* R
                      const double* zeta, const double* clm, const double* mesh, const int* ctl,
                      double tol, double* vlm, double* u, double* stats, double* hist);
 
+/* Inside the spheres (Section 3, Eq. 3.4-3.7).  Radial mesh r_j = R exp((j-(n-1)) dx),
+ * dx = ln(R/r_min)/(n-1); rho_LM(r_j) by the surface projection of Eq. 3.7 at each radius;
+ * the inner Dirichlet solve of Eq. 3.4 in the Green's-function form of Eq. 3.5. */
+void or_radial_mesh(int n, double r_min, double R, double* r);
+int or_sphere_density(int na, const double* pos, const double* R, const double* w, const double* zeta,
+                      const double* clm, int n_rad, double r_min, int n_theta, int n_phi, double* out);
+int or_inner_solve(int na, const double* R, const double* Z, int n_rad, double r_min, const double* rho_lm,
+                   const double* v_R, double* v);
+
 #ifdef __cplusplus
 }
 #endif
