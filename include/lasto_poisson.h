@@ -137,6 +137,31 @@ typedef struct lasto_poisson lasto_poisson;   /* opaque; owns workspace, plans a
 int lasto_poisson_tune_table(const lasto_poisson* h, char* buf, size_t cap);
 int lasto_poisson_set_tune_table(lasto_poisson* h, const char* text);
 
+/* Inside the atom spheres (Section 3, Eq. 3.4-3.7).  Radial mesh of sphere a (the paper:
+ * logarithmic, 429 points): r_j = R_a exp((j - (n_rad-1)) dx), dx = ln(R_a / r_min)/(n_rad-1),
+ * so r_0 = r_min and r_{n_rad-1} = R_a.
+ *
+ * lasto_op_sphere_density: rho_LM(r_j), the surface projection of Eq. 3.7 on the sphere of
+ * radius r_j about each atom (n_theta-point Gauss-Legendre in cos(theta) x n_phi uniform
+ * phi), of the cluster's electron density (all atoms' Slater shells plus the atom's own
+ * nonspherical part).  rho_lm: device [n_atoms][25][n_rad]; the cluster's arrays and axes
+ * are device arrays as for lasto_poisson_solve (the axes are used for the sphere geometry
+ * check, whose failure sets *status = LASTO_ERR_GEOMETRY).
+ *
+ * lasto_op_inner_solve: the inner Dirichlet problem of Eq. 3.4 with the boundary values
+ * V_LM(R) of Eq. 3.6 (v_R: device [n_atoms][25], as written by lasto_poisson_solve), solved
+ * in the Green's-function form of Eq. 3.5 (read with the overall sign that satisfies Eq. 3.4,
+ * and integrands rho r^(L+2), rho r^(1-L)):
+ *   V_LM(r) = V_LM(R)(r/R)^L - 4pi/(2L+1)[r^-(L+1) I1(r) + r^L I2(r) - r^L R^-(2L+1) I1(R)]
+ *             + delta_L0 sqrt(4pi) Z (1/r - 1/R),
+ * I1(r) = int_0^r rho_LM r'^(L+2) dr', I2(r) = int_r^R rho_LM r'^(1-L) dr', integrated in
+ * ln r (cubic through the four nearest samples per interval; rho constant on [0, r_min]).
+ * R, Z: device [n_atoms]; rho_lm, v: device [n_atoms][25][n_rad], distinct arrays. */
+int lasto_op_sphere_density(const lasto_cluster* cl, int n_rad, double r_min, int n_theta, int n_phi, double* rho_lm,
+                            int* status, void* stream);
+int lasto_op_inner_solve(int n_atoms, const double* R, const double* Z, int n_rad, double r_min, const double* rho_lm,
+                         const double* v_R, double* v, void* stream);
+
 /* Learned initial guess.  The paper has no counterpart: it solves every SCF step from
  * scratch.  A small 3-D U-Net (four levels, 16-32-64-64 channels, 3x3x3 convolutions with
  * BF16 tensor-core products and FP32 accumulation) maps the right-hand side restricted to a

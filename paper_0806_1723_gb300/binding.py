@@ -48,7 +48,7 @@ EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve"
            "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
            "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
-           "lasto_op_project", "lasto_guess_param_count", "lasto_poisson_set_guess",
+           "lasto_op_project", "lasto_op_sphere_density", "lasto_op_inner_solve", "lasto_guess_param_count", "lasto_poisson_set_guess",
            "lasto_poisson_tune_table", "lasto_poisson_set_tune_table", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
            "lasto_nn_relu_grad", "lasto_nn_to_bf16", "lasto_nn_copy_channels", "lasto_nn_down", "lasto_nn_up",
            "lasto_nn_mse", "lasto_nn_adam", "lasto_nn_guess_features", "lasto_nn_guess_grid"]
@@ -91,6 +91,8 @@ def _declare(L):
         "lasto_op_prolong_add": (i, [ip, vp, vp, vp, vp, vp, vp]),
         "lasto_op_coarse_solve": (i, [ip, vp, vp, vp, vp, vp, vp]),
         "lasto_op_project": (i, [ip, vp, vp, vp, vp, i, vp, vp, i, i, vp, vp, vp]),
+        "lasto_op_sphere_density": (i, [clp, i, d, i, i, vp, vp, vp]),
+        "lasto_op_inner_solve": (i, [i, vp, vp, i, d, vp, vp, vp, vp]),
         "lasto_nn_conv3d_fwd": (i, [i, ip, i, i, vp, vp, vp, i, vp, i, i, vp, i, i, vp]),
         "lasto_nn_pack_weights": (i, [i, i, vp, vp, vp]),
         "lasto_nn_conv3d_fwd_tc": (i, [i, ip, i, i, vp, vp, vp, i, vp, i, i, vp, i, i, vp, vp]),
@@ -391,3 +393,21 @@ def lasto_op_project(x, y, z, u, pos, R, n_theta=16, n_phi=32, stream=None):
     _check(load().lasto_op_project(*_axes(x, y, z), _ptr(u), na, _ptr(pos), _ptr(R), int(n_theta), int(n_phi),
                                    _ptr(vlm), _ptr(status), _stream(stream)), "lasto_op_project")
     return vlm, status
+
+
+def lasto_op_sphere_density(dc: DeviceCluster, n_rad=429, r_min=1e-5, n_theta=16, n_phi=32, stream=None):
+    """rho_LM(r_j) [n_atoms][25][n_rad] inside every sphere (Eq. 3.7 at each radius)."""
+    out = torch.empty((dc.n_atoms, 25, n_rad), dtype=torch.float64, device=dc.pos.device)
+    status = torch.zeros(1, dtype=torch.int32, device=dc.pos.device)
+    c = dc.struct()
+    _check(load().lasto_op_sphere_density(ctypes.byref(c), int(n_rad), float(r_min), int(n_theta), int(n_phi),
+                                          _ptr(out), _ptr(status), _stream(stream)), "lasto_op_sphere_density")
+    return out, status
+
+
+def lasto_op_inner_solve(R, Z, rho_lm, v_R, r_min=1e-5, stream=None):
+    """V_LM(r_j) [n_atoms][25][n_rad] inside every sphere (Eq. 3.4-3.5, Dirichlet values v_R)."""
+    v = torch.empty_like(rho_lm)
+    _check(load().lasto_op_inner_solve(int(R.shape[0]), _ptr(R), _ptr(Z), int(rho_lm.shape[2]), float(r_min),
+                                       _ptr(rho_lm), _ptr(v_R), _ptr(v), _stream(stream)), "lasto_op_inner_solve")
+    return v

@@ -1470,4 +1470,39 @@ int lasto_op_project(const int n[3], const double* x, const double* y, const dou
     return op_status(e);
 }
 
+int lasto_op_sphere_density(const lasto_cluster* cl, int n_rad, double r_min, int n_theta, int n_phi, double* rho_lm,
+                            int* status, void* stream)
+{
+    if (!cl || cl->n_atoms < 1 || !cl->pos || !cl->R || !cl->slater_w || !cl->slater_zeta || !cl->c_lm || !cl->x ||
+        !cl->y || !cl->z || !rho_lm || n_rad < 4 || !(r_min > 0.0) || n_theta < 1 || n_theta > 32 || n_phi < 1 ||
+        n_phi > 64)
+        return LASTO_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++)
+        if (cl->n[d] < 5) return LASTO_ERR_INVALID_ARG;
+    init_device_constants();
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nq = n_theta * n_phi;
+    std::vector<double> tab((size_t)nq * 28);
+    host_quadrature(n_theta, n_phi, tab.data());
+    Scratch q(sizeof(double) * tab.size(), s);
+    Scratch rec(sizeof(double) * SPHERE_REC_DOUBLES * (size_t)cl->n_atoms, s);
+    if (!q.p || !rec.p) return LASTO_ERR_NO_MEMORY;
+    cudaError_t e = cudaMemcpyAsync(q.p, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess)
+        e = launch_sphere_params(*cl, cl->x, cl->y, cl->z, rec.as<double>(), nullptr, nullptr, nullptr, nullptr,
+                                 status, s);
+    if (e == cudaSuccess)
+        e = launch_sphere_density(cl->n_atoms, rec.as<double>(), cl->c_lm, q.as<double>(), nq, n_rad, r_min, rho_lm, s);
+    return op_status(e);
+}
+
+int lasto_op_inner_solve(int n_atoms, const double* R, const double* Z, int n_rad, double r_min, const double* rho_lm,
+                         const double* v_R, double* v, void* stream)
+{
+    if (n_atoms < 1 || !R || !Z || n_rad < 4 || !(r_min > 0.0) || !rho_lm || !v_R || !v || rho_lm == v)
+        return LASTO_ERR_INVALID_ARG;
+    return op_status(launch_inner_solve(n_atoms, R, Z, n_rad, r_min, rho_lm, v_R, v, (cudaStream_t)stream));
+}
+
 }  // extern "C"

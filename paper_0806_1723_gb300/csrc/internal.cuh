@@ -221,6 +221,12 @@ cudaError_t launch_multipoles(const int n[3], const double* x, const double* y, 
 cudaError_t launch_boundary_fill(const int n[3], const double* x, const double* y, const double* z, double cx,
                                  double cy, double cz, const double* Q, double* u, cudaStream_t s);
 
+// inner.cu: inside the spheres (Eq. 3.4-3.7)
+cudaError_t launch_sphere_density(int na, const double* rec, const double* clm, const double* quad, int nq,
+                                  int n_rad, double r_min, double* out, cudaStream_t s);
+cudaError_t launch_inner_solve(int na, const double* R, const double* Z, int n_rad, double r_min,
+                               const double* rho_lm, const double* vR, double* v, cudaStream_t s);
+
 // guess.cu: the learned initial guess (a 3-D U-Net on a 33^3 subgrid)
 constexpr int GUESS_N = 33;
 struct GuessNet;
