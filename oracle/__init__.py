@@ -72,6 +72,7 @@ def _declare(L):
         "or_radial_mesh": (None, [i, d, d, _D]),
         "or_sphere_density": (i, [i, _D, _D, _D, _D, _D, i, d, i, i, _D]),
         "or_inner_solve": (i, [i, _D, _D, i, d, _D, _D, _D]),
+        "or_boundary_exact": (None, [i, _D, _D, _D, _D, _D, _D, i, i, i, _D, _D, _D, _D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -253,6 +254,14 @@ def project(x, y, z, u, pos, R, n_theta=16, n_phi=32):
     return vlm
 
 
+def boundary_exact(cl, x, y, z, u=None):
+    """u with its six faces set to the exact superposition of the atoms' potentials."""
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    u = np.zeros((len(z), len(y), len(x))) if u is None else u
+    lib().or_boundary_exact(*_atoms(cl), len(x), len(y), len(z), _p(x), _p(y), _p(z), _p(u))
+    return u
+
+
 def radial_mesh(n, r_min, R):
     """Logarithmic radial mesh of a sphere (Section 4: 429 points; last point on the sphere)."""
     r = np.zeros(n)
@@ -280,11 +289,17 @@ def inner_solve(R, Z, rho_lm, v_R, r_min=1e-5):
     return v
 
 
-def poisson_solve(cl, nu1=2, nu2=2, n_f=1, tol=1e-13, max_cycles=60, n_theta=16, n_phi=32, want_u=False):
-    """The whole step on one cluster.  Returns dict(status, cycles, rel_resid, vlm, hist[, u])."""
+BC = {"multipole": 0, "zero": 1, "exact": 2}
+
+
+def poisson_solve(cl, nu1=2, nu2=2, n_f=1, tol=1e-13, max_cycles=60, n_theta=16, n_phi=32, want_u=False,
+                  bc="multipole"):
+    """The whole step on one cluster.  Returns dict(status, cycles, rel_resid, vlm, hist[, u]).
+    bc: Dirichlet values from the l <= 4 multipole expansion of the grid charge, zero (Eq. 3.3),
+    or the exact superposition of the atoms' potentials."""
     n = cl.n
     meshp = np.array([n, *cl.centre, cl.half_width, cl.h_min, cl.h_max, cl.p_max], dtype=np.float64)
-    ctl = np.array([nu1, nu2, n_f, max_cycles, n_theta, n_phi], dtype=np.int32)
+    ctl = np.array([nu1, nu2, n_f, max_cycles, n_theta, n_phi, BC[bc]], dtype=np.int32)
     vlm = np.zeros((cl.n_atoms, 25))
     u = np.zeros((n, n, n)) if want_u else None
     stats, hist = np.zeros(3), np.zeros(max_cycles + 1)

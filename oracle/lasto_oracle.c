@@ -367,6 +367,58 @@ void or_boundary_fill(int nx, int ny, int nz, const double* x, const double* y, 
             }
 }
 
+/* Exact superposition Dirichlet values (the alternative to Eq. 3.3's zero and to the
+ * truncated multipole expansion): on each face node the continuum potential of the density
+ * model, atom by atom, valid outside every sphere:
+ *   Phi_j(r) = Z_j/r - sum_k w_k [1/r - e^{-zeta_k r}(1/r + zeta_k/2)]
+ *              - sum_{l>=1,m} 4pi/(2l+1) c_lm M_l y_lm(r^) / r^(l+1),
+ * the normalised-exponential potential of each Slater shell and the exterior multipoles of
+ * the atom's nonspherical part, M_l = int_0^R zeta_1^3/(8pi) e^{-zeta_1 r}(1 - r^2/R^2)^2
+ * (r/R)^l r^(l+2) dr (64-point Gauss-Legendre).  Writes only the six faces of u. */
+void or_boundary_exact(int na, const double* pos, const double* Z, const double* R, const double* w,
+                       const double* zeta, const double* clm, int nx, int ny, int nz, const double* x,
+                       const double* y, const double* z, double* u)
+{
+    double* M = malloc(sizeof(double) * 5 * (na > 0 ? na : 1));
+    double t[64], wt[64];
+    or_gauss_legendre(64, t, wt);
+    for (int j = 0; j < na; j++) {
+        const double Rj = R[j], z1 = zeta[3 * j];
+        for (int l = 0; l < 5; l++) {
+            double s = 0.0;
+            for (int q = 0; q < 64; q++) {
+                const double r = 0.5 * Rj * (t[q] + 1.0), tt = 1.0 - r * r / (Rj * Rj);
+                s += 0.5 * Rj * wt[q] * slater(z1, r) * tt * tt * pow(r / Rj, l) * pow(r, l + 2);
+            }
+            M[5 * j + l] = s;
+        }
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < nz; k++)
+        for (int jj = 0; jj < ny; jj++)
+            for (int i = 0; i < nx; i++) {
+                if (!(i == 0 || jj == 0 || k == 0 || i == nx - 1 || jj == ny - 1 || k == nz - 1)) continue;
+                double v = 0.0;
+                for (int j = 0; j < na; j++) {
+                    const double dx = x[i] - pos[3 * j], dy = y[jj] - pos[3 * j + 1], dz = z[k] - pos[3 * j + 2];
+                    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+                    v += Z[j] / r;
+                    for (int q = 0; q < 3; q++) {
+                        const double zq = zeta[3 * j + q];
+                        v -= w[3 * j + q] * (1.0 / r - exp(-zq * r) * (1.0 / r + 0.5 * zq));
+                    }
+                    double S[25];
+                    or_solid_harmonics(dx, dy, dz, S);
+                    for (int lm = 1; lm < 25; lm++) {
+                        const int l = l_of(lm);
+                        v -= 4.0 * PI / (2 * l + 1) * clm[24 * j + lm - 1] * M[5 * j + l] * S[lm] / pow(r, 2 * l + 1);
+                    }
+                }
+                u[IDX(i, jj, k, nx, ny)] = v;
+            }
+    free(M);
+}
+
 /* ------------------------------------------------------------------ operator */
 /* One axis of the 7-point Laplacian on a nonuniform mesh:
  * 2/(h- + h+) [ (u+ - uP)/h+ - (uP - u-)/h- ]. */
@@ -811,6 +863,7 @@ int or_poisson_solve(int na, const double* pos, const double* Z, const double* R
     const double c[3] = {mesh[1], mesh[2], mesh[3]};
     const double L = mesh[4], h_min = mesh[5], h_max = mesh[6], p_max = mesh[7];
     const int nu1 = ctl[0], nu2 = ctl[1], n_f = ctl[2], max_cycles = ctl[3], n_theta = ctl[4], n_phi = ctl[5];
+    const int bc = ctl[6];   /* 0 multipole (default), 1 zero (Eq. 3.3), 2 exact superposition */
     if (stats) { stats[0] = 0; stats[1] = -1; stats[2] = OR_INVALID_ARG; }
     double* ax[3];
     for (int a = 0; a < 3; a++) {
@@ -847,9 +900,13 @@ int or_poisson_solve(int na, const double* pos, const double* Z, const double* R
     int cycles = 0;
     if (st == OR_OK) {
         double Q[25];
-        or_multipoles(n, n, n, ax[0], ax[1], ax[2], b, c[0], c[1], c[2], Q);
         memset(uu, 0, sizeof(double) * N);
-        or_boundary_fill(n, n, n, ax[0], ax[1], ax[2], c[0], c[1], c[2], Q, uu);
+        if (bc == 0) {          /* multipole expansion of the grid charge, l <= 4 */
+            or_multipoles(n, n, n, ax[0], ax[1], ax[2], b, c[0], c[1], c[2], Q);
+            or_boundary_fill(n, n, n, ax[0], ax[1], ax[2], c[0], c[1], c[2], Q, uu);
+        } else if (bc == 2) {   /* exact superposition of the atoms' potentials */
+            or_boundary_exact(na, pos, Z, R, w, zeta, clm, n, n, n, ax[0], ax[1], ax[2], uu);
+        }                       /* bc == 1: zero (Eq. 3.3) */
         st = or_mg_solve(n, n, n, ax[0], ax[1], ax[2], b, uu, nu1, nu2, n_f, tol, max_cycles, hist, &cycles);
         int sp = or_project(n, n, n, ax[0], ax[1], ax[2], uu, na, pos, R, n_theta, n_phi, vlm);
         if (st == OR_OK && sp != OR_OK) st = sp;

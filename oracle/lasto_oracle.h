@@ -129,6 +129,12 @@ int or_poisson_solve(int na, const double* pos, const double* Z, const double* R
                      const double* zeta, const double* clm, const double* mesh, const int* ctl,
                      double tol, double* vlm, double* u, double* stats, double* hist);
 
+/* Exact superposition Dirichlet values: on the six faces, the continuum potential of every
+ * atom (normalised-exponential shells, nucleus, exterior multipoles of the nonspherical part). */
+void or_boundary_exact(int na, const double* pos, const double* Z, const double* R, const double* w,
+                       const double* zeta, const double* clm, int nx, int ny, int nz, const double* x,
+                       const double* y, const double* z, double* u);
+
 /* Inside the spheres (Section 3, Eq. 3.4-3.7).  Radial mesh r_j = R exp((j-(n-1)) dx),
  * dx = ln(R/r_min)/(n-1); rho_LM(r_j) by the surface projection of Eq. 3.7 at each radius;
  * the inner Dirichlet solve of Eq. 3.4 in the Green's-function form of Eq. 3.5. */
