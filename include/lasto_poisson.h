@@ -75,6 +75,17 @@ enum lasto_cycle {
     LASTO_CYCLE_PCG = 2   /* conjugate gradients preconditioned by one symmetric V-cycle (default) */
 };
 
+/* Dirichlet values on the box faces.  MULTIPOLE: the l <= 4 exterior expansion of the grid
+ * charge about the box centre (Eq. 2.7's decay made finite; default).  ZERO: V_C = 0 as
+ * Eq. 3.3 states.  EXACT: the superposition of every atom's continuum potential (nucleus,
+ * normalised Slater shells Z/r - sum_k w_k [1/r - e^{-zeta_k r}(1/r + zeta_k/2)], exterior
+ * multipoles of the nonspherical part), exact for the density model outside the spheres. */
+enum lasto_boundary {
+    LASTO_BC_MULTIPOLE = 0,
+    LASTO_BC_ZERO = 1,
+    LASTO_BC_EXACT = 2
+};
+
 typedef struct lasto_config {
     int n_max;        /* largest nodes per axis any solve will use (sizes the workspace) */
     int max_atoms;    /* largest total atom count per solve call */
@@ -90,10 +101,11 @@ typedef struct lasto_config {
                          1: the same kernels launched directly with a host-side loop that
                          synchronises once per iteration (for profilers that cannot see
                          kernels inside conditional graph nodes) */
+    int boundary;     /* enum lasto_boundary: Dirichlet values on the box faces */
 } lasto_config;
 
 /* Fills cfg with the defaults: n_max 129, max_atoms 561, max_batch 1, FP64, PCG,
- * nu1 = nu2 = 4 (the fastest time to 1e-10 measured on GB300 for both precisions: more sweeps
+ * multipole faces, nu1 = nu2 = 4 (the fastest time to 1e-10 measured on GB300 for both precisions: more sweeps
  * per level cost less than the CG iterations and reductions they save), 50 cycles, rel_tol
  * 1e-10, 16 x 32 sphere points, graph launch. */
 void lasto_config_default(lasto_config* cfg);
@@ -273,6 +285,10 @@ int lasto_op_multipoles(const int n[3], const double* x, const double* y, const 
  * decay).  Writes only the six faces of u. */
 int lasto_op_boundary_fill(const int n[3], const double* x, const double* y, const double* z,
                            const double centre[3], const double* Q, double* u, void* stream);
+
+/* The six faces of u set to the exact superposition of the atoms' continuum potentials
+ * (LASTO_BC_EXACT); the cluster's arrays and axes are device arrays. */
+int lasto_op_boundary_exact(const lasto_cluster* cl, double* u, void* stream);
 
 /* Au = A u on interior nodes (7-point nonuniform difference), 0 on faces. */
 int lasto_op_apply(const int n[3], const double* x, const double* y, const double* z, const double* u,

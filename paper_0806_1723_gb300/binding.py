@@ -19,6 +19,7 @@ LASTO_OK, LASTO_ERR_INVALID_ARG, LASTO_ERR_GEOMETRY, LASTO_ERR_NONFINITE = 0, 1,
 LASTO_ERR_NOT_CONVERGED, LASTO_ERR_TIMEOUT, LASTO_ERR_CUDA, LASTO_ERR_NO_MEMORY = 4, 5, 6, 7
 LASTO_PREC_FP64, LASTO_PREC_MIXED = 0, 1
 LASTO_CYCLE_V, LASTO_CYCLE_FV, LASTO_CYCLE_PCG = 0, 1, 2
+LASTO_BC_MULTIPOLE, LASTO_BC_ZERO, LASTO_BC_EXACT = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "GEOMETRY", 3: "NONFINITE", 4: "NOT_CONVERGED", 5: "TIMEOUT",
                 6: "CUDA", 7: "NO_MEMORY"}
 
@@ -29,7 +30,7 @@ class lasto_config(ctypes.Structure):
     _fields_ = [("n_max", ctypes.c_int), ("max_atoms", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cycle", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("rel_tol", ctypes.c_double), ("n_theta", ctypes.c_int),
-                ("n_phi", ctypes.c_int), ("launch", ctypes.c_int)]
+                ("n_phi", ctypes.c_int), ("launch", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 class lasto_cluster(ctypes.Structure):
@@ -46,7 +47,7 @@ class lasto_stats(ctypes.Structure):
 EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve", "lasto_poisson_destroy",
            "lasto_poisson_last_error", "lasto_poisson_kernel_counts", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
            "lasto_op_deposit_noalloc",
-           "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
+           "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_boundary_exact", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
            "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
            "lasto_op_project", "lasto_op_sphere_density", "lasto_op_inner_solve", "lasto_guess_param_count", "lasto_poisson_set_guess",
            "lasto_poisson_tune_table", "lasto_poisson_set_tune_table", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
@@ -81,6 +82,7 @@ def _declare(L):
         "lasto_op_deposit_noalloc": (i, [clp, i, vp, vp, vp, vp]),
         "lasto_op_multipoles": (i, [ip, vp, vp, vp, vp, ctypes.POINTER(d), vp, vp]),
         "lasto_op_boundary_fill": (i, [ip, vp, vp, vp, ctypes.POINTER(d), vp, vp, vp]),
+        "lasto_op_boundary_exact": (i, [clp, vp, vp]),
         "lasto_op_apply": (i, [ip, vp, vp, vp, vp, vp, vp]),
         "lasto_op_residual": (i, [ip, vp, vp, vp, vp, vp, vp, vp]),
         "lasto_op_smooth": (i, [ip, vp, vp, vp, vp, vp, i, vp]),
@@ -207,13 +209,14 @@ class Poisson:
     """Owns one ``lasto_poisson`` handle."""
 
     def __init__(self, n_max=129, max_atoms=561, max_batch=1, precision=LASTO_PREC_FP64, cycle=LASTO_CYCLE_PCG,
-                 nu1=4, nu2=4, max_cycles=50, rel_tol=1e-10, n_theta=16, n_phi=32, launch=0):
+                 nu1=4, nu2=4, max_cycles=50, rel_tol=1e-10, n_theta=16, n_phi=32, launch=0, boundary=0):
         L = load()
         cfg = lasto_config_default()
         cfg.n_max, cfg.max_atoms, cfg.max_batch = n_max, max_atoms, max_batch
         cfg.precision, cfg.cycle, cfg.nu1, cfg.nu2 = precision, cycle, nu1, nu2
         cfg.max_cycles, cfg.rel_tol, cfg.n_theta, cfg.n_phi = max_cycles, rel_tol, n_theta, n_phi
         cfg.launch = launch
+        cfg.boundary = boundary
         self.cfg = cfg
         h = ctypes.c_void_p()
         st = L.lasto_poisson_create(ctypes.byref(cfg), ctypes.byref(h))
@@ -411,3 +414,10 @@ def lasto_op_inner_solve(R, Z, rho_lm, v_R, r_min=1e-5, stream=None):
     _check(load().lasto_op_inner_solve(int(R.shape[0]), _ptr(R), _ptr(Z), int(rho_lm.shape[2]), float(r_min),
                                        _ptr(rho_lm), _ptr(v_R), _ptr(v), _stream(stream)), "lasto_op_inner_solve")
     return v
+
+
+def lasto_op_boundary_exact(dc: DeviceCluster, u, stream=None):
+    """The six faces of u set to the exact superposition of the atoms' potentials."""
+    c = dc.struct()
+    _check(load().lasto_op_boundary_exact(ctypes.byref(c), _ptr(u), _stream(stream)), "lasto_op_boundary_exact")
+    return u

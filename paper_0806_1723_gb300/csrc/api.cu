@@ -486,9 +486,13 @@ int enqueue_rhs(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const
     double* tabs = P.mom;
     double* rowm = tabs + 5 * ((size_t)n[0] + n[1] + n[2]);
     double* plane = rowm + 5 * (size_t)n[1] * n[2];
-    TRY(launch_multipoles(n, cl.x, cl.y, cl.z, F.b, cl.centre, tabs, rowm, plane, P.Q, s));
     TRY(cudaMemsetAsync(F.u, 0, sizeof(double) * F.N(), s));
-    TRY(launch_boundary_fill(n, cl.x, cl.y, cl.z, cl.centre[0], cl.centre[1], cl.centre[2], P.Q, F.u, s));
+    if (h->cfg.boundary == LASTO_BC_MULTIPOLE) {
+        TRY(launch_multipoles(n, cl.x, cl.y, cl.z, F.b, cl.centre, tabs, rowm, plane, P.Q, s));
+        TRY(launch_boundary_fill(n, cl.x, cl.y, cl.z, cl.centre[0], cl.centre[1], cl.centre[2], P.Q, F.u, s));
+    } else if (h->cfg.boundary == LASTO_BC_EXACT) {
+        TRY(launch_boundary_exact(cl, tabs, F.u, s));   // the multipole scratch holds the moments
+    }   // LASTO_BC_ZERO: the faces stay 0 (Eq. 3.3)
     if (guess) {
         k_copy_interior<<<(unsigned)((F.N() + 255) / 256), 256, 0, s>>>(guess, F.u, n[0], n[1], n[2]);
         TRY(cudaGetLastError());
@@ -987,6 +991,7 @@ void lasto_config_default(lasto_config* c)
     c->n_theta = 16;
     c->n_phi = 32;
     c->launch = 0;
+    c->boundary = LASTO_BC_MULTIPOLE;
 }
 
 int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
@@ -1000,7 +1005,8 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
         cfg->n_theta < 1 || cfg->n_theta > 32 || cfg->n_phi < 1 || cfg->n_phi > 64 ||
         (cfg->precision != LASTO_PREC_FP64 && cfg->precision != LASTO_PREC_MIXED) ||
         (cfg->cycle != LASTO_CYCLE_V && cfg->cycle != LASTO_CYCLE_FV && cfg->cycle != LASTO_CYCLE_PCG) ||
-        (cfg->launch != 0 && cfg->launch != 1))
+        (cfg->launch != 0 && cfg->launch != 1) ||
+        (cfg->boundary != LASTO_BC_MULTIPOLE && cfg->boundary != LASTO_BC_ZERO && cfg->boundary != LASTO_BC_EXACT))
         return LASTO_ERR_INVALID_ARG;
     lasto_poisson* h = new (std::nothrow) lasto_poisson();
     if (!h) return LASTO_ERR_NO_MEMORY;
@@ -1343,6 +1349,20 @@ int lasto_op_boundary_fill(const int n[3], const double* x, const double* y, con
     if (!op_grid_ok(n, x, y, z) || !centre || !Q || !u) return LASTO_ERR_INVALID_ARG;
     init_device_constants();
     return op_status(launch_boundary_fill(n, x, y, z, centre[0], centre[1], centre[2], Q, u, (cudaStream_t)stream));
+}
+
+int lasto_op_boundary_exact(const lasto_cluster* cl, double* u, void* stream)
+{
+    if (!cl || cl->n_atoms < 1 || !cl->pos || !cl->Z || !cl->R || !cl->slater_w || !cl->slater_zeta || !cl->c_lm ||
+        !cl->x || !cl->y || !cl->z || !u)
+        return LASTO_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++)
+        if (cl->n[d] < 2) return LASTO_ERR_INVALID_ARG;
+    init_device_constants();
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch M(sizeof(double) * 5 * (size_t)cl->n_atoms, s);
+    if (!M.p) return LASTO_ERR_NO_MEMORY;
+    return op_status(launch_boundary_exact(*cl, M.as<double>(), u, s));
 }
 
 int lasto_op_apply(const int n[3], const double* x, const double* y, const double* z, const double* u, double* Au,

@@ -776,4 +776,118 @@ cudaError_t launch_boundary_fill(const int n[3], const double* x, const double* 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- exact superposition faces
+// M_l = int_0^R zeta_1^3/(8pi) e^{-zeta_1 r} (1 - r^2/R^2)^2 (r/R)^l r^(l+2) dr, l = 0..4, by a
+// 64-point Gauss-Legendre rule: block = atom, thread = node (found by Newton's method on the
+// Legendre recurrence).
+__global__ void k_nonsph_moments(int na, const double* __restrict__ R, const double* __restrict__ zeta,
+                                 double* __restrict__ M)
+{
+    __shared__ double part[5][64];
+    const int a = blockIdx.x, q = threadIdx.x;
+    // node q of the 64-point rule (ascending cos), initial guess from the Chebyshev nodes
+    double t = -cos(PI * (q + 0.75) / (64 + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; it++) {
+        double p0 = 1.0, p1 = t;
+        for (int k = 2; k <= 64; k++) {
+            const double p2 = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = 64 * (t * p1 - p0) / (t * t - 1.0);
+        const double dt = p1 / dp;
+        t -= dt;
+        if (fabs(dt) < 1e-16) break;
+    }
+    const double wq = 2.0 / ((1.0 - t * t) * dp * dp);
+    const double Ra = R[a], z1 = zeta[3 * a];
+    const double r = 0.5 * Ra * (t + 1.0), tt = 1.0 - r * r / (Ra * Ra);
+    const double f = 0.5 * Ra * wq * z1 * z1 * z1 / (8.0 * PI) * exp(-z1 * r) * tt * tt * r * r;
+    double pl = 1.0;
+    for (int l = 0; l < 5; l++) {
+        part[l][q] = f * pl;
+        pl *= (r / Ra) * r;
+    }
+    __syncthreads();
+    for (int st = 32; st > 0; st >>= 1) {
+        if (q < st)
+            for (int l = 0; l < 5; l++) part[l][q] += part[l][q + st];
+        __syncthreads();
+    }
+    if (q < 5) M[5 * (size_t)a + q] = part[q][0];
+}
+
+// u on the faces = sum over atoms of Z/r - sum_k w_k [1/r - e^{-zeta_k r}(1/r + zeta_k/2)]
+// - sum_{l>=1,m} 4pi/(2l+1) c_lm M_l S_lm(d) / r^(2l+1)
+__global__ void k_boundary_exact(int nx, int ny, int nz, const double* __restrict__ x, const double* __restrict__ y,
+                                 const double* __restrict__ z, int na, const double* __restrict__ pos,
+                                 const double* __restrict__ Zn, const double* __restrict__ w,
+                                 const double* __restrict__ zeta, const double* __restrict__ clm,
+                                 const double* __restrict__ M, double* __restrict__ u)
+{
+    const size_t fx = (size_t)ny * nz, fy = (size_t)nx * nz, fz = (size_t)nx * ny;
+    const size_t total = 2 * (fx + fy + fz);
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    size_t r = t;
+    if (r < 2 * fx) {
+        const int side = (int)(r / fx);
+        r %= fx;
+        i = side ? nx - 1 : 0;
+        j = (int)(r % ny);
+        k = (int)(r / ny);
+    } else if ((r -= 2 * fx) < 2 * fy) {
+        const int side = (int)(r / fy);
+        r %= fy;
+        j = side ? ny - 1 : 0;
+        i = (int)(r % nx);
+        k = (int)(r / nx);
+    } else {
+        r -= 2 * fy;
+        const int side = (int)(r / fz);
+        r %= fz;
+        k = side ? nz - 1 : 0;
+        i = (int)(r % nx);
+        j = (int)(r / nx);
+    }
+    double v = 0.0;
+    for (int a = 0; a < na; a++) {
+        const double dx = x[i] - pos[3 * a], dy = y[j] - pos[3 * a + 1], dz = z[k] - pos[3 * a + 2];
+        const double d = sqrt(dx * dx + dy * dy + dz * dz), id = 1.0 / d;
+        v += Zn[a] * id;
+        for (int q = 0; q < 3; q++) {
+            const double zq = zeta[3 * a + q];
+            v -= w[3 * a + q] * (id - exp(-zq * d) * (id + 0.5 * zq));
+        }
+        double S[NLM];
+        solid_harmonics(dx, dy, dz, S);
+        double pw = id * id * id;   // d^-(2l+1)
+        int l = 1;
+        for (int lm = 1; lm < NLM; lm++) {
+            const int ll = l_of_lm(lm);
+            if (ll != l) {
+                pw *= id * id;
+                l = ll;
+            }
+            v -= 4.0 * PI / (2 * l + 1) * clm[24 * (size_t)a + lm - 1] * M[5 * (size_t)a + l] * S[lm] * pw;
+        }
+    }
+    u[((size_t)k * ny + j) * nx + i] = v;
+}
+
+cudaError_t launch_boundary_exact(const lasto_cluster& cl, double* M, double* u, cudaStream_t s)
+{
+    cudaError_t e = ensure_monomials();
+    if (e != cudaSuccess) return e;
+    k_nonsph_moments<<<cl.n_atoms, 64, 0, s>>>(cl.n_atoms, cl.R, cl.slater_zeta, M);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int* n = cl.n;
+    const size_t total = 2 * ((size_t)n[1] * n[2] + (size_t)n[0] * n[2] + (size_t)n[0] * n[1]);
+    k_boundary_exact<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(n[0], n[1], n[2], cl.x, cl.y, cl.z, cl.n_atoms,
+                                                                     cl.pos, cl.Z, cl.slater_w, cl.slater_zeta,
+                                                                     cl.c_lm, M, u);
+    return cudaGetLastError();
+}
+
 }  // namespace lasto

@@ -218,6 +218,7 @@ size_t multipole_scratch_doubles(const int n[3]);
 cudaError_t launch_multipoles(const int n[3], const double* x, const double* y, const double* z, const double* b,
                               const double centre[3], double* tabs, double* row_mom, double* plane, double* Q,
                               cudaStream_t s);
+cudaError_t launch_boundary_exact(const lasto_cluster& cl, double* M, double* u, cudaStream_t s);   // M: 5 n_atoms scratch
 cudaError_t launch_boundary_fill(const int n[3], const double* x, const double* y, const double* z, double cx,
                                  double cy, double cz, const double* Q, double* u, cudaStream_t s);
 

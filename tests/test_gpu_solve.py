@@ -233,3 +233,35 @@ def test_tune_table_rejects_bad_lines():
         with pytest.raises(RuntimeError, match="INVALID_ARG"):
             solver.set_tune_table(bad)
     solver.set_tune_table("\n  \n")   # empty is fine
+
+
+def test_boundary_exact_op(orc):
+    B = need_gpu()
+    import torch
+    for cl in (synth.pd13_small(n=33), synth.pd2_dimer(n=33)):
+        dc = B.DeviceCluster(cl)
+        u = torch.zeros((cl.n,) * 3, dtype=torch.float64, device="cuda")
+        got = host(B.lasto_op_boundary_exact(dc, u))
+        ref = orc.boundary_exact(cl, host(dc.x), host(dc.y), host(dc.z))
+        # the faces carry the small remainder of the nuclei's Z/r and the shells' potentials
+        assert np.abs(got - ref).max() < 1e-14 * 46.0 * cl.n_atoms / cl.half_width * 10
+
+
+@pytest.mark.parametrize("bc", ["zero", "exact"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_solve_boundary_choices(orc, bc, precision):
+    """Zero faces (Eq. 3.3) and exact-superposition faces through the whole solve, against the
+    oracle with the same faces."""
+    B = need_gpu()
+    import torch
+    cl = synth.pd13_small(n=33)
+    dc = B.DeviceCluster(cl)
+    prec = B.LASTO_PREC_MIXED if precision == "mixed" else B.LASTO_PREC_FP64
+    code = B.LASTO_BC_ZERO if bc == "zero" else B.LASTO_BC_EXACT
+    solver = B.Poisson(n_max=33, max_atoms=13, precision=prec, boundary=code)
+    v = torch.empty((13, 25), dtype=torch.float64, device="cuda")
+    st = solver.solve(dc, v)[0]
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.rel_resid <= 1e-10
+    ref = orc.poisson_solve(cl, tol=1e-13, max_cycles=200, bc=bc)["vlm"]
+    assert np.abs(host(v) - ref).max() < 1e-8 * np.abs(ref).max()
