@@ -73,6 +73,8 @@ def _declare(L):
         "or_sphere_density": (i, [i, _D, _D, _D, _D, _D, i, d, i, i, _D]),
         "or_inner_solve": (i, [i, _D, _D, i, d, _D, _D, _D]),
         "or_boundary_exact": (None, [i, _D, _D, _D, _D, _D, _D, i, i, i, _D, _D, _D, _D]),
+        "or_raw_sphere_params": (i, [i, _D, _D, i, d, _D, _D, _D, _D, _D]),
+        "or_raw_deposit": (i, [i, _D, _D, _D, i, i, i, _D, _D, _D, _D, i, d, _D, _D, _I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -260,6 +262,29 @@ def boundary_exact(cl, x, y, z, u=None):
     u = np.zeros((len(z), len(y), len(x))) if u is None else u
     lib().or_boundary_exact(*_atoms(cl), len(x), len(y), len(z), _p(x), _p(y), _p(z), _p(u))
     return u
+
+
+def raw_sphere_params(Z, R, rho00, r_min=1e-5):
+    """(q, rho(R), rho'(R), coef [na][3]) of each sphere from its rho_00 radial table."""
+    Z, R, rho00 = _f64(Z), _f64(R), _f64(rho00)
+    na = len(R)
+    q, rr, dr, coef = np.zeros(na), np.zeros(na), np.zeros(na), np.zeros((na, 3))
+    st = lib().or_raw_sphere_params(na, _p(Z), _p(R), rho00.shape[1], r_min, _p(rho00), _p(q), _p(rr), _p(dr), _p(coef))
+    if st != OK:
+        raise ValueError(f"raw_sphere_params status {st}")
+    return q, rr, dr, coef
+
+
+def raw_deposit(pos, Z, R, x, y, z, ne, rho00, r_min=1e-5):
+    """b = 4 pi rho~_grid from a grid density ne [nz][ny][nx] and rho_00 tables [na][n_rad]."""
+    pos, Z, R, x, y, z, ne, rho00 = (_f64(a) for a in (pos, Z, R, x, y, z, ne, rho00))
+    b = np.zeros((len(z), len(y), len(x)))
+    owner = np.zeros(b.shape, dtype=np.int32)
+    st = lib().or_raw_deposit(len(R), _p(pos), _p(Z), _p(R), len(x), len(y), len(z), _p(x), _p(y), _p(z), _p(ne),
+                              rho00.shape[1], r_min, _p(rho00), _p(b), owner.ctypes.data_as(_I))
+    if st != OK:
+        raise ValueError(f"raw_deposit status {st}")
+    return b, owner
 
 
 def radial_mesh(n, r_min, R):

@@ -1027,3 +1027,99 @@ int or_inner_solve(int na, const double* R, const double* Z, int n_rad, double r
     free(r); free(g1); free(g2); free(I1); free(I2);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------ raw density (Eq. 3.1) */
+/* rho_00 at radius r from its samples on the logarithmic mesh: cubic Lagrange interpolation
+ * in x = ln r on the four nearest samples; below r_min the straight line through the first
+ * two samples (the density has a cusp at the nucleus: constant would miss -zeta rho r_min) */
+static double radial_interp(const double* f, int n, double r_min, double dx, double r)
+{
+    if (r <= r_min) {
+        const double r1 = r_min * exp(dx);
+        return f[0] + (f[1] - f[0]) * (r - r_min) / (r1 - r_min);
+    }
+    const double t = log(r / r_min) / dx;
+    int j = (int)floor(t);
+    if (j < 1) j = 1;
+    if (j > n - 3) j = n - 3;
+    const double s = t - j;   /* position relative to sample j; the stencil is j-1 .. j+2 */
+    const double l0 = -s * (s - 1.0) * (s - 2.0) / 6.0, l1 = (s + 1.0) * (s - 1.0) * (s - 2.0) / 2.0;
+    const double l2 = -(s + 1.0) * s * (s - 2.0) / 2.0, l3 = (s + 1.0) * s * (s - 1.0) / 6.0;
+    return l0 * f[j - 1] + l1 * f[j] + l2 * f[j + 1] + l3 * f[j + 2];
+}
+
+/* Pseudo-density of each sphere from the density's own spherical component (Section 3's
+ * three constraints, as or_sphere_params but with rho taken from the radial table):
+ * q = sqrt(4pi) int_0^R rho_00 r^2 dr - Z (cubic rule in ln r, rho_00 constant on [0, r_min]),
+ * rho(R) = rho_00(R)/sqrt(4pi), rho'(R) = (d rho_00/d ln r)(R) / (R sqrt(4pi)) with the
+ * one-sided fourth-order difference; coef = (a, b, c) of a + b r^2 + c r^4. */
+int or_raw_sphere_params(int na, const double* Z, const double* R, int n_rad, double r_min, const double* rho00,
+                         double* q, double* rhoR, double* drhoR, double* coef)
+{
+    if (n_rad < 5 || !(r_min > 0.0)) return OR_INVALID_ARG;
+    double* g = malloc(sizeof(double) * n_rad);
+    double* r = malloc(sizeof(double) * n_rad);
+    const double s4 = sqrt(4.0 * PI);
+    for (int i = 0; i < na; i++) {
+        const double* f = rho00 + (size_t)i * n_rad;
+        or_radial_mesh(n_rad, r_min, R[i], r);
+        const double h = log(R[i] / r_min) / (n_rad - 1);
+        for (int j = 0; j < n_rad; j++) g[j] = f[j] * r[j] * r[j] * r[j];
+        double acc = f[0] * r[0] * r[0] * r[0] / 3.0;
+        for (int j = 0; j + 1 < n_rad; j++) acc += seg_integral(g, n_rad, j, h);
+        q[i] = s4 * acc - Z[i];
+        const int m = n_rad - 1;
+        rhoR[i] = f[m] / s4;
+        drhoR[i] = (25.0 * f[m] - 48.0 * f[m - 1] + 36.0 * f[m - 2] - 16.0 * f[m - 3] + 3.0 * f[m - 4]) /
+                   (12.0 * h) / (R[i] * s4);
+        const double Ri = R[i];
+        double M[3][3] = {{4.0 * PI * pow(Ri, 3) / 3.0, 4.0 * PI * pow(Ri, 5) / 5.0, 4.0 * PI * pow(Ri, 7) / 7.0},
+                          {1.0, Ri * Ri, pow(Ri, 4)},
+                          {0.0, 2.0 * Ri, 4.0 * pow(Ri, 3)}};
+        double rhs[3] = {q[i], rhoR[i], drhoR[i]};
+        solve3(M, rhs, &coef[3 * i]);
+    }
+    free(g); free(r);
+    return OR_OK;
+}
+
+/* Deposit from a raw density: b = 4pi rho~_grid with rho~_grid = ne outside the spheres and
+ * ne - rho_00(r)/sqrt(4pi) + pseudo(r) inside sphere i (the monopole swap of Section 1 with the
+ * spherical part from the radial table).  ne: [nz][ny][nx]; rho00: [na][n_rad]. */
+int or_raw_deposit(int na, const double* pos, const double* Z, const double* R, int nx, int ny, int nz,
+                   const double* x, const double* y, const double* z, const double* ne, int n_rad, double r_min,
+                   const double* rho00, double* b, int* owner)
+{
+    double* q = malloc(sizeof(double) * na);
+    double* rhoR = malloc(sizeof(double) * na);
+    double* drhoR = malloc(sizeof(double) * na);
+    double* coef = malloc(sizeof(double) * 3 * na);
+    const int st = or_raw_sphere_params(na, Z, R, n_rad, r_min, rho00, q, rhoR, drhoR, coef);
+    if (st == OR_OK) {
+        const double s4 = sqrt(4.0 * PI);
+#pragma omp parallel for schedule(dynamic)
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    int own = -1;
+                    double r = 0.0;
+                    for (int a = 0; a < na; a++) {
+                        const double dx = x[i] - pos[3 * a], dy = y[j] - pos[3 * a + 1], dz = z[k] - pos[3 * a + 2];
+                        const double ra = sqrt(dx * dx + dy * dy + dz * dz);
+                        if (ra < R[a]) { own = a; r = ra; break; }
+                    }
+                    const size_t P = IDX(i, j, k, nx, ny);
+                    double val = ne[P];
+                    if (own >= 0) {
+                        const double hh = log(R[own] / r_min) / (n_rad - 1);
+                        const double rho0 = radial_interp(rho00 + (size_t)own * n_rad, n_rad, r_min, hh, r) / s4;
+                        const double* c = &coef[3 * own];
+                        val = val - rho0 + (c[0] + c[1] * r * r + c[2] * r * r * r * r);
+                    }
+                    b[P] = 4.0 * PI * val;
+                    if (owner) owner[P] = own;
+                }
+    }
+    free(q); free(rhoR); free(drhoR); free(coef);
+    return st;
+}

@@ -144,6 +144,15 @@ int or_sphere_density(int na, const double* pos, const double* R, const double* 
 int or_inner_solve(int na, const double* R, const double* Z, int n_rad, double r_min, const double* rho_lm,
                    const double* v_R, double* v);
 
+/* Raw density (Eq. 3.1's representation: a grid density and, per sphere, the spherical
+ * component rho_00 on the logarithmic radial mesh): pseudo-density from the table and the
+ * deposit with the monopole swap. */
+int or_raw_sphere_params(int na, const double* Z, const double* R, int n_rad, double r_min, const double* rho00,
+                         double* q, double* rhoR, double* drhoR, double* coef);
+int or_raw_deposit(int na, const double* pos, const double* Z, const double* R, int nx, int ny, int nz,
+                   const double* x, const double* y, const double* z, const double* ne, int n_rad, double r_min,
+                   const double* rho00, double* b, int* owner);
+
 #ifdef __cplusplus
 }
 #endif
