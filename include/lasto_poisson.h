@@ -149,6 +149,40 @@ typedef struct lasto_poisson lasto_poisson;   /* opaque; owns workspace, plans a
 int lasto_poisson_tune_table(const lasto_poisson* h, char* buf, size_t cap);
 int lasto_poisson_set_tune_table(lasto_poisson* h, const char* text);
 
+/* Raw density (Eq. 3.1's representation: the density on the grid and, inside each sphere,
+ * its spherical-harmonic components on the logarithmic radial mesh; the entry point for
+ * densities that do not come from the synthetic Slater model, e.g. an SCF iteration's).
+ * density: the electron density at every node (device [n2][n1][n0], x fastest, the same
+ * nodes as x, y, z); rho00: each sphere's spherical component rho_00(r_j) = integral of the
+ * density times y_00 over the sphere of radius r_j (device [n_atoms][n_rad]) on the mesh
+ * r_j = R_a exp((j - (n_rad-1)) dx), dx = ln(R_a/r_min)/(n_rad-1).  From each table: q =
+ * sqrt(4pi) int_0^R rho_00 r^2 dr - Z (cubic rule in ln r), rho(R), rho'(R) (one-sided
+ * fourth-order difference in ln r) and the quartic pseudo-density of Section 3; inside the
+ * sphere the deposit takes density - rho_00(r)/sqrt(4pi) + pseudo(r) with rho_00(r) by cubic
+ * interpolation in ln r (the straight line through the first two samples below r_min).  The
+ * rest of the solve is lasto_poisson_solve's (faces: multipole or zero; EXACT needs the model
+ * density and gives INVALID_ARG).  Arguments otherwise as lasto_poisson_solve; n_rad >= 5. */
+typedef struct lasto_raw_cluster {
+    int n_atoms;
+    const double* pos;      /* [n_atoms][3] device */
+    const double* Z;        /* [n_atoms] device */
+    const double* R;        /* [n_atoms] device */
+    int n[3];
+    const double* x;        /* [n[0]] device node coordinates */
+    const double* y;
+    const double* z;
+    double centre[3];       /* host: expansion centre of the boundary multipoles */
+    const double* density;  /* [n[2]][n[1]][n[0]] device */
+    int n_rad;
+    double r_min;
+    const double* rho00;    /* [n_atoms][n_rad] device */
+} lasto_raw_cluster;
+int lasto_poisson_solve_raw(lasto_poisson* h, const lasto_raw_cluster* clusters, int n_clusters, double* v_lm,
+                            double* potential, const double* guess, lasto_stats* stats, void* stream);
+/* The raw deposit alone: b (device [N]) = 4 pi rho~_grid, owner (optional, device int [N]) the
+ * sphere holding each node or -1, status (device int) GEOMETRY / NONFINITE. */
+int lasto_op_raw_deposit(const lasto_raw_cluster* cl, double* b, int* owner, int* status, void* stream);
+
 /* Inside the atom spheres (Section 3, Eq. 3.4-3.7).  Radial mesh of sphere a (the paper:
  * logarithmic, 429 points): r_j = R_a exp((j - (n_rad-1)) dx), dx = ln(R_a / r_min)/(n_rad-1),
  * so r_0 = r_min and r_{n_rad-1} = R_a.

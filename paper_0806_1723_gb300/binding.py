@@ -39,12 +39,19 @@ class lasto_cluster(ctypes.Structure):
                 ("centre", ctypes.c_double * 3)]
 
 
+class lasto_raw_cluster(ctypes.Structure):
+    _fields_ = [("n_atoms", ctypes.c_int), ("pos", _P), ("Z", _P), ("R", _P), ("n", ctypes.c_int * 3), ("x", _P),
+                ("y", _P), ("z", _P), ("centre", ctypes.c_double * 3), ("density", _P), ("n_rad", ctypes.c_int),
+                ("r_min", ctypes.c_double), ("rho00", _P)]
+
+
 class lasto_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("status", ctypes.c_int), ("rel_resid", ctypes.c_double),
                 ("bnorm", ctypes.c_double), ("outer", ctypes.c_int), ("guess", ctypes.c_int)]
 
 
-EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve", "lasto_poisson_destroy",
+EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve", "lasto_poisson_solve_raw",
+           "lasto_op_raw_deposit", "lasto_poisson_destroy",
            "lasto_poisson_last_error", "lasto_poisson_kernel_counts", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
            "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_boundary_exact", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
@@ -69,6 +76,8 @@ def _declare(L):
         "lasto_config_default": (None, [cfgp]),
         "lasto_poisson_create": (i, [cfgp, ctypes.POINTER(vp)]),
         "lasto_poisson_solve": (i, [vp, clp, i, vp, vp, vp, stp, vp]),
+        "lasto_poisson_solve_raw": (i, [vp, ctypes.POINTER(lasto_raw_cluster), i, vp, vp, vp, stp, vp]),
+        "lasto_op_raw_deposit": (i, [ctypes.POINTER(lasto_raw_cluster), vp, vp, vp, vp]),
         "lasto_poisson_destroy": (None, [vp]),
         "lasto_poisson_last_error": (ctypes.c_char_p, [vp]),
         "lasto_poisson_kernel_counts": (i, [vp, ip, ip, ip]),
@@ -258,6 +267,20 @@ class Poisson:
         if st != LASTO_OK:
             raise RuntimeError(f"lasto_poisson_set_tune_table failed: {STATUS_NAMES.get(st, st)}: {self.last_error()}")
 
+    def solve_raw(self, clusters, v_lm, potential=None, guess=None, stats=True, stream=None):
+        """lasto_poisson_solve_raw on RawCluster inputs (grid density + rho_00 tables)."""
+        if not isinstance(clusters, (list, tuple)):
+            clusters = [clusters]
+        arr = (lasto_raw_cluster * len(clusters))(*[c.struct() for c in clusters])
+        self._keep = (clusters, arr)
+        st_arr = (lasto_stats * len(clusters))() if stats else None
+        self._stats = st_arr
+        st = load().lasto_poisson_solve_raw(self.h, arr, len(clusters), _ptr(v_lm), _ptr(potential), _ptr(guess),
+                                            st_arr, _stream(stream))
+        if st != LASTO_OK:
+            raise RuntimeError(f"lasto_poisson_solve_raw failed: {STATUS_NAMES.get(st, st)}: {self.last_error()}")
+        return st_arr
+
     def set_guess(self, weights=GUESS_WEIGHTS):
         """Load the learned initial-guess network (an .npz of per-layer weights [27][cin][cout],
         biases and the JSON input/output scales); None removes it."""
@@ -421,3 +444,43 @@ def lasto_op_boundary_exact(dc: DeviceCluster, u, stream=None):
     c = dc.struct()
     _check(load().lasto_op_boundary_exact(ctypes.byref(c), _ptr(u), _stream(stream)), "lasto_op_boundary_exact")
     return u
+
+
+class RawCluster:
+    """A raw-density input on the device: atoms, mesh axes, the electron density at every node
+    and each sphere's spherical component rho_00 on the logarithmic radial mesh."""
+
+    def __init__(self, pos, Z, R, x, y, z, centre, density, rho00, r_min=1e-5, device="cuda"):
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).to(device) \
+            if not isinstance(a, torch.Tensor) else a.contiguous()
+        self.pos, self.Z, self.R = f(pos), f(Z), f(R)
+        self.x, self.y, self.z = f(x), f(y), f(z)
+        self.density, self.rho00 = f(density), f(rho00)
+        self.centre = tuple(float(c) for c in centre)
+        self.r_min = float(r_min)
+        self.n_atoms = int(self.R.shape[0])
+        self.n = (int(self.x.shape[0]), int(self.y.shape[0]), int(self.z.shape[0]))
+
+    def struct(self):
+        c = lasto_raw_cluster()
+        c.n_atoms = self.n_atoms
+        c.pos, c.Z, c.R = _ptr(self.pos), _ptr(self.Z), _ptr(self.R)
+        c.n = (ctypes.c_int * 3)(*self.n)
+        c.x, c.y, c.z = _ptr(self.x), _ptr(self.y), _ptr(self.z)
+        c.centre = (ctypes.c_double * 3)(*self.centre)
+        c.density = _ptr(self.density)
+        c.n_rad = int(self.rho00.shape[1])
+        c.r_min = self.r_min
+        c.rho00 = _ptr(self.rho00)
+        return c
+
+
+def lasto_op_raw_deposit(rc: RawCluster, stream=None):
+    n = rc.n[0] * rc.n[1] * rc.n[2]
+    b = torch.empty(n, dtype=torch.float64, device=rc.x.device)
+    owner = torch.empty(n, dtype=torch.int32, device=rc.x.device)
+    status = torch.zeros(1, dtype=torch.int32, device=rc.x.device)
+    c = rc.struct()
+    _check(load().lasto_op_raw_deposit(ctypes.byref(c), _ptr(b), _ptr(owner), _ptr(status), _stream(stream)),
+           "lasto_op_raw_deposit")
+    return b, owner, status

@@ -87,6 +87,7 @@ struct ClusterPlan {
     int gm[3] = {0, 0, 0};
     int gl = -1;      // -1: no learned guess for this cluster
     int gslot = -1;   // its grid in the network's batch
+    const lasto_raw_cluster* raw = nullptr;   // raw-density input (null: the synthetic model)
     Red red(int op, cudaGraphConditionalHandle cond = 0, int use_cond = 0) const
     {
         return Red{part, reinterpret_cast<unsigned int*>(status + 1), ctl, op, cond, use_cond};
@@ -235,6 +236,7 @@ struct lasto_poisson {
     // smoother choice per level shape {nx, ny, nz, element bytes}: measured once, reused
     std::map<std::array<int, 4>, SmoothChoice> tune;
     GuessNet* net = nullptr;             // learned initial guess (optional)
+    std::vector<lasto_raw_cluster> raw_copy;   // raw-density inputs of the current solve call
     std::vector<cudaEvent_t> eg;         // per slot: features written
     cudaEvent_t ev_net = nullptr;        // network forward done
 };
@@ -477,12 +479,55 @@ int enqueue_setup(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, cud
     return LASTO_OK;
 }
 
+RawArgs raw_args(const lasto_raw_cluster& r)
+{
+    RawArgs a;
+    a.na = r.n_atoms;
+    a.pos = r.pos;
+    a.Z = r.Z;
+    a.R = r.R;
+    for (int d = 0; d < 3; d++) a.n[d] = r.n[d];
+    a.ax[0] = r.x;
+    a.ax[1] = r.y;
+    a.ax[2] = r.z;
+    a.ne = r.density;
+    a.n_rad = r.n_rad;
+    a.r_min = r.r_min;
+    a.rho00 = r.rho00;
+    return a;
+}
+
+// the geometry part of a raw cluster as a lasto_cluster (no model arrays)
+lasto_cluster cluster_of(const lasto_raw_cluster& r)
+{
+    lasto_cluster c;
+    std::memset(&c, 0, sizeof(c));
+    c.n_atoms = r.n_atoms;
+    c.pos = r.pos;
+    c.Z = r.Z;
+    c.R = r.R;
+    for (int d = 0; d < 3; d++) {
+        c.n[d] = r.n[d];
+        c.centre[d] = r.centre[d];
+    }
+    c.x = r.x;
+    c.y = r.y;
+    c.z = r.z;
+    return c;
+}
+
 int enqueue_rhs(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const double* guess, cudaStream_t s)
 {
     LevelStore& F = P.lv[0];
     const int* n = cl.n;
-    TRY(launch_sphere_params(cl, cl.x, cl.y, cl.z, P.rec, nullptr, nullptr, nullptr, nullptr, P.status, s));
-    TRY(launch_deposit(cl, P.rec, h->cfg.precision, F.b, nullptr, nullptr, nullptr, P.status, s));
+    if (P.raw) {
+        const RawArgs ra = raw_args(*P.raw);
+        TRY(launch_raw_sphere_params(ra, P.rec, P.status, s));
+        TRY(launch_raw_deposit(ra, P.rec, F.b, nullptr, P.status, s));
+    } else {
+        TRY(launch_sphere_params(cl, cl.x, cl.y, cl.z, P.rec, nullptr, nullptr, nullptr, nullptr, P.status, s));
+        TRY(launch_deposit(cl, P.rec, h->cfg.precision, F.b, nullptr, nullptr, nullptr, P.status, s));
+    }
     double* tabs = P.mom;
     double* rowm = tabs + 5 * ((size_t)n[0] + n[1] + n[2]);
     double* plane = rowm + 5 * (size_t)n[1] * n[2];
@@ -911,15 +956,17 @@ static int copy_stats(lasto_poisson* h, int nc, lasto_stats* stats, cudaStream_t
 
 // The same kernels as the captured graph, launched directly; the iteration loop runs
 // on the host and reads the device control block once per iteration.
-static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,
-                        const double* guess, cudaStream_t s)
+static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, const lasto_raw_cluster* raws, int nc,
+                        double* v_lm, double* potential, const double* guess, cudaStream_t s)
 {
     h->plans.assign(nc, ClusterPlan());
     h->key.clear();
     Carver cv{h->pool, h->pool_bytes};
-    for (int c = 0; c < nc; c++)
+    for (int c = 0; c < nc; c++) {
         if (!carve_cluster(cv, cls[c].n, cls[c].n_atoms, h->plans[c]))
             return fail(h, LASTO_ERR_NO_MEMORY, "workspace too small for this batch");
+        h->plans[c].raw = raws ? raws + c : nullptr;
+    }
     if (int st = tune_plans(h, cls, nc, s)) return st;
     size_t atom_off = 0, grid_off = 0;
     const int nguess = plan_guesses(h, cls, nc, guess);
@@ -1153,8 +1200,8 @@ const char* lasto_poisson_last_error(const lasto_poisson* h)
     return h ? h->err.msg.c_str() : "null handle";
 }
 
-int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,
-                        const double* guess, lasto_stats* stats, void* stream)
+static int solve_impl(lasto_poisson* h, const lasto_cluster* cls, const lasto_raw_cluster* raws, int nc,
+                      double* v_lm, double* potential, const double* guess, lasto_stats* stats, void* stream)
 {
     if (!h) return LASTO_ERR_INVALID_ARG;
     h->err = Err();
@@ -1166,24 +1213,30 @@ int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
         const char* c = static_cast<const char*>(p);
         key.insert(key.end(), c, c + n);
     };
-    size_t total_atoms = 0;
     for (int c = 0; c < nc; c++) {
         const lasto_cluster& cl = cls[c];
         if (!valid_n(cl.n) || cl.n[0] > h->cfg.n_max || cl.n[1] > h->cfg.n_max || cl.n[2] > h->cfg.n_max)
             return fail(h, LASTO_ERR_INVALID_ARG, "grid size: odd, >= 3, coarsening to <= 9 nodes, <= n_max");
-        if (cl.n_atoms < 1 || cl.n_atoms > h->cfg.max_atoms || !cl.pos || !cl.Z || !cl.R || !cl.slater_w ||
-            !cl.slater_zeta || !cl.c_lm || !cl.x || !cl.y || !cl.z)
+        if (cl.n_atoms < 1 || cl.n_atoms > h->cfg.max_atoms || !cl.pos || !cl.Z || !cl.R || !cl.x || !cl.y || !cl.z)
             return fail(h, LASTO_ERR_INVALID_ARG, "cluster arrays");
-        total_atoms += cl.n_atoms;
+        if (raws) {
+            const lasto_raw_cluster& r = raws[c];
+            if (!r.density || !r.rho00 || r.n_rad < 5 || !(r.r_min > 0.0))
+                return fail(h, LASTO_ERR_INVALID_ARG, "raw density arrays");
+            if (h->cfg.boundary == LASTO_BC_EXACT)
+                return fail(h, LASTO_ERR_INVALID_ARG, "exact faces need the model density");
+            put(&r, sizeof(r));
+        } else if (!cl.slater_w || !cl.slater_zeta || !cl.c_lm) {
+            return fail(h, LASTO_ERR_INVALID_ARG, "cluster arrays");
+        }
         put(&cl, sizeof(cl));
     }
     put(&v_lm, sizeof(v_lm));
     put(&potential, sizeof(potential));
     put(&guess, sizeof(guess));
     put(&nc, sizeof(nc));
-    (void)total_atoms;
     if (h->cfg.launch == 1) {
-        int st = direct_solve(h, cls, nc, v_lm, potential, guess, s);
+        int st = direct_solve(h, cls, raws, nc, v_lm, potential, guess, s);
         if (st) return st;
         return copy_stats(h, nc, stats, s);
     }
@@ -1191,9 +1244,11 @@ int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
         // carve the workspace for these clusters
         h->plans.assign(nc, ClusterPlan());
         Carver cv{h->pool, h->pool_bytes};
-        for (int c = 0; c < nc; c++)
+        for (int c = 0; c < nc; c++) {
             if (!carve_cluster(cv, cls[c].n, cls[c].n_atoms, h->plans[c]))
                 return fail(h, LASTO_ERR_NO_MEMORY, "workspace too small for this batch");
+            h->plans[c].raw = raws ? raws + c : nullptr;
+        }
         h->key.clear();
         int st = tune_plans(h, cls, nc, s);
         if (st) return st;
@@ -1207,6 +1262,23 @@ int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, doub
     return copy_stats(h, nc, stats, s);
 }
 
+extern "C" int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,
+                                   const double* guess, lasto_stats* stats, void* stream)
+{
+    return solve_impl(h, cls, nullptr, nc, v_lm, potential, guess, stats, stream);
+}
+
+extern "C" int lasto_poisson_solve_raw(lasto_poisson* h, const lasto_raw_cluster* raws, int nc, double* v_lm,
+                                       double* potential, const double* guess, lasto_stats* stats, void* stream)
+{
+    if (!h) return LASTO_ERR_INVALID_ARG;
+    if (!raws || nc < 1 || nc > h->cfg.max_batch) return fail(h, LASTO_ERR_INVALID_ARG, "bad clusters");
+    std::vector<lasto_cluster> cls(nc);
+    for (int c = 0; c < nc; c++) cls[c] = cluster_of(raws[c]);
+    // the raw structs must outlive the capture only: the graph keeps copies of their values
+    h->raw_copy.assign(raws, raws + nc);
+    return solve_impl(h, cls.data(), h->raw_copy.data(), nc, v_lm, potential, guess, stats, stream);
+}
 
 // ---------------------------------------------------------------- mesh
 int lasto_mesh_axis(int n, double centre, double half_width, double h_min, double h_max, double p_max, double* x,
@@ -1514,6 +1586,22 @@ int lasto_op_sphere_density(const lasto_cluster* cl, int n_rad, double r_min, in
                                  status, s);
     if (e == cudaSuccess)
         e = launch_sphere_density(cl->n_atoms, rec.as<double>(), cl->c_lm, q.as<double>(), nq, n_rad, r_min, rho_lm, s);
+    return op_status(e);
+}
+
+int lasto_op_raw_deposit(const lasto_raw_cluster* cl, double* b, int* owner, int* status, void* stream)
+{
+    if (!cl || cl->n_atoms < 1 || !cl->pos || !cl->Z || !cl->R || !cl->x || !cl->y || !cl->z || !cl->density ||
+        !cl->rho00 || cl->n_rad < 5 || !(cl->r_min > 0.0) || !b)
+        return LASTO_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++)
+        if (cl->n[d] < 5) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch rec(sizeof(double) * RAW_REC * (size_t)cl->n_atoms, s);
+    if (!rec.p) return LASTO_ERR_NO_MEMORY;
+    const RawArgs ra = raw_args(*cl);
+    cudaError_t e = launch_raw_sphere_params(ra, rec.as<double>(), status, s);
+    if (e == cudaSuccess) e = launch_raw_deposit(ra, rec.as<double>(), b, owner, status, s);
     return op_status(e);
 }
 

@@ -222,6 +222,21 @@ cudaError_t launch_boundary_exact(const lasto_cluster& cl, double* M, double* u,
 cudaError_t launch_boundary_fill(const int n[3], const double* x, const double* y, const double* z, double cx,
                                  double cy, double cz, const double* Q, double* u, cudaStream_t s);
 
+// raw.cu: the raw-density entry point (grid density + each sphere's rho_00 table)
+struct RawArgs {
+    int na;
+    const double *pos, *Z, *R;
+    int n[3];
+    const double* ax[3];
+    const double* ne;      // [N] electron density at the nodes
+    int n_rad;
+    double r_min;
+    const double* rho00;   // [na][n_rad]
+};
+constexpr int RAW_REC = 8;   // x y z R a b c h per sphere
+cudaError_t launch_raw_sphere_params(const RawArgs& a, double* rec, int* status, cudaStream_t s);
+cudaError_t launch_raw_deposit(const RawArgs& a, const double* rec, double* b, int* owner, int* status, cudaStream_t s);
+
 // inner.cu: inside the spheres (Eq. 3.4-3.7)
 cudaError_t launch_sphere_density(int na, const double* rec, const double* clm, const double* quad, int nq,
                                   int n_rad, double r_min, double* out, cudaStream_t s);
