@@ -74,6 +74,7 @@ def _declare(L):
         "or_inner_solve": (i, [i, _D, _D, i, d, _D, _D, _D]),
         "or_boundary_exact": (None, [i, _D, _D, _D, _D, _D, _D, i, i, i, _D, _D, _D, _D]),
         "or_raw_sphere_params": (i, [i, _D, _D, i, d, _D, _D, _D, _D, _D]),
+        "or_interstitial_hs": (i, [i, _D, _D, i, _I, _I, _D, i, i, i, _D, _D, _D, _D, _D, _D]),
         "or_raw_deposit": (i, [i, _D, _D, _D, i, i, i, _D, _D, _D, _D, i, d, _D, _D, _I]),
     }
     for name, (res, args) in sig.items():
@@ -262,6 +263,25 @@ def boundary_exact(cl, x, y, z, u=None):
     u = np.zeros((len(z), len(y), len(x))) if u is None else u
     lib().or_boundary_exact(*_atoms(cl), len(x), len(y), len(z), _p(x), _p(y), _p(z), _p(u))
     return u
+
+
+# Table 1's LASTO basis per Pd atom: (n, l, zeta) of 4d 5d 5s 5p 6s 6p 4f
+LASTO_BASIS = [(4, 2, 2.20), (5, 2, 2.60), (5, 0, 1.00), (5, 1, 1.00), (6, 0, 2.00), (6, 1, 2.00), (4, 3, 1.60)]
+
+
+def interstitial_hs(pos, R, x, y, z, V, basis=LASTO_BASIS):
+    """(S, H) [M][M] over the nodes outside every sphere (Eq. 3.11-3.14, grid-point form)."""
+    pos, R, x, y, z, V = (_f64(a) for a in (pos, R, x, y, z, V))
+    bn = np.array([b[0] for b in basis], dtype=np.int32)
+    bl = np.array([b[1] for b in basis], dtype=np.int32)
+    bz = np.array([b[2] for b in basis], dtype=np.float64)
+    M = len(R) * int(sum(2 * l + 1 for l in bl))
+    S, H = np.zeros((M, M)), np.zeros((M, M))
+    st = lib().or_interstitial_hs(len(R), _p(pos), _p(R), len(basis), bn.ctypes.data_as(_I), bl.ctypes.data_as(_I),
+                                  _p(bz), len(x), len(y), len(z), _p(x), _p(y), _p(z), _p(V), _p(S), _p(H))
+    if st != OK:
+        raise ValueError(f"interstitial_hs status {st}")
+    return S, H
 
 
 def raw_sphere_params(Z, R, rho00, r_min=1e-5):

@@ -16,6 +16,12 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#else
+static int omp_get_max_threads(void) { return 1; }
+static int omp_get_thread_num(void) { return 0; }
+#endif
 
 static const double PI = 3.14159265358979323846;
 
@@ -1122,4 +1128,88 @@ int or_raw_deposit(int na, const double* pos, const double* Z, const double* R, 
     }
     free(q); free(rhoR); free(drhoR); free(coef);
     return st;
+}
+
+/* ------------------------------------------------------------------ interstitial H and S (Eq. 3.11-3.14) */
+/* Interstitial overlap and Hamiltonian contributions of a Slater-type basis (Eq. 3.13:
+ * phi_inlm = r_i^(n-1) e^{-zeta r_i} y_lm(r^_i), for every atom i and every (n, l, zeta) of the
+ * basis table, all m), summed over the grid nodes outside every sphere with the dual-cell
+ * volume (the grid-point form S^1, H^1 of Section 3):
+ *   S_ab = sum_P phi_a(P) phi_b(P) Vol(P),
+ *   H_ab = 1/2 sum_P (phi_a(P) phit_b(P) + phi_b(P) phit_a(P)) Vol(P),
+ *   phit = 1/2 [(l(l+1) - n(n-1)) r^(n-3) + 2 zeta n r^(n-2) - zeta^2 r^(n-1)] e^{-zeta r} y_lm
+ *          + V(P) phi (Eq. 3.14, -1/2 Lap + V applied to phi).
+ * Function order: atom-major, then the basis table's order, then m = -l..l (lm = l^2+l+m).
+ * V: potential energy at the nodes [nz][ny][nx]; S, H: [M][M], M = na * sum(2l+1). */
+int or_interstitial_hs(int na, const double* pos, const double* R, int nb, const int* bn, const int* bl,
+                       const double* bz, int nx, int ny, int nz, const double* x, const double* y, const double* z,
+                       const double* V, double* S, double* H)
+{
+    int per = 0;
+    for (int q = 0; q < nb; q++) {
+        if (bl[q] < 0 || bl[q] > 4 || bn[q] < bl[q] + 1) return OR_INVALID_ARG;
+        per += 2 * bl[q] + 1;
+    }
+    const int M = na * per;
+    double *vx = malloc(sizeof(double) * nx), *vy = malloc(sizeof(double) * ny), *vz = malloc(sizeof(double) * nz);
+    or_dual_lengths(nx, x, vx);
+    or_dual_lengths(ny, y, vy);
+    or_dual_lengths(nz, z, vz);
+    memset(S, 0, sizeof(double) * M * M);
+    memset(H, 0, sizeof(double) * M * M);
+    const int nthr = omp_get_max_threads();
+    double* part = calloc((size_t)nthr * 2 * M * M, sizeof(double));
+#pragma omp parallel
+    {
+        double* ph = malloc(sizeof(double) * M);
+        double* pt = malloc(sizeof(double) * M);
+        double* Sp = part + (size_t)omp_get_thread_num() * 2 * M * M;
+        double* Hp = Sp + (size_t)M * M;
+#pragma omp for schedule(static)
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    int inside = 0;
+                    for (int a = 0; a < na && !inside; a++) {
+                        const double dx = x[i] - pos[3 * a], dy = y[j] - pos[3 * a + 1], dz = z[k] - pos[3 * a + 2];
+                        if (sqrt(dx * dx + dy * dy + dz * dz) < R[a]) inside = 1;
+                    }
+                    if (inside) continue;
+                    const double vol = vx[i] * vy[j] * vz[k], Vp = V[IDX(i, j, k, nx, ny)];
+                    int f = 0;
+                    for (int a = 0; a < na; a++) {
+                        const double dx = x[i] - pos[3 * a], dy = y[j] - pos[3 * a + 1], dz = z[k] - pos[3 * a + 2];
+                        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+                        double Sl[25];
+                        or_solid_harmonics(dx, dy, dz, Sl);
+                        for (int q = 0; q < nb; q++) {
+                            const int n = bn[q], l = bl[q];
+                            const double zt = bz[q], e = exp(-zt * r);
+                            const double rad = pow(r, n - 1 - l) * e;   /* r^(n-1) y_lm = r^(n-1-l) S_lm */
+                            const double kin = 0.5 * ((l * (l + 1) - n * (n - 1)) / (r * r) + 2.0 * zt * n / r - zt * zt) * rad;
+                            for (int m = -l; m <= l; m++) {
+                                const double s = Sl[l * l + l + m];
+                                ph[f] = rad * s;
+                                pt[f] = kin * s + Vp * rad * s;
+                                f++;
+                            }
+                        }
+                    }
+                    for (int p = 0; p < M; p++) {
+                        const double wp = vol * ph[p], wt = vol * pt[p];
+                        for (int qq = 0; qq < M; qq++) {
+                            Sp[(size_t)p * M + qq] += wp * ph[qq];
+                            Hp[(size_t)p * M + qq] += 0.5 * (wp * pt[qq] + wt * ph[qq]);
+                        }
+                    }
+                }
+        free(ph); free(pt);
+    }
+    for (int t = 0; t < nthr; t++)
+        for (size_t e = 0; e < (size_t)M * M; e++) {
+            S[e] += part[(size_t)t * 2 * M * M + e];
+            H[e] += part[(size_t)t * 2 * M * M + (size_t)M * M + e];
+        }
+    free(part); free(vx); free(vy); free(vz);
+    return OR_OK;
 }

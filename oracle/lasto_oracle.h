@@ -153,6 +153,14 @@ int or_raw_deposit(int na, const double* pos, const double* Z, const double* R, 
                    const double* x, const double* y, const double* z, const double* ne, int n_rad, double r_min,
                    const double* rho00, double* b, int* owner);
 
+/* Interstitial overlap and Hamiltonian contributions of a Slater-type basis (Eq. 3.11-3.14,
+ * grid-point form): nodes outside every sphere, dual-cell volumes; bn, bl, bz: the basis
+ * table's n, l, zeta (nb entries); V: potential energy at the nodes; S, H: [M][M],
+ * M = na * sum(2l+1), functions atom-major, table order, m = -l..l. */
+int or_interstitial_hs(int na, const double* pos, const double* R, int nb, const int* bn, const int* bl,
+                       const double* bz, int nx, int ny, int nz, const double* x, const double* y, const double* z,
+                       const double* V, double* S, double* H);
+
 #ifdef __cplusplus
 }
 #endif
