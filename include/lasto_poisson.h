@@ -444,6 +444,31 @@ int lasto_nn_guess_grid(const int n[3], const float* pred, int ld, float scale, 
 int lasto_nn_adam(size_t n, float* w, const float* g, float* m, float* v, float lr, float b1, float b2, float eps,
                   int step, void* w16, void* stream);
 
+/* Interstitial overlap and Hamiltonian contributions (Section 3, Eq. 3.11-3.14, the
+ * grid-point form of the interstitial integrals) of a Slater-type basis: over the nodes
+ * outside every sphere (|P - pos_a| < R_a excludes a node), with Vol(P) the dual-cell volume,
+ *   S_ab = sum_P phi_a phi_b Vol,  H_ab = 1/2 sum_P (phi_a phi~_b + phi~_a phi_b) Vol,
+ * phi = r^(n-1) e^{-zeta r} y_lm about the function's atom (Eq. 3.13) and
+ * phi~ = -1/2 Lap phi + V phi (Eq. 3.14, the radial Laplacian in closed form).
+ * Basis (HOST arrays of nb <= 8 entries): principal number bn >= bl + 1, angular number
+ * bl <= 4, exponent bz > 0; per atom sum(2 bl + 1) <= 64 functions.  Functions are
+ * atom-major, then in the table's order, then m = -l..l (y_lm the real harmonics of the
+ * solver's projections).  Device arrays: x, y, z node coordinates [n[d]]; pos [n_atoms][3];
+ * R [n_atoms]; V the potential energy at the nodes [n[2]][n[1]][n[0]] (x fastest);
+ * S, H [M][M] with M = n_atoms * functions per atom, written whole (symmetric).
+ * Basis values in FP32 (weighted by sqrt(Vol)); mode LASTO_HS_TENSOR (the default) contracts
+ * them on the tensor cores, each value split into two TF32 parts and a product taken as
+ * hi*hi + hi*lo + lo*hi, FP32 accumulation over 512-node intervals added in FP64;
+ * LASTO_HS_SIMT takes FP32 products summed over 32-node steps, added in FP64.  Allocates its
+ * scratch stream-ordered (at most about 2 GiB of basis tables, 8 bytes per node and 256 KiB
+ * per SM) and synchronises the stream twice.  INVALID_ARG for bad sizes, basis or mode,
+ * n[0] n[1] n[2] >= 2^31 or M > 65536; NO_MEMORY when the scratch cannot be had; TIMEOUT when
+ * a bounded wait of the tensor-core kernel ran out (outputs then undefined). */
+enum lasto_hs_mode { LASTO_HS_DEFAULT = 0, LASTO_HS_SIMT = 1, LASTO_HS_TENSOR = 2 };
+int lasto_op_interstitial_hs(const int n[3], const double* x, const double* y, const double* z, int n_atoms,
+                             const double* pos, const double* R, int nb, const int* bn, const int* bl, const double* bz,
+                             const double* V, double* S, double* H, int mode, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,7 +56,7 @@ EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve"
            "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_boundary_exact", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
            "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
-           "lasto_op_project", "lasto_op_sphere_density", "lasto_op_inner_solve", "lasto_guess_param_count", "lasto_poisson_set_guess",
+           "lasto_op_project", "lasto_op_sphere_density", "lasto_op_inner_solve", "lasto_op_interstitial_hs", "lasto_guess_param_count", "lasto_poisson_set_guess",
            "lasto_poisson_tune_table", "lasto_poisson_set_tune_table", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
            "lasto_nn_relu_grad", "lasto_nn_to_bf16", "lasto_nn_copy_channels", "lasto_nn_down", "lasto_nn_up",
            "lasto_nn_mse", "lasto_nn_adam", "lasto_nn_guess_features", "lasto_nn_guess_grid"]
@@ -104,6 +104,8 @@ def _declare(L):
         "lasto_op_project": (i, [ip, vp, vp, vp, vp, i, vp, vp, i, i, vp, vp, vp]),
         "lasto_op_sphere_density": (i, [clp, i, d, i, i, vp, vp, vp]),
         "lasto_op_inner_solve": (i, [i, vp, vp, i, d, vp, vp, vp, vp]),
+        "lasto_op_interstitial_hs": (i, [ip, vp, vp, vp, i, vp, vp, i, ip, ip, ctypes.POINTER(ctypes.c_double), vp,
+                                         vp, vp, i, vp]),
         "lasto_nn_conv3d_fwd": (i, [i, ip, i, i, vp, vp, vp, i, vp, i, i, vp, i, i, vp]),
         "lasto_nn_pack_weights": (i, [i, i, vp, vp, vp]),
         "lasto_nn_conv3d_fwd_tc": (i, [i, ip, i, i, vp, vp, vp, i, vp, i, i, vp, i, i, vp, vp]),
@@ -437,6 +439,29 @@ def lasto_op_inner_solve(R, Z, rho_lm, v_R, r_min=1e-5, stream=None):
     _check(load().lasto_op_inner_solve(int(R.shape[0]), _ptr(R), _ptr(Z), int(rho_lm.shape[2]), float(r_min),
                                        _ptr(rho_lm), _ptr(v_R), _ptr(v), _stream(stream)), "lasto_op_inner_solve")
     return v
+
+
+# the basis of Table 1 per Pd atom: (n, l, zeta) of 4d, 5d, 5s, 5p, 6s, 6p, 4f
+PD_BASIS = [(4, 2, 2.20), (5, 2, 2.60), (5, 0, 1.00), (5, 1, 1.00), (6, 0, 2.00), (6, 1, 2.00), (4, 3, 1.60)]
+
+LASTO_HS_DEFAULT, LASTO_HS_SIMT, LASTO_HS_TENSOR = 0, 1, 2
+
+
+def lasto_op_interstitial_hs(x, y, z, pos, R, V, basis=PD_BASIS, mode=LASTO_HS_DEFAULT, stream=None):
+    """(S, H) [M][M] over the nodes outside every sphere (Eq. 3.11-3.14, grid-point form);
+    V the potential energy at the nodes [nz][ny][nx]; M = n_atoms * sum(2l + 1)."""
+    n = (ctypes.c_int * 3)(int(x.shape[0]), int(y.shape[0]), int(z.shape[0]))
+    bn = (ctypes.c_int * len(basis))(*[int(b[0]) for b in basis])
+    bl = (ctypes.c_int * len(basis))(*[int(b[1]) for b in basis])
+    bz = (ctypes.c_double * len(basis))(*[float(b[2]) for b in basis])
+    na = int(R.shape[0])
+    M = na * sum(2 * int(b[1]) + 1 for b in basis)
+    S = torch.empty((M, M), dtype=torch.float64, device=x.device)
+    H = torch.empty_like(S)
+    _check(load().lasto_op_interstitial_hs(n, _ptr(x), _ptr(y), _ptr(z), na, _ptr(pos), _ptr(R), len(basis), bn, bl,
+                                           bz, _ptr(V), _ptr(S), _ptr(H), int(mode), _stream(stream)),
+           "lasto_op_interstitial_hs")
+    return S, H
 
 
 def lasto_op_boundary_exact(dc: DeviceCluster, u, stream=None):

@@ -1613,4 +1613,21 @@ int lasto_op_inner_solve(int n_atoms, const double* R, const double* Z, int n_ra
     return op_status(launch_inner_solve(n_atoms, R, Z, n_rad, r_min, rho_lm, v_R, v, (cudaStream_t)stream));
 }
 
+int lasto_op_interstitial_hs(const int n[3], const double* x, const double* y, const double* z, int n_atoms,
+                             const double* pos, const double* R, int nb, const int* bn, const int* bl, const double* bz,
+                             const double* V, double* S, double* H, int mode, void* stream)
+{
+    if (!n || !x || !y || !z || n_atoms < 1 || !pos || !R || !V || !S || !H || S == H) return LASTO_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++)
+        if (n[d] < 2) return LASTO_ERR_INVALID_ARG;
+    if ((size_t)n[0] * n[1] * n[2] >= ((size_t)1 << 31)) return LASTO_ERR_INVALID_ARG;
+    int per = 0;
+    if (hs_basis_check(nb, bn, bl, bz, &per) != LASTO_OK) return LASTO_ERR_INVALID_ARG;
+    if ((size_t)n_atoms * per > 65536) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch w(hs_scratch_bytes(n, n_atoms * per), s);
+    if (!w.p) return LASTO_ERR_NO_MEMORY;
+    return launch_interstitial_hs(n, x, y, z, n_atoms, pos, R, nb, bn, bl, bz, V, S, H, w.p, mode, s);
+}
+
 }  // extern "C"
