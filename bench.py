@@ -55,11 +55,13 @@ def parse():
     p.add_argument("--quiet", action="store_true")
     p.add_argument("--no-batch64", action="store_true")
     p.add_argument("--no-pd561", action="store_true")
-    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561"], default=None,
+    p.add_argument("--no-hs", action="store_true")
+    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "hs"], default=None,
                    help="run one kernel family for a profiler and exit: 'smoother' = one FP32 red-black sweep "
                         "on an n^3 graded mesh, 'solve' = one mixed solve of the workload with direct launches, "
                         "'guess' = the same with the learned initial guess, 'pd561' = one chosen-form solve "
-                        "of the Pd561 graded 385^3 workload with direct launches")
+                        "of the Pd561 graded 385^3 workload with direct launches, 'hs' = one interstitial H and S "
+                        "call (tensor cores) for Pd55 on the graded 129^3 mesh")
     p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
     p.add_argument("--direct", action="store_true",
                    help="launch the kernels directly instead of one CUDA graph per solve (for ncu)")
@@ -348,6 +350,11 @@ def main():
     if not args.no_pd561:
         pd561 = pd561_sequence(B, synth, flush, stream, dev)
 
+    # ---------------- the interstitial H and S contraction (Eq. 3.11-3.14)
+    hs = None
+    if not args.no_hs:
+        hs = interstitial_hs(B, synth, flush, stream, dev)
+
     # ---------------- roofline of the dominant kernel (FP32 red-black half sweep)
     roof = smoother_roofline(B, stream, flush, dev)
     roof["deposit_fp32pair_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 1)["ms"]
@@ -378,6 +385,7 @@ def main():
             "forms": forms,
             "batch64_uneven": b64,
             "pd561_graded385": pd561,
+            "interstitial_hs": hs,
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": r_chosen["launches"],
@@ -396,7 +404,18 @@ def run_profile(args, B):
     import torch
 
     import synth
-    if args.profile == "smoother":
+    if args.profile == "hs":
+        cl = synth.pd55_graded129()
+        dc = B.DeviceCluster(cl)
+        x, y, z = (t.cpu().numpy() for t in (dc.x, dc.y, dc.z))
+        V = torch.as_tensor(synth.potential_energy(cl.pos, x, y, z, seed=5)).cuda()
+        B.lasto_op_interstitial_hs(dc.x, dc.y, dc.z, dc.pos, dc.R, V)   # untimed first call
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        B.lasto_op_interstitial_hs(dc.x, dc.y, dc.z, dc.pos, dc.R, V)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+    elif args.profile == "smoother":
         n = args.n
         axes = [B.lasto_mesh_axis(n, 0.0, 30.0, 0.12, 0.6, 6.0) for _ in range(3)]
         u = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
@@ -499,6 +518,59 @@ def pd561_sequence(B, synth, flush, stream, dev):
         torch.cuda.empty_cache()
     out["nodes"] = c0.n ** 3
     out["chosen_over_plain"] = out["chosen"]["value"] / out["plain_fp64"]["value"]
+    return out
+
+
+def interstitial_hs(B, synth, flush, stream, dev):
+    """The interstitial H and S contributions (Eq. 3.11-3.14) of Table 1's basis (25 functions
+    per Pd atom) for Pd55 on the graded 129^3 mesh, V a seeded potential-energy field: the
+    whole call and its stages (CUDA events inside the call), tensor-core and SIMT contractions.
+    Tensor-pipe work per interstitial node: 9 MMAs of 128 x 128 x 8 per 8 nodes per
+    upper-triangle tile pair (3 for S, 6 for 2H, hi*hi + hi*lo + lo*hi each); algorithmic work:
+    6 flops per node per (a <= b) entry (S: 1 product, 2H: 2)."""
+    import json as _json
+    import torch
+    cl = synth.pd55_graded129()
+    dc = B.DeviceCluster(cl)
+    x, y, z = (t.cpu().numpy() for t in (dc.x, dc.y, dc.z))
+    V = torch.as_tensor(synth.potential_energy(cl.pos, x, y, z, seed=5)).to(dev)
+    out = {"workload": f"{cl.name}, Table 1 basis (25 functions per atom)"}
+    for name, mode in (("tensor", B.LASTO_HS_TENSOR), ("simt", B.LASTO_HS_SIMT)):
+        st = B.lasto_hs_stats()
+        B.lasto_op_interstitial_hs(dc.x, dc.y, dc.z, dc.pos, dc.R, V, mode=mode)   # warm-up
+        ms = []
+        for _ in range(3 if name == "tensor" else 1):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            S, H = B.lasto_op_interstitial_hs(dc.x, dc.y, dc.z, dc.pos, dc.R, V, mode=mode, stats=st)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out[name] = {"ms": min(ms), "ms_contract": st.ms_contract, "ms_tables": st.ms_tables, "ms_list": st.ms_list,
+                     "ms_mirror": st.ms_mirror, "chunks": st.chunks, "tile": st.tile}
+        M = S.shape[0]
+        nodes = st.interstitial_nodes
+        out["M"], out["interstitial_nodes"] = M, nodes
+        del S, H
+    nT = (out["M"] + 127) // 128
+    pairs = nT * (nT + 1) // 2
+    tensor_flops = 9 * 2 * 128 * 128 * pairs * out["interstitial_nodes"]
+    alg_flops = 6 * (out["M"] * (out["M"] + 1) // 2) * out["interstitial_nodes"]
+    peaks = {}
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tf32_peak = bf16 * 1.1 / 2.25   # the nominal dense TF32 : BF16 ratio
+    t = out["tensor"]["ms_contract"] / 1e3
+    out["roofline"] = {"kernel": "k_hs_gemm_tc", "bound": "tensor", "achieved": tensor_flops / t / 1e12,
+                       "peak": tf32_peak, "unit": "TFLOP/s", "frac": tensor_flops / t / 1e12 / tf32_peak,
+                       "traffic": None,
+                       "peak_source": ("measured bf16 burst x 1.1/2.25 (nominal TF32:BF16)" if "bf16_tflops" in peaks
+                                       else "fallback bf16 x 1.1/2.25")}
+    out["algorithmic_tflops"] = {"tensor": alg_flops / t / 1e12,
+                                 "simt": alg_flops / (out["simt"]["ms_contract"] / 1e3) / 1e12}
+    out["tensor_over_simt"] = out["simt"]["ms"] / out["tensor"]["ms"]
     return out
 
 

@@ -457,17 +457,30 @@ int lasto_nn_adam(size_t n, float* w, const float* g, float* m, float* v, float 
  * R [n_atoms]; V the potential energy at the nodes [n[2]][n[1]][n[0]] (x fastest);
  * S, H [M][M] with M = n_atoms * functions per atom, written whole (symmetric).
  * Basis values in FP32 (weighted by sqrt(Vol)); mode LASTO_HS_TENSOR (the default) contracts
- * them on the tensor cores, each value split into two TF32 parts and a product taken as
- * hi*hi + hi*lo + lo*hi, FP32 accumulation over 512-node intervals added in FP64;
- * LASTO_HS_SIMT takes FP32 products summed over 32-node steps, added in FP64.  Allocates its
- * scratch stream-ordered (at most about 2 GiB of basis tables, 8 bytes per node and 256 KiB
- * per SM) and synchronises the stream twice.  INVALID_ARG for bad sizes, basis or mode,
+ * them on the tensor cores: each value, scaled by a power of two per function (one more
+ * common power of two for phi~) below 2^14, is split into two FP16 parts and a product taken
+ * as hi*hi + hi*lo + lo*hi (22 significant bits), FP32 accumulation over 512-node intervals
+ * added in FP64 with the scales undone; LASTO_HS_SIMT takes FP32 products summed over 32-node
+ * steps, added in FP64.  Sums across CTAs meet by FP64 atomic addition, so the last bits may
+ * differ between calls.  Allocates its scratch stream-ordered (at most about 2 GiB of basis
+ * tables, 8 bytes per node and 256 KiB per SM) and synchronises the stream twice.  INVALID_ARG for bad sizes, basis or mode,
  * n[0] n[1] n[2] >= 2^31 or M > 65536; NO_MEMORY when the scratch cannot be had; TIMEOUT when
  * a bounded wait of the tensor-core kernel ran out (outputs then undefined). */
 enum lasto_hs_mode { LASTO_HS_DEFAULT = 0, LASTO_HS_SIMT = 1, LASTO_HS_TENSOR = 2 };
+/* stats (host, may be NULL): what the call did and the device time of its stages (CUDA events
+ * on the stream; all chunks summed). */
+typedef struct lasto_hs_stats {
+    long long interstitial_nodes;   /* nodes outside every sphere */
+    int chunks;                     /* basis-table chunks */
+    int tile;                       /* tile side of the contraction: 128 tensor, 64 SIMT */
+    float ms_list;                  /* interstitial node list */
+    float ms_tables;                /* basis tables */
+    float ms_contract;              /* contraction */
+    float ms_mirror;                /* lower triangle and the 1/2 of H */
+} lasto_hs_stats;
 int lasto_op_interstitial_hs(const int n[3], const double* x, const double* y, const double* z, int n_atoms,
                              const double* pos, const double* R, int nb, const int* bn, const int* bl, const double* bz,
-                             const double* V, double* S, double* H, int mode, void* stream);
+                             const double* V, double* S, double* H, int mode, lasto_hs_stats* stats, void* stream);
 
 #ifdef __cplusplus
 }

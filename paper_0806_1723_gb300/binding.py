@@ -105,7 +105,7 @@ def _declare(L):
         "lasto_op_sphere_density": (i, [clp, i, d, i, i, vp, vp, vp]),
         "lasto_op_inner_solve": (i, [i, vp, vp, i, d, vp, vp, vp, vp]),
         "lasto_op_interstitial_hs": (i, [ip, vp, vp, vp, i, vp, vp, i, ip, ip, ctypes.POINTER(ctypes.c_double), vp,
-                                         vp, vp, i, vp]),
+                                         vp, vp, i, ctypes.POINTER(lasto_hs_stats), vp]),
         "lasto_nn_conv3d_fwd": (i, [i, ip, i, i, vp, vp, vp, i, vp, i, i, vp, i, i, vp]),
         "lasto_nn_pack_weights": (i, [i, i, vp, vp, vp]),
         "lasto_nn_conv3d_fwd_tc": (i, [i, ip, i, i, vp, vp, vp, i, vp, i, i, vp, i, i, vp, vp]),
@@ -441,15 +441,22 @@ def lasto_op_inner_solve(R, Z, rho_lm, v_R, r_min=1e-5, stream=None):
     return v
 
 
+class lasto_hs_stats(ctypes.Structure):
+    _fields_ = [("interstitial_nodes", ctypes.c_longlong), ("chunks", ctypes.c_int), ("tile", ctypes.c_int),
+                ("ms_list", ctypes.c_float), ("ms_tables", ctypes.c_float), ("ms_contract", ctypes.c_float),
+                ("ms_mirror", ctypes.c_float)]
+
+
 # the basis of Table 1 per Pd atom: (n, l, zeta) of 4d, 5d, 5s, 5p, 6s, 6p, 4f
 PD_BASIS = [(4, 2, 2.20), (5, 2, 2.60), (5, 0, 1.00), (5, 1, 1.00), (6, 0, 2.00), (6, 1, 2.00), (4, 3, 1.60)]
 
 LASTO_HS_DEFAULT, LASTO_HS_SIMT, LASTO_HS_TENSOR = 0, 1, 2
 
 
-def lasto_op_interstitial_hs(x, y, z, pos, R, V, basis=PD_BASIS, mode=LASTO_HS_DEFAULT, stream=None):
+def lasto_op_interstitial_hs(x, y, z, pos, R, V, basis=PD_BASIS, mode=LASTO_HS_DEFAULT, stream=None, stats=None):
     """(S, H) [M][M] over the nodes outside every sphere (Eq. 3.11-3.14, grid-point form);
-    V the potential energy at the nodes [nz][ny][nx]; M = n_atoms * sum(2l + 1)."""
+    V the potential energy at the nodes [nz][ny][nx]; M = n_atoms * sum(2l + 1).  stats: an
+    optional lasto_hs_stats filled with the node count and stage times."""
     n = (ctypes.c_int * 3)(int(x.shape[0]), int(y.shape[0]), int(z.shape[0]))
     bn = (ctypes.c_int * len(basis))(*[int(b[0]) for b in basis])
     bl = (ctypes.c_int * len(basis))(*[int(b[1]) for b in basis])
@@ -459,7 +466,8 @@ def lasto_op_interstitial_hs(x, y, z, pos, R, V, basis=PD_BASIS, mode=LASTO_HS_D
     S = torch.empty((M, M), dtype=torch.float64, device=x.device)
     H = torch.empty_like(S)
     _check(load().lasto_op_interstitial_hs(n, _ptr(x), _ptr(y), _ptr(z), na, _ptr(pos), _ptr(R), len(basis), bn, bl,
-                                           bz, _ptr(V), _ptr(S), _ptr(H), int(mode), _stream(stream)),
+                                           bz, _ptr(V), _ptr(S), _ptr(H), int(mode),
+                                           ctypes.byref(stats) if stats is not None else None, _stream(stream)),
            "lasto_op_interstitial_hs")
     return S, H
 

@@ -1615,7 +1615,8 @@ int lasto_op_inner_solve(int n_atoms, const double* R, const double* Z, int n_ra
 
 int lasto_op_interstitial_hs(const int n[3], const double* x, const double* y, const double* z, int n_atoms,
                              const double* pos, const double* R, int nb, const int* bn, const int* bl, const double* bz,
-                             const double* V, double* S, double* H, int mode, void* stream)
+                             const double* V, double* S, double* H, int mode, lasto_hs_stats* stats,
+                             void* stream)
 {
     if (!n || !x || !y || !z || n_atoms < 1 || !pos || !R || !V || !S || !H || S == H) return LASTO_ERR_INVALID_ARG;
     for (int d = 0; d < 3; d++)
@@ -1625,9 +1626,9 @@ int lasto_op_interstitial_hs(const int n[3], const double* x, const double* y, c
     if (hs_basis_check(nb, bn, bl, bz, &per) != LASTO_OK) return LASTO_ERR_INVALID_ARG;
     if ((size_t)n_atoms * per > 65536) return LASTO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    Scratch w(hs_scratch_bytes(n, n_atoms * per), s);
+    Scratch w(hs_scratch_bytes(n, n_atoms * per, n_atoms), s);
     if (!w.p) return LASTO_ERR_NO_MEMORY;
-    return launch_interstitial_hs(n, x, y, z, n_atoms, pos, R, nb, bn, bl, bz, V, S, H, w.p, mode, s);
+    return launch_interstitial_hs(n, x, y, z, n_atoms, pos, R, nb, bn, bl, bz, V, S, H, w.p, mode, stats, s);
 }
 
 }  // extern "C"

@@ -18,6 +18,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace lasto {
@@ -36,6 +38,25 @@ struct MonoF32 {
     float coef;
     unsigned char a, b, c, pad;
 };
+
+// The 56 monomial terms of the real solid harmonics r^l y_lm (l <= 4) as (index, lm, a, b, c)
+// of x^a y^b z^c, in the order of the library's monomial table (checked against it at setup);
+// the coefficients come from that table.
+#define HS_TERMS(X)                                                                                              \
+    X(0, 0, 0, 0, 0) X(1, 1, 0, 1, 0) X(2, 2, 0, 0, 1) X(3, 3, 1, 0, 0) X(4, 4, 1, 1, 0) X(5, 5, 0, 1, 1)        \
+    X(6, 6, 0, 0, 2) X(7, 6, 2, 0, 0) X(8, 6, 0, 2, 0) X(9, 7, 1, 0, 1) X(10, 8, 2, 0, 0) X(11, 8, 0, 2, 0)      \
+    X(12, 9, 2, 1, 0) X(13, 9, 0, 3, 0) X(14, 10, 1, 1, 1) X(15, 11, 0, 1, 2) X(16, 11, 2, 1, 0)                 \
+    X(17, 11, 0, 3, 0) X(18, 12, 0, 0, 3) X(19, 12, 2, 0, 1) X(20, 12, 0, 2, 1) X(21, 13, 1, 0, 2)               \
+    X(22, 13, 3, 0, 0) X(23, 13, 1, 2, 0) X(24, 14, 2, 0, 1) X(25, 14, 0, 2, 1) X(26, 15, 3, 0, 0)               \
+    X(27, 15, 1, 2, 0) X(28, 16, 3, 1, 0) X(29, 16, 1, 3, 0) X(30, 17, 2, 1, 1) X(31, 17, 0, 3, 1)               \
+    X(32, 18, 1, 1, 2) X(33, 18, 3, 1, 0) X(34, 18, 1, 3, 0) X(35, 19, 0, 1, 3) X(36, 19, 2, 1, 1)               \
+    X(37, 19, 0, 3, 1) X(38, 20, 0, 0, 4) X(39, 20, 4, 0, 0) X(40, 20, 0, 4, 0) X(41, 20, 2, 2, 0)               \
+    X(42, 20, 2, 0, 2) X(43, 20, 0, 2, 2) X(44, 21, 1, 0, 3) X(45, 21, 3, 0, 1) X(46, 21, 1, 2, 1)               \
+    X(47, 22, 2, 0, 2) X(48, 22, 0, 2, 2) X(49, 22, 4, 0, 0) X(50, 22, 0, 4, 0) X(51, 23, 3, 0, 1)               \
+    X(52, 23, 1, 2, 1) X(53, 24, 4, 0, 0) X(54, 24, 2, 2, 0) X(55, 24, 0, 4, 0)
+constexpr int HS_L3_TERMS = 28;   // terms of l <= 3 (the l = 4 terms follow)
+
+__constant__ float c_hs_coef[N_MONO_TERMS];
 
 __constant__ MonoF32 c_hs_mono[N_MONO_TERMS];   // grouped by lm
 __constant__ int c_hs_first[NLM + 1];            // terms of lm: [first[lm], first[lm+1])
@@ -61,7 +82,15 @@ cudaError_t ensure_hs_tables()
                 o.push_back(MonoF32{(float)m.coef, (unsigned char)m.a, (unsigned char)m.b, (unsigned char)m.c, 0});
     }
     first[NLM] = (int)o.size();
-    e = cudaMemcpyToSymbol(c_hs_mono, o.data(), sizeof(MonoF32) * o.size());
+    bool same = true;
+#define HS_CHECK(i, LM, EA, EB, EC) same = same && t[i].lm == LM && t[i].a == EA && t[i].b == EB && t[i].c == EC;
+    HS_TERMS(HS_CHECK)
+#undef HS_CHECK
+    if (!same) return cudaErrorInvalidValue;
+    float coef[N_MONO_TERMS];
+    for (int i = 0; i < N_MONO_TERMS; i++) coef[i] = (float)t[i].coef;
+    e = cudaMemcpyToSymbol(c_hs_coef, coef, sizeof(coef));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hs_mono, o.data(), sizeof(MonoF32) * o.size());
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_hs_first, first, sizeof(first));
     if (e == cudaSuccess) g_hs_device = dev;
     return e;
@@ -69,7 +98,8 @@ cudaError_t ensure_hs_tables()
 
 struct HsBasis {
     int per;                        // functions per atom
-    int n[HS_MAXB], l[HS_MAXB];
+    int nb, lmax;
+    int n[HS_MAXB], l[HS_MAXB], off[HS_MAXB];   // off: first function of the entry within its atom
     float zeta[HS_MAXB];
     unsigned char q_of[HS_MAXF];    // function within an atom -> table entry
     signed char m_of[HS_MAXF];      // -> m
@@ -80,14 +110,30 @@ struct HsGrid {
     const double *x, *y, *z, *pos, *R;
 };
 
-__device__ __forceinline__ bool hs_inside(const HsGrid& g, int i, int j, int k)
+// Inside a sphere: |P - pos_a| < R_a in FP64; an FP32 pass settles every atom whose squared
+// distance is not within 0.1 % of R_a^2 (FP32 rounding of the coordinates moves it by < 1e-5).
+__device__ __forceinline__ bool hs_inside(const HsGrid& g, const float4* __restrict__ at4, int i, int j, int k)
 {
+    const float px = (float)g.x[i], py = (float)g.y[j], pz = (float)g.z[k];
     for (int a = 0; a < g.na; a++) {
-        const double dx = g.x[i] - g.pos[3 * a], dy = g.y[j] - g.pos[3 * a + 1], dz = g.z[k] - g.pos[3 * a + 2];
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        if (sqrt(d2) < g.R[a]) return true;
+        const float4 A = __ldg(at4 + a);
+        const float ex = px - A.x, ey = py - A.y, ez = pz - A.z;
+        const float d2f = ex * ex + ey * ey + ez * ez;
+        if (d2f < 0.999f * A.w) return true;
+        if (d2f <= 1.001f * A.w) {
+            const double dx = g.x[i] - g.pos[3 * a], dy = g.y[j] - g.pos[3 * a + 1], dz = g.z[k] - g.pos[3 * a + 2];
+            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            if (sqrt(d2) < g.R[a]) return true;
+        }
     }
     return false;
+}
+
+// FP32 copies of the spheres for the prefilter: (x, y, z, R^2)
+__global__ void k_hs_atoms(int na, const double* __restrict__ pos, const double* __restrict__ R, float4* __restrict__ at4)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < na) at4[a] = make_float4((float)pos[3 * a], (float)pos[3 * a + 1], (float)pos[3 * a + 2], (float)(R[a] * R[a]));
 }
 
 __device__ __forceinline__ double hs_dual(const double* c, int n, int q)
@@ -118,7 +164,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int* warp_tot, int& total)
 }
 
 // (1a) interstitial nodes per block of HS_CNT nodes
-__global__ void __launch_bounds__(256) k_hs_count(HsGrid g, int* __restrict__ cnt)
+__global__ void __launch_bounds__(256) k_hs_count(HsGrid g, const float4* __restrict__ at4, int* __restrict__ cnt)
 {
     __shared__ int wt[8];
     const size_t N = (size_t)g.nx * g.ny * g.nz;
@@ -127,7 +173,7 @@ __global__ void __launch_bounds__(256) k_hs_count(HsGrid g, int* __restrict__ cn
         const size_t P = (size_t)blockIdx.x * HS_CNT + e * 256 + threadIdx.x;
         if (P < N) {
             const int i = (int)(P % g.nx), j = (int)((P / g.nx) % g.ny), k = (int)(P / ((size_t)g.nx * g.ny));
-            c += !hs_inside(g, i, j, k);
+            c += !hs_inside(g, at4, i, j, k);
         }
     }
     int total;
@@ -152,8 +198,8 @@ __global__ void __launch_bounds__(1024) k_hs_scan(int nblk, const int* __restric
 }
 
 // (1c) list the interstitial nodes of each block in grid order, with sqrt(Vol)
-__global__ void __launch_bounds__(256) k_hs_scatter(HsGrid g, const int* __restrict__ off, int* __restrict__ idx,
-                                                    float* __restrict__ sw)
+__global__ void __launch_bounds__(256) k_hs_scatter(HsGrid g, const float4* __restrict__ at4, const int* __restrict__ off,
+                                                    int* __restrict__ idx, float* __restrict__ sw)
 {
     __shared__ int wt[8];
     const size_t N = (size_t)g.nx * g.ny * g.nz;
@@ -165,7 +211,7 @@ __global__ void __launch_bounds__(256) k_hs_scatter(HsGrid g, const int* __restr
             i = (int)(P % g.nx);
             j = (int)((P / g.nx) % g.ny);
             k = (int)(P / ((size_t)g.nx * g.ny));
-            f = !hs_inside(g, i, j, k);
+            f = !hs_inside(g, at4, i, j, k);
         }
         int total;
         const int ex = block_excl_scan(f, wt, total);
@@ -304,58 +350,42 @@ __global__ void __launch_bounds__(HS_NT) k_hs_gemm_f32(int M, int Mp, int nT, co
         }
 }
 
-// (3') The same contraction on the fifth-generation tensor cores: tcgen05.mma kind::tf32 with
-// 128 x 128 function tiles (M = N = 128, K = 8 nodes per MMA) and FP32 accumulators in tensor
-// memory.  Each FP32 table value x is split into x_hi = x rounded to TF32 (10 stored mantissa
-// bits) and x_lo = x - x_hi rounded to TF32; a product is formed as hi*hi + hi*lo + lo*hi
-// (the dropped lo*lo is below 2^-21 of it), so S takes 3 MMAs per K step and 2H = A_I T_J^T +
-// T_I A_J^T takes 6, all accumulating into two 128-column tensor-memory regions.
+// (2', 3') The contraction on the fifth-generation tensor cores.  Every table value x (A or
+// T, scaled by a power of two per function so that |x| < 2^14) is split into two FP16 parts,
+// x_hi = fp16(x) and x_lo = fp16(x - x_hi), 22 significant bits together (the splitting error
+// stays below 2^-25 absolute in scaled units, far under FP32 rounding of the sums); a product
+// is taken as hi*hi + hi*lo + lo*hi (the dropped lo*lo is below 2^-22 of it), exact in the FP32
+// accumulator.  So S takes 3 tcgen05.mma kind::f16 (M = N = 128, K = 16 nodes) per 16 nodes
+// and 2H = A_I T_J^T + T_I A_J^T takes 6, into two 128-column tensor-memory regions.
 //
-// A work unit is one upper-triangle tile and one segment of HS_SEG table rows; units are
-// numbered segment-major so that the CTAs running at one time read the same table rows (which
-// stay in L2).  A CTA's 256 threads produce the operands of a 16-node stage (thread m, h: row
-// m, nodes 8h .. 8h+7) from the FP32 tables into a ring of three shared-memory stages in the
-// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix; the two K halves
-// of an MMA 128 bytes apart, 8-row groups 256 bytes apart), the next stage's table values
-// already loaded into registers; one thread issues the stage's 18 MMAs and commits them to the
-// stage's mbarrier, which frees the stage.  Every HS_IV nodes the accumulation moves to the
-// other pair of tensor-memory regions while the finished pair is read (tcgen05.ld) and added
-// into the CTA's FP64 partial sums in global memory; at the end of a unit the partial sums go
-// to S and 2H by FP64 atomic addition.  Every mbarrier wait is bounded; on a timeout the CTA
-// records an error, stops issuing, waits (bounded) for its last MMAs, frees its tensor memory
-// and returns.
-constexpr int TC_TM = 128;                         // functions per tile side (MMA M and N)
-constexpr int TC_NT = 256;                         // threads
-constexpr int TC_SK = 16;                          // nodes per stage
-constexpr int TC_RING = 3;                         // stages in shared memory
-constexpr int TC_SLOT = TC_TM * TC_SK * 4;         // one operand of one stage: 8 KB
-constexpr int TC_STAGE = 8 * TC_SLOT;              // A_I, T_I, A_J, T_J, each hi and lo
-constexpr int TC_SMEM = TC_RING * TC_STAGE + 128;  // + alignment slack
-constexpr int HS_IV = 512;                         // nodes per FP32 accumulation interval
-constexpr int HS_SEG = 4096;                       // nodes per work unit
-constexpr long long TC_SPIN = 1LL << 20;
+// The table kernel writes the operands already in the MMA's shared-memory layout (no-swizzle
+// K-major core matrices of 8 rows x 16 bytes; the two 8-node halves of a K step 128 bytes
+// apart, 8-function groups 256 bytes apart): one 4 KiB image per (16 nodes, 128 functions,
+// array), the four arrays (A_hi, A_lo, T_hi, T_lo) of a block adjacent, so that a stage of a
+// tile is two 16 KiB bulk copies (cp.async.bulk, completion counted on an mbarrier).
+//
+// Warp roles: one thread issues the bulk copies into a ring of six 32 KiB stages, one thread
+// issues the MMAs (and frees a stage by tcgen05.commit to its mbarrier), four warps drain the
+// accumulators every HS_IV nodes (tcgen05.ld; tensor-memory lane = function row) into the
+// CTA's FP64 partial sums, undoing the scales, while the MMAs fill the other pair of regions.
+// A work unit is one upper-triangle tile and HS_SEG nodes, numbered segment-major so that the
+// CTAs running together read the same table rows (from L2); at a unit's end its partial sums
+// go to S and 2H by FP64 atomic addition.  Every wait is bounded (about two seconds, or until
+// another role has given up): the CTA then records an error, lets its copies and MMAs in
+// flight finish (bounded), frees its tensor memory and returns.
+constexpr int TC_TM = 128;                       // functions per tile side (MMA M and N)
+constexpr int TC_NT = 256;                       // threads
+constexpr int TC_SK = 16;                        // nodes per stage (one MMA K step)
+constexpr int TC_IMG = TC_TM * TC_SK * 2;        // one FP16 operand image: 4 KiB
+constexpr int TC_SIDE = 4 * TC_IMG;              // A_hi, A_lo, T_hi, T_lo of one function block
+constexpr int TC_STAGE = 2 * TC_SIDE;            // the I and J blocks of a tile
+constexpr int TC_RING = 6;
+constexpr int TC_SMEM = TC_RING * TC_STAGE + 128;
+constexpr int HS_IV = 512;                       // nodes per FP32 accumulation interval
+constexpr int HS_SEG = 2048;                     // nodes per work unit
+constexpr int HS_SCALE_MAX = 14;                 // scaled |x| < 2^14
 
 __device__ __forceinline__ uint32_t hs_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// round to TF32 (nearest, ties away from zero, on the magnitude)
-__device__ __forceinline__ float tf32_round(float v)
-{
-    return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
-}
-
-__device__ __forceinline__ uint64_t hs_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(128 >> 4) << 16;   // leading byte offset: the second K half
-    d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset: the next 8-row group
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// FP32 accumulator, TF32 A and B, both K-major, M = N = 128
-constexpr uint32_t HS_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_TM >> 3) << 17) |
-                              ((uint32_t)(TC_TM >> 4) << 24);
 
 __device__ __forceinline__ uint64_t hs_now()
 {
@@ -364,11 +394,12 @@ __device__ __forceinline__ uint64_t hs_now()
     return t;
 }
 
-// bounded wait on an mbarrier phase: false after about two seconds
-__device__ __forceinline__ bool hs_wait(uint32_t mbar, uint32_t parity)
+// Bounded wait on an mbarrier phase: false after about two seconds or once *abort is set
+// (then *abort is set).
+__device__ __forceinline__ bool hs_wait(uint32_t mbar, uint32_t parity, volatile int* abort)
 {
     uint64_t t0 = 0;
-    for (long long it = 0; it < TC_SPIN; it++) {
+    for (;;) {
         uint32_t ok;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -376,22 +407,43 @@ __device__ __forceinline__ bool hs_wait(uint32_t mbar, uint32_t parity)
             : "r"(mbar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (*abort) return false;
         const uint64_t t = hs_now();
-        if (t0 == 0)
+        if (t0 == 0) {
             t0 = t;
-        else if (t - t0 > 2000000000ull)
+        } else if (t - t0 > 2000000000ull) {
+            *abort = 1;
             return false;
+        }
     }
-    return false;
 }
+
+__device__ __forceinline__ uint64_t hs_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;   // leading byte offset: the second 8-node half
+    d |= (uint64_t)(256 >> 4) << 32;   // stride byte offset: the next 8-function group
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// FP32 accumulator, FP16 A and B, both K-major, M = N = 128
+constexpr uint32_t HS_IDESC = (1u << 4) | ((uint32_t)(TC_TM >> 3) << 17) | ((uint32_t)(TC_TM >> 4) << 24);
 
 __device__ __forceinline__ void hs_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc)
 {
     asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             tmem),
         "l"(a), "l"(b), "r"(HS_IDESC), "r"(acc)
         : "memory");
+}
+
+__device__ __forceinline__ void hs_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
 }
 
 __device__ __forceinline__ void hs_tmem_ld16(uint32_t taddr, float* v)
@@ -405,6 +457,173 @@ __device__ __forceinline__ void hs_tmem_ld16(uint32_t taddr, float* v)
         : "r"(taddr));
 #pragma unroll
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// phi and phi~ (FP32, times sqrt(Vol)) of every function of atom `at` at listed node P:
+// out(loc, phi, phi~) for loc in [0, per).  Radial factors per table entry, then the solid
+// harmonics one lm at a time (the same monomial terms in every lane: broadcast constant reads).
+template <typename Out>
+__device__ __forceinline__ void hs_eval_atom(const HsBasis& B, const HsGrid& g, int P, float w, float Vp, int at,
+                                             Out&& out)
+{
+    const int i = P % g.nx, j = (P / g.nx) % g.ny, k = P / (g.nx * g.ny);
+    const float dx = (float)(g.x[i] - g.pos[3 * at]), dy = (float)(g.y[j] - g.pos[3 * at + 1]),
+                dz = (float)(g.z[k] - g.pos[3 * at + 2]);
+    const float r = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float ir = 1.0f / r;
+    float rad[HS_MAXB], fac[HS_MAXB];
+#pragma unroll
+    for (int q = 0; q < HS_MAXB; q++) {
+        rad[q] = 0.0f;
+        fac[q] = 0.0f;
+        if (q < B.nb) {
+            const int n = B.n[q], l = B.l[q];
+            const float zt = B.zeta[q];
+            float v = w * expf(-zt * r);
+            for (int t = 0; t < n - 1 - l; t++) v *= r;   // sqrt(Vol) r^(n-1-l) e^{-zeta r}
+            rad[q] = v;
+            fac[q] = 0.5f * ((float)(l * (l + 1) - n * (n - 1)) * ir * ir + 2.0f * zt * (float)n * ir - zt * zt) + Vp;
+        }
+    }
+    float px[5], py[5], pz[5];
+    px[0] = py[0] = pz[0] = 1.0f;
+#pragma unroll
+    for (int e = 1; e < 5; e++) {
+        px[e] = px[e - 1] * dx;
+        py[e] = py[e - 1] * dy;
+        pz[e] = pz[e - 1] * dz;
+    }
+    float sh[NLM];
+#pragma unroll
+    for (int lm = 0; lm < NLM; lm++) sh[lm] = 0.0f;
+#define HS_ACC(i, LM, EA, EB, EC) \
+    if (i < HS_L3_TERMS || B.lmax >= 4) sh[LM] = fmaf(c_hs_coef[i], px[EA] * py[EB] * pz[EC], sh[LM]);
+    HS_TERMS(HS_ACC)
+#undef HS_ACC
+#pragma unroll
+    for (int lm = 0; lm < NLM; lm++) {
+        const int l = l_of_lm(lm), m = lm - l * l - l;
+        if (l > B.lmax) break;
+#pragma unroll
+        for (int q = 0; q < HS_MAXB; q++)
+            if (q < B.nb && B.l[q] == l) {
+                const float ph = rad[q] * sh[lm];
+                out(B.off[q] + l + m, ph, fac[q] * ph);
+            }
+    }
+}
+
+__device__ __forceinline__ float hs_warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// (2'a) scale exponents from closed-form bounds over the interstitial nodes (r >= R_a from
+// the function's own atom): |phi_f| <= sqrt(max Vol) max_{r >= R_a} r^(n-1) e^{-zeta r}
+// sqrt(2 (2l+1) / 4pi) (real harmonics) and |phi~_f| <= (|kinetic factor at R_a, terms in
+// absolute value| + max |V| over the listed nodes) times that.  e_f makes the first bound
+// < 2^14; one c makes every second bound times 2^(e_f + c) < 2^14.  ea[f] = e_f, ea[M] = c.
+// One block.
+__device__ __forceinline__ int hs_scale_exp(float bound, int lo, int hi)
+{
+    int x = 0;
+    if (!(bound > 0.0f)) return 0;
+    frexpf(bound, &x);
+    return min(hi, max(lo, HS_SCALE_MAX - x));
+}
+
+__global__ void __launch_bounds__(1024) k_hs_bounds(HsBasis B, HsGrid g, const int* __restrict__ idx, int n_list,
+                                                    const double* __restrict__ V, int* __restrict__ ea)
+{
+    __shared__ float red[32];
+    __shared__ float s_w, s_v;
+    auto block_max = [&](float v) {
+        v = hs_warp_max(v);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        float r = 0.0f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) r = fmaxf(r, red[q]);
+        return r;
+    };
+    // largest dual-cell volume and |V| over the listed nodes
+    float w = 1.0f;
+    const double* ax[3] = {g.x, g.y, g.z};
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    for (int d = 0; d < 3; d++) {
+        float m = 0.0f;
+        for (int q = threadIdx.x; q < nn[d]; q += blockDim.x) m = fmaxf(m, (float)hs_dual(ax[d], nn[d], q));
+        w *= block_max(m);
+    }
+    float vm = 0.0f;
+    for (int p = threadIdx.x; p < n_list; p += blockDim.x) vm = fmaxf(vm, fabsf((float)V[idx[p]]));
+    vm = block_max(vm);
+    if (threadIdx.x == 0) {
+        s_w = sqrtf(w) * 1.001f;
+        s_v = vm * 1.001f;
+    }
+    __syncthreads();
+    const int M = g.na * B.per;
+    float rt = 0.0f;
+    for (int f = threadIdx.x; f < M; f += blockDim.x) {
+        const int at = f / B.per, q = B.q_of[f - at * B.per];
+        const int n = B.n[q], l = B.l[q];
+        const float zt = B.zeta[q], Ra = (float)g.R[at];
+        const float rs = fmaxf(Ra, (float)(n - 1) / zt);   // the radial factor peaks at (n-1)/zeta
+        float rad = expf(-zt * rs);
+        for (int t = 0; t < n - 1; t++) rad *= rs;
+        const float bphi = 1.01f * s_w * rad * sqrtf(2.0f * (2 * l + 1) / (4.0f * 3.14159265f));
+        const float kin = 0.5f * (fabsf((float)(l * (l + 1) - n * (n - 1))) / (Ra * Ra) + 2.0f * zt * n / Ra + zt * zt);
+        const int e = hs_scale_exp(bphi, -100, 100);
+        ea[f] = e;
+        rt = fmaxf(rt, ldexpf((kin + s_v) * bphi, e));
+    }
+    rt = block_max(rt);
+    if (threadIdx.x == 0) ea[M] = hs_scale_exp(rt, -20, 20);
+}
+
+// (2'c) the FP16 operand images of one chunk: rows p in [0, K) are listed nodes p0 + p (zero
+// past n_list); functions past M keep the zeros the tables were cleared to.  Block: 32 nodes
+// (lanes) x 8 atoms (warps).  Each warp stages its atom's four FP16 arrays for its 32 nodes in
+// shared memory ([array][function][node]) and writes them out as 16-byte pieces (8 nodes of one
+// function), so that a warp store fills whole 128-byte lines (8 consecutive functions).
+__global__ void __launch_bounds__(256) k_hs_basis16(HsBasis B, HsGrid g, int nT, const int* __restrict__ idx,
+                                                    const float* __restrict__ sw, const double* __restrict__ V,
+                                                    const int* __restrict__ ea, int p0, int n_list,
+                                                    __half* __restrict__ img)
+{
+    extern __shared__ __align__(16) __half hs_stage[];   // [8 warps][4][per][32]
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, at = blockIdx.y * 8 + wp;
+    if (at >= g.na) return;
+    __half* st = hs_stage + (size_t)wp * 4 * B.per * 32;
+    const int p = blockIdx.x * 32 + lane;   // row within the chunk
+    const bool live = p0 + p < n_list;
+    const int P = live ? idx[p0 + p] : 0;
+    const int ec = ea[g.na * B.per];
+    hs_eval_atom(B, g, P, live ? sw[p0 + p] : 0.0f, live ? (float)V[P] : 0.0f, at, [&](int loc, float ph, float pt) {
+        const int e = ea[at * B.per + loc];
+        const float a = live ? ph * __int_as_float((127 + e) << 23) : 0.0f;
+        const float t = live ? pt * __int_as_float((127 + e + ec) << 23) : 0.0f;
+        const __half ah = __float2half_rn(a), th = __float2half_rn(t);
+        st[(0 * B.per + loc) * 32 + lane] = ah;
+        st[(1 * B.per + loc) * 32 + lane] = __float2half_rn(a - __half2float(ah));
+        st[(2 * B.per + loc) * 32 + lane] = th;
+        st[(3 * B.per + loc) * 32 + lane] = __float2half_rn(t - __half2float(th));
+    });
+    __syncwarp();
+    // piece (array, function, kb, k half): 8 nodes = 16 bytes
+    const int kb0 = blockIdx.x * 2;
+    for (int t = lane; t < 4 * B.per * 4; t += 32) {
+        const int arr = t / (4 * B.per), rem = t - arr * 4 * B.per, loc = rem >> 2, kbh = rem & 3;
+        const int kb = kb0 + (kbh >> 1), kh = kbh & 1;
+        const int f = at * B.per + loc, fb = f >> 7, r = f & 127;
+        const uint4 v = *reinterpret_cast<const uint4*>(st + (arr * B.per + loc) * 32 + (kbh >> 1) * 16 + kh * 8);
+        __half* dst = img + ((size_t)kb * nT + fb) * (TC_SIDE / 2) + arr * (TC_IMG / 2) + (r >> 3) * 128 + kh * 64 +
+                      (r & 7) * 8;
+        *reinterpret_cast<uint4*>(dst) = v;
+    }
 }
 
 struct HsUnit {
@@ -421,24 +640,30 @@ __device__ __forceinline__ HsUnit hs_unit(int u, int pairs, int nT, int K)
     return w;
 }
 
-__global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int Mp, int nT, const float* __restrict__ A,
-                                                        const float* __restrict__ T, int K, int units,
+__global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const unsigned char* __restrict__ img, int K,
+                                                        int units, const int* __restrict__ ea,
                                                         double* __restrict__ S, double* __restrict__ H2,
                                                         double* __restrict__ part, int* __restrict__ err)
 {
     extern __shared__ unsigned char hs_dyn[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)hs_dyn + 127) & ~(uintptr_t)127);
-    __shared__ __align__(8) unsigned long long mbar[TC_RING];
+    __shared__ __align__(8) unsigned long long full[TC_RING], empty[TC_RING], accf[2], acce[2];
     __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m = tid & (TC_TM - 1), h = tid >> 7;         // operand row, stage half
-    const int q = warp & 3, cb = (warp >> 2) * TC_TM;      // drain: lane quarter, S or H columns
     const int pairs = nT * (nT + 1) / 2;
     double* mypart = part + (size_t)blockIdx.x * 2 * TC_TM * TC_TM;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_RING; s++)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&mbar[s])) : "memory");
+        abort_flag = 0;
+        for (int s = 0; s < TC_RING; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&empty[s])) : "memory");
+        }
+        for (int s = 0; s < 2; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&accf[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(hs_smem_u32(&acce[s])) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -451,167 +676,156 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int Mp, int nT, 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_slot;
+    int last_mma = -1;   // the MMA thread's last committed stage
 
-    // table values of one stage for this thread: 4 arrays x 8 nodes
-    auto load_stage = [&](const HsUnit& w, int row0, float (&v)[4][8]) {
-        const size_t base = (size_t)(row0 + 8 * h) * Mp;
-        const int cI = w.I * TC_TM + m, cJ = w.J * TC_TM + m;
-#pragma unroll
-        for (int kk = 0; kk < 8; kk++) {
-            const size_t r = base + (size_t)kk * Mp;
-            v[0][kk] = __ldg(A + r + cI);
-            v[1][kk] = __ldg(T + r + cI);
-            v[2][kk] = __ldg(A + r + cJ);
-            v[3][kk] = __ldg(T + r + cJ);
-        }
-    };
-    // drain the accumulator pair `set` into the partial sums (store on a unit's first interval)
-    auto drain = [&](int set, bool first) {
-        const uint32_t ta = tmem + (uint32_t)(set * 2 * TC_TM + cb) + ((uint32_t)(32 * q) << 16);
-        const int row = 32 * q + lane;
-        for (int c = 0; c < TC_TM; c += 16) {
-            float v[16];
-            hs_tmem_ld16(ta + (uint32_t)c, v);
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                double* p = mypart + (size_t)(cb + c + j) * TC_TM + row;
-                *p = first ? (double)v[j] : *p + (double)v[j];
-            }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    };
-    auto flush = [&](const HsUnit& w) {
-        const int row = 32 * q + lane;
-        const int a = w.I * TC_TM + row;
-        double* dst = cb ? H2 : S;
-        if (a >= M) return;
-        for (int c = 0; c < TC_TM; c++) {
-            const int b = w.J * TC_TM + c;
-            if (b < M && a <= b) atomicAdd(dst + (size_t)a * M + b, mypart[(size_t)(cb + c) * TC_TM + row]);
-        }
-    };
-
-    // a failed wait sets `fail` in its thread; the stage barriers combine the flags
-    // (__syncthreads_or), so that every thread stops at the same point
-    bool fail = false, stop = false;
-    int g = 0;            // stages issued by this CTA
-    int ic = 0;           // intervals started by this CTA
-    // the interval whose accumulators wait to be drained
-    bool pend = false, pend_first = false, pend_last = false;
-    int pend_set = 0, pend_stage = 0;
-    HsUnit pend_unit{0, 0, 0, 0};
-    float vc[4][8], vn[4][8];
-
-    for (int u = blockIdx.x; u < units && !stop; u += gridDim.x) {
-        const HsUnit w = hs_unit(u, pairs, nT, K);
-        load_stage(w, w.k0, vc);
-        for (int c0 = w.k0; c0 < w.k1 && !stop; c0 += HS_IV) {
-            const int c1 = min(w.k1, c0 + HS_IV);
-            const int set = ic & 1;
-            const uint32_t tS = tmem + (uint32_t)(set * 2 * TC_TM), tH = tS + TC_TM;
-            for (int r0 = c0; r0 < c1; r0 += TC_SK) {
+    if (warp == 0 && lane == 0) {
+        // ---------------- producer: two bulk copies per stage
+        int g = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+            const HsUnit w = hs_unit(u, pairs, nT, K);
+            for (int r0 = w.k0; r0 < w.k1 && ok; r0 += TC_SK, g++) {
                 const int slot = g % TC_RING;
-                const bool more = r0 + TC_SK < w.k1;
-                if (more) load_stage(w, r0 + TC_SK, vn);
-                if (g >= TC_RING && !hs_wait(hs_smem_u32(&mbar[slot]), (uint32_t)((g / TC_RING - 1) & 1)))
-                    fail = true;
-                unsigned char* st = ring + (size_t)slot * TC_STAGE;
-#pragma unroll
-                for (int x = 0; x < 4; x++) {
-                    unsigned char* hi = st + (2 * x) * TC_SLOT + h * (TC_SLOT / 2) + (m >> 3) * 256 + (m & 7) * 16;
-                    unsigned char* lo = hi + TC_SLOT;
-#pragma unroll
-                    for (int kq = 0; kq < 2; kq++) {
-                        float4 H4, L4;
-                        float* hp = &H4.x;
-                        float* lp = &L4.x;
-#pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            const float v = vc[x][4 * kq + e];
-                            const float vh = tf32_round(v);
-                            hp[e] = vh;
-                            lp[e] = tf32_round(v - vh);
-                        }
-                        *reinterpret_cast<float4*>(hi + kq * 128) = H4;
-                        *reinterpret_cast<float4*>(lo + kq * 128) = L4;
-                    }
-                }
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                if (__syncthreads_or(fail)) {
-                    stop = true;
+                if (g >= TC_RING && !hs_wait(hs_smem_u32(&empty[slot]), (uint32_t)((g / TC_RING - 1) & 1), &abort_flag)) {
+                    ok = false;
                     break;
                 }
-                if (tid == 0) {
+                const uint32_t fb = hs_smem_u32(&full[slot]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(fb), "r"(TC_STAGE)
+                             : "memory");
+                const size_t kb = (size_t)(r0 / TC_SK) * nT;
+                const unsigned char* srcI = img + (kb + w.I) * TC_SIDE;
+                const unsigned char* srcJ = img + (kb + w.J) * TC_SIDE;
+                const uint32_t dst = hs_smem_u32(ring + (size_t)slot * TC_STAGE);
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                        dst),
+                    "l"(srcI), "r"(TC_SIDE), "r"(fb)
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                        dst + TC_SIDE),
+                    "l"(srcJ), "r"(TC_SIDE), "r"(fb)
+                    : "memory");
+            }
+        }
+        if (!ok) {
+            // copies still in flight land before the CTA leaves
+            for (int q = max(0, g - TC_RING); q < g; q++) {
+                volatile int never = 0;
+                hs_wait(hs_smem_u32(&full[q % TC_RING]), (uint32_t)((q / TC_RING) & 1), &never);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        int g = 0, ic = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+            const HsUnit w = hs_unit(u, pairs, nT, K);
+            for (int c0 = w.k0; c0 < w.k1 && ok; c0 += HS_IV, ic++) {
+                const int c1 = min(w.k1, c0 + HS_IV), set = ic & 1;
+                if (ic >= 2 && !hs_wait(hs_smem_u32(&acce[set]), (uint32_t)((ic / 2 - 1) & 1), &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t tS = tmem + (uint32_t)(set * 2 * TC_TM), tH = tS + TC_TM;
+                for (int r0 = c0; r0 < c1; r0 += TC_SK, g++) {
+                    const int slot = g % TC_RING;
+                    if (!hs_wait(hs_smem_u32(&full[slot]), (uint32_t)((g / TC_RING) & 1), &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const uint32_t sb = hs_smem_u32(st);
-#pragma unroll
-                    for (int ks = 0; ks < 2; ks++) {
-                        const uint32_t o = (uint32_t)(ks * (TC_SLOT / 2));
-                        const uint64_t aIh = hs_desc(sb + 0 * TC_SLOT + o), aIl = hs_desc(sb + 1 * TC_SLOT + o);
-                        const uint64_t tIh = hs_desc(sb + 2 * TC_SLOT + o), tIl = hs_desc(sb + 3 * TC_SLOT + o);
-                        const uint64_t aJh = hs_desc(sb + 4 * TC_SLOT + o), aJl = hs_desc(sb + 5 * TC_SLOT + o);
-                        const uint64_t tJh = hs_desc(sb + 6 * TC_SLOT + o), tJl = hs_desc(sb + 7 * TC_SLOT + o);
-                        const uint32_t acc = (r0 > c0 || ks > 0) ? 1u : 0u;
-                        hs_mma(tS, aIh, aJh, acc);
-                        hs_mma(tS, aIh, aJl, 1u);
-                        hs_mma(tS, aIl, aJh, 1u);
-                        hs_mma(tH, aIh, tJh, acc);
-                        hs_mma(tH, aIh, tJl, 1u);
-                        hs_mma(tH, aIl, tJh, 1u);
-                        hs_mma(tH, tIh, aJh, 1u);
-                        hs_mma(tH, tIh, aJl, 1u);
-                        hs_mma(tH, tIl, aJh, 1u);
-                    }
-                    asm volatile(
-                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                            hs_smem_u32(&mbar[slot]))
-                        : "memory");
+                    const uint32_t sb = hs_smem_u32(ring + (size_t)slot * TC_STAGE);
+                    const uint64_t aIh = hs_desc(sb), aIl = hs_desc(sb + TC_IMG);
+                    const uint64_t tIh = hs_desc(sb + 2 * TC_IMG), tIl = hs_desc(sb + 3 * TC_IMG);
+                    const uint64_t aJh = hs_desc(sb + TC_SIDE), aJl = hs_desc(sb + TC_SIDE + TC_IMG);
+                    const uint64_t tJh = hs_desc(sb + TC_SIDE + 2 * TC_IMG), tJl = hs_desc(sb + TC_SIDE + 3 * TC_IMG);
+                    const uint32_t acc = r0 > c0 ? 1u : 0u;
+                    hs_mma(tS, aIh, aJh, acc);
+                    hs_mma(tS, aIh, aJl, 1u);
+                    hs_mma(tS, aIl, aJh, 1u);
+                    hs_mma(tH, aIh, tJh, acc);
+                    hs_mma(tH, aIh, tJl, 1u);
+                    hs_mma(tH, aIl, tJh, 1u);
+                    hs_mma(tH, tIh, aJh, 1u);
+                    hs_mma(tH, tIh, aJl, 1u);
+                    hs_mma(tH, tIl, aJh, 1u);
+                    hs_commit(hs_smem_u32(&empty[slot]));
+                    last_mma = g;
                 }
-                // the previous interval's accumulators, once its last MMAs are done
-                if (pend) {
-                    // warp-uniform, since tcgen05.ld is a whole-warp instruction
-                    const bool ok = hs_wait(hs_smem_u32(&mbar[pend_stage % TC_RING]), (uint32_t)((pend_stage / TC_RING) & 1));
-                    if (!__all_sync(0xffffffffu, ok))
-                        fail = true;
-                    else {
-                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                        drain(pend_set, pend_first);
-                        if (pend_last) flush(pend_unit);
-                    }
-                    pend = false;
+                if (ok) hs_commit(hs_smem_u32(&accf[set]));
+            }
+        }
+    } else if (warp >= 4) {
+        // ---------------- drain: row = tensor-memory lane, S then H columns.  The CTA's partial
+        // sums are FP32 pairs (sum, compensation; TwoSum per interval) of the scaled values;
+        // the flush at the unit's end forms them in FP64, undoes the scales and adds them to S, 2H.
+        const int q = warp - 4, row = 32 * q + lane;
+        float* phi_ = reinterpret_cast<float*>(mypart);   // [256][128] sums
+        float* plo_ = phi_ + 2 * TC_TM * TC_TM;           // [256][128] compensations
+        int ic = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+            const HsUnit w = hs_unit(u, pairs, nT, K);
+            for (int c0 = w.k0; c0 < w.k1; c0 += HS_IV, ic++) {
+                const int set = ic & 1;
+                const bool got = hs_wait(hs_smem_u32(&accf[set]), (uint32_t)((ic / 2) & 1), &abort_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    abort_flag = 1;
+                    break;
                 }
-                g++;
-                if (more) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const bool first = c0 == w.k0;
+#pragma unroll 1
+                for (int cc = 0; cc < 2 * TC_TM; cc += 16) {
+                    float v[16];
+                    hs_tmem_ld16(tmem + (uint32_t)(set * 2 * TC_TM + cc) + ((uint32_t)(32 * q) << 16), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-                    for (int x = 0; x < 4; x++)
-#pragma unroll
-                        for (int kk = 0; kk < 8; kk++) vc[x][kk] = vn[x][kk];
+                    for (int jj = 0; jj < 16; jj++) {
+                        const size_t ix = (size_t)(cc + jj) * TC_TM + row;
+                        if (first) {
+                            phi_[ix] = v[jj];
+                            plo_[ix] = 0.0f;
+                        } else {
+                            const float a = phi_[ix], t = a + v[jj], bb = t - a;
+                            plo_[ix] += (a - (t - bb)) + (v[jj] - bb);
+                            phi_[ix] = t;
+                        }
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(hs_smem_u32(&acce[set])) : "memory");
+            }
+            if (!ok) break;
+            const int a = w.I * TC_TM + row;
+            if (a < M) {
+                const int e_a = ea[a], ec = ea[M];
+                for (int c = 0; c < TC_TM; c++) {
+                    const int b = w.J * TC_TM + c;
+                    if (b < M && a <= b) {
+                        // 2^-(e_a + e_b) and 2^-(e_a + e_b + c) built from their exponent bits
+                        const int e = e_a + __ldg(ea + b);
+                        const double sS = __longlong_as_double((long long)(1023 - e) << 52);
+                        const double sH = __longlong_as_double((long long)(1023 - e - ec) << 52);
+                        const size_t iS = (size_t)c * TC_TM + row, iH = (size_t)(TC_TM + c) * TC_TM + row;
+                        atomicAdd(S + (size_t)a * M + b, ((double)phi_[iS] + (double)plo_[iS]) * sS);
+                        atomicAdd(H2 + (size_t)a * M + b, ((double)phi_[iH] + (double)plo_[iH]) * sH);
+                    }
                 }
             }
-            if (stop) break;
-            pend = true;
-            pend_first = c0 == w.k0;
-            pend_last = c1 == w.k1;
-            pend_set = set;
-            pend_stage = g - 1;
-            pend_unit = w;
-            ic++;
         }
     }
-    if (pend && !stop) {
-        const bool ok = hs_wait(hs_smem_u32(&mbar[pend_stage % TC_RING]), (uint32_t)((pend_stage / TC_RING) & 1));
-        if (!__all_sync(0xffffffffu, ok))
-            fail = true;
-        else {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            drain(pend_set, pend_first);
-            if (pend_last) flush(pend_unit);
+    __syncthreads();
+    if (abort_flag) {
+        // the MMAs already issued finish before the tensor memory is released
+        if (warp == 1 && lane == 0 && last_mma >= 0) {
+            volatile int never = 0;
+            hs_wait(hs_smem_u32(&empty[last_mma % TC_RING]), (uint32_t)((last_mma / TC_RING) & 1), &never);
         }
-    }
-    if (__syncthreads_or(fail)) {
-        // let the MMAs already issued finish before the tensor memory is released
-        if (tid == 0 && g > 0) hs_wait(hs_smem_u32(&mbar[(g - 1) % TC_RING]), (uint32_t)(((g - 1) / TC_RING) & 1));
         if (tid == 0 && err) atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -658,6 +872,9 @@ cudaError_t ensure_hs_attributes()
     std::lock_guard<std::mutex> lock(g_hs_mutex);
     if (g_hs_attr_device == dev) return cudaSuccess;
     e = cudaFuncSetAttribute(k_hs_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_hs_basis16, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(8 * 4 * HS_MAXF * 32 * sizeof(__half)));
     if (e == cudaSuccess) g_hs_attr_device = dev;
     return e;
 }
@@ -677,7 +894,7 @@ int hs_basis_check(int nb, const int* bn, const int* bl, const double* bz, int* 
     return LASTO_OK;
 }
 
-size_t hs_scratch_bytes(const int n[3], int M)
+size_t hs_scratch_bytes(const int n[3], int M, int na)
 {
     const size_t N = (size_t)n[0] * n[1] * n[2];
     const size_t nblk = (N + HS_CNT - 1) / HS_CNT;
@@ -685,18 +902,19 @@ size_t hs_scratch_bytes(const int n[3], int M)
     const size_t K = hs_rows_per_chunk(N, Mp);
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     return up(sizeof(int) * nblk) + up(sizeof(int) * (nblk + 1)) + up(sizeof(int) * N) + up(sizeof(float) * N) +
-           2 * up(sizeof(float) * (size_t)Mp * K) + up(sizeof(double) * 2 * TC_TM * TC_TM * (size_t)hs_sm_count()) +
-           up(sizeof(int));
+           up(8 * (size_t)Mp * K) + up(sizeof(double) * 2 * TC_TM * TC_TM * (size_t)hs_sm_count()) +
+           up(sizeof(int) * (Mp + 1)) + up(sizeof(int)) + up(sizeof(float) * 4 * na);
 }
 
 // scratch: hs_scratch_bytes(n, M) bytes, 256-byte aligned; carved into the block counts,
-// offsets, listed nodes, sqrt(Vol), the two tables, the tensor-core CTAs' FP64 partial sums
-// and an error flag.  Synchronises the stream twice (the number of listed nodes sizes the
-// chunk loop; the error flag is read at the end).
+// offsets, listed nodes, sqrt(Vol), the basis tables (FP32 A and T for the SIMT contraction,
+// FP16 operand images for the tensor cores), the tensor-core CTAs' FP64 partial sums, the
+// per-function maxima and scale exponents, and an error flag.  Synchronises the stream twice
+// (the number of listed nodes sizes the chunk loop; the error flag is read at the end).
 int launch_interstitial_hs(const int n[3], const double* x, const double* y, const double* z, int na,
                            const double* pos, const double* R, int nb, const int* bn, const int* bl,
                            const double* bz, const double* V, double* S, double* H, void* scratch, int mode,
-                           cudaStream_t s)
+                           lasto_hs_stats* stats, cudaStream_t s)
 {
     int per = 0;
     if (hs_basis_check(nb, bn, bl, bz, &per) != LASTO_OK) return LASTO_ERR_INVALID_ARG;
@@ -704,10 +922,13 @@ int launch_interstitial_hs(const int n[3], const double* x, const double* y, con
     const bool tensor = mode != LASTO_HS_SIMT;
     HsBasis B{};
     B.per = per;
+    B.nb = nb;
     for (int q = 0, f = 0; q < nb; q++) {
         B.n[q] = bn[q];
         B.l[q] = bl[q];
+        B.off[q] = f;
         B.zeta[q] = (float)bz[q];
+        B.lmax = std::max(B.lmax, bl[q]);
         for (int m = -bl[q]; m <= bl[q]; m++, f++) {
             B.q_of[f] = (unsigned char)q;
             B.m_of[f] = (signed char)m;
@@ -722,7 +943,8 @@ int launch_interstitial_hs(const int n[3], const double* x, const double* y, con
     const int nT = Mp / tile;
     const size_t N = (size_t)n[0] * n[1] * n[2];
     const int nblk = (int)((N + HS_CNT - 1) / HS_CNT);
-    const size_t Kmax = hs_rows_per_chunk(N, (M + TC_TM - 1) / TC_TM * TC_TM);
+    const int Mp128 = (M + TC_TM - 1) / TC_TM * TC_TM;
+    const size_t Kmax = hs_rows_per_chunk(N, Mp128);
     char* base = reinterpret_cast<char*>(scratch);
     auto carve = [&](size_t bytes) {
         char* p = base;
@@ -733,34 +955,72 @@ int launch_interstitial_hs(const int n[3], const double* x, const double* y, con
     int* off = reinterpret_cast<int*>(carve(sizeof(int) * (nblk + 1)));
     int* idx = reinterpret_cast<int*>(carve(sizeof(int) * N));
     float* sw = reinterpret_cast<float*>(carve(sizeof(float) * N));
-    float* A = reinterpret_cast<float*>(carve(sizeof(float) * Mp * Kmax));
-    float* T = reinterpret_cast<float*>(carve(sizeof(float) * Mp * Kmax));
+    char* tables = carve(8 * (size_t)Mp128 * Kmax);
+    float* A = reinterpret_cast<float*>(tables);                  // SIMT: [K][Mp] FP32 each
+    float* T = A + (size_t)Mp * Kmax;
     double* part = reinterpret_cast<double*>(carve(sizeof(double) * 2 * TC_TM * TC_TM * (size_t)sms));
+    int* ea = reinterpret_cast<int*>(carve(sizeof(int) * (Mp128 + 1)));
     int* err = reinterpret_cast<int*>(carve(sizeof(int)));
+    float4* at4 = reinterpret_cast<float4*>(carve(sizeof(float4) * na));
 
     const HsGrid g{n[0], n[1], n[2], na, x, y, z, pos, R};
+    // optional device timing: events around the list, every chunk's two kernels and the mirror
+    std::vector<cudaEvent_t> ev;
+    auto mark = [&]() {
+        if (!stats) return;
+        cudaEvent_t t;
+        if (cudaEventCreate(&t) == cudaSuccess) {
+            cudaEventRecord(t, s);
+            ev.push_back(t);
+        }
+    };
+    struct EvFree {
+        std::vector<cudaEvent_t>& v;
+        ~EvFree()
+        {
+            for (cudaEvent_t t : v) cudaEventDestroy(t);
+        }
+    } ev_free{ev};
     cudaError_t e = cudaMemsetAsync(S, 0, sizeof(double) * (size_t)M * M, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(H, 0, sizeof(double) * (size_t)M * M, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
     if (e != cudaSuccess) return LASTO_ERR_CUDA;
-    k_hs_count<<<nblk, 256, 0, s>>>(g, cnt);
+    mark();
+    k_hs_atoms<<<(na + 127) / 128, 128, 0, s>>>(na, pos, R, at4);
+    k_hs_count<<<nblk, 256, 0, s>>>(g, at4, cnt);
     k_hs_scan<<<1, 1024, 0, s>>>(nblk, cnt, off);
-    k_hs_scatter<<<nblk, 256, 0, s>>>(g, off, idx, sw);
+    k_hs_scatter<<<nblk, 256, 0, s>>>(g, at4, off, idx, sw);
+    mark();
     int n_list = 0;
     e = cudaMemcpyAsync(&n_list, off + nblk, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return LASTO_ERR_CUDA;
 
+    const unsigned ablocks = (unsigned)((na + 7) / 8);
+    if (tensor && n_list > 0) {
+        // per-function scales; operand images cleared once (the padding functions past M stay zero)
+        e = cudaMemsetAsync(tables, 0, 8 * (size_t)Mp128 * Kmax, s);
+        if (e != cudaSuccess) return LASTO_ERR_CUDA;
+        k_hs_bounds<<<1, 1024, 0, s>>>(B, g, idx, n_list, V, ea);
+    }
     const int pairs = nT * (nT + 1) / 2;
     for (int p0 = 0; p0 < n_list; p0 += (int)Kmax) {
         const int K = (int)std::min<size_t>(Kmax, ((size_t)(n_list - p0) + HS_KC - 1) / HS_KC * HS_KC);
-        const size_t tot = (size_t)K * Mp;
-        const unsigned gb = (unsigned)std::min<size_t>((tot + 255) / 256, (size_t)sms * 16);
-        k_hs_basis<<<gb, 256, 0, s>>>(B, g, M, Mp, idx, sw, V, p0, n_list, K, A, T);
+        mark();
+        if (tensor) {
+            k_hs_basis16<<<dim3((unsigned)(K / 32), ablocks), 256, (size_t)8 * 4 * per * 32 * sizeof(__half), s>>>(
+                B, g, nT, idx, sw, V, ea, p0, n_list, reinterpret_cast<__half*>(tables));
+        } else {
+            const size_t tot = (size_t)K * Mp;
+            const unsigned gb = (unsigned)std::min<size_t>((tot + 255) / 256, (size_t)sms * 16);
+            k_hs_basis<<<gb, 256, 0, s>>>(B, g, M, Mp, idx, sw, V, p0, n_list, K, A, T);
+        }
+        mark();
         if (tensor) {
             const int units = pairs * ((K + HS_SEG - 1) / HS_SEG);
             const int grid = std::min(units, sms);
-            k_hs_gemm_tc<<<grid, TC_NT, TC_SMEM, s>>>(M, Mp, nT, A, T, K, units, S, H, part, err);
+            k_hs_gemm_tc<<<grid, TC_NT, TC_SMEM, s>>>(M, nT, reinterpret_cast<const unsigned char*>(tables), K, units,
+                                                       ea, S, H, part, err);
         } else {
             // node ranges per tile: about eight CTAs per SM in all
             int split = std::max(1, (8 * sms + pairs - 1) / pairs);
@@ -769,13 +1029,36 @@ int launch_interstitial_hs(const int n[3], const double* x, const double* y, con
             split = (K + kper - 1) / kper;
             k_hs_gemm_f32<<<dim3((unsigned)pairs, (unsigned)split), HS_NT, 0, s>>>(M, Mp, nT, A, T, kper, K, S, H);
         }
+        mark();
     }
+    mark();
     k_hs_mirror<<<(unsigned)(((size_t)M * M + 255) / 256), 256, 0, s>>>(M, S, H);
+    mark();
     if (cudaGetLastError() != cudaSuccess) return LASTO_ERR_CUDA;
     int flag = 0;
     e = cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return LASTO_ERR_CUDA;
+    if (stats) {
+        const int chunks = n_list > 0 ? (int)((n_list + Kmax - 1) / Kmax) : 0;
+        *stats = lasto_hs_stats{};
+        stats->interstitial_nodes = n_list;
+        stats->chunks = chunks;
+        stats->tile = tile;
+        auto span = [&](size_t i, size_t j) {
+            float ms = 0.0f;
+            if (j < ev.size() && cudaEventElapsedTime(&ms, ev[i], ev[j]) != cudaSuccess) ms = 0.0f;
+            return ms;
+        };
+        if (ev.size() == (size_t)(2 + 3 * chunks + 2)) {
+            stats->ms_list = span(0, 1);
+            for (int c = 0; c < chunks; c++) {
+                stats->ms_tables += span(2 + 3 * c, 3 + 3 * c);
+                stats->ms_contract += span(3 + 3 * c, 4 + 3 * c);
+            }
+            stats->ms_mirror = span(2 + 3 * chunks, 3 + 3 * chunks);
+        }
+    }
     return flag ? LASTO_ERR_TIMEOUT : LASTO_OK;
 }
 

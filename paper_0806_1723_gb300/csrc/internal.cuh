@@ -245,11 +245,11 @@ cudaError_t launch_inner_solve(int na, const double* R, const double* Z, int n_r
 
 // hs.cu: interstitial H and S (Eq. 3.11-3.14)
 int hs_basis_check(int nb, const int* bn, const int* bl, const double* bz, int* per_out);
-size_t hs_scratch_bytes(const int n[3], int M);
+size_t hs_scratch_bytes(const int n[3], int M, int na);
 int launch_interstitial_hs(const int n[3], const double* x, const double* y, const double* z, int na,
                            const double* pos, const double* R, int nb, const int* bn, const int* bl,
                            const double* bz, const double* V, double* S, double* H, void* scratch, int mode,
-                           cudaStream_t s);
+                           lasto_hs_stats* stats, cudaStream_t s);
 
 // guess.cu: the learned initial guess (a 3-D U-Net on a 33^3 subgrid)
 constexpr int GUESS_N = 33;

@@ -83,6 +83,20 @@ def graded_box(pos, vacuum=10.0):
     return clusters.cluster_radius(pos) + R_SPHERE + vacuum
 
 
+def potential_energy(pos, x, y, z, seed: int = 0) -> np.ndarray:
+    """A seeded potential-energy field at the nodes [nz][ny][nx] (x fastest) for the H and S
+    contributions: a screened attraction to every atom, A e^{-k r} / max(r, 0.5) with
+    A ~ U(8, 12) hartree bohr and k ~ U(0.5, 0.8) / bohr per atom, plus N(0, 0.05^2) noise.
+    It stands in for the SCF potential, which is not available."""
+    rng = np.random.default_rng(seed)
+    V = np.zeros((len(z), len(y), len(x)))
+    zz, yy, xx = z[:, None, None], y[None, :, None], x[None, None, :]
+    for p in np.asarray(pos, float):
+        r = np.sqrt((xx - p[0]) ** 2 + (yy - p[1]) ** 2 + (zz - p[2]) ** 2)
+        V -= rng.uniform(8.0, 12.0) * np.exp(-rng.uniform(0.5, 0.8) * r) / np.maximum(r, 0.5)
+    return V + 0.05 * rng.normal(size=V.shape)
+
+
 # ---------------------------------------------------------------- the five workloads
 def pd13_uniform65(seed: int = 0) -> Cluster:
     """Pd13 cuboctahedron, uniform 65^3 box of side 24 bohr (h = 0.375)."""

@@ -23,14 +23,7 @@ def _axes(orc, cl):
 
 
 def _potential(cl, x, y, z, seed):
-    """A seeded potential-energy field: screened attraction to every atom plus a small ripple."""
-    rng = np.random.default_rng(seed)
-    Zg, Yg, Xg = np.meshgrid(z, y, x, indexing="ij")
-    V = np.zeros(Xg.shape)
-    for p in cl.pos:
-        r = np.sqrt((Xg - p[0]) ** 2 + (Yg - p[1]) ** 2 + (Zg - p[2]) ** 2)
-        V -= rng.uniform(8.0, 12.0) * np.exp(-rng.uniform(0.5, 0.8) * r) / np.maximum(r, 0.5)
-    return V + 0.05 * rng.normal(size=V.shape)
+    return synth.potential_energy(cl.pos, x, y, z, seed)
 
 
 def _outside(cl, x, y, z):
