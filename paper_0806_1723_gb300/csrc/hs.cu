@@ -366,11 +366,13 @@ __global__ void __launch_bounds__(HS_NT) k_hs_gemm_f32(int M, int Mp, int nT, co
 //
 // Warp roles: one thread issues the bulk copies into a ring of six 32 KiB stages, one thread
 // issues the MMAs (and frees a stage by tcgen05.commit to its mbarrier), four warps drain the
-// accumulators every HS_IV nodes (tcgen05.ld; tensor-memory lane = function row) into the
-// CTA's FP64 partial sums, undoing the scales, while the MMAs fill the other pair of regions.
-// A work unit is one upper-triangle tile and HS_SEG nodes, numbered segment-major so that the
-// CTAs running together read the same table rows (from L2); at a unit's end its partial sums
-// go to S and 2H by FP64 atomic addition.  Every wait is bounded (about two seconds, or until
+// accumulators (tensor-memory columns 0-255; lane = function row) every HS_IV nodes into the
+// unit's FP32 partial sums, which stay in tensor memory (columns 256-511; tcgen05.ld, add,
+// tcgen05.st), so that the FP32 sums are never longer than one interval.  A work unit is one
+// upper-triangle tile and HS_SEG nodes, numbered segment-major so that the CTAs running
+// together read the same table rows (from L2); at a unit's end the drain warps form its
+// partial sums in FP64, undo the scales (exponent arithmetic) and add them to S and 2H by
+// FP64 atomic addition while the MMAs run on.  Every wait is bounded (about two seconds, or until
 // another role has given up): the CTA then records an error, lets its copies and MMAs in
 // flight finish (bounded), frees its tensor memory and returns.
 constexpr int TC_TM = 128;                       // functions per tile side (MMA M and N)
@@ -640,19 +642,38 @@ __device__ __forceinline__ HsUnit hs_unit(int u, int pairs, int nT, int K)
     return w;
 }
 
+__device__ __forceinline__ void hs_tmem_st16(uint32_t taddr, const float* v)
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};\n" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+        "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+        "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+
+// x * 2^-e for a double x whose result stays a normal number: the exponent field lowered by e
+__device__ __forceinline__ double hs_unscale(float v, int e)
+{
+    const double x = (double)v;
+    return v == 0.0f ? 0.0 : __longlong_as_double(__double_as_longlong(x) - ((long long)e << 52));
+}
+
 __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const unsigned char* __restrict__ img, int K,
                                                         int units, const int* __restrict__ ea,
                                                         double* __restrict__ S, double* __restrict__ H2,
-                                                        double* __restrict__ part, int* __restrict__ err)
+                                                        int* __restrict__ err)
 {
     extern __shared__ unsigned char hs_dyn[];
     unsigned char* ring = reinterpret_cast<unsigned char*>(((uintptr_t)hs_dyn + 127) & ~(uintptr_t)127);
-    __shared__ __align__(8) unsigned long long full[TC_RING], empty[TC_RING], accf[2], acce[2];
+    __shared__ __align__(8) unsigned long long full[TC_RING], empty[TC_RING], accf, acce;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int pairs = nT * (nT + 1) / 2;
-    double* mypart = part + (size_t)blockIdx.x * 2 * TC_TM * TC_TM;
 
     if (tid == 0) {
         abort_flag = 0;
@@ -660,10 +681,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&full[s])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&empty[s])) : "memory");
         }
-        for (int s = 0; s < 2; s++) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&accf[s])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(hs_smem_u32(&acce[s])) : "memory");
-        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&accf)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(hs_smem_u32(&acce)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -717,19 +736,20 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer: accumulators in columns 0-127 (S) and 128-255 (2H)
         int g = 0, ic = 0;
         bool ok = true;
+        const uint32_t tS = tmem, tH = tmem + TC_TM;
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
             const HsUnit w = hs_unit(u, pairs, nT, K);
             for (int c0 = w.k0; c0 < w.k1 && ok; c0 += HS_IV, ic++) {
-                const int c1 = min(w.k1, c0 + HS_IV), set = ic & 1;
-                if (ic >= 2 && !hs_wait(hs_smem_u32(&acce[set]), (uint32_t)((ic / 2 - 1) & 1), &abort_flag)) {
+                const int c1 = min(w.k1, c0 + HS_IV);
+                // the previous interval has been drained
+                if (ic >= 1 && !hs_wait(hs_smem_u32(&acce), (uint32_t)((ic - 1) & 1), &abort_flag)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t tS = tmem + (uint32_t)(set * 2 * TC_TM), tH = tS + TC_TM;
                 for (int r0 = c0; r0 < c1; r0 += TC_SK, g++) {
                     const int slot = g % TC_RING;
                     if (!hs_wait(hs_smem_u32(&full[slot]), (uint32_t)((g / TC_RING) & 1), &abort_flag)) {
@@ -755,23 +775,20 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
                     hs_commit(hs_smem_u32(&empty[slot]));
                     last_mma = g;
                 }
-                if (ok) hs_commit(hs_smem_u32(&accf[set]));
+                if (ok) hs_commit(hs_smem_u32(&accf));
             }
         }
     } else if (warp >= 4) {
-        // ---------------- drain: row = tensor-memory lane, S then H columns.  The CTA's partial
-        // sums are FP32 pairs (sum, compensation; TwoSum per interval) of the scaled values;
-        // the flush at the unit's end forms them in FP64, undoes the scales and adds them to S, 2H.
+        // ---------------- drain: row = tensor-memory lane; interval sums (columns 0-255) added
+        // into the unit's partial sums (columns 256-511)
         const int q = warp - 4, row = 32 * q + lane;
-        float* phi_ = reinterpret_cast<float*>(mypart);   // [256][128] sums
-        float* plo_ = phi_ + 2 * TC_TM * TC_TM;           // [256][128] compensations
+        const uint32_t lanes = (uint32_t)(32 * q) << 16;
         int ic = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
             const HsUnit w = hs_unit(u, pairs, nT, K);
             for (int c0 = w.k0; c0 < w.k1; c0 += HS_IV, ic++) {
-                const int set = ic & 1;
-                const bool got = hs_wait(hs_smem_u32(&accf[set]), (uint32_t)((ic / 2) & 1), &abort_flag);
+                const bool got = hs_wait(hs_smem_u32(&accf), (uint32_t)(ic & 1), &abort_flag);
                 if (!__all_sync(0xffffffffu, got)) {
                     ok = false;
                     abort_flag = 1;
@@ -781,40 +798,35 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
                 const bool first = c0 == w.k0;
 #pragma unroll 1
                 for (int cc = 0; cc < 2 * TC_TM; cc += 16) {
-                    float v[16];
-                    hs_tmem_ld16(tmem + (uint32_t)(set * 2 * TC_TM + cc) + ((uint32_t)(32 * q) << 16), v);
+                    float v[16], pv[16];
+                    hs_tmem_ld16(tmem + lanes + (uint32_t)cc, v);
+                    if (!first) hs_tmem_ld16(tmem + lanes + (uint32_t)(2 * TC_TM + cc), pv);
                     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    if (!first)
 #pragma unroll
-                    for (int jj = 0; jj < 16; jj++) {
-                        const size_t ix = (size_t)(cc + jj) * TC_TM + row;
-                        if (first) {
-                            phi_[ix] = v[jj];
-                            plo_[ix] = 0.0f;
-                        } else {
-                            const float a = phi_[ix], t = a + v[jj], bb = t - a;
-                            plo_[ix] += (a - (t - bb)) + (v[jj] - bb);
-                            phi_[ix] = t;
-                        }
-                    }
+                        for (int jj = 0; jj < 16; jj++) v[jj] += pv[jj];
+                    hs_tmem_st16(tmem + lanes + (uint32_t)(2 * TC_TM + cc), v);
                 }
+                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(hs_smem_u32(&acce[set])) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(hs_smem_u32(&acce)) : "memory");
             }
             if (!ok) break;
+            // the unit's sums: FP64, scales undone, into S and 2H
             const int a = w.I * TC_TM + row;
-            if (a < M) {
-                const int e_a = ea[a], ec = ea[M];
-                for (int c = 0; c < TC_TM; c++) {
-                    const int b = w.J * TC_TM + c;
-                    if (b < M && a <= b) {
-                        // 2^-(e_a + e_b) and 2^-(e_a + e_b + c) built from their exponent bits
-                        const int e = e_a + __ldg(ea + b);
-                        const double sS = __longlong_as_double((long long)(1023 - e) << 52);
-                        const double sH = __longlong_as_double((long long)(1023 - e - ec) << 52);
-                        const size_t iS = (size_t)c * TC_TM + row, iH = (size_t)(TC_TM + c) * TC_TM + row;
-                        atomicAdd(S + (size_t)a * M + b, ((double)phi_[iS] + (double)plo_[iS]) * sS);
-                        atomicAdd(H2 + (size_t)a * M + b, ((double)phi_[iH] + (double)plo_[iH]) * sH);
-                    }
+            const int e_a = a < M ? ea[a] : 0, ec = ea[M];
+#pragma unroll 1
+            for (int cc = 0; cc < 2 * TC_TM; cc += 16) {
+                float v[16];
+                hs_tmem_ld16(tmem + lanes + (uint32_t)(2 * TC_TM + cc), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                if (a >= M) continue;
+                const bool isH = cc >= TC_TM;
+                double* dst = (isH ? H2 : S) + (size_t)a * M;
+#pragma unroll
+                for (int jj = 0; jj < 16; jj++) {
+                    const int b = w.J * TC_TM + (cc & (TC_TM - 1)) + jj;
+                    if (b < M && a <= b) atomicAdd(dst + b, hs_unscale(v[jj], e_a + __ldg(ea + b) + (isH ? ec : 0)));
                 }
             }
         }
@@ -902,14 +914,14 @@ size_t hs_scratch_bytes(const int n[3], int M, int na)
     const size_t K = hs_rows_per_chunk(N, Mp);
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     return up(sizeof(int) * nblk) + up(sizeof(int) * (nblk + 1)) + up(sizeof(int) * N) + up(sizeof(float) * N) +
-           up(8 * (size_t)Mp * K) + up(sizeof(double) * 2 * TC_TM * TC_TM * (size_t)hs_sm_count()) +
+           up(8 * (size_t)Mp * K) +
            up(sizeof(int) * (Mp + 1)) + up(sizeof(int)) + up(sizeof(float) * 4 * na);
 }
 
 // scratch: hs_scratch_bytes(n, M) bytes, 256-byte aligned; carved into the block counts,
 // offsets, listed nodes, sqrt(Vol), the basis tables (FP32 A and T for the SIMT contraction,
-// FP16 operand images for the tensor cores), the tensor-core CTAs' FP64 partial sums, the
-// per-function maxima and scale exponents, and an error flag.  Synchronises the stream twice
+// FP16 operand images for the tensor cores), the per-function scale exponents, an error flag
+// and the FP32 copies of the spheres.  Synchronises the stream twice
 // (the number of listed nodes sizes the chunk loop; the error flag is read at the end).
 int launch_interstitial_hs(const int n[3], const double* x, const double* y, const double* z, int na,
                            const double* pos, const double* R, int nb, const int* bn, const int* bl,
@@ -958,7 +970,6 @@ int launch_interstitial_hs(const int n[3], const double* x, const double* y, con
     char* tables = carve(8 * (size_t)Mp128 * Kmax);
     float* A = reinterpret_cast<float*>(tables);                  // SIMT: [K][Mp] FP32 each
     float* T = A + (size_t)Mp * Kmax;
-    double* part = reinterpret_cast<double*>(carve(sizeof(double) * 2 * TC_TM * TC_TM * (size_t)sms));
     int* ea = reinterpret_cast<int*>(carve(sizeof(int) * (Mp128 + 1)));
     int* err = reinterpret_cast<int*>(carve(sizeof(int)));
     float4* at4 = reinterpret_cast<float4*>(carve(sizeof(float4) * na));
@@ -1020,7 +1031,7 @@ int launch_interstitial_hs(const int n[3], const double* x, const double* y, con
             const int units = pairs * ((K + HS_SEG - 1) / HS_SEG);
             const int grid = std::min(units, sms);
             k_hs_gemm_tc<<<grid, TC_NT, TC_SMEM, s>>>(M, nT, reinterpret_cast<const unsigned char*>(tables), K, units,
-                                                       ea, S, H, part, err);
+                                                       ea, S, H, err);
         } else {
             // node ranges per tile: about eight CTAs per SM in all
             int split = std::max(1, (8 * sms + pairs - 1) / pairs);
