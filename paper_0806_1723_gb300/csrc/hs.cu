@@ -383,7 +383,7 @@ constexpr int TC_SIDE = 4 * TC_IMG;              // A_hi, A_lo, T_hi, T_lo of on
 constexpr int TC_STAGE = 2 * TC_SIDE;            // the I and J blocks of a tile
 constexpr int TC_RING = 6;
 constexpr int TC_SMEM = TC_RING * TC_STAGE + 128;
-constexpr int HS_IV = 512;                       // nodes per FP32 accumulation interval
+constexpr int HS_IV = 1024;                      // nodes per FP32 accumulation interval
 constexpr int HS_SEG = 2048;                     // nodes per work unit
 constexpr int HS_SCALE_MAX = 14;                 // scaled |x| < 2^14
 
@@ -462,8 +462,9 @@ __device__ __forceinline__ void hs_tmem_ld16(uint32_t taddr, float* v)
 }
 
 // phi and phi~ (FP32, times sqrt(Vol)) of every function of atom `at` at listed node P:
-// out(loc, phi, phi~) for loc in [0, per).  Radial factors per table entry, then the solid
-// harmonics one lm at a time (the same monomial terms in every lane: broadcast constant reads).
+// out(loc, phi, phi~) for loc in [0, per).  The 25 solid harmonics first (straight-line, the
+// same monomial terms in every lane), then per table entry its radial factors and its 2l+1
+// functions (a switch on l keeps the harmonic index a compile-time constant).
 template <typename Out>
 __device__ __forceinline__ void hs_eval_atom(const HsBasis& B, const HsGrid& g, int P, float w, float Vp, int at,
                                              Out&& out)
@@ -473,20 +474,6 @@ __device__ __forceinline__ void hs_eval_atom(const HsBasis& B, const HsGrid& g, 
                 dz = (float)(g.z[k] - g.pos[3 * at + 2]);
     const float r = sqrtf(dx * dx + dy * dy + dz * dz);
     const float ir = 1.0f / r;
-    float rad[HS_MAXB], fac[HS_MAXB];
-#pragma unroll
-    for (int q = 0; q < HS_MAXB; q++) {
-        rad[q] = 0.0f;
-        fac[q] = 0.0f;
-        if (q < B.nb) {
-            const int n = B.n[q], l = B.l[q];
-            const float zt = B.zeta[q];
-            float v = w * expf(-zt * r);
-            for (int t = 0; t < n - 1 - l; t++) v *= r;   // sqrt(Vol) r^(n-1-l) e^{-zeta r}
-            rad[q] = v;
-            fac[q] = 0.5f * ((float)(l * (l + 1) - n * (n - 1)) * ir * ir + 2.0f * zt * (float)n * ir - zt * zt) + Vp;
-        }
-    }
     float px[5], py[5], pz[5];
     px[0] = py[0] = pz[0] = 1.0f;
 #pragma unroll
@@ -502,16 +489,29 @@ __device__ __forceinline__ void hs_eval_atom(const HsBasis& B, const HsGrid& g, 
     if (i < HS_L3_TERMS || B.lmax >= 4) sh[LM] = fmaf(c_hs_coef[i], px[EA] * py[EB] * pz[EC], sh[LM]);
     HS_TERMS(HS_ACC)
 #undef HS_ACC
-#pragma unroll
-    for (int lm = 0; lm < NLM; lm++) {
-        const int l = l_of_lm(lm), m = lm - l * l - l;
-        if (l > B.lmax) break;
-#pragma unroll
-        for (int q = 0; q < HS_MAXB; q++)
-            if (q < B.nb && B.l[q] == l) {
-                const float ph = rad[q] * sh[lm];
-                out(B.off[q] + l + m, ph, fac[q] * ph);
-            }
+#pragma unroll 1
+    for (int q = 0; q < B.nb; q++) {
+        const int n = B.n[q], l = B.l[q], f0 = B.off[q];
+        const float zt = B.zeta[q];
+        float rad = w * expf(-zt * r);
+        for (int t = 0; t < n - 1 - l; t++) rad *= r;   // sqrt(Vol) r^(n-1-l) e^{-zeta r}
+        const float fac =
+            0.5f * ((float)(l * (l + 1) - n * (n - 1)) * ir * ir + 2.0f * zt * (float)n * ir - zt * zt) + Vp;
+#define HS_OUT(m, LM)                         \
+    {                                         \
+        const float ph = rad * sh[LM];        \
+        out(f0 + (m), ph, fac * ph);          \
+    }
+        switch (l) {
+        case 0: HS_OUT(0, 0) break;
+        case 1: HS_OUT(0, 1) HS_OUT(1, 2) HS_OUT(2, 3) break;
+        case 2: HS_OUT(0, 4) HS_OUT(1, 5) HS_OUT(2, 6) HS_OUT(3, 7) HS_OUT(4, 8) break;
+        case 3: HS_OUT(0, 9) HS_OUT(1, 10) HS_OUT(2, 11) HS_OUT(3, 12) HS_OUT(4, 13) HS_OUT(5, 14) HS_OUT(6, 15) break;
+        default:
+            HS_OUT(0, 16) HS_OUT(1, 17) HS_OUT(2, 18) HS_OUT(3, 19) HS_OUT(4, 20) HS_OUT(5, 21) HS_OUT(6, 22)
+            HS_OUT(7, 23) HS_OUT(8, 24) break;
+        }
+#undef HS_OUT
     }
 }
 
@@ -536,8 +536,19 @@ __device__ __forceinline__ int hs_scale_exp(float bound, int lo, int hi)
     return min(hi, max(lo, HS_SCALE_MAX - x));
 }
 
-__global__ void __launch_bounds__(1024) k_hs_bounds(HsBasis B, HsGrid g, const int* __restrict__ idx, int n_list,
-                                                    const double* __restrict__ V, int* __restrict__ ea)
+// max |V| over the listed nodes (non-negative floats as ordered integers)
+__global__ void __launch_bounds__(256) k_hs_vmax(const int* __restrict__ idx, int n_list, const double* __restrict__ V,
+                                                 unsigned* __restrict__ vmax)
+{
+    float m = 0.0f;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_list; p += gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf((float)V[idx[p]]));
+    m = hs_warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(vmax, __float_as_uint(m));
+}
+
+__global__ void __launch_bounds__(1024) k_hs_bounds(HsBasis B, HsGrid g, const unsigned* __restrict__ vmax,
+                                                    int* __restrict__ ea)
 {
     __shared__ float red[32];
     __shared__ float s_w, s_v;
@@ -559,9 +570,7 @@ __global__ void __launch_bounds__(1024) k_hs_bounds(HsBasis B, HsGrid g, const i
         for (int q = threadIdx.x; q < nn[d]; q += blockDim.x) m = fmaxf(m, (float)hs_dual(ax[d], nn[d], q));
         w *= block_max(m);
     }
-    float vm = 0.0f;
-    for (int p = threadIdx.x; p < n_list; p += blockDim.x) vm = fmaxf(vm, fabsf((float)V[idx[p]]));
-    vm = block_max(vm);
+    const float vm = __uint_as_float(*vmax);
     if (threadIdx.x == 0) {
         s_w = sqrtf(w) * 1.001f;
         s_v = vm * 1.001f;
@@ -591,7 +600,7 @@ __global__ void __launch_bounds__(1024) k_hs_bounds(HsBasis B, HsGrid g, const i
 // (lanes) x 8 atoms (warps).  Each warp stages its atom's four FP16 arrays for its 32 nodes in
 // shared memory ([array][function][node]) and writes them out as 16-byte pieces (8 nodes of one
 // function), so that a warp store fills whole 128-byte lines (8 consecutive functions).
-__global__ void __launch_bounds__(256) k_hs_basis16(HsBasis B, HsGrid g, int nT, const int* __restrict__ idx,
+__global__ void __launch_bounds__(256) k_hs_basis16(const __grid_constant__ HsBasis B, HsGrid g, int nT, const int* __restrict__ idx,
                                                     const float* __restrict__ sw, const double* __restrict__ V,
                                                     const int* __restrict__ ea, int p0, int n_list,
                                                     __half* __restrict__ img)
@@ -915,7 +924,7 @@ size_t hs_scratch_bytes(const int n[3], int M, int na)
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     return up(sizeof(int) * nblk) + up(sizeof(int) * (nblk + 1)) + up(sizeof(int) * N) + up(sizeof(float) * N) +
            up(8 * (size_t)Mp * K) +
-           up(sizeof(int) * (Mp + 1)) + up(sizeof(int)) + up(sizeof(float) * 4 * na);
+           up(sizeof(int) * (Mp + 1)) + 2 * up(sizeof(int)) + up(sizeof(float) * 4 * na);
 }
 
 // scratch: hs_scratch_bytes(n, M) bytes, 256-byte aligned; carved into the block counts,
@@ -972,6 +981,7 @@ int launch_interstitial_hs(const int n[3], const double* x, const double* y, con
     float* T = A + (size_t)Mp * Kmax;
     int* ea = reinterpret_cast<int*>(carve(sizeof(int) * (Mp128 + 1)));
     int* err = reinterpret_cast<int*>(carve(sizeof(int)));
+    unsigned* vmax = reinterpret_cast<unsigned*>(carve(sizeof(unsigned)));
     float4* at4 = reinterpret_cast<float4*>(carve(sizeof(float4) * na));
 
     const HsGrid g{n[0], n[1], n[2], na, x, y, z, pos, R};
@@ -1012,7 +1022,10 @@ int launch_interstitial_hs(const int n[3], const double* x, const double* y, con
         // per-function scales; operand images cleared once (the padding functions past M stay zero)
         e = cudaMemsetAsync(tables, 0, 8 * (size_t)Mp128 * Kmax, s);
         if (e != cudaSuccess) return LASTO_ERR_CUDA;
-        k_hs_bounds<<<1, 1024, 0, s>>>(B, g, idx, n_list, V, ea);
+        e = cudaMemsetAsync(vmax, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return LASTO_ERR_CUDA;
+        k_hs_vmax<<<(unsigned)std::min(4 * sms, (n_list + 255) / 256), 256, 0, s>>>(idx, n_list, V, vmax);
+        k_hs_bounds<<<1, 1024, 0, s>>>(B, g, vmax, ea);
     }
     const int pairs = nT * (nT + 1) / 2;
     for (int p0 = 0; p0 < n_list; p0 += (int)Kmax) {
