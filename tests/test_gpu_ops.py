@@ -207,11 +207,11 @@ def test_deposit(orc, small_clusters, precision, tol):
     carries about 44 bits, so both agree to far below the 1e-8 solve tolerance."""
     B = need_gpu()
     for cl in small_clusters:
-        dc = B.DeviceCluster(cl)
         x, y, z = orc.mesh(cl)
-        assert np.abs(host(dc.x) - x).max() < 1e-14 * cl.half_width
+        assert np.abs(host(B.DeviceCluster(cl).x) - x).max() < 1e-14 * cl.half_width
+        dc = B.DeviceCluster(cl, axes=(x, y, z))   # both sides on the oracle's nodes
         b, owner, status = B.lasto_op_deposit(dc, precision=precision)
-        ref, rowner = orc.deposit(cl, host(dc.x), host(dc.y), host(dc.z))
+        ref, rowner = orc.deposit(cl, x, y, z)
         assert host(status)[0] == 0
         assert np.array_equal(host(owner), rowner)
         b = host(b)
@@ -225,8 +225,8 @@ def test_deposit(orc, small_clusters, precision, tol):
 def test_multipoles_and_faces(orc, small_clusters):
     B = need_gpu()
     for cl in small_clusters:
-        dc = B.DeviceCluster(cl)
-        x, y, z = host(dc.x), host(dc.y), host(dc.z)
+        x, y, z = orc.mesh(cl)
+        dc = B.DeviceCluster(cl, axes=(x, y, z))
         b, _, _ = B.lasto_op_deposit(dc)
         bh = host(b)
         Q = host(B.lasto_op_multipoles(dc.x, dc.y, dc.z, b))
@@ -242,8 +242,8 @@ def test_multipoles_and_faces(orc, small_clusters):
 def test_projection(orc):
     B = need_gpu()
     cl = synth.pd13_small(n=33)
-    dc = B.DeviceCluster(cl)
-    x, y, z = host(dc.x), host(dc.y), host(dc.z)
+    x, y, z = orc.mesh(cl)
+    dc = B.DeviceCluster(cl, axes=(x, y, z))
     u = np.random.default_rng(11).normal(size=(33, 33, 33))
     vlm, status = B.lasto_op_project(dc.x, dc.y, dc.z, dev(u), dc.pos, dc.R)
     ref = orc.project(x, y, z, u, cl.pos, cl.R)

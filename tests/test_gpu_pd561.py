@@ -16,7 +16,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
 @pytest.fixture(scope="module")
-def pd561_solution():
+def pd561_solution(orc):
     import torch
     B = need_gpu()
     seq = synth.pd561_graded385(n_densities=2)
@@ -24,7 +24,7 @@ def pd561_solution():
     out = []
     pot = torch.empty(385 ** 3, dtype=torch.float64, device="cuda")
     for cl in seq:          # two SCF-like densities back to back, the second warm-started from the first
-        dc = B.DeviceCluster(cl)
+        dc = B.DeviceCluster(cl, axes=orc.mesh(cl))   # the oracle's nodes on both sides
         vlm = torch.empty((561, 25), dtype=torch.float64, device="cuda")
         st = solver.solve(dc, vlm, potential=pot, guess=pot if out else None)
         torch.cuda.synchronize()
@@ -43,7 +43,7 @@ def test_converged_and_warm_start_helps(pd561_solution):
 def test_deposit_at_sampled_nodes(orc, pd561_solution):
     out, b, owner = pd561_solution
     cl, dc = out[0][0], out[0][1]
-    x, y, z = host(dc.x), host(dc.y), host(dc.z)
+    x, y, z = orc.mesh(cl)
     q, rhoR, drhoR, coef = orc.sphere_params(cl)
     rng = np.random.default_rng(0)
     n = cl.n
@@ -66,7 +66,7 @@ def test_equation_holds_at_sampled_nodes(orc, pd561_solution):
     there: each local residual is at the level the global 1e-10 residual allows."""
     out, b, owner = pd561_solution
     cl, dc, vlm, pot, st = out[0]
-    x, y, z = host(dc.x), host(dc.y), host(dc.z)
+    x, y, z = orc.mesh(cl)
     n = cl.n
     u = pot.reshape(n, n, n)
     rng = np.random.default_rng(1)
@@ -93,5 +93,5 @@ def test_projection_of_the_gpu_potential(orc, pd561_solution):
     out, _, _ = pd561_solution
     cl, dc, vlm, pot, st = out[0]
     n = cl.n
-    ref = orc.project(host(dc.x), host(dc.y), host(dc.z), pot.reshape(n, n, n), cl.pos, cl.R)
+    ref = orc.project(*orc.mesh(cl), pot.reshape(n, n, n), cl.pos, cl.R)
     assert np.abs(vlm - ref).max() <= 1e-12 * np.abs(ref).max()

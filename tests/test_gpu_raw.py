@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _raw_inputs(orc, cl, B, dc):
-    x, y, z = host(dc.x), host(dc.y), host(dc.z)
+    x, y, z = orc.mesh(cl)
     ne = orc.density_grid(cl, x, y, z)
     rho00 = orc.sphere_density(cl)[:, 0, :]
     rc = B.RawCluster(cl.pos, cl.Z, cl.R, dc.x, dc.y, dc.z, cl.centre, ne, rho00)
@@ -21,7 +21,7 @@ def _raw_inputs(orc, cl, B, dc):
 def test_raw_deposit(orc, make):
     B = need_gpu()
     cl = make()
-    dc = B.DeviceCluster(cl)
+    dc = B.DeviceCluster(cl, axes=orc.mesh(cl))
     x, y, z, ne, rho00, rc = _raw_inputs(orc, cl, B, dc)
     b, owner, status = B.lasto_op_raw_deposit(rc)
     ref, rowner = orc.raw_deposit(cl.pos, cl.Z, cl.R, x, y, z, ne, rho00)
@@ -38,7 +38,7 @@ def test_raw_solve_matches_the_oracle_chain(orc, precision):
     import torch
     B = need_gpu()
     cl = synth.pd13_small(n=33)
-    dc = B.DeviceCluster(cl)
+    dc = B.DeviceCluster(cl, axes=orc.mesh(cl))
     x, y, z, ne, rho00, rc = _raw_inputs(orc, cl, B, dc)
     prec = B.LASTO_PREC_MIXED if precision == "mixed" else B.LASTO_PREC_FP64
     solver = B.Poisson(n_max=33, max_atoms=13, precision=prec)

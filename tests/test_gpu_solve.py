@@ -239,10 +239,11 @@ def test_boundary_exact_op(orc):
     B = need_gpu()
     import torch
     for cl in (synth.pd13_small(n=33), synth.pd2_dimer(n=33)):
-        dc = B.DeviceCluster(cl)
+        x, y, z = orc.mesh(cl)
+        dc = B.DeviceCluster(cl, axes=(x, y, z))
         u = torch.zeros((cl.n,) * 3, dtype=torch.float64, device="cuda")
         got = host(B.lasto_op_boundary_exact(dc, u))
-        ref = orc.boundary_exact(cl, host(dc.x), host(dc.y), host(dc.z))
+        ref = orc.boundary_exact(cl, x, y, z)
         # the faces carry the small remainder of the nuclei's Z/r and the shells' potentials
         assert np.abs(got - ref).max() < 1e-14 * 46.0 * cl.n_atoms / cl.half_width * 10
 
