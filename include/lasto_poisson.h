@@ -459,7 +459,7 @@ int lasto_nn_adam(size_t n, float* w, const float* g, float* m, float* v, float 
  * Basis values in FP32 (weighted by sqrt(Vol)); mode LASTO_HS_TENSOR (the default) contracts
  * them on the tensor cores: each value, scaled by a power of two per function (one more
  * common power of two for phi~) below 2^14, is split into two FP16 parts and a product taken
- * as hi*hi + hi*lo + lo*hi (22 significant bits), FP32 accumulation over 1024-node intervals
+ * as hi*hi + hi*lo + lo*hi (22 significant bits), FP32 accumulation over 512-node intervals
  * added in FP64 with the scales undone; LASTO_HS_SIMT takes FP32 products summed over 32-node
  * steps, added in FP64.  Sums across CTAs meet by FP64 atomic addition, so the last bits may
  * differ between calls.  Allocates its scratch stream-ordered (at most about 2 GiB of basis

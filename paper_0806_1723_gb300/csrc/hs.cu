@@ -364,26 +364,25 @@ __global__ void __launch_bounds__(HS_NT) k_hs_gemm_f32(int M, int Mp, int nT, co
 // array), the four arrays (A_hi, A_lo, T_hi, T_lo) of a block adjacent, so that a stage of a
 // tile is two 16 KiB bulk copies (cp.async.bulk, completion counted on an mbarrier).
 //
-// Warp roles: one thread issues the bulk copies into a ring of six 32 KiB stages, one thread
-// issues the MMAs (and frees a stage by tcgen05.commit to its mbarrier), four warps drain the
-// accumulators (tensor-memory columns 0-255; lane = function row) every HS_IV nodes into the
-// unit's FP32 partial sums, which stay in tensor memory (columns 256-511; tcgen05.ld, add,
-// tcgen05.st), so that the FP32 sums are never longer than one interval.  A work unit is one
-// upper-triangle tile and HS_SEG nodes, numbered segment-major so that the CTAs running
-// together read the same table rows (from L2); at a unit's end the drain warps form its
-// partial sums in FP64, undo the scales (exponent arithmetic) and add them to S and 2H by
-// FP64 atomic addition while the MMAs run on.  Every wait is bounded (about two seconds, or until
-// another role has given up): the CTA then records an error, lets its copies and MMAs in
-// flight finish (bounded), frees its tensor memory and returns.
+// Warp roles (10 warps): one thread issues the bulk copies into a ring of six 32 KiB stages,
+// one thread issues the MMAs (and frees a stage by tcgen05.commit to its mbarrier) into the
+// accumulators (tensor-memory columns 0-127 S, 128-255 2H; lane = function row), and eight
+// warps (warp w: lanes 32 (w % 4) .. +31, S for w < 4 and 2H for w >= 4) add each HS_IV-node
+// interval's sums into the unit's FP32 partial sums, which stay in tensor memory (columns
+// 256-511; tcgen05.ld, add, tcgen05.st), so that no FP32 accumulation inside the tensor core
+// is longer than one interval.  A work unit is one upper-triangle tile and HS_SEG nodes,
+// numbered segment-major so that the CTAs running together read the same table rows (from
+// L2); at a unit's end the drain warps form its partial sums in FP64, undo the scales
+// (exponent arithmetic) and add them to S and 2H by FP64 atomic addition while the MMAs run on.
 constexpr int TC_TM = 128;                       // functions per tile side (MMA M and N)
-constexpr int TC_NT = 256;                       // threads
+constexpr int TC_NT = 320;                       // threads: 8 drain warps, producer, MMA issuer
 constexpr int TC_SK = 16;                        // nodes per stage (one MMA K step)
 constexpr int TC_IMG = TC_TM * TC_SK * 2;        // one FP16 operand image: 4 KiB
 constexpr int TC_SIDE = 4 * TC_IMG;              // A_hi, A_lo, T_hi, T_lo of one function block
 constexpr int TC_STAGE = 2 * TC_SIDE;            // the I and J blocks of a tile
 constexpr int TC_RING = 6;
 constexpr int TC_SMEM = TC_RING * TC_STAGE + 128;
-constexpr int HS_IV = 1024;                      // nodes per FP32 accumulation interval
+constexpr int HS_IV = 512;                       // nodes per FP32 accumulation interval
 constexpr int HS_SEG = 2048;                     // nodes per work unit
 constexpr int HS_SCALE_MAX = 14;                 // scaled |x| < 2^14
 
@@ -691,7 +690,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&empty[s])) : "memory");
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(hs_smem_u32(&accf)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;\n" ::"r"(hs_smem_u32(&acce)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;\n" ::"r"(hs_smem_u32(&acce)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -706,7 +705,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
     const uint32_t tmem = tmem_slot;
     int last_mma = -1;   // the MMA thread's last committed stage
 
-    if (warp == 0 && lane == 0) {
+    if (warp == 8 && lane == 0) {
         // ---------------- producer: two bulk copies per stage
         int g = 0;
         bool ok = true;
@@ -744,7 +743,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
                 hs_wait(hs_smem_u32(&full[q % TC_RING]), (uint32_t)((q / TC_RING) & 1), &never);
             }
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 9 && lane == 0) {
         // ---------------- MMA issuer: accumulators in columns 0-127 (S) and 128-255 (2H)
         int g = 0, ic = 0;
         bool ok = true;
@@ -787,11 +786,12 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
                 if (ok) hs_commit(hs_smem_u32(&accf));
             }
         }
-    } else if (warp >= 4) {
-        // ---------------- drain: row = tensor-memory lane; interval sums (columns 0-255) added
-        // into the unit's partial sums (columns 256-511)
-        const int q = warp - 4, row = 32 * q + lane;
-        const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    } else if (warp < 8) {
+        // ---------------- drain: row = tensor-memory lane; S (warps 0-3) or 2H (4-7) columns of
+        // the interval added into the unit's partial sums 256 columns further on
+        const int q = warp & 3, half = warp >> 2, row = 32 * q + lane;
+        const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(half * TC_TM);
+        const uint32_t tp = ta + 2 * TC_TM;
         int ic = 0;
         bool ok = true;
         for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
@@ -806,36 +806,40 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const bool first = c0 == w.k0;
 #pragma unroll 1
-                for (int cc = 0; cc < 2 * TC_TM; cc += 16) {
-                    float v[16], pv[16];
-                    hs_tmem_ld16(tmem + lanes + (uint32_t)cc, v);
-                    if (!first) hs_tmem_ld16(tmem + lanes + (uint32_t)(2 * TC_TM + cc), pv);
+                for (int cc = 0; cc < TC_TM; cc += 32) {
+                    float v[32], pv[32];
+                    hs_tmem_ld16(ta + (uint32_t)cc, v);
+                    hs_tmem_ld16(ta + (uint32_t)(cc + 16), v + 16);
+                    if (!first) {
+                        hs_tmem_ld16(tp + (uint32_t)cc, pv);
+                        hs_tmem_ld16(tp + (uint32_t)(cc + 16), pv + 16);
+                    }
                     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                     if (!first)
 #pragma unroll
-                        for (int jj = 0; jj < 16; jj++) v[jj] += pv[jj];
-                    hs_tmem_st16(tmem + lanes + (uint32_t)(2 * TC_TM + cc), v);
+                        for (int jj = 0; jj < 32; jj++) v[jj] += pv[jj];
+                    hs_tmem_st16(tp + (uint32_t)cc, v);
+                    hs_tmem_st16(tp + (uint32_t)(cc + 16), v + 16);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(hs_smem_u32(&acce)) : "memory");
             }
             if (!ok) break;
-            // the unit's sums: FP64, scales undone, into S and 2H
+            // the unit's sums: FP64, scales undone, into S or 2H
             const int a = w.I * TC_TM + row;
-            const int e_a = a < M ? ea[a] : 0, ec = ea[M];
+            const int e_a = a < M ? ea[a] + (half ? ea[M] : 0) : 0;
+            double* dst = (half ? H2 : S) + (size_t)(a < M ? a : 0) * M;
 #pragma unroll 1
-            for (int cc = 0; cc < 2 * TC_TM; cc += 16) {
+            for (int cc = 0; cc < TC_TM; cc += 16) {
                 float v[16];
-                hs_tmem_ld16(tmem + lanes + (uint32_t)(2 * TC_TM + cc), v);
+                hs_tmem_ld16(tp + (uint32_t)cc, v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                 if (a >= M) continue;
-                const bool isH = cc >= TC_TM;
-                double* dst = (isH ? H2 : S) + (size_t)a * M;
 #pragma unroll
                 for (int jj = 0; jj < 16; jj++) {
-                    const int b = w.J * TC_TM + (cc & (TC_TM - 1)) + jj;
-                    if (b < M && a <= b) atomicAdd(dst + b, hs_unscale(v[jj], e_a + __ldg(ea + b) + (isH ? ec : 0)));
+                    const int b = w.J * TC_TM + cc + jj;
+                    if (b < M && a <= b) atomicAdd(dst + b, hs_unscale(v[jj], e_a + __ldg(ea + b)));
                 }
             }
         }
@@ -843,7 +847,7 @@ __global__ void __launch_bounds__(TC_NT, 1) k_hs_gemm_tc(int M, int nT, const un
     __syncthreads();
     if (abort_flag) {
         // the MMAs already issued finish before the tensor memory is released
-        if (warp == 1 && lane == 0 && last_mma >= 0) {
+        if (warp == 9 && lane == 0 && last_mma >= 0) {
             volatile int never = 0;
             hs_wait(hs_smem_u32(&empty[last_mma % TC_RING]), (uint32_t)((last_mma / TC_RING) & 1), &never);
         }
