@@ -44,6 +44,12 @@ void host_solid_harmonics(double x, double y, double z, double* S);
 
 __host__ __device__ __forceinline__ int l_of_lm(int lm) { return lm >= 16 ? 4 : lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0; }
 
+// ---------------------------------------------------------------- FP32 point update
+// u = acc / (-dsum) of a red-black FP32 update as acc times the correctly rounded reciprocal:
+// the same expression in every FP32 smoother variant (so they stay bitwise equal), and about
+// 10 % faster than the IEEE division in the memory-bound half sweep.
+__device__ __forceinline__ float rb_point32(float acc, float dsum) { return acc * __frcp_rn(-dsum); }
+
 // ---------------------------------------------------------------- block reductions
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* smem)

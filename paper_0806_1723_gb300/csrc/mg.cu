@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, co
     if constexpr (sizeof(T) == 8) {
         u[P] = acc * L.inv_diag[P];
     } else {
-        u[P] = acc / (-dsum(L, i, j, k));
+        u[P] = rb_point32(acc, dsum(L, i, j, k));
     }
 }
 
@@ -356,7 +356,7 @@ __device__ void bot_rbgs(const LevelT<T>& L, T* __restrict__ u, const T* __restr
         if (is_face(L, i, j, k)) continue;
         const T acc = b[P] - offdiag(L, u, P, i, j, k);
         if constexpr (sizeof(T) == 8) u[P] = acc * L.inv_diag[P];
-        else u[P] = acc / (-dsum(L, i, j, k));
+        else u[P] = rb_point32(acc, dsum(L, i, j, k));
     }
     __syncthreads();
 }

@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(SLAB_NT) k_rb_slab(LevelT<T> L, const T* __res
                     if constexpr (sizeof(T) == 8) {
                         pc[o] = acc * L.inv_diag[P];
                     } else {
-                        pc[o] = acc / (-(L.ax[0].dg[i] + L.ax[1].dg[j] + L.ax[2].dg[q]));
+                        pc[o] = rb_point32(acc, L.ax[0].dg[i] + L.ax[1].dg[j] + L.ax[2].dg[q]);
                     }
                 }
             }
@@ -265,7 +265,7 @@ __device__ __forceinline__ void col_sweep(const LevelT<T>& L, const T* __restric
                     if constexpr (sizeof(T) == 8)
                         ua[r1] = acc * va[r1];
                     else
-                        ua[r1] = acc / (-(dga + dgy + zc[2]));
+                        ua[r1] = rb_point32(acc, dga + dgy + zc[2]);
                 } else {
                     t = cmxb * ua[r1];
                     t = fma(cpxb, A[oA + 2], t);
@@ -277,7 +277,7 @@ __device__ __forceinline__ void col_sweep(const LevelT<T>& L, const T* __restric
                     if constexpr (sizeof(T) == 8)
                         ub[r1] = acc * vb[r1];
                     else
-                        ub[r1] = acc / (-(dgb + dgy + zc[2]));
+                        ub[r1] = rb_point32(acc, dgb + dgy + zc[2]);
                 }
             }
             // black node of plane p-2 (tile nodes only): node a when RB + s is odd
@@ -297,7 +297,7 @@ __device__ __forceinline__ void col_sweep(const LevelT<T>& L, const T* __restric
                     if constexpr (sizeof(T) == 8)
                         ua[r2] = acc * va[r2];
                     else
-                        ua[r2] = acc / (-(dga + dgy + zc[2]));
+                        ua[r2] = rb_point32(acc, dga + dgy + zc[2]);
                 } else {
                     t = cmxb * ua[r2];
                     t = fma(cpxb, Bp[oB + 2], t);
@@ -309,7 +309,7 @@ __device__ __forceinline__ void col_sweep(const LevelT<T>& L, const T* __restric
                     if constexpr (sizeof(T) == 8)
                         ub[r2] = acc * vb[r2];
                     else
-                        ub[r2] = acc / (-(dgb + dgy + zc[2]));
+                        ub[r2] = rb_point32(acc, dgb + dgy + zc[2]);
                 }
             }
             if (q2 >= k0 && q2 < k1) {

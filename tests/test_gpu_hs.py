@@ -153,3 +153,18 @@ def test_rejects_bad_arguments():
     for mode in (-1, 3):
         with pytest.raises(RuntimeError):
             B.lasto_op_interstitial_hs(x, x, x, pos, R, V, mode=mode)
+
+
+@pytest.mark.parametrize("mode", MODES[1:])
+def test_no_interstitial_nodes(orc, mode):
+    """A sphere that holds the whole box leaves no interstitial node: S = H = 0 (the oracle's
+    sums are empty too)."""
+    B = need_gpu()
+    cl = synth.pd2_dimer(n=17)
+    x, y, z = _axes(orc, cl)
+    pos, R = np.zeros((1, 3)), np.array([100.0])
+    V = _potential(cl, x, y, z, 7)
+    S, H = B.lasto_op_interstitial_hs(dev(x), dev(y), dev(z), dev(pos), dev(R), dev(V), basis=PD, mode=mode)
+    Sr, Hr = orc.interstitial_hs(pos, R, x, y, z, V, PD)
+    assert not np.any(Sr) and not np.any(Hr)
+    assert not np.any(host(S)) and not np.any(host(H))
