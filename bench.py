@@ -44,6 +44,12 @@ FORM = ("learned initial guess (U-Net in the graph) + FP64 defect correction aro
 BATCH = 8
 
 
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per FP32 half sweep at 257^3 (mean of the red
+# and black launch) by launch shape of the current kernels; a shape without a capture reports
+# traffic null
+DRAM_BYTES_257 = {0: 153.2e6, 128: 153.4e6, 256: 153.3e6}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -63,6 +69,8 @@ def parse():
                         "of the Pd561 graded 385^3 workload with direct launches, 'hs' = one interstitial H and S "
                         "call (tensor cores) for Pd55 on the graded 129^3 mesh")
     p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
+    p.add_argument("--threads", type=int, default=256,
+                   help="launch shape of --profile smoother: threads per block, 0 = one block per row")
     p.add_argument("--direct", action="store_true",
                    help="launch the kernels directly instead of one CUDA graph per solve (for ncu)")
     return p.parse_args()
@@ -275,7 +283,8 @@ def main():
         barrier(ws)
     tuned = [line.split() for line in chosen.tune_table().strip().splitlines()]
     smoother_choice = {f"{r[0]}x{r[1]}x{r[2]}/{'f32' if r[3] == '4' else 'f64'}":
-                       (f"in-place half sweeps, {r[5]} threads" if r[4] == "0" else
+                       ((f"in-place half sweeps, {r[5]} threads" if r[5] != "0" else "in-place half sweeps, one block per row")
+                        if r[4] == "0" else
                         f"fused {r[9]}-sweep passes, tile {r[6]}x{r[7]}x{r[8]}") + f" ({float(r[10]):.1f} us)"
                        for r in tuned}
     span_max = max_over_ranks(sum(r_chosen["ms"]), ws, dev)
@@ -420,7 +429,7 @@ def run_profile(args, B):
         axes = [B.lasto_mesh_axis(n, 0.0, 30.0, 0.12, 0.6, 6.0) for _ in range(3)]
         u = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
         b = torch.rand(n ** 3, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
-        B.lasto_op_smooth(*axes, u, b, sweeps=1)
+        B.lasto_op_smooth(*axes, u, b, sweeps=1, threads=args.threads)
     else:
         cl = synth.pd561_graded385(n_densities=1)[0] if args.profile == "pd561" else synth.pd55_graded129()
         solver = B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, precision=B.LASTO_PREC_MIXED, launch=1)
@@ -578,7 +587,8 @@ def smoother_roofline(B, stream, flush, dev):
     """FP32 red-black half sweep on the 385^3 graded Pd561 mesh (456 MB of u and b, far beyond
     L2).  Algorithmic bytes per half sweep: every node's u read once (4 B), the colour's b read
     and u written (8 B per updated node) = 8 B per node.  Time per launch from a 1-sweep and a
-    3-sweep call (the difference is 4 launches), L2 flushed before each call."""
+    3-sweep call (the difference is 4 launches), L2 flushed before each call, for each launch
+    shape the solver's tuner chooses among; the fastest is reported."""
     import json as _json
     import torch
 
@@ -589,20 +599,25 @@ def smoother_roofline(B, stream, flush, dev):
     u = torch.zeros(n ** 3, dtype=torch.float32, device=dev)
     b = torch.rand(n ** 3, dtype=torch.float32, device=dev)
 
-    def timed(sweeps):
+    def timed(sweeps, threads):
         ts = []
         for _ in range(3):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            B.lasto_op_smooth(*axes, u, b, sweeps=sweeps)
+            B.lasto_op_smooth(*axes, u, b, sweeps=sweeps, threads=threads)
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
-    timed(1)
-    t_launch = (timed(3) - timed(1)) / 4 / 1e3
+    # the launch shapes the solver's tuner chooses among (flat 128/256/512, one block per row)
+    per = {}
+    for threads in (0, 128, 256, 512):
+        timed(1, threads)
+        per[threads] = (timed(3, threads) - timed(1, threads)) / 4 / 1e3
+    best = min(per, key=per.get)
+    t_launch = per[best]
     bytes_per_launch = 8.0 * n ** 3
     peaks = {}
     try:
@@ -613,12 +628,15 @@ def smoother_roofline(B, stream, flush, dev):
     achieved = bytes_per_launch / t_launch / 1e9
     del u, b
     torch.cuda.empty_cache()
-    # DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel at 257^3
-    # (134.8 MB + 18.3 MB, mean of the red and the black launch), scaled by the node count
-    traffic = 153.1e6 * (n / 257.0) ** 3
-    return {"kernel": "k_rbgs<float> (red-black half sweep, 385^3 graded)", "bound": "hbm", "achieved": achieved,
+    # DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of the chosen
+    # launch shape at 257^3 (mean of the red and the black launch), scaled by the node count
+    traffic_257 = DRAM_BYTES_257.get(best)
+    traffic = traffic_257 * (n / 257.0) ** 3 if traffic_257 else None
+    name = "k_rbgs_row<float>, one block per row" if best == 0 else f"k_rbgs<float>, {best} threads per block"
+    return {"kernel": f"{name} (red-black half sweep, 385^3 graded)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
+            "us_per_launch_by_shape": {("rows" if k == 0 else str(k)): v * 1e6 for k, v in per.items()},
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
 

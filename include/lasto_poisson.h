@@ -138,9 +138,10 @@ typedef struct lasto_poisson lasto_poisson;   /* opaque; owns workspace, plans a
 
 /* Smoother tuning (no counterpart in the paper, which gives no implementation).  The first
  * solve of each new batch layout times, per level shape and precision, the red-black
- * smoother as in-place half sweeps (128, 256 or 512 threads per block) and as fused passes
- * of the z-slab and register-column kernels (several tile shapes), and the cycle uses the
- * fastest; all give bitwise the same iterates.  lasto_poisson_tune_table writes the table as
+ * smoother as in-place half sweeps (128, 256 or 512 threads per block over the flat node
+ * index, or one block per (j, k) row: threads = 0) and as fused passes of the z-slab and
+ * register-column kernels (several tile shapes), and the cycle uses the fastest; all give
+ * bitwise the same iterates.  lasto_poisson_tune_table writes the table as
  * text, one line per shape: "nx ny nz elem_bytes fused threads tx ty kz sweeps_per_pass us"
  * (NUL-terminated into buf when cap > 0) and returns its length, -1 for a null handle.
  * lasto_poisson_set_tune_table adds such lines (shapes it lists are then not timed);
@@ -332,13 +333,14 @@ int lasto_op_apply(const int n[3], const double* x, const double* y, const doubl
 int lasto_op_residual(const int n[3], const double* x, const double* y, const double* z, const double* u,
                       const double* b, double* r, void* stream);
 
-/* Red-black Gauss-Seidel: `sweeps` sweeps, each a red (i+j+k even) then a black
- * half sweep, in place on u.  fp32 != 0 runs the FP32 smoother on float copies
- * (u32, b32 device float [N]) instead of u, b. */
+/* Red-black Gauss-Seidel (Section 3): `sweeps` sweeps, each a red (i+j+k even) then a black
+ * half sweep, in place on u (FP64, or FP32 for the _f32 form).  threads: 32..512 (a multiple
+ * of 32) threads per block over the flat node index, or 0 for one block per (j, k) row (rows
+ * of at most 1023 nodes); every choice gives bitwise the same result. */
 int lasto_op_smooth(const int n[3], const double* x, const double* y, const double* z, double* u,
-                    const double* b, int sweeps, void* stream);
+                    const double* b, int sweeps, int threads, void* stream);
 int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const double* z, float* u,
-                        const float* b, int sweeps, void* stream);
+                        const float* b, int sweeps, int threads, void* stream);
 
 /* Red-black Gauss-Seidel on z-slabs staged in shared memory (the Section 3 smoother):
  * `sweeps` full sweeps, each colour `first` (0 = red, i+j+k even) then the other, from

@@ -94,8 +94,8 @@ def _declare(L):
         "lasto_op_boundary_exact": (i, [clp, vp, vp]),
         "lasto_op_apply": (i, [ip, vp, vp, vp, vp, vp, vp]),
         "lasto_op_residual": (i, [ip, vp, vp, vp, vp, vp, vp, vp]),
-        "lasto_op_smooth": (i, [ip, vp, vp, vp, vp, vp, i, vp]),
-        "lasto_op_smooth_f32": (i, [ip, vp, vp, vp, vp, vp, i, vp]),
+        "lasto_op_smooth": (i, [ip, vp, vp, vp, vp, vp, i, i, vp]),
+        "lasto_op_smooth_f32": (i, [ip, vp, vp, vp, vp, vp, i, i, vp]),
         "lasto_op_smooth_slab": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, ip, vp]),
         "lasto_op_smooth_slab_f32": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, ip, vp]),
         "lasto_op_restrict": (i, [ip, vp, vp, vp, vp, vp, vp]),
@@ -382,9 +382,10 @@ def lasto_op_residual(x, y, z, u, b, stream=None):
     return out
 
 
-def lasto_op_smooth(x, y, z, u, b, sweeps=1, stream=None):
+def lasto_op_smooth(x, y, z, u, b, sweeps=1, threads=256, stream=None):
+    """`sweeps` red-black sweeps in place on u (FP64 or FP32); threads 0 = one block per row."""
     fn = load().lasto_op_smooth if u.dtype == torch.float64 else load().lasto_op_smooth_f32
-    _check(fn(*_axes(x, y, z), _ptr(u), _ptr(b), int(sweeps), _stream(stream)), "lasto_op_smooth")
+    _check(fn(*_axes(x, y, z), _ptr(u), _ptr(b), int(sweeps), int(threads), _stream(stream)), "lasto_op_smooth")
     return u
 
 

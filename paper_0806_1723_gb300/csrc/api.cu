@@ -311,7 +311,7 @@ int fused_passes(int nu, int ns) { return nu / ns + (nu % ns ? 1 : 0); }
 
 bool choice_usable(const lasto_poisson* h, const SmoothChoice& c, size_t elem)
 {
-    if (!c.fused) return c.nt >= 32 && c.nt <= 512 && c.nt % 32 == 0;
+    if (!c.fused) return c.nt == 0 || (c.nt >= 32 && c.nt <= 512 && c.nt % 32 == 0);
     // the pre- and post-smoothing passes together must return the data to its home array
     return slab_shape_ok(c.sh, elem) && (fused_passes(h->cfg.nu1, c.sh.ns) + fused_passes(h->cfg.nu2, c.sh.ns)) % 2 == 0;
 }
@@ -342,6 +342,11 @@ int tune_level(lasto_poisson* h, LevelStore& S, cudaStream_t st)
     for (int nt : {128, 256, 512}) {
         SmoothChoice c;
         c.nt = nt;
+        cand.push_back(c);
+    }
+    if ((S.n[0] + 1) / 2 <= 512) {
+        SmoothChoice c;
+        c.nt = 0;   // one block per row
         cand.push_back(c);
     }
     const bool f32 = sizeof(T) == 4;
@@ -1458,31 +1463,35 @@ int lasto_op_residual(const int n[3], const double* x, const double* y, const do
 }
 
 int lasto_op_smooth(const int n[3], const double* x, const double* y, const double* z, double* u, const double* b,
-                    int sweeps, void* stream)
+                    int sweeps, int threads, void* stream)
 {
     if (!op_grid_ok(n, x, y, z) || !u || !b || sweeps < 0) return LASTO_ERR_INVALID_ARG;
+    if (threads != 0 && (threads < 32 || threads > 512 || threads % 32)) return LASTO_ERR_INVALID_ARG;
+    if (threads == 0 && n[0] > 1023) return LASTO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     OpLevel L(n, x, y, z, true, s);
     if (!L.ok()) return LASTO_ERR_NO_MEMORY;
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < sweeps && e == cudaSuccess; it++) {
-        e = launch_rbgs<double>(L.S.view64(), u, b, 0, s);
-        if (e == cudaSuccess) e = launch_rbgs<double>(L.S.view64(), u, b, 1, s);
+        e = launch_rbgs<double>(L.S.view64(), u, b, 0, s, threads);
+        if (e == cudaSuccess) e = launch_rbgs<double>(L.S.view64(), u, b, 1, s, threads);
     }
     return op_status(e);
 }
 
 int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const double* z, float* u, const float* b,
-                        int sweeps, void* stream)
+                        int sweeps, int threads, void* stream)
 {
     if (!op_grid_ok(n, x, y, z) || !u || !b || sweeps < 0) return LASTO_ERR_INVALID_ARG;
+    if (threads != 0 && (threads < 32 || threads > 512 || threads % 32)) return LASTO_ERR_INVALID_ARG;
+    if (threads == 0 && n[0] > 1023) return LASTO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     OpLevel L(n, x, y, z, false, s);
     if (!L.ok()) return LASTO_ERR_NO_MEMORY;
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < sweeps && e == cudaSuccess; it++) {
-        e = launch_rbgs<float>(L.S.view32(), u, b, 0, s);
-        if (e == cudaSuccess) e = launch_rbgs<float>(L.S.view32(), u, b, 1, s);
+        e = launch_rbgs<float>(L.S.view32(), u, b, 0, s, threads);
+        if (e == cudaSuccess) e = launch_rbgs<float>(L.S.view32(), u, b, 1, s, threads);
     }
     return op_status(e);
 }

@@ -73,9 +73,34 @@ __global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, co
     }
 }
 
+// The same half sweep with one block per interior (j, k) row and one thread per node of the
+// colour along i: no index division, the row's y and z coefficients the same in every thread.
+// The node update is k_rbgs's expression, so the two are bitwise equal.
+template <typename T>
+__global__ void __launch_bounds__(512) k_rbgs_row(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour)
+{
+    const int j = blockIdx.x + 1, k = blockIdx.y + 1;
+    const int i = 2 * (int)threadIdx.x + ((colour + j + k) & 1);   // flat-index parity = parity of i + j + k
+    if (i == 0 || i >= L.nx - 1) return;
+    const size_t P = ((size_t)k * L.ny + j) * L.nx + i;
+    const T acc = b[P] - offdiag(L, u, P, i, j, k);
+    if constexpr (sizeof(T) == 8) {
+        u[P] = acc * L.inv_diag[P];
+    } else {
+        u[P] = rb_point32(acc, dsum(L, i, j, k));
+    }
+}
+
+// nt > 0: k_rbgs with nt threads per block; nt == 0: k_rbgs_row (rows of at most 1023 nodes)
 template <typename T>
 cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt)
 {
+    if (nt == 0) {
+        const int th = ((L.nx + 1) / 2 + 31) / 32 * 32;
+        if (th > 512 || L.ny < 3 || L.nz < 3 || L.nz - 2 > 65535) return cudaErrorInvalidValue;
+        k_rbgs_row<T><<<dim3((unsigned)(L.ny - 2), (unsigned)(L.nz - 2)), th, 0, s>>>(L, u, b, colour);
+        return cudaGetLastError();
+    }
     if (nt < 32 || nt > 512 || nt % 32) return cudaErrorInvalidValue;
     const size_t N = L.N();
     const size_t nhalf = (N + 1 - colour) / 2;

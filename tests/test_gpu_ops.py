@@ -130,6 +130,24 @@ def test_slab_smoother_fp32(orc):
     assert torch.equal(o5, B.lasto_op_smooth(dev(x), dev(y), dev(z), u32.clone(), b32, sweeps=5))
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_row_mapped_half_sweeps(dtype):
+    """One block per (j, k) row gives bitwise the flat-index half sweeps (any block size)."""
+    B = need_gpu()
+    import torch
+    n = (65, 33, 49)
+    x, y, z = _grid(n, 21)
+    rng = np.random.default_rng(22)
+    t = torch.float32 if dtype == "f32" else torch.float64
+    u = torch.as_tensor(rng.normal(size=n[::-1])).to(t).cuda()
+    b = torch.as_tensor(rng.normal(size=n[::-1])).to(t).cuda()
+    outs = [B.lasto_op_smooth(dev(x), dev(y), dev(z), u.clone(), b, sweeps=3, threads=th) for th in (0, 128, 512)]
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    for bad in (-1, 16, 100, 1024):
+        with pytest.raises(RuntimeError):
+            B.lasto_op_smooth(dev(x), dev(y), dev(z), u.clone(), b, sweeps=1, threads=bad)
+
+
 def test_slab_smoother_rejects_bad_arguments():
     B = need_gpu()
     import torch

@@ -191,8 +191,9 @@ def test_batch_of_uneven_clusters(orc, precision):
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_smoother_tuning_and_forced_choices(precision):
     """The first solve measures the smoother of every level the cycle smooths with separate
-    launches; whatever the table says (in-place half sweeps, fused register-column passes,
-    fused two-sweep z-slab passes) the converged solution is bitwise the same."""
+    launches; whatever the table says (in-place half sweeps over the flat index or one block per
+    row, fused register-column passes, fused two-sweep z-slab passes) the converged solution is
+    bitwise the same."""
     B = need_gpu()
     import torch
     prec = B.LASTO_PREC_MIXED if precision == "mixed" else B.LASTO_PREC_FP64
@@ -208,7 +209,8 @@ def test_smoother_tuning_and_forced_choices(precision):
     shapes = sorted({tuple(int(v) for v in r[:3]) for r in rows if int(r[3]) == elem})
     assert (65, 65, 65) in shapes and (33, 33, 33) in shapes
     col_ty = 14 if elem == 4 else 6
-    forms = {"inplace": "0 256 0 0 0 0", "column": f"1 256 62 {col_ty} 32 1", "slab": "1 256 64 16 32 2"}
+    forms = {"inplace": "0 256 0 0 0 0", "rows": "0 0 0 0 0 0", "column": f"1 256 62 {col_ty} 32 1",
+             "slab": "1 256 64 16 32 2"}
     out = {}
     for name, choice in forms.items():
         solver = B.Poisson(n_max=65, max_atoms=13, precision=prec)
@@ -220,8 +222,8 @@ def test_smoother_tuning_and_forced_choices(precision):
         out[name] = (v.clone(), s.cycles)
         assert all(line.split()[4:10] == choice.split() for line in solver.tune_table().strip().splitlines()
                    if int(line.split()[3]) == elem and tuple(int(x) for x in line.split()[:3]) in shapes)
-    assert torch.equal(out["inplace"][0], out["column"][0]) and torch.equal(out["inplace"][0], out["slab"][0])
-    assert out["inplace"][1] == out["column"][1] == out["slab"][1]
+    for name in ("rows", "column", "slab"):
+        assert torch.equal(out["inplace"][0], out[name][0]) and out["inplace"][1] == out[name][1], name
     assert torch.equal(out["inplace"][0], v_auto)
 
 
