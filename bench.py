@@ -364,6 +364,11 @@ def main():
     if not args.no_hs:
         hs = interstitial_hs(B, synth, flush, stream, dev)
 
+    # ---------------- the inner Dirichlet problem, exact faces and raw-density deposit
+    rows = None
+    if not args.no_hs:
+        rows = next_rows(B, synth, flush, stream, dev)
+
     # ---------------- roofline of the dominant kernel (FP32 red-black half sweep)
     roof = smoother_roofline(B, stream, flush, dev)
     roof["deposit_fp32pair_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 1)["ms"]
@@ -395,6 +400,7 @@ def main():
             "batch64_uneven": b64,
             "pd561_graded385": pd561,
             "interstitial_hs": hs,
+            "inner_faces_raw": rows,
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": r_chosen["launches"],
@@ -581,6 +587,55 @@ def interstitial_hs(B, synth, flush, stream, dev):
                                  "simt": alg_flops / (out["simt"]["ms_contract"] / 1e3) / 1e12}
     out["tensor_over_simt"] = out["simt"]["ms"] / out["tensor"]["ms"]
     return out
+
+
+def next_rows(B, synth, flush, stream, dev):
+    """The rows built beyond the Poisson step, each timed alone with CUDA events (median of 5,
+    L2 flushed) on the Pd55 graded 129^3 workload: the inner Dirichlet problem (Eq. 3.4-3.7:
+    rho_LM on the 429-point logarithmic mesh of every sphere, then the radial solve), the
+    exact-superposition faces (f2) and the raw-density deposit (Eq. 3.1, f4; its inputs are the
+    model's deposit and the GPU's rho_00 tables, which only set the values, not the cost)."""
+    import torch
+    cl = synth.pd55_graded129()
+    dc = B.DeviceCluster(cl)
+    na, n_rad, nq = cl.n_atoms, 429, 16 * 32
+
+    def median_ms(fn):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(5):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    rho, _ = B.lasto_op_sphere_density(dc, n_rad=n_rad)
+    vR = torch.zeros((na, 25), dtype=torch.float64, device=dev)
+    t_sd = median_ms(lambda: B.lasto_op_sphere_density(dc, n_rad=n_rad))
+    t_in = median_ms(lambda: B.lasto_op_inner_solve(dc.R, dc.Z, rho, vR))
+    u = torch.zeros((cl.n,) * 3, dtype=torch.float64, device=dev)
+    t_bx = median_ms(lambda: B.lasto_op_boundary_exact(dc, u))
+    b, _, _ = B.lasto_op_deposit(dc, precision=B.LASTO_PREC_MIXED)
+    rc = B.RawCluster(cl.pos, cl.Z, cl.R, dc.x, dc.y, dc.z, cl.centre, (b / (4 * 3.141592653589793)).reshape(-1),
+                      rho[:, 0, :].contiguous())
+    t_raw = median_ms(lambda: B.lasto_op_raw_deposit(rc))
+    t_dep = median_ms(lambda: B.lasto_op_deposit(dc, precision=B.LASTO_PREC_MIXED))
+    faces = 6 * cl.n * cl.n
+    return {
+        "workload": cl.name,
+        "inner_sphere_density": {"ms": t_sd, "unit": "Gpair/s",
+                                 "achieved": na * n_rad * nq * na / (t_sd / 1e3) / 1e9,
+                                 "work": f"{na} spheres x {n_rad} radii x {nq} quadrature points x {na} atoms"},
+        "inner_solve": {"ms": t_in, "points": na * 25 * n_rad},
+        "boundary_exact": {"ms": t_bx, "unit": "Gpair/s", "achieved": faces * na / (t_bx / 1e3) / 1e9,
+                           "work": f"{faces} face nodes x {na} atoms"},
+        "raw_deposit": {"ms": t_raw, "model_deposit_ms": t_dep},
+    }
 
 
 def smoother_roofline(B, stream, flush, dev):
