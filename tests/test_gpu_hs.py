@@ -168,3 +168,22 @@ def test_no_interstitial_nodes(orc, mode):
     Sr, Hr = orc.interstitial_hs(pos, R, x, y, z, V, PD)
     assert not np.any(Sr) and not np.any(Hr)
     assert not np.any(host(S)) and not np.any(host(H))
+
+
+@pytest.mark.parametrize("mode", MODES[1:])
+def test_non_cubic_box(orc, mode):
+    """Axes of different lengths (33, 29, 25 nodes; every other coordinate dropped where
+    needed) keep the node indexing right."""
+    B = need_gpu()
+    cl = synth.pd2_dimer(n=33)
+    x, y, z = _axes(orc, cl)
+    y = np.ascontiguousarray(np.concatenate([y[:14], y[18:]]))
+    z = np.ascontiguousarray(np.concatenate([z[:12], z[20:]]))
+    assert (len(x), len(y), len(z)) == (33, 29, 25)
+    V = _potential(cl, x, y, z, 8)
+    S, H = B.lasto_op_interstitial_hs(dev(x), dev(y), dev(z), dev(cl.pos), dev(cl.R), dev(V), basis=PD, mode=mode)
+    Sr, Hr = orc.interstitial_hs(cl.pos, cl.R, x, y, z, V, PD)
+    diag = np.sqrt((x[-1] - x[0]) ** 2 + (y[-1] - y[0]) ** 2 + (z[-1] - z[0]) ** 2)
+    sS, sH = _scale(Sr, V[_outside(cl, x, y, z)], PD, cl.R, diag)
+    assert np.all(np.abs(host(S) - Sr) <= 1e-5 * sS)
+    assert np.all(np.abs(host(H) - Hr) <= 1e-5 * sH)
