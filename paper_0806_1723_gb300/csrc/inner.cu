@@ -10,7 +10,12 @@
 //   V_LM(r) = V_LM(R) (r/R)^L - 4pi/(2L+1) [ r^-(L+1) I1(r) + r^L I2(r) - r^L R^-(2L+1) I1(R) ]
 //           + delta_L0 sqrt(4pi) Z (1/r - 1/R),
 // I1(r) = int_0^r rho_LM r'^(L+2) dr', I2(r) = int_r^R rho_LM r'^(1-L) dr', integrated in
-// x = ln r with the cubic through the four nearest samples per interval.
+// x = ln r with the cubic through the four nearest samples per interval.  The density
+// projection runs its Slater sums in FP32 pairs; the radial solve is one block per (atom, LM)
+// with the interval integrals summed as block-wide prefix (I1) and suffix (I2) scans.
+#include <cmath>
+
+#include "df.cuh"
 #include "internal.cuh"
 
 namespace lasto {
@@ -19,40 +24,93 @@ namespace {
 
 constexpr int SD_NT = 128;
 constexpr double SD_EXP_CUT = 40.0;
-constexpr double SD_FAR = 20.0;   // Slater terms beyond zeta r = 20 in plain FP32
+constexpr float SD_FAR = 20.0f;   // Slater terms beyond zeta r = 20 in plain FP32
+
+using dfa::df;
+
+struct SdExp {
+    float h[64], l[64];   // 2^(-j/64) as double-floats
+};
 
 // rho_LM(r_j) of atom a = blockIdx.y at radius j = blockIdx.x.  rec: sphere records
 // (position, radius, Slater weights and exponents per atom); quad [nq][28]: unit vector and
-// w_q S_lm(u_q).
+// w_q S_lm(u_q).  The Slater sum at each quadrature point runs in FP32 pairs (about 44 bits:
+// Tang's table-driven exp), with positions taken relative to the sphere's centre so that the
+// pairs stay small; terms beyond zeta r = 20 (below e^-20 of their weight) in plain FP32.  The
+// projection sums over the quadrature points are FP64.
 __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* __restrict__ rec,
                                                           const double* __restrict__ clm,
                                                           const double* __restrict__ quad, int nq, int n_rad,
-                                                          double r_min, double* __restrict__ out)
+                                                          double r_min, SdExp tab, double* __restrict__ out)
 {
+    extern __shared__ float sd_sm[];   // per atom: D = pos_t - pos_a (3 pairs), W (3 pairs)
     __shared__ double red[NLM][SD_NT];
     const int a = blockIdx.y, j = blockIdx.x, tid = threadIdx.x;
     const double* ra = rec + (size_t)SPHERE_REC_DOUBLES * a;
     const double Ra = ra[3];
     const double dx = log(Ra / r_min) / (n_rad - 1);
     const double r = (j == n_rad - 1) ? Ra : Ra * exp((j - (n_rad - 1)) * dx);
+    for (int t = tid; t < na; t += SD_NT) {
+        const double* rt = rec + (size_t)SPHERE_REC_DOUBLES * t;
+        float* o = sd_sm + 12 * t;
+        for (int c = 0; c < 3; c++) {
+            const df D = dfa::from_double(rt[c] - ra[c]);
+            o[2 * c] = D.h;
+            o[2 * c + 1] = D.l;
+            const df W = dfa::from_double(rt[4 + c]);
+            o[6 + 2 * c] = W.h;
+            o[7 + 2 * c] = W.l;
+        }
+    }
+    __syncthreads();
+    // the exponents are the same on every atom (checked by the sphere kernel)
+    df zt[3];
+    float zmin = 1e30f;
+    for (int c = 0; c < 3; c++) {
+        zt[c] = dfa::from_double(ra[7 + c]);
+        zmin = fminf(zmin, zt[c].h);
+    }
+    const float cut = (float)SD_EXP_CUT / zmin, cut2 = cut * cut * (1.0f + 1e-5f);
+    const float far = SD_FAR / zmin, far2 = far * far * (1.0f + 1e-4f);
     const double y00 = 0.28209479177387814;   // S_00 = 1 / (2 sqrt(pi)); quad[3] = w_q S_00
     double acc[NLM];
 #pragma unroll
     for (int lm = 0; lm < NLM; lm++) acc[lm] = 0.0;
     for (int q = tid; q < nq; q += SD_NT) {
         const double* Q = quad + 28 * (size_t)q;
-        const double px = ra[0] + r * Q[0], py = ra[1] + r * Q[1], pz = ra[2] + r * Q[2];
-        double rho = 0.0;
+        const df px = dfa::from_double(r * Q[0]), py = dfa::from_double(r * Q[1]), pz = dfa::from_double(r * Q[2]);
+        df rho = {0.0f, 0.0f};
         for (int t = 0; t < na; t++) {
-            const double* rt = rec + (size_t)SPHERE_REC_DOUBLES * t;
-            const double ex = px - rt[0], ey = py - rt[1], ez = pz - rt[2];
-            const double d = sqrt(ex * ex + ey * ey + ez * ez);
-            for (int k = 0; k < 3; k++) {
-                const double e = rt[7 + k] * d;
-                if (e >= SD_EXP_CUT) continue;
-                rho += (e > SD_FAR) ? (double)((float)rt[4 + k] * expf(-(float)e)) : rt[4 + k] * exp(-e);
+            const float* o = sd_sm + 12 * t;
+            const float fx = (px.h - o[0]) + (px.l - o[1]), fy = (py.h - o[2]) + (py.l - o[3]);
+            const float fz = (pz.h - o[4]) + (pz.l - o[5]);
+            const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+            if (r2f > cut2) continue;
+            if (r2f > far2) {
+                const float rf = sqrtf(r2f);
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const float e = zt[c].h * rf;
+                    if (e < (float)SD_EXP_CUT) rho = dfa::add_f(rho, o[6 + 2 * c] * expf(-e));
+                }
+                continue;
+            }
+            const df ex = dfa::add(px, df{-o[0], -o[1]});
+            const df ey = dfa::add(py, df{-o[2], -o[3]});
+            const df ez = dfa::add(pz, df{-o[4], -o[5]});
+            const df d2 = dfa::add(dfa::add(dfa::sqr(ex), dfa::sqr(ey)), dfa::sqr(ez));
+            const df d = dfa::sqrt_df(d2);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const df e = dfa::mul(d, zt[c]);
+                if (e.h >= (float)SD_EXP_CUT) continue;
+                if (e.h > SD_FAR)
+                    rho = dfa::add_f(rho, o[6 + 2 * c] * expf(-e.h));
+                else
+                    rho = dfa::add(rho, dfa::mul(df{o[6 + 2 * c], o[7 + 2 * c]}, dfa::exp_neg(e, tab.h, tab.l)));
             }
         }
+        double rhod = dfa::to_double(rho);
         // own nonspherical part: zeta_1^3/(8 pi) e^{-zeta_1 r} (1 - r^2/R^2)^2 sum c_lm (r/R)^l y_lm
         if (r < Ra) {
             const double z1 = ra[7], w = Q[3] / y00, s = r / Ra, tt = 1.0 - s * s;
@@ -61,10 +119,10 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
                 if (lm == 4 || lm == 9 || lm == 16) sl *= s;
                 ang += clm[24 * (size_t)a + lm - 1] * sl * (Q[3 + lm] / w);
             }
-            rho += z1 * z1 * z1 / (8.0 * 3.14159265358979323846) * exp(-z1 * r) * tt * tt * ang;
+            rhod += z1 * z1 * z1 / (8.0 * 3.14159265358979323846) * exp(-z1 * r) * tt * tt * ang;
         }
 #pragma unroll
-        for (int lm = 0; lm < NLM; lm++) acc[lm] = fma(Q[3 + lm], rho, acc[lm]);
+        for (int lm = 0; lm < NLM; lm++) acc[lm] = fma(Q[3 + lm], rhod, acc[lm]);
     }
 #pragma unroll
     for (int lm = 0; lm < NLM; lm++) red[lm][tid] = acc[lm];
@@ -85,43 +143,106 @@ __device__ __forceinline__ double seg_integral(double g0, double g1, double g2, 
     return h / 24.0 * (-g0 + 13.0 * g1 + 13.0 * g2 - g3);
 }
 
-// One thread per (atom, lm).  The forward integral I1 is parked in v, then the backward pass
-// forms I2 and overwrites v with V_LM.
-__global__ void k_inner_solve(int na, const double* __restrict__ R, const double* __restrict__ Z, int n,
-                              double r_min, const double* __restrict__ rho_lm, const double* __restrict__ vR,
-                              double* __restrict__ v)
+constexpr int IS_NT = 128;
+constexpr int IS_MAX = 4096;   // radial points per sphere
+
+// inclusive scan of one double per thread over the block (warp shuffles, then the warps' totals)
+__device__ __forceinline__ double block_incl_scan(double v, double* wsum)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= na * NLM) return;
-    const int a = t / NLM, lm = t % NLM, L = l_of_lm(lm);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    __syncthreads();
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    for (int q = 0; q < w; q++) v += wsum[q];
+    return v;
+}
+
+// One block per (atom, lm).  The integrands at the mesh points, the cubic-rule integral over
+// each interval, then I1 as a prefix sum and I2 as a suffix sum of the intervals (each thread
+// a contiguous run of intervals, the runs' totals scanned across the block), then V_LM.
+__global__ void __launch_bounds__(IS_NT) k_inner_solve(int na, const double* __restrict__ R,
+                                                       const double* __restrict__ Z, int n, double r_min,
+                                                       const double* __restrict__ rho_lm,
+                                                       const double* __restrict__ vR, double* __restrict__ v)
+{
+    extern __shared__ double is_sm[];   // x[n], g1[n], g2[n], seg1[n], seg2[n]
+    __shared__ double wsum[IS_NT / 32];
+    double* xs = is_sm;
+    double* g1 = xs + n;
+    double* g2 = g1 + n;
+    double* s1 = g2 + n;
+    double* s2 = s1 + n;
+    const int t = blockIdx.x, a = t / NLM, lm = t % NLM, L = l_of_lm(lm);
     const double Ra = R[a];
     const double h = log(Ra / r_min) / (n - 1);
     const double* rho = rho_lm + (size_t)t * n;
     double* out = v + (size_t)t * n;
-    auto rr = [&](int j) { return j == n - 1 ? Ra : Ra * exp((j - (n - 1)) * h); };
-    auto g1 = [&](int j) { const double x = rr(j); return rho[j] * pow(x, L + 2) * x; };
-    auto g2 = [&](int j) { const double x = rr(j); return rho[j] * pow(x, 1 - L) * x; };
-    auto seg = [&](auto g, int j) {
-        if (j == 0) return seg_integral(g(0), g(1), g(2), g(3), 0, h);
-        if (j == n - 2) return seg_integral(g(n - 4), g(n - 3), g(n - 2), g(n - 1), 2, h);
-        return seg_integral(g(j - 1), g(j), g(j + 1), g(j + 2), 1, h);
-    };
-    double I1 = rho[0] * pow(rr(0), L + 3) / (L + 3);
-    out[0] = I1;
-    for (int j = 0; j + 1 < n; j++) {
-        I1 += seg(g1, j);
-        out[j + 1] = I1;
+    for (int j = threadIdx.x; j < n; j += IS_NT) {
+        const double x = j == n - 1 ? Ra : Ra * exp((j - (n - 1)) * h);
+        double xl = 1.0;
+        for (int e = 0; e < L; e++) xl *= x;
+        xs[j] = x;
+        g1[j] = rho[j] * xl * x * x * x;   // rho r^(L+2) dr = rho r^(L+3) d(ln r)
+        g2[j] = rho[j] * x * x / xl;       // rho r^(1-L) dr = rho r^(2-L) d(ln r)
     }
-    const double I1R = I1, vr = vR[(size_t)a * NLM + lm];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n - 1; j += IS_NT) {
+        const int b = j == 0 ? 0 : (j == n - 2 ? n - 4 : j - 1);
+        const int kind = j == 0 ? 0 : (j == n - 2 ? 2 : 1);
+        s1[j] = seg_integral(g1[b], g1[b + 1], g1[b + 2], g1[b + 3], kind, h);
+        s2[j] = seg_integral(g2[b], g2[b + 1], g2[b + 2], g2[b + 3], kind, h);
+    }
+    __syncthreads();
+    // contiguous runs of intervals per thread: [c0, c1)
+    const int m = n - 1, per = (m + IS_NT - 1) / IS_NT;
+    const int c0 = min(m, (int)threadIdx.x * per), c1 = min(m, c0 + per);
+    double run1 = 0.0, run2 = 0.0;
+    for (int j = c0; j < c1; j++) {
+        run1 += s1[j];
+        run2 += s2[j];
+    }
+    const double inc1 = block_incl_scan(run1, wsum);
+    __syncthreads();
+    const double inc2 = block_incl_scan(run2, wsum);
+    __syncthreads();
+    if (threadIdx.x == IS_NT - 1) {
+        wsum[0] = inc1;   // I1 over all intervals
+        wsum[1] = inc2;   // I2 over all intervals
+    }
+    __syncthreads();
+    const double tot1 = wsum[0], tot2 = wsum[1];
+    const double I1_0 = g1[0] / (L + 3);   // rho taken constant on [0, r_0]: rho_0 r_0^(L+3) / (L+3)
+    const double vr = vR[(size_t)a * NLM + lm];
     const double c = 4.0 * 3.14159265358979323846 / (2 * L + 1);
     const double sq4pi = 3.5449077018110318;
-    double I2 = 0.0;
-    for (int j = n - 1; j >= 0; j--) {
-        if (j < n - 1) I2 += seg(g2, j);
-        const double x = rr(j), rl = pow(x, L);
-        double val = vr * pow(x / Ra, L) - c * (out[j] / pow(x, L + 1) + rl * I2 - rl * I1R / pow(Ra, 2 * L + 1));
-        if (L == 0) val += sq4pi * Z[a] * (1.0 / x - 1.0 / Ra);
-        out[j] = val;
+    double RaL = 1.0;
+    for (int e = 0; e < L; e++) RaL *= Ra;
+    const double R2L1 = RaL * RaL * Ra;
+    const double I1R = I1_0 + tot1;
+    // points [c0, c1) of this thread's run, and the last point m with the run that ends there:
+    // I1 at point j = I1_0 + intervals [0, j), I2 = intervals [j, m)
+    if (c0 < c1) {
+        double p1 = inc1 - run1, p2 = tot2 - (inc2 - run2);
+        const int last = c1 == m ? m : c1 - 1;
+        for (int j = c0; j <= last; j++) {
+            if (j > c0) {
+                p1 += s1[j - 1];
+                p2 -= s2[j - 1];
+            }
+            const double x = xs[j];
+            double xl = 1.0;
+            for (int e = 0; e < L; e++) xl *= x;
+            const double I1 = I1_0 + p1;
+            const double I2 = j == m ? 0.0 : p2;
+            double val = vr * (xl / RaL) - c * (I1 / (xl * x) + xl * I2 - xl * I1R / R2L1);
+            if (L == 0) val += sq4pi * Z[a] * (1.0 / x - 1.0 / Ra);
+            out[j] = val;
+        }
     }
 }
 
@@ -130,16 +251,30 @@ __global__ void k_inner_solve(int na, const double* __restrict__ R, const double
 cudaError_t launch_sphere_density(int na, const double* rec, const double* clm, const double* quad, int nq,
                                   int n_rad, double r_min, double* out, cudaStream_t s)
 {
-    k_sphere_density<<<dim3((unsigned)n_rad, (unsigned)na), SD_NT, 0, s>>>(na, rec, clm, quad, nq, n_rad, r_min,
-                                                                           out);
+    SdExp tab;
+    for (int q = 0; q < 64; q++) {
+        const double v = std::exp2(-q / 64.0);
+        tab.h[q] = (float)v;
+        tab.l[q] = (float)(v - (double)tab.h[q]);
+    }
+    const size_t smem = sizeof(float) * 12 * (size_t)na;
+    if (smem > 160 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_sphere_density, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    k_sphere_density<<<dim3((unsigned)n_rad, (unsigned)na), SD_NT, smem, s>>>(na, rec, clm, quad, nq, n_rad, r_min,
+                                                                              tab, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_inner_solve(int na, const double* R, const double* Z, int n_rad, double r_min,
                                const double* rho_lm, const double* vR, double* v, cudaStream_t s)
 {
-    const int total = na * NLM;
-    k_inner_solve<<<(total + 127) / 128, 128, 0, s>>>(na, R, Z, n_rad, r_min, rho_lm, vR, v);
+    if (n_rad > IS_MAX) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * 5 * (size_t)n_rad;
+    cudaError_t e = cudaFuncSetAttribute(k_inner_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * 5 * IS_MAX));
+    if (e != cudaSuccess) return e;
+    k_inner_solve<<<(unsigned)(na * NLM), IS_NT, smem, s>>>(na, R, Z, n_rad, r_min, rho_lm, vR, v);
     return cudaGetLastError();
 }
 
