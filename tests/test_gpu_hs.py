@@ -121,18 +121,21 @@ def test_potential_shift_on_the_gpu(orc):
     assert np.all(np.abs(H1 - H0 - 0.75 * S0) <= 2e-5 * sH)
 
 
-def test_full_size_pd55_sub_basis(orc):
+@pytest.mark.parametrize("sub,locs", [((2, 5), (10, 15, 16, 17)), ((0,), (0, 1, 2, 3, 4))],
+                         ids=["5s+6p", "4d"])
+def test_full_size_pd55_sub_basis(orc, sub, locs):
     """Pd55 on the graded 129^3 mesh with the whole Table 1 basis (1375 functions) on the GPU;
-    the entries of the 5s and 6p functions checked against the oracle run on that sub-basis."""
+    the entries of a sub-basis (5s and 6p; 4d) checked against the oracle run on that
+    sub-basis."""
     B = need_gpu()
     cl = synth.pd55_graded129()
     x, y, z = _axes(orc, cl)
     V = _potential(cl, x, y, z, 5)
     S, H = B.lasto_op_interstitial_hs(dev(x), dev(y), dev(z), dev(cl.pos), dev(cl.R), dev(V), basis=PD)
-    sub = [PD[2], PD[5]]
+    sub = [PD[q] for q in sub]
     Sr, Hr = orc.interstitial_hs(cl.pos, cl.R, x, y, z, V, sub)
     # within an atom's 25 functions: 4d 0-4, 5d 5-9, 5s 10, 5p 11-13, 6s 14, 6p 15-17, 4f 18-24
-    pick = np.array([a * 25 + loc for a in range(cl.n_atoms) for loc in (10, 15, 16, 17)])
+    pick = np.array([a * 25 + loc for a in range(cl.n_atoms) for loc in locs])
     S, H = host(S)[np.ix_(pick, pick)], host(H)[np.ix_(pick, pick)]
     diag = np.sqrt(3) * 2 * cl.half_width
     sS, sH = _scale(Sr, V[_outside(cl, x, y, z)], sub, cl.R, diag)

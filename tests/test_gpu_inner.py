@@ -10,7 +10,8 @@ from gpu_common import dev, host, need_gpu
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("make", [lambda: synth.pd13_small(n=33), lambda: synth.pd2_dimer(n=33)])
+@pytest.mark.parametrize("make", [lambda: synth.pd13_small(n=33), lambda: synth.pd2_dimer(n=33),
+                                  lambda: synth.pd55_graded129()], ids=["pd13", "pd2", "pd55-full"])
 def test_sphere_density(orc, make):
     B = need_gpu()
     cl = make()
@@ -19,7 +20,8 @@ def test_sphere_density(orc, make):
     ref = orc.sphere_density(cl, n_rad=429)
     got = host(rho)
     assert int(host(status)[0]) == 0
-    # the far Slater tails (zeta r > 20) are summed in FP32: ~1e-16 of the density scale
+    # FP32-pair Slater sums (~44 bits), the far tails (zeta r > 20) in FP32: ~1e-13 of the
+    # density scale
     assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
 
 
