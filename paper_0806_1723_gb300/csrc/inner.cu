@@ -23,6 +23,7 @@ namespace lasto {
 namespace {
 
 constexpr int SD_NT = 128;
+constexpr int SD_MAXQ = 2048;      // quadrature points per sphere
 constexpr double SD_EXP_CUT = 40.0;
 constexpr float SD_FAR = 20.0f;   // Slater terms beyond zeta r = 20 in plain FP32
 
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
                                                           double r_min, SdExp tab, double* __restrict__ out)
 {
     extern __shared__ float sd_sm[];   // per atom: D = pos_t - pos_a (3 pairs), W (3 pairs)
-    __shared__ double red[NLM][SD_NT];
+    __shared__ double rq[SD_MAXQ];     // the density at the quadrature points
     const int a = blockIdx.y, j = blockIdx.x, tid = threadIdx.x;
     const double* ra = rec + (size_t)SPHERE_REC_DOUBLES * a;
     const double Ra = ra[3];
@@ -73,9 +74,6 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
     const float cut = (float)SD_EXP_CUT / zmin, cut2 = cut * cut * (1.0f + 1e-5f);
     const float far = SD_FAR / zmin, far2 = far * far * (1.0f + 1e-4f);
     const double y00 = 0.28209479177387814;   // S_00 = 1 / (2 sqrt(pi)); quad[3] = w_q S_00
-    double acc[NLM];
-#pragma unroll
-    for (int lm = 0; lm < NLM; lm++) acc[lm] = 0.0;
     for (int q = tid; q < nq; q += SD_NT) {
         const double* Q = quad + 28 * (size_t)q;
         const df px = dfa::from_double(r * Q[0]), py = dfa::from_double(r * Q[1]), pz = dfa::from_double(r * Q[2]);
@@ -121,18 +119,18 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
             }
             rhod += z1 * z1 * z1 / (8.0 * 3.14159265358979323846) * exp(-z1 * r) * tt * tt * ang;
         }
-#pragma unroll
-        for (int lm = 0; lm < NLM; lm++) acc[lm] = fma(Q[3 + lm], rhod, acc[lm]);
+        rq[q] = rhod;
     }
-#pragma unroll
-    for (int lm = 0; lm < NLM; lm++) red[lm][tid] = acc[lm];
     __syncthreads();
-    for (int st = SD_NT / 2; st > 0; st >>= 1) {
-        if (tid < st)
-            for (int lm = 0; lm < NLM; lm++) red[lm][tid] += red[lm][tid + st];
-        __syncthreads();
+    // the projection: warp w takes lm = w, w + 4, ...; lanes split the quadrature points
+    const int lane = tid & 31, w = tid >> 5;
+    for (int lm = w; lm < NLM; lm += SD_NT / 32) {
+        double acc = 0.0;
+        for (int q = lane; q < nq; q += 32) acc = fma(quad[28 * (size_t)q + 3 + lm], rq[q], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[((size_t)a * NLM + lm) * n_rad + j] = acc;
     }
-    if (tid < NLM) out[((size_t)a * NLM + tid) * n_rad + j] = red[tid][0];
 }
 
 __device__ __forceinline__ double seg_integral(double g0, double g1, double g2, double g3, int kind, double h)
@@ -258,7 +256,7 @@ cudaError_t launch_sphere_density(int na, const double* rec, const double* clm, 
         tab.l[q] = (float)(v - (double)tab.h[q]);
     }
     const size_t smem = sizeof(float) * 12 * (size_t)na;
-    if (smem > 160 * 1024) return cudaErrorInvalidValue;
+    if (smem > 160 * 1024 || nq > SD_MAXQ) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_sphere_density, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     if (e != cudaSuccess) return e;
     k_sphere_density<<<dim3((unsigned)n_rad, (unsigned)na), SD_NT, smem, s>>>(na, rec, clm, quad, nq, n_rad, r_min,
