@@ -478,6 +478,9 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     }
     const float cut = EXP_CUT / zmin;
     const float cut2 = cut * cut * (1.0f + 1e-5f);
+    bool twice[3];   // zeta_q exactly twice zeta_0 (both parts of the double-float)
+#pragma unroll
+    for (int q = 0; q < 3; q++) twice[q] = q > 0 && zt[q].h == 2.0f * zt[0].h && zt[q].l == 2.0f * zt[0].l;
     // beyond zeta_min r = FAR_T every Slater term is below e^-20 of its weight: plain FP32
     // (relative error ~1e-7 of terms that small is ~1e-16 of the node's density scale)
     const float far = FAR_T / zmin;
@@ -517,14 +520,23 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
             }
         }
         const df r = dfa::sqrt_df(r2);
+        df e0 = {0.0f, 0.0f};   // e^{-zeta_0 r} when it was taken in double-float
+        bool have0 = false;
 #pragma unroll
         for (int q = 0; q < 3; q++) {
             const df tq = dfa::mul(r, zt[q]);
             if (tq.h >= EXP_CUT) continue;
-            if (tq.h > FAR_T)
+            if (tq.h > FAR_T) {
                 s = dfa::add_f(s, o[6 + 2 * q] * expf(-tq.h));
-            else
-                s = dfa::add(s, dfa::mul(df{o[6 + 2 * q], o[7 + 2 * q]}, dfa::exp_neg(tq, th, tl)));
+            } else {
+                // zeta_q = 2 zeta_0 (as in the density model's 1.5, 3.0): e^{-zeta_q r} = (e^{-zeta_0 r})^2
+                const df eq = (q > 0 && twice[q] && have0) ? dfa::sqr(e0) : dfa::exp_neg(tq, th, tl);
+                if (q == 0) {
+                    e0 = eq;
+                    have0 = true;
+                }
+                s = dfa::add(s, dfa::mul(df{o[6 + 2 * q], o[7 + 2 * q]}, eq));
+            }
         }
     }
     if (own >= 0) {

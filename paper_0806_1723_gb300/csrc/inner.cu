@@ -72,6 +72,9 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
         zmin = fminf(zmin, zt[c].h);
     }
     const float cut = (float)SD_EXP_CUT / zmin, cut2 = cut * cut * (1.0f + 1e-5f);
+    bool twice[3];   // zeta_c exactly twice zeta_0
+#pragma unroll
+    for (int c = 0; c < 3; c++) twice[c] = c > 0 && zt[c].h == 2.0f * zt[0].h && zt[c].l == 2.0f * zt[0].l;
     const float far = SD_FAR / zmin, far2 = far * far * (1.0f + 1e-4f);
     const double y00 = 0.28209479177387814;   // S_00 = 1 / (2 sqrt(pi)); quad[3] = w_q S_00
     for (int q = tid; q < nq; q += SD_NT) {
@@ -98,14 +101,23 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
             const df ez = dfa::add(pz, df{-o[4], -o[5]});
             const df d2 = dfa::add(dfa::add(dfa::sqr(ex), dfa::sqr(ey)), dfa::sqr(ez));
             const df d = dfa::sqrt_df(d2);
+            df e0 = {0.0f, 0.0f};
+            bool have0 = false;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const df e = dfa::mul(d, zt[c]);
                 if (e.h >= (float)SD_EXP_CUT) continue;
-                if (e.h > SD_FAR)
+                if (e.h > SD_FAR) {
                     rho = dfa::add_f(rho, o[6 + 2 * c] * expf(-e.h));
-                else
-                    rho = dfa::add(rho, dfa::mul(df{o[6 + 2 * c], o[7 + 2 * c]}, dfa::exp_neg(e, tab.h, tab.l)));
+                } else {
+                    // zeta_c = 2 zeta_0: e^{-zeta_c d} = (e^{-zeta_0 d})^2
+                    const df ec = (c > 0 && twice[c] && have0) ? dfa::sqr(e0) : dfa::exp_neg(e, tab.h, tab.l);
+                    if (c == 0) {
+                        e0 = ec;
+                        have0 = true;
+                    }
+                    rho = dfa::add(rho, dfa::mul(df{o[6 + 2 * c], o[7 + 2 * c]}, ec));
+                }
             }
         }
         double rhod = dfa::to_double(rho);

@@ -248,23 +248,29 @@ cudaError_t launch_inv_diag(const LevelStore& lv, cudaStream_t s)
 // S = V^{1/2} T V^{-1/2} (V = dual lengths), whose off-diagonal is sqrt(cp_i cm_{i+1}).
 // Cyclic Jacobi rotations (Golub & Van Loan, symmetric Schur decomposition) give
 // S = Q diag(lam) Q^T, so A^{-1} = (x) V^{-1/2} Q  diag(1/(lx+ly+lz))  (x) Q^T V^{1/2}.
-__global__ void k_coarse_eig(AxisStore ax0, AxisStore ax1, AxisStore ax2, CoarseEig* out)
+// One warp per axis; a rotation's row and column updates run across the lanes (lane k owns
+// element k), each element computed exactly as in the sequential sweep.
+__global__ void __launch_bounds__(96) k_coarse_eig(AxisStore ax0, AxisStore ax1, AxisStore ax2, CoarseEig* out)
 {
-    const int d = threadIdx.x;
-    if (d >= 3) return;
+    constexpr int MM = MAX_COARSE - 2;
+    __shared__ double Ssh[3][MM][MM], Qsh[3][MM][MM];
+    const int d = threadIdx.x >> 5, k = threadIdx.x & 31;
     const AxisStore& A = d == 0 ? ax0 : d == 1 ? ax1 : ax2;
     const int m = A.n - 2;
-    constexpr int MM = MAX_COARSE - 2;
-    double S[MM][MM], Q[MM][MM];
-    for (int i = 0; i < m; i++)
+    double(*S)[MM] = Ssh[d];
+    double(*Q)[MM] = Qsh[d];
+    if (k < m) {
         for (int j = 0; j < m; j++) {
-            S[i][j] = 0.0;
-            Q[i][j] = (i == j) ? 1.0 : 0.0;
+            S[k][j] = 0.0;
+            Q[k][j] = (k == j) ? 1.0 : 0.0;
         }
-    for (int i = 0; i < m; i++) {
-        S[i][i] = -A.dg[i + 1];
-        if (i + 1 < m) S[i][i + 1] = S[i + 1][i] = sqrt(A.cp[i + 1] * A.cm[i + 2]);
     }
+    __syncwarp();
+    if (k < m) {
+        S[k][k] = -A.dg[k + 1];
+        if (k + 1 < m) S[k][k + 1] = S[k + 1][k] = sqrt(A.cp[k + 1] * A.cm[k + 2]);
+    }
+    __syncwarp();
     int ok = 0;
     for (int sweep = 0; sweep < 60; sweep++) {
         double off = 0.0, dia = 0.0;
@@ -278,42 +284,46 @@ __global__ void k_coarse_eig(AxisStore ax0, AxisStore ax1, AxisStore ax2, Coarse
         }
         for (int p = 0; p < m; p++)
             for (int q = p + 1; q < m; q++) {
-                if (S[p][q] == 0.0) continue;
-                const double tau = (S[q][q] - S[p][p]) / (2.0 * S[p][q]);
+                const double spq = S[p][q];
+                if (spq == 0.0) continue;
+                const double tau = (S[q][q] - S[p][p]) / (2.0 * spq);
                 const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                 const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                for (int k = 0; k < m; k++) {
+                __syncwarp();
+                if (k < m) {
                     const double kp = S[k][p], kq = S[k][q];
                     S[k][p] = c * kp - s * kq;
                     S[k][q] = s * kp + c * kq;
                 }
-                for (int k = 0; k < m; k++) {
+                __syncwarp();
+                if (k < m) {
                     const double pk = S[p][k], qk = S[q][k];
                     S[p][k] = c * pk - s * qk;
                     S[q][k] = s * pk + c * qk;
+                    const double qp = Q[k][p], qq = Q[k][q];
+                    Q[k][p] = c * qp - s * qq;
+                    Q[k][q] = s * qp + c * qq;
                 }
-                for (int k = 0; k < m; k++) {
-                    const double kp = Q[k][p], kq = Q[k][q];
-                    Q[k][p] = c * kp - s * kq;
-                    Q[k][q] = s * kp + c * kq;
-                }
+                __syncwarp();
             }
     }
-    out->m[d] = m;
+    if (k == 0) {
+        out->m[d] = m;
+        out->ok[d] = ok;
+    }
     for (int p = 0; p < m; p++) {
-        out->lam[d][p] = S[p][p];
-        for (int i = 0; i < m; i++) {
-            const double sv = sqrt(A.dual[i + 1]);
-            out->F[d][p * m + i] = Q[i][p] * sv;
-            out->B[d][i * m + p] = Q[i][p] / sv;
+        if (k == 0) out->lam[d][p] = S[p][p];
+        if (k < m) {
+            const double sv = sqrt(A.dual[k + 1]);
+            out->F[d][p * m + k] = Q[k][p] * sv;
+            out->B[d][k * m + p] = Q[k][p] / sv;
         }
     }
-    out->ok[d] = ok;
 }
 
 cudaError_t launch_coarse_eig(const LevelStore& L, CoarseEig* eig, cudaStream_t s)
 {
-    k_coarse_eig<<<1, 32, 0, s>>>(L.ax[0], L.ax[1], L.ax[2], eig);
+    k_coarse_eig<<<1, 96, 0, s>>>(L.ax[0], L.ax[1], L.ax[2], eig);
     return cudaGetLastError();
 }
 
