@@ -90,7 +90,7 @@ def test_l4_basis_single_atom(orc, mode):
 
 
 def test_modes_agree(orc):
-    """The tensor-core (3 x TF32) and SIMT (FP32) contractions of the same tables agree to their
+    """The tensor-core (FP16 pairs) and SIMT (FP32) contractions of the same tables agree to their
     rounding."""
     B = need_gpu()
     cl = synth.pd13_small(n=33)
