@@ -44,10 +44,16 @@ FORM = ("learned initial guess (U-Net in the graph) + FP64 defect correction aro
 BATCH = 8
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per FP32 half sweep at 257^3 (mean of the red
-# and black launch) by launch shape of the current kernels; a shape without a capture reports
-# traffic null
-DRAM_BYTES_257 = {0: 153.2e6, 128: 153.4e6, 256: 153.3e6}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per half sweep at 257^3, one block per row, in
+# steady state (launches 5-8 of 4 sweeps, caches not flushed between launches, so each launch also
+# writes back what the one before left dirty in L2): mean of the four launches.  FP32: 130.2 MB
+# read + 67.6 MB written; FP64: 403.3 + 134.6 MB.  A launch shape without a capture reports null.
+DRAM_BYTES_257 = {0: 197.8e6}
+DRAM_BYTES_257_F64 = 537.8e6
+
+# FP64 FMA throughput of one GB300 (a DFMA chain over every SM, CUDA events: 1.19 TFLOP/s at
+# 1995 MHz); the copy and BF16 peaks come from the measured-peaks file
+FP64_TFLOPS = 1.19
 
 
 def parse():
@@ -71,6 +77,8 @@ def parse():
     p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
     p.add_argument("--threads", type=int, default=256,
                    help="launch shape of --profile smoother: threads per block, 0 = one block per row")
+    p.add_argument("--sweeps", type=int, default=1, help="red-black sweeps of --profile smoother")
+    p.add_argument("--fp64", action="store_true", help="--profile smoother in FP64 (the plain form's smoother)")
     p.add_argument("--direct", action="store_true",
                    help="launch the kernels directly instead of one CUDA graph per solve (for ncu)")
     return p.parse_args()
@@ -433,9 +441,10 @@ def run_profile(args, B):
     elif args.profile == "smoother":
         n = args.n
         axes = [B.lasto_mesh_axis(n, 0.0, 30.0, 0.12, 0.6, 6.0) for _ in range(3)]
-        u = torch.zeros(n ** 3, dtype=torch.float32, device="cuda")
-        b = torch.rand(n ** 3, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
-        B.lasto_op_smooth(*axes, u, b, sweeps=1, threads=args.threads)
+        dt = torch.float64 if args.fp64 else torch.float32
+        u = torch.zeros(n ** 3, dtype=dt, device="cuda")
+        b = torch.rand(n ** 3, dtype=dt, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+        B.lasto_op_smooth(*axes, u, b, sweeps=args.sweeps, threads=args.threads)
     else:
         cl = synth.pd561_graded385(n_densities=1)[0] if args.profile == "pd561" else synth.pd55_graded129()
         solver = B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, precision=B.LASTO_PREC_MIXED, launch=1)
@@ -684,7 +693,7 @@ def smoother_roofline(B, stream, flush, dev):
     del u, b
     torch.cuda.empty_cache()
     # DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of the chosen
-    # launch shape at 257^3 (mean of the red and the black launch), scaled by the node count
+    # launch shape at 257^3 (steady state), scaled by the node count
     traffic_257 = DRAM_BYTES_257.get(best)
     traffic = traffic_257 * (n / 257.0) ** 3 if traffic_257 else None
     name = "k_rbgs_row<float>, one block per row" if best == 0 else f"k_rbgs<float>, {best} threads per block"
@@ -692,7 +701,47 @@ def smoother_roofline(B, stream, flush, dev):
             "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
             "us_per_launch_by_shape": {("rows" if k == 0 else str(k)): v * 1e6 for k, v in per.items()},
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "plain_fp64": fp64_half_sweep(B, cl, axes, timed_fn=lambda uu, bb, sw, th: _timed_smooth(
+                B, axes, uu, bb, sw, th, flush, stream), peak=peak)}
+
+
+def _timed_smooth(B, axes, u, b, sweeps, threads, flush, stream):
+    import torch
+    ts = []
+    for _ in range(3):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.lasto_op_smooth(*axes, u, b, sweeps=sweeps, threads=threads)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def fp64_half_sweep(B, cl, axes, timed_fn, peak):
+    """The plain form's FP64 red-black half sweep at the same 385^3 mesh, one block per row.
+    Algorithmic bytes per launch: u read once (8 B per node), the colour's b and 1/diagonal read
+    and u written (24 B per updated node) = 20 B per node.  FP64 work per updated node: one
+    multiply, five FMAs, a subtraction and the multiply by 1/diagonal = 13 FLOP in 8 FP64
+    instructions; GB300's FP64 pipe (1.19 TFLOP/s of DFMA measured = 0.595 T instructions/s)
+    therefore caps this sweep near 0.45 of the HBM copy peak in algorithmic bytes."""
+    import torch
+    n = cl.n
+    u = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
+    b = torch.rand(n ** 3, dtype=torch.float64, device="cuda")
+    timed_fn(u, b, 1, 0)
+    t = (timed_fn(u, b, 3, 0) - timed_fn(u, b, 1, 0)) / 4 / 1e3
+    upd = (n - 2) ** 3 / 2
+    del u, b
+    torch.cuda.empty_cache()
+    bytes_per_launch = 20.0 * n ** 3
+    return {"kernel": "k_rbgs_row<double> (FP64 red-black half sweep, 385^3 graded)", "us_per_launch": t * 1e6,
+            "achieved_gbs": bytes_per_launch / t / 1e9, "hbm_frac": bytes_per_launch / t / 1e9 / peak,
+            "fp64_tflops": 13 * upd / t / 1e12, "fp64_peak_tflops": FP64_TFLOPS,
+            "fp64_issue_frac": 8 * upd / t / (FP64_TFLOPS / 2 * 1e12), "bytes_per_launch": bytes_per_launch,
+            "traffic": DRAM_BYTES_257_F64 * (n / 257.0) ** 3}
 
 
 def kernel_roofline(B, cl, dc, stream, flush, dev, precision=1):
