@@ -297,6 +297,8 @@ __global__ void k_deposit_df(DepArgs a);
 // per-atom fields staged in shared memory
 constexpr int SA = 14;  // x y z R^2 W0 W1 W2 A0 A1 A2 B0 B1 B2 R
 constexpr int DEP_NT = 256;
+constexpr int DT_X = 8, DT_Y = 8, DT_Z = 4;   // FP32-pair deposit: one 8 x 8 x 4 tile of nodes per block
+static_assert(DT_X * DT_Y * DT_Z == DEP_NT, "deposit tile = one block");
 constexpr double EXP_CUT = 40.0;   // e^{-40} * max W < 1e-14 absolute; skipped terms are below FP64 rounding of n_e
 constexpr float FAR_T = 20.0f;     // FP32-pair deposit: Slater terms with zeta r > 20 in plain FP32
 
@@ -412,9 +414,12 @@ cudaError_t launch_deposit(const lasto_cluster& cl, const double* rec, int preci
     const size_t N = (size_t)cl.n[0] * cl.n[1] * cl.n[2];
     const size_t smem = sizeof(double) * SA * (size_t)cl.n_atoms;
     if (precision == LASTO_PREC_MIXED) {
-        const size_t smf = sizeof(float) * (128 + SAF * (size_t)cl.n_atoms);
+        const size_t smf = sizeof(float) * (128 + SAF * (size_t)cl.n_atoms) + sizeof(int) * (size_t)cl.n_atoms;
         if (smf > 200 * 1024) return cudaErrorInvalidValue;
-        k_deposit_df<<<(unsigned)((N + DEP_NT - 1) / DEP_NT), DEP_NT, smf, s>>>(a);
+        const dim3 grid((unsigned)((cl.n[0] + DT_X - 1) / DT_X), (unsigned)((cl.n[1] + DT_Y - 1) / DT_Y),
+                        (unsigned)((cl.n[2] + DT_Z - 1) / DT_Z));
+        if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+        k_deposit_df<<<grid, DEP_NT, smf, s>>>(a);
         return cudaGetLastError();
     }
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
@@ -432,44 +437,28 @@ __device__ __forceinline__ bool inside_fp64(const DepArgs& a, double x, double y
     return fma(dx, dx, fma(dy, dy, dz * dz)) < r[RR] * r[RR];
 }
 
+// The FP32-pair deposit works on 8 x 8 x 4 tiles of nodes (a warp covers 8 x 4 x 1): a compact
+// footprint lets a whole warp agree more often on which branch an atom takes (double-float,
+// plain FP32 far field, beyond the cut-off), and lets the block drop, once, every atom whose
+// distance from the tile's bounding box exceeds the cut-off (each node would skip it anyway).
+
 __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
 {
     extern __shared__ float sf[];
+    __shared__ int s_cnt[DEP_NT / 32];
     float* th = sf;
     float* tl = sf + 64;
     float* sat = sf + 128;
-    const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
-    const size_t nxy = (size_t)a.n[0] * a.n[1];
-    // block origin: the block's first node; offsets from it keep the pairs' magnitudes small
-    const size_t P0 = blockIdx.x * (size_t)DEP_NT;
-    const int k0 = (int)(P0 / nxy), j0 = (int)((P0 - (size_t)k0 * nxy) / a.n[0]);
-    const int i0 = (int)(P0 - (size_t)k0 * nxy - (size_t)j0 * a.n[0]);
+    int* list = reinterpret_cast<int*>(sat + SAF * (size_t)a.na);
+    const int i0 = blockIdx.x * DT_X, j0 = blockIdx.y * DT_Y, k0 = blockIdx.z * DT_Z;
+    const int i = i0 + (threadIdx.x & 7), j = j0 + ((threadIdx.x >> 3) & 7), k = k0 + (threadIdx.x >> 6);
+    const bool valid = i < a.n[0] && j < a.n[1] && k < a.n[2];
+    // tile origin: its first node; offsets from it keep the pairs' magnitudes small
     const double ox = a.ax[0][i0], oy = a.ax[1][j0], oz = a.ax[2][k0];
     for (int t = threadIdx.x; t < 64; t += DEP_NT) {
         th[t] = c_exp_h[t];
         tl[t] = c_exp_l[t];
     }
-    for (int t = threadIdx.x; t < a.na; t += DEP_NT) {
-        const double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * t;
-        float* o = sat + SAF * t;
-        const df Dx = dfa::from_double(r[RX] - ox), Dy = dfa::from_double(r[RX + 1] - oy),
-                 Dz = dfa::from_double(r[RX + 2] - oz);
-        o[0] = Dx.h; o[1] = Dx.l; o[2] = Dy.h; o[3] = Dy.l; o[4] = Dz.h; o[5] = Dz.l;
-        for (int q = 0; q < 3; q++) {
-            const df W = dfa::from_double(r[RW + q]);
-            o[6 + 2 * q] = W.h;
-            o[7 + 2 * q] = W.l;
-        }
-        o[12] = (float)(r[RR] * r[RR]);
-    }
-    __syncthreads();
-    const size_t P = P0 + threadIdx.x;
-    if (P >= N) return;
-    const int k = (int)(P / nxy);
-    const int j = (int)((P - (size_t)k * nxy) / a.n[0]);
-    const int i = (int)(P - (size_t)k * nxy - (size_t)j * a.n[0]);
-    const double x = a.ax[0][i], y = a.ax[1][j], z = a.ax[2][k];
-    const df px = dfa::from_double(x - ox), py = dfa::from_double(y - oy), pz = dfa::from_double(z - oz);
     df zt[3];
     float zmin = 1e30f;
     for (int q = 0; q < 3; q++) {
@@ -478,6 +467,60 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     }
     const float cut = EXP_CUT / zmin;
     const float cut2 = cut * cut * (1.0f + 1e-5f);
+    int nkept;
+    // atoms within the cut-off of the tile's bounding box, in ascending order.  The margin
+    // 1e-3 covers the FP32 rounding of a node's own distance test (~1e-6 relative), so an atom
+    // dropped here fails that test at every node of the tile.
+    {
+        const double bx0 = ox, bx1 = a.ax[0][min(i0 + DT_X - 1, a.n[0] - 1)];
+        const double by0 = oy, by1 = a.ax[1][min(j0 + DT_Y - 1, a.n[1] - 1)];
+        const double bz0 = oz, bz1 = a.ax[2][min(k0 + DT_Z - 1, a.n[2] - 1)];
+        const double lim = (double)cut2 * (1.0 + 1e-3);
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        int total = 0;
+        for (int base = 0; base < a.na; base += DEP_NT) {
+            const int t = base + threadIdx.x;
+            bool keep = false;
+            if (t < a.na) {
+                const double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * t;
+                const double ex = fmax(fmax(bx0 - r[RX], r[RX] - bx1), 0.0);
+                const double ey = fmax(fmax(by0 - r[RX + 1], r[RX + 1] - by1), 0.0);
+                const double ez = fmax(fmax(bz0 - r[RX + 2], r[RX + 2] - bz1), 0.0);
+                keep = ex * ex + ey * ey + ez * ez <= lim;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (l == 0) s_cnt[w] = __popc(m);
+            __syncthreads();
+            int off = total, sum = 0;
+            for (int q = 0; q < DEP_NT / 32; q++) {
+                off += q < w ? s_cnt[q] : 0;
+                sum += s_cnt[q];
+            }
+            if (keep) list[off + __popc(m & ((1u << l) - 1u))] = t;
+            __syncthreads();
+            total += sum;
+        }
+        // stage the kept atoms' fields in list order
+        for (int q = threadIdx.x; q < total; q += DEP_NT) {
+            const double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * list[q];
+            float* o = sat + SAF * q;
+            const df Dx = dfa::from_double(r[RX] - ox), Dy = dfa::from_double(r[RX + 1] - oy),
+                     Dz = dfa::from_double(r[RX + 2] - oz);
+            o[0] = Dx.h; o[1] = Dx.l; o[2] = Dy.h; o[3] = Dy.l; o[4] = Dz.h; o[5] = Dz.l;
+            for (int c = 0; c < 3; c++) {
+                const df W = dfa::from_double(r[RW + c]);
+                o[6 + 2 * c] = W.h;
+                o[7 + 2 * c] = W.l;
+            }
+            o[12] = (float)(r[RR] * r[RR]);
+        }
+        __syncthreads();
+        nkept = total;
+    }
+    if (!valid) return;
+    const size_t P = ((size_t)k * a.n[1] + j) * a.n[0] + i;
+    const double x = a.ax[0][i], y = a.ax[1][j], z = a.ax[2][k];
+    const df px = dfa::from_double(x - ox), py = dfa::from_double(y - oy), pz = dfa::from_double(z - oz);
     bool twice[3];   // zeta_q exactly twice zeta_0 (both parts of the double-float)
 #pragma unroll
     for (int q = 0; q < 3; q++) twice[q] = q > 0 && zt[q].h == 2.0f * zt[0].h && zt[q].l == 2.0f * zt[0].l;
@@ -488,8 +531,8 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     df s = {0.0f, 0.0f};
     int own = -1;
     df orr2 = {0.0f, 0.0f}, odx = s, ody = s, odz = s;
-    for (int t = 0; t < a.na; t++) {
-        const float* o = sat + SAF * t;
+    for (int q0 = 0; q0 < nkept; q0++) {
+        const float* o = sat + SAF * q0;
         const float fx = (px.h - o[0]) + (px.l - o[1]), fy = (py.h - o[2]) + (py.l - o[3]);
         const float fz = (pz.h - o[4]) + (pz.l - o[5]);
         const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
@@ -509,6 +552,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
         const df r2 = dfa::add(dfa::add(dfa::sqr(dx), dfa::sqr(dy)), dfa::sqr(dz));
         if (r2.h > cut2) continue;
         if (r2.h < o[12] * (1.0f + 2e-6f)) {
+            const int t = list[q0];
             const bool in = (r2.h < o[12] * (1.0f - 2e-6f)) ? true : inside_fp64(a, x, y, z, t);
             if (in) {
                 own = t;

@@ -240,6 +240,33 @@ def test_deposit(orc, small_clusters, precision, tol):
         assert np.abs((b - ref)[big] / ref[big]).max() < 1e-10
 
 
+def test_deposit_far_apart_atoms_non_cubic(orc):
+    """Two atoms 50 bohr apart on a 49 x 41 x 45 mesh: tiles at either end of the box lie
+    farther than the cut-off (40 / zeta_min = 26.7 bohr) from the other atom, so the FP32-pair
+    deposit drops that atom for the whole tile; ragged 8 x 8 x 4 tiles on every axis.  Both
+    precisions against the oracle node by node."""
+    B = need_gpu()
+    from synth import clusters, workloads
+    cl = workloads.make_cluster("far-dimer", clusters.dimer(50.0), np.random.default_rng(21), n=49, half_width=36.0,
+                                h_min=1.5, h_max=1.5)
+    x, y, z = orc.mesh(cl)
+    y = np.ascontiguousarray(y[4:-4])
+    z = np.ascontiguousarray(z[2:-2])
+    assert (len(x), len(y), len(z)) == (49, 41, 45)
+    dc = B.DeviceCluster(cl, axes=(x, y, z))
+    dc.n = (len(x), len(y), len(z))
+    ref, rowner = orc.deposit(cl, x, y, z)
+    for precision, tol in ((0, 1e-12), (1, 1e-11)):
+        b, owner, status = B.lasto_op_deposit(dc, precision=precision)
+        assert host(status)[0] == 0
+        assert np.array_equal(host(owner), rowner)
+        b = host(b)
+        assert b.shape == ref.shape
+        assert np.abs(b - ref).max() < tol * np.abs(ref).max()
+        big = np.abs(ref) > 1e-3 * np.abs(ref).max()
+        assert np.abs((b - ref)[big] / ref[big]).max() < 1e-10
+
+
 def test_multipoles_and_faces(orc, small_clusters):
     B = need_gpu()
     for cl in small_clusters:
