@@ -68,12 +68,13 @@ def parse():
     p.add_argument("--no-batch64", action="store_true")
     p.add_argument("--no-pd561", action="store_true")
     p.add_argument("--no-hs", action="store_true")
-    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "hs"], default=None,
+    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "hs", "batch"], default=None,
                    help="run one kernel family for a profiler and exit: 'smoother' = one FP32 red-black sweep "
                         "on an n^3 graded mesh, 'solve' = one mixed solve of the workload with direct launches, "
                         "'guess' = the same with the learned initial guess, 'pd561' = one chosen-form solve "
                         "of the Pd561 graded 385^3 workload with direct launches, 'hs' = one interstitial H and S "
-                        "call (tensor cores) for Pd55 on the graded 129^3 mesh")
+                        "call (tensor cores) for Pd55 on the graded 129^3 mesh, 'batch' = one graph launch of the "
+                        "chosen form over the 8 Pd55 clusters of the workload (for ncu --graph-profiling graph)")
     p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
     p.add_argument("--threads", type=int, default=256,
                    help="launch shape of --profile smoother: threads per block, 0 = one block per row")
@@ -438,6 +439,19 @@ def run_profile(args, B):
         B.lasto_op_interstitial_hs(dc.x, dc.y, dc.z, dc.pos, dc.R, V)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
+    elif args.profile == "batch":
+        cls = [synth.pd55_graded129(seed=1 + k) for k in range(BATCH)]
+        solver = B.Poisson(n_max=cls[0].n, max_atoms=cls[0].n_atoms, max_batch=BATCH, precision=B.LASTO_PREC_MIXED)
+        solver.set_guess()
+        dcs = [B.DeviceCluster(c) for c in cls]
+        v = torch.empty((BATCH * cls[0].n_atoms, 25), dtype=torch.float64, device="cuda")
+        st = solver.solve(dcs, v)     # first solve: smoother tuning, graph capture
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        st = solver.solve(dcs, v)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        assert all(x.status == 0 for x in st)
     elif args.profile == "smoother":
         n = args.n
         axes = [B.lasto_mesh_axis(n, 0.0, 30.0, 0.12, 0.6, 6.0) for _ in range(3)]

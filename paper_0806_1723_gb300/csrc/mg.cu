@@ -370,18 +370,67 @@ cudaError_t launch_resid_restrict(const LevelT<T>& F, const LevelT<T>& C, const 
 // prolongation run as phases separated by __syncthreads.  u[lb] must be zero on entry.
 constexpr int BOT_NT = 1024;
 
+// A level's interior nodes of one colour as items (row, slot): row = (j - 1) + (ny - 2)(k - 1)
+// over the interior rows, slot s -> i = 2 s + ((colour + j + k) & 1), skipped when i leaves the
+// interior.  The first BOT_IT items of each thread are decoded once per level visit and packed
+// as (k << 20) | (j << 10) | s (axes have at most 1023 nodes); any further items (large
+// non-cubic levels only) are decoded in the loop.
+constexpr int BOT_IT = 4;
+
+struct BotItems {
+    int packed[BOT_IT];
+    int count;   // items held in packed[]
+};
+
 template <typename T>
-__device__ void bot_rbgs(const LevelT<T>& L, T* __restrict__ u, const T* __restrict__ b, int colour)
+__device__ __forceinline__ BotItems bot_items(const LevelT<T>& L)
 {
-    const size_t N = L.N(), nhalf = (N + 1 - colour) / 2;
-    for (size_t t = threadIdx.x; t < nhalf; t += BOT_NT) {
-        const size_t P = 2 * t + colour;
-        int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
-        if (is_face(L, i, j, k)) continue;
-        const T acc = b[P] - offdiag(L, u, P, i, j, k);
-        if constexpr (sizeof(T) == 8) u[P] = acc * L.inv_diag[P];
-        else u[P] = rb_point32(acc, dsum(L, i, j, k));
+    BotItems it;
+    const int my = L.ny - 2, slots = L.nx / 2;
+    const int items = my * (L.nz - 2) * slots;
+    it.count = 0;
+#pragma unroll
+    for (int c = 0; c < BOT_IT; c++) {
+        const int q = (int)threadIdx.x + c * BOT_NT;
+        it.packed[c] = 0;
+        if (q < items) {
+            const int row = q / slots, sl = q - row * slots;
+            const int k = 1 + row / my, j = 1 + row - (k - 1) * my;
+            it.packed[c] = (k << 20) | (j << 10) | sl;
+            it.count = c + 1;
+        }
+    }
+    return it;
+}
+
+template <typename T>
+__device__ __forceinline__ void bot_point(const LevelT<T>& L, T* __restrict__ u, const T* __restrict__ b, int colour,
+                                          int k, int j, int sl)
+{
+    const int i = 2 * sl + ((colour + j + k) & 1);
+    if (i < 1 || i > L.nx - 2) return;
+    const size_t P = ((size_t)k * L.ny + j) * L.nx + i;
+    const T acc = b[P] - offdiag(L, u, P, i, j, k);
+    if constexpr (sizeof(T) == 8) u[P] = acc * L.inv_diag[P];
+    else u[P] = rb_point32(acc, dsum(L, i, j, k));
+}
+
+template <typename T>
+__device__ void bot_rbgs(const LevelT<T>& L, const BotItems& it, T* __restrict__ u, const T* __restrict__ b,
+                         int colour)
+{
+#pragma unroll
+    for (int c = 0; c < BOT_IT; c++)
+        if (c < it.count) {
+            const int w = it.packed[c];
+            bot_point(L, u, b, colour, w >> 20, (w >> 10) & 1023, w & 1023);
+        }
+    const int my = L.ny - 2, slots = L.nx / 2;
+    const int items = my * (L.nz - 2) * slots;
+    for (int q = (int)threadIdx.x + BOT_IT * BOT_NT; q < items; q += BOT_NT) {
+        const int row = q / slots, sl = q - row * slots;
+        const int k = 1 + row / my, j = 1 + row - (k - 1) * my;
+        bot_point(L, u, b, colour, k, j, sl);
     }
     __syncthreads();
 }
@@ -441,9 +490,10 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
     __syncthreads();
     for (int l = 0; l < nl - 1; l++) {
         const LevelT<T>& F = lv[l];
+        const BotItems items = bot_items(F);
         for (int it = 0; it < a.nu1; it++) {
-            bot_rbgs(F, u[l], b[l], 0);
-            bot_rbgs(F, u[l], b[l], 1);
+            bot_rbgs(F, items, u[l], b[l], 0);
+            bot_rbgs(F, items, u[l], b[l], 1);
         }
         const LevelT<T>& C = lv[l + 1];
         for (unsigned t = threadIdx.x; t < C.N(); t += BOT_NT) {
@@ -499,9 +549,10 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
             ul[P] += e;
         }
         __syncthreads();
+        const BotItems items = bot_items(F);
         for (int it = 0; it < a.nu2; it++) {
-            bot_rbgs(F, ul, b[l], a.sym ? 1 : 0);
-            bot_rbgs(F, ul, b[l], a.sym ? 0 : 1);
+            bot_rbgs(F, items, ul, b[l], a.sym ? 1 : 0);
+            bot_rbgs(F, items, ul, b[l], a.sym ? 0 : 1);
         }
     }
     for (unsigned t = threadIdx.x; t < lv[0].N(); t += BOT_NT) a.u[0][t] = u[0][t];
