@@ -178,7 +178,7 @@ bool valid_n(const int n[3])
 {
     for (int d = 0; d < 3; d++)
         if (n[d] < 3 || n[d] % 2 == 0) return false;
-    if ((size_t)n[0] * n[1] * n[2] >= (size_t(1) << 32)) return false;   // kernels index with 32 bits
+    if ((size_t)n[0] * n[1] * n[2] >= (size_t(1) << 31)) return false;   // kernels index with 31 bits
     int nn[3] = {n[0], n[1], n[2]};
     return num_levels(nn) >= 1;
 }
@@ -1345,7 +1345,7 @@ bool op_grid_ok(const int n[3], const double* x, const double* y, const double* 
     if (!n || !x || !y || !z) return false;
     for (int d = 0; d < 3; d++)
         if (n[d] < 3 || n[d] % 2 == 0) return false;
-    return true;
+    return (size_t)n[0] * n[1] * n[2] < (size_t(1) << 31);   // kernels index with 31 bits
 }
 
 }  // namespace
@@ -1518,9 +1518,7 @@ int lasto_op_restrict(const int n[3], const double* x, const double* y, const do
     OpLevel L(n, x, y, z, false, s);
     if (!L.ok()) return LASTO_ERR_NO_MEMORY;
     LevelT<double> C = L.S.view64();
-    C.nx = (n[0] + 1) / 2;
-    C.ny = (n[1] + 1) / 2;
-    C.nz = (n[2] + 1) / 2;
+    set_dims(C, (n[0] + 1) / 2, (n[1] + 1) / 2, (n[2] + 1) / 2);
     return op_status(launch_restrict<double>(L.S.view64(), C, r, bc, s));
 }
 
@@ -1532,9 +1530,7 @@ int lasto_op_prolong_add(const int n[3], const double* x, const double* y, const
     OpLevel L(n, x, y, z, false, s);
     if (!L.ok()) return LASTO_ERR_NO_MEMORY;
     LevelT<double> C = L.S.view64();
-    C.nx = (n[0] + 1) / 2;
-    C.ny = (n[1] + 1) / 2;
-    C.nz = (n[2] + 1) / 2;
+    set_dims(C, (n[0] + 1) / 2, (n[1] + 1) / 2, (n[2] + 1) / 2);
     return op_status(launch_prolong_add<double>(L.S.view64(), C, ec, u, s));
 }
 

@@ -85,13 +85,50 @@ struct AxisT {
     int n;
 };
 
+// Division of a node index by an invariant divisor as a multiply-high and a shift: with
+// 2^(l-1) < d <= 2^l and m = ceil(2^(31+l) / d) (which fits in 32 bits), floor(n / d) =
+// floor(m n / 2^(31+l)) for every 0 <= n < 2^31 (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", 1994, Theorem 4.2 with N = 31).  Node indices stay
+// below 2^31 (checked where grids are accepted).
+struct DivMagic {
+    unsigned m;
+    int s;   // l - 1
+};
+
+inline DivMagic div_magic(unsigned d)
+{
+    int l = 0;
+    while ((1ull << l) < d) l++;
+    DivMagic r;
+    r.m = (unsigned)(((1ull << (31 + l)) + d - 1) / d);
+    r.s = l - 1;
+    return r;
+}
+
+__device__ __forceinline__ unsigned div_by(unsigned n, DivMagic q)
+{
+    return __umulhi(n, q.m) >> q.s;
+}
+
 template <typename T>
 struct LevelT {
     AxisT<T> ax[3];
     const T* inv_diag;  // [N] or nullptr (FP32 smoother computes the diagonal)
     int nx, ny, nz;
+    DivMagic dvx, dvxy;  // division by nx and by nx * ny (set_dims)
     __host__ __device__ size_t N() const { return (size_t)nx * ny * nz; }
 };
+
+// The only way dimensions are set: keeps the division constants in step (every axis >= 3 nodes).
+template <typename T>
+inline void set_dims(LevelT<T>& v, int nx, int ny, int nz)
+{
+    v.nx = nx;
+    v.ny = ny;
+    v.nz = nz;
+    v.dvx = div_magic((unsigned)nx);
+    v.dvxy = div_magic((unsigned)nx * (unsigned)ny);
+}
 
 // Raw (writable) per-axis storage of one level in one pool.
 struct AxisStore {

@@ -85,7 +85,7 @@ LevelT<double> LevelStore::view64() const
     LevelT<double> v;
     for (int d = 0; d < 3; d++) v.ax[d] = axis_view<double>(ax[d]);
     v.inv_diag = inv_diag;
-    v.nx = n[0]; v.ny = n[1]; v.nz = n[2];
+    set_dims(v, n[0], n[1], n[2]);
     return v;
 }
 LevelT<float> LevelStore::view32() const
@@ -93,7 +93,7 @@ LevelT<float> LevelStore::view32() const
     LevelT<float> v;
     for (int d = 0; d < 3; d++) v.ax[d] = axis_view<float>(ax[d]);
     v.inv_diag = nullptr;
-    v.nx = n[0]; v.ny = n[1]; v.nz = n[2];
+    set_dims(v, n[0], n[1], n[2]);
     return v;
 }
 

@@ -16,16 +16,19 @@ namespace lasto {
 
 constexpr int NT = 256;
 
-// Flat index -> (i, j, k).  Grids hold fewer than 2^32 nodes (checked at planning), so the
-// decomposition uses 32-bit unsigned division: a 64-bit division is a long subroutine and
-// would cost more than the stencil update it indexes.
-__device__ __forceinline__ void node_ijk(size_t P, int nx, int ny, int& i, int& j, int& k)
+// Flat index -> (i, j, k).  Grids hold fewer than 2^31 nodes (checked where they are accepted),
+// so the decomposition divides by the level's invariant nx and nx * ny with a multiply-high and
+// a shift (LevelT's division constants): a hardware-less integer division would cost more than
+// the stencil update it indexes.
+template <typename T>
+__device__ __forceinline__ void node_ijk(size_t P, const LevelT<T>& L, int& i, int& j, int& k)
 {
-    const unsigned p = (unsigned)P, nxy = (unsigned)nx * (unsigned)ny;
-    const unsigned kk = p / nxy, rem = p - kk * nxy, jj = rem / (unsigned)nx;
+    const unsigned p = (unsigned)P;
+    const unsigned kk = div_by(p, L.dvxy), rem = p - kk * ((unsigned)L.nx * (unsigned)L.ny);
+    const unsigned jj = div_by(rem, L.dvx);
     k = (int)kk;
     j = (int)jj;
-    i = (int)(rem - jj * (unsigned)nx);
+    i = (int)(rem - jj * (unsigned)L.nx);
 }
 
 template <typename T>
@@ -35,16 +38,19 @@ __device__ __forceinline__ bool is_face(const LevelT<T>& L, int i, int j, int k)
 }
 
 // sum of the six neighbour terms in the fixed order x-, x+, y-, y+, z-, z+
+// (neighbours addressed from the node's own pointer with 32-bit offsets: a plane holds fewer
+// than 2^31 nodes)
 template <typename T>
 __device__ __forceinline__ T offdiag(const LevelT<T>& L, const T* __restrict__ u, size_t P, int i, int j, int k)
 {
-    const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
-    T t = L.ax[0].cm[i] * u[P - 1];
-    t = fma(L.ax[0].cp[i], u[P + 1], t);
-    t = fma(L.ax[1].cm[j], u[P - sy], t);
-    t = fma(L.ax[1].cp[j], u[P + sy], t);
-    t = fma(L.ax[2].cm[k], u[P - sz], t);
-    t = fma(L.ax[2].cp[k], u[P + sz], t);
+    const int sy = L.nx, sz = L.nx * L.ny;
+    const T* __restrict__ c = u + P;
+    T t = L.ax[0].cm[i] * c[-1];
+    t = fma(L.ax[0].cp[i], c[1], t);
+    t = fma(L.ax[1].cm[j], c[-sy], t);
+    t = fma(L.ax[1].cp[j], c[sy], t);
+    t = fma(L.ax[2].cm[k], c[-sz], t);
+    t = fma(L.ax[2].cp[k], c[sz], t);
     return t;
 }
 
@@ -59,11 +65,11 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour,
                                              size_t nhalf)
 {
-    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (t >= nhalf) return;
-    const size_t P = 2 * t + colour;
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;   // nodes < 2^31
+    if (t >= (unsigned)nhalf) return;
+    const unsigned P = 2 * t + colour;
     int i, j, k;
-    node_ijk(P, L.nx, L.ny, i, j, k);
+    node_ijk(P, L, i, j, k);
     if (is_face(L, i, j, k)) return;
     const T acc = b[P] - offdiag(L, u, P, i, j, k);
     if constexpr (sizeof(T) == 8) {
@@ -82,7 +88,7 @@ __global__ void __launch_bounds__(512) k_rbgs_row(LevelT<T> L, T* __restrict__ u
     const int j = blockIdx.x + 1, k = blockIdx.y + 1;
     const int i = 2 * (int)threadIdx.x + ((colour + j + k) & 1);   // flat-index parity = parity of i + j + k
     if (i == 0 || i >= L.nx - 1) return;
-    const size_t P = ((size_t)k * L.ny + j) * L.nx + i;
+    const unsigned P = ((unsigned)k * L.ny + j) * L.nx + i;   // nodes < 2^31
     const T acc = b[P] - offdiag(L, u, P, i, j, k);
     if constexpr (sizeof(T) == 8) {
         u[P] = acc * L.inv_diag[P];
@@ -116,7 +122,7 @@ __global__ void __launch_bounds__(NT) k_residual(LevelT<T> L, const T* __restric
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
     if (P >= L.N()) return;
     int i, j, k;
-    node_ijk(P, L.nx, L.ny, i, j, k);
+    node_ijk(P, L, i, j, k);
     if (is_face(L, i, j, k)) {
         r[P] = T(0);
         return;
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(NT) k_apply(LevelT<T> L, const T* __restrict__
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
     if (P >= L.N()) return;
     int i, j, k;
-    node_ijk(P, L.nx, L.ny, i, j, k);
+    node_ijk(P, L, i, j, k);
     Au[P] = is_face(L, i, j, k) ? T(0) : fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
 }
 
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelT<T> F, LevelT<T> C, const
     const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
     if (t >= C.N()) return;
     int I, J, K;
-    node_ijk(t, C.nx, C.ny, I, J, K);
+    node_ijk(t, C, I, J, K);
     if (is_face(C, I, J, K)) {
         bc[t] = T(0);
         return;
@@ -196,7 +202,7 @@ __global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, co
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
     if (P >= F.N()) return;
     int i, j, k;
-    node_ijk(P, F.nx, F.ny, i, j, k);
+    node_ijk(P, F, i, j, k);
     if (is_face(F, i, j, k)) return;
     const int I = i >> 1, J = j >> 1, K = k >> 1;
     const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
@@ -331,7 +337,7 @@ __global__ void __launch_bounds__(NT) k_resid_restrict(LevelT<T> F, LevelT<T> C,
     const size_t t = blockIdx.x * (size_t)NT + threadIdx.x;
     if (t >= C.N()) return;
     int I, J, K;
-    node_ijk(t, C.nx, C.ny, I, J, K);
+    node_ijk(t, C, I, J, K);
     uc[t] = T(0);
     if (is_face(C, I, J, K)) {
         bc[t] = T(0);
@@ -498,7 +504,7 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
         const LevelT<T>& C = lv[l + 1];
         for (unsigned t = threadIdx.x; t < C.N(); t += BOT_NT) {
             int I, J, K;
-            node_ijk(t, C.nx, C.ny, I, J, K);
+            node_ijk(t, C, I, J, K);
             u[l + 1][t] = T(0);
             if (is_face(C, I, J, K)) {
                 b[l + 1][t] = T(0);
@@ -530,7 +536,7 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
         T* ul = u[l];
         for (unsigned P = threadIdx.x; P < F.N(); P += BOT_NT) {
             int i, j, k;
-            node_ijk(P, F.nx, F.ny, i, j, k);
+            node_ijk(P, F, i, j, k);
             if (is_face(F, i, j, k)) continue;
             const int I = i >> 1, J = j >> 1, K = k >> 1;
             const int ni = (i & 1) ? 2 : 1, nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
@@ -747,7 +753,7 @@ __global__ void __launch_bounds__(NT) k_bnorm(LevelT<double> L, const double* __
     GRID_STRIDE(P, L.N())
     {
         int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
+        node_ijk(P, L, i, j, k);
         if (is_face(L, i, j, k)) continue;
         const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
         double v = b[P];
@@ -772,7 +778,7 @@ __global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const doubl
     GRID_STRIDE(P, L.N())
     {
         int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
+        node_ijk(P, L, i, j, k);
         double v = 0.0;
         if (!is_face(L, i, j, k)) v = b[P] - fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
         if (r) r[P] = v;
@@ -791,7 +797,7 @@ __global__ void __launch_bounds__(NT) k_apply_dot(LevelT<double> L, const double
     GRID_STRIDE(P, L.N())
     {
         int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
+        node_ijk(P, L, i, j, k);
         double v = 0.0;
         if (!is_face(L, i, j, k)) {
             v = fma(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
@@ -813,7 +819,7 @@ __global__ void __launch_bounds__(NT) k_update_ur(LevelT<double> L, const Ctl* _
     GRID_STRIDE(P, L.N())
     {
         int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
+        node_ijk(P, L, i, j, k);
         if (is_face(L, i, j, k)) continue;
         u[P] = fma(alpha, p[P], u[P]);
         const double rv = fma(-alpha, q[P], r[P]);
@@ -831,7 +837,7 @@ __global__ void __launch_bounds__(NT) k_dot_rz(LevelT<double> L, const double* _
     GRID_STRIDE(P, L.N())
     {
         int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
+        node_ijk(P, L, i, j, k);
         if (!is_face(L, i, j, k)) acc = fma(vol(L, i, j, k) * r[P], z[P], acc);
     }
     reduce_finish(block_sum<NT>(acc, sm), red, sm);
@@ -843,7 +849,7 @@ __global__ void __launch_bounds__(NT) k_update_p(LevelT<double> L, const Ctl* __
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
     if (P >= L.N()) return;
     int i, j, k;
-    node_ijk(P, L.nx, L.ny, i, j, k);
+    node_ijk(P, L, i, j, k);
     p[P] = is_face(L, i, j, k) ? 0.0 : fma(ctl->beta, p[P], z[P]);
 }
 
@@ -861,7 +867,7 @@ __global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float
     GRID_STRIDE(P, L.N())
     {
         int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
+        node_ijk(P, L, i, j, k);
         float v = 0.0f;
         if (!is_face(L, i, j, k)) {
             v = fmaf(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
@@ -882,7 +888,7 @@ __global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* 
     GRID_STRIDE(P, L.N())
     {
         int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
+        node_ijk(P, L, i, j, k);
         if (is_face(L, i, j, k)) continue;
         e[P] = fmaf(alpha, p[P], e[P]);
         const float rv = fmaf(-alpha, q[P], r[P]);
@@ -901,7 +907,7 @@ __global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __re
     GRID_STRIDE(P, L.N())
     {
         int i, j, k;
-        node_ijk(P, L.nx, L.ny, i, j, k);
+        node_ijk(P, L, i, j, k);
         if (is_face(L, i, j, k)) continue;
         acc = z ? fmaf(vol32(L, i, j, k) * r[P], z[P], acc) : fmaf(r[P], r[P], acc);
     }
@@ -914,7 +920,7 @@ __global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* _
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
     if (P >= L.N()) return;
     int i, j, k;
-    node_ijk(P, L.nx, L.ny, i, j, k);
+    node_ijk(P, L, i, j, k);
     p[P] = is_face(L, i, j, k) ? 0.0f : fmaf((float)ctl->beta_in, p[P], z[P]);
 }
 
