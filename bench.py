@@ -46,10 +46,12 @@ BATCH = 8
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per half sweep at 257^3, one block per row, in
 # steady state (launches 5-8 of 4 sweeps, caches not flushed between launches, so each launch also
-# writes back what the one before left dirty in L2): mean of the four launches.  FP32: 130.2 MB
-# read + 67.6 MB written; FP64: 403.3 + 134.6 MB.  A launch shape without a capture reports null.
-DRAM_BYTES_257 = {0: 197.8e6}
-DRAM_BYTES_257_F64 = 537.8e6
+# writes back what the one before left dirty in L2): mean of the four launches, by launch shape
+# (0 = one block per row, else threads per block).  FP32 rows: 130.3 MB read + 67.6 MB written,
+# flat 128: 129.3 + 66.3, flat 256: 129.5 + 66.3; FP64 rows: 403.3 + 134.5 MB.  A launch shape
+# without a capture reports null.
+DRAM_BYTES_257 = {0: 197.9e6, 128: 195.6e6, 256: 195.8e6}
+DRAM_BYTES_257_F64 = 537.7e6
 
 # FP64 FMA throughput of one GB300 (a DFMA chain over every SM, CUDA events: 1.19 TFLOP/s at
 # 1995 MHz); the copy and BF16 peaks come from the measured-peaks file
