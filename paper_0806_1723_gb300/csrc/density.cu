@@ -874,62 +874,121 @@ __global__ void k_nonsph_moments(int na, const double* __restrict__ R, const dou
 }
 
 // u on the faces = sum over atoms of Z/r - sum_k w_k [1/r - e^{-zeta_k r}(1/r + zeta_k/2)]
-// - sum_{l>=1,m} 4pi/(2l+1) c_lm M_l S_lm(d) / r^(2l+1)
-__global__ void k_boundary_exact(int nx, int ny, int nz, const double* __restrict__ x, const double* __restrict__ y,
-                                 const double* __restrict__ z, int na, const double* __restrict__ pos,
-                                 const double* __restrict__ Zn, const double* __restrict__ w,
-                                 const double* __restrict__ zeta, const double* __restrict__ clm,
-                                 const double* __restrict__ M, double* __restrict__ u)
+// - sum_{l>=1,m} 4pi/(2l+1) c_lm M_l S_lm(d) / r^(2l+1), evaluated per atom as
+// (Z - sum_k w_k)/r + sum_k w_k e^{-zeta_k r}(1/r + zeta_k/2) - sum_l r^-(2l+1) P_l(d), where
+// P_l = sum_m 4pi/(2l+1) c_lm M_l S_lm is a homogeneous polynomial of degree l whose monomial
+// coefficients each block forms once per atom (34 for l = 1..4).  Terms with zeta_k r >= 40
+// (below e^-40 of w_k) are dropped, as in the deposit.
+constexpr int EX_NT = 128;
+constexpr int EX_CH = 64;        // atoms staged per pass
+constexpr int EX_NC = 34;        // monomials of degree 1..4
+constexpr int EX_REC = 10 + EX_NC;  // x y z q w0 w1 w2 zeta0 zeta1 zeta2 | coefficients
+
+// slot of x^a y^b z^c (a + b + c = l, 1 <= l <= 4): degree offset + s(s+1)/2 + c, s = b + c
+__host__ __device__ constexpr int ex_slot(int l, int b, int c)
 {
+    return (l == 1 ? 0 : l == 2 ? 3 : l == 3 ? 9 : 19) + (b + c) * (b + c + 1) / 2 + c;
+}
+
+__global__ void __launch_bounds__(EX_NT) k_boundary_exact(int nx, int ny, int nz, const double* __restrict__ x,
+                                                          const double* __restrict__ y, const double* __restrict__ z,
+                                                          int na, const double* __restrict__ pos,
+                                                          const double* __restrict__ Zn, const double* __restrict__ w,
+                                                          const double* __restrict__ zeta,
+                                                          const double* __restrict__ clm,
+                                                          const double* __restrict__ M, double* __restrict__ u)
+{
+    __shared__ double rec[EX_CH][EX_REC];
     const size_t fx = (size_t)ny * nz, fy = (size_t)nx * nz, fz = (size_t)nx * ny;
     const size_t total = 2 * (fx + fy + fz);
-    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    int i, j, k;
-    size_t r = t;
-    if (r < 2 * fx) {
-        const int side = (int)(r / fx);
-        r %= fx;
-        i = side ? nx - 1 : 0;
-        j = (int)(r % ny);
-        k = (int)(r / ny);
-    } else if ((r -= 2 * fx) < 2 * fy) {
-        const int side = (int)(r / fy);
-        r %= fy;
-        j = side ? ny - 1 : 0;
-        i = (int)(r % nx);
-        k = (int)(r / nx);
-    } else {
-        r -= 2 * fy;
-        const int side = (int)(r / fz);
-        r %= fz;
-        k = side ? nz - 1 : 0;
-        i = (int)(r % nx);
-        j = (int)(r / nx);
+    const size_t t = blockIdx.x * (size_t)EX_NT + threadIdx.x;
+    const bool valid = t < total;
+    int i = 0, j = 0, k = 0;
+    if (valid) {
+        size_t r = t;
+        if (r < 2 * fx) {
+            const int side = (int)(r / fx);
+            r %= fx;
+            i = side ? nx - 1 : 0;
+            j = (int)(r % ny);
+            k = (int)(r / ny);
+        } else if ((r -= 2 * fx) < 2 * fy) {
+            const int side = (int)(r / fy);
+            r %= fy;
+            j = side ? ny - 1 : 0;
+            i = (int)(r % nx);
+            k = (int)(r / nx);
+        } else {
+            r -= 2 * fy;
+            const int side = (int)(r / fz);
+            r %= fz;
+            k = side ? nz - 1 : 0;
+            i = (int)(r % nx);
+            j = (int)(r / nx);
+        }
     }
+    const double px = x[i], py = y[j], pz = z[k];
     double v = 0.0;
-    for (int a = 0; a < na; a++) {
-        const double dx = x[i] - pos[3 * a], dy = y[j] - pos[3 * a + 1], dz = z[k] - pos[3 * a + 2];
-        const double d = sqrt(dx * dx + dy * dy + dz * dz), id = 1.0 / d;
-        v += Zn[a] * id;
-        for (int q = 0; q < 3; q++) {
-            const double zq = zeta[3 * a + q];
-            v -= w[3 * a + q] * (id - exp(-zq * d) * (id + 0.5 * zq));
-        }
-        double S[NLM];
-        solid_harmonics(dx, dy, dz, S);
-        double pw = id * id * id;   // d^-(2l+1)
-        int l = 1;
-        for (int lm = 1; lm < NLM; lm++) {
-            const int ll = l_of_lm(lm);
-            if (ll != l) {
-                pw *= id * id;
-                l = ll;
+    for (int base = 0; base < na; base += EX_CH) {
+        const int nch = min(EX_CH, na - base);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nch; q += EX_NT) {
+            const int at = base + q;
+            double* o = rec[q];
+            o[0] = pos[3 * at];
+            o[1] = pos[3 * at + 1];
+            o[2] = pos[3 * at + 2];
+            o[3] = Zn[at] - (w[3 * at] + w[3 * at + 1] + w[3 * at + 2]);
+            o[4] = w[3 * at];
+            o[5] = w[3 * at + 1];
+            o[6] = w[3 * at + 2];
+            o[7] = zeta[3 * at];
+            o[8] = zeta[3 * at + 1];
+            o[9] = zeta[3 * at + 2];
+            for (int c = 0; c < EX_NC; c++) o[10 + c] = 0.0;
+            for (int tm = 1; tm < N_MONO_TERMS; tm++) {
+                const Mono mo = c_mono[tm];
+                const int l = l_of_lm(mo.lm);
+                const double K = 4.0 * PI / (2 * l + 1) * clm[24 * (size_t)at + mo.lm - 1] * M[5 * (size_t)at + l];
+                o[10 + ex_slot(l, mo.b, mo.c)] += K * mo.coef;
             }
-            v -= 4.0 * PI / (2 * l + 1) * clm[24 * (size_t)a + lm - 1] * M[5 * (size_t)a + l] * S[lm] * pw;
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int q = 0; q < nch; q++) {
+            const double* o = rec[q];
+            const double dx = px - o[0], dy = py - o[1], dz = pz - o[2];
+            const double d = sqrt(fma(dx, dx, fma(dy, dy, dz * dz))), id = 1.0 / d, id2 = id * id;
+            double e = o[3] * id;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const double zc = o[7 + c];
+                if (zc * d < EXP_CUT) e = fma(o[4 + c] * exp(-zc * d), id + 0.5 * zc, e);
+            }
+            double xp[5], yp[5], zp[5];
+            xp[0] = yp[0] = zp[0] = 1.0;
+#pragma unroll
+            for (int p = 1; p < 5; p++) {
+                xp[p] = xp[p - 1] * dx;
+                yp[p] = yp[p - 1] * dy;
+                zp[p] = zp[p - 1] * dz;
+            }
+            double P[5];
+#pragma unroll
+            for (int l = 1; l <= 4; l++) {
+                double acc = 0.0;
+#pragma unroll
+                for (int sb = 0; sb <= l; sb++)
+#pragma unroll
+                    for (int c = 0; c <= sb; c++)
+                        acc = fma(o[10 + ex_slot(l, sb - c, c)], xp[l - sb] * yp[sb - c] * zp[c], acc);
+                P[l] = acc;
+            }
+            const double multi = id2 * id * fma(id2, fma(id2, fma(id2, P[4], P[3]), P[2]), P[1]);
+            v += e - multi;
         }
     }
-    u[((size_t)k * ny + j) * nx + i] = v;
+    if (valid) u[((size_t)k * ny + j) * nx + i] = v;
 }
 
 cudaError_t launch_boundary_exact(const lasto_cluster& cl, double* M, double* u, cudaStream_t s)
@@ -940,7 +999,7 @@ cudaError_t launch_boundary_exact(const lasto_cluster& cl, double* M, double* u,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int* n = cl.n;
     const size_t total = 2 * ((size_t)n[1] * n[2] + (size_t)n[0] * n[2] + (size_t)n[0] * n[1]);
-    k_boundary_exact<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(n[0], n[1], n[2], cl.x, cl.y, cl.z, cl.n_atoms,
+    k_boundary_exact<<<(unsigned)((total + EX_NT - 1) / EX_NT), EX_NT, 0, s>>>(n[0], n[1], n[2], cl.x, cl.y, cl.z, cl.n_atoms,
                                                                      cl.pos, cl.Z, cl.slater_w, cl.slater_zeta,
                                                                      cl.c_lm, M, u);
     return cudaGetLastError();
