@@ -137,8 +137,9 @@ __device__ __forceinline__ void solid_harmonics(double x, double y, double z, do
 
 // ---------------------------------------------------------------- sphere records
 // rec[i][*]: 0-2 pos, 3 R, 4-6 W_k, 7-9 zeta_k, 10-12 A_k, 13-15 B_k, 16-18 (a, b, c),
-// 19 q, 20 rho0(R), 21 rho0'(R), 24-47: c_lm / R^l as 24 double-floats (float pairs)
-enum { RX = 0, RR = 3, RW = 4, RZ = 7, RA = 10, RB = 13, RC = 16, RQ = 19, RRHO = 20, RDRHO = 21, RNS = 24 };
+// 19 q, 20 rho0(R), 21 rho0'(R), 22-23: x y z R^2 as four floats, 24-47: c_lm / R^l as 24
+// double-floats (float pairs)
+enum { RX = 0, RR = 3, RW = 4, RZ = 7, RA = 10, RB = 13, RC = 16, RQ = 19, RRHO = 20, RDRHO = 21, RXF = 22, RNS = 24 };
 
 struct SphArgs {
     int na;
@@ -194,6 +195,13 @@ __global__ void __launch_bounds__(SPH_NT) k_sphere_params(SphArgs a)
     r[RX + 1] = yi;
     r[RX + 2] = zi;
     r[RR] = Ri;
+    {
+        float* xf = reinterpret_cast<float*>(r + RXF);
+        xf[0] = (float)xi;
+        xf[1] = (float)yi;
+        xf[2] = (float)zi;
+        xf[3] = (float)(Ri * Ri);
+    }
     double rho = 0.0, drho = 0.0, inside = 0.0;
     for (int k = 0; k < 3; k++) {
         const double z = zt[k], wk = a.w[3 * i + k];
@@ -446,6 +454,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
 {
     extern __shared__ float sf[];
     __shared__ int s_cnt[DEP_NT / 32];
+    __shared__ float s_off[2 * (DT_X + DT_Y + DT_Z)];   // node coordinate - tile origin, double-float
     float* th = sf;
     float* tl = sf + 64;
     float* sat = sf + 128;
@@ -459,6 +468,16 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
         th[t] = c_exp_h[t];
         tl[t] = c_exp_l[t];
     }
+    if (threadIdx.x < DT_X + DT_Y + DT_Z) {
+        const int t = threadIdx.x;
+        const int d = t < DT_X ? 0 : t < DT_X + DT_Y ? 1 : 2;
+        const int o = t - (d == 0 ? 0 : d == 1 ? DT_X : DT_X + DT_Y);
+        const int first = d == 0 ? i0 : d == 1 ? j0 : k0;
+        const double org = d == 0 ? ox : d == 1 ? oy : oz;
+        const df v = dfa::from_double(a.ax[d][min(first + o, a.n[d] - 1)] - org);
+        s_off[2 * t] = v.h;
+        s_off[2 * t + 1] = v.l;
+    }
     df zt[3];
     float zmin = 1e30f;
     for (int q = 0; q < 3; q++) {
@@ -468,25 +487,26 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     const float cut = EXP_CUT / zmin;
     const float cut2 = cut * cut * (1.0f + 1e-5f);
     int nkept;
-    // atoms within the cut-off of the tile's bounding box, in ascending order.  The margin
-    // 1e-3 covers the FP32 rounding of a node's own distance test (~1e-6 relative), so an atom
-    // dropped here fails that test at every node of the tile.
+    // atoms within the cut-off of the tile's bounding box, in ascending order, tested in FP32
+    // on the records' float copies of the positions.  The margin 1e-3 on the squared distance
+    // covers the rounding of this test (~1e-6 relative) and of a node's own FP32 distance test,
+    // so an atom dropped here fails that test at every node of the tile.
     {
-        const double bx0 = ox, bx1 = a.ax[0][min(i0 + DT_X - 1, a.n[0] - 1)];
-        const double by0 = oy, by1 = a.ax[1][min(j0 + DT_Y - 1, a.n[1] - 1)];
-        const double bz0 = oz, bz1 = a.ax[2][min(k0 + DT_Z - 1, a.n[2] - 1)];
-        const double lim = (double)cut2 * (1.0 + 1e-3);
+        const float bx0 = (float)ox, bx1 = (float)a.ax[0][min(i0 + DT_X - 1, a.n[0] - 1)];
+        const float by0 = (float)oy, by1 = (float)a.ax[1][min(j0 + DT_Y - 1, a.n[1] - 1)];
+        const float bz0 = (float)oz, bz1 = (float)a.ax[2][min(k0 + DT_Z - 1, a.n[2] - 1)];
+        const float lim = cut2 * (1.0f + 1e-3f);
         const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
         int total = 0;
         for (int base = 0; base < a.na; base += DEP_NT) {
             const int t = base + threadIdx.x;
             bool keep = false;
             if (t < a.na) {
-                const double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * t;
-                const double ex = fmax(fmax(bx0 - r[RX], r[RX] - bx1), 0.0);
-                const double ey = fmax(fmax(by0 - r[RX + 1], r[RX + 1] - by1), 0.0);
-                const double ez = fmax(fmax(bz0 - r[RX + 2], r[RX + 2] - bz1), 0.0);
-                keep = ex * ex + ey * ey + ez * ez <= lim;
+                const float4 c = *reinterpret_cast<const float4*>(a.rec + (size_t)SPHERE_REC_DOUBLES * t + RXF);
+                const float ex = fmaxf(fmaxf(bx0 - c.x, c.x - bx1), 0.0f);
+                const float ey = fmaxf(fmaxf(by0 - c.y, c.y - by1), 0.0f);
+                const float ez = fmaxf(fmaxf(bz0 - c.z, c.z - bz1), 0.0f);
+                keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= lim;
             }
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (l == 0) s_cnt[w] = __popc(m);
@@ -512,7 +532,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
                 o[6 + 2 * c] = W.h;
                 o[7 + 2 * c] = W.l;
             }
-            o[12] = (float)(r[RR] * r[RR]);
+            o[12] = reinterpret_cast<const float*>(r + RXF)[3];
         }
         __syncthreads();
         nkept = total;
@@ -520,7 +540,9 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     if (!valid) return;
     const size_t P = ((size_t)k * a.n[1] + j) * a.n[0] + i;
     const double x = a.ax[0][i], y = a.ax[1][j], z = a.ax[2][k];
-    const df px = dfa::from_double(x - ox), py = dfa::from_double(y - oy), pz = dfa::from_double(z - oz);
+    const int li = threadIdx.x & 7, lj = DT_X + ((threadIdx.x >> 3) & 7), lk = DT_X + DT_Y + (threadIdx.x >> 6);
+    const df px = {s_off[2 * li], s_off[2 * li + 1]}, py = {s_off[2 * lj], s_off[2 * lj + 1]},
+             pz = {s_off[2 * lk], s_off[2 * lk + 1]};
     bool twice[3];   // zeta_q exactly twice zeta_0 (both parts of the double-float)
 #pragma unroll
     for (int q = 0; q < 3; q++) twice[q] = q > 0 && zt[q].h == 2.0f * zt[0].h && zt[q].l == 2.0f * zt[0].l;
