@@ -46,11 +46,25 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
 {
     extern __shared__ float sd_sm[];   // per atom: D = pos_t - pos_a (3 pairs), W (3 pairs)
     __shared__ double rq[SD_MAXQ];     // the density at the quadrature points
+    __shared__ double cs[NLM];         // own nonspherical part: prefactor(r) c_lm (r/R)^l
     const int a = blockIdx.y, j = blockIdx.x, tid = threadIdx.x;
     const double* ra = rec + (size_t)SPHERE_REC_DOUBLES * a;
     const double Ra = ra[3];
     const double dx = log(Ra / r_min) / (n_rad - 1);
     const double r = (j == n_rad - 1) ? Ra : Ra * exp((j - (n_rad - 1)) * dx);
+    // own nonspherical part zeta_1^3/(8 pi) e^{-zeta_1 r} (1 - r^2/R^2)^2 sum c_lm (r/R)^l y_lm:
+    // everything but y_lm depends on the radius only, once per block
+    if (tid < NLM) {
+        double v = 0.0;
+        if (tid > 0 && r < Ra) {
+            const double z1 = ra[7], sr = r / Ra, tt = 1.0 - sr * sr;
+            const int l = tid >= 16 ? 4 : tid >= 9 ? 3 : tid >= 4 ? 2 : 1;
+            double sl = sr;
+            for (int p = 1; p < l; p++) sl *= sr;
+            v = z1 * z1 * z1 / (8.0 * 3.14159265358979323846) * exp(-z1 * r) * tt * tt * clm[24 * (size_t)a + tid - 1] * sl;
+        }
+        cs[tid] = v;
+    }
     for (int t = tid; t < na; t += SD_NT) {
         const double* rt = rec + (size_t)SPHERE_REC_DOUBLES * t;
         float* o = sd_sm + 12 * t;
@@ -121,15 +135,11 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
             }
         }
         double rhod = dfa::to_double(rho);
-        // own nonspherical part: zeta_1^3/(8 pi) e^{-zeta_1 r} (1 - r^2/R^2)^2 sum c_lm (r/R)^l y_lm
         if (r < Ra) {
-            const double z1 = ra[7], w = Q[3] / y00, s = r / Ra, tt = 1.0 - s * s;
-            double ang = 0.0, sl = s;
-            for (int lm = 1; lm < NLM; lm++) {
-                if (lm == 4 || lm == 9 || lm == 16) sl *= s;
-                ang += clm[24 * (size_t)a + lm - 1] * sl * (Q[3 + lm] / w);
-            }
-            rhod += z1 * z1 * z1 / (8.0 * 3.14159265358979323846) * exp(-z1 * r) * tt * tt * ang;
+            // quad[4..] = w_q y_lm(q): one division by w_q = quad[3] / y_00 per point
+            double ang = 0.0;
+            for (int lm = 1; lm < NLM; lm++) ang = fma(cs[lm], Q[3 + lm], ang);
+            rhod += ang * (y00 / Q[3]);
         }
         rq[q] = rhod;
     }
