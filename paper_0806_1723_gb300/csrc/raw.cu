@@ -94,20 +94,30 @@ __global__ void __launch_bounds__(256) k_raw_deposit(RawArgs a, const double* __
                                                     double* __restrict__ b, int* __restrict__ owner,
                                                     int* __restrict__ status)
 {
-    const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
-    const size_t P = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    // per atom, once per block: the FP32 position and the FP32 sphere-test bound (the node loop
+    // then needs no FP64 conversion)
+    extern __shared__ float4 raw_at[];
+    for (int t = threadIdx.x; t < a.na; t += blockDim.x) {
+        const double* o = rec + (size_t)RAW_REC * t;
+        const float R2f = (float)(o[3] * o[3]);
+        raw_at[t] = make_float4((float)o[0], (float)o[1], (float)o[2], R2f * (1.0f + 1e-4f));
+    }
+    __syncthreads();
+    const unsigned N = (unsigned)a.n[0] * a.n[1] * a.n[2];   // < 2^31 (checked where grids are accepted)
+    const unsigned P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= N) return;
-    const size_t nxy = (size_t)a.n[0] * a.n[1];
-    const int k = (int)(P / nxy), j = (int)((P - (size_t)k * nxy) / a.n[0]), i = (int)(P - (size_t)k * nxy - (size_t)j * a.n[0]);
+    const unsigned nxy = (unsigned)a.n[0] * a.n[1];
+    const int k = (int)(P / nxy), j = (int)((P - (unsigned)k * nxy) / a.n[0]), i = (int)(P - (unsigned)k * nxy - (unsigned)j * a.n[0]);
     const double x = a.ax[0][i], y = a.ax[1][j], z = a.ax[2][k];
     const float xf = (float)x, yf = (float)y, zf = (float)z;
     int own = -1;
     double r = 0.0;
     for (int t = 0; t < a.na; t++) {
+        const float4 c = raw_at[t];
+        const float dx = xf - c.x, dy = yf - c.y, dz = zf - c.z;
+        const float r2f = dx * dx + dy * dy + dz * dz;
+        if (r2f > c.w) continue;
         const double* o = rec + (size_t)RAW_REC * t;
-        const float dx = xf - (float)o[0], dy = yf - (float)o[1], dz = zf - (float)o[2];
-        const float r2f = dx * dx + dy * dy + dz * dz, R2f = (float)(o[3] * o[3]);
-        if (r2f > R2f * (1.0f + 1e-4f)) continue;
         const double ex = x - o[0], ey = y - o[1], ez = z - o[2];
         const double d = sqrt(ex * ex + ey * ey + ez * ez);
         if (d < o[3]) {
@@ -140,7 +150,13 @@ cudaError_t launch_raw_sphere_params(const RawArgs& a, double* rec, int* status,
 cudaError_t launch_raw_deposit(const RawArgs& a, const double* rec, double* b, int* owner, int* status, cudaStream_t s)
 {
     const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
-    k_raw_deposit<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(a, rec, b, owner, status);
+    const size_t smem = sizeof(float4) * (size_t)a.na;
+    if (smem > 200 * 1024 || N >= (size_t(1) << 31)) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_raw_deposit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_raw_deposit<<<(unsigned)((N + 255) / 256), 256, smem, s>>>(a, rec, b, owner, status);
     return cudaGetLastError();
 }
 
