@@ -92,7 +92,8 @@ typedef struct lasto_config {
     int max_batch;    /* largest number of clusters per solve call */
     int precision;    /* enum lasto_precision */
     int cycle;        /* enum lasto_cycle */
-    int nu1, nu2;     /* pre/post Gauss-Seidel sweeps per level (red+black = one sweep) */
+    int nu1, nu2;     /* pre/post Gauss-Seidel sweeps per level (red+black = one sweep; the mixed
+                         precision's one-block coarse levels use nu_coarse) */
     int max_cycles;   /* cap on cycles / CG iterations */
     double rel_tol;   /* stop when ||b - A u||_2 <= rel_tol ||b_eff||_2 (b_eff: b with the faces moved in) */
     int n_theta;      /* Gauss-Legendre points in cos(theta) of the sphere quadrature (<= 32) */
@@ -102,12 +103,16 @@ typedef struct lasto_config {
                          synchronises once per iteration (for profilers that cannot see
                          kernels inside conditional graph nodes) */
     int boundary;     /* enum lasto_boundary: Dirichlet values on the box faces */
+    int nu_coarse;    /* pre/post sweeps per level on the coarse levels the FP32 cycle of the
+                         mixed precision runs inside one thread block (at most 17 nodes per axis,
+                         above the exact solve); >= 0.  The other levels use nu1/nu2. */
 } lasto_config;
 
 /* Fills cfg with the defaults: n_max 129, max_atoms 561, max_batch 1, FP64, PCG,
  * multipole faces, nu1 = nu2 = 4 (the fastest time to 1e-10 measured on GB300 for both precisions: more sweeps
- * per level cost less than the CG iterations and reductions they save), 50 cycles, rel_tol
- * 1e-10, 16 x 32 sphere points, graph launch. */
+ * per level cost less than the CG iterations and reductions they save), nu_coarse = 4 (1 keeps
+ * the Pd55 129^3 iteration count and shortens each cycle, but costs iterations on smaller
+ * grids), 50 cycles, rel_tol 1e-10, 16 x 32 sphere points, graph launch. */
 void lasto_config_default(lasto_config* cfg);
 
 typedef struct lasto_cluster {

@@ -420,8 +420,8 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
             a.b[q] = Arr<T>::b(P.lv[l + q]);
         }
         a.eig = P.eig;
-        a.nu1 = nu1;
-        a.nu2 = nu2;
+        a.nu1 = h->cfg.nu_coarse;   // one-block levels: their own (symmetric) sweep count
+        a.nu2 = h->cfg.nu_coarse;
         a.sym = sym ? 1 : 0;
         TRY(launch_bottom<T>(a, s));
         return LASTO_OK;
@@ -1044,6 +1044,7 @@ void lasto_config_default(lasto_config* c)
     c->n_phi = 32;
     c->launch = 0;
     c->boundary = LASTO_BC_MULTIPOLE;
+    c->nu_coarse = 4;
 }
 
 int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
@@ -1057,7 +1058,7 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
         cfg->n_theta < 1 || cfg->n_theta > 32 || cfg->n_phi < 1 || cfg->n_phi > 64 ||
         (cfg->precision != LASTO_PREC_FP64 && cfg->precision != LASTO_PREC_MIXED) ||
         (cfg->cycle != LASTO_CYCLE_V && cfg->cycle != LASTO_CYCLE_FV && cfg->cycle != LASTO_CYCLE_PCG) ||
-        (cfg->launch != 0 && cfg->launch != 1) ||
+        (cfg->launch != 0 && cfg->launch != 1) || cfg->nu_coarse < 0 || cfg->nu_coarse > 64 ||
         (cfg->boundary != LASTO_BC_MULTIPOLE && cfg->boundary != LASTO_BC_ZERO && cfg->boundary != LASTO_BC_EXACT))
         return LASTO_ERR_INVALID_ARG;
     lasto_poisson* h = new (std::nothrow) lasto_poisson();

@@ -268,3 +268,20 @@ def test_solve_boundary_choices(orc, bc, precision):
     assert st.status == 0 and st.rel_resid <= 1e-10
     ref = orc.poisson_solve(cl, tol=1e-13, max_cycles=200, bc=bc)["vlm"]
     assert np.abs(host(v) - ref).max() < 1e-8 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("nu_coarse", [0, 1, 4])
+def test_coarse_level_sweeps(orc, nu_coarse):
+    """The one-block coarse levels of the mixed-precision cycle with 0, 1 or 4 (default) sweeps:
+    the solve converges to the same V_LM (against the oracle)."""
+    B = need_gpu()
+    import torch
+    cl = synth.pd13_small(n=65)
+    dc = B.DeviceCluster(cl)
+    solver = B.Poisson(n_max=65, max_atoms=13, precision=B.LASTO_PREC_MIXED, nu_coarse=nu_coarse)
+    v = torch.empty((13, 25), dtype=torch.float64, device="cuda")
+    st = solver.solve(dc, v)[0]
+    torch.cuda.synchronize()
+    assert st.status == 0 and st.rel_resid <= 1e-10
+    ref = oracle_vlm(orc, cl)
+    assert np.abs(host(v) - ref).max() < 1e-8 * np.abs(ref).max()
