@@ -551,6 +551,10 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     const float far = FAR_T / zmin;
     const float far2 = far * far * (1.0f + 1e-4f);
     df s = {0.0f, 0.0f};
+    // the Slater terms beyond zeta r = FAR_T (each below e^-20 of its weight) summed in plain
+    // FP32 and added to the double-float sum once: their total is below 1e-6 of the node's
+    // density wherever that density matters, so FP32 rounding of it stays below 1e-13
+    float sfar = 0.0f;
     int own = -1;
     df orr2 = {0.0f, 0.0f}, odx = s, ody = s, odz = s;
     for (int q0 = 0; q0 < nkept; q0++) {
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
 #pragma unroll
             for (int q = 0; q < 3; q++) {
                 const float e = zt[q].h * rf;
-                if (e < EXP_CUT) s = dfa::add_f(s, o[6 + 2 * q] * expf(-e));
+                if (e < EXP_CUT) sfar = fmaf(o[6 + 2 * q], expf(-e), sfar);
             }
             continue;
         }
@@ -593,7 +597,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
             const df tq = dfa::mul(r, zt[q]);
             if (tq.h >= EXP_CUT) continue;
             if (tq.h > FAR_T) {
-                s = dfa::add_f(s, o[6 + 2 * q] * expf(-tq.h));
+                sfar = fmaf(o[6 + 2 * q], expf(-tq.h), sfar);
             } else {
                 // zeta_q = 2 zeta_0 (as in the density model's 1.5, 3.0): e^{-zeta_q r} = (e^{-zeta_0 r})^2
                 const df eq = (q > 0 && twice[q] && have0) ? dfa::sqr(e0) : dfa::exp_neg(tq, th, tl);
@@ -655,6 +659,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
         const df nsv = dfa::mul(radial, ang);
         s = dfa::add(dfa::add(s, dfa::neg(nbr)), dfa::add(pseudo, nsv));
     }
+    s = dfa::add_f(s, sfar);
     const df fourpi = dfa::from_double(4.0 * PI);
     const double bv = dfa::to_double(dfa::mul(fourpi, s));
     a.b[P] = bv;
