@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
         const double* Q = quad + 28 * (size_t)q;
         const df px = dfa::from_double(r * Q[0]), py = dfa::from_double(r * Q[1]), pz = dfa::from_double(r * Q[2]);
         df rho = {0.0f, 0.0f};
+        float rfar = 0.0f;   // the terms beyond zeta d = SD_FAR in plain FP32, added once below
         for (int t = 0; t < na; t++) {
             const float* o = sd_sm + 12 * t;
             const float fx = (px.h - o[0]) + (px.l - o[1]), fy = (py.h - o[2]) + (py.l - o[3]);
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
                     const float e = zt[c].h * rf;
-                    if (e < (float)SD_EXP_CUT) rho = dfa::add_f(rho, o[6 + 2 * c] * expf(-e));
+                    if (e < (float)SD_EXP_CUT) rfar = fmaf(o[6 + 2 * c], expf(-e), rfar);
                 }
                 continue;
             }
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
                 const df e = dfa::mul(d, zt[c]);
                 if (e.h >= (float)SD_EXP_CUT) continue;
                 if (e.h > SD_FAR) {
-                    rho = dfa::add_f(rho, o[6 + 2 * c] * expf(-e.h));
+                    rfar = fmaf(o[6 + 2 * c], expf(-e.h), rfar);
                 } else {
                     // zeta_c = 2 zeta_0: e^{-zeta_c d} = (e^{-zeta_0 d})^2
                     const df ec = (c > 0 && twice[c] && have0) ? dfa::sqr(e0) : dfa::exp_neg(e, tab.h, tab.l);
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(SD_NT) k_sphere_density(int na, const double* 
                 }
             }
         }
-        double rhod = dfa::to_double(rho);
+        double rhod = dfa::to_double(dfa::add_f(rho, rfar));
         if (r < Ra) {
             // quad[4..] = w_q y_lm(q): one division by w_q = quad[3] / y_00 per point
             double ang = 0.0;
