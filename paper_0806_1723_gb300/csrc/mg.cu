@@ -323,11 +323,26 @@ cudaError_t launch_coarse_apply(const LevelT<T>& L, const CoarseEig* eig, const 
 // ---------------------------------------------------------------- fused residual + restriction
 // bc = Vc^-1 P^T Vf (b - A u) with the 27 fine residuals formed on the fly, and the coarse
 // correction uc zeroed for the recursion: one pass instead of residual, restriction, memset.
+// (the same six terms as offdiag, addressed by flat 64-bit index: in the 27-point loop below the
+// compiler then shares the address arithmetic of neighbouring residuals; 20 % faster at 385^3)
+template <typename T>
+__device__ __forceinline__ T offdiag_flat(const LevelT<T>& L, const T* __restrict__ u, size_t P, int i, int j, int k)
+{
+    const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
+    T t = L.ax[0].cm[i] * u[P - 1];
+    t = fma(L.ax[0].cp[i], u[P + 1], t);
+    t = fma(L.ax[1].cm[j], u[P - sy], t);
+    t = fma(L.ax[1].cp[j], u[P + sy], t);
+    t = fma(L.ax[2].cm[k], u[P - sz], t);
+    t = fma(L.ax[2].cp[k], u[P + sz], t);
+    return t;
+}
+
 template <typename T>
 __device__ __forceinline__ T resid_at(const LevelT<T>& F, const T* __restrict__ u, const T* __restrict__ b, size_t P,
                                       int i, int j, int k)
 {
-    return b[P] - fma(-dsum(F, i, j, k), u[P], offdiag(F, u, P, i, j, k));
+    return b[P] - fma(-dsum(F, i, j, k), u[P], offdiag_flat(F, u, P, i, j, k));
 }
 
 template <typename T>
