@@ -24,7 +24,8 @@
  *     u -> +Z/r near a bare nucleus (the sign of Eq. 2.6).
  *   - Grids: n[0]*n[1]*n[2] nodes, x-fastest, index (k*n[1] + j)*n[0] + i, FP64.
  *     Nodes on the six faces carry Dirichlet values.  n[a] is odd and coarsens
- *     (n+1)/2 repeatedly to at most 9 nodes per axis.
+ *     (n+1)/2 repeatedly to at most 9 nodes per axis; a grid holds fewer than 2^31
+ *     nodes (the kernels index with 31 bits; larger grids are INVALID_ARG).
  *   - Atoms: pos[n_atoms][3], Z[n_atoms], R[n_atoms], slater_w[n_atoms][3]
  *     (electrons in each normalised Slater term zeta^3/(8 pi) e^{-zeta r}),
  *     slater_zeta[n_atoms][3] (the same three exponents for every atom of a
