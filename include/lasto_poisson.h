@@ -308,8 +308,11 @@ int lasto_op_deposit(const lasto_cluster* cl, int precision, double* b, int* own
  * in one file-scope device array sized for 1024 atoms (384 KiB, held by every device
  * that loads the library until exit) instead of allocator scratch.  No cudaMalloc,
  * cudaFree or allocating library routine is called.
- * Errors: INVALID_ARG when n_atoms > 1024 (or as lasto_op_deposit), CUDA when the
- * array's device address cannot be found.
+ * b (and owner, when given) must hold N = n0 n1 n2 elements: the entry point takes no
+ * lengths and writes all N.  status may be NULL; when given, the caller zeroes it first
+ * (the kernels only raise it, so a stale nonzero value would be carried into the result).
+ * Errors: INVALID_ARG when n_atoms > 1024 (or as lasto_op_deposit, grid checks included),
+ * CUDA when the array's device address cannot be found or a launch fails.
  * The first call on each device looks up that address (and uploads the constant tables)
  * with the device current; make that first call before any stream capture.  Every call
  * shares the one array: calls that overlap on the GPU (two streams, or two host threads)
@@ -366,6 +369,34 @@ int lasto_op_smooth_slab(const int n[3], const double* x, const double* y, const
 int lasto_op_smooth_slab_f32(const int n[3], const double* x, const double* y, const double* z, const float* u_in,
                              float* u_out, const float* b, int sweeps, int ns, int first, const int tile[3],
                              void* stream);
+
+/* Red-black Gauss-Seidel (Section 3) as fused FP32 passes, one full sweep per pass, each
+ * walking z as a wavefront over row chunks staged in shared memory: the first colour of
+ * plane k+1, then the other colour of plane k.  `sweeps` sweeps, each colour `first` (0 =
+ * red, i+j+k even) then the other, from u_in into u_out (distinct, 16-byte aligned device
+ * arrays [n0*n1*n2], x fastest; u_in unchanged; every node of u_out written, faces copied).
+ * Bitwise the result of `sweeps` in-place sweeps.  tx (16..60) columns and ty (8, 12 or 16)
+ * rows per thread-block tile (any tile gives the same result); rows of at least 69 nodes.
+ * More than one sweep takes one device scratch grid from the stream-ordered allocator.
+ * INVALID_ARG for sweeps < 1, a bad tile, a short row, misaligned arrays or u_in == u_out. */
+int lasto_op_smooth_wave_f32(const int n[3], const double* x, const double* y, const double* z, const float* u_in,
+                             float* u_out, const float* b, int sweeps, int first, int tx, int ty, void* stream);
+
+/* Self-test of the bounded device waits (the paper has no counterpart).  The staged
+ * tensor-core kernels (the H/S contraction, the convolution of the learned guess) wait on
+ * mbarriers with a time limit and, when it runs out, raise
+ * LASTO_ERR_TIMEOUT in a device status and return instead of hanging.  This entry launches
+ * one thread that waits on an mbarrier nothing ever arrives at, for `seconds` (0 < s <= 60),
+ * and then raises *status (device int, caller-zeroed) to LASTO_ERR_TIMEOUT the same way.
+ * Asynchronous on the stream; the stream stays usable afterwards. */
+int lasto_selftest_bounded_wait(double seconds, int* status, void* stream);
+
+/* Arithmetic throughput probe (the paper has no counterpart): `blocks` blocks of 256
+ * threads, each thread 8 independent fused multiply-add chains of 16 * iters steps, in FP64
+ * (precision 0) or FP32 (precision 1); out: device array of blocks * 256 elements of that
+ * type (written, so nothing is folded away).  Work: 2 * 8 * 16 * iters FLOP per thread.  It
+ * measures the ALU ceilings the roofline of the ALU-bound kernels is stated against. */
+int lasto_probe_fma(int precision, int blocks, int iters, void* out, void* stream);
 
 /* Full weighting bc = Vc^-1 P^T Vf r onto the every-other-node mesh; bc device
  * [(n0+1)/2 * (n1+1)/2 * (n2+1)/2], faces set to 0.  x, y, z are the fine axes. */

@@ -56,7 +56,8 @@ EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve"
            "lasto_poisson_last_error", "lasto_poisson_kernel_counts", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
            "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_boundary_exact", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
-           "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
+           "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_smooth_wave_f32", "lasto_selftest_bounded_wait",
+           "lasto_probe_fma", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
            "lasto_op_project", "lasto_op_sphere_density", "lasto_op_inner_solve", "lasto_op_interstitial_hs", "lasto_guess_param_count", "lasto_poisson_set_guess",
            "lasto_poisson_tune_table", "lasto_poisson_set_tune_table", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
            "lasto_nn_relu_grad", "lasto_nn_to_bf16", "lasto_nn_copy_channels", "lasto_nn_down", "lasto_nn_up",
@@ -99,6 +100,9 @@ def _declare(L):
         "lasto_op_smooth_f32": (i, [ip, vp, vp, vp, vp, vp, i, i, vp]),
         "lasto_op_smooth_slab": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, ip, vp]),
         "lasto_op_smooth_slab_f32": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, ip, vp]),
+        "lasto_op_smooth_wave_f32": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, i, vp]),
+        "lasto_selftest_bounded_wait": (i, [d, vp, vp]),
+        "lasto_probe_fma": (i, [i, i, i, vp, vp]),
         "lasto_op_restrict": (i, [ip, vp, vp, vp, vp, vp, vp]),
         "lasto_op_prolong_add": (i, [ip, vp, vp, vp, vp, vp, vp]),
         "lasto_op_coarse_solve": (i, [ip, vp, vp, vp, vp, vp, vp]),
@@ -345,8 +349,30 @@ def lasto_op_deposit(dc: DeviceCluster, precision=LASTO_PREC_FP64, stream=None):
     return b, owner, status
 
 
+def _check_buffer(t, name, dtype, count, device):
+    """A caller buffer the C ABI writes without a length: checked here, before any launch."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: a torch tensor is required")
+    if not t.is_cuda or t.device != device:
+        raise ValueError(f"{name}: must live on {device}, got {t.device}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {dtype} required, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() < count:
+        raise ValueError(f"{name}: at least {count} elements required, got {t.numel()}")
+
+
 def lasto_op_deposit_noalloc(dc: DeviceCluster, b, owner=None, status=None, precision=LASTO_PREC_FP64, stream=None):
-    """Allocation-free deposit into caller buffers b (float64 [N]) and optional owner / status."""
+    """Allocation-free deposit into caller buffers: b (float64, >= N elements), optional owner
+    (int32, >= N) and status (int32, >= 1, zeroed by the caller: the kernels only raise it).
+    The buffers are checked here because the C entry point takes no lengths."""
+    dev = dc.pos.device
+    _check_buffer(b, "b", torch.float64, dc.N, dev)
+    if owner is not None:
+        _check_buffer(owner, "owner", torch.int32, dc.N, dev)
+    if status is not None:
+        _check_buffer(status, "status", torch.int32, 1, dev)
     c = dc.struct()
     _check(load().lasto_op_deposit_noalloc(ctypes.byref(c), int(precision), _ptr(b), _ptr(owner), _ptr(status),
                                            _stream(stream)), "lasto_op_deposit_noalloc")
@@ -399,6 +425,34 @@ def lasto_op_smooth_slab(x, y, z, u_in, u_out, b, sweeps=None, ns=1, first=0, ti
     _check(fn(*_axes(x, y, z), _ptr(u_in), _ptr(u_out), _ptr(b), int(sweeps), int(ns), int(first), _n3(tile),
               _stream(stream)), "lasto_op_smooth_slab")
     return u_out
+
+
+def lasto_op_smooth_wave(x, y, z, u_in, u_out, b, sweeps=1, first=0, tile=(60, 16), stream=None):
+    """`sweeps` FP32 red-black sweeps from u_in into u_out as z-wavefront passes (one sweep each)."""
+    _check(load().lasto_op_smooth_wave_f32(*_axes(x, y, z), _ptr(u_in), _ptr(u_out), _ptr(b), int(sweeps), int(first),
+                                           int(tile[0]), int(tile[1]), _stream(stream)),
+           "lasto_op_smooth_wave_f32")
+    return u_out
+
+
+def lasto_selftest_bounded_wait(seconds, status, stream=None):
+    """One device thread waits on an mbarrier nothing arrives at for `seconds`, then raises
+    status (int32 device tensor) to LASTO_ERR_TIMEOUT."""
+    _check_buffer(status, "status", torch.int32, 1, status.device)
+    _check(load().lasto_selftest_bounded_wait(float(seconds), _ptr(status), _stream(stream)),
+           "lasto_selftest_bounded_wait")
+    return status
+
+
+PROBE_FLOP_PER_THREAD_ITER = 2 * 8 * 16
+
+
+def lasto_probe_fma(precision, blocks, iters, out, stream=None):
+    """FMA-chain throughput probe; out: float64 (precision 0) or float32 (1) tensor of blocks*256."""
+    _check_buffer(out, "out", torch.float64 if precision == 0 else torch.float32, blocks * 256, out.device)
+    _check(load().lasto_probe_fma(int(precision), int(blocks), int(iters), _ptr(out), _stream(stream)),
+           "lasto_probe_fma")
+    return out
 
 
 def lasto_op_restrict(x, y, z, r, stream=None):

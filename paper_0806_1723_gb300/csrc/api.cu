@@ -57,8 +57,9 @@ struct Carver {
     }
 };
 
-// How one level is smoothed: in-place half sweeps (block size nt) or fused passes of the
-// z-slab / register-column kernels (shape sh) ping-ponging with a partner array.
+// How one level is smoothed: in-place half sweeps (block size nt) or fused passes ping-ponging
+// with a partner array: fused = 1, the z-slab / register-column kernels (shape sh); fused = 2,
+// the FP32 wavefront sweep over bulk-copied row chunks (sh.tx columns, sh.ty rows).
 struct SmoothChoice {
     int fused = 0;
     int nt = 256;
@@ -283,9 +284,20 @@ struct Arr<float> {
 // `cur` into the other of {home, partner}; cur follows the data.
 template <typename T>
 cudaError_t smooth(const LevelT<T>& V, T*& cur, T* partner, T* home, const T* b, int nu, int first,
-                   const SmoothChoice& ch, cudaStream_t s)
+                   const SmoothChoice& ch, int* status, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
+    if (ch.fused == 2) {
+        if constexpr (sizeof(T) == 4) {
+            for (int m = 0; m < nu && e == cudaSuccess; m++) {
+                T* dst = cur == home ? partner : home;
+                e = launch_rb_wave(V, cur, dst, b, first, ch.sh, s);
+                cur = dst;
+            }
+            return e;
+        }
+        return cudaErrorInvalidValue;
+    }
     if (!ch.fused) {
         for (int it = 0; it < nu && e == cudaSuccess; it++) {
             e = launch_rbgs<T>(V, cur, b, first, s, ch.nt);
@@ -312,6 +324,7 @@ int fused_passes(int nu, int ns) { return nu / ns + (nu % ns ? 1 : 0); }
 bool choice_usable(const lasto_poisson* h, const SmoothChoice& c, size_t elem)
 {
     if (!c.fused) return c.nt == 0 || (c.nt >= 32 && c.nt <= 512 && c.nt % 32 == 0);
+    if (c.fused == 2) return elem == 4 && wave_shape_ok(c.sh) && (h->cfg.nu1 + h->cfg.nu2) % 2 == 0;
     // the pre- and post-smoothing passes together must return the data to its home array
     return slab_shape_ok(c.sh, elem) && (fused_passes(h->cfg.nu1, c.sh.ns) + fused_passes(h->cfg.nu2, c.sh.ns)) % 2 == 0;
 }
@@ -363,6 +376,14 @@ int tune_level(lasto_poisson* h, LevelStore& S, cudaStream_t st)
         c.sh = sh;
         cand.push_back(c);
     }
+    if (f32 && wave_level_ok(S.n[0], S.n[1], S.n[2]))
+        for (int ty : {8, 16})
+            for (int tx : {48, 60}) {
+                SmoothChoice c;
+                c.fused = 2;
+                c.sh = SlabShape{tx, ty, 8, 1};
+                cand.push_back(c);
+            }
     cudaEvent_t e0, e1;
     TRY(cudaEventCreate(&e0));
     TRY(cudaEventCreate(&e1));
@@ -371,9 +392,10 @@ int tune_level(lasto_poisson* h, LevelStore& S, cudaStream_t st)
     for (const SmoothChoice& c : cand) {
         if (!choice_usable(h, c, sizeof(T))) continue;
         T* cur = u;
-        cudaError_t e = smooth<T>(V, cur, partner, u, b, h->cfg.nu1, 0, c, st);   // warm
+        cudaError_t e = smooth<T>(V, cur, partner, u, b, h->cfg.nu1, 0, c, nullptr, st);   // warm
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        for (int r = 0; r < 3 && e == cudaSuccess; r++) e = smooth<T>(V, cur, partner, u, b, h->cfg.nu1, 0, c, st);
+        for (int r = 0; r < 3 && e == cudaSuccess; r++)
+            e = smooth<T>(V, cur, partner, u, b, h->cfg.nu1, 0, c, nullptr, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
@@ -437,7 +459,7 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
     }
     const SmoothChoice ch = smooth_choice<T>(h, S);
     T* cur = u;   // fused passes move the iterate between u and the partner array
-    TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu1, 0, ch, s));
+    TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu1, 0, ch, P.status, s));
     LevelStore& C = P.lv[l + 1];
     const LevelT<T> VC = Arr<T>::view(C);
     if (sizeof(T) == 4) {
@@ -456,7 +478,7 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
         if (st) return st;
     }
     TRY(launch_prolong_add<T>(V, VC, Arr<T>::u(C), cur, s));
-    TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu2, sym ? 1 : 0, ch, s));
+    TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu2, sym ? 1 : 0, ch, P.status, s));
     if (cur != u) return fail(h, LASTO_ERR_INVALID_ARG, "smoother passes do not return to the level array");
     return LASTO_OK;
 }
@@ -1339,16 +1361,6 @@ struct OpLevel {
     bool ok() const { return mem.p != nullptr; }
 };
 
-int op_status(cudaError_t e) { return e == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA; }
-
-bool op_grid_ok(const int n[3], const double* x, const double* y, const double* z)
-{
-    if (!n || !x || !y || !z) return false;
-    for (int d = 0; d < 3; d++)
-        if (n[d] < 3 || n[d] % 2 == 0) return false;
-    return (size_t)n[0] * n[1] * n[2] < (size_t(1) << 31);   // kernels index with 31 bits
-}
-
 }  // namespace
 
 template <typename T>
@@ -1509,6 +1521,42 @@ int lasto_op_smooth_slab_f32(const int n[3], const double* x, const double* y, c
                              void* stream)
 {
     return op_smooth_slab<float>(n, x, y, z, u_in, u_out, b, sweeps, ns, first, tile, stream);
+}
+
+int lasto_op_smooth_wave_f32(const int n[3], const double* x, const double* y, const double* z, const float* u_in,
+                             float* u_out, const float* b, int sweeps, int first, int tx, int ty, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !u_in || !u_out || !b || u_in == u_out || sweeps < 1) return LASTO_ERR_INVALID_ARG;
+    const SlabShape sh{tx, ty, 8, 1};
+    if (!wave_shape_ok(sh) || !wave_level_ok(n[0], n[1], n[2])) return LASTO_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(u_in) | reinterpret_cast<uintptr_t>(u_out) | reinterpret_cast<uintptr_t>(b)) & 15)
+        return LASTO_ERR_INVALID_ARG;
+    init_device_constants();
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, false, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    Scratch tmp(sweeps > 1 ? sizeof(float) * (size_t)n[0] * n[1] * n[2] : 0, s);
+    if (sweeps > 1 && !tmp.p) return LASTO_ERR_NO_MEMORY;
+    const float* src = u_in;
+    cudaError_t e = cudaSuccess;
+    for (int m = 1; m <= sweeps && e == cudaSuccess; m++) {
+        float* dst = ((sweeps - m) % 2 == 0) ? u_out : tmp.as<float>();   // the last pass lands in u_out
+        e = launch_rb_wave(L.S.view32(), src, dst, b, first & 1, sh, s);
+        src = dst;
+    }
+    return op_status(e);
+}
+
+int lasto_selftest_bounded_wait(double seconds, int* status, void* stream)
+{
+    if (!status || !(seconds > 0.0) || seconds > 60.0) return LASTO_ERR_INVALID_ARG;
+    return op_status(launch_wait_selftest((unsigned long long)(seconds * 1e9), status, (cudaStream_t)stream));
+}
+
+int lasto_probe_fma(int precision, int blocks, int iters, void* out, void* stream)
+{
+    if ((precision != 0 && precision != 1) || blocks < 1 || iters < 1 || !out) return LASTO_ERR_INVALID_ARG;
+    return op_status(launch_fma_probe(precision, blocks, iters, out, (cudaStream_t)stream));
 }
 
 int lasto_op_restrict(const int n[3], const double* x, const double* y, const double* z, const double* r, double* bc,

@@ -20,6 +20,8 @@
 #include <cmath>
 
 #include "df.cuh"
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace lasto {
@@ -82,13 +84,21 @@ void host_solid_harmonics(double x, double y, double z, double* S)
     for (int i = 0; i < N_MONO_TERMS; i++) S[t[i].lm] += t[i].coef * px[t[i].a] * py[t[i].b] * pz[t[i].c];
 }
 
-static int g_mono_uploaded_device = -1;
+// Constant tables are per device: each device gets its own upload, once, with that device
+// current (a flag per device, so alternating devices uploads nothing again).
+constexpr int MAX_DEVICES = 64;
+static bool g_mono_uploaded[MAX_DEVICES] = {};
+static bool g_constants_done[MAX_DEVICES] = {};
+static std::mutex g_constants_mutex;
+
 static cudaError_t ensure_monomials()
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (g_mono_uploaded_device == dev) return cudaSuccess;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_constants_mutex);
+    if (g_mono_uploaded[dev]) return cudaSuccess;
     Mono t[N_MONO_TERMS];
     host_monomials(t);
     e = cudaMemcpyToSymbol(c_mono, t, sizeof(t));
@@ -112,7 +122,7 @@ static cudaError_t ensure_monomials()
     }
     e = cudaMemcpyToSymbol(c_exp_h, eh, sizeof(eh));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_exp_l, el, sizeof(el));
-    if (e == cudaSuccess) g_mono_uploaded_device = dev;
+    if (e == cudaSuccess) g_mono_uploaded[dev] = true;
     return e;
 }
 
@@ -669,15 +679,20 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
 
 void init_device_constants()
 {
-    static int done_dev = -1;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev == done_dev) return;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return;
+    {
+        std::lock_guard<std::mutex> lock(g_constants_mutex);
+        if (g_constants_done[dev]) return;
+    }
     ensure_monomials();
     cudaFuncSetAttribute(k_deposit64, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_deposit_df, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     init_mg_attributes();
     init_slab_attributes();
-    done_dev = dev;
+    init_wave_attributes();
+    std::lock_guard<std::mutex> lock(g_constants_mutex);
+    g_constants_done[dev] = true;
 }
 
 // ---------------------------------------------------------------- boundary multipoles

@@ -31,6 +31,19 @@ int set_cuda_error(Err* e, cudaError_t c, const char* what);
         if (c_ != cudaSuccess) return ::lasto::set_cuda_error(err, c_, #call); \
     } while (0)
 
+// Status of a single-operation entry point from the CUDA error of its launches.
+inline int op_status(cudaError_t e) { return e == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA; }
+
+// The grid conditions every single-operation entry point checks: three axis arrays, an odd
+// number (>= 3) of nodes per axis, and fewer than 2^31 nodes (kernels index with 31 bits).
+inline bool op_grid_ok(const int n[3], const double* x, const double* y, const double* z)
+{
+    if (!n || !x || !y || !z) return false;
+    for (int d = 0; d < 3; d++)
+        if (n[d] < 3 || n[d] % 2 == 0) return false;
+    return (size_t)n[0] * n[1] * n[2] < (size_t(1) << 31);
+}
+
 // ---------------------------------------------------------------- spherical harmonics
 // Real solid harmonics r^l y_lm as sums of monomials x^a y^b z^c (a+b+c = l <= 4).
 struct Mono {
@@ -205,6 +218,22 @@ void init_slab_attributes();   // shared-memory opt-in; call outside capture
 template <typename T>
 cudaError_t launch_rb_slab(const LevelT<T>& L, const T* uin, T* uout, const T* b, int first, int zero_in,
                            const SlabShape& sh, cudaStream_t s);
+
+// wave.cu: fused red-black sweep as a z wavefront over row chunks staged in shared memory
+// (FP32).  One pass = one full sweep (colour `first`, then the other), u_in -> u_out
+// (distinct, 16-byte aligned; every node of u_out written, faces copied).  Shape: tx (16..60)
+// columns and ty (8, 12 or 16) rows per tile, kz = 8 (the ring of staged planes); levels of at
+// least 69 nodes per row.
+bool wave_shape_ok(const SlabShape& sh);
+bool wave_level_ok(int nx, int ny, int nz);
+void init_wave_attributes();   // shared-memory opt-in; call outside capture
+cudaError_t launch_rb_wave(const LevelT<float>& L, const float* uin, float* uout, const float* b, int first,
+                           const SlabShape& sh, cudaStream_t s);
+// probe.cu: one thread waits on an mbarrier nothing arrives at, for limit_ns, then raises TIMEOUT
+cudaError_t launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t s);
+
+// probe.cu: arithmetic throughput probes (FMA chains on every SM)
+cudaError_t launch_fma_probe(int precision, int blocks, int iters, void* out, cudaStream_t s);
 
 // Levels lb..L-1 of a V-cycle in one thread block (u[0] = 0 on entry).
 constexpr int BOTTOM_MAX_LEVELS = 4;

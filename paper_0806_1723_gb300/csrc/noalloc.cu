@@ -47,9 +47,8 @@ int records_address(double** out)
 extern "C" int lasto_op_deposit_noalloc(const lasto_cluster* cl, int precision, double* b, int* owner, int* status,
                                         void* stream)
 {
-    if (!cl || !b || cl->n_atoms < 1 || !cl->x || !cl->y || !cl->z) return LASTO_ERR_INVALID_ARG;
-    for (int d = 0; d < 3; d++)
-        if (cl->n[d] < 3 || cl->n[d] % 2 == 0) return LASTO_ERR_INVALID_ARG;
+    // the same grid checks as lasto_op_deposit, then the array's atom limit
+    if (!cl || !b || cl->n_atoms < 1 || !lasto::op_grid_ok(cl->n, cl->x, cl->y, cl->z)) return LASTO_ERR_INVALID_ARG;
     if (cl->n_atoms > LASTO_NOALLOC_MAX_ATOMS) return LASTO_ERR_INVALID_ARG;
     if (precision != LASTO_PREC_FP64 && precision != LASTO_PREC_MIXED) return LASTO_ERR_INVALID_ARG;
     double* rec = nullptr;
@@ -60,5 +59,5 @@ extern "C" int lasto_op_deposit_noalloc(const lasto_cluster* cl, int precision, 
     cudaError_t e = lasto::launch_sphere_params(*cl, cl->x, cl->y, cl->z, rec, nullptr, nullptr, nullptr, nullptr,
                                                 status, s);
     if (e == cudaSuccess) e = lasto::launch_deposit(*cl, rec, precision, b, owner, nullptr, nullptr, status, s);
-    return e == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
+    return lasto::op_status(e);
 }
