@@ -3,20 +3,30 @@
 
 Metric: converged Poisson solves per second (relative residual <= 1e-10).  One solve =
 density, pseudo-density deposit, boundary multipoles, faces, iteration to 1e-10, sphere
-projection, for a Pd55 Mackay icosahedron on the graded 129^3 mesh (0.12 -> 0.6 bohr,
-10 bohr vacuum) with a seeded synthetic Slater-model density.
+projection (V_LM, Eq. 3.6).
 
-`value` is the chosen form: 8 such clusters (density seeds 1..8) per call, solved as
-independent branches of one CUDA graph, each started from the learned guess (the U-Net
-runs inside the graph, once for the batch), with FP64 defect correction around FP32
-multigrid-preconditioned CG and the FP32-pair density deposit.  A step is one batch of 8
-solves.  The plain form (one cluster per call, zero start, FP64 throughout) is timed in the
-same clock-sampled region and reported beside it, as are the forms between the two.  The
-working set fits the 129 MB L2, so L2 is flushed (a 512 MiB write) before every timed step
-and each step is timed alone with CUDA events on the launch stream.
+`value` is the largest single-GPU workload: the Pd561 five-shell icosahedron on the graded
+385^3 mesh (57 M nodes, 0.12 -> 0.6 bohr, 10 bohr vacuum) with 8 SCF-like densities (seeded
+1 % perturbations of the Slater weights and nonspherical coefficients) solved back to back.
+A step is the sequence of 8 solves, in the chosen form: FP64 defect correction around FP32
+multigrid-preconditioned CG, FP32-pair density; the first density starts from the learned
+guess (the U-Net inside the solve's graph), each later one from the previous density's
+potential (an SCF loop has it).  The plain form (FP64 throughout, zero start) is timed beside
+it, and so are the other starts (zero, learned guess for every density).  Every result
+carries its error against the FP64 oracle: max |dV_LM| / max |V_LM| over the spheres, from
+the oracle's answers stored by tests/golden/make_oracle_vlm.py (null when that file is
+absent).  The working set (~6 GB) is far beyond L2; L2 is flushed anyway before each step.
+
+Extra keys: the former headline (8 Pd55 clusters on graded 129^3 in one graph launch), the
+uneven batch of 64 Pd13/Pd55/Pd147 clusters, the interstitial H and S contraction and the
+other rows beyond the Poisson step, the roofline of the dominant kernel (the FP32 smoother
+at 385^3), the arithmetic ceilings measured by the library's FMA probe, and the FP64 CPU
+oracle timed on a bounded sample of the same workload.
 
 `--impl reference` times the FP64 CPU oracle on the same workload and metric (the
-reference arm; the paper publishes no implementation or timing).
+reference arm; the paper publishes no implementation or timing), one bounded sample per
+step: the deposit on 4 planes of the 385^3 grid and one and two stationary V(2,2) cycles on
+the whole grid, extrapolated to a whole solve with the oracle's own cycle count to 1e-10.
 
 Multi-GPU: the step does not shard; N ranks run N independent replicas (weak scaling),
 value = solves of all ranks / max over ranks of the timed span.
@@ -34,34 +44,32 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+sys.path.insert(0, os.path.join(ROOT, "tests"))
 
 METRIC = "converged Poisson solves/sec (resid <=1e-10)"
 UNIT = "solves/s"
-WORKLOAD = ("Pd55 Mackay icosahedron, graded 129^3 (0.12->0.6 bohr, 10 bohr vacuum), synthetic Slater densities; "
-            "8 clusters (density seeds 1-8) per step")
-FORM = ("learned initial guess (U-Net in the graph) + FP64 defect correction around FP32 multigrid-preconditioned CG "
-        "+ FP32-pair density; 8 clusters per graph launch")
+SEQ = 8            # densities per step
+WORKLOAD = ("Pd561 5-shell icosahedron, graded 385^3 (57 M nodes; 0.12->0.6 bohr, 10 bohr vacuum), synthetic Slater "
+            "densities; 8 SCF-like densities (seed 4, 1% perturbations) solved back to back per step")
+FORM = ("FP64 defect correction around FP32 multigrid-preconditioned CG + FP32-pair density; first density from the "
+        "learned guess (U-Net in the graph), each later density warm-started from the previous potential")
+PD55_WORKLOAD = ("Pd55 Mackay icosahedron, graded 129^3 (0.12->0.6 bohr, 10 bohr vacuum); 8 clusters (density seeds "
+                 "1-8) per graph launch")
 BATCH = 8
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per half sweep at 257^3, one block per row, in
-# steady state (launches 5-8 of 4 sweeps, caches not flushed between launches, so each launch also
-# writes back what the one before left dirty in L2): mean of the four launches, by launch shape
-# (0 = one block per row, else threads per block).  FP32 rows: 130.3 MB read + 67.6 MB written,
-# flat 128: 129.3 + 66.3, flat 256: 129.5 + 66.3; FP64 rows: 403.3 + 134.5 MB.  A launch shape
-# without a capture reports null.
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch at 257^3 (steady state: launches 5-8
+# of a 4-sweep call, caches not flushed between launches), by launch shape: in-place half sweep
+# with one block per row (0) or 128 / 256 threads per block; the FP32 wavefront sweep ("wave").
+# Scaled to 385^3 by the node count (the traffic is proportional to the nodes beyond L2).
 DRAM_BYTES_257 = {0: 197.9e6, 128: 195.6e6, 256: 195.8e6}
 DRAM_BYTES_257_F64 = 537.7e6
-
-# FP64 FMA throughput of one GB300 (a DFMA chain over every SM, CUDA events: 1.19 TFLOP/s at
-# 1995 MHz); the copy and BF16 peaks come from the measured-peaks file
-FP64_TFLOPS = 1.19
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -167,46 +175,105 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-# ------------------------------------------------------------------ CPU oracle timing
-def oracle_solves(cl, n_solves, tol=1e-10):
-    import oracle
-    oracle.build()
-    t0 = time.perf_counter()
-    out = None
-    for _ in range(n_solves):
-        out = oracle.poisson_solve(cl, tol=tol, max_cycles=200)
-    dt = time.perf_counter() - t0
-    return dt, out
+# ------------------------------------------------------------------ oracle: stored answers and CPU timing
+def oracle_errors(group, clusters, vlm, first=0):
+    """max |dV_LM| / max |V_LM| of each cluster of a concatenated GPU V_LM against the oracle's
+    stored answer (clusters at positions first, first + 1, ... of the group); None when the
+    stored answers are absent."""
+    try:
+        from golden.make_oracle_vlm import stored_vlm
+    except ImportError:
+        return None
+    out, off = [], 0
+    try:
+        for q, cl in enumerate(clusters):
+            ref = stored_vlm(group, cl, first + q)
+            out.append(float(abs(vlm[off:off + cl.n_atoms] - ref).max() / abs(ref).max()))
+            off += cl.n_atoms
+    except (FileNotFoundError, IndexError, KeyError):
+        return None
+    return out
+
+
+def oracle_cycles_to(tol, group="pd561", index=0, fallback=85):
+    """Stationary V(2,2) cycles the oracle needs to reach `tol` on a stored cluster (its residual
+    history), else `fallback`."""
+    try:
+        from golden.make_oracle_vlm import history
+        h = history(group, index)
+        return int(next(i for i, r in enumerate(h) if r <= tol)), "oracle residual history (stored)"
+    except (ImportError, FileNotFoundError, KeyError, StopIteration):
+        return fallback, "assumed"
 
 
 def oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+class OracleSample:
+    """A bounded sample of the oracle on the Pd561 workload: the deposit on `planes` planes at
+    the middle of the 385^3 grid, and one and two stationary V(2,2) cycles on the whole grid.
+    Extrapolated solve time = deposit per plane x 385 planes + cycles to 1e-10 x (t2 - t1) +
+    (2 t1 - t2) (the cycle's fixed part: norms, hierarchy set-up)."""
+
+    def __init__(self, planes=4):
+        import numpy as np
+
+        import oracle
+        import synth
+        oracle.build()
+        self.oracle, self.planes = oracle, planes
+        self.cl = synth.pd561_graded385(n_densities=1)[0]
+        self.x, self.y, self.z = oracle.mesh(self.cl)
+        n = self.cl.n
+        self.b = np.random.default_rng(0).normal(size=(n, n, n))
+        self.u = np.zeros((n, n, n))
+        self.cycles, self.cycles_source = oracle_cycles_to(1e-10)
+
+    def step(self):
+        n, k0 = self.cl.n, self.cl.n // 2 - self.planes // 2
+        t0 = time.perf_counter()
+        self.oracle.deposit(self.cl, self.x, self.y, self.z[k0:k0 + self.planes])
+        t1 = time.perf_counter()
+        self.u[...] = 0.0
+        self.oracle.mg_solve(self.x, self.y, self.z, self.b, self.u, max_cycles=1, tol=1e-30)
+        t2 = time.perf_counter()
+        self.u[...] = 0.0
+        self.oracle.mg_solve(self.x, self.y, self.z, self.b, self.u, max_cycles=2, tol=1e-30)
+        t3 = time.perf_counter()
+        dep = (t1 - t0) / self.planes * n
+        c1, c2 = t2 - t1, t3 - t2
+        cyc = max(c2 - c1, 1e-9)
+        solve = dep + self.cycles * cyc + max(2 * c1 - c2, 0.0)
+        return {"sample_s": t3 - t0, "solve_s": solve, "deposit_s": dep, "cycle_s": cyc}
+
+    def describe(self, steps):
+        return (f"{steps} samples of the Pd561 385^3 workload: deposit on {self.planes} planes (x385/{self.planes}) and "
+                f"1 and 2 stationary V(2,2) cycles on the whole grid; solve = deposit + {self.cycles} cycles to 1e-10 "
+                f"({self.cycles_source}) + the cycle's fixed part")
+
+
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle, one whole solve per step, on the host cores."""
+    """The reference arm: the FP64 CPU oracle on the host cores, a bounded sample per step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import synth
-    cl = synth.pd55_graded129()
+    smp = OracleSample()
     for _ in range(args.warmup):
-        oracle_solves(cl, 1)
-    times = []
-    out = None
-    for _ in range(args.steps):
-        dt, out = oracle_solves(cl, 1)
-        times.append(dt)
-    total = sum(times)
-    value = args.steps / total
+        smp.step()
+    res = [smp.step() for _ in range(args.steps)]
+    solve_s = statistics.median(r["solve_s"] for r in res)
+    value = 1.0 / solve_s
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * solve_s * SEQ,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "mesh": "129^3 graded", "precision": "f64 (CPU oracle, stationary V(2,2))",
-                   "l2": "n/a (CPU)", "cycles": out["cycles"], "rel_resid": out["rel_resid"]},
+        "config": {"workload": WORKLOAD, "precision": "f64 (CPU oracle, stationary V(2,2) to 1e-10)",
+                   "l2": "n/a (CPU)", "deposit_s": statistics.median(r["deposit_s"] for r in res),
+                   "cycle_s": statistics.median(r["cycle_s"] for r in res), "cycles": smp.cycles,
+                   "sample_s": statistics.median(r["sample_s"] for r in res)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                         "sample": f"{args.steps} whole solves of the workload (after {args.warmup} warm-up)"},
+                         "sample": smp.describe(args.steps)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -214,6 +281,39 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def _events(torch, stream):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def pd561_run(B, solvers, dcs, v, pot, start, stream, flush):
+    """One pass over the density sequence.  start 'warm': the first density from the learned
+    guess (solvers['learned']), each later one from the previous potential (solvers['warm']);
+    'learned': every density from the learned guess; 'zero': every density from zero
+    (solvers['zero']).  As in an SCF loop, each handle solves in one set of device arrays (its
+    slot, solvers[name + '_slot']) into which the next density's Slater weights and
+    nonspherical coefficients are copied on the device, so its captured graph is replayed.
+    Returns (ms of the pass, stats per density, V_LM per density)."""
+    import torch
+    flush.fill_(1.0)
+    e0, e1 = _events(torch, stream)
+    e0.record(stream)
+    stats, vl = [], []
+    for s, dc in enumerate(dcs):
+        name = "warm" if (start == "warm" and s > 0) else ("learned" if start in ("warm", "learned") else "zero")
+        slot = solvers[name + "_slot"]
+        slot.w.copy_(dc.w, non_blocking=True)
+        slot.clm.copy_(dc.clm, non_blocking=True)
+        if name == "warm":
+            st = solvers[name].solve(slot, v, potential=pot, guess=pot)
+        else:
+            st = solvers[name].solve(slot, v, potential=pot)
+        stats.append(st[0])
+        vl.append(v.clone())
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), [(x.cycles, x.outer, x.rel_resid, x.status, x.guess) for x in stats], vl
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -235,114 +335,97 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     B.load()
-
-    cls8 = [synth.pd55_graded129(seed=1 + k) for k in range(BATCH)]
-    cl = cls8[0]
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     launch = 1 if args.direct else 0
 
-    def make(precision, batch=1, guess=False):
-        s_ = B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, max_batch=batch, precision=precision, launch=launch)
-        if guess:
-            s_.set_guess()
-        return s_
-
-    dcs8 = [B.DeviceCluster(c) for c in cls8]
-    vlm8 = torch.empty((BATCH * cl.n_atoms, 25), dtype=torch.float64, device=dev)
-    dc = dcs8[0]
-    vlm = vlm8[:cl.n_atoms]
-
-    def timed(solver, dcs, out, steps, warmup):
-        """steps timed calls (L2 flushed before each); kernel launches counted from the graph."""
-        st = None
-        for _ in range(warmup):
-            st = solver.solve(dcs, out)
-        torch.cuda.synchronize()
-        assert all(x.status == 0 and x.rel_resid <= 1e-10 for x in st), [(x.status, x.rel_resid) for x in st]
-        fixed, per_it, per_out = solver.kernel_counts() if not args.direct else (0, 0, 0)
-        ms, launches = [], 0
-        for _ in range(steps):
-            flush.fill_(1.0)                       # evict the working set from L2
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = solver.solve(dcs, out)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            launches += fixed + sum(x.cycles * per_it + x.outer * per_out for x in st)
-            assert all(x.status == 0 and x.rel_resid <= 1e-10 for x in st)
-        return {"ms": ms, "launches": launches, "stats": list(st)}
-
-    def summary(r, nclusters):
-        st = r["stats"]
-        return {"value": nclusters * len(r["ms"]) / (sum(r["ms"]) / 1e3), "unit": UNIT,
-                "ms_per_call": sum(r["ms"]) / len(r["ms"]), "clusters_per_call": nclusters,
-                "cycles": [x.cycles for x in st], "outer": [x.outer for x in st],
-                "max_rel_resid": max(x.rel_resid for x in st), "learned_guess": [x.guess for x in st]}
-
-    plain = make(B.LASTO_PREC_FP64)
-    chosen = make(B.LASTO_PREC_MIXED, BATCH, guess=True)
+    # ---------------- the headline: Pd561 / graded 385^3, 8 SCF-like densities per step
+    seq = synth.pd561_graded385()
+    na, n = seq[0].n_atoms, seq[0].n
+    dcs = [B.DeviceCluster(c) for c in seq]
+    v = torch.empty((na, 25), dtype=torch.float64, device=dev)
+    pot = torch.empty(n ** 3, dtype=torch.float64, device=dev)
+    mk = lambda prec: B.Poisson(n_max=n, max_atoms=na, precision=prec, launch=launch)
+    solvers = {"learned": mk(B.LASTO_PREC_MIXED), "warm": mk(B.LASTO_PREC_MIXED),
+               "learned_slot": B.DeviceCluster(seq[0]), "warm_slot": B.DeviceCluster(seq[0])}
+    solvers["learned"].set_guess()
+    for _ in range(args.warmup):
+        pd561_run(B, solvers, dcs, v, pot, "warm", stream, flush)
+    torch.cuda.synchronize()
+    counts = {k: (solvers[k].kernel_counts() if not args.direct else (0, 0, 0)) for k in ("learned", "warm")}
     barrier(ws)
     torch.cuda.synchronize()
+    ms, launches, stats, vlms = [], 0, None, None
     with ClockSampler(local) as clk:
-        r_plain = timed(plain, dc, vlm, args.steps, args.warmup)
-        barrier(ws)
+        for _ in range(args.steps):
+            t, stats, vlms = pd561_run(B, solvers, dcs, v, pot, "warm", stream, flush)
+            ms.append(t)
+            for s, (c, o, _, _, _) in enumerate(stats):
+                f_, i_, o_ = counts["warm" if s else "learned"]
+                launches += f_ + c * i_ + o * o_
+            assert all(st == 0 and r <= 1e-10 for _, _, r, st, _ in stats), stats
         torch.cuda.synchronize()
-        r_chosen = timed(chosen, dcs8, vlm8, args.steps, args.warmup)
-        torch.cuda.synchronize()
         barrier(ws)
-    tuned = [line.split() for line in chosen.tune_table().strip().splitlines()]
-    smoother_choice = {f"{r[0]}x{r[1]}x{r[2]}/{'f32' if r[3] == '4' else 'f64'}":
-                       ((f"in-place half sweeps, {r[5]} threads" if r[5] != "0" else "in-place half sweeps, one block per row")
-                        if r[4] == "0" else
-                        f"fused {r[9]}-sweep passes, tile {r[6]}x{r[7]}x{r[8]}") + f" ({float(r[10]):.1f} us)"
-                       for r in tuned}
-    span_max = max_over_ranks(sum(r_chosen["ms"]), ws, dev)
-    value = (BATCH * args.steps * ws) / (span_max / 1e3)
-    plain_value = (args.steps * ws) / (max_over_ranks(sum(r_plain["ms"]), ws, dev) / 1e3)
+    span_max = max_over_ranks(sum(ms), ws, dev)
+    value = SEQ * args.steps * ws / (span_max / 1e3)
+    err = oracle_errors("pd561", seq, torch.cat(vlms).cpu().numpy())
+    tuned = solvers["warm"].tune_table().strip().splitlines()
 
-    # ---------------- the forms between plain and chosen (one factor at a time)
-    steps_b = max(3, args.steps // 4)
-    mixed1 = make(B.LASTO_PREC_MIXED)
-    forms = {"mixed_single": summary(timed(mixed1, dc, vlm, steps_b, 2), 1)}
-    mixed1.set_guess()
-    forms["mixed_learned_single"] = summary(timed(mixed1, dc, vlm, steps_b, 2), 1)
-    mixed1.close()
-    mixed8 = make(B.LASTO_PREC_MIXED, BATCH)
-    forms["mixed_batched"] = summary(timed(mixed8, dcs8, vlm8, steps_b, 2), BATCH)
-    mixed8.close()
+    # ---------------- the other starts at 385^3 (one pass each) and the plain FP64 form
+    starts = {"warm": {"ms_per_solve": sum(ms) / len(ms) / SEQ, "cycles": [c for c, *_ in stats],
+                       "defect_correction_steps": [o for _, o, *_ in stats],
+                       "oracle_error_max": max(err) if err else None}}
+    solvers["zero"], solvers["zero_slot"] = mk(B.LASTO_PREC_MIXED), B.DeviceCluster(seq[0])
+    for name in ("learned", "zero"):
+        pd561_run(B, solvers, dcs[:1], v, pot, name, stream, flush)          # capture, tuning
+        t, st_, vl = pd561_run(B, solvers, dcs, v, pot, name, stream, flush)
+        e_ = oracle_errors("pd561", seq, torch.cat(vl).cpu().numpy())
+        starts[name] = {"ms_per_solve": t / SEQ, "cycles": [c for c, *_ in st_],
+                        "defect_correction_steps": [o for _, o, *_ in st_],
+                        "oracle_error_max": max(e_) if e_ else None}
+    solvers["zero"].close()
+    plain = {"zero": mk(B.LASTO_PREC_FP64), "zero_slot": solvers["zero_slot"]}
+    pd561_run(B, plain, dcs[:1], v, pot, "zero", stream, flush)
+    pms, pst = [], None
+    for _ in range(2):
+        t, pst, pvl = pd561_run(B, plain, dcs[:1], v, pot, "zero", stream, flush)
+        pms.append(t)
+    plain_value = ws * len(pms) / (max_over_ranks(sum(pms), ws, dev) / 1e3)
+    perr = oracle_errors("pd561", seq[:1], pvl[0].cpu().numpy())
+    plain["zero"].close()
 
     # ---------------- end to end through the C ABI with host buffers (the chosen form)
     e2e = None
     if not args.no_e2e:
         fields = ("pos", "Z", "R", "slater_w", "slater_zeta", "c_lm")
         host = [{k: torch.as_tensor(np.ascontiguousarray(getattr(c, k), dtype=np.float64)).pin_memory()
-                 for k in fields} for c in cls8]
-        devbuf = [{k: torch.empty_like(v, device=dev) for k, v in hb.items()} for hb in host]
-        vlm_host = torch.empty((BATCH * cl.n_atoms, 25), dtype=torch.float64).pin_memory()
-        dces = []
-        for c, dbuf in zip(cls8, devbuf):
-            d = B.DeviceCluster(c)
-            d.pos, d.Z, d.R = dbuf["pos"], dbuf["Z"], dbuf["R"]
-            d.w, d.zeta, d.clm = dbuf["slater_w"], dbuf["slater_zeta"], dbuf["c_lm"]
-            d.x, d.y, d.z = (torch.empty(c.n, dtype=torch.float64, device=dev) for _ in range(3))
-            dces.append(d)
-        h2d = sum(v.numel() * v.element_size() for hb in host for v in hb.values())
+                 for k in fields} for c in seq]
+        # one set of device arrays per handle (as an SCF code keeps), filled from the host each solve
+        slots = {}
+        for name in ("learned", "warm"):
+            d = B.DeviceCluster(seq[0])
+            d.x, d.y, d.z = (torch.empty(n, dtype=torch.float64, device=dev) for _ in range(3))
+            slots[name] = (d, {"pos": d.pos, "Z": d.Z, "R": d.R, "slater_w": d.w, "slater_zeta": d.zeta,
+                               "c_lm": d.clm})
+        vlm_host = torch.empty((SEQ, na, 25), dtype=torch.float64).pin_memory()
+        h2d = sum(t_.numel() * t_.element_size() for hb in host for t_ in hb.values())
         d2h = vlm_host.numel() * vlm_host.element_size()
         lib = B.load()
 
         def e2e_step():
-            for hb, dbuf in zip(host, devbuf):
+            sts = []
+            for s, (c, hb) in enumerate(zip(seq, host)):
+                name = "warm" if s else "learned"
+                d, dbuf = slots[name]
                 for k in fields:
                     dbuf[k].copy_(hb[k], non_blocking=True)
-            for c, d in zip(cls8, dces):
                 for a, ax in enumerate((d.x, d.y, d.z)):
                     lib.lasto_mesh_axis(c.n, float(c.centre[a]), c.half_width, c.h_min, c.h_max, c.p_max,
                                         B._ptr(ax), None, B._stream(None))
-            st = chosen.solve(dces, vlm8)
-            vlm_host.copy_(vlm8, non_blocking=True)
-            return st
+                sv = solvers[name]
+                sts.append((sv.solve(d, v, potential=pot, guess=pot) if s else sv.solve(d, v, potential=pot))[0])
+                vlm_host[s].copy_(v, non_blocking=True)
+            return sts
 
         for _ in range(args.warmup):
             e2e_step()
@@ -350,71 +433,78 @@ def main():
         ms_e2e = []
         for _ in range(args.steps):
             flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1 = _events(torch, stream)
             e0.record(stream)
-            st = e2e_step()
+            sts = e2e_step()
             e1.record(stream)
             e1.synchronize()
             ms_e2e.append(e0.elapsed_time(e1))
-            assert all(x.status == 0 for x in st)
-        e2e_val = (BATCH * args.steps * ws) / (max_over_ranks(sum(ms_e2e), ws, dev) / 1e3)
-        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            assert all(x.status == 0 and x.rel_resid <= 1e-10 for x in sts)
+        e2e_err = oracle_errors("pd561", seq, vlm_host.reshape(SEQ * na, 25).numpy())
+        e2e_val = SEQ * args.steps * ws / (max_over_ranks(sum(ms_e2e), ws, dev) / 1e3)
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "oracle_error_max": max(e2e_err) if e2e_err else None}
+        del slots
+    for k in ("learned", "warm"):
+        solvers[k].close()
+    del dcs, v, pot, solvers
+    torch.cuda.empty_cache()
+
+    # ---------------- the former headline: 8 Pd55 clusters per graph launch, and its forms
+    pd55 = pd55_forms(B, synth, flush, stream, dev, args, launch)
 
     # ---------------- the uneven batch of 64 (Pd13/55/147 on 65^3 .. 193^3), chosen form
     b64 = None
     if not args.no_batch64:
-        b64 = batch_throughput(B, synth.batch64(), B.LASTO_PREC_MIXED, 2, flush, stream, dev, warmup=1, guess=True)
+        b64 = batch_throughput(B, synth.batch64(), B.LASTO_PREC_MIXED, 2, flush, stream, dev, warmup=1, guess=True,
+                               group="batch64")
 
-    # ---------------- Pd561 on the graded 385^3 mesh: 8 SCF-like densities back to back
-    pd561 = None
-    if not args.no_pd561:
-        pd561 = pd561_sequence(B, synth, flush, stream, dev)
-
-    # ---------------- the interstitial H and S contraction (Eq. 3.11-3.14)
-    hs = None
+    # ---------------- the interstitial H and S contraction (Eq. 3.11-3.14) and the other rows
+    hs = rows = None
     if not args.no_hs:
         hs = interstitial_hs(B, synth, flush, stream, dev)
-
-    # ---------------- the inner Dirichlet problem, exact faces and raw-density deposit
-    rows = None
-    if not args.no_hs:
         rows = next_rows(B, synth, flush, stream, dev)
 
-    # ---------------- roofline of the dominant kernel (FP32 red-black half sweep)
-    roof = smoother_roofline(B, stream, flush, dev)
-    roof["deposit_fp32pair_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 1)["ms"]
-    roof["deposit_fp64_ms"] = kernel_roofline(B, cl, dc, stream, flush, dev, 0)["ms"]
+    # ---------------- arithmetic ceilings (the library's FMA probe) and the roofline
+    probes = fma_ceilings(B, stream, dev)
+    roof = smoother_roofline(B, stream, flush, dev, tuned, probes)
+    dep = deposit_rate(B, synth, stream, flush, dev, probes)
 
-    # ---------------- CPU baseline: the oracle as it stands, one whole solve
+    # ---------------- CPU baseline: the oracle as it stands, a bounded sample of the workload
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        dt, out = oracle_solves(cl, 1)
-        cpu = {"value": 1.0 / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-               "sample": f"1 whole solve of one cluster of the workload to 1e-10 ({out['cycles']} V(2,2) cycles), "
-                         f"{dt:.1f} s"}
+        smp = OracleSample()
+        r = smp.step()
+        cpu = {"value": 1.0 / r["solve_s"], "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+               "sample": smp.describe(1) + f"; {r['sample_s']:.1f} s of CPU work"}
 
     if rank == 0:
-        ch = summary(r_chosen, BATCH)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": span_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32+bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "form": FORM, "l2": "flushed before every timed step (512 MiB write)",
-                       "cycles": ch["cycles"], "defect_correction_steps": ch["outer"],
-                       "max_rel_resid": ch["max_rel_resid"], "parallelism": f"replicas x{ws}",
-                       "smoother_tuned": smoother_choice},
-            "plain_fp64": {"value": plain_value, "unit": UNIT, "ms_per_step": sum(r_plain["ms"]) / args.steps,
-                           "cycles": r_plain["stats"][0].cycles, "rel_resid": r_plain["stats"][0].rel_resid,
-                           "form": "one cluster per call, zero start, FP64 deposit and FP64 multigrid-preconditioned CG"},
+            "config": {"workload": WORKLOAD, "form": FORM, "solves_per_step": SEQ,
+                       "l2": "inputs far larger than L2 (~6 GB working set); flushed before every step anyway",
+                       "cycles": [c for c, *_ in stats], "defect_correction_steps": [o for _, o, *_ in stats],
+                       "learned_guess": [g for *_, g in stats],
+                       "max_rel_resid": max(r for _, _, r, _, _ in stats), "parallelism": f"replicas x{ws}",
+                       "oracle_error": {"max": max(err) if err else None, "per_density": err,
+                                        "definition": "max|dV_LM|/max|V_LM| against the FP64 oracle solved to 1e-13"},
+                       "smoother_tuned": tuned},
+            "plain_fp64": {"value": plain_value, "unit": UNIT, "ms_per_solve": sum(pms) / len(pms),
+                           "cycles": pst[0][0], "rel_resid": pst[0][2], "oracle_error": perr[0] if perr else None,
+                           "form": "FP64 deposit and FP64 multigrid-preconditioned CG, zero start, first density"},
             "chosen_over_plain": value / plain_value,
-            "forms": forms,
+            "starts_385": starts,
+            "pd55_batch8": pd55,
             "batch64_uneven": b64,
-            "pd561_graded385": pd561,
             "interstitial_hs": hs,
             "inner_faces_raw": rows,
+            "probes": probes,
+            "deposit": dep,
             "clocks": clk.summary(),
             "e2e": e2e,
-            "gpu_launches": r_chosen["launches"],
+            "gpu_launches": launches,
             "roofline": roof,
             "cpu_baseline": cpu,
         }
@@ -423,6 +513,66 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def pd55_forms(B, synth, flush, stream, dev, args, launch):
+    """The 8-cluster Pd55 / graded 129^3 batch (one graph launch, learned guess, mixed), the
+    plain FP64 form (one cluster per call) and the forms between, each with its oracle error."""
+    import torch
+    cls8 = [synth.pd55_graded129(seed=1 + k) for k in range(BATCH)]
+    cl = cls8[0]
+    dcs8 = [B.DeviceCluster(c) for c in cls8]
+    vlm8 = torch.empty((BATCH * cl.n_atoms, 25), dtype=torch.float64, device=dev)
+    dc, vlm = dcs8[0], vlm8[:cl.n_atoms]
+
+    def make(precision, batch=1, guess=False):
+        s_ = B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, max_batch=batch, precision=precision, launch=launch)
+        if guess:
+            s_.set_guess()
+        return s_
+
+    def timed(solver, dcs, out, clusters, steps, warmup):
+        st = None
+        for _ in range(warmup):
+            st = solver.solve(dcs, out)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = _events(torch, stream)
+            e0.record(stream)
+            st = solver.solve(dcs, out)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            assert all(x.status == 0 and x.rel_resid <= 1e-10 for x in st)
+        err = oracle_errors("pd55x8", clusters, out.cpu().numpy())
+        nc = len(clusters)
+        return {"value": nc * len(ms) / (sum(ms) / 1e3), "unit": UNIT, "ms_per_call": sum(ms) / len(ms),
+                "clusters_per_call": nc, "cycles": [x.cycles for x in st], "outer": [x.outer for x in st],
+                "max_rel_resid": max(x.rel_resid for x in st), "learned_guess": [x.guess for x in st],
+                "oracle_error_max": max(err) if err else None}
+
+    steps = max(3, args.steps)
+    out = {"workload": PD55_WORKLOAD}
+    s_ = make(B.LASTO_PREC_MIXED, BATCH, guess=True)
+    out["chosen"] = timed(s_, dcs8, vlm8, cls8, steps, 2)
+    s_.close()
+    s_ = make(B.LASTO_PREC_FP64)
+    out["plain_fp64"] = timed(s_, dc, vlm, cls8[:1], steps, 2)
+    s_.close()
+    s_ = make(B.LASTO_PREC_MIXED)
+    out["mixed_single"] = timed(s_, dc, vlm, cls8[:1], steps, 2)
+    s_.set_guess()
+    out["mixed_learned_single"] = timed(s_, dc, vlm, cls8[:1], steps, 2)
+    s_.close()
+    s_ = make(B.LASTO_PREC_MIXED, BATCH)
+    out["mixed_batched"] = timed(s_, dcs8, vlm8, cls8, steps, 2)
+    s_.close()
+    out["chosen_over_plain"] = out["chosen"]["value"] / out["plain_fp64"]["value"]
+    del dcs8, vlm8
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_profile(args, B):
@@ -487,8 +637,9 @@ def run_profile(args, B):
     return 0
 
 
-def batch_throughput(B, clusters, precision, steps, flush, stream, dev, warmup=2, guess=False):
-    """Solves/s of a batch of clusters solved in one call (one graph launch)."""
+def batch_throughput(B, clusters, precision, steps, flush, stream, dev, warmup=2, guess=False, group=None):
+    """Solves/s of a batch of clusters solved in one call (one graph launch), with the oracle
+    error of every cluster (max over the batch)."""
     import torch
     n_max = max(c.n for c in clusters)
     solver = B.Poisson(n_max=n_max, max_atoms=max(c.n_atoms for c in clusters), max_batch=len(clusters),
@@ -503,62 +654,21 @@ def batch_throughput(B, clusters, precision, steps, flush, stream, dev, warmup=2
     ms = []
     for _ in range(steps):
         flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch, stream)
         e0.record(stream)
         st = solver.solve(dcs, vlm)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     ok = all(s.status == 0 and s.rel_resid <= 1e-10 for s in st)
+    err = oracle_errors(group, clusters, vlm.cpu().numpy()) if group else None
     solver.close()
     del dcs, vlm
     torch.cuda.empty_cache()
     return {"value": len(clusters) * steps / (sum(ms) / 1e3), "unit": UNIT, "clusters": len(clusters),
             "ms_per_batch": sum(ms) / steps, "all_converged": ok, "mean_cycles": sum(s.cycles for s in st) / len(st),
             "max_cycles": max(s.cycles for s in st), "learned_guess": sum(s.guess for s in st),
-            "nodes": sum(c.n ** 3 for c in clusters)}
-
-
-def pd561_sequence(B, synth, flush, stream, dev):
-    """Chosen form (learned guess, FP64 defect correction around FP32 multigrid-preconditioned
-    CG) on 8 successive Pd561 densities (graded 385^3, 57 M nodes), one solve per call, after
-    one untimed solve; the plain FP64 form on the first density for comparison."""
-    import torch
-    cls = synth.pd561_graded385()
-    c0 = cls[0]
-    mk = lambda prec: B.Poisson(n_max=c0.n, max_atoms=c0.n_atoms, precision=prec)
-    out = {}
-    for name, prec, seq in (("chosen", B.LASTO_PREC_MIXED, cls), ("plain_fp64", B.LASTO_PREC_FP64, cls[:1])):
-        solver = mk(prec)
-        if name == "chosen":
-            solver.set_guess()
-        v = torch.empty((c0.n_atoms, 25), dtype=torch.float64, device=dev)
-        dc = B.DeviceCluster(c0)
-        st = solver.solve(dc, v)   # capture, tuning
-        torch.cuda.synchronize()
-        ms, cyc, res = [], [], []
-        for c in seq:
-            dc = B.DeviceCluster(c)
-            flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = solver.solve(dc, v)
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-            cyc.append(st[0].cycles)
-            res.append(st[0].rel_resid)
-            assert st[0].status == 0 and st[0].rel_resid <= 1e-10
-        out[name] = {"value": len(seq) / (sum(ms) / 1e3), "unit": UNIT, "ms_per_solve": sum(ms) / len(seq),
-                     "cycles": cyc, "max_rel_resid": max(res), "learned_guess": st[0].guess}
-        if name == "chosen":
-            out["smoother_tuned"] = solver.tune_table().strip().splitlines()
-        solver.close()
-        del v, dc
-        torch.cuda.empty_cache()
-    out["nodes"] = c0.n ** 3
-    out["chosen_over_plain"] = out["chosen"]["value"] / out["plain_fp64"]["value"]
-    return out
+            "nodes": sum(c.n ** 3 for c in clusters), "oracle_error_max": max(err) if err else None}
 
 
 def interstitial_hs(B, synth, flush, stream, dev):
@@ -603,11 +713,14 @@ def interstitial_hs(B, synth, flush, stream, dev):
     # the MMAs are kind::f16 on FP16 operands: the dense FP16 rate equals the BF16 one
     f16_peak = peaks.get("bf16_tflops", 1900.0)
     t = out["tensor"]["ms_contract"] / 1e3
-    out["roofline"] = {"kernel": "k_hs_gemm_tc", "bound": "tensor", "achieved": tensor_flops / t / 1e12,
-                       "peak": f16_peak, "unit": "TFLOP/s", "frac": tensor_flops / t / 1e12 / f16_peak,
-                       "traffic": None,
+    # the fraction counts the method's own products (S_ab and 2H_ab over a <= b), not the three
+    # hi/lo MMAs per product nor the padding of the 128 x 128 tiles
+    out["roofline"] = {"kernel": "k_hs_gemm_tc", "bound": "tensor", "achieved": alg_flops / t / 1e12,
+                       "peak": f16_peak, "unit": "TFLOP/s", "frac": alg_flops / t / 1e12 / f16_peak,
+                       "traffic": None, "flops": "algorithmic: 6 per interstitial node per (a <= b) entry",
                        "peak_source": ("measured bf16 burst (FP16 dense rate = BF16)" if "bf16_tflops" in peaks
                                        else "fallback bf16 burst")}
+    out["tensor_pipe_tflops"] = tensor_flops / t / 1e12   # all issued MMAs (3 per product, padded tiles)
     out["algorithmic_tflops"] = {"tensor": alg_flops / t / 1e12,
                                  "simt": alg_flops / (out["simt"]["ms_contract"] / 1e3) / 1e12}
     out["tensor_over_simt"] = out["simt"]["ms"] / out["tensor"]["ms"]
@@ -663,13 +776,46 @@ def next_rows(B, synth, flush, stream, dev):
     }
 
 
-def smoother_roofline(B, stream, flush, dev):
-    """FP32 red-black half sweep on the 385^3 graded Pd561 mesh (456 MB of u and b, far beyond
-    L2).  Algorithmic bytes per half sweep: every node's u read once (4 B), the colour's b read
-    and u written (8 B per updated node) = 8 B per node.  Time per launch from a 1-sweep and a
-    3-sweep call (the difference is 4 launches), L2 flushed before each call, for each launch
-    shape the solver's tuner chooses among; the fastest is reported."""
-    import json as _json
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def fma_ceilings(B, stream, dev):
+    """FP64 and FP32 fused multiply-add throughput of this GPU (the library's FMA-chain probe on
+    every SM, CUDA events, best of 3): the ceilings of the ALU-bound kernels."""
+    import torch
+    out = {}
+    for name, prec, dt, iters in (("fp64", 0, torch.float64, 200), ("fp32", 1, torch.float32, 4000)):
+        blocks = 152 * 16
+        buf = torch.empty(blocks * 256, dtype=dt, device=dev)
+        B.lasto_probe_fma(prec, blocks, iters, buf)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(3):
+            e0, e1 = _events(torch, stream)
+            e0.record(stream)
+            B.lasto_probe_fma(prec, blocks, iters, buf)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        flops = B.PROBE_FLOP_PER_THREAD_ITER * iters * blocks * 256
+        out[f"{name}_tflops"] = flops / best / 1e12
+        out[f"{name}_ms"] = best * 1e3
+    out["how"] = "lasto_probe_fma: 8 independent FMA chains per thread, 2432 blocks x 256 threads, best of 3"
+    return out
+
+
+def smoother_roofline(B, stream, flush, dev, tuned, probes):
+    """The dominant kernel of the headline: the FP32 smoother at 385^3, in the launch shape the
+    tuner chose for that level.  Algorithmic bytes (the smoother's compulsory traffic, 12 B per
+    node per FP32 sweep: u read, b read, u written): 6 B per node for one in-place half-sweep
+    launch (one colour), 12 B per node for one fused wavefront sweep.  Each shape is timed alone
+    with CUDA events (L2 flushed; the difference of a longer and a shorter call, so table set-up
+    cancels), and the line reports the tuner's choice; `traffic` is ncu's DRAM bytes per launch
+    (dram__bytes_read.sum + dram__bytes_write.sum at 257^3 in steady state, scaled by nodes)."""
     import torch
 
     import synth
@@ -678,106 +824,142 @@ def smoother_roofline(B, stream, flush, dev):
     axes = [B.lasto_mesh_axis(n, 0.0, cl.half_width, cl.h_min, cl.h_max, cl.p_max) for _ in range(3)]
     u = torch.zeros(n ** 3, dtype=torch.float32, device=dev)
     b = torch.rand(n ** 3, dtype=torch.float32, device=dev)
+    o = torch.empty_like(u)
 
-    def timed(sweeps, threads):
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
         ts = []
         for _ in range(3):
             flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1 = _events(torch, stream)
             e0.record(stream)
-            B.lasto_op_smooth(*axes, u, b, sweeps=sweeps, threads=threads)
+            fn()
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
-        return statistics.median(ts)
+        return statistics.median(ts) / 1e3
 
-    # the launch shapes the solver's tuner chooses among (flat 128/256/512, one block per row)
-    per = {}
-    for threads in (0, 128, 256, 512):
-        timed(1, threads)
-        per[threads] = (timed(3, threads) - timed(1, threads)) / 4 / 1e3
-    best = min(per, key=per.get)
-    t_launch = per[best]
-    bytes_per_launch = 8.0 * n ** 3
-    peaks = {}
-    try:
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = bytes_per_launch / t_launch / 1e9
-    del u, b
+    shapes = {}
+    for th in (0, 128, 256):   # in-place half sweeps: per launch (2 launches per sweep)
+        t = (timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=3, threads=th)) -
+             timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=1, threads=th))) / 4
+        shapes[f"inplace_{th if th else 'rows'}"] = {"us_per_launch": t * 1e6, "bytes_per_launch": 6.0 * n ** 3,
+                                                     "launches_per_sweep": 2, "nt": th}
+    for tile in ((60, 16), (60, 12), (60, 8)):   # wavefront sweeps: per launch (1 per sweep)
+        t = (timed(lambda: B.lasto_op_smooth_wave(*axes, u, o, b, sweeps=4, tile=tile)) -
+             timed(lambda: B.lasto_op_smooth_wave(*axes, u, o, b, sweeps=2, tile=tile))) / 2
+        shapes[f"wave_{tile[0]}x{tile[1]}"] = {"us_per_launch": t * 1e6, "bytes_per_launch": 12.0 * n ** 3,
+                                               "launches_per_sweep": 1, "tile": list(tile)}
+    del u, b, o
     torch.cuda.empty_cache()
-    # DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum of the chosen
-    # launch shape at 257^3 (steady state), scaled by the node count
-    traffic_257 = DRAM_BYTES_257.get(best)
-    traffic = traffic_257 * (n / 257.0) ** 3 if traffic_257 else None
-    name = "k_rbgs_row<float>, one block per row" if best == 0 else f"k_rbgs<float>, {best} threads per block"
-    return {"kernel": f"{name} (red-black half sweep, 385^3 graded)", "bound": "hbm", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-            "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
-            "us_per_launch_by_shape": {("rows" if k == 0 else str(k)): v * 1e6 for k, v in per.items()},
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "plain_fp64": fp64_half_sweep(B, cl, axes, timed_fn=lambda uu, bb, sw, th: _timed_smooth(
-                B, axes, uu, bb, sw, th, flush, stream), peak=peak)}
+    peaks = _peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    for v_ in shapes.values():
+        v_["achieved_gbs"] = v_["bytes_per_launch"] / (v_["us_per_launch"] / 1e6) / 1e9
+        v_["frac"] = v_["achieved_gbs"] / peak
+        v_["us_per_sweep"] = v_["us_per_launch"] * v_["launches_per_sweep"]
+    # the tuner's choice for the 385^3 FP32 level (table line: nx ny nz elem fused nt tx ty kz ns us)
+    pick = None
+    for line in tuned:
+        f = line.split()
+        if f[:4] == [str(n), str(n), str(n), "4"]:
+            fused, nt, tx, ty = int(f[4]), int(f[5]), int(f[6]), int(f[7])
+            pick = (f"wave_{tx}x{ty}" if fused == 2 else f"inplace_{nt if nt else 'rows'}" if fused == 0
+                    else None)
+    if pick not in shapes:
+        pick = min(shapes, key=lambda k: shapes[k]["us_per_sweep"])
+    c = shapes[pick]
+    if pick.startswith("inplace"):
+        t257 = DRAM_BYTES_257.get(c["nt"])
+        kernel = ("k_rbgs_row<float> (in-place red-black half sweep, one block per row, 385^3 graded)" if c["nt"] == 0
+                  else f"k_rbgs<float> (in-place red-black half sweep, {c['nt']} threads per block, 385^3 graded)")
+    else:
+        t257 = DRAM_BYTES_257.get("wave")
+        kernel = f"k_rb_wave<float> (fused red-black wavefront sweep, tile {c['tile']}, 385^3 graded)"
+    traffic = t257 * (n / 257.0) ** 3 if t257 else None
+    return {"kernel": kernel, "bound": "hbm", "achieved": c["achieved_gbs"], "peak": peak, "unit": "GB/s",
+            "frac": c["frac"], "traffic": traffic,
+            "traffic_over_algorithmic": traffic / c["bytes_per_launch"] if traffic else None,
+            "bytes_per_launch": c["bytes_per_launch"], "us_per_launch": c["us_per_launch"],
+            "bytes_rule": "12 B per node per FP32 sweep (u read, b read, u written): 6 per half-sweep launch",
+            "peak_source": "measured (hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
+            "shapes": shapes, "tuner_choice": pick,
+            "plain_fp64": fp64_half_sweep(B, cl, axes, flush, stream, dev, peak, probes)}
 
 
-def _timed_smooth(B, axes, u, b, sweeps, threads, flush, stream):
-    import torch
-    ts = []
-    for _ in range(3):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        B.lasto_op_smooth(*axes, u, b, sweeps=sweeps, threads=threads)
-        e1.record(stream)
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    return statistics.median(ts)
-
-
-def fp64_half_sweep(B, cl, axes, timed_fn, peak):
-    """The plain form's FP64 red-black half sweep at the same 385^3 mesh, one block per row.
-    Algorithmic bytes per launch: u read once (8 B per node), the colour's b and 1/diagonal read
-    and u written (24 B per updated node) = 20 B per node.  FP64 work per updated node: one
-    multiply, five FMAs, a subtraction and the multiply by 1/diagonal = 13 FLOP in 8 FP64
-    instructions; GB300's FP64 pipe (1.19 TFLOP/s of DFMA measured = 0.595 T instructions/s)
-    therefore caps this sweep near 0.45 of the HBM copy peak in algorithmic bytes."""
+def fp64_half_sweep(B, cl, axes, flush, stream, dev, peak, probes):
+    """The plain form's FP64 red-black half sweep at 385^3, one block per row.  Algorithmic bytes
+    per launch: 12 B per node (u read, the colour's b read and u written: 24 B per node per FP64
+    sweep).  FP64 work per updated node: one multiply, five FMAs, a subtraction and the multiply by
+    the stored 1/diagonal = 8 FP64 instructions (13 FLOP), against the FP64 FMA rate the probe
+    measured (2 FLOP per FMA instruction)."""
     import torch
     n = cl.n
-    u = torch.zeros(n ** 3, dtype=torch.float64, device="cuda")
-    b = torch.rand(n ** 3, dtype=torch.float64, device="cuda")
-    timed_fn(u, b, 1, 0)
-    t = (timed_fn(u, b, 3, 0) - timed_fn(u, b, 1, 0)) / 4 / 1e3
+    u = torch.zeros(n ** 3, dtype=torch.float64, device=dev)
+    b = torch.rand(n ** 3, dtype=torch.float64, device=dev)
+
+    def timed(sweeps):
+        B.lasto_op_smooth(*axes, u, b, sweeps=sweeps, threads=0)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            e0, e1 = _events(torch, stream)
+            e0.record(stream)
+            B.lasto_op_smooth(*axes, u, b, sweeps=sweeps, threads=0)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts) / 1e3
+
+    t = (timed(3) - timed(1)) / 4
     upd = (n - 2) ** 3 / 2
     del u, b
     torch.cuda.empty_cache()
-    bytes_per_launch = 20.0 * n ** 3
+    bytes_per_launch = 12.0 * n ** 3
+    fp64_peak = probes["fp64_tflops"]
     return {"kernel": "k_rbgs_row<double> (FP64 red-black half sweep, 385^3 graded)", "us_per_launch": t * 1e6,
             "achieved_gbs": bytes_per_launch / t / 1e9, "hbm_frac": bytes_per_launch / t / 1e9 / peak,
-            "fp64_tflops": 13 * upd / t / 1e12, "fp64_peak_tflops": FP64_TFLOPS,
-            "fp64_issue_frac": 8 * upd / t / (FP64_TFLOPS / 2 * 1e12), "bytes_per_launch": bytes_per_launch,
+            "fp64_tflops": 13 * upd / t / 1e12, "fp64_fma_tflops_measured": fp64_peak,
+            "fp64_issue_frac": 8 * upd / t / (fp64_peak / 2 * 1e12), "bytes_per_launch": bytes_per_launch,
             "traffic": DRAM_BYTES_257_F64 * (n / 257.0) ** 3}
 
 
-def kernel_roofline(B, cl, dc, stream, flush, dev, precision=1):
-    """The deposit kernel family timed alone with CUDA events (median of 5, L2 flushed)."""
+def deposit_rate(B, synth, stream, flush, dev, probes):
+    """The FP32-pair density deposit (the second kernel of the Pd561 solve) timed alone: (node,
+    atom) pairs per second, and FP32 work per second against the FP32 FMA rate the probe
+    measured, with the FP32 work per launch from ncu (DEPOSIT_FP32_FLOP)."""
     import torch
-    B.lasto_op_deposit(dc, precision=precision)   # warm
+    cl = synth.pd561_graded385(n_densities=1)[0]
+    dc = B.DeviceCluster(cl)
+    B.lasto_op_deposit(dc, precision=B.LASTO_PREC_MIXED)
     torch.cuda.synchronize()
     ms = []
-    for _ in range(5):
+    for _ in range(3):
         flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = _events(torch, stream)
         e0.record(stream)
-        B.lasto_op_deposit(dc, precision=precision)
+        B.lasto_op_deposit(dc, precision=B.LASTO_PREC_MIXED)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     t = statistics.median(ms) / 1e3
     pairs = cl.n ** 3 * cl.n_atoms
-    return {"kernel": f"lasto_op_deposit precision={precision}", "bound": "alu", "unit": "Gpair/s",
-            "achieved": pairs / t / 1e9, "peak": None, "frac": None, "traffic": None, "ms": t * 1e3}
+    out = {"kernel": "k_deposit_df (FP32-pair Slater sums, Pd561 graded 385^3)", "ms": t * 1e3,
+           "gpair_s": pairs / t / 1e9, "pairs": pairs, "bound": "alu",
+           "fp32_fma_tflops_measured": probes["fp32_tflops"]}
+    if DEPOSIT_FP32_FLOP is not None:
+        out["fp32_tflops"] = DEPOSIT_FP32_FLOP / t / 1e12
+        out["frac"] = out["fp32_tflops"] / probes["fp32_tflops"]
+    del dc
+    torch.cuda.empty_cache()
+    return out
+
+
+# FP32 FLOP of one Pd561 385^3 deposit launch (2 per FFMA, 1 per FADD / FMUL thread instruction),
+# from ncu's sass thread-instruction counts; None until captured
+DEPOSIT_FP32_FLOP = None
 
 
 if __name__ == "__main__":

@@ -246,14 +246,18 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out);
  *             concatenated grids.
  *   guess     device, optional (NULL): interior initial guess, same layout as
  *             potential (faces are overwritten by the multipole values).
- *   stats     host [n_clusters], optional (NULL); valid after stream sync; must
- *             stay alive until then.
+ *   stats     host [n_clusters], optional (NULL); written from the stream after the
+ *             solve (valid after stream sync); must stay alive until then.
  * The handle replays a CUDA graph captured for the same pointers and sizes, so
- * repeated solves on the same buffers cost one graph launch.  Not thread-safe
- * per handle.  Device outcomes per cluster go to stats[c].status. */
+ * repeated solves on the same buffers cost one graph launch; solves may be enqueued
+ * back to back without synchronising, each filling its own stats.  New pointers or
+ * sizes recapture the graph: that call first waits for the handle's previous solve
+ * to finish.  Not thread-safe per handle.  Device outcomes per cluster go to
+ * stats[c].status. */
 int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* clusters, int n_clusters, double* v_lm,
                         double* potential, const double* guess, lasto_stats* stats, void* stream);
 
+/* Frees the handle after waiting for its last solve (and that solve's stats copy). */
 void lasto_poisson_destroy(lasto_poisson* h);
 
 /* Kernel launches of the graph captured by the last lasto_poisson_solve on h:

@@ -240,7 +240,7 @@ class Poisson:
         st = L.lasto_poisson_create(ctypes.byref(cfg), ctypes.byref(h))
         _check(st, "lasto_poisson_create")
         self.h = h
-        self._stats = None
+        self._pending = []   # (event, stats array) of solves whose stats are still to be written
 
     def close(self):
         if getattr(self, "h", None):
@@ -283,12 +283,21 @@ class Poisson:
         arr = (lasto_raw_cluster * len(clusters))(*[c.struct() for c in clusters])
         self._keep = (clusters, arr)
         st_arr = (lasto_stats * len(clusters))() if stats else None
-        self._stats = st_arr
         st = load().lasto_poisson_solve_raw(self.h, arr, len(clusters), _ptr(v_lm), _ptr(potential), _ptr(guess),
                                             st_arr, _stream(stream))
         if st != LASTO_OK:
             raise RuntimeError(f"lasto_poisson_solve_raw failed: {STATUS_NAMES.get(st, st)}: {self.last_error()}")
+        self._hold(st_arr, stream)
         return st_arr
+
+    def _hold(self, st_arr, stream):
+        """The library writes a solve's stats into st_arr from the stream, after the solve: keep the
+        array alive until that has happened (an event after the call), even if the caller drops it."""
+        self._pending = [(ev, a) for ev, a in self._pending if not ev.query()]
+        if st_arr is not None:
+            ev = torch.cuda.Event()
+            ev.record(stream if stream is not None else torch.cuda.current_stream())
+            self._pending.append((ev, st_arr))
 
     def set_guess(self, weights=GUESS_WEIGHTS):
         """Load the learned initial-guess network (an .npz of per-layer weights [27][cin][cout],
@@ -318,11 +327,11 @@ class Poisson:
         arr = (lasto_cluster * len(clusters))(*[c.struct() for c in clusters])
         self._keep = (clusters, arr)
         st_arr = (lasto_stats * len(clusters))() if stats else None
-        self._stats = st_arr
         st = load().lasto_poisson_solve(self.h, arr, len(clusters), _ptr(v_lm), _ptr(potential), _ptr(guess),
                                         st_arr, _stream(stream))
         if st != LASTO_OK:
             raise RuntimeError(f"lasto_poisson_solve failed: {STATUS_NAMES.get(st, st)}: {self.last_error()}")
+        self._hold(st_arr, stream)
         return st_arr
 
 

@@ -230,8 +230,6 @@ struct lasto_poisson {
     int n_clusters = 0;
     std::vector<ClusterPlan> plans;
     lasto_stats* stats_pinned = nullptr;
-    lasto_stats* stats_user = nullptr;
-    int stats_count = 0;
     int kernels_fixed = -1, kernels_iter = -1, kernels_outer = 0;
     std::vector<cudaGraph_t> bodies, outer_bodies;
     // smoother choice per level shape {nx, ny, nz, element bytes}: measured once, reused
@@ -240,6 +238,9 @@ struct lasto_poisson {
     std::vector<lasto_raw_cluster> raw_copy;   // raw-density inputs of the current solve call
     std::vector<cudaEvent_t> eg;         // per slot: features written
     cudaEvent_t ev_net = nullptr;        // network forward done
+    // the last solve's work on the caller's stream (graph launch and stats copy): waited for
+    // before the workspace is re-carved, the graph replaced, or the handle freed
+    cudaEvent_t ev_launch = nullptr;
 };
 
 namespace {
@@ -956,10 +957,20 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
     return LASTO_OK;
 }
 
+// One solve's stats, from the pinned staging buffer to the caller's array.  Each call carries
+// its own destination, so solves enqueued back to back on one handle (before the first has
+// finished) each fill their own array; the staging buffer is reused in stream order.
+struct StatsCopy {
+    lasto_stats* dst;
+    const lasto_stats* src;
+    int count;
+};
+
 void CUDART_CB copy_stats_out(void* arg)
 {
-    lasto_poisson* h = static_cast<lasto_poisson*>(arg);
-    if (h->stats_user) std::memcpy(h->stats_user, h->stats_pinned, sizeof(lasto_stats) * h->stats_count);
+    StatsCopy* c = static_cast<StatsCopy*>(arg);
+    std::memcpy(c->dst, c->src, sizeof(lasto_stats) * c->count);
+    delete c;
 }
 
 }  // namespace
@@ -973,10 +984,12 @@ static int copy_stats(lasto_poisson* h, int nc, lasto_stats* stats, cudaStream_t
                                 cudaMemcpyDeviceToHost, s);
             if (e != cudaSuccess) return set_cuda_error(&h->err, e, "stats copy");
         }
-        h->stats_user = stats;
-        h->stats_count = nc;
-        e = cudaLaunchHostFunc(s, copy_stats_out, h);
-        if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaLaunchHostFunc");
+        StatsCopy* c = new StatsCopy{stats, h->stats_pinned, nc};
+        e = cudaLaunchHostFunc(s, copy_stats_out, c);
+        if (e != cudaSuccess) {
+            delete c;
+            return set_cuda_error(&h->err, e, "cudaLaunchHostFunc");
+        }
     }
     return LASTO_OK;
 }
@@ -1105,6 +1118,7 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cs3, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_origin, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_net, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_launch, cudaEventDisableTiming);
     h->bs.assign(cfg->max_batch, nullptr);
     h->ss.assign(cfg->max_batch, nullptr);
     h->ef.assign(cfg->max_batch, nullptr);
@@ -1131,6 +1145,7 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
 void lasto_poisson_destroy(lasto_poisson* h)
 {
     if (!h) return;
+    if (h->ev_launch) cudaEventSynchronize(h->ev_launch);   // the last solve and its stats copy
     if (h->cs) cudaStreamSynchronize(h->cs);
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
@@ -1148,6 +1163,7 @@ void lasto_poisson_destroy(lasto_poisson* h)
     for (auto x : h->ed) if (x) cudaEventDestroy(x);
     for (auto x : h->eg) if (x) cudaEventDestroy(x);
     if (h->ev_net) cudaEventDestroy(h->ev_net);
+    if (h->ev_launch) cudaEventDestroy(h->ev_launch);
     guess_net_free(h->net);
     delete h;
 }
@@ -1264,11 +1280,15 @@ static int solve_impl(lasto_poisson* h, const lasto_cluster* cls, const lasto_ra
     put(&guess, sizeof(guess));
     put(&nc, sizeof(nc));
     if (h->cfg.launch == 1) {
+        TRY(cudaEventSynchronize(h->ev_launch));
         int st = direct_solve(h, cls, raws, nc, v_lm, potential, guess, s);
-        if (st) return st;
-        return copy_stats(h, nc, stats, s);
+        if (!st) st = copy_stats(h, nc, stats, s);
+        if (!st) TRY(cudaEventRecord(h->ev_launch, s));
+        return st;
     }
     if (key != h->key || !h->exec) {
+        // a solve launched earlier (possibly still running) uses the workspace and the graph
+        TRY(cudaEventSynchronize(h->ev_launch));
         // carve the workspace for these clusters
         h->plans.assign(nc, ClusterPlan());
         Carver cv{h->pool, h->pool_bytes};
@@ -1287,7 +1307,10 @@ static int solve_impl(lasto_poisson* h, const lasto_cluster* cls, const lasto_ra
     }
     cudaError_t e = cudaGraphLaunch(h->exec, s);
     if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaGraphLaunch");
-    return copy_stats(h, nc, stats, s);
+    const int st = copy_stats(h, nc, stats, s);
+    if (st) return st;
+    TRY(cudaEventRecord(h->ev_launch, s));
+    return LASTO_OK;
 }
 
 extern "C" int lasto_poisson_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,

@@ -4,12 +4,18 @@
 Every value here comes from the FP64 CPU oracle (``oracle/``) solving the same seeded
 synthetic clusters the GPU tests build (``synth/``), to the oracle's floor (relative
 residual 1e-13, stationary V(2,2) cycles, l <= 4 multipole faces).  Nothing here touches
-the CUDA library.  One ``.npz`` per workload group, keyed by cluster name:
+the CUDA library.  One ``.npz`` per workload group, keyed by the cluster's position in the
+group (names repeat across seeds):
 
-  <name>/vlm          V_LM on every sphere [n_atoms][25] (Eq. 3.6)
-  <name>/stats        oracle status, cycles, final relative residual
-  <name>/fingerprint  a few sums of the cluster's inputs, so a test can tell that the
-                      stored answer belongs to the cluster it rebuilt
+  NNN/name         the cluster's name
+  NNN/vlm          V_LM on every sphere [n_atoms][25] (Eq. 3.6)
+  NNN/stats        oracle status, cycles, final relative residual
+  NNN/hist         the oracle's relative residual after each cycle (cycle 0 = the start)
+  NNN/fingerprint  a few sums of the cluster's inputs, so a test can tell that the
+                   stored answer belongs to the cluster it rebuilt
+
+A group is written after every cluster, so an interrupted run keeps what it finished and
+the next run resumes after it.
 
 Groups (the workloads are synth's):
   pd55x8      Pd55 graded 129^3, density seeds 1..8 (the 8-cluster batch)
@@ -69,33 +75,50 @@ def path(group: str) -> str:
 def make(group: str) -> None:
     clusters = GROUPS[group]()
     data = {}
-    for cl in clusters:
+    if os.path.exists(path(group)):                   # resume: keep the clusters already solved
+        z = np.load(path(group))
+        data = {k: z[k] for k in z.files}
+    for i, cl in enumerate(clusters):
+        key = f"{i:03d}"
+        if f"{key}/hist" in data and str(data[f"{key}/name"]) == cl.name and np.allclose(
+                data[f"{key}/fingerprint"], fingerprint(cl), rtol=1e-12, atol=0.0):
+            continue
         t0 = time.perf_counter()
         out = oracle.poisson_solve(cl, tol=TOL, max_cycles=MAX_CYCLES)
         dt = time.perf_counter() - t0
         if out["status"] != 0:
             raise SystemExit(f"{cl.name}: oracle status {out['status']} after {out['cycles']} cycles "
                              f"(residual {out['rel_resid']:.2e})")
-        data[f"{cl.name}/vlm"] = out["vlm"]
-        data[f"{cl.name}/stats"] = np.array([out["status"], out["cycles"], out["rel_resid"]])
-        data[f"{cl.name}/fingerprint"] = fingerprint(cl)
-        print(f"{group}: {cl.name} cycles={out['cycles']} rel_resid={out['rel_resid']:.2e} {dt:.1f} s", flush=True)
-    np.savez_compressed(path(group), **data)
+        data[f"{key}/name"] = np.array(cl.name)
+        data[f"{key}/vlm"] = out["vlm"]
+        data[f"{key}/stats"] = np.array([out["status"], out["cycles"], out["rel_resid"]])
+        data[f"{key}/hist"] = np.asarray(out["hist"], dtype=np.float64)
+        data[f"{key}/fingerprint"] = fingerprint(cl)
+        tmp = path(group) + ".tmp.npz"
+        np.savez_compressed(tmp, **data)
+        os.replace(tmp, path(group))
+        print(f"{group}: {i} {cl.name} cycles={out['cycles']} rel_resid={out['rel_resid']:.2e} {dt:.1f} s",
+              flush=True)
 
 
-def load(group: str) -> dict:
-    """name -> (vlm, stats, fingerprint) of a stored group (FileNotFoundError if absent)."""
+def load(group: str) -> list:
+    """[(name, vlm, stats, fingerprint)] of a stored group, in group order (FileNotFoundError if absent)."""
     z = np.load(path(group))
-    names = sorted({k.rsplit("/", 1)[0] for k in z.files})
-    return {n: (z[f"{n}/vlm"], z[f"{n}/stats"], z[f"{n}/fingerprint"]) for n in names}
+    keys = sorted({k.split("/", 1)[0] for k in z.files})
+    return [(str(z[f"{k}/name"]), z[f"{k}/vlm"], z[f"{k}/stats"], z[f"{k}/fingerprint"]) for k in keys]
 
 
-def stored_vlm(group: str, cl) -> np.ndarray:
-    """The stored oracle V_LM of cluster cl, after checking that it belongs to cl."""
-    vlm, stats, fp = load(group)[cl.name]
-    mine = fingerprint(cl)
-    if not np.allclose(fp, mine, rtol=1e-12, atol=0.0):
-        raise ValueError(f"{cl.name}: stored oracle answer was made for other inputs")
+def history(group: str, index: int) -> np.ndarray:
+    """The oracle's relative residual after each cycle for cluster `index` of a stored group."""
+    return np.load(path(group))[f"{index:03d}/hist"]
+
+
+def stored_vlm(group: str, cl, index: int) -> np.ndarray:
+    """The stored oracle V_LM of cluster cl, position `index` of its group, after checking that
+    the stored answer was made for cl's inputs."""
+    name, vlm, stats, fp = load(group)[index]
+    if name != cl.name or not np.allclose(fp, fingerprint(cl), rtol=1e-12, atol=0.0):
+        raise ValueError(f"{cl.name}: stored oracle answer {index} of {group} was made for other inputs")
     return vlm
 
 

@@ -285,3 +285,42 @@ def test_coarse_level_sweeps(orc, nu_coarse):
     assert st.status == 0 and st.rel_resid <= 1e-10
     ref = oracle_vlm(orc, cl)
     assert np.abs(host(v) - ref).max() < 1e-8 * np.abs(ref).max()
+
+
+def test_back_to_back_solves_on_one_handle_keep_their_stats(orc):
+    """Solves enqueued one after another on the same handle, with no synchronisation between
+    them, each deliver their own stats (every call carries its own destination)."""
+    import torch
+    B = need_gpu()
+    cls = [synth.pd13_small(n=33, seed=s) for s in (11, 12, 13)]
+    solver = B.Poisson(n_max=33, max_atoms=13, precision=B.LASTO_PREC_MIXED)
+    dcs = [B.DeviceCluster(c) for c in cls]
+    outs = [torch.empty((13, 25), dtype=torch.float64, device="cuda") for _ in cls]
+    solver.solve(dcs[0], outs[0])
+    torch.cuda.synchronize()
+    sts = [solver.solve(d, o) for d, o in zip(dcs, outs)]      # no sync in between
+    torch.cuda.synchronize()
+    for c, st, o in zip(cls, sts, outs):
+        s = st[0]
+        assert s.status == 0 and 0 < s.rel_resid <= 1e-10 and s.cycles > 0, (s.status, s.rel_resid, s.cycles)
+        ref = oracle_vlm(orc, c)
+        assert np.abs(host(o) - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_dropped_stats_arrays_are_kept_until_written():
+    """Solves whose returned stats the caller drops at once (no synchronisation), with new
+    pointers every few calls (recapture while earlier solves run): the library writes every
+    stats array after its solve, the binding keeps each alive until then, nothing crashes, and
+    the last solve is right."""
+    import torch
+    B = need_gpu()
+    cls = [synth.pd13_small(n=33, seed=s) for s in (31, 32, 33)]
+    solver = B.Poisson(n_max=33, max_atoms=13, precision=B.LASTO_PREC_MIXED)
+    dcs = [B.DeviceCluster(c) for c in cls]
+    outs = [torch.empty((13, 25), dtype=torch.float64, device="cuda") for _ in cls]
+    for r in range(24):
+        solver.solve(dcs[(r // 4) % 3], outs[(r // 4) % 3])      # result dropped immediately
+    st = solver.solve(dcs[0], outs[0])
+    torch.cuda.synchronize()
+    assert st[0].status == 0 and 0 < st[0].rel_resid <= 1e-10
+    solver.close()
