@@ -318,7 +318,10 @@ constexpr int DEP_NT = 256;
 constexpr int DT_X = 8, DT_Y = 8, DT_Z = 4;   // FP32-pair deposit: one 8 x 8 x 4 tile of nodes per block
 static_assert(DT_X * DT_Y * DT_Z == DEP_NT, "deposit tile = one block");
 constexpr double EXP_CUT = 40.0;   // e^{-40} * max W < 1e-14 absolute; skipped terms are below FP64 rounding of n_e
-constexpr float FAR_T = 20.0f;     // FP32-pair deposit: Slater terms with zeta r > 20 in plain FP32
+// FP32-pair deposit: Slater terms with zeta r > FAR_T in plain FP32.  FP32 carries a relative
+// error of a few 1e-6 in e^{-zeta r} there (the FP32 distance and exponent); at 20 the node-wise
+// deposit error stays near 1e-10 of the local density, while 16 (measured) raises it to ~4e-9.
+constexpr float FAR_T = 20.0f;
 
 __device__ __forceinline__ double nonspherical(const double* __restrict__ c, double dx, double dy, double dz,
                                                double r, double R, double z1)
@@ -574,11 +577,21 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
         const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
         if (r2f > cut2) continue;
         if (r2f > far2) {
+            // far pair: every term is below e^-FAR_T of its weight.  r in FP32 already carries a
+            // relative error of ~1e-7 (so ~2e-6 in e^{-zeta r} at zeta r = 20); the fast
+            // exponential adds an error of the same size, and e^{-zeta_q r} for zeta_q = 2 zeta_0
+            // is the square of e^{-zeta_0 r}.  Terms beyond zeta r = EXP_CUT are dropped.
             const float rf = sqrtf(r2f);
+            const float e0 = __expf(-zt[0].h * rf);
+            sfar = fmaf(o[6], e0, sfar);
 #pragma unroll
-            for (int q = 0; q < 3; q++) {
-                const float e = zt[q].h * rf;
-                if (e < EXP_CUT) sfar = fmaf(o[6 + 2 * q], expf(-e), sfar);
+            for (int q = 1; q < 3; q++) {
+                if (twice[q]) {
+                    sfar = fmaf(o[6 + 2 * q], e0 * e0, sfar);
+                } else {
+                    const float e = zt[q].h * rf;
+                    if (e < EXP_CUT) sfar = fmaf(o[6 + 2 * q], __expf(-e), sfar);
+                }
             }
             continue;
         }
