@@ -78,11 +78,14 @@ def parse():
     p.add_argument("--no-batch64", action="store_true")
     p.add_argument("--no-pd561", action="store_true")
     p.add_argument("--no-hs", action="store_true")
-    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "hs", "batch"], default=None,
+    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "pd561warm", "hs", "batch"],
+                   default=None,
                    help="run one kernel family for a profiler and exit: 'smoother' = one FP32 red-black sweep "
                         "on an n^3 graded mesh, 'solve' = one mixed solve of the workload with direct launches, "
                         "'guess' = the same with the learned initial guess, 'pd561' = one chosen-form solve "
-                        "of the Pd561 graded 385^3 workload with direct launches, 'hs' = one interstitial H and S "
+                        "of the Pd561 graded 385^3 workload with direct launches, 'pd561warm' = the second density "
+                        "of that sequence warm-started from the first one's potential (the headline's steady "
+                        "state), 'hs' = one interstitial H and S "
                         "call (tensor cores) for Pd55 on the graded 129^3 mesh, 'batch' = one graph launch of the "
                         "chosen form over the 8 Pd55 clusters of the workload (for ncu --graph-profiling graph)")
     p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
@@ -611,6 +614,23 @@ def run_profile(args, B):
         u = torch.zeros(n ** 3, dtype=dt, device="cuda")
         b = torch.rand(n ** 3, dtype=dt, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
         B.lasto_op_smooth(*axes, u, b, sweeps=args.sweeps, threads=args.threads)
+    elif args.profile == "pd561warm":
+        seq = synth.pd561_graded385(n_densities=2)
+        solver = B.Poisson(n_max=385, max_atoms=561, precision=B.LASTO_PREC_MIXED, launch=1)
+        solver.set_tune_table("".join(f"{m} {m} {m} 4 0 128 0 0 0 0 0\n" for m in (385, 193, 97, 49, 25)))
+        v = torch.empty((561, 25), dtype=torch.float64, device="cuda")
+        pot = torch.empty(385 ** 3, dtype=torch.float64, device="cuda")
+        st = solver.solve(B.DeviceCluster(seq[0]), v, potential=pot)   # the previous density
+        dc = B.DeviceCluster(seq[1])
+        st = solver.solve(dc, v, potential=pot, guess=pot)              # tables, first launch of each kernel
+        torch.cuda.synchronize()
+        st = solver.solve(B.DeviceCluster(seq[0]), v, potential=pot)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()   # ncu --profile-from-start off captures this solve only
+        st = solver.solve(dc, v, potential=pot, guess=pot)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        assert st[0].status == 0
     else:
         cl = synth.pd561_graded385(n_densities=1)[0] if args.profile == "pd561" else synth.pd55_graded129()
         solver = B.Poisson(n_max=cl.n, max_atoms=cl.n_atoms, precision=B.LASTO_PREC_MIXED, launch=1)

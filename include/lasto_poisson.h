@@ -107,13 +107,14 @@ typedef struct lasto_config {
     int nu_coarse;    /* pre/post sweeps per level on the coarse levels the FP32 cycle of the
                          mixed precision runs inside one thread block (at most 17 nodes per axis,
                          above the exact solve); >= 0.  The other levels use nu1/nu2. */
+    int nu_fine;      /* pre/post sweeps on the finest level when > 0 (0: nu1/nu2 there too) */
 } lasto_config;
 
 /* Fills cfg with the defaults: n_max 129, max_atoms 561, max_batch 1, FP64, PCG,
  * multipole faces, nu1 = nu2 = 4 (the fastest time to 1e-10 measured on GB300 for both precisions: more sweeps
  * per level cost less than the CG iterations and reductions they save), nu_coarse = 4 (1 keeps
  * the Pd55 129^3 iteration count and shortens each cycle, but costs iterations on smaller
- * grids), 50 cycles, rel_tol 1e-10, 16 x 32 sphere points, graph launch. */
+ * grids), nu_fine = 0, 50 cycles, rel_tol 1e-10, 16 x 32 sphere points, graph launch. */
 void lasto_config_default(lasto_config* cfg);
 
 typedef struct lasto_cluster {

@@ -31,7 +31,7 @@ class lasto_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("cycle", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("rel_tol", ctypes.c_double), ("n_theta", ctypes.c_int),
                 ("n_phi", ctypes.c_int), ("launch", ctypes.c_int), ("boundary", ctypes.c_int),
-                ("nu_coarse", ctypes.c_int)]
+                ("nu_coarse", ctypes.c_int), ("nu_fine", ctypes.c_int)]
 
 
 class lasto_cluster(ctypes.Structure):
@@ -226,7 +226,7 @@ class Poisson:
 
     def __init__(self, n_max=129, max_atoms=561, max_batch=1, precision=LASTO_PREC_FP64, cycle=LASTO_CYCLE_PCG,
                  nu1=4, nu2=4, max_cycles=50, rel_tol=1e-10, n_theta=16, n_phi=32, launch=0, boundary=0,
-                 nu_coarse=4):
+                 nu_coarse=4, nu_fine=0):
         L = load()
         cfg = lasto_config_default()
         cfg.n_max, cfg.max_atoms, cfg.max_batch = n_max, max_atoms, max_batch
@@ -235,6 +235,7 @@ class Poisson:
         cfg.launch = launch
         cfg.boundary = boundary
         cfg.nu_coarse = nu_coarse
+        cfg.nu_fine = nu_fine
         self.cfg = cfg
         h = ctypes.c_void_p()
         st = L.lasto_poisson_create(ctypes.byref(cfg), ctypes.byref(h))

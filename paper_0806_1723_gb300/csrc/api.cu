@@ -433,7 +433,8 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
 {
     LevelStore& S = P.lv[l];
     const LevelT<T> V = Arr<T>::view(S);
-    const int nu1 = h->cfg.nu1, nu2 = h->cfg.nu2;
+    const int nu1 = (l == 0 && h->cfg.nu_fine > 0) ? h->cfg.nu_fine : h->cfg.nu1;
+    const int nu2 = (l == 0 && h->cfg.nu_fine > 0) ? h->cfg.nu_fine : h->cfg.nu2;
     if (sizeof(T) == 4 && !fcycle && l > 0 && l == bottom_level(P)) {
         BottomArgs<T> a;
         a.nlev = P.L - l;
@@ -1080,6 +1081,7 @@ void lasto_config_default(lasto_config* c)
     c->launch = 0;
     c->boundary = LASTO_BC_MULTIPOLE;
     c->nu_coarse = 4;
+    c->nu_fine = 0;
 }
 
 int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
@@ -1093,7 +1095,7 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
         cfg->n_theta < 1 || cfg->n_theta > 32 || cfg->n_phi < 1 || cfg->n_phi > 64 ||
         (cfg->precision != LASTO_PREC_FP64 && cfg->precision != LASTO_PREC_MIXED) ||
         (cfg->cycle != LASTO_CYCLE_V && cfg->cycle != LASTO_CYCLE_FV && cfg->cycle != LASTO_CYCLE_PCG) ||
-        (cfg->launch != 0 && cfg->launch != 1) || cfg->nu_coarse < 0 || cfg->nu_coarse > 64 ||
+        (cfg->launch != 0 && cfg->launch != 1) || cfg->nu_coarse < 0 || cfg->nu_coarse > 64 || cfg->nu_fine < 0 || cfg->nu_fine > 64 ||
         (cfg->boundary != LASTO_BC_MULTIPOLE && cfg->boundary != LASTO_BC_ZERO && cfg->boundary != LASTO_BC_EXACT))
         return LASTO_ERR_INVALID_ARG;
     lasto_poisson* h = new (std::nothrow) lasto_poisson();
