@@ -356,6 +356,16 @@ int lasto_op_smooth(const int n[3], const double* x, const double* y, const doub
 int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const double* z, float* u,
                         const float* b, int sweeps, int threads, void* stream);
 
+/* The same FP32 sweeps over colour-split storage, the layout the solver gives its finest FP32
+ * level when the smoother tuner finds it faster: u and b hold the red nodes (even flat index
+ * P = i + n0 (j + n1 k), i.e. i+j+k even, every axis odd) in flat order at P / 2, then the
+ * black ones at (P - 1) / 2 + ceil(N / 2), N = n0 n1 n2.  Each half sweep then reads only the
+ * other colour and its own right-hand side and writes only its own colour, all with unit
+ * stride.  Bitwise the result of lasto_op_smooth_f32 on the same values in natural order.
+ * INVALID_ARG also for an even axis. */
+int lasto_op_smooth_split_f32(const int n[3], const double* x, const double* y, const double* z, float* u,
+                              const float* b, int sweeps, int threads, void* stream);
+
 /* Red-black Gauss-Seidel on z-slabs staged in shared memory (the Section 3 smoother):
  * `sweeps` full sweeps, each colour `first` (0 = red, i+j+k even) then the other, from
  * u_in into u_out, fused ns (1 or 2) sweeps per pass over the grid.  u_in, u_out, b:

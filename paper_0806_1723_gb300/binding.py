@@ -56,7 +56,7 @@ EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve"
            "lasto_poisson_last_error", "lasto_poisson_kernel_counts", "lasto_mesh_axis", "lasto_op_sphere_params", "lasto_op_deposit",
            "lasto_op_deposit_noalloc",
            "lasto_op_multipoles", "lasto_op_boundary_fill", "lasto_op_boundary_exact", "lasto_op_apply", "lasto_op_residual", "lasto_op_smooth",
-           "lasto_op_smooth_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_smooth_wave_f32", "lasto_selftest_bounded_wait",
+           "lasto_op_smooth_f32", "lasto_op_smooth_split_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_smooth_wave_f32", "lasto_selftest_bounded_wait",
            "lasto_probe_fma", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
            "lasto_op_project", "lasto_op_sphere_density", "lasto_op_inner_solve", "lasto_op_interstitial_hs", "lasto_guess_param_count", "lasto_poisson_set_guess",
            "lasto_poisson_tune_table", "lasto_poisson_set_tune_table", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
@@ -98,6 +98,7 @@ def _declare(L):
         "lasto_op_residual": (i, [ip, vp, vp, vp, vp, vp, vp, vp]),
         "lasto_op_smooth": (i, [ip, vp, vp, vp, vp, vp, i, i, vp]),
         "lasto_op_smooth_f32": (i, [ip, vp, vp, vp, vp, vp, i, i, vp]),
+        "lasto_op_smooth_split_f32": (i, [ip, vp, vp, vp, vp, vp, i, i, vp]),
         "lasto_op_smooth_slab": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, ip, vp]),
         "lasto_op_smooth_slab_f32": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, ip, vp]),
         "lasto_op_smooth_wave_f32": (i, [ip, vp, vp, vp, vp, vp, vp, i, i, i, i, vp]),
@@ -426,6 +427,28 @@ def lasto_op_smooth(x, y, z, u, b, sweeps=1, threads=256, stream=None):
     fn = load().lasto_op_smooth if u.dtype == torch.float64 else load().lasto_op_smooth_f32
     _check(fn(*_axes(x, y, z), _ptr(u), _ptr(b), int(sweeps), int(threads), _stream(stream)), "lasto_op_smooth")
     return u
+
+
+def lasto_op_smooth_split(x, y, z, u, b, sweeps=1, threads=256, stream=None):
+    """`sweeps` FP32 red-black sweeps in place on u and b held in colour-split storage
+    (split_colours)."""
+    _check(load().lasto_op_smooth_split_f32(*_axes(x, y, z), _ptr(u), _ptr(b), int(sweeps), int(threads),
+                                            _stream(stream)), "lasto_op_smooth_split_f32")
+    return u
+
+
+def split_colours(a):
+    """A natural-order node array in colour-split storage: the even flat indices, then the odd ones."""
+    return torch.cat([a[0::2], a[1::2]])
+
+
+def merge_colours(a):
+    """Inverse of split_colours."""
+    h = (a.numel() + 1) // 2
+    out = torch.empty_like(a)
+    out[0::2] = a[:h]
+    out[1::2] = a[h:]
+    return out
 
 
 def lasto_op_smooth_slab(x, y, z, u_in, u_out, b, sweeps=None, ns=1, first=0, tile=(32, 8, 16), stream=None):

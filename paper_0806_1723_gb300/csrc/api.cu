@@ -59,7 +59,10 @@ struct Carver {
 
 // How one level is smoothed: in-place half sweeps (block size nt) or fused passes ping-ponging
 // with a partner array: fused = 1, the z-slab / register-column kernels (shape sh); fused = 2,
-// the FP32 wavefront sweep over bulk-copied row chunks (sh.tx columns, sh.ty rows).
+// the FP32 wavefront sweep over bulk-copied row chunks (sh.tx columns, sh.ty rows); fused = 3,
+// in-place half sweeps over colour-split storage (FP32, block size nt), which the finest level
+// of a cluster then uses for all its FP32 arrays (another level with these dimensions runs the
+// natural in-place sweeps with the same block size).
 struct SmoothChoice {
     int fused = 0;
     int nt = 256;
@@ -299,7 +302,7 @@ cudaError_t smooth(const LevelT<T>& V, T*& cur, T* partner, T* home, const T* b,
         }
         return cudaErrorInvalidValue;
     }
-    if (!ch.fused) {
+    if (ch.fused == 0 || ch.fused == 3) {   // the view's storage order picks the kernel
         for (int it = 0; it < nu && e == cudaSuccess; it++) {
             e = launch_rbgs<T>(V, cur, b, first, s, ch.nt);
             if (e == cudaSuccess) e = launch_rbgs<T>(V, cur, b, 1 - first, s, ch.nt);
@@ -324,7 +327,8 @@ int fused_passes(int nu, int ns) { return nu / ns + (nu % ns ? 1 : 0); }
 
 bool choice_usable(const lasto_poisson* h, const SmoothChoice& c, size_t elem)
 {
-    if (!c.fused) return c.nt == 0 || (c.nt >= 32 && c.nt <= 512 && c.nt % 32 == 0);
+    if (c.fused == 0 || c.fused == 3)
+        return (c.fused == 0 || elem == 4) && (c.nt == 0 || (c.nt >= 32 && c.nt <= 512 && c.nt % 32 == 0));
     if (c.fused == 2) return elem == 4 && wave_shape_ok(c.sh) && (h->cfg.nu1 + h->cfg.nu2) % 2 == 0;
     // the pre- and post-smoothing passes together must return the data to its home array
     return slab_shape_ok(c.sh, elem) && (fused_passes(h->cfg.nu1, c.sh.ns) + fused_passes(h->cfg.nu2, c.sh.ns)) % 2 == 0;
@@ -341,11 +345,14 @@ SmoothChoice smooth_choice(const lasto_poisson* h, const LevelStore& S)
 // Time the candidates on this level's own arrays (zeroed; the stream is idle and not being
 // captured) and keep the fastest pre-smoothing phase.
 template <typename T>
-int tune_level(lasto_poisson* h, LevelStore& S, cudaStream_t st)
+int tune_level(lasto_poisson* h, LevelStore& S, bool finest, cudaStream_t st)
 {
     const std::array<int, 4> key{S.n[0], S.n[1], S.n[2], (int)sizeof(T)};
     if (h->tune.count(key)) return LASTO_OK;
-    const LevelT<T> V = Arr<T>::view(S);
+    LevelT<T> V = Arr<T>::view(S);
+    set_split(V, false);
+    LevelT<T> Vs = V;   // the same arrays read as colour-split storage
+    set_split(Vs, true);
     T* u = Arr<T>::u(S);
     T* partner = Arr<T>::partner(S);
     T* b = Arr<T>::b(S);
@@ -364,6 +371,14 @@ int tune_level(lasto_poisson* h, LevelStore& S, cudaStream_t st)
         cand.push_back(c);
     }
     const bool f32 = sizeof(T) == 4;
+    if (f32 && finest)
+        for (int nt : {128, 256, 512, 0}) {
+            if (nt == 0 && (S.n[0] + 1) / 2 > 512) continue;
+            SmoothChoice c;
+            c.fused = 3;
+            c.nt = nt;
+            cand.push_back(c);
+        }
     for (int ty : f32 ? std::vector<int>{6, 14} : std::vector<int>{2, 6})
         for (int kz : {16, 32}) {
             SmoothChoice c;
@@ -393,10 +408,11 @@ int tune_level(lasto_poisson* h, LevelStore& S, cudaStream_t st)
     for (const SmoothChoice& c : cand) {
         if (!choice_usable(h, c, sizeof(T))) continue;
         T* cur = u;
-        cudaError_t e = smooth<T>(V, cur, partner, u, b, h->cfg.nu1, 0, c, nullptr, st);   // warm
+        const LevelT<T>& Vc = c.fused == 3 ? Vs : V;
+        cudaError_t e = smooth<T>(Vc, cur, partner, u, b, h->cfg.nu1, 0, c, nullptr, st);   // warm
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         for (int r = 0; r < 3 && e == cudaSuccess; r++)
-            e = smooth<T>(V, cur, partner, u, b, h->cfg.nu1, 0, c, nullptr, st);
+            e = smooth<T>(Vc, cur, partner, u, b, h->cfg.nu1, 0, c, nullptr, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
@@ -459,7 +475,13 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
         }
         return LASTO_OK;
     }
-    const SmoothChoice ch = smooth_choice<T>(h, S);
+    SmoothChoice ch = smooth_choice<T>(h, S);
+    if (V.lsh) {   // colour-split storage: in-place sweeps only
+        if (ch.fused != 0 && ch.fused != 3) ch = SmoothChoice{};
+        ch.fused = 3;
+    } else if (ch.fused == 3) {
+        ch.fused = 0;
+    }
     T* cur = u;   // fused passes move the iterate between u and the partner array
     TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu1, 0, ch, P.status, s));
     LevelStore& C = P.lv[l + 1];
@@ -694,8 +716,17 @@ int tune_plans(lasto_poisson* h, const lasto_cluster* cls, int nc, cudaStream_t 
         if (!need) continue;
         int st = enqueue_setup(h, P, cls[c], s);   // the level's own coefficients
         if (st) return st;
-        for (int l = 0; l <= last && !st; l++) st = f32 ? tune_level<float>(h, P.lv[l], s) : tune_level<double>(h, P.lv[l], s);
+        for (int l = 0; l <= last && !st; l++)
+            st = f32 ? tune_level<float>(h, P.lv[l], l == 0, s) : tune_level<double>(h, P.lv[l], l == 0, s);
         if (st) return st;
+    }
+    // the finest level's FP32 storage order follows its choice (fixed for every kernel of the
+    // solve that touches those arrays)
+    for (int c = 0; c < nc; c++) {
+        ClusterPlan& P = h->plans[c];
+        for (int l = 0; l < P.L; l++) P.lv[l].split32 = false;
+        const int bl = bottom_level(P);
+        P.lv[0].split32 = f32 && P.L >= 2 && bl != 0 && smooth_choice<float>(h, P.lv[0]).fused == 3;
     }
     return LASTO_OK;
 }
@@ -714,7 +745,7 @@ int enqueue_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHandle c
         int st = enqueue_cycle<double>(h, P, 0, F.u, F.b, F.r, true, false, s);
         if (st) return st;
     }
-    TRY(launch_resid_norm(V, F.u, F.b, F.r, dc ? F.b32 : nullptr, P.red(FIN_START, cond, use_cond), s));
+    TRY(launch_resid_norm(V, F.u, F.b, F.r, dc ? F.b32 : nullptr, F.view32().H, P.red(FIN_START, cond, use_cond), s));
     if (cyc == LASTO_CYCLE_PCG) TRY(cudaMemsetAsync(P.p, 0, sizeof(double) * F.N(), s));
     if (dc) TRY(cudaMemsetAsync(P.e32, 0, sizeof(float) * F.N(), s));
     return LASTO_OK;
@@ -728,7 +759,7 @@ int enqueue_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHand
     if (h->cfg.cycle != LASTO_CYCLE_PCG) {
         int st = enqueue_cycle<double>(h, P, 0, F.u, F.b, F.r, false, false, s);
         if (st) return st;
-        TRY(launch_resid_norm(V, F.u, F.b, F.r, nullptr, P.red(FIN_CHECK, cond, use_cond), s));
+        TRY(launch_resid_norm(V, F.u, F.b, F.r, nullptr, 0u, P.red(FIN_CHECK, cond, use_cond), s));
         return LASTO_OK;
     }
     TRY(cudaMemsetAsync(P.z, 0, sizeof(double) * F.N(), s));
@@ -771,8 +802,8 @@ int enqueue_outer_finish(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalH
                          cudaStream_t s)
 {
     LevelStore& F = P.lv[0];
-    TRY(launch_add_correction(F.N(), F.u, P.e32, s));
-    TRY(launch_resid_norm(F.view64(), F.u, F.b, F.r, F.b32, P.red(FIN_OUTER, cond, use_cond), s));
+    TRY(launch_add_correction(F.N(), F.u, P.e32, F.view32().H, s));
+    TRY(launch_resid_norm(F.view64(), F.u, F.b, F.r, F.b32, F.view32().H, P.red(FIN_OUTER, cond, use_cond), s));
     return LASTO_OK;
 }
 
@@ -781,7 +812,7 @@ int enqueue_finish(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, do
 {
     LevelStore& F = P.lv[0];
     const LevelT<double> V = F.view64();
-    TRY(launch_resid_norm(V, F.u, F.b, nullptr, nullptr, P.red(FIN_TRUE), s));
+    TRY(launch_resid_norm(V, F.u, F.b, nullptr, nullptr, 0u, P.red(FIN_TRUE), s));
     TRY(launch_project(cl.n, cl.x, cl.y, cl.z, F.u, cl.n_atoms, cl.pos, cl.R, h->quad, h->nq, vlm, P.status, s));
     if (potential) TRY(cudaMemcpyAsync(potential, F.u, sizeof(double) * F.N(), cudaMemcpyDeviceToDevice, s));
     k_write_stats<<<1, 1, 0, s>>>(P.ctl, P.status, P.gl >= 0 ? 1 : 0, P.stats_dev);
@@ -1530,6 +1561,27 @@ int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const 
     for (int it = 0; it < sweeps && e == cudaSuccess; it++) {
         e = launch_rbgs<float>(L.S.view32(), u, b, 0, s, threads);
         if (e == cudaSuccess) e = launch_rbgs<float>(L.S.view32(), u, b, 1, s, threads);
+    }
+    return op_status(e);
+}
+
+int lasto_op_smooth_split_f32(const int n[3], const double* x, const double* y, const double* z, float* u,
+                              const float* b, int sweeps, int threads, void* stream)
+{
+    if (!op_grid_ok(n, x, y, z) || !u || !b || sweeps < 0) return LASTO_ERR_INVALID_ARG;
+    if (threads != 0 && (threads < 32 || threads > 512 || threads % 32)) return LASTO_ERR_INVALID_ARG;
+    if (threads == 0 && n[0] > 1023) return LASTO_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++)
+        if (n[d] % 2 == 0) return LASTO_ERR_INVALID_ARG;   // the colour is the flat-index parity
+    cudaStream_t s = (cudaStream_t)stream;
+    OpLevel L(n, x, y, z, false, s);
+    if (!L.ok()) return LASTO_ERR_NO_MEMORY;
+    LevelT<float> V = L.S.view32();
+    set_split(V, true);
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < sweeps && e == cudaSuccess; it++) {
+        e = launch_rbgs<float>(V, u, b, 0, s, threads);
+        if (e == cudaSuccess) e = launch_rbgs<float>(V, u, b, 1, s, threads);
     }
     return op_status(e);
 }

@@ -123,16 +123,25 @@ __device__ __forceinline__ unsigned div_by(unsigned n, DivMagic q)
     return __umulhi(n, q.m) >> q.s;
 }
 
+// Storage order of a level's node arrays.  Natural: node P (flat index, x fastest) at P.
+// Colour-split: the even flat indices (red, i+j+k even, as every axis has an odd node count)
+// first, in order, then the odd ones: node P at (P >> 1) + (P & 1) H, H = ceil(N / 2).  Every
+// neighbour of a node has the other colour, so a half sweep over split storage reads only the
+// other half and its own right-hand side and writes only its own half, all with unit stride,
+// where natural storage moves every sector of both colours in each half sweep.
 template <typename T>
 struct LevelT {
     AxisT<T> ax[3];
     const T* inv_diag;  // [N] or nullptr (FP32 smoother computes the diagonal)
     int nx, ny, nz;
     DivMagic dvx, dvxy;  // division by nx and by nx * ny (set_dims)
+    unsigned lsh;        // 0: natural storage; 1: colour-split storage
+    unsigned H;          // colour-split: offset of the odd half, ceil(N / 2); natural: 0
     __host__ __device__ size_t N() const { return (size_t)nx * ny * nz; }
 };
 
-// The only way dimensions are set: keeps the division constants in step (every axis >= 3 nodes).
+// The only way dimensions are set: keeps the division constants in step (every axis >= 3 nodes);
+// natural storage.
 template <typename T>
 inline void set_dims(LevelT<T>& v, int nx, int ny, int nz)
 {
@@ -141,6 +150,22 @@ inline void set_dims(LevelT<T>& v, int nx, int ny, int nz)
     v.nz = nz;
     v.dvx = div_magic((unsigned)nx);
     v.dvxy = div_magic((unsigned)nx * (unsigned)ny);
+    v.lsh = 0;
+    v.H = 0;
+}
+
+template <typename T>
+inline void set_split(LevelT<T>& v, bool split)
+{
+    v.lsh = split ? 1u : 0u;
+    v.H = split ? (unsigned)((v.N() + 1) / 2) : 0u;
+}
+
+// storage position of flat node P (nodes < 2^31)
+template <typename T>
+__host__ __device__ __forceinline__ unsigned at(const LevelT<T>& L, unsigned P)
+{
+    return (P >> L.lsh) + (P & L.lsh) * L.H;
 }
 
 // Raw (writable) per-axis storage of one level in one pool.
@@ -158,6 +183,7 @@ struct LevelStore {
     double *u, *b, *r;  // FP64 work arrays (level 0: u unused by the preconditioner)
     double* u2;         // FP64 partner of the fused smoother passes (FP32 levels use r32)
     float *u32, *b32, *r32;
+    bool split32 = false;   // the FP32 arrays in colour-split storage (view32 says so)
     size_t N() const { return (size_t)n[0] * n[1] * n[2]; }
     LevelT<double> view64() const;
     LevelT<float> view32() const;
@@ -264,7 +290,7 @@ struct Red {
 int reduce_blocks(const LevelT<double>& L);
 cudaError_t launch_bnorm(const LevelT<double>& L, const double* u, const double* b, const Red& red, cudaStream_t s);
 cudaError_t launch_resid_norm(const LevelT<double>& L, const double* u, const double* b, double* r, float* r32,
-                              const Red& red, cudaStream_t s);
+                              unsigned h32, const Red& red, cudaStream_t s);
 cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, const Red& red, cudaStream_t s);
 cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const double* p, const double* q, double* u,
                              double* r, const Red& red, cudaStream_t s);
@@ -275,7 +301,8 @@ cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const flo
                                float* r, const Red& red, cudaStream_t s);
 cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, const Red& red, cudaStream_t s);
 cudaError_t launch_update_p32(const LevelT<float>& L, const Ctl* ctl, const float* z, float* p, cudaStream_t s);
-cudaError_t launch_add_correction(size_t N, double* u, float* e, cudaStream_t s);
+// (e in colour-split storage when h32 = ceil(N / 2) is nonzero)
+cudaError_t launch_add_correction(size_t N, double* u, float* e, unsigned h32, cudaStream_t s);
 cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s);
 
 // density.cu

@@ -94,6 +94,7 @@ LevelT<float> LevelStore::view32() const
     for (int d = 0; d < 3; d++) v.ax[d] = axis_view<float>(ax[d]);
     v.inv_diag = nullptr;
     set_dims(v, n[0], n[1], n[2]);
+    set_split(v, split32);
     return v;
 }
 

@@ -40,18 +40,40 @@ __device__ __forceinline__ bool is_face(const LevelT<T>& L, int i, int j, int k)
 // sum of the six neighbour terms in the fixed order x-, x+, y-, y+, z-, z+
 // (neighbours addressed from the node's own pointer with 32-bit offsets: a plane holds fewer
 // than 2^31 nodes)
-template <typename T>
+// LS = 1: colour-split storage (LevelT): the neighbours all sit in the other colour's half, at
+// (P +- d) >> 1.  The terms and their order are the same in both storage orders.
+template <int LS = 0, typename T>
 __device__ __forceinline__ T offdiag(const LevelT<T>& L, const T* __restrict__ u, size_t P, int i, int j, int k)
 {
-    const int sy = L.nx, sz = L.nx * L.ny;
-    const T* __restrict__ c = u + P;
-    T t = L.ax[0].cm[i] * c[-1];
-    t = fma(L.ax[0].cp[i], c[1], t);
-    t = fma(L.ax[1].cm[j], c[-sy], t);
-    t = fma(L.ax[1].cp[j], c[sy], t);
-    t = fma(L.ax[2].cm[k], c[-sz], t);
-    t = fma(L.ax[2].cp[k], c[sz], t);
-    return t;
+    if constexpr (LS == 0) {
+        const int sy = L.nx, sz = L.nx * L.ny;
+        const T* __restrict__ c = u + P;
+        T t = L.ax[0].cm[i] * c[-1];
+        t = fma(L.ax[0].cp[i], c[1], t);
+        t = fma(L.ax[1].cm[j], c[-sy], t);
+        t = fma(L.ax[1].cp[j], c[sy], t);
+        t = fma(L.ax[2].cm[k], c[-sz], t);
+        t = fma(L.ax[2].cp[k], c[sz], t);
+        return t;
+    } else {
+        const unsigned p = (unsigned)P, sy = (unsigned)L.nx, sz = (unsigned)L.nx * (unsigned)L.ny;
+        const T* __restrict__ o = u + (size_t)(1u - (p & 1u)) * L.H;
+        T t = L.ax[0].cm[i] * o[(p - 1u) >> 1];
+        t = fma(L.ax[0].cp[i], o[(p + 1u) >> 1], t);
+        t = fma(L.ax[1].cm[j], o[(p - sy) >> 1], t);
+        t = fma(L.ax[1].cp[j], o[(p + sy) >> 1], t);
+        t = fma(L.ax[2].cm[k], o[(p - sz) >> 1], t);
+        t = fma(L.ax[2].cp[k], o[(p + sz) >> 1], t);
+        return t;
+    }
+}
+
+// storage position of node P for a compile-time storage order
+template <int LS, typename T>
+__device__ __forceinline__ unsigned pos(const LevelT<T>& L, size_t P)
+{
+    if constexpr (LS == 0) return (unsigned)P;
+    else return ((unsigned)P >> 1) + ((unsigned)P & 1u) * L.H;
 }
 
 template <typename T>
@@ -61,7 +83,9 @@ __device__ __forceinline__ T dsum(const LevelT<T>& L, int i, int j, int k)
 }
 
 // ---------------------------------------------------------------- smoother
-template <typename T>
+// (LS = 1: colour-split storage, FP32 only; thread t's node is then at t + colour H, so every
+// load and store of a warp is one unit-stride run)
+template <typename T, int LS>
 __global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour,
                                              size_t nhalf)
 {
@@ -71,46 +95,165 @@ __global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, co
     int i, j, k;
     node_ijk(P, L, i, j, k);
     if (is_face(L, i, j, k)) return;
-    const T acc = b[P] - offdiag(L, u, P, i, j, k);
+    const unsigned Q = pos<LS>(L, P);
+    const T acc = b[Q] - offdiag<LS>(L, u, P, i, j, k);
     if constexpr (sizeof(T) == 8) {
-        u[P] = acc * L.inv_diag[P];
+        u[Q] = acc * L.inv_diag[P];
     } else {
-        u[P] = rb_point32(acc, dsum(L, i, j, k));
+        u[Q] = rb_point32(acc, dsum(L, i, j, k));
     }
 }
 
 // The same half sweep with one block per interior (j, k) row and one thread per node of the
 // colour along i: no index division, the row's y and z coefficients the same in every thread.
 // The node update is k_rbgs's expression, so the two are bitwise equal.
-template <typename T>
+template <typename T, int LS>
 __global__ void __launch_bounds__(512) k_rbgs_row(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour)
 {
     const int j = blockIdx.x + 1, k = blockIdx.y + 1;
     const int i = 2 * (int)threadIdx.x + ((colour + j + k) & 1);   // flat-index parity = parity of i + j + k
     if (i == 0 || i >= L.nx - 1) return;
     const unsigned P = ((unsigned)k * L.ny + j) * L.nx + i;   // nodes < 2^31
-    const T acc = b[P] - offdiag(L, u, P, i, j, k);
+    const unsigned Q = pos<LS>(L, P);
+    const T acc = b[Q] - offdiag<LS>(L, u, P, i, j, k);
     if constexpr (sizeof(T) == 8) {
-        u[P] = acc * L.inv_diag[P];
+        u[Q] = acc * L.inv_diag[P];
     } else {
-        u[P] = rb_point32(acc, dsum(L, i, j, k));
+        u[Q] = rb_point32(acc, dsum(L, i, j, k));
     }
 }
 
-// nt > 0: k_rbgs with nt threads per block; nt == 0: k_rbgs_row (rows of at most 1023 nodes)
+// The FP32 half sweep over colour-split storage with one warp per interior (j, k) row: lane l
+// updates the row's interior nodes of the colour numbered l, l + 32, ..., l + 32 (V - 1) in x
+// order, so every load and store of the warp is one unit-stride run.  The row's y and z
+// coefficients, its flat index and the six neighbour offsets (row constants in this storage:
+// node q of the colour has its neighbours at q + d in the other colour's half) are formed once
+// per row.  A row's own right-hand side and the other colour's row one plane further on (where
+// the sweep first touches it, as a z+ neighbour; its other reads then hit L2) are prefetched
+// into L2 `pf` rows ahead, about half a wave of resident warps, which keeps more DRAM requests
+// in flight than the warps' own loads do.  The node update is k_rbgs's expression, so the two
+// are bitwise equal.
+template <int V>
+__global__ void __launch_bounds__(256) k_rbgs_split_rows(LevelT<float> L, float* __restrict__ u,
+                                                        const float* __restrict__ b, int colour, int pf)
+{
+    const int my = L.ny - 2;
+    const int row = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    if (row >= my * (L.nz - 2)) return;
+    const int lane = threadIdx.x & 31;
+    const int k = row / my + 1, j = row - (k - 1) * my + 1;
+    const int nx = L.nx;
+    const unsigned nxy = (unsigned)nx * (unsigned)L.ny;
+    const int c = colour;
+    const int i1 = ((c + j + k) & 1) ? 1 : 2;             // first interior node of the colour
+    const int cnt = (nx - i1) >> 1;                        // interior nodes of the colour in the row
+    const unsigned q0 = ((unsigned)k * nxy + (unsigned)j * (unsigned)nx + (unsigned)i1) >> 1;
+    const int hx = (nx - 1) >> 1, hxy = (int)((nxy - 1) >> 1);
+    const int dxm = c - 1, dxp = c, dym = c - 1 - hx, dyp = c + hx, dzm = c - 1 - hxy, dzp = c + hxy;
+    const float* __restrict__ o = u + (size_t)(1 - c) * L.H + q0;   // the other colour, from q0
+    float* __restrict__ uo = u + (size_t)c * L.H + q0;
+    const float* __restrict__ bo = b + (size_t)c * L.H + q0;
+    const float cmy = L.ax[1].cm[j], cpy = L.ax[1].cp[j], dgy = L.ax[1].dg[j];
+    const float cmz = L.ax[2].cm[k], cpz = L.ax[2].cp[k], dgz = L.ax[2].dg[k];
+    const float* __restrict__ cmx = L.ax[0].cm + i1;
+    const float* __restrict__ cpx = L.ax[0].cp + i1;
+    const float* __restrict__ dgx = L.ax[0].dg + i1;
+    if (row + pf < my * (L.nz - 2)) {
+        // (an interior row's lines, up to 31 values past its end: still inside the array, as
+        // the face plane follows)
+        const int r2 = row + pf;
+        const int k2 = r2 / my + 1, j2 = r2 - (k2 - 1) * my + 1;
+        const int i2 = ((c + j2 + k2) & 1) ? 1 : 2;
+        const unsigned q2 = ((unsigned)k2 * nxy + (unsigned)j2 * (unsigned)nx + (unsigned)i2) >> 1;
+        if (lane <= (cnt + 31) / 32) {
+            const float* pb = b + (size_t)c * L.H + q2 + 32 * lane;
+            const float* pz = u + (size_t)(1 - c) * L.H + q2 + dzp + 32 * lane;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pb));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(pz));
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        const int s = lane + 32 * v;
+        if (s < cnt) {
+            const float* __restrict__ n = o + s;
+            float t = cmx[2 * s] * n[dxm];
+            t = fmaf(cpx[2 * s], n[dxp], t);
+            t = fmaf(cmy, n[dym], t);
+            t = fmaf(cpy, n[dyp], t);
+            t = fmaf(cmz, n[dzm], t);
+            t = fmaf(cpz, n[dzp], t);
+            const float acc = bo[s] - t;
+            uo[s] = rb_point32(acc, dgx[2 * s] + dgy + dgz);
+        }
+    }
+}
+
+template <int V>
+cudaError_t launch_split_rows_v(const LevelT<float>& L, float* u, const float* b, int colour, cudaStream_t s)
+{
+    // prefetch distance: half the rows the device holds resident (cached per device)
+    static int pf_rows[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (pf_rows[dev] == 0) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_split_rows<V>, 256, 0);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        pf_rows[dev] = std::max(1, per_sm * sms * 8 / 2);
+    }
+    const int rows = (L.ny - 2) * (L.nz - 2);
+    k_rbgs_split_rows<V><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(L, u, b, colour, pf_rows[dev]);
+    return cudaGetLastError();
+}
+
+// nodes of one colour per interior row, in units of 32 (0: too long for the row-per-warp kernel)
+inline int split_rows_v(int nx) { return (nx - 1) / 2 <= 256 ? std::max(1, ((nx - 1) / 2 + 31) / 32) : 0; }
+
+// nt > 0: k_rbgs with nt threads per block; nt == 0: k_rbgs_row (rows of at most 1023 nodes),
+// over colour-split storage k_rbgs_split_rows (rows of at most 513 nodes)
 template <typename T>
 cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt)
 {
+    const bool split = L.lsh != 0;
+    if (split && sizeof(T) != 4) return cudaErrorInvalidValue;   // FP64 levels keep natural storage
+    if (nt == 0 && split) {
+        if constexpr (sizeof(T) == 4) {
+            if (L.ny < 3 || L.nz < 3) return cudaErrorInvalidValue;
+            switch (split_rows_v(L.nx)) {
+                case 1: return launch_split_rows_v<1>(L, u, b, colour, s);
+                case 2: return launch_split_rows_v<2>(L, u, b, colour, s);
+                case 3: return launch_split_rows_v<3>(L, u, b, colour, s);
+                case 4: return launch_split_rows_v<4>(L, u, b, colour, s);
+                case 5: return launch_split_rows_v<5>(L, u, b, colour, s);
+                case 6: return launch_split_rows_v<6>(L, u, b, colour, s);
+                case 7: return launch_split_rows_v<7>(L, u, b, colour, s);
+                case 8: return launch_split_rows_v<8>(L, u, b, colour, s);
+                default: return cudaErrorInvalidValue;
+            }
+        }
+    }
     if (nt == 0) {
         const int th = ((L.nx + 1) / 2 + 31) / 32 * 32;
         if (th > 512 || L.ny < 3 || L.nz < 3 || L.nz - 2 > 65535) return cudaErrorInvalidValue;
-        k_rbgs_row<T><<<dim3((unsigned)(L.ny - 2), (unsigned)(L.nz - 2)), th, 0, s>>>(L, u, b, colour);
+        const dim3 g((unsigned)(L.ny - 2), (unsigned)(L.nz - 2));
+        if (split)
+            k_rbgs_row<T, 1><<<g, th, 0, s>>>(L, u, b, colour);
+        else
+            k_rbgs_row<T, 0><<<g, th, 0, s>>>(L, u, b, colour);
         return cudaGetLastError();
     }
     if (nt < 32 || nt > 512 || nt % 32) return cudaErrorInvalidValue;
     const size_t N = L.N();
     const size_t nhalf = (N + 1 - colour) / 2;
-    k_rbgs<T><<<(unsigned)((nhalf + nt - 1) / nt), nt, 0, s>>>(L, u, b, colour, nhalf);
+    const unsigned g = (unsigned)((nhalf + nt - 1) / nt);
+    if (split)
+        k_rbgs<T, 1><<<g, nt, 0, s>>>(L, u, b, colour, nhalf);
+    else
+        k_rbgs<T, 0><<<g, nt, 0, s>>>(L, u, b, colour, nhalf);
     return cudaGetLastError();
 }
 
@@ -144,6 +287,7 @@ __global__ void __launch_bounds__(NT) k_apply(LevelT<T> L, const T* __restrict__
 template <typename T>
 cudaError_t launch_residual(const LevelT<T>& L, const T* u, const T* b, T* r, cudaStream_t s)
 {
+    if (L.lsh) return cudaErrorInvalidValue;   // natural storage only
     k_residual<T><<<(unsigned)((L.N() + NT - 1) / NT), NT, 0, s>>>(L, u, b, r);
     return cudaGetLastError();
 }
@@ -151,6 +295,7 @@ cudaError_t launch_residual(const LevelT<T>& L, const T* u, const T* b, T* r, cu
 template <typename T>
 cudaError_t launch_apply(const LevelT<T>& L, const T* u, T* Au, cudaStream_t s)
 {
+    if (L.lsh) return cudaErrorInvalidValue;
     k_apply<T><<<(unsigned)((L.N() + NT - 1) / NT), NT, 0, s>>>(L, u, Au);
     return cudaGetLastError();
 }
@@ -189,13 +334,14 @@ __global__ void __launch_bounds__(NT) k_restrict(LevelT<T> F, LevelT<T> C, const
 template <typename T>
 cudaError_t launch_restrict(const LevelT<T>& F, const LevelT<T>& C, const T* r, T* bc, cudaStream_t s)
 {
+    if (F.lsh || C.lsh) return cudaErrorInvalidValue;
     k_restrict<T><<<(unsigned)((C.N() + NT - 1) / NT), NT, 0, s>>>(F, C, r, bc);
     return cudaGetLastError();
 }
 
 // u += P ec: per axis an even fine node sits on a coarse node (weight 1), an odd one
 // between two (weights pl, pr in physical coordinates).
-template <typename T>
+template <typename T, int LS>
 __global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, const T* __restrict__ ec,
                                                    T* __restrict__ u)
 {
@@ -218,13 +364,19 @@ __global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, co
             const T s = (ni == 2) ? fma(wx[0], row[0], wx[1] * row[1]) : row[0];
             e = fma(wz[c] * wy[bb], s, e);
         }
-    u[P] += e;
+    u[pos<LS>(F, P)] += e;
 }
 
+// (the fine level in either storage order, the coarse one natural)
 template <typename T>
 cudaError_t launch_prolong_add(const LevelT<T>& F, const LevelT<T>& C, const T* ec, T* u, cudaStream_t s)
 {
-    k_prolong_add<T><<<(unsigned)((F.N() + NT - 1) / NT), NT, 0, s>>>(F, C, ec, u);
+    if (C.lsh) return cudaErrorInvalidValue;
+    const unsigned g = (unsigned)((F.N() + NT - 1) / NT);
+    if (F.lsh)
+        k_prolong_add<T, 1><<<g, NT, 0, s>>>(F, C, ec, u);
+    else
+        k_prolong_add<T, 0><<<g, NT, 0, s>>>(F, C, ec, u);
     return cudaGetLastError();
 }
 
@@ -338,14 +490,19 @@ __device__ __forceinline__ T offdiag_flat(const LevelT<T>& L, const T* __restric
     return t;
 }
 
-template <typename T>
+template <typename T, int LS = 0>
 __device__ __forceinline__ T resid_at(const LevelT<T>& F, const T* __restrict__ u, const T* __restrict__ b, size_t P,
                                       int i, int j, int k)
 {
-    return b[P] - fma(-dsum(F, i, j, k), u[P], offdiag_flat(F, u, P, i, j, k));
+    if constexpr (LS == 0) {
+        return b[P] - fma(-dsum(F, i, j, k), u[P], offdiag_flat(F, u, P, i, j, k));
+    } else {
+        const unsigned Q = pos<LS>(F, P);
+        return b[Q] - fma(-dsum(F, i, j, k), u[Q], offdiag<LS>(F, u, P, i, j, k));
+    }
 }
 
-template <typename T>
+template <typename T, int LS>
 __global__ void __launch_bounds__(NT) k_resid_restrict(LevelT<T> F, LevelT<T> C, const T* __restrict__ u,
                                                       const T* __restrict__ b, T* __restrict__ bc, T* __restrict__ uc)
 {
@@ -369,19 +526,25 @@ __global__ void __launch_bounds__(NT) k_resid_restrict(LevelT<T> F, LevelT<T> C,
         for (int bb = 0; bb < 3; bb++) {
             const int fk = 2 * K - 1 + c, fj = 2 * J - 1 + bb, fi = 2 * I - 1;
             const size_t P = (size_t)fk * sz + (size_t)fj * sy + fi;
-            const T r0 = resid_at(F, u, b, P, fi, fj, fk);
-            const T r1 = resid_at(F, u, b, P + 1, fi + 1, fj, fk);
-            const T r2 = resid_at(F, u, b, P + 2, fi + 2, fj, fk);
+            const T r0 = resid_at<T, LS>(F, u, b, P, fi, fj, fk);
+            const T r1 = resid_at<T, LS>(F, u, b, P + 1, fi + 1, fj, fk);
+            const T r2 = resid_at<T, LS>(F, u, b, P + 2, fi + 2, fj, fk);
             acc = fma(wz[c] * wy[bb], fma(wx[0], r0, fma(wx[1], r1, wx[2] * r2)), acc);
         }
     bc[t] = acc;
 }
 
+// (the fine level in either storage order, the coarse one natural)
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelT<T>& F, const LevelT<T>& C, const T* u, const T* b, T* bc, T* uc,
                                   cudaStream_t s)
 {
-    k_resid_restrict<T><<<(unsigned)((C.N() + NT - 1) / NT), NT, 0, s>>>(F, C, u, b, bc, uc);
+    if (C.lsh) return cudaErrorInvalidValue;
+    const unsigned g = (unsigned)((C.N() + NT - 1) / NT);
+    if (F.lsh)
+        k_resid_restrict<T, 1><<<g, NT, 0, s>>>(F, C, u, b, bc, uc);
+    else
+        k_resid_restrict<T, 0><<<g, NT, 0, s>>>(F, C, u, b, bc, uc);
     return cudaGetLastError();
 }
 
@@ -595,6 +758,8 @@ cudaError_t launch_bottom(const BottomArgs<T>& a, cudaStream_t s)
 {
     const size_t smem = bottom_smem_bytes(a);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    for (int q = 0; q < a.nlev; q++)
+        if (a.lv[q].lsh) return cudaErrorInvalidValue;   // natural storage only
     k_bottom<T><<<1, BOT_NT, smem, s>>>(a);
     return cudaGetLastError();
 }
@@ -783,10 +948,11 @@ __global__ void __launch_bounds__(NT) k_bnorm(LevelT<double> L, const double* __
     reduce_finish(block_sum<NT>(acc, sm), red, sm);
 }
 
-// r = b - A u (written when r != nullptr, FP32 copy when r32 != nullptr) and ||r||^2
+// r = b - A u (written when r != nullptr, FP32 copy when r32 != nullptr, in colour-split
+// storage when h32 = ceil(N / 2) is nonzero) and ||r||^2
 __global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const double* __restrict__ u,
                                                   const double* __restrict__ b, double* __restrict__ r,
-                                                  float* __restrict__ r32, Red red)
+                                                  float* __restrict__ r32, unsigned h32, Red red)
 {
     __shared__ double sm[32];
     double acc = 0.0;
@@ -797,7 +963,7 @@ __global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const doubl
         double v = 0.0;
         if (!is_face(L, i, j, k)) v = b[P] - fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
         if (r) r[P] = v;
-        if (r32) r32[P] = (float)v;
+        if (r32) r32[h32 ? ((unsigned)P >> 1) + ((unsigned)P & 1u) * h32 : (unsigned)P] = (float)v;
         acc = fma(v, v, acc);
     }
     reduce_finish(block_sum<NT>(acc, sm), red, sm);
@@ -874,6 +1040,9 @@ __device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int
     return L.ax[0].dual[i] * L.ax[1].dual[j] * L.ax[2].dual[k];
 }
 
+// (the inner CG vectors share the finest level's FP32 storage order; every kernel walks the
+// nodes in flat order, so sums are formed in the same order in both)
+template <int LS>
 __global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p,
                                                    float* __restrict__ q, Red red)
 {
@@ -883,16 +1052,18 @@ __global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float
     {
         int i, j, k;
         node_ijk(P, L, i, j, k);
+        const unsigned Q = pos<LS>(L, P);
         float v = 0.0f;
         if (!is_face(L, i, j, k)) {
-            v = fmaf(-dsum(L, i, j, k), p[P], offdiag(L, p, P, i, j, k));
-            acc = fmaf(vol32(L, i, j, k) * p[P], v, acc);
+            v = fmaf(-dsum(L, i, j, k), p[Q], offdiag<LS>(L, p, P, i, j, k));
+            acc = fmaf(vol32(L, i, j, k) * p[Q], v, acc);
         }
-        q[P] = v;
+        q[Q] = v;
     }
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
 
+template <int LS>
 __global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* __restrict__ ctl,
                                                    const float* __restrict__ p, const float* __restrict__ q,
                                                    float* __restrict__ e, float* __restrict__ r, Red red)
@@ -905,15 +1076,17 @@ __global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* 
         int i, j, k;
         node_ijk(P, L, i, j, k);
         if (is_face(L, i, j, k)) continue;
-        e[P] = fmaf(alpha, p[P], e[P]);
-        const float rv = fmaf(-alpha, q[P], r[P]);
-        r[P] = rv;
+        const unsigned Q = pos<LS>(L, P);
+        e[Q] = fmaf(alpha, p[Q], e[Q]);
+        const float rv = fmaf(-alpha, q[Q], r[Q]);
+        r[Q] = rv;
         acc = fmaf(rv, rv, acc);
     }
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
 
 // <r, z>_vol, or ||r||^2 when z == nullptr
+template <int LS>
 __global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __restrict__ r,
                                              const float* __restrict__ z, Red red)
 {
@@ -924,11 +1097,13 @@ __global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __re
         int i, j, k;
         node_ijk(P, L, i, j, k);
         if (is_face(L, i, j, k)) continue;
-        acc = z ? fmaf(vol32(L, i, j, k) * r[P], z[P], acc) : fmaf(r[P], r[P], acc);
+        const unsigned Q = pos<LS>(L, P);
+        acc = z ? fmaf(vol32(L, i, j, k) * r[Q], z[Q], acc) : fmaf(r[Q], r[Q], acc);
     }
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
 
+template <int LS>
 __global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* __restrict__ ctl,
                                                   const float* __restrict__ z, float* __restrict__ p)
 {
@@ -936,16 +1111,20 @@ __global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* _
     if (P >= L.N()) return;
     int i, j, k;
     node_ijk(P, L, i, j, k);
-    p[P] = is_face(L, i, j, k) ? 0.0f : fmaf((float)ctl->beta_in, p[P], z[P]);
+    const unsigned Q = pos<LS>(L, P);
+    p[Q] = is_face(L, i, j, k) ? 0.0f : fmaf((float)ctl->beta_in, p[Q], z[Q]);
 }
 
-// u += e (FP64 accumulation of the FP32 correction); e = 0 for the next inner solve
-__global__ void __launch_bounds__(NT) k_add_correction(size_t N, double* __restrict__ u, float* __restrict__ e)
+// u += e (FP64 accumulation of the FP32 correction, e in colour-split storage when h32 =
+// ceil(N / 2) is nonzero); e = 0 for the next inner solve
+__global__ void __launch_bounds__(NT) k_add_correction(size_t N, double* __restrict__ u, float* __restrict__ e,
+                                                      unsigned h32)
 {
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
     if (P >= N) return;
-    u[P] += (double)e[P];
-    e[P] = 0.0f;
+    const unsigned Q = h32 ? ((unsigned)P >> 1) + ((unsigned)P & 1u) * h32 : (unsigned)P;
+    u[P] += (double)e[Q];
+    e[Q] = 0.0f;
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n)
@@ -963,9 +1142,9 @@ cudaError_t launch_bnorm(const LevelT<double>& L, const double* u, const double*
     return cudaGetLastError();
 }
 cudaError_t launch_resid_norm(const LevelT<double>& L, const double* u, const double* b, double* r, float* r32,
-                              const Red& red, cudaStream_t s)
+                              unsigned h32, const Red& red, cudaStream_t s)
 {
-    k_resid_norm<<<RGRID(L)>>>(L, u, b, r, r32, red);
+    k_resid_norm<<<RGRID(L)>>>(L, u, b, r, r32, h32, red);
     return cudaGetLastError();
 }
 cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, const Red& red, cudaStream_t s)
@@ -991,28 +1170,40 @@ cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const doubl
 }
 cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s)
 {
-    k_apply_dot32<<<RGRID(L)>>>(L, p, q, red);
+    if (L.lsh)
+        k_apply_dot32<1><<<RGRID(L)>>>(L, p, q, red);
+    else
+        k_apply_dot32<0><<<RGRID(L)>>>(L, p, q, red);
     return cudaGetLastError();
 }
 cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
                                float* r, const Red& red, cudaStream_t s)
 {
-    k_update_er32<<<RGRID(L)>>>(L, ctl, p, q, e, r, red);
+    if (L.lsh)
+        k_update_er32<1><<<RGRID(L)>>>(L, ctl, p, q, e, r, red);
+    else
+        k_update_er32<0><<<RGRID(L)>>>(L, ctl, p, q, e, r, red);
     return cudaGetLastError();
 }
 cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, const Red& red, cudaStream_t s)
 {
-    k_dot32<<<RGRID(L)>>>(L, r, z, red);
+    if (L.lsh)
+        k_dot32<1><<<RGRID(L)>>>(L, r, z, red);
+    else
+        k_dot32<0><<<RGRID(L)>>>(L, r, z, red);
     return cudaGetLastError();
 }
 cudaError_t launch_update_p32(const LevelT<float>& L, const Ctl* ctl, const float* z, float* p, cudaStream_t s)
 {
-    k_update_p32<<<GRID(L)>>>(L, ctl, z, p);
+    if (L.lsh)
+        k_update_p32<1><<<GRID(L)>>>(L, ctl, z, p);
+    else
+        k_update_p32<0><<<GRID(L)>>>(L, ctl, z, p);
     return cudaGetLastError();
 }
-cudaError_t launch_add_correction(size_t N, double* u, float* e, cudaStream_t s)
+cudaError_t launch_add_correction(size_t N, double* u, float* e, unsigned h32, cudaStream_t s)
 {
-    k_add_correction<<<(unsigned)((N + NT - 1) / NT), NT, 0, s>>>(N, u, e);
+    k_add_correction<<<(unsigned)((N + NT - 1) / NT), NT, 0, s>>>(N, u, e, h32);
     return cudaGetLastError();
 }
 cudaError_t launch_to_f32(const double* a, float* b, size_t n, cudaStream_t s)

@@ -406,7 +406,7 @@ template <typename T>
 cudaError_t launch_rb_slab(const LevelT<T>& L, const T* uin, T* uout, const T* b, int first, int zero_in,
                            const SlabShape& sh, cudaStream_t s)
 {
-    if (!slab_shape_ok(sh, sizeof(T)) || uin == uout) return cudaErrorInvalidValue;
+    if (!slab_shape_ok(sh, sizeof(T)) || uin == uout || L.lsh) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((L.nx + sh.tx - 1) / sh.tx), (unsigned)((L.ny + sh.ty - 1) / sh.ty),
                     (unsigned)((L.nz + sh.kz - 1) / sh.kz));
     const size_t smem = slab_smem_bytes(sh, sizeof(T));

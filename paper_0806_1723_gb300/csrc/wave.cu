@@ -366,7 +366,7 @@ void init_wave_attributes()
 cudaError_t launch_rb_wave(const LevelT<float>& L, const float* uin, float* uout, const float* b, int first,
                            const SlabShape& sh, cudaStream_t s)
 {
-    if (!wave_shape_ok(sh) || !wave_level_ok(L.nx, L.ny, L.nz) || uin == uout) return cudaErrorInvalidValue;
+    if (!wave_shape_ok(sh) || !wave_level_ok(L.nx, L.ny, L.nz) || uin == uout || L.lsh) return cudaErrorInvalidValue;
     // 16-byte aligned arrays: the staged copies read 16-byte aligned chunks
     if ((reinterpret_cast<uintptr_t>(uin) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(uout)) & 15)
         return cudaErrorInvalidValue;
