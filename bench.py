@@ -64,6 +64,10 @@ BATCH = 8
 # Scaled to 385^3 by the node count (the traffic is proportional to the nodes beyond L2).
 DRAM_BYTES_257 = {0: 197.9e6, 128: 195.6e6, 256: 195.8e6}
 DRAM_BYTES_257_F64 = 537.7e6
+# the half sweep over colour-split storage, one warp per row (k_rbgs_split_rows<6>), captured at
+# 385^3 itself (third launch of `bench.py --profile smoother --n 385 --split --threads 0
+# --sweeps 2`, ncu --set full: caches flushed before the launch): 230.9 MB read + 87.2 MB written
+DRAM_BYTES_385_SPLIT_ROWS = 318.1e6
 
 
 def parse():
@@ -78,14 +82,14 @@ def parse():
     p.add_argument("--no-batch64", action="store_true")
     p.add_argument("--no-pd561", action="store_true")
     p.add_argument("--no-hs", action="store_true")
-    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "pd561warm", "hs", "batch"],
+    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "pd561warm", "deposit", "hs", "batch"],
                    default=None,
                    help="run one kernel family for a profiler and exit: 'smoother' = one FP32 red-black sweep "
                         "on an n^3 graded mesh, 'solve' = one mixed solve of the workload with direct launches, "
                         "'guess' = the same with the learned initial guess, 'pd561' = one chosen-form solve "
                         "of the Pd561 graded 385^3 workload with direct launches, 'pd561warm' = the second density "
                         "of that sequence warm-started from the first one's potential (the headline's steady "
-                        "state), 'hs' = one interstitial H and S "
+                        "state), 'deposit' = two FP32-pair density deposits of the Pd561 graded 385^3 density, 'hs' = one interstitial H and S "
                         "call (tensor cores) for Pd55 on the graded 129^3 mesh, 'batch' = one graph launch of the "
                         "chosen form over the 8 Pd55 clusters of the workload (for ncu --graph-profiling graph)")
     p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
@@ -93,6 +97,8 @@ def parse():
                    help="launch shape of --profile smoother: threads per block, 0 = one block per row")
     p.add_argument("--sweeps", type=int, default=1, help="red-black sweeps of --profile smoother")
     p.add_argument("--fp64", action="store_true", help="--profile smoother in FP64 (the plain form's smoother)")
+    p.add_argument("--split", action="store_true",
+                   help="--profile smoother over colour-split storage (the finest FP32 level's layout)")
     p.add_argument("--direct", action="store_true",
                    help="launch the kernels directly instead of one CUDA graph per solve (for ncu)")
     return p.parse_args()
@@ -508,7 +514,16 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "gpu_launches": launches,
-            "roofline": roof,
+            # the dominant kernel of the Pd561 solve is the deposit (about 39 % of a warm solve,
+            # ahead of the finest level's smoother at about 20 %): instruction-issue bound
+            "roofline": {"kernel": dep["kernel"], "bound": "alu", "achieved": dep.get("issue_ginst_s"),
+                         "peak": dep.get("issue_peak_ginst_s"), "unit": "Ginst/s", "frac": dep.get("frac"),
+                         "traffic": DEPOSIT_DRAM_BYTES, "ms_per_launch": dep["ms"],
+                         "achieved_rule": "warp instructions issued per launch (ncu smsp__inst_executed.sum) / "
+                                          "CUDA-event launch time",
+                         "peak_rule": "4 schedulers x 152 SMs x 1 warp instruction per cycle x 2070 MHz",
+                         "fp32_tflops": dep.get("fp32_tflops"), "fp32_frac_of_measured_fma": dep.get("fp32_frac")},
+            "roofline_smoother": roof,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
@@ -613,11 +628,21 @@ def run_profile(args, B):
         dt = torch.float64 if args.fp64 else torch.float32
         u = torch.zeros(n ** 3, dtype=dt, device="cuda")
         b = torch.rand(n ** 3, dtype=dt, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
-        B.lasto_op_smooth(*axes, u, b, sweeps=args.sweeps, threads=args.threads)
+        if args.split and not args.fp64:
+            B.lasto_op_smooth_split(*axes, u, b, sweeps=args.sweeps, threads=args.threads)
+        else:
+            B.lasto_op_smooth(*axes, u, b, sweeps=args.sweeps, threads=args.threads)
+    elif args.profile == "deposit":
+        dc = B.DeviceCluster(synth.pd561_graded385(n_densities=1)[0])
+        for _ in range(2):
+            B.lasto_op_deposit(dc, precision=B.LASTO_PREC_MIXED)
     elif args.profile == "pd561warm":
         seq = synth.pd561_graded385(n_densities=2)
         solver = B.Poisson(n_max=385, max_atoms=561, precision=B.LASTO_PREC_MIXED, launch=1)
-        solver.set_tune_table("".join(f"{m} {m} {m} 4 0 128 0 0 0 0 0\n" for m in (385, 193, 97, 49, 25)))
+        # under a profiler the tuner's timings mean nothing; take the choices it makes without one
+        # (the finest level in colour-split storage, one warp per row; in-place half sweeps below)
+        solver.set_tune_table("385 385 385 4 3 0 0 0 0 0 0\n" +
+                              "".join(f"{m} {m} {m} 4 0 128 0 0 0 0 0\n" for m in (193, 97, 49, 25)))
         v = torch.empty((561, 25), dtype=torch.float64, device="cuda")
         pot = torch.empty(385 ** 3, dtype=torch.float64, device="cuda")
         st = solver.solve(B.DeviceCluster(seq[0]), v, potential=pot)   # the previous density
@@ -829,10 +854,10 @@ def fma_ceilings(B, stream, dev):
 
 
 def smoother_roofline(B, stream, flush, dev, tuned, probes):
-    """The dominant kernel of the headline: the FP32 smoother at 385^3, in the launch shape the
+    """The second kernel of the headline: the FP32 smoother at 385^3, in the launch shape the
     tuner chose for that level.  Algorithmic bytes (the smoother's compulsory traffic, 12 B per
-    node per FP32 sweep: u read, b read, u written): 6 B per node for one in-place half-sweep
-    launch (one colour), 12 B per node for one fused wavefront sweep.  Each shape is timed alone
+    node per FP32 sweep: u read, b read, u written): 6 B per node for one half-sweep launch (one
+    colour; natural or colour-split storage), 12 B per node for one fused wavefront sweep.  Each shape is timed alone
     with CUDA events (L2 flushed; the difference of a longer and a shorter call, so table set-up
     cancels), and the line reports the tuner's choice; `traffic` is ncu's DRAM bytes per launch
     (dram__bytes_read.sum + dram__bytes_write.sum at 257^3 in steady state, scaled by nodes)."""
@@ -861,6 +886,11 @@ def smoother_roofline(B, stream, flush, dev, tuned, probes):
         return statistics.median(ts) / 1e3
 
     shapes = {}
+    for th in (0, 128):   # half sweeps over colour-split storage (the layout's data is irrelevant here)
+        t = (timed(lambda: B.lasto_op_smooth_split(*axes, u, b, sweeps=3, threads=th)) -
+             timed(lambda: B.lasto_op_smooth_split(*axes, u, b, sweeps=1, threads=th))) / 4
+        shapes[f"split_{th if th else 'rows'}"] = {"us_per_launch": t * 1e6, "bytes_per_launch": 6.0 * n ** 3,
+                                                   "launches_per_sweep": 2, "nt": th}
     for th in (0, 128, 256):   # in-place half sweeps: per launch (2 launches per sweep)
         t = (timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=3, threads=th)) -
              timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=1, threads=th))) / 4
@@ -886,18 +916,26 @@ def smoother_roofline(B, stream, flush, dev, tuned, probes):
         if f[:4] == [str(n), str(n), str(n), "4"]:
             fused, nt, tx, ty = int(f[4]), int(f[5]), int(f[6]), int(f[7])
             pick = (f"wave_{tx}x{ty}" if fused == 2 else f"inplace_{nt if nt else 'rows'}" if fused == 0
-                    else None)
+                    else f"split_{nt if nt else 'rows'}" if fused == 3 else None)
     if pick not in shapes:
         pick = min(shapes, key=lambda k: shapes[k]["us_per_sweep"])
     c = shapes[pick]
-    if pick.startswith("inplace"):
+    traffic = None
+    if pick.startswith("split"):
+        traffic = DRAM_BYTES_385_SPLIT_ROWS if (c["nt"] == 0 and n == 385) else None
+        kernel = ("k_rbgs_split_rows<6> (red-black half sweep over colour-split storage, one warp per row, "
+                  "385^3 graded)" if c["nt"] == 0 else
+                  f"k_rbgs<float,split> (red-black half sweep over colour-split storage, {c['nt']} threads per "
+                  "block, 385^3 graded)")
+    elif pick.startswith("inplace"):
         t257 = DRAM_BYTES_257.get(c["nt"])
         kernel = ("k_rbgs_row<float> (in-place red-black half sweep, one block per row, 385^3 graded)" if c["nt"] == 0
                   else f"k_rbgs<float> (in-place red-black half sweep, {c['nt']} threads per block, 385^3 graded)")
     else:
         t257 = DRAM_BYTES_257.get("wave")
         kernel = f"k_rb_wave<float> (fused red-black wavefront sweep, tile {c['tile']}, 385^3 graded)"
-    traffic = t257 * (n / 257.0) ** 3 if t257 else None
+    if not pick.startswith("split"):
+        traffic = t257 * (n / 257.0) ** 3 if t257 else None
     return {"kernel": kernel, "bound": "hbm", "achieved": c["achieved_gbs"], "peak": peak, "unit": "GB/s",
             "frac": c["frac"], "traffic": traffic,
             "traffic_over_algorithmic": traffic / c["bytes_per_launch"] if traffic else None,
@@ -971,15 +1009,28 @@ def deposit_rate(B, synth, stream, flush, dev, probes):
            "fp32_fma_tflops_measured": probes["fp32_tflops"]}
     if DEPOSIT_FP32_FLOP is not None:
         out["fp32_tflops"] = DEPOSIT_FP32_FLOP / t / 1e12
-        out["frac"] = out["fp32_tflops"] / probes["fp32_tflops"]
+        out["fp32_frac"] = out["fp32_tflops"] / probes["fp32_tflops"]
+    # the bound it meets: instruction issue (one warp instruction per cycle per scheduler, four
+    # schedulers per SM, 152 SMs, at the sampled SM clock)
+    if DEPOSIT_WARP_INST is not None:
+        peak = 4 * 152 * MAX_SM_MHZ * 1e6 / 1e9
+        out["issue_ginst_s"] = DEPOSIT_WARP_INST / t / 1e9
+        out["issue_peak_ginst_s"] = peak
+        out["frac"] = out["issue_ginst_s"] / peak
     del dc
     torch.cuda.empty_cache()
     return out
 
 
-# FP32 FLOP of one Pd561 385^3 deposit launch (2 per FFMA, 1 per FADD / FMUL thread instruction),
-# from ncu's sass thread-instruction counts; None until captured
-DEPOSIT_FP32_FLOP = None
+# One Pd561 385^3 deposit launch (k_deposit_df) under ncu (`bench.py --profile deposit`, second
+# launch): FP32 FLOP from the sass thread-instruction counts (2 per FFMA: 148.0 G, 1 per FADD:
+# 334.6 G and per FMUL: 109.4 G), the warp instructions issued (smsp__inst_executed.sum) and the
+# DRAM bytes (read 11.8 MB + written 848.0 MB); the launch issued 0.90 instructions per cycle per
+# scheduler.
+DEPOSIT_FP32_FLOP = 740.0e9
+DEPOSIT_WARP_INST = 40.160e9
+DEPOSIT_DRAM_BYTES = 859.8e6
+MAX_SM_MHZ = 2070.0   # the GB300's maximum SM clock (the clock the timed runs hold)
 
 
 if __name__ == "__main__":

@@ -309,7 +309,9 @@ struct DepArgs {
     int* status;
 };
 
-constexpr int SAF = 16;   // FP32-pair deposit, per atom floats: D(x,y,z) pairs, W_k pairs, R^2, pad
+// FP32-pair deposit, per atom floats: {D(x,y,z) rounded to FP32, R^2}, {W_k rounded to FP32, 0},
+// then the double-float D(x,y,z) and W_k pairs (D = atom - tile origin)
+constexpr int SAF = 20;
 __global__ void k_deposit_df(DepArgs a);
 
 // per-atom fields staged in shared memory
@@ -539,13 +541,16 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
             float* o = sat + SAF * q;
             const df Dx = dfa::from_double(r[RX] - ox), Dy = dfa::from_double(r[RX + 1] - oy),
                      Dz = dfa::from_double(r[RX + 2] - oz);
-            o[0] = Dx.h; o[1] = Dx.l; o[2] = Dy.h; o[3] = Dy.l; o[4] = Dz.h; o[5] = Dz.l;
+            o[0] = Dx.h; o[1] = Dy.h; o[2] = Dz.h;
+            o[3] = reinterpret_cast<const float*>(r + RXF)[3];
+            o[8] = Dx.h; o[9] = Dx.l; o[10] = Dy.h; o[11] = Dy.l; o[12] = Dz.h; o[13] = Dz.l;
             for (int c = 0; c < 3; c++) {
                 const df W = dfa::from_double(r[RW + c]);
-                o[6 + 2 * c] = W.h;
-                o[7 + 2 * c] = W.l;
+                o[4 + c] = W.h;
+                o[14 + 2 * c] = W.h;
+                o[15 + 2 * c] = W.l;
             }
-            o[12] = reinterpret_cast<const float*>(r + RXF)[3];
+            o[7] = 0.0f;
         }
         __syncthreads();
         nkept = total;
@@ -572,37 +577,44 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     df orr2 = {0.0f, 0.0f}, odx = s, ody = s, odz = s;
     for (int q0 = 0; q0 < nkept; q0++) {
         const float* o = sat + SAF * q0;
-        const float fx = (px.h - o[0]) + (px.l - o[1]), fy = (py.h - o[2]) + (py.l - o[3]);
-        const float fz = (pz.h - o[4]) + (pz.l - o[5]);
+        // the pair's distance in FP32 from the FP32 roundings of the two offsets (one subtraction
+        // per axis): the atom's offset is at most r + the tile's extent, so r carries a relative
+        // error of ~1.5e-7 wherever the far field applies (r >= FAR_T / zeta_max)
+        const float4 A = *reinterpret_cast<const float4*>(o);
+        const float fx = px.h - A.x, fy = py.h - A.y, fz = pz.h - A.z;
         const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
         if (r2f > cut2) continue;
         if (r2f > far2) {
-            // far pair: every term is below e^-FAR_T of its weight.  r in FP32 already carries a
-            // relative error of ~1e-7 (so ~2e-6 in e^{-zeta r} at zeta r = 20); the fast
-            // exponential adds an error of the same size, and e^{-zeta_q r} for zeta_q = 2 zeta_0
+            // far pair: every term is below e^-FAR_T of its weight; the ~1.5e-7 relative error of
+            // r is ~3e-6 in e^{-zeta r} at zeta r = 20, the fast reciprocal square root and
+            // exponential add errors of the same size, and e^{-zeta_q r} for zeta_q = 2 zeta_0
             // is the square of e^{-zeta_0 r}.  Terms beyond zeta r = EXP_CUT are dropped.
-            const float rf = sqrtf(r2f);
+            const float4 W = *reinterpret_cast<const float4*>(o + 4);
+            const float rf = r2f * rsqrtf(r2f);
             const float e0 = __expf(-zt[0].h * rf);
-            sfar = fmaf(o[6], e0, sfar);
-#pragma unroll
-            for (int q = 1; q < 3; q++) {
-                if (twice[q]) {
-                    sfar = fmaf(o[6 + 2 * q], e0 * e0, sfar);
-                } else {
-                    const float e = zt[q].h * rf;
-                    if (e < EXP_CUT) sfar = fmaf(o[6 + 2 * q], __expf(-e), sfar);
-                }
+            sfar = fmaf(W.x, e0, sfar);
+            if (twice[1]) {
+                sfar = fmaf(W.y, e0 * e0, sfar);
+            } else {
+                const float e = zt[1].h * rf;
+                if (e < EXP_CUT) sfar = fmaf(W.y, __expf(-e), sfar);
+            }
+            if (twice[2]) {
+                sfar = fmaf(W.z, e0 * e0, sfar);
+            } else {
+                const float e = zt[2].h * rf;
+                if (e < EXP_CUT) sfar = fmaf(W.z, __expf(-e), sfar);
             }
             continue;
         }
-        const df dx = dfa::add(px, df{-o[0], -o[1]});
-        const df dy = dfa::add(py, df{-o[2], -o[3]});
-        const df dz = dfa::add(pz, df{-o[4], -o[5]});
+        const df dx = dfa::add(px, df{-o[8], -o[9]});
+        const df dy = dfa::add(py, df{-o[10], -o[11]});
+        const df dz = dfa::add(pz, df{-o[12], -o[13]});
         const df r2 = dfa::add(dfa::add(dfa::sqr(dx), dfa::sqr(dy)), dfa::sqr(dz));
         if (r2.h > cut2) continue;
-        if (r2.h < o[12] * (1.0f + 2e-6f)) {
+        if (r2.h < A.w * (1.0f + 2e-6f)) {
             const int t = list[q0];
-            const bool in = (r2.h < o[12] * (1.0f - 2e-6f)) ? true : inside_fp64(a, x, y, z, t);
+            const bool in = (r2.h < A.w * (1.0f - 2e-6f)) ? true : inside_fp64(a, x, y, z, t);
             if (in) {
                 own = t;
                 orr2 = r2;
@@ -620,7 +632,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
             const df tq = dfa::mul(r, zt[q]);
             if (tq.h >= EXP_CUT) continue;
             if (tq.h > FAR_T) {
-                sfar = fmaf(o[6 + 2 * q], expf(-tq.h), sfar);
+                sfar = fmaf(o[14 + 2 * q], expf(-tq.h), sfar);
             } else {
                 // zeta_q = 2 zeta_0 (as in the density model's 1.5, 3.0): e^{-zeta_q r} = (e^{-zeta_0 r})^2
                 const df eq = (q > 0 && twice[q] && have0) ? dfa::sqr(e0) : dfa::exp_neg(tq, th, tl);
@@ -628,7 +640,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
                     e0 = eq;
                     have0 = true;
                 }
-                s = dfa::add(s, dfa::mul(df{o[6 + 2 * q], o[7 + 2 * q]}, eq));
+                s = dfa::add(s, dfa::mul(df{o[14 + 2 * q], o[15 + 2 * q]}, eq));
             }
         }
     }
