@@ -488,7 +488,8 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
     const LevelT<T> VC = Arr<T>::view(C);
     if (sizeof(T) == 4) {
         // FP32: form the 27 fine residuals inside the restriction (cheaper than a pass)
-        TRY(launch_resid_restrict<T>(V, VC, cur, b, Arr<T>::b(C), Arr<T>::u(C), s));
+        // after nu1 >= 1 sweeps that end on the black half sweep the black residuals are zero
+        TRY(launch_resid_restrict<T>(V, VC, cur, b, Arr<T>::b(C), Arr<T>::u(C), nu1 > 0, s));
     } else {
         // FP64: each residual once (FP64 arithmetic, not bandwidth, bounds this chip)
         TRY(launch_residual<T>(V, cur, b, r, s));

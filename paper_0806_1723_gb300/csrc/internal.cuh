@@ -225,9 +225,11 @@ cudaError_t launch_prolong_add(const LevelT<T>& fine, const LevelT<T>& coarse, c
 template <typename T>
 cudaError_t launch_coarse_apply(const LevelT<T>& L, const CoarseEig* eig, const T* b, T* e, bool add, cudaStream_t s);
 
+// red_only (FP32): the fine iterate's last half sweep was black, so only the red residuals are
+// formed (the black ones are zero)
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelT<T>& fine, const LevelT<T>& coarse, const T* u, const T* b, T* bc, T* uc,
-                                  cudaStream_t s);
+                                  bool red_only, cudaStream_t s);
 
 // slab.cu: fused red-black smoother.  One pass = ns full sweeps (colour `first`, then the
 // other), u_in -> u_out (distinct arrays; every node of u_out written).  A CTA owns a

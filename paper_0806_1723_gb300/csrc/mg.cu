@@ -367,11 +367,54 @@ __global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, co
     u[pos<LS>(F, P)] += e;
 }
 
+// The same in FP32 with one warp per interior fine (j, k) row, lanes along i: the row's y and z
+// weights and coarse rows once per warp, no index division; the node expression is
+// k_prolong_add's, so the two are bitwise equal.
+template <int LS>
+__global__ void __launch_bounds__(256) k_prolong_add_rows(LevelT<float> F, LevelT<float> C,
+                                                         const float* __restrict__ ec, float* __restrict__ u)
+{
+    const int my = F.ny - 2;
+    const int row = (int)(blockIdx.x * 8 + (threadIdx.x >> 5));
+    if (row >= my * (F.nz - 2)) return;
+    const int lane = threadIdx.x & 31;
+    const int k = row / my + 1, j = row - (k - 1) * my + 1;
+    const int nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
+    const float wy[2] = {F.ax[1].pl[j], F.ax[1].pr[j]};
+    const float wz[2] = {F.ax[2].pl[k], F.ax[2].pr[k]};
+    const size_t sy = C.nx, sz = (size_t)C.nx * C.ny;
+    const float* __restrict__ crow = ec + (size_t)(k >> 1) * sz + (size_t)(j >> 1) * sy;
+    const unsigned f0 = ((unsigned)k * (unsigned)F.ny + (unsigned)j) * (unsigned)F.nx;
+    for (int i = 1 + lane; i < F.nx - 1; i += 32) {
+        const int ni = (i & 1) ? 2 : 1;
+        const float wx[2] = {F.ax[0].pl[i], F.ax[0].pr[i]};
+        const float* base = crow + (i >> 1);
+        float e = 0.0f;
+        for (int c = 0; c < nk; c++)
+            for (int bb = 0; bb < nj; bb++) {
+                const float* r = base + c * sz + bb * sy;
+                const float sv = (ni == 2) ? fmaf(wx[0], r[0], wx[1] * r[1]) : r[0];
+                e = fmaf(wz[c] * wy[bb], sv, e);
+            }
+        u[pos<LS>(F, f0 + (unsigned)i)] += e;
+    }
+}
+
 // (the fine level in either storage order, the coarse one natural)
 template <typename T>
 cudaError_t launch_prolong_add(const LevelT<T>& F, const LevelT<T>& C, const T* ec, T* u, cudaStream_t s)
 {
     if (C.lsh) return cudaErrorInvalidValue;
+    if constexpr (sizeof(T) == 4) {
+        if (F.ny >= 3 && F.nz >= 3) {
+            const unsigned g = (unsigned)(((size_t)(F.ny - 2) * (F.nz - 2) + 7) / 8);
+            if (F.lsh)
+                k_prolong_add_rows<1><<<g, 256, 0, s>>>(F, C, ec, u);
+            else
+                k_prolong_add_rows<0><<<g, 256, 0, s>>>(F, C, ec, u);
+            return cudaGetLastError();
+        }
+    }
     const unsigned g = (unsigned)((F.N() + NT - 1) / NT);
     if (F.lsh)
         k_prolong_add<T, 1><<<g, NT, 0, s>>>(F, C, ec, u);
@@ -534,12 +577,73 @@ __global__ void __launch_bounds__(NT) k_resid_restrict(LevelT<T> F, LevelT<T> C,
     bc[t] = acc;
 }
 
-// (the fine level in either storage order, the coarse one natural)
+// The same in FP32 with one warp per coarse (J, K) row, lanes along I (no index division; the
+// row's y and z weights once per warp).  RED_ONLY: the fine iterate comes straight from a half
+// sweep of the black nodes, whose residuals are then zero (each black equation was just solved
+// with its red neighbours fixed), so only the red residuals are formed and the black ones enter
+// the weighted sum as zeros: 13 of the 27 residuals per coarse node, and the black half of b is
+// not read.
+template <int LS, int RED_ONLY>
+__global__ void __launch_bounds__(256) k_resid_restrict_rows(LevelT<float> F, LevelT<float> C,
+                                                            const float* __restrict__ u, const float* __restrict__ b,
+                                                            float* __restrict__ bc, float* __restrict__ uc)
+{
+    const int row = (int)(blockIdx.x * 8 + (threadIdx.x >> 5));
+    if (row >= C.ny * C.nz) return;
+    const int lane = threadIdx.x & 31;
+    const int K = row / C.ny, J = row - K * C.ny;
+    const size_t cb = (size_t)row * C.nx;
+    const bool face_row = J == 0 || K == 0 || J == C.ny - 1 || K == C.nz - 1;
+    const float* wy = F.ax[1].rw + 3 * (face_row ? 0 : J);
+    const float* wz = F.ax[2].rw + 3 * (face_row ? 0 : K);
+    const unsigned sy = (unsigned)F.nx, sz = (unsigned)F.nx * (unsigned)F.ny;
+    for (int I = lane; I < C.nx; I += 32) {
+        uc[cb + I] = 0.0f;
+        if (face_row || I == 0 || I == C.nx - 1) {
+            bc[cb + I] = 0.0f;
+            continue;
+        }
+        const float* wx = F.ax[0].rw + 3 * I;
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int bb = 0; bb < 3; bb++) {
+                const int fk = 2 * K - 1 + c, fj = 2 * J - 1 + bb, fi = 2 * I - 1;
+                const unsigned P = (unsigned)fk * sz + (unsigned)fj * sy + (unsigned)fi;
+                float r0 = 0.0f, r1 = 0.0f, r2 = 0.0f;
+                if (!RED_ONLY || ((fj + fk) & 1)) {   // (fi, fj, fk) and (fi + 2, fj, fk) red
+                    r0 = resid_at<float, LS>(F, u, b, P, fi, fj, fk);
+                    r2 = resid_at<float, LS>(F, u, b, P + 2, fi + 2, fj, fk);
+                }
+                if (!RED_ONLY || !((fj + fk) & 1))    // (fi + 1, fj, fk) red
+                    r1 = resid_at<float, LS>(F, u, b, P + 1, fi + 1, fj, fk);
+                acc = fmaf(wz[c] * wy[bb], fmaf(wx[0], r0, fmaf(wx[1], r1, wx[2] * r2)), acc);
+            }
+        bc[cb + I] = acc;
+    }
+}
+
+// (the fine level in either storage order, the coarse one natural; red_only: the fine iterate's
+// last half sweep was black, FP32 only)
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelT<T>& F, const LevelT<T>& C, const T* u, const T* b, T* bc, T* uc,
-                                  cudaStream_t s)
+                                  bool red_only, cudaStream_t s)
 {
     if (C.lsh) return cudaErrorInvalidValue;
+    if constexpr (sizeof(T) == 4) {
+        const unsigned g = (unsigned)(((size_t)C.ny * C.nz + 7) / 8);
+        if (F.lsh && red_only)
+            k_resid_restrict_rows<1, 1><<<g, 256, 0, s>>>(F, C, u, b, bc, uc);
+        else if (F.lsh)
+            k_resid_restrict_rows<1, 0><<<g, 256, 0, s>>>(F, C, u, b, bc, uc);
+        else if (red_only)
+            k_resid_restrict_rows<0, 1><<<g, 256, 0, s>>>(F, C, u, b, bc, uc);
+        else
+            k_resid_restrict_rows<0, 0><<<g, 256, 0, s>>>(F, C, u, b, bc, uc);
+        return cudaGetLastError();
+    }
+    if (red_only) return cudaErrorInvalidValue;
     const unsigned g = (unsigned)((C.N() + NT - 1) / NT);
     if (F.lsh)
         k_resid_restrict<T, 1><<<g, NT, 0, s>>>(F, C, u, b, bc, uc);
@@ -1040,25 +1144,32 @@ __device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int
     return L.ax[0].dual[i] * L.ax[1].dual[j] * L.ax[2].dual[k];
 }
 
-// (the inner CG vectors share the finest level's FP32 storage order; every kernel walks the
-// nodes in flat order, so sums are formed in the same order in both)
+// (the inner CG vectors share the finest level's FP32 storage order; every kernel addresses them
+// through the storage map, and the sums are formed in the same order in both)
+// q = A p and <p, q>_vol with one warp per (j, k) row (faces included: q = 0 there), lanes along
+// i, rows dealt round robin over the reduction grid; the sums are formed in the same order in
+// both storage orders.
 template <int LS>
-__global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p,
-                                                   float* __restrict__ q, Red red)
+__global__ void __launch_bounds__(NT) k_apply_dot32_rows(LevelT<float> L, const float* __restrict__ p,
+                                                        float* __restrict__ q, Red red)
 {
     __shared__ double sm[32];
     float acc = 0.0f;
-    GRID_STRIDE(P, L.N())
-    {
-        int i, j, k;
-        node_ijk(P, L, i, j, k);
-        const unsigned Q = pos<LS>(L, P);
-        float v = 0.0f;
-        if (!is_face(L, i, j, k)) {
-            v = fmaf(-dsum(L, i, j, k), p[Q], offdiag<LS>(L, p, P, i, j, k));
-            acc = fmaf(vol32(L, i, j, k) * p[Q], v, acc);
+    const int rows = L.ny * L.nz, lane = threadIdx.x & 31;
+    for (int row = (int)(blockIdx.x * (NT / 32) + (threadIdx.x >> 5)); row < rows; row += (int)gridDim.x * (NT / 32)) {
+        const int k = row / L.ny, j = row - k * L.ny;
+        const unsigned f0 = (unsigned)row * (unsigned)L.nx;
+        const bool face_row = j == 0 || k == 0 || j == L.ny - 1 || k == L.nz - 1;
+        for (int i = lane; i < L.nx; i += 32) {
+            const unsigned P = f0 + (unsigned)i;
+            const unsigned Q = pos<LS>(L, P);
+            float v = 0.0f;
+            if (!face_row && i != 0 && i != L.nx - 1) {
+                v = fmaf(-dsum(L, i, j, k), p[Q], offdiag<LS>(L, p, P, i, j, k));
+                acc = fmaf(vol32(L, i, j, k) * p[Q], v, acc);
+            }
+            q[Q] = v;
         }
-        q[Q] = v;
     }
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
@@ -1171,9 +1282,9 @@ cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const doubl
 cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s)
 {
     if (L.lsh)
-        k_apply_dot32<1><<<RGRID(L)>>>(L, p, q, red);
+        k_apply_dot32_rows<1><<<RGRID(L)>>>(L, p, q, red);
     else
-        k_apply_dot32<0><<<RGRID(L)>>>(L, p, q, red);
+        k_apply_dot32_rows<0><<<RGRID(L)>>>(L, p, q, red);
     return cudaGetLastError();
 }
 cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
@@ -1241,7 +1352,7 @@ cudaError_t launch_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter,
 // ---------------------------------------------------------------- instantiations
 #define INST(T)                                                                                              \
     template cudaError_t launch_resid_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, const T*, T*, T*, \
-                                                  cudaStream_t);                                             \
+                                                  bool, cudaStream_t);                                       \
     template cudaError_t launch_bottom<T>(const BottomArgs<T>&, cudaStream_t);                              \
     template cudaError_t launch_rbgs<T>(const LevelT<T>&, T*, const T*, int, cudaStream_t, int);               \
     template cudaError_t launch_residual<T>(const LevelT<T>&, const T*, const T*, T*, cudaStream_t);        \
