@@ -198,13 +198,15 @@ __global__ void k_copy_interior(const double* __restrict__ src, double* __restri
     dst[P] = src[P];
 }
 
+// true_is_last: the loop's last residual is already the true FP64 residual of the final iterate
+// (defect correction: each step ends with it, and the iterate does not change after it)
 __global__ void k_write_stats(const Ctl* __restrict__ ctl, const int* __restrict__ status, int guess,
-                              lasto_stats* out)
+                              int true_is_last, lasto_stats* out)
 {
     lasto_stats s;
     s.guess = guess;
     s.cycles = ctl->iter;
-    s.rel_resid = ctl->true_rel;
+    s.rel_resid = true_is_last ? ctl->rel : ctl->true_rel;
     s.bnorm = ctl->bnorm;
     s.status = status[0] != 0 ? status[0] : ctl->status;
     s.outer = ctl->outer;
@@ -813,10 +815,11 @@ int enqueue_finish(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, do
 {
     LevelStore& F = P.lv[0];
     const LevelT<double> V = F.view64();
-    TRY(launch_resid_norm(V, F.u, F.b, nullptr, nullptr, 0u, P.red(FIN_TRUE), s));
+    const bool dc = is_defect_correction(h);
+    if (!dc) TRY(launch_resid_norm(V, F.u, F.b, nullptr, nullptr, 0u, P.red(FIN_TRUE), s));
     TRY(launch_project(cl.n, cl.x, cl.y, cl.z, F.u, cl.n_atoms, cl.pos, cl.R, h->quad, h->nq, vlm, P.status, s));
     if (potential) TRY(cudaMemcpyAsync(potential, F.u, sizeof(double) * F.N(), cudaMemcpyDeviceToDevice, s));
-    k_write_stats<<<1, 1, 0, s>>>(P.ctl, P.status, P.gl >= 0 ? 1 : 0, P.stats_dev);
+    k_write_stats<<<1, 1, 0, s>>>(P.ctl, P.status, P.gl >= 0 ? 1 : 0, dc ? 1 : 0, P.stats_dev);
     TRY(cudaGetLastError());
     return LASTO_OK;
 }

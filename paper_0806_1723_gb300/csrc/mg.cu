@@ -367,9 +367,9 @@ __global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, co
     u[pos<LS>(F, P)] += e;
 }
 
-// The same in FP32 with one warp per interior fine (j, k) row, lanes along i: the row's y and z
-// weights and coarse rows once per warp, no index division; the node expression is
-// k_prolong_add's, so the two are bitwise equal.
+// The same in FP32 with one warp per interior fine (j, k) row, lanes along the row's red nodes and
+// then its black ones: the row's y and z weights and coarse rows once per warp, no index
+// division; the node expression is k_prolong_add's, so the two are bitwise equal.
 template <int LS>
 __global__ void __launch_bounds__(256) k_prolong_add_rows(LevelT<float> F, LevelT<float> C,
                                                          const float* __restrict__ ec, float* __restrict__ u)
@@ -385,18 +385,23 @@ __global__ void __launch_bounds__(256) k_prolong_add_rows(LevelT<float> F, Level
     const size_t sy = C.nx, sz = (size_t)C.nx * C.ny;
     const float* __restrict__ crow = ec + (size_t)(k >> 1) * sz + (size_t)(j >> 1) * sy;
     const unsigned f0 = ((unsigned)k * (unsigned)F.ny + (unsigned)j) * (unsigned)F.nx;
-    for (int i = 1 + lane; i < F.nx - 1; i += 32) {
-        const int ni = (i & 1) ? 2 : 1;
-        const float wx[2] = {F.ax[0].pl[i], F.ax[0].pr[i]};
-        const float* base = crow + (i >> 1);
-        float e = 0.0f;
-        for (int c = 0; c < nk; c++)
-            for (int bb = 0; bb < nj; bb++) {
-                const float* r = base + c * sz + bb * sy;
-                const float sv = (ni == 2) ? fmaf(wx[0], r[0], wx[1] * r[1]) : r[0];
-                e = fmaf(wz[c] * wy[bb], sv, e);
-            }
-        u[pos<LS>(F, f0 + (unsigned)i)] += e;
+    // the red nodes of the row, then the black ones (unit stride over colour-split storage); the
+    // parity of i, and with it the x stencil, is the same along a run
+    for (int t = 0; t < 2; t++) {
+        const int ic = (t + j + k) & 1;
+        for (int i = (ic ? 1 : 2) + 2 * lane; i < F.nx - 1; i += 64) {
+            const int ni = (i & 1) ? 2 : 1;
+            const float wx[2] = {F.ax[0].pl[i], F.ax[0].pr[i]};
+            const float* base = crow + (i >> 1);
+            float e = 0.0f;
+            for (int c = 0; c < nk; c++)
+                for (int bb = 0; bb < nj; bb++) {
+                    const float* r = base + c * sz + bb * sy;
+                    const float sv = (ni == 2) ? fmaf(wx[0], r[0], wx[1] * r[1]) : r[0];
+                    e = fmaf(wz[c] * wy[bb], sv, e);
+                }
+            u[pos<LS>(F, f0 + (unsigned)i)] += e;
+        }
     }
 }
 
@@ -597,13 +602,23 @@ __global__ void __launch_bounds__(256) k_resid_restrict_rows(LevelT<float> F, Le
     const float* wy = F.ax[1].rw + 3 * (face_row ? 0 : J);
     const float* wz = F.ax[2].rw + 3 * (face_row ? 0 : K);
     const unsigned sy = (unsigned)F.nx, sz = (unsigned)F.nx * (unsigned)F.ny;
-    for (int I = lane; I < C.nx; I += 32) {
-        uc[cb + I] = 0.0f;
-        if (face_row || I == 0 || I == C.nx - 1) {
+    if (face_row) {
+        for (int I = lane; I < C.nx; I += 32) {
+            uc[cb + I] = 0.0f;
             bc[cb + I] = 0.0f;
-            continue;
         }
-        const float* wx = F.ax[0].rw + 3 * I;
+        return;
+    }
+    // the residual at fine i = 2I + 1 is the one at 2(I + 1) - 1 of the next coarse node: each
+    // lane forms it once and passes it up the warp (lane 0 takes lane 31's from the last step)
+    float carry[9];
+#pragma unroll
+    for (int q = 0; q < 9; q++) carry[q] = 0.0f;
+    for (int I0 = 0; I0 < C.nx; I0 += 32) {
+        const int I = I0 + lane;
+        const bool in = I >= 1 && I <= C.nx - 2;
+        if (I < C.nx) uc[cb + I] = 0.0f;
+        const float* wx = F.ax[0].rw + 3 * (in ? I : 1);
         float acc = 0.0f;
 #pragma unroll
         for (int c = 0; c < 3; c++)
@@ -611,16 +626,18 @@ __global__ void __launch_bounds__(256) k_resid_restrict_rows(LevelT<float> F, Le
             for (int bb = 0; bb < 3; bb++) {
                 const int fk = 2 * K - 1 + c, fj = 2 * J - 1 + bb, fi = 2 * I - 1;
                 const unsigned P = (unsigned)fk * sz + (unsigned)fj * sy + (unsigned)fi;
+                const bool edges_red = (c + bb) & 1;   // (fj + fk) odd: (fi, fj, fk) red
                 float r0 = 0.0f, r1 = 0.0f, r2 = 0.0f;
-                if (!RED_ONLY || ((fj + fk) & 1)) {   // (fi, fj, fk) and (fi + 2, fj, fk) red
-                    r0 = resid_at<float, LS>(F, u, b, P, fi, fj, fk);
-                    r2 = resid_at<float, LS>(F, u, b, P + 2, fi + 2, fj, fk);
+                if (!RED_ONLY || edges_red) {
+                    if (I <= C.nx - 2) r2 = resid_at<float, LS>(F, u, b, P + 2, fi + 2, fj, fk);   // I = 0 too
+                    r0 = __shfl_up_sync(0xffffffffu, r2, 1);
+                    if (lane == 0) r0 = carry[3 * c + bb];
+                    carry[3 * c + bb] = __shfl_sync(0xffffffffu, r2, 31);
                 }
-                if (!RED_ONLY || !((fj + fk) & 1))    // (fi + 1, fj, fk) red
-                    r1 = resid_at<float, LS>(F, u, b, P + 1, fi + 1, fj, fk);
+                if ((!RED_ONLY || !edges_red) && in) r1 = resid_at<float, LS>(F, u, b, P + 1, fi + 1, fj, fk);
                 acc = fmaf(wz[c] * wy[bb], fmaf(wx[0], r0, fmaf(wx[1], r1, wx[2] * r2)), acc);
             }
-        bc[cb + I] = acc;
+        if (I < C.nx) bc[cb + I] = in ? acc : 0.0f;
     }
 }
 
@@ -1144,32 +1161,25 @@ __device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int
     return L.ax[0].dual[i] * L.ax[1].dual[j] * L.ax[2].dual[k];
 }
 
-// (the inner CG vectors share the finest level's FP32 storage order; every kernel addresses them
-// through the storage map, and the sums are formed in the same order in both)
-// q = A p and <p, q>_vol with one warp per (j, k) row (faces included: q = 0 there), lanes along
-// i, rows dealt round robin over the reduction grid; the sums are formed in the same order in
-// both storage orders.
+// (the inner CG vectors share the finest level's FP32 storage order; every kernel walks the
+// nodes in flat order, so sums are formed in the same order in both)
 template <int LS>
-__global__ void __launch_bounds__(NT) k_apply_dot32_rows(LevelT<float> L, const float* __restrict__ p,
-                                                        float* __restrict__ q, Red red)
+__global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p,
+                                                   float* __restrict__ q, Red red)
 {
     __shared__ double sm[32];
     float acc = 0.0f;
-    const int rows = L.ny * L.nz, lane = threadIdx.x & 31;
-    for (int row = (int)(blockIdx.x * (NT / 32) + (threadIdx.x >> 5)); row < rows; row += (int)gridDim.x * (NT / 32)) {
-        const int k = row / L.ny, j = row - k * L.ny;
-        const unsigned f0 = (unsigned)row * (unsigned)L.nx;
-        const bool face_row = j == 0 || k == 0 || j == L.ny - 1 || k == L.nz - 1;
-        for (int i = lane; i < L.nx; i += 32) {
-            const unsigned P = f0 + (unsigned)i;
-            const unsigned Q = pos<LS>(L, P);
-            float v = 0.0f;
-            if (!face_row && i != 0 && i != L.nx - 1) {
-                v = fmaf(-dsum(L, i, j, k), p[Q], offdiag<LS>(L, p, P, i, j, k));
-                acc = fmaf(vol32(L, i, j, k) * p[Q], v, acc);
-            }
-            q[Q] = v;
+    GRID_STRIDE(P, L.N())
+    {
+        int i, j, k;
+        node_ijk(P, L, i, j, k);
+        const unsigned Q = pos<LS>(L, P);
+        float v = 0.0f;
+        if (!is_face(L, i, j, k)) {
+            v = fmaf(-dsum(L, i, j, k), p[Q], offdiag<LS>(L, p, P, i, j, k));
+            acc = fmaf(vol32(L, i, j, k) * p[Q], v, acc);
         }
+        q[Q] = v;
     }
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
@@ -1282,9 +1292,9 @@ cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const doubl
 cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s)
 {
     if (L.lsh)
-        k_apply_dot32_rows<1><<<RGRID(L)>>>(L, p, q, red);
+        k_apply_dot32<1><<<RGRID(L)>>>(L, p, q, red);
     else
-        k_apply_dot32_rows<0><<<RGRID(L)>>>(L, p, q, red);
+        k_apply_dot32<0><<<RGRID(L)>>>(L, p, q, red);
     return cudaGetLastError();
 }
 cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
