@@ -235,14 +235,14 @@ def test_deposit(orc, small_clusters, precision, tol):
         b = host(b)
         assert np.abs(b - ref).max() < tol * np.abs(ref).max()
         # node by node where the density matters; far out the GPU drops Slater terms below
-        # e^-40 of their weight (about 1e-14 absolute), which the oracle keeps
+        # e^-40 (FP64) or e^-37 (FP32 pairs) of their weight, which the oracle keeps
         big = np.abs(ref) > 1e-3 * np.abs(ref).max()
         assert np.abs((b - ref)[big] / ref[big]).max() < 1e-10
 
 
 def test_deposit_far_apart_atoms_non_cubic(orc):
     """Two atoms 50 bohr apart on a 49 x 41 x 45 mesh: tiles at either end of the box lie
-    farther than the cut-off (40 / zeta_min = 26.7 bohr) from the other atom, so the FP32-pair
+    farther than the cut-off (37 / zeta_min = 24.7 bohr) from the other atom, so the FP32-pair
     deposit drops that atom for the whole tile; ragged 8 x 8 x 4 tiles on every axis.  Both
     precisions against the oracle node by node."""
     B = need_gpu()
