@@ -476,6 +476,7 @@ def main():
 
     # ---------------- arithmetic ceilings (the library's FMA probe) and the roofline
     probes = fma_ceilings(B, stream, dev)
+    training = training_rate(B, stream, dev)
     roof = smoother_roofline(B, stream, flush, dev, tuned, probes)
     dep = deposit_rate(B, synth, stream, flush, dev, probes)
 
@@ -510,6 +511,7 @@ def main():
             "interstitial_hs": hs,
             "inner_faces_raw": rows,
             "probes": probes,
+            "guess_training": training,
             "deposit": dep,
             "clocks": clk.summary(),
             "e2e": e2e,
@@ -826,6 +828,48 @@ def _peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+def training_rate(B, stream, dev, steps=10, warmup=3):
+    """Training throughput of the learned guess's U-Net (batches of 8 grids of 33^3, one step =
+    forward, masked MSE, backward, Adam), on the tcgen05 kernels and on the warp-level MMA
+    kernels, with random inputs and targets (the rate does not depend on the values)."""
+    import torch
+
+    from paper_0806_1723_gb300 import unet
+    out = {"batch": 8, "grid": "33^3", "steps": steps}
+    for name, tc in (("tcgen05", True), ("wmma", False)):
+        net = unet.UNet(n=33, nb=8, seed=1, tc=tc)
+        g = torch.Generator(device=dev).manual_seed(2)
+        N = 8 * 33 ** 3
+        x = torch.randn(N, 16, generator=g, device=dev) * 0.5
+        x[:, 3:] = 0
+        tgt = torch.randn(N, generator=g, device=dev)
+        mask = torch.ones(N, device=dev)
+        net._mask_count = float(N)
+
+        def step():
+            net.forward(x)
+            net.loss_and_grad(tgt, mask)
+            net.backward(net.dpred)
+            net.adam(1e-4)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = _events(torch, stream)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "samples_per_s": 8 / (ms / 1e3)}
+        if tc:
+            out[name]["timeouts"] = int(net.tc_err.item())
+        del net
+        torch.cuda.empty_cache()
+    return out
 
 
 def fma_ceilings(B, stream, dev):

@@ -469,6 +469,18 @@ int lasto_nn_conv3d_dgrad(int nb, const int dims[3], int cin, int cout, const vo
  * from dy32 (FP32 copy of dy).  dw accumulates with atomics (order not fixed). */
 int lasto_nn_conv3d_wgrad(int nb, const int dims[3], int cin, int cout, const void* x, const void* dy16,
                           const float* dy32, float* dw, float* db, void* stream);
+/* The data and weight gradients on the fifth-generation tensor cores (the paper has no
+ * counterpart; training of the learned guess).  dgrad_tc: as lasto_nn_conv3d_dgrad, the
+ * flipped weights packed into wpk_flip (caller scratch, 27*cin*cout BF16) and convolved with
+ * dy by the tcgen05 forward kernel; cin in {16, 32, 48, 64, 96, 128}.  wgrad_tc: as
+ * lasto_nn_conv3d_wgrad, as a tcgen05 GEMM over the nodes (M = rows of (tap, input channel),
+ * N = cout, both operands read from the channels-last rows), cin <= 128, cout in {16, 32,
+ * 48, 64, 96, 128}.  err (device int, optional) is set to 1 if a tensor-core completion wait
+ * timed out (dx32 / dw are then incomplete). */
+int lasto_nn_conv3d_dgrad_tc(int nb, const int dims[3], int cin, int cout, const void* dy, const void* w, void* w_flip,
+                             void* wpk_flip, float* dx32, int* err, void* stream);
+int lasto_nn_conv3d_wgrad_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* dy16,
+                             const float* dy32, float* dw, float* db, int* err, void* stream);
 /* dx = dy where y > 0 else 0 (FP32 and / or BF16 output). */
 int lasto_nn_relu_grad(size_t n, const float* y, const float* dy, float* dx, void* dx16, void* stream);
 int lasto_nn_to_bf16(size_t n, const float* a, void* b, void* stream);

@@ -59,7 +59,7 @@ EXPORTS = ["lasto_config_default", "lasto_poisson_create", "lasto_poisson_solve"
            "lasto_op_smooth_f32", "lasto_op_smooth_split_f32", "lasto_op_smooth_slab", "lasto_op_smooth_slab_f32", "lasto_op_smooth_wave_f32", "lasto_selftest_bounded_wait",
            "lasto_probe_fma", "lasto_op_restrict", "lasto_op_prolong_add", "lasto_op_coarse_solve",
            "lasto_op_project", "lasto_op_sphere_density", "lasto_op_inner_solve", "lasto_op_interstitial_hs", "lasto_guess_param_count", "lasto_poisson_set_guess",
-           "lasto_poisson_tune_table", "lasto_poisson_set_tune_table", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad",
+           "lasto_poisson_tune_table", "lasto_poisson_set_tune_table", "lasto_nn_conv3d_fwd", "lasto_nn_pack_weights", "lasto_nn_conv3d_fwd_tc", "lasto_nn_conv3d_dgrad", "lasto_nn_conv3d_wgrad", "lasto_nn_conv3d_dgrad_tc", "lasto_nn_conv3d_wgrad_tc",
            "lasto_nn_relu_grad", "lasto_nn_to_bf16", "lasto_nn_copy_channels", "lasto_nn_down", "lasto_nn_up",
            "lasto_nn_mse", "lasto_nn_adam", "lasto_nn_guess_features", "lasto_nn_guess_grid"]
 
@@ -117,6 +117,8 @@ def _declare(L):
         "lasto_nn_conv3d_fwd_tc": (i, [i, ip, i, i, vp, vp, vp, i, vp, i, i, vp, i, i, vp, vp]),
         "lasto_nn_conv3d_dgrad": (i, [i, ip, i, i, vp, vp, vp, vp, vp]),
         "lasto_nn_conv3d_wgrad": (i, [i, ip, i, i, vp, vp, vp, vp, vp, vp]),
+        "lasto_nn_conv3d_dgrad_tc": (i, [i, ip, i, i, vp, vp, vp, vp, vp, vp, vp]),
+        "lasto_nn_conv3d_wgrad_tc": (i, [i, ip, i, i, vp, vp, vp, vp, vp, vp, vp]),
         "lasto_nn_relu_grad": (i, [ctypes.c_size_t, vp, vp, vp, vp, vp]),
         "lasto_nn_to_bf16": (i, [ctypes.c_size_t, vp, vp, vp]),
         "lasto_nn_copy_channels": (i, [ctypes.c_size_t, i, vp, i, i, vp, i, i, i, vp]),

@@ -267,6 +267,180 @@ __global__ void k_tc_epilogue(size_t N, int cout, int groups, const float* __res
     if (y16) y16[nd * ldy16 + off16 + co] = __float2bfloat16(v);
 }
 
+// ---------------------------------------------------------------- weight gradient
+// dw[tap][ci][co] += sum over nodes of x[node + tap][ci] dy[node][co]: a GEMM with M = the
+// (tap, ci) rows of a tile of taps (TPT = floor(128 / cin) taps, 128 rows, rows past TPT cin
+// zero), N = cout, K = nodes, one CTA per (node chunk, tile).  Both operands are read
+// MN-major from channels-last rows: a stage holds 64 nodes, for each node the TPT neighbour
+// rows of cin channels (16-byte pieces; zero outside the grid) in A and its cout channels of
+// dy in B, and is consumed by four K = 16 MMAs.  Core matrices (8 nodes x 8 channels, 128
+// contiguous bytes) sit 128 bytes apart along the channels and 16 * rows bytes apart along
+// the nodes; for these MN-major operands the descriptor's leading byte offset is the step
+// along K (nodes) and its stride byte offset the step along M / N (channels) -- the other
+// assignment reads outside the tiles (measured: wrong sums).  The accumulator (128 lanes x
+// cout columns of tensor memory) is added to dw with FP32 atomics at the end.
+constexpr int WG_STAGES = 3;
+constexpr int WG_AHEAD = 2;
+constexpr int WG_STEP = 64;                          // nodes per stage (four MMAs)
+constexpr int WG_CHUNK = 2048;                       // nodes per CTA
+constexpr int WG_A_BYTES = TC_M * 2 * WG_STEP;       // 128 rows x 64 nodes
+__host__ __device__ constexpr int wg_smem(int cout) { return WG_STAGES * (WG_A_BYTES + cout * 2 * WG_STEP); }
+
+__device__ __forceinline__ uint64_t make_desc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(lbo >> 4) << 16;
+    d |= (uint64_t)(sbo >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// node index -> (b, z, y, x) by multiply-high division by the invariant W, H, D (nodes < 2^31)
+struct GridDiv {
+    DivMagic w, h, d;
+};
+
+template <int COUT>
+__global__ void __launch_bounds__(TC_M) k_conv_wgrad_tc(Grid g, GridDiv gd, int cin, const bf16* __restrict__ x,
+                                                       const bf16* __restrict__ dy, float* __restrict__ dw,
+                                                       int* __restrict__ err)
+{
+    constexpr int B_BYTES = COUT * 2 * WG_STEP;
+    constexpr int NCOL = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : 128);
+    extern __shared__ __align__(1024) unsigned char wg_smem_raw[];
+    unsigned char* sA = wg_smem_raw;                               // [WG_STAGES][WG_A_BYTES]
+    unsigned char* sB = wg_smem_raw + WG_STAGES * WG_A_BYTES;      // [WG_STAGES][B_BYTES]
+    __shared__ __align__(8) unsigned long long mbar[WG_STAGES];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const size_t N = g.nodes();
+    const size_t node0 = (size_t)blockIdx.x * WG_CHUNK;
+    const int tpt = TC_M / cin, tap0 = blockIdx.y * tpt;
+    const int ntap = min(tpt, 27 - tap0);
+    const int rows = ntap * cin;                                   // live rows of the tile
+    const int r8n = rows / 8;                                      // 16-byte pieces per node in A
+
+    // zero the ring (padding rows stay zero; no copy ever writes them)
+    for (int t = tid; t < WG_STAGES * (WG_A_BYTES + B_BYTES) / 16; t += TC_M)
+        reinterpret_cast<uint4*>(wg_smem_raw)[t] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        abort_flag = 0;
+        for (int st = 0; st < WG_STAGES; st++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[st])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(NCOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const size_t nodes = N > node0 ? min((size_t)WG_CHUNK, N - node0) : 0;
+    const int nk = (int)((nodes + WG_STEP - 1) / WG_STEP);
+    // core-matrix steps: along the channels (M / N) and along the nodes (K)
+    constexpr uint32_t A_CH = 128, A_ND = 16 * 128, B_CH = 128, B_ND = (COUT / 8) * 128;
+    const uint32_t idesc = make_idesc(COUT) | (1u << 15) | (1u << 16);   // A and B MN-major
+
+    auto prefetch = [&](int k) {
+        const int st = k % WG_STAGES;
+        if (k >= WG_STAGES) {
+            if (!mbar_wait(smem_u32(&mbar[st]), (uint32_t)((k / WG_STAGES - 1) & 1))) abort_flag = 1;
+        }
+        // A: piece p = (node kk, row group r8), r8 fastest (one node's row read contiguously)
+        for (int p = tid; p < WG_STEP * r8n; p += TC_M) {
+            const int kk = p / r8n, r8 = p - kk * r8n;
+            const int m = r8 * 8, tl = m / cin, c0 = m - tl * cin;
+            const size_t node = node0 + (size_t)k * WG_STEP + kk;
+            bool in = node < N;
+            size_t nbn = 0;
+            if (in) {
+                const unsigned r = (unsigned)node, q1 = div_by(r, gd.w), q2 = div_by(q1, gd.h), b = div_by(q2, gd.d);
+                const int xx = (int)(r - q1 * (unsigned)g.W), yy = (int)(q1 - q2 * (unsigned)g.H);
+                const int z = (int)(q2 - b * (unsigned)g.D);
+                const int tap = tap0 + tl;
+                const int zz = z + tap / 9 - 1, y2 = yy + (tap / 3) % 3 - 1, x2 = xx + tap % 3 - 1;
+                in = zz >= 0 && zz < g.D && y2 >= 0 && y2 < g.H && x2 >= 0 && x2 < g.W;
+                nbn = in ? (((size_t)b * g.D + zz) * g.H + y2) * g.W + x2 : 0;
+            }
+            const uint32_t dst = smem_u32(sA + st * WG_A_BYTES + r8 * A_CH + (kk >> 3) * A_ND + (kk & 7) * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(x + nbn * cin + c0),
+                         "r"(in ? 16u : 0u)
+                         : "memory");
+        }
+        for (int p = tid; p < WG_STEP * (COUT / 8); p += TC_M) {
+            const int kk = p / (COUT / 8), c8 = p - kk * (COUT / 8);
+            const size_t node = node0 + (size_t)k * WG_STEP + kk;
+            const bool in = node < N;
+            const uint32_t dst = smem_u32(sB + st * B_BYTES + c8 * B_CH + (kk >> 3) * B_ND + (kk & 7) * 16);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst),
+                         "l"(dy + (in ? node : 0) * COUT + c8 * 8), "r"(in ? 16u : 0u)
+                         : "memory");
+        }
+    };
+    for (int k = 0; k < WG_AHEAD; k++) {
+        if (k < nk) prefetch(k);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int kc = 0; kc < nk; kc++) {
+        const int st = kc % WG_STAGES;
+        if (kc + WG_AHEAD < nk) prefetch(kc + WG_AHEAD);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(WG_AHEAD) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (abort_flag) break;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < WG_STEP / 16; j++) {   // 16 nodes = two core matrices along K
+                const uint64_t ad = make_desc_mn(smem_u32(sA + st * WG_A_BYTES + j * 2 * A_ND), A_ND, A_CH);
+                const uint64_t bd = make_desc_mn(smem_u32(sB + st * B_BYTES + j * 2 * B_ND), B_ND, B_CH);
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                        tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"((kc > 0 || j > 0) ? 1 : 0)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             smem_u32(&mbar[st]))
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (!abort_flag && nk > 0) {
+        const int st = (nk - 1) % WG_STAGES;
+        if (!mbar_wait(smem_u32(&mbar[st]), (uint32_t)(((nk - 1) / WG_STAGES) & 1))) abort_flag = 1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!abort_flag && nk > 0) {
+        // thread tid owns accumulator row m = tid (tensor-memory lane tid)
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        float acc[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; c += 16) tmem_ld16(lane_base + (uint32_t)c, acc + c);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        const int m = tid;
+        if (m < rows) {
+            const int tl = m / cin, ci = m - tl * cin;
+            float* dst = dw + ((size_t)(tap0 + tl) * cin + ci) * COUT;
+#pragma unroll
+            for (int c = 0; c < COUT; c++) atomicAdd(dst + c, acc[c]);
+        }
+    } else if (abort_flag && tid == 0 && err) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(NCOL) : "memory");
+}
+
 }  // namespace tc
 
 cudaError_t launch_pack_weights(int cin, int cout, const void* w, void* wpk, cudaStream_t s)
@@ -315,6 +489,42 @@ int conv_fwd_tc(int nb, const int dims[3], int cin, int cout, const void* x, con
         k_tc_epilogue<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g.nodes(), cout, groups, part, bias, relu, y32,
                                                                   ldy32, off32, Y16, ldy16, off16);
     }
+    return cudaGetLastError() == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
+}
+
+int conv_wgrad_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* dy16, float* dw,
+                  int* err, void* stream)
+{
+    using namespace tc;
+    if (nb < 1 || !dims || cin % 16 || cin < 16 || cin > 128 || !x || !dy16 || !dw ||
+        !(cout == 16 || cout == 32 || cout == 48 || cout == 64 || cout == 96 || cout == 128))
+        return LASTO_ERR_INVALID_ARG;
+    Grid g{nb, dims[2], dims[1], dims[0]};
+    if (g.nodes() == 0) return LASTO_OK;
+    if (g.nodes() >= (size_t(1) << 31)) return LASTO_ERR_INVALID_ARG;
+    const GridDiv gd{div_magic((unsigned)g.W), div_magic((unsigned)g.H), div_magic((unsigned)g.D)};
+    cudaStream_t s = (cudaStream_t)stream;
+    const int tpt = TC_M / cin;
+    const dim3 grid((unsigned)((g.nodes() + WG_CHUNK - 1) / WG_CHUNK), (unsigned)((27 + tpt - 1) / tpt));
+    const bf16* X = (const bf16*)x;
+    const bf16* DY = (const bf16*)dy16;
+#define LASTO_WG_CASE(C)                                                                                 \
+    case C:                                                                                              \
+        if (cudaFuncSetAttribute(k_conv_wgrad_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, wg_smem(C)) != \
+            cudaSuccess)                                                                                 \
+            return LASTO_ERR_CUDA;                                                                       \
+        k_conv_wgrad_tc<C><<<grid, TC_M, wg_smem(C), s>>>(g, gd, cin, X, DY, dw, err);                     \
+        break;
+    switch (cout) {
+        LASTO_WG_CASE(16)
+        LASTO_WG_CASE(32)
+        LASTO_WG_CASE(48)
+        LASTO_WG_CASE(64)
+        LASTO_WG_CASE(96)
+        LASTO_WG_CASE(128)
+        default: return LASTO_ERR_INVALID_ARG;
+    }
+#undef LASTO_WG_CASE
     return cudaGetLastError() == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
 }
 

@@ -373,6 +373,9 @@ cudaError_t launch_pack_weights(int cin, int cout, const void* w, void* wpk, cud
 int conv_fwd_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* wpk, const float* bias,
                 int relu, float* y32, int ldy32, int off32, void* y16, int ldy16, int off16, float* scratch,
                 size_t scratch_floats, int* err, void* stream);
+// dw (FP32 [27][cin][cout]) += weight gradient on the tensor cores (FP32 atomics)
+int conv_wgrad_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* dy16, float* dw,
+                  int* err, void* stream);
 cudaError_t launch_axis_stride(const double* src, int m, int n, double* dst, cudaStream_t s);
 cudaError_t launch_resample(const int na[3], const double* ax, const double* ay, const double* az, const double* src,
                             const int nb[3], const double* bx, const double* by, const double* bz, double* dst,

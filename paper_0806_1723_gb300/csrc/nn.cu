@@ -190,20 +190,28 @@ __global__ void __launch_bounds__(CT) k_conv_wgrad(Grid g, int cin, const bf16* 
     }
 }
 
-// dbias[co] = sum over nodes of dy[node][co] (FP32 gradient)
-__global__ void k_bias_grad(size_t N, int cout, const float* __restrict__ dy, float* __restrict__ db)
+// dbias[co] += sum over nodes of dy[node][co] (FP32 gradient): each block sums a span of node
+// rows with the threads along the row (coalesced), reduces per channel in shared memory and
+// adds its partial with one atomic per channel
+constexpr int BG_ROWS = 128;    // node rows per block
+__global__ void __launch_bounds__(256) k_bias_grad(size_t N, int cout, const float* __restrict__ dy,
+                                                   float* __restrict__ db)
 {
-    const int co = blockIdx.x;
-    float acc = 0.0f;
-    for (size_t n = threadIdx.x; n < N; n += blockDim.x) acc += dy[n * cout + co];
     __shared__ float sm[256];
-    sm[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
-        __syncthreads();
+    const int per = 256 / cout;                      // rows in flight per block step
+    const int t = threadIdx.x, c = t % cout, r0 = t / cout;
+    float acc = 0.0f;
+    if (r0 < per) {
+        const size_t first = (size_t)blockIdx.x * BG_ROWS, last = min(first + BG_ROWS, N);
+        for (size_t n = first + r0; n < last; n += per) acc += dy[n * cout + c];
     }
-    if (threadIdx.x == 0) db[co] += sm[0];
+    sm[t] = acc;
+    __syncthreads();
+    if (t < cout) {
+        float s = 0.0f;
+        for (int r = 0; r < per; r++) s += sm[r * cout + t];
+        atomicAdd(db + t, s);
+    }
 }
 
 // w_t[tap'][co][ci] = w[26 - tap'][ci][co]: the weights of the data-gradient convolution
@@ -529,7 +537,34 @@ int lasto_nn_conv3d_wgrad(int nb, const int dims[3], int cin, int cout, const vo
         case 64: k_conv_wgrad<64><<<grid, CT, 0, s>>>(g, cin, X, DY, dw); break;
         default: return LASTO_ERR_INVALID_ARG;
     }
-    if (db && dy32) k_bias_grad<<<cout, 256, 0, s>>>(g.nodes(), cout, dy32, db);
+    if (db && dy32) k_bias_grad<<<blocks(g.nodes(), BG_ROWS), 256, 0, s>>>(g.nodes(), cout, dy32, db);
+    return cudaGetLastError() == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
+}
+
+int lasto_nn_conv3d_dgrad_tc(int nb, const int dims[3], int cin, int cout, const void* dy, const void* w, void* w_flip,
+                             void* wpk_flip, float* dx32, int* err, void* stream)
+{
+    if (!w || !w_flip || !wpk_flip || !dx32 || cin < 16 || cin % 16 || cout < 16 || cout % 16) return LASTO_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nw = (size_t)27 * cin * cout;
+    k_flip_weights<<<blocks(nw, 256), 256, 0, s>>>(cin, cout, (const bf16*)w, (bf16*)w_flip);
+    if (cudaGetLastError() != cudaSuccess) return LASTO_ERR_CUDA;
+    // the data gradient is the forward convolution of dy with the flipped, transposed weights
+    if (lasto::launch_pack_weights(cout, cin, w_flip, wpk_flip, s) != cudaSuccess) return LASTO_ERR_CUDA;
+    return lasto::conv_fwd_tc(nb, dims, cout, cin, dy, wpk_flip, nullptr, 0, dx32, cin, 0, nullptr, 0, 0, nullptr, 0,
+                              err, stream);
+}
+
+int lasto_nn_conv3d_wgrad_tc(int nb, const int dims[3], int cin, int cout, const void* x, const void* dy16,
+                             const float* dy32, float* dw, float* db, int* err, void* stream)
+{
+    if (nb < 1 || !dims || !x || !dy16 || !dw) return LASTO_ERR_INVALID_ARG;
+    const int st = lasto::conv_wgrad_tc(nb, dims, cin, cout, x, dy16, dw, err, stream);
+    if (st) return st;
+    if (db && dy32) {
+        Grid g{nb, dims[2], dims[1], dims[0]};
+        k_bias_grad<<<blocks(g.nodes(), BG_ROWS), 256, 0, (cudaStream_t)stream>>>(g.nodes(), cout, dy32, db);
+    }
     return cudaGetLastError() == cudaSuccess ? LASTO_OK : LASTO_ERR_CUDA;
 }
 

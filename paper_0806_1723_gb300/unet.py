@@ -41,11 +41,16 @@ def _chk(st, what):
 
 
 class UNet:
-    """Parameters, Adam state and activation buffers for batches of nb grids of n^3 nodes."""
+    """Parameters, Adam state and activation buffers for batches of nb grids of n^3 nodes.
 
-    def __init__(self, n=33, nb=8, seed=0, device="cuda"):
+    tc=True runs every convolution of training on the fifth-generation tensor cores (tcgen05:
+    the forward pass on weights packed into the operand tiles after each update, the data
+    gradient as the forward kernel on the flipped weights, the weight gradient as a GEMM over
+    the nodes); tc=False on the warp-level MMA kernels."""
+
+    def __init__(self, n=33, nb=8, seed=0, device="cuda", tc=False):
         self.L = B.load()
-        self.n, self.nb, self.dev = n, nb, device
+        self.n, self.nb, self.dev, self.tc = n, nb, device, tc
         self.dims = [n, (n + 1) // 2, ((n + 1) // 2 + 1) // 2, (((n + 1) // 2 + 1) // 2 + 1) // 2]
         for d in self.dims[:3]:
             assert d % 2 == 1, "every level but the last must have an odd node count"
@@ -63,6 +68,10 @@ class UNet:
                 st[name + ".b"] = torch.zeros_like(self.b32[name])
         self.step_count = 0
         self.wflip = torch.empty(27 * 128 * 64, dtype=torch.bfloat16, device=device)
+        self.wpk_flip = torch.empty(27 * 128 * 64, dtype=torch.bfloat16, device=device)
+        self.wpk = {name: torch.empty_like(self.w16[name]) for name in self.w16}
+        self.packed = False
+        self.tc_err = torch.zeros(1, dtype=torch.int32, device=device)
         self._alloc(nb)
         self.scales = {"s0": 1.0, "s1": 1.0, "h_ref": 1.0, "out": 1.0}
 
@@ -96,9 +105,21 @@ class UNet:
         return (ctypes.c_int * 3)(d, d, d)
 
     # ------------------------------------------------------------ building blocks
+    def _pack(self):
+        if not self.packed:
+            for name, cin, cout, _ in LAYERS:
+                _chk(self.L.lasto_nn_pack_weights(cin, cout, _p(self.w16[name]), _p(self.wpk[name]), _s()), "pack")
+            self.packed = True
+
     def _conv(self, name, x16, y32, ldy=None, off=0):
         _, cin, cout, relu = next(l for l in LAYERS if l[0] == name)
         lv = self.level[name]
+        if self.tc:
+            self._pack()
+            _chk(self.L.lasto_nn_conv3d_fwd_tc(self.nb, self._d3(lv), cin, cout, _p(x16), _p(self.wpk[name]),
+                                               _p(self.b32[name]), relu, _p(y32), ldy or cout, off, None, 0, 0,
+                                               _p(self.tc_err), _s()), "conv_tc " + name)
+            return
         _chk(self.L.lasto_nn_conv3d_fwd(self.nb, self._d3(lv), cin, cout, _p(x16), _p(self.w16[name]),
                                         _p(self.b32[name]), relu, _p(y32), ldy or cout, off, None, 0, 0, _s()),
              "conv " + name)
@@ -174,9 +195,17 @@ class UNet:
         else:
             dpre32.copy_(dy32.view(-1)[:n])
             self._tobf(dpre32, dpre16)
+        dx = self.gtmp[lv].view(-1)[: self.N[lv] * cin]
+        if self.tc:
+            _chk(self.L.lasto_nn_conv3d_wgrad_tc(self.nb, self._d3(lv), cin, cout, _p(xin), _p(dpre16), _p(dpre32),
+                                                 _p(self.gw[name]), _p(self.gb[name]), _p(self.tc_err), _s()),
+                 "wgrad_tc " + name)
+            _chk(self.L.lasto_nn_conv3d_dgrad_tc(self.nb, self._d3(lv), cin, cout, _p(dpre16), _p(self.w16[name]),
+                                                 _p(self.wflip), _p(self.wpk_flip), _p(dx), _p(self.tc_err), _s()),
+                 "dgrad_tc " + name)
+            return dx.clone()
         _chk(self.L.lasto_nn_conv3d_wgrad(self.nb, self._d3(lv), cin, cout, _p(xin), _p(dpre16), _p(dpre32),
                                           _p(self.gw[name]), _p(self.gb[name]), _s()), "wgrad " + name)
-        dx = self.gtmp[lv].view(-1)[: self.N[lv] * cin]
         _chk(self.L.lasto_nn_conv3d_dgrad(self.nb, self._d3(lv), cin, cout, _p(dpre16), _p(self.w16[name]),
                                           _p(self.wflip), _p(dx), _s()), "dgrad " + name)
         return dx.clone()
@@ -233,6 +262,7 @@ class UNet:
 
     def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         self.step_count += 1
+        self.packed = False
         for name in self.w32:
             _chk(self.L.lasto_nn_adam(self.w32[name].numel(), _p(self.w32[name]), _p(self.gw[name]),
                                       _p(self.m[name + ".w"]), _p(self.v[name + ".w"]), lr, b1, b2, eps,
@@ -248,6 +278,7 @@ class UNet:
             self.w32[name].copy_(torch.as_tensor(P[name + ".w"], dtype=torch.float32))
             self.b32[name].copy_(torch.as_tensor(P[name + ".b"], dtype=torch.float32))
             self.w16[name].copy_(self.w32[name].to(torch.bfloat16))
+        self.packed = False
 
     def get_params(self):
         P = {}

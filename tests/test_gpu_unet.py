@@ -105,6 +105,41 @@ def test_conv_gradients(cin, cout):
     assert np.abs(db.double().cpu().numpy() - rdb).max() <= 2e-5 * np.abs(rdb).max()
 
 
+@pytest.mark.parametrize("cin,cout,dims", [(16, 32, (7, 6, 5)), (64, 16, (7, 6, 5)), (96, 32, (7, 6, 5)),
+                                           (48, 64, (9, 5, 7)), (128, 128, (5, 5, 5)), (32, 48, (33, 9, 11))])
+def test_conv_gradients_tensor_memory(cin, cout, dims):
+    """The tcgen05 data gradient (flipped weights through the tcgen05 forward kernel) and
+    weight gradient (GEMM over the nodes, both operands read MN-major from the channels-last
+    rows) against the FP64 oracle; node counts that leave a ragged last K step and a ragged
+    last chunk (33 x 9 x 11 x 2 = 6534 nodes = 3 chunks of 2048 + 390), tap tiles with padding
+    rows (cin 48 and 96) and the largest channel counts."""
+    import torch
+    B = need_gpu()
+    L = B.load()
+    rng = np.random.default_rng(11 * cin + cout)
+    nb, (W, H, D) = 2, dims
+    x = _bf16(rng.normal(size=(nb, D, H, W, cin))).cuda()
+    w = _bf16(rng.normal(size=(27, cin, cout)) * 0.1).cuda()
+    dy16 = _bf16(rng.normal(size=(nb * D * H * W, cout))).cuda()
+    dy32 = dy16.float()
+    dx = torch.full((nb * D * H * W, cin), float("nan"), dtype=torch.float32, device="cuda")
+    wf = torch.empty(27 * cin * cout, dtype=torch.bfloat16, device="cuda")
+    wpk = torch.empty_like(wf)
+    dw = torch.zeros(27, cin, cout, dtype=torch.float32, device="cuda")
+    db = torch.zeros(cout, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert L.lasto_nn_conv3d_dgrad_tc(nb, _d3((W, H, D)), cin, cout, B._ptr(dy16), B._ptr(w), B._ptr(wf), B._ptr(wpk),
+                                      B._ptr(dx), B._ptr(err), B._stream()) == 0
+    assert L.lasto_nn_conv3d_wgrad_tc(nb, _d3((W, H, D)), cin, cout, B._ptr(x), B._ptr(dy16), B._ptr(dy32),
+                                      B._ptr(dw), B._ptr(db), B._ptr(err), B._stream()) == 0
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    rdx, rdw, rdb = U.conv3d_backward(_f64(x), _f64(w), _f64(dy16).reshape(nb, D, H, W, cout))
+    assert np.abs(dx.double().cpu().numpy().reshape(rdx.shape) - rdx).max() <= 2e-5 * np.abs(rdx).max()
+    assert np.abs(dw.double().cpu().numpy() - rdw).max() <= 2e-5 * np.abs(rdw).max()
+    assert np.abs(db.double().cpu().numpy() - rdb).max() <= 2e-5 * np.abs(rdb).max()
+
+
 def test_sampling_and_adjoints():
     import torch
     B = need_gpu()
@@ -134,14 +169,16 @@ def test_sampling_and_adjoints():
     assert np.abs(out_c.double().cpu().numpy() - U.up_adjoint(x).reshape(-1, C)).max() < 1e-5
 
 
-def test_whole_network_matches_oracle():
-    """Forward, loss and every parameter gradient of the U-Net on a batch of two 17^3 grids."""
+@pytest.mark.parametrize("tc", [False, True])
+def test_whole_network_matches_oracle(tc):
+    """Forward, loss and every parameter gradient of the U-Net on a batch of two 17^3 grids, on
+    the warp-level MMA kernels and on the tcgen05 kernels (forward, data and weight gradients)."""
     import torch
     B = need_gpu()
     from paper_0806_1723_gb300 import unet
     rng = np.random.default_rng(5)
     P = U.init_params(seed=6)
-    net = unet.UNet(n=17, nb=2)
+    net = unet.UNet(n=17, nb=2, tc=tc)
     net.set_params(P)
     x = rng.normal(size=(2, 17, 17, 17, 16)) * 0.5
     x[..., 3:] = 0
@@ -155,6 +192,7 @@ def test_whole_network_matches_oracle():
                       torch.as_tensor(mask.reshape(-1), dtype=torch.float32).cuda())
     net.backward(net.dpred)
     torch.cuda.synchronize()
+    assert int(net.tc_err.item()) == 0
     rpred, cache = U.forward(P, xb)
     assert np.linalg.norm(pred.double().cpu().numpy() - rpred.reshape(-1)) <= 2e-2 * np.linalg.norm(rpred)
     loss, dpred = U.mse(rpred, target, mask)
