@@ -119,12 +119,13 @@ def main(argv=None):
     p.add_argument("--lr", type=float, default=1e-3)
     p.add_argument("--seed", type=int, default=3)
     p.add_argument("--out", default="unet.npz")
+    p.add_argument("--wmma", action="store_true", help="train on the warp-level MMA kernels instead of tcgen05")
     a = p.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
     import synth
     clusters = synth.workloads.guess_training_set(a.samples, seed=a.seed)
-    net = U.UNet(n=33, nb=a.batch, seed=a.seed)
+    net = U.UNet(n=33, nb=a.batch, seed=a.seed, tc=not a.wmma)
     X, Y = build_dataset(net, clusters)
     set_scales(net, X, Y)
     hist = train(net, X, Y, epochs=a.epochs, lr=a.lr)
