@@ -99,10 +99,16 @@ typedef struct lasto_config {
     double rel_tol;   /* stop when ||b - A u||_2 <= rel_tol ||b_eff||_2 (b_eff: b with the faces moved in) */
     int n_theta;      /* Gauss-Legendre points in cos(theta) of the sphere quadrature (<= 32) */
     int n_phi;        /* uniform points in phi (<= 64) */
-    int launch;       /* 0: one CUDA graph per solve, iteration loop on the device (default);
+    int launch;       /* 0: one CUDA graph per solve, iteration loop on the device (default;
+                         each cluster of a batch an independent branch of the graph);
                          1: the same kernels launched directly with a host-side loop that
                          synchronises once per iteration (for profilers that cannot see
-                         kernels inside conditional graph nodes) */
+                         kernels inside conditional graph nodes);
+                         2: one CUDA graph in which the mixed-precision clusters of a batch
+                         whose grids have the same shape run their iterations in lockstep:
+                         every kernel of an iteration is launched once for all of them (a
+                         cluster whose loop has ended returns at once), with the same
+                         arithmetic per cluster as 0 (bitwise the same results) */
     int boundary;     /* enum lasto_boundary: Dirichlet values on the box faces */
     int nu_coarse;    /* pre/post sweeps per level on the coarse levels the FP32 cycle of the
                          mixed precision runs inside one thread block (at most 17 nodes per axis,

@@ -228,6 +228,10 @@ struct lasto_poisson {
     // per batch slot: the cluster's branch stream, its setup stream and fork/join/done events
     std::vector<cudaStream_t> bs, ss;
     std::vector<cudaEvent_t> ef, ej, ed;
+    std::vector<cudaEvent_t> es, eb;     // per slot: iteration prologue done; lockstep loops done
+    // lockstep batches (launch = 2): the members' kernel arguments, on the device
+    char* bat_args = nullptr;
+    size_t bat_bytes = 0;
     // cached graph
     std::vector<char> key;
     cudaGraph_t graph = nullptr;
@@ -876,12 +880,238 @@ int count_kernels(cudaGraph_t g)
     return k;
 }
 
+// ---------------------------------------------------------------- lockstep batches (launch = 2)
+// Clusters of a defect-correction batch whose hierarchies have the same shape and storage run
+// their iterations in lockstep: each kernel is launched once for the whole group.
+constexpr size_t LOCKSTEP_MAX = BAT_MAX;   // members per lockstep group
+static_assert(sizeof(BatPack<BatLevel>) < 32000 && sizeof(BatPack<BatVec>) < 32000, "kernel parameter size");
+
+std::vector<std::vector<int>> lockstep_groups(const lasto_poisson* h, int nc)
+{
+    std::vector<std::vector<int>> groups;
+    if (h->cfg.launch != 2 || !is_defect_correction(h) || nc < 2) return groups;
+    std::map<std::array<int, 4>, std::vector<int>> by;
+    for (int c = 0; c < nc; c++) {
+        const ClusterPlan& P = h->plans[c];
+        if (P.L < 2 || bottom_level(P) < 1) continue;   // the group's coarsest levels run in one block
+        by[{P.lv[0].n[0], P.lv[0].n[1], P.lv[0].n[2], P.lv[0].split32 ? 1 : 0}].push_back(c);
+    }
+    for (auto& kv : by)
+        for (size_t a = 0; a < kv.second.size(); a += LOCKSTEP_MAX) {
+            std::vector<int> g(kv.second.begin() + a, kv.second.begin() + std::min(kv.second.size(), a + LOCKSTEP_MAX));
+            if (g.size() >= 2) groups.push_back(g);
+        }
+    return groups;
+}
+
+// a group's member arguments: by value for the level and vector kernels, in the handle's
+// device buffer for the bottom kernel and the loop conditions
+struct BatLayout {
+    std::vector<BatPack<BatLevel>> lev;
+    BatPack<BatVec> vec;
+    size_t bot = 0, ctls = 0;
+    int bl = 0;
+};
+
+BottomArgs<float> bottom_args(const lasto_poisson* h, const ClusterPlan& P, int l, bool sym)
+{
+    BottomArgs<float> a;
+    a.nlev = P.L - l;
+    for (int q = 0; q < a.nlev; q++) {
+        a.lv[q] = P.lv[l + q].view32();
+        a.u[q] = P.lv[l + q].u32;
+        a.b[q] = P.lv[l + q].b32;
+    }
+    a.eig = P.eig;
+    a.nu1 = h->cfg.nu_coarse;
+    a.nu2 = h->cfg.nu_coarse;
+    a.sym = sym ? 1 : 0;
+    return a;
+}
+
+// Fill the groups' argument arrays and copy them to the device (outside any capture).
+int upload_bat_args(lasto_poisson* h, const std::vector<std::vector<int>>& groups, std::vector<BatLayout>& lay)
+{
+    std::vector<char> blob;
+    auto put = [&](const void* src, size_t bytes) {
+        const size_t off = (blob.size() + 255) & ~size_t(255);
+        blob.resize(off + bytes);
+        std::memcpy(blob.data() + off, src, bytes);
+        return off;
+    };
+    lay.assign(groups.size(), BatLayout());
+    for (size_t gi = 0; gi < groups.size(); gi++) {
+        const std::vector<int>& g = groups[gi];
+        const int nm = (int)g.size();
+        BatLayout& L = lay[gi];
+        if (nm > BAT_MAX) return fail(h, LASTO_ERR_INVALID_ARG, "lockstep group too large");
+        L.bl = bottom_level(h->plans[g[0]]);
+        L.lev.assign(L.bl, BatPack<BatLevel>());
+        std::memset(L.lev.data(), 0, sizeof(BatPack<BatLevel>) * L.lev.size());
+        for (int l = 0; l < L.bl; l++) {
+            for (int q = 0; q < nm; q++) {
+                const ClusterPlan& P = h->plans[g[q]];
+                BatLevel& v = L.lev[l].m[q];
+                v.V = P.lv[l].view32();
+                v.VC = P.lv[l + 1].view32();
+                v.u = P.lv[l].u32;
+                v.b = P.lv[l].b32;
+                v.uc = P.lv[l + 1].u32;
+                v.bc = P.lv[l + 1].b32;
+                v.ctl = P.ctl;
+            }
+        }
+        std::memset(&L.vec, 0, sizeof(L.vec));
+        std::vector<BatBottom> bb(nm);
+        std::vector<Ctl*> cc(nm);
+        for (int q = 0; q < nm; q++) {
+            const ClusterPlan& P = h->plans[g[q]];
+            const LevelStore& F = P.lv[0];
+            bb[q].a = bottom_args(h, P, L.bl, true);
+            bb[q].ctl = P.ctl;
+            BatVec& a = L.vec.m[q];
+            a.V32 = F.view32();
+            a.V64 = F.view64();
+            a.u32 = F.u32;
+            a.b32 = F.b32;
+            a.e32 = P.e32;
+            a.p32 = P.p32;
+            a.q32 = P.q32;
+            a.u = F.u;
+            a.b = F.b;
+            a.r = F.r;
+            a.part = P.part;
+            a.counter = reinterpret_cast<unsigned int*>(P.status + 1);
+            a.ctl = P.ctl;
+            cc[q] = P.ctl;
+        }
+        L.bot = put(bb.data(), sizeof(BatBottom) * nm);
+        L.ctls = put(cc.data(), sizeof(Ctl*) * nm);
+    }
+    if (blob.empty()) return LASTO_OK;
+    if (blob.size() > h->bat_bytes) {
+        if (h->bat_args) cudaFree(h->bat_args);
+        h->bat_args = nullptr;
+        h->bat_bytes = 0;
+        TRY(cudaMalloc(&h->bat_args, blob.size()));
+        h->bat_bytes = blob.size();
+    }
+    TRY(cudaMemcpy(h->bat_args, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+    return LASTO_OK;
+}
+
+// One FP32 V-cycle of every member of a group (the preconditioner of the inner CG: symmetric
+// smoothing order), levels 0 .. bl-1 launched, the rest in one block per member.
+int enqueue_cycle_bat(lasto_poisson* h, const std::vector<int>& g, const BatLayout& L, cudaStream_t s)
+{
+    const ClusterPlan& P = h->plans[g[0]];
+    const int nm = (int)g.size();
+    auto lev = [&](int l) -> const BatPack<BatLevel>& { return L.lev[l]; };
+    auto nu_of = [&](int l, int v) { return (l == 0 && h->cfg.nu_fine > 0) ? h->cfg.nu_fine : v; };
+    auto nt_of = [&](int l) {
+        const SmoothChoice ch = smooth_choice<float>(h, P.lv[l]);
+        return ((ch.fused == 0 || ch.fused == 3) && ch.nt > 0) ? ch.nt : 256;
+    };
+    for (int l = 0; l < L.bl; l++) {
+        const LevelT<float> V = P.lv[l].view32(), VC = P.lv[l + 1].view32();
+        const int nu1 = nu_of(l, h->cfg.nu1), nt = nt_of(l);
+        for (int it = 0; it < nu1; it++) {
+            TRY(launch_rbgs_bat(V, lev(l), nm, 0, nt, s));
+            TRY(launch_rbgs_bat(V, lev(l), nm, 1, nt, s));
+        }
+        // after nu1 >= 1 sweeps that end on the black half sweep the black residuals are zero
+        TRY(launch_resid_restrict_bat(V, VC, lev(l), nm, nu1 > 0, s));
+    }
+    TRY(launch_bottom_bat(bottom_args(h, P, L.bl, true), reinterpret_cast<const BatBottom*>(h->bat_args + L.bot), nm,
+                          s));
+    for (int l = L.bl - 1; l >= 0; l--) {
+        const LevelT<float> V = P.lv[l].view32(), VC = P.lv[l + 1].view32();
+        const int nu2 = nu_of(l, h->cfg.nu2), nt = nt_of(l);
+        TRY(launch_prolong_add_bat(V, VC, lev(l), nm, s));
+        for (int it = 0; it < nu2; it++) {
+            TRY(launch_rbgs_bat(V, lev(l), nm, 1, nt, s));
+            TRY(launch_rbgs_bat(V, lev(l), nm, 0, nt, s));
+        }
+    }
+    return LASTO_OK;
+}
+
+// The defect-correction loops of one group, captured on stream gs: the outer WHILE over the
+// members' FP64 corrections around the inner WHILE of their FP32 CG iterations.
+int capture_group_loops(lasto_poisson* h, const std::vector<int>& g, const BatLayout& L, cudaStream_t gs)
+{
+    const ClusterPlan& P = h->plans[g[0]];
+    const int nm = (int)g.size();
+    const LevelStore& F = P.lv[0];
+    const LevelT<float> V32 = F.view32();
+    const BatPack<BatVec>& vec = L.vec;
+    Ctl* const* ctls = reinterpret_cast<Ctl* const*>(h->bat_args + L.ctls);
+    cudaGraphConditionalHandle cout_;
+    int st = new_handle(h, gs, &cout_);
+    if (st) return st;
+    TRY(launch_any_bat(ctls, nm, BAT_OUTER, cout_, gs));
+    cudaGraph_t body;
+    if ((st = add_while(h, gs, cout_, &body))) return st;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(h->cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaStreamBeginCaptureToGraph");
+    h->outer_bodies.push_back(body);
+    auto outer = [&]() -> int {
+        TRY(launch_dot32_bat(V32, vec, nm, 0, FIN_IN_START, BAT_OUTER, h->cs2));
+        TRY(launch_zero_bat(vec, nm, F.N(), 1, BAT_OUTER, h->cs2));
+        cudaGraphConditionalHandle cin;
+        int r = new_handle(h, h->cs2, &cin);
+        if (r) return r;
+        TRY(launch_any_bat(ctls, nm, BAT_INNER, cin, h->cs2));
+        cudaGraph_t ibody;
+        if ((r = add_while(h, h->cs2, cin, &ibody))) return r;
+        h->bodies.push_back(ibody);
+        cudaError_t e2 = cudaStreamBeginCaptureToGraph(h->cs3, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e2 != cudaSuccess) return set_cuda_error(&h->err, e2, "cudaStreamBeginCaptureToGraph(inner)");
+        auto inner = [&]() -> int {
+            TRY(launch_zero_bat(vec, nm, F.N(), 0, BAT_INNER, h->cs3));
+            int q = enqueue_cycle_bat(h, g, L, h->cs3);
+            if (q) return q;
+            TRY(launch_dot32_bat(V32, vec, nm, 1, FIN_IN_BETA, BAT_INNER, h->cs3));
+            TRY(launch_update_p32_bat(V32, vec, nm, h->cs3));
+            TRY(launch_apply_dot32_bat(V32, vec, nm, h->cs3));
+            TRY(launch_update_er32_bat(V32, vec, nm, h->cs3));
+            TRY(launch_any_bat(ctls, nm, BAT_INNER, cin, h->cs3));
+            return LASTO_OK;
+        };
+        r = inner();
+        cudaGraph_t iout = nullptr;
+        e2 = cudaStreamEndCapture(h->cs3, &iout);
+        if (r) return r;
+        if (e2 != cudaSuccess) return set_cuda_error(&h->err, e2, "cudaStreamEndCapture(inner)");
+        TRY(launch_outer_bat(F.view64(), vec, nm, V32.H, h->cs2));
+        TRY(launch_any_bat(ctls, nm, BAT_OUTER, cout_, h->cs2));
+        return LASTO_OK;
+    };
+    st = outer();
+    cudaGraph_t bout = nullptr;
+    e = cudaStreamEndCapture(h->cs2, &bout);
+    if (st) return st;
+    if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaStreamEndCapture(body)");
+    return LASTO_OK;
+}
+
 int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_lm, double* potential,
                   const double* guess)
 {
     cudaStream_t s = h->cs;
     h->bodies.clear();
     h->outer_bodies.clear();
+    const std::vector<std::vector<int>> groups = lockstep_groups(h, nc);
+    std::vector<BatLayout> lay;
+    if (int r = upload_bat_args(h, groups, lay)) return r;
+    std::vector<int> group_of(nc, -1);
+    for (size_t gi = 0; gi < groups.size(); gi++)
+        for (int c : groups[gi]) group_of[c] = (int)gi;
+    std::vector<size_t> atom_offs(nc, 0), grid_offs(nc, 0);
+    for (int c = 1; c < nc; c++) {
+        atom_offs[c] = atom_offs[c - 1] + cls[c - 1].n_atoms;
+        grid_offs[c] = grid_offs[c - 1] + (size_t)cls[c - 1].n[0] * cls[c - 1].n[1] * cls[c - 1].n[2];
+    }
     TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     int st = LASTO_OK;
     size_t atom_off = 0, grid_off = 0;
@@ -919,6 +1149,15 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
             e = cudaStreamWaitEvent(bsc, h->ev_net, 0);
             if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "guess fork"); break; }
             if ((st = enqueue_guess_out(h, P, cl, bsc))) break;
+        }
+        if (group_of[c] >= 0) {
+            // a lockstep member: its loops run with its group's (below)
+            if ((st = enqueue_start(h, P, 0, 0, bsc))) break;
+            e = cudaEventRecord(h->es[c], bsc);
+            if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "lockstep start"); break; }
+            atom_off += cl.n_atoms;
+            grid_off += (size_t)cl.n[0] * cl.n[1] * cl.n[2];
+            continue;
         }
         // conditional WHILE node(s) for the iteration
         cudaGraphConditionalHandle cond;
@@ -963,6 +1202,29 @@ int capture_solve(lasto_poisson* h, const lasto_cluster* cls, int nc, double* v_
         if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "join"); break; }
         atom_off += cl.n_atoms;
         grid_off += (size_t)cl.n[0] * cl.n[1] * cl.n[2];
+    }
+    for (size_t gi = 0; gi < groups.size() && st == LASTO_OK; gi++) {
+        const std::vector<int>& grp = groups[gi];
+        cudaStream_t gs = h->bs[grp[0]];
+        cudaError_t e = cudaSuccess;
+        for (int c : grp)
+            if (e == cudaSuccess && c != grp[0]) e = cudaStreamWaitEvent(gs, h->es[c], 0);
+        if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "lockstep join"); break; }
+        if ((st = capture_group_loops(h, grp, lay[gi], gs))) break;
+        if ((e = cudaEventRecord(h->eb[grp[0]], gs)) != cudaSuccess) { st = set_cuda_error(&h->err, e, "lockstep fork"); break; }
+        for (int c : grp) {
+            cudaStream_t bsc = h->bs[c];
+            if (c != grp[0] && (e = cudaStreamWaitEvent(bsc, h->eb[grp[0]], 0)) != cudaSuccess) {
+                st = set_cuda_error(&h->err, e, "lockstep fork");
+                break;
+            }
+            if ((st = enqueue_finish(h, h->plans[c], cls[c], v_lm + NLM * atom_offs[c],
+                                     potential ? potential + grid_offs[c] : nullptr, bsc)))
+                break;
+            e = cudaEventRecord(h->ed[c], bsc);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ed[c], 0);
+            if (e != cudaSuccess) { st = set_cuda_error(&h->err, e, "join"); break; }
+        }
     }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -1130,7 +1392,7 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
         cfg->n_theta < 1 || cfg->n_theta > 32 || cfg->n_phi < 1 || cfg->n_phi > 64 ||
         (cfg->precision != LASTO_PREC_FP64 && cfg->precision != LASTO_PREC_MIXED) ||
         (cfg->cycle != LASTO_CYCLE_V && cfg->cycle != LASTO_CYCLE_FV && cfg->cycle != LASTO_CYCLE_PCG) ||
-        (cfg->launch != 0 && cfg->launch != 1) || cfg->nu_coarse < 0 || cfg->nu_coarse > 64 || cfg->nu_fine < 0 || cfg->nu_fine > 64 ||
+        (cfg->launch < 0 || cfg->launch > 2) || cfg->nu_coarse < 0 || cfg->nu_coarse > 64 || cfg->nu_fine < 0 || cfg->nu_fine > 64 ||
         (cfg->boundary != LASTO_BC_MULTIPOLE && cfg->boundary != LASTO_BC_ZERO && cfg->boundary != LASTO_BC_EXACT))
         return LASTO_ERR_INVALID_ARG;
     lasto_poisson* h = new (std::nothrow) lasto_poisson();
@@ -1162,6 +1424,8 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
     h->ej.assign(cfg->max_batch, nullptr);
     h->ed.assign(cfg->max_batch, nullptr);
     h->eg.assign(cfg->max_batch, nullptr);
+    h->es.assign(cfg->max_batch, nullptr);
+    h->eb.assign(cfg->max_batch, nullptr);
     for (int c = 0; c < cfg->max_batch && e == cudaSuccess; c++) {
         e = cudaStreamCreateWithFlags(&h->bs[c], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->ss[c], cudaStreamNonBlocking);
@@ -1169,6 +1433,8 @@ int lasto_poisson_create(const lasto_config* cfg, lasto_poisson** out)
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ej[c], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ed[c], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->eg[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->es[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->eb[c], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaMallocHost(&h->stats_pinned, sizeof(lasto_stats) * cfg->max_batch);
     if (e != cudaSuccess) {
@@ -1199,6 +1465,9 @@ void lasto_poisson_destroy(lasto_poisson* h)
     for (auto x : h->ej) if (x) cudaEventDestroy(x);
     for (auto x : h->ed) if (x) cudaEventDestroy(x);
     for (auto x : h->eg) if (x) cudaEventDestroy(x);
+    for (auto x : h->es) if (x) cudaEventDestroy(x);
+    for (auto x : h->eb) if (x) cudaEventDestroy(x);
+    if (h->bat_args) cudaFree(h->bat_args);
     if (h->ev_net) cudaEventDestroy(h->ev_net);
     if (h->ev_launch) cudaEventDestroy(h->ev_launch);
     guess_net_free(h->net);

@@ -387,4 +387,62 @@ cudaError_t launch_project(const int n[3], const double* x, const double* y, con
                            int n_atoms, const double* pos, const double* R, const double* quad, int nq,
                            double* vlm, int* status, cudaStream_t s);
 
+// ---------------------------------------------------------------- lockstep batches (mg.cu)
+// Clusters whose grids have the same shape advance together: each kernel of the FP32 cycle and
+// of the CG / defect-correction steps is launched once for all members (blockIdx.y = member,
+// blockIdx.x as in the single-cluster launch), and a member whose loop has ended returns at the
+// top of every block.  `mode` picks the member's flag: BAT_INNER runs while its inner CG goes on
+// (Ctl::go_in), BAT_OUTER while its defect correction is not done.  Each member keeps its own
+// control block and reduction partials, so its arithmetic and sums are those of a
+// single-cluster launch.
+enum BatMode { BAT_INNER = 1, BAT_OUTER = 2 };
+
+struct BatLevel {            // one member's FP32 level l and l + 1
+    LevelT<float> V, VC;
+    float *u, *b, *uc, *bc;
+    const Ctl* ctl;
+};
+struct BatVec {              // one member's finest-level vectors, partials and control block
+    LevelT<float> V32;
+    LevelT<double> V64;
+    float *u32, *b32, *e32, *p32, *q32;
+    double *u, *b, *r;
+    double* part;
+    unsigned int* counter;
+    Ctl* ctl;
+};
+struct BatBottom {           // one member's one-block bottom levels
+    BottomArgs<float> a;
+    const Ctl* ctl;
+};
+
+// A group's member arguments, passed by value as a kernel parameter (constant bank; member =
+// blockIdx.y), at most BAT_MAX members.
+constexpr int BAT_MAX = 16;
+template <typename A>
+struct BatPack {
+    A m[BAT_MAX];
+};
+
+// In-place FP32 half sweep of colour `colour` on every member's level (V0: the shared shape):
+// the flat-index kernel (nt threads) in natural storage, one warp per row in colour-split storage.
+cudaError_t launch_rbgs_bat(const LevelT<float>& V0, const BatPack<BatLevel>& m, int nm, int colour, int nt,
+                            cudaStream_t s);
+cudaError_t launch_resid_restrict_bat(const LevelT<float>& F0, const LevelT<float>& C0, const BatPack<BatLevel>& m,
+                                      int nm, bool red_only, cudaStream_t s);
+cudaError_t launch_prolong_add_bat(const LevelT<float>& F0, const LevelT<float>& C0, const BatPack<BatLevel>& m,
+                                   int nm, cudaStream_t s);
+cudaError_t launch_bottom_bat(const BottomArgs<float>& a0, const BatBottom* m, int nm, cudaStream_t s);
+// finest-level steps; `op` the reduction's scalar step (FinOp)
+cudaError_t launch_zero_bat(const BatPack<BatVec>& m, int nm, size_t n, int which, int mode, cudaStream_t s);
+cudaError_t launch_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, int with_z, int op, int mode,
+                             cudaStream_t s);
+cudaError_t launch_update_p32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s);
+cudaError_t launch_apply_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s);
+cudaError_t launch_update_er32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s);
+cudaError_t launch_outer_bat(const LevelT<double>& V0, const BatPack<BatVec>& m, int nm, unsigned h32,
+                             cudaStream_t s);
+// the loop condition of a batch: 1 while any member's flag (mode) is set
+cudaError_t launch_any_bat(Ctl* const* ctls, int nm, int mode, cudaGraphConditionalHandle cond, cudaStream_t s);
+
 }  // namespace lasto

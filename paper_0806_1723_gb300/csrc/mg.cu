@@ -86,8 +86,7 @@ __device__ __forceinline__ T dsum(const LevelT<T>& L, int i, int j, int k)
 // (LS = 1: colour-split storage, FP32 only; thread t's node is then at t + colour H, so every
 // load and store of a warp is one unit-stride run)
 template <typename T, int LS>
-__global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour,
-                                             size_t nhalf)
+__device__ __forceinline__ void k_rbgs_body(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour, size_t nhalf)
 {
     const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;   // nodes < 2^31
     if (t >= (unsigned)nhalf) return;
@@ -102,6 +101,12 @@ __global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, co
     } else {
         u[Q] = rb_point32(acc, dsum(L, i, j, k));
     }
+}
+
+template <typename T, int LS>
+__global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour, size_t nhalf)
+{
+    k_rbgs_body<T, LS>(L, u, b, colour, nhalf);
 }
 
 // The same half sweep with one block per interior (j, k) row and one thread per node of the
@@ -134,8 +139,7 @@ __global__ void __launch_bounds__(512) k_rbgs_row(LevelT<T> L, T* __restrict__ u
 // in flight than the warps' own loads do.  The node update is k_rbgs's expression, so the two
 // are bitwise equal.
 template <int V>
-__global__ void __launch_bounds__(256) k_rbgs_split_rows(LevelT<float> L, float* __restrict__ u,
-                                                        const float* __restrict__ b, int colour, int pf)
+__device__ __forceinline__ void k_rbgs_split_rows_body(LevelT<float> L, float* __restrict__ u, const float* __restrict__ b, int colour, int pf)
 {
     const int my = L.ny - 2;
     const int row = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
@@ -190,9 +194,16 @@ __global__ void __launch_bounds__(256) k_rbgs_split_rows(LevelT<float> L, float*
 }
 
 template <int V>
-cudaError_t launch_split_rows_v(const LevelT<float>& L, float* u, const float* b, int colour, cudaStream_t s)
+__global__ void __launch_bounds__(256) k_rbgs_split_rows(LevelT<float> L, float* __restrict__ u, const float* __restrict__ b, int colour, int pf)
 {
-    // prefetch distance: half the rows the device holds resident (cached per device)
+    k_rbgs_split_rows_body<V>(L, u, b, colour, pf);
+}
+
+// prefetch distance of the row-per-warp sweep: half the rows the device holds resident
+// (cached per device)
+template <int V>
+cudaError_t split_rows_pf(int* pf)
+{
     static int pf_rows[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -205,8 +216,18 @@ cudaError_t launch_split_rows_v(const LevelT<float>& L, float* u, const float* b
         if (e != cudaSuccess) return e;
         pf_rows[dev] = std::max(1, per_sm * sms * 8 / 2);
     }
+    *pf = pf_rows[dev];
+    return cudaSuccess;
+}
+
+template <int V>
+cudaError_t launch_split_rows_v(const LevelT<float>& L, float* u, const float* b, int colour, cudaStream_t s)
+{
+    int pf = 0;
+    const cudaError_t e = split_rows_pf<V>(&pf);
+    if (e != cudaSuccess) return e;
     const int rows = (L.ny - 2) * (L.nz - 2);
-    k_rbgs_split_rows<V><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(L, u, b, colour, pf_rows[dev]);
+    k_rbgs_split_rows<V><<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(L, u, b, colour, pf);
     return cudaGetLastError();
 }
 
@@ -371,8 +392,7 @@ __global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, co
 // then its black ones: the row's y and z weights and coarse rows once per warp, no index
 // division; the node expression is k_prolong_add's, so the two are bitwise equal.
 template <int LS>
-__global__ void __launch_bounds__(256) k_prolong_add_rows(LevelT<float> F, LevelT<float> C,
-                                                         const float* __restrict__ ec, float* __restrict__ u)
+__device__ __forceinline__ void k_prolong_add_rows_body(LevelT<float> F, LevelT<float> C, const float* __restrict__ ec, float* __restrict__ u)
 {
     const int my = F.ny - 2;
     const int row = (int)(blockIdx.x * 8 + (threadIdx.x >> 5));
@@ -403,6 +423,12 @@ __global__ void __launch_bounds__(256) k_prolong_add_rows(LevelT<float> F, Level
             u[pos<LS>(F, f0 + (unsigned)i)] += e;
         }
     }
+}
+
+template <int LS>
+__global__ void __launch_bounds__(256) k_prolong_add_rows(LevelT<float> F, LevelT<float> C, const float* __restrict__ ec, float* __restrict__ u)
+{
+    k_prolong_add_rows_body<LS>(F, C, ec, u);
 }
 
 // (the fine level in either storage order, the coarse one natural)
@@ -589,9 +615,7 @@ __global__ void __launch_bounds__(NT) k_resid_restrict(LevelT<T> F, LevelT<T> C,
 // the weighted sum as zeros: 13 of the 27 residuals per coarse node, and the black half of b is
 // not read.
 template <int LS, int RED_ONLY>
-__global__ void __launch_bounds__(256) k_resid_restrict_rows(LevelT<float> F, LevelT<float> C,
-                                                            const float* __restrict__ u, const float* __restrict__ b,
-                                                            float* __restrict__ bc, float* __restrict__ uc)
+__device__ __forceinline__ void k_resid_restrict_rows_body(LevelT<float> F, LevelT<float> C, const float* __restrict__ u, const float* __restrict__ b, float* __restrict__ bc, float* __restrict__ uc)
 {
     const int row = (int)(blockIdx.x * 8 + (threadIdx.x >> 5));
     if (row >= C.ny * C.nz) return;
@@ -639,6 +663,12 @@ __global__ void __launch_bounds__(256) k_resid_restrict_rows(LevelT<float> F, Le
             }
         if (I < C.nx) bc[cb + I] = in ? acc : 0.0f;
     }
+}
+
+template <int LS, int RED_ONLY>
+__global__ void __launch_bounds__(256) k_resid_restrict_rows(LevelT<float> F, LevelT<float> C, const float* __restrict__ u, const float* __restrict__ b, float* __restrict__ bc, float* __restrict__ uc)
+{
+    k_resid_restrict_rows_body<LS, RED_ONLY>(F, C, u, b, bc, uc);
 }
 
 // (the fine level in either storage order, the coarse one natural; red_only: the fine iterate's
@@ -744,7 +774,7 @@ __device__ void bot_rbgs(const LevelT<T>& L, const BotItems& it, T* __restrict__
 // each axis; the kernel copies the tables and b in, works in shared memory only, and writes
 // the top bottom level's u back for the prolongation above it.
 template <typename T>
-__global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
+__device__ __forceinline__ void k_bottom_body(const BottomArgs<T>& a)
 {
     extern __shared__ __align__(16) unsigned char bot_smem[];
     // one block-wide copy of the level descriptors (pointing into shared memory)
@@ -864,6 +894,12 @@ __global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
 }
 
 template <typename T>
+__global__ void __launch_bounds__(BOT_NT) k_bottom(BottomArgs<T> a)
+{
+    k_bottom_body<T>(a);
+}
+
+template <typename T>
 size_t bottom_smem_bytes(const BottomArgs<T>& a)
 {
     size_t bytes = 2 * sizeof(double) * MC3;
@@ -885,8 +921,11 @@ cudaError_t launch_bottom(const BottomArgs<T>& a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+void init_bat_attributes();
+
 void init_mg_attributes()
 {
+    init_bat_attributes();
     cudaFuncSetAttribute(k_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_bottom<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
@@ -1071,9 +1110,7 @@ __global__ void __launch_bounds__(NT) k_bnorm(LevelT<double> L, const double* __
 
 // r = b - A u (written when r != nullptr, FP32 copy when r32 != nullptr, in colour-split
 // storage when h32 = ceil(N / 2) is nonzero) and ||r||^2
-__global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const double* __restrict__ u,
-                                                  const double* __restrict__ b, double* __restrict__ r,
-                                                  float* __restrict__ r32, unsigned h32, Red red)
+__device__ __forceinline__ void k_resid_norm_body(LevelT<double> L, const double* __restrict__ u, const double* __restrict__ b, double* __restrict__ r, float* __restrict__ r32, unsigned h32, Red red)
 {
     __shared__ double sm[32];
     double acc = 0.0;
@@ -1088,6 +1125,11 @@ __global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const doubl
         acc = fma(v, v, acc);
     }
     reduce_finish(block_sum<NT>(acc, sm), red, sm);
+}
+
+__global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const double* __restrict__ u, const double* __restrict__ b, double* __restrict__ r, float* __restrict__ r32, unsigned h32, Red red)
+{
+    k_resid_norm_body(L, u, b, r, r32, h32, red);
 }
 
 // q = A p and <p, q>_vol
@@ -1164,8 +1206,7 @@ __device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int
 // (the inner CG vectors share the finest level's FP32 storage order; every kernel walks the
 // nodes in flat order, so sums are formed in the same order in both)
 template <int LS>
-__global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p,
-                                                   float* __restrict__ q, Red red)
+__device__ __forceinline__ void k_apply_dot32_body(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q, Red red)
 {
     __shared__ double sm[32];
     float acc = 0.0f;
@@ -1185,9 +1226,13 @@ __global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float
 }
 
 template <int LS>
-__global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* __restrict__ ctl,
-                                                   const float* __restrict__ p, const float* __restrict__ q,
-                                                   float* __restrict__ e, float* __restrict__ r, Red red)
+__global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q, Red red)
+{
+    k_apply_dot32_body<LS>(L, p, q, red);
+}
+
+template <int LS>
+__device__ __forceinline__ void k_update_er32_body(LevelT<float> L, const Ctl* __restrict__ ctl, const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ e, float* __restrict__ r, Red red)
 {
     __shared__ double sm[32];
     const float alpha = (float)ctl->alpha_in;
@@ -1206,10 +1251,15 @@ __global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* 
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
 
+template <int LS>
+__global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* __restrict__ ctl, const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ e, float* __restrict__ r, Red red)
+{
+    k_update_er32_body<LS>(L, ctl, p, q, e, r, red);
+}
+
 // <r, z>_vol, or ||r||^2 when z == nullptr
 template <int LS>
-__global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __restrict__ r,
-                                             const float* __restrict__ z, Red red)
+__device__ __forceinline__ void k_dot32_body(LevelT<float> L, const float* __restrict__ r, const float* __restrict__ z, Red red)
 {
     __shared__ double sm[32];
     float acc = 0.0f;
@@ -1225,8 +1275,13 @@ __global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __re
 }
 
 template <int LS>
-__global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* __restrict__ ctl,
-                                                  const float* __restrict__ z, float* __restrict__ p)
+__global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __restrict__ r, const float* __restrict__ z, Red red)
+{
+    k_dot32_body<LS>(L, r, z, red);
+}
+
+template <int LS>
+__device__ __forceinline__ void k_update_p32_body(LevelT<float> L, const Ctl* __restrict__ ctl, const float* __restrict__ z, float* __restrict__ p)
 {
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
     if (P >= L.N()) return;
@@ -1236,16 +1291,26 @@ __global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* _
     p[Q] = is_face(L, i, j, k) ? 0.0f : fmaf((float)ctl->beta_in, p[Q], z[Q]);
 }
 
+template <int LS>
+__global__ void __launch_bounds__(NT) k_update_p32(LevelT<float> L, const Ctl* __restrict__ ctl, const float* __restrict__ z, float* __restrict__ p)
+{
+    k_update_p32_body<LS>(L, ctl, z, p);
+}
+
 // u += e (FP64 accumulation of the FP32 correction, e in colour-split storage when h32 =
 // ceil(N / 2) is nonzero); e = 0 for the next inner solve
-__global__ void __launch_bounds__(NT) k_add_correction(size_t N, double* __restrict__ u, float* __restrict__ e,
-                                                      unsigned h32)
+__device__ __forceinline__ void k_add_correction_body(size_t N, double* __restrict__ u, float* __restrict__ e, unsigned h32)
 {
     const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
     if (P >= N) return;
     const unsigned Q = h32 ? ((unsigned)P >> 1) + ((unsigned)P & 1u) * h32 : (unsigned)P;
     u[P] += (double)e[Q];
     e[Q] = 0.0f;
+}
+
+__global__ void __launch_bounds__(NT) k_add_correction(size_t N, double* __restrict__ u, float* __restrict__ e, unsigned h32)
+{
+    k_add_correction_body(N, u, e, h32);
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n)
@@ -1351,12 +1416,262 @@ __global__ void k_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter)
     c.iter_in = 0;
     c.max_in = 40;
     c.outer = 0;
+    c.go_in = 0;
 }
 
 cudaError_t launch_ctl_init(Ctl* ctl, double tol, double tol_iter, int max_iter, cudaStream_t s)
 {
     k_ctl_init<<<1, 1, 0, s>>>(ctl, tol, tol_iter, max_iter);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- lockstep batches
+__device__ __forceinline__ bool bat_on(const Ctl* c, int mode)
+{
+    return mode == BAT_INNER ? c->go_in != 0 : c->done == 0;
+}
+
+__global__ void __launch_bounds__(512) k_rbgs_bat(const __grid_constant__ BatPack<BatLevel> pk, int colour, size_t nhalf)
+{
+    const BatLevel& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    k_rbgs_body<float, 0>(a.V, a.u, a.b, colour, nhalf);
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_rbgs_split_rows_bat(const __grid_constant__ BatPack<BatLevel> pk, int colour, int pf)
+{
+    const BatLevel& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    k_rbgs_split_rows_body<V>(a.V, a.u, a.b, colour, pf);
+}
+
+template <int LS, int RED_ONLY>
+__global__ void __launch_bounds__(256) k_resid_restrict_rows_bat(const __grid_constant__ BatPack<BatLevel> pk)
+{
+    const BatLevel& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    k_resid_restrict_rows_body<LS, RED_ONLY>(a.V, a.VC, a.u, a.b, a.bc, a.uc);
+}
+
+template <int LS>
+__global__ void __launch_bounds__(256) k_prolong_add_rows_bat(const __grid_constant__ BatPack<BatLevel> pk)
+{
+    const BatLevel& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    k_prolong_add_rows_body<LS>(a.V, a.VC, a.uc, a.u);
+}
+
+__global__ void __launch_bounds__(BOT_NT) k_bottom_bat(const BatBottom* __restrict__ m)
+{
+    const BatBottom& a = m[blockIdx.x];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    k_bottom_body<float>(a.a);
+}
+
+__global__ void __launch_bounds__(NT) k_zero_bat(const __grid_constant__ BatPack<BatVec> pk, size_t n, int which, int mode)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, mode)) return;
+    float* x = which == 0 ? a.u32 : a.p32;
+    GRID_STRIDE(P, n) x[P] = 0.0f;
+}
+
+template <int LS>
+__global__ void __launch_bounds__(NT) k_dot32_bat(const __grid_constant__ BatPack<BatVec> pk, int with_z, int op, int mode)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, mode)) return;
+    const Red red{a.part, a.counter, a.ctl, op, 0, 0};
+    k_dot32_body<LS>(a.V32, a.b32, with_z ? a.u32 : nullptr, red);
+}
+
+template <int LS>
+__global__ void __launch_bounds__(NT) k_update_p32_bat(const __grid_constant__ BatPack<BatVec> pk)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    k_update_p32_body<LS>(a.V32, a.ctl, a.u32, a.p32);
+}
+
+template <int LS>
+__global__ void __launch_bounds__(NT) k_apply_dot32_bat(const __grid_constant__ BatPack<BatVec> pk)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    const Red red{a.part, a.counter, a.ctl, FIN_IN_ALPHA, 0, 0};
+    k_apply_dot32_body<LS>(a.V32, a.p32, a.q32, red);
+}
+
+template <int LS>
+__global__ void __launch_bounds__(NT) k_update_er32_bat(const __grid_constant__ BatPack<BatVec> pk)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    const Red red{a.part, a.counter, a.ctl, FIN_IN_CHECK, 0, 0};
+    k_update_er32_body<LS>(a.V32, a.ctl, a.p32, a.q32, a.e32, a.b32, red);
+}
+
+__global__ void __launch_bounds__(NT) k_add_correction_bat(const __grid_constant__ BatPack<BatVec> pk, size_t n, unsigned h32)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_OUTER)) return;
+    k_add_correction_body(n, a.u, a.e32, h32);
+}
+
+__global__ void __launch_bounds__(NT) k_resid_norm_bat(const __grid_constant__ BatPack<BatVec> pk, unsigned h32)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_OUTER)) return;
+    const Red red{a.part, a.counter, a.ctl, FIN_OUTER, 0, 0};
+    k_resid_norm_body(a.V64, a.u, a.b, a.r, a.b32, h32, red);
+}
+
+__global__ void k_any_bat(Ctl* const* __restrict__ ctls, int nm, int mode, cudaGraphConditionalHandle cond)
+{
+    int any = 0;
+    for (int c = 0; c < nm; c++) any |= bat_on(ctls[c], mode) ? 1 : 0;
+    cudaGraphSetConditional(cond, (unsigned)any);
+}
+
+cudaError_t launch_rbgs_bat(const LevelT<float>& V0, const BatPack<BatLevel>& m, int nm, int colour, int nt, cudaStream_t s)
+{
+    if (nm < 1 || nm > BAT_MAX) return cudaErrorInvalidValue;
+    if (V0.lsh) {
+        int pf = 0;
+        cudaError_t e = cudaSuccess;
+        const unsigned g = (unsigned)(((size_t)(V0.ny - 2) * (V0.nz - 2) + 7) / 8);
+#define LASTO_SPLIT_BAT(VV)                                                              \
+    case VV:                                                                             \
+        e = split_rows_pf<VV>(&pf);                                                      \
+        if (e != cudaSuccess) return e;                                                  \
+        k_rbgs_split_rows_bat<VV><<<dim3(g, (unsigned)nm), 256, 0, s>>>(m, colour, pf);   \
+        break;
+        switch (split_rows_v(V0.nx)) {
+            LASTO_SPLIT_BAT(1)
+            LASTO_SPLIT_BAT(2)
+            LASTO_SPLIT_BAT(3)
+            LASTO_SPLIT_BAT(4)
+            LASTO_SPLIT_BAT(5)
+            LASTO_SPLIT_BAT(6)
+            LASTO_SPLIT_BAT(7)
+            LASTO_SPLIT_BAT(8)
+            default: return cudaErrorInvalidValue;
+        }
+#undef LASTO_SPLIT_BAT
+        return cudaGetLastError();
+    }
+    if (nt < 32 || nt > 512 || nt % 32) nt = 256;
+    const size_t nhalf = (V0.N() + 1 - colour) / 2;
+    k_rbgs_bat<<<dim3((unsigned)((nhalf + nt - 1) / nt), (unsigned)nm), nt, 0, s>>>(m, colour, nhalf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resid_restrict_bat(const LevelT<float>& F0, const LevelT<float>& C0, const BatPack<BatLevel>& m, int nm,
+                                      bool red_only, cudaStream_t s)
+{
+    if (nm < 1 || nm > BAT_MAX || C0.lsh) return cudaErrorInvalidValue;
+    const dim3 g((unsigned)(((size_t)C0.ny * C0.nz + 7) / 8), (unsigned)nm);
+    if (F0.lsh && red_only)
+        k_resid_restrict_rows_bat<1, 1><<<g, 256, 0, s>>>(m);
+    else if (F0.lsh)
+        k_resid_restrict_rows_bat<1, 0><<<g, 256, 0, s>>>(m);
+    else if (red_only)
+        k_resid_restrict_rows_bat<0, 1><<<g, 256, 0, s>>>(m);
+    else
+        k_resid_restrict_rows_bat<0, 0><<<g, 256, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add_bat(const LevelT<float>& F0, const LevelT<float>& C0, const BatPack<BatLevel>& m, int nm,
+                                   cudaStream_t s)
+{
+    if (nm < 1 || nm > BAT_MAX || C0.lsh || F0.ny < 3 || F0.nz < 3) return cudaErrorInvalidValue;
+    const dim3 g((unsigned)(((size_t)(F0.ny - 2) * (F0.nz - 2) + 7) / 8), (unsigned)nm);
+    if (F0.lsh)
+        k_prolong_add_rows_bat<1><<<g, 256, 0, s>>>(m);
+    else
+        k_prolong_add_rows_bat<0><<<g, 256, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bottom_bat(const BottomArgs<float>& a0, const BatBottom* m, int nm, cudaStream_t s)
+{
+    const size_t smem = bottom_smem_bytes(a0);
+    if (smem > 200 * 1024 || nm < 1) return cudaErrorInvalidValue;
+    for (int q = 0; q < a0.nlev; q++)
+        if (a0.lv[q].lsh) return cudaErrorInvalidValue;
+    k_bottom_bat<<<(unsigned)nm, BOT_NT, smem, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_bat(const BatPack<BatVec>& m, int nm, size_t n, int which, int mode, cudaStream_t s)
+{
+    if (nm < 1 || nm > BAT_MAX) return cudaErrorInvalidValue;
+    k_zero_bat<<<dim3(red_grid(n), (unsigned)nm), NT, 0, s>>>(m, n, which, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, int with_z, int op, int mode,
+                             cudaStream_t s)
+{
+    const dim3 g(red_grid(V0.N()), (unsigned)nm);
+    if (V0.lsh)
+        k_dot32_bat<1><<<g, NT, 0, s>>>(m, with_z, op, mode);
+    else
+        k_dot32_bat<0><<<g, NT, 0, s>>>(m, with_z, op, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_p32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
+{
+    const dim3 g((unsigned)((V0.N() + NT - 1) / NT), (unsigned)nm);
+    if (V0.lsh)
+        k_update_p32_bat<1><<<g, NT, 0, s>>>(m);
+    else
+        k_update_p32_bat<0><<<g, NT, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
+{
+    const dim3 g(red_grid(V0.N()), (unsigned)nm);
+    if (V0.lsh)
+        k_apply_dot32_bat<1><<<g, NT, 0, s>>>(m);
+    else
+        k_apply_dot32_bat<0><<<g, NT, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_er32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
+{
+    const dim3 g(red_grid(V0.N()), (unsigned)nm);
+    if (V0.lsh)
+        k_update_er32_bat<1><<<g, NT, 0, s>>>(m);
+    else
+        k_update_er32_bat<0><<<g, NT, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_outer_bat(const LevelT<double>& V0, const BatPack<BatVec>& m, int nm, unsigned h32, cudaStream_t s)
+{
+    const size_t N = V0.N();
+    k_add_correction_bat<<<dim3((unsigned)((N + NT - 1) / NT), (unsigned)nm), NT, 0, s>>>(m, N, h32);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_resid_norm_bat<<<dim3(red_grid(N), (unsigned)nm), NT, 0, s>>>(m, h32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_any_bat(Ctl* const* ctls, int nm, int mode, cudaGraphConditionalHandle cond, cudaStream_t s)
+{
+    k_any_bat<<<1, 1, 0, s>>>(ctls, nm, mode, cond);
+    return cudaGetLastError();
+}
+
+void init_bat_attributes()
+{
+    cudaFuncSetAttribute(k_bottom_bat, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 // ---------------------------------------------------------------- instantiations

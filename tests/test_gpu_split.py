@@ -130,3 +130,50 @@ def test_tuner_offers_split_storage_on_the_finest_level():
     with pytest.raises(RuntimeError, match="INVALID_ARG"):
         solver.set_tune_table("97 97 97 8 3 256 0 0 0 0 0\n")
     solver.close()
+
+
+def _batch_solve(B, cls, launch, guess=True):
+    import torch
+    solver = B.Poisson(n_max=max(c.n for c in cls), max_atoms=max(c.n_atoms for c in cls), max_batch=len(cls),
+                       precision=B.LASTO_PREC_MIXED, launch=launch)
+    if guess:
+        solver.set_guess()
+    dcs = [B.DeviceCluster(c) for c in cls]
+    v = torch.empty((sum(c.n_atoms for c in cls), 25), dtype=torch.float64, device="cuda")
+    pot = torch.empty(sum(c.n ** 3 for c in cls), dtype=torch.float64, device="cuda")
+    out = []
+    for rep in range(2):                      # capture, then replay
+        st = solver.solve(dcs, v, potential=pot)
+        torch.cuda.synchronize()
+        out.append((host(v).copy(), host(pot).copy(), [(s.status, s.cycles, s.outer, s.rel_resid) for s in st]))
+    solver.close()
+    return out
+
+
+def test_lockstep_batch_equals_branches():
+    """launch = 2: clusters of the same grid shape run their iterations in lockstep (each kernel
+    launched once for the group, members that have converged skip it); a mixed batch of two
+    groups (three Pd13 65^3 with different densities, two Pd13 33^3) and a cluster alone in its
+    shape (97^3) gives bitwise the V_LM, potentials and stats of the branch graph (itself
+    checked against the oracle elsewhere), on the capture and on the replay."""
+    B = need_gpu()
+    cls = [synth.pd13_small(n=65, seed=1), synth.pd13_small(n=33, seed=2), synth.pd13_small(n=65, seed=3),
+           synth.pd13_small(n=97, seed=4), synth.pd13_small(n=33, seed=5), synth.pd13_small(n=65, seed=6)]
+    ref = _batch_solve(B, cls, 0)
+    got = _batch_solve(B, cls, 2)
+    for (v0, p0, s0), (v1, p1, s1) in zip(ref, got):
+        assert all(s[0] == 0 and s[3] <= 1e-10 for s in s1)
+        assert s0 == s1
+        assert np.array_equal(v0, v1) and np.array_equal(p0, p1)
+
+
+def test_lockstep_batch_of_eight_pd55():
+    """The benchmarked batch (8 Pd55 densities on the graded 129^3 mesh, learned guess) in
+    lockstep: bitwise the branch graph's results."""
+    B = need_gpu()
+    cls = [synth.pd55_graded129(seed=1 + k) for k in range(8)]
+    ref = _batch_solve(B, cls, 0)
+    got = _batch_solve(B, cls, 2)
+    for (v0, p0, s0), (v1, p1, s1) in zip(ref, got):
+        assert s0 == s1
+        assert np.array_equal(v0, v1) and np.array_equal(p0, p1)
