@@ -20,7 +20,7 @@ def test_defaults():
 
 
 @pytest.mark.parametrize("field,value", [("nu_coarse", -1), ("nu_coarse", 65), ("nu1", -1), ("n_max", 64),
-                                         ("max_batch", 0), ("rel_tol", 0.0), ("launch", 2), ("boundary", 7),
+                                         ("max_batch", 0), ("rel_tol", 0.0), ("launch", 3), ("boundary", 7),
                                          ("precision", 5), ("n_theta", 33)])
 def test_create_rejects_bad_config(field, value):
     binding, L = _lib()
