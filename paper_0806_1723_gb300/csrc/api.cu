@@ -17,6 +17,8 @@
 #include <vector>
 
 #include "ctl.cuh"
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 using namespace lasto;
@@ -253,6 +255,15 @@ struct lasto_poisson {
 };
 
 namespace {
+
+// A named range on the host thread's NVTX timeline (shown by profilers beside the kernels it
+// enqueues; a no-op without a profiler attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int fail(lasto_poisson* h, int code, const std::string& msg)
 {
@@ -1305,21 +1316,27 @@ static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, const lasto_
             return fail(h, LASTO_ERR_NO_MEMORY, "workspace too small for this batch");
         h->plans[c].raw = raws ? raws + c : nullptr;
     }
-    if (int st = tune_plans(h, cls, nc, s)) return st;
+    {
+        NvtxRange r("lasto: smoother tuning");
+        if (int st = tune_plans(h, cls, nc, s)) return st;
+    }
     size_t atom_off = 0, grid_off = 0;
     const int nguess = plan_guesses(h, cls, nc, guess);
     for (int c = 0; c < nc; c++) {
+        NvtxRange r("lasto: deposit, multipoles, faces");
         int st;
         if ((st = enqueue_prologue(h, h->plans[c], cls[c], guess ? guess + grid_off : nullptr, s, 0))) return st;
         if ((st = enqueue_guess_in(h, h->plans[c], cls[c], s))) return st;
         grid_off += (size_t)cls[c].n[0] * cls[c].n[1] * cls[c].n[2];
     }
     if (nguess > 0) {
+        NvtxRange r("lasto: learned guess");
         const int st = guess_net_forward(h->net, nguess, s);
         if (st) return fail(h, st, "guess network forward");
     }
     grid_off = 0;
     for (int c = 0; c < nc; c++) {
+        NvtxRange r("lasto: iteration");
         ClusterPlan& P = h->plans[c];
         const lasto_cluster& cl = cls[c];
         int st;
@@ -1350,6 +1367,7 @@ static int direct_solve(lasto_poisson* h, const lasto_cluster* cls, const lasto_
                 TRY(cudaStreamSynchronize(s));
             }
         }
+        NvtxRange rf("lasto: projection");
         if ((st = enqueue_finish(h, P, cl, v_lm + NLM * atom_off, potential ? potential + grid_off : nullptr, s)))
             return st;
         atom_off += cl.n_atoms;
@@ -1554,6 +1572,7 @@ static int solve_impl(lasto_poisson* h, const lasto_cluster* cls, const lasto_ra
                       double* v_lm, double* potential, const double* guess, lasto_stats* stats, void* stream)
 {
     if (!h) return LASTO_ERR_INVALID_ARG;
+    NvtxRange range("lasto_poisson_solve");
     h->err = Err();
     if (!cls || nc < 1 || nc > h->cfg.max_batch || !v_lm) return fail(h, LASTO_ERR_INVALID_ARG, "bad clusters/outputs");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1604,13 +1623,21 @@ static int solve_impl(lasto_poisson* h, const lasto_cluster* cls, const lasto_ra
             h->plans[c].raw = raws ? raws + c : nullptr;
         }
         h->key.clear();
-        int st = tune_plans(h, cls, nc, s);
+        int st;
+        {
+            NvtxRange r("lasto: smoother tuning");
+            st = tune_plans(h, cls, nc, s);
+        }
         if (st) return st;
-        st = capture_solve(h, cls, nc, v_lm, potential, guess);
+        {
+            NvtxRange r("lasto: graph capture");
+            st = capture_solve(h, cls, nc, v_lm, potential, guess);
+        }
         if (st) return st;
         h->key = key;
         h->n_clusters = nc;
     }
+    NvtxRange rl("lasto: graph launch");
     cudaError_t e = cudaGraphLaunch(h->exec, s);
     if (e != cudaSuccess) return set_cuda_error(&h->err, e, "cudaGraphLaunch");
     const int st = copy_stats(h, nc, stats, s);
