@@ -82,14 +82,15 @@ def parse():
     p.add_argument("--no-batch64", action="store_true")
     p.add_argument("--no-pd561", action="store_true")
     p.add_argument("--no-hs", action="store_true")
-    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "pd561warm", "deposit", "hs", "batch"],
+    p.add_argument("--profile", choices=["smoother", "solve", "guess", "pd561", "pd561warm", "deposit", "hs", "batch",
+                                          "train"],
                    default=None,
                    help="run one kernel family for a profiler and exit: 'smoother' = one FP32 red-black sweep "
                         "on an n^3 graded mesh, 'solve' = one mixed solve of the workload with direct launches, "
                         "'guess' = the same with the learned initial guess, 'pd561' = one chosen-form solve "
                         "of the Pd561 graded 385^3 workload with direct launches, 'pd561warm' = the second density "
                         "of that sequence warm-started from the first one's potential (the headline's steady "
-                        "state), 'deposit' = two FP32-pair density deposits of the Pd561 graded 385^3 density, 'hs' = one interstitial H and S "
+                        "state), 'deposit' = two FP32-pair density deposits of the Pd561 graded 385^3 density, 'train' = one training step of the learned guess's U-Net on 8 grids of 33^3 (tcgen05 kernels; --wmma for the warp-level MMA ones), 'hs' = one interstitial H and S "
                         "call (tensor cores) for Pd55 on the graded 129^3 mesh, 'batch' = one graph launch of the "
                         "chosen form over the 8 Pd55 clusters of the workload (for ncu --graph-profiling graph)")
     p.add_argument("--n", type=int, default=257, help="grid size of --profile smoother")
@@ -97,6 +98,7 @@ def parse():
                    help="launch shape of --profile smoother: threads per block, 0 = one block per row")
     p.add_argument("--sweeps", type=int, default=1, help="red-black sweeps of --profile smoother")
     p.add_argument("--fp64", action="store_true", help="--profile smoother in FP64 (the plain form's smoother)")
+    p.add_argument("--wmma", action="store_true", help="--profile train on the warp-level MMA kernels")
     p.add_argument("--split", action="store_true",
                    help="--profile smoother over colour-split storage (the finest FP32 level's layout)")
     p.add_argument("--direct", action="store_true",
@@ -634,6 +636,30 @@ def run_profile(args, B):
             B.lasto_op_smooth_split(*axes, u, b, sweeps=args.sweeps, threads=args.threads)
         else:
             B.lasto_op_smooth(*axes, u, b, sweeps=args.sweeps, threads=args.threads)
+    elif args.profile == "train":
+        from paper_0806_1723_gb300 import unet
+        net = unet.UNet(n=33, nb=8, seed=1, tc=not args.wmma)
+        N = 8 * 33 ** 3
+        g = torch.Generator(device="cuda").manual_seed(2)
+        x = torch.randn(N, 16, generator=g, device="cuda") * 0.5
+        x[:, 3:] = 0
+        tgt = torch.randn(N, generator=g, device="cuda")
+        mask = torch.ones(N, device="cuda")
+        net._mask_count = float(N)
+
+        def step():
+            net.forward(x)
+            net.loss_and_grad(tgt, mask)
+            net.backward(net.dpred)
+            net.adam(1e-4)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()   # ncu --profile-from-start off captures this step only
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     elif args.profile == "deposit":
         dc = B.DeviceCluster(synth.pd561_graded385(n_densities=1)[0])
         for _ in range(2):
