@@ -507,11 +507,15 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     }
     const float cut = DF_EXP_CUT / zmin;
     const float cut2 = cut * cut * (1.0f + 1e-5f);
-    int nkept;
-    // atoms within the cut-off of the tile's bounding box, in ascending order, tested in FP32
-    // on the records' float copies of the positions.  The margin 1e-3 on the squared distance
-    // covers the rounding of this test (~1e-6 relative) and of a node's own FP32 distance test,
-    // so an atom dropped here fails that test at every node of the tile.
+    int nkept, nnear;
+    // Atoms within the cut-off of the tile's bounding box, in ascending order, tested in FP32
+    // on the records' float copies of the positions: first those that may come within
+    // FAR_T / zeta_min of a node of the tile (near candidates), then those farther than that
+    // from every node (far-only).  The margins 1e-3 on the squared distances cover the
+    // rounding of these tests (~1e-6 relative) and of a node's own FP32 distance tests, so an
+    // atom dropped here fails the cut-off test, and a far-only atom passes the far test, at
+    // every node of the tile.
+    const float far_box2 = (FAR_T / zmin) * (FAR_T / zmin) * (1.0f + 1e-3f);
     {
         const float bx0 = (float)ox, bx1 = (float)a.ax[0][min(i0 + DT_X - 1, a.n[0] - 1)];
         const float by0 = (float)oy, by1 = (float)a.ax[1][min(j0 + DT_Y - 1, a.n[1] - 1)];
@@ -519,32 +523,46 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
         const float lim = cut2 * (1.0f + 1e-3f);
         const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
         int total = 0;
-        for (int base = 0; base < a.na; base += DEP_NT) {
-            const int t = base + threadIdx.x;
-            bool keep = false;
-            if (t < a.na) {
-                const float4 c = *reinterpret_cast<const float4*>(a.rec + (size_t)SPHERE_REC_DOUBLES * t + RXF);
-                const float ex = fmaxf(fmaxf(bx0 - c.x, c.x - bx1), 0.0f);
-                const float ey = fmaxf(fmaxf(by0 - c.y, c.y - by1), 0.0f);
-                const float ez = fmaxf(fmaxf(bz0 - c.z, c.z - bz1), 0.0f);
-                keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= lim;
+        for (int pass = 0; pass < 2; pass++) {
+            if (pass == 1) nnear = total;
+            for (int base = 0; base < a.na; base += DEP_NT) {
+                const int t = base + threadIdx.x;
+                bool keep = false;
+                if (t < a.na) {
+                    const float4 c = *reinterpret_cast<const float4*>(a.rec + (size_t)SPHERE_REC_DOUBLES * t + RXF);
+                    const float ex = fmaxf(fmaxf(bx0 - c.x, c.x - bx1), 0.0f);
+                    const float ey = fmaxf(fmaxf(by0 - c.y, c.y - by1), 0.0f);
+                    const float ez = fmaxf(fmaxf(bz0 - c.z, c.z - bz1), 0.0f);
+                    const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    keep = d2 <= lim && ((d2 > far_box2) == (pass == 1));
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, keep);
+                if (l == 0) s_cnt[w] = __popc(m);
+                __syncthreads();
+                int off = total, sum = 0;
+                for (int q = 0; q < DEP_NT / 32; q++) {
+                    off += q < w ? s_cnt[q] : 0;
+                    sum += s_cnt[q];
+                }
+                if (keep) list[off + __popc(m & ((1u << l) - 1u))] = t;
+                __syncthreads();
+                total += sum;
             }
-            const unsigned m = __ballot_sync(0xffffffffu, keep);
-            if (l == 0) s_cnt[w] = __popc(m);
-            __syncthreads();
-            int off = total, sum = 0;
-            for (int q = 0; q < DEP_NT / 32; q++) {
-                off += q < w ? s_cnt[q] : 0;
-                sum += s_cnt[q];
-            }
-            if (keep) list[off + __popc(m & ((1u << l) - 1u))] = t;
-            __syncthreads();
-            total += sum;
         }
-        // stage the kept atoms' fields in list order
+        // stage the kept atoms' fields in list order (far-only atoms: offsets and weights only,
+        // {D(x,y,z), W_0} and {W_1, W_2}, the layout of their loop below)
         for (int q = threadIdx.x; q < total; q += DEP_NT) {
             const double* r = a.rec + (size_t)SPHERE_REC_DOUBLES * list[q];
             float* o = sat + SAF * q;
+            if (q >= nnear) {
+                o[0] = (float)(r[RX] - ox);
+                o[1] = (float)(r[RX + 1] - oy);
+                o[2] = (float)(r[RX + 2] - oz);
+                o[3] = (float)r[RW];
+                o[4] = (float)r[RW + 1];
+                o[5] = (float)r[RW + 2];
+                continue;
+            }
             const df Dx = dfa::from_double(r[RX] - ox), Dy = dfa::from_double(r[RX + 1] - oy),
                      Dz = dfa::from_double(r[RX + 2] - oz);
             o[0] = Dx.h; o[1] = Dy.h; o[2] = Dz.h;
@@ -581,7 +599,7 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
     float sfar = 0.0f;
     int own = -1;
     df orr2 = {0.0f, 0.0f}, odx = s, ody = s, odz = s;
-    for (int q0 = 0; q0 < nkept; q0++) {
+    for (int q0 = 0; q0 < nnear; q0++) {
         const float* o = sat + SAF * q0;
         // the pair's distance in FP32 from the FP32 roundings of the two offsets (one subtraction
         // per axis): the atom's offset is at most r + the tile's extent, so r carries a relative
@@ -648,6 +666,25 @@ __global__ void __launch_bounds__(DEP_NT) k_deposit_df(DepArgs a)
                 }
                 s = dfa::add(s, dfa::mul(df{o[14 + 2 * q], o[15 + 2 * q]}, eq));
             }
+        }
+    }
+    // far-only atoms: every node of the tile is beyond FAR_T / zeta_min of them, so only the
+    // far-field terms remain, and a term whose exponent exceeds DF_EXP_CUT at that distance
+    // (zeta_q >= zeta_min DF_EXP_CUT / FAR_T) is dropped for all of them at once
+    {
+        bool qf[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) qf[q] = zt[q].h * (FAR_T / zmin) < DF_EXP_CUT;
+        const float z0 = zt[0].h, z1 = zt[1].h, z2 = zt[2].h;
+        for (int q0 = nnear; q0 < nkept; q0++) {
+            const float* o = sat + SAF * q0;
+            const float4 A = *reinterpret_cast<const float4*>(o);
+            const float fx = px.h - A.x, fy = py.h - A.y, fz = pz.h - A.z;
+            const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+            const float rf = r2f * rsqrtf(r2f);
+            if (qf[0]) sfar = fmaf(A.w, __expf(-z0 * rf), sfar);
+            if (qf[1]) sfar = fmaf(o[4], __expf(-z1 * rf), sfar);
+            if (qf[2]) sfar = fmaf(o[5], __expf(-z2 * rf), sfar);
         }
     }
     if (own >= 0) {
