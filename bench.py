@@ -1093,13 +1093,13 @@ def deposit_rate(B, synth, stream, flush, dev, probes):
 
 
 # One Pd561 385^3 deposit launch (k_deposit_df) under ncu (`bench.py --profile deposit`, second
-# launch): FP32 FLOP from the sass thread-instruction counts (2 per FFMA: 138.6 G, 1 per FADD:
-# 328.6 G and per FMUL: 96.4 G), the warp instructions issued (smsp__inst_executed.sum) and the
-# DRAM bytes (read 11.0 MB + written 848.5 MB); the launch issued 0.90 instructions per cycle per
+# launch): FP32 FLOP from the sass thread-instruction counts (2 per FFMA: 132.4 G, 1 per FADD:
+# 329.4 G and per FMUL: 89.9 G), the warp instructions issued (smsp__inst_executed.sum) and the
+# DRAM bytes (read 14.6 MB + written 850.7 MB); the launch issued 0.87 instructions per cycle per
 # scheduler.
-DEPOSIT_FP32_FLOP = 702.3e9
-DEPOSIT_WARP_INST = 36.975e9
-DEPOSIT_DRAM_BYTES = 859.5e6
+DEPOSIT_FP32_FLOP = 684.0e9
+DEPOSIT_WARP_INST = 32.623e9
+DEPOSIT_DRAM_BYTES = 865.3e6
 MAX_SM_MHZ = 2070.0   # the GB300's maximum SM clock (the clock the timed runs hold)
 
 
