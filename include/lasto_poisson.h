@@ -368,6 +368,11 @@ int lasto_op_smooth_f32(const int n[3], const double* x, const double* y, const 
  * black ones at (P - 1) / 2 + ceil(N / 2), N = n0 n1 n2.  Each half sweep then reads only the
  * other colour and its own right-hand side and writes only its own colour, all with unit
  * stride.  Bitwise the result of lasto_op_smooth_f32 on the same values in natural order.
+ * threads: as lasto_op_smooth_f32 (0: one warp per row, rows of at most 513 nodes), or 1 for
+ * the plane-staged kernel (a block marches a tile of 8 rows through a chunk of planes with the
+ * other colour's planes bulk-copied into shared memory one plane ahead; every axis at least 9
+ * nodes, rows of at most 513, u and b 16-byte aligned; this form synchronises the stream at the
+ * end and returns LASTO_ERR_TIMEOUT if one of its bounded device waits ran out).
  * INVALID_ARG also for an even axis. */
 int lasto_op_smooth_split_f32(const int n[3], const double* x, const double* y, const double* z, float* u,
                               const float* b, int sweeps, int threads, void* stream);

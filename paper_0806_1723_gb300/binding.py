@@ -431,9 +431,12 @@ def lasto_op_smooth(x, y, z, u, b, sweeps=1, threads=256, stream=None):
     return u
 
 
+SPLIT_STAGED = 1   # threads value of the plane-staged split half sweep
+
+
 def lasto_op_smooth_split(x, y, z, u, b, sweeps=1, threads=256, stream=None):
     """`sweeps` FP32 red-black sweeps in place on u and b held in colour-split storage
-    (split_colours)."""
+    (split_colours); threads = SPLIT_STAGED runs the plane-staged kernel."""
     _check(load().lasto_op_smooth_split_f32(*_axes(x, y, z), _ptr(u), _ptr(b), int(sweeps), int(threads),
                                             _stream(stream)), "lasto_op_smooth_split_f32")
     return u

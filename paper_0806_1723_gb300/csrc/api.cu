@@ -321,8 +321,8 @@ cudaError_t smooth(const LevelT<T>& V, T*& cur, T* partner, T* home, const T* b,
     }
     if (ch.fused == 0 || ch.fused == 3) {   // the view's storage order picks the kernel
         for (int it = 0; it < nu && e == cudaSuccess; it++) {
-            e = launch_rbgs<T>(V, cur, b, first, s, ch.nt);
-            if (e == cudaSuccess) e = launch_rbgs<T>(V, cur, b, 1 - first, s, ch.nt);
+            e = launch_rbgs<T>(V, cur, b, first, s, ch.nt, status);
+            if (e == cudaSuccess) e = launch_rbgs<T>(V, cur, b, 1 - first, s, ch.nt, status);
         }
         return e;
     }
@@ -344,6 +344,7 @@ int fused_passes(int nu, int ns) { return nu / ns + (nu % ns ? 1 : 0); }
 
 bool choice_usable(const lasto_poisson* h, const SmoothChoice& c, size_t elem)
 {
+    if (c.fused == 3 && c.nt == RBGS_STAGED) return elem == 4;
     if (c.fused == 0 || c.fused == 3)
         return (c.fused == 0 || elem == 4) && (c.nt == 0 || (c.nt >= 32 && c.nt <= 512 && c.nt % 32 == 0));
     if (c.fused == 2) return elem == 4 && wave_shape_ok(c.sh) && (h->cfg.nu1 + h->cfg.nu2) % 2 == 0;
@@ -389,8 +390,9 @@ int tune_level(lasto_poisson* h, LevelStore& S, bool finest, cudaStream_t st)
     }
     const bool f32 = sizeof(T) == 4;
     if (f32 && finest)
-        for (int nt : {128, 256, 512, 0}) {
+        for (int nt : {128, 256, 512, 0, RBGS_STAGED}) {
             if (nt == 0 && (S.n[0] + 1) / 2 > 512) continue;
+            if (nt == RBGS_STAGED && !split_stage_ok(S.n[0], S.n[1], S.n[2])) continue;
             SmoothChoice c;
             c.fused = 3;
             c.nt = nt;
@@ -498,6 +500,7 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
         ch.fused = 3;
     } else if (ch.fused == 3) {
         ch.fused = 0;
+        if (ch.nt == RBGS_STAGED) ch.nt = 0;   // natural storage: one block per row
     }
     T* cur = u;   // fused passes move the iterate between u and the partner array
     TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu1, 0, ch, P.status, s));
@@ -1021,7 +1024,7 @@ int enqueue_cycle_bat(lasto_poisson* h, const std::vector<int>& g, const BatLayo
     auto nu_of = [&](int l, int v) { return (l == 0 && h->cfg.nu_fine > 0) ? h->cfg.nu_fine : v; };
     auto nt_of = [&](int l) {
         const SmoothChoice ch = smooth_choice<float>(h, P.lv[l]);
-        return ((ch.fused == 0 || ch.fused == 3) && ch.nt > 0) ? ch.nt : 256;
+        return ((ch.fused == 0 || ch.fused == 3) && ch.nt >= 32) ? ch.nt : 256;
     };
     for (int l = 0; l < L.bl; l++) {
         const LevelT<float> V = P.lv[l].view32(), VC = P.lv[l + 1].view32();
@@ -1869,19 +1872,31 @@ int lasto_op_smooth_split_f32(const int n[3], const double* x, const double* y, 
                               const float* b, int sweeps, int threads, void* stream)
 {
     if (!op_grid_ok(n, x, y, z) || !u || !b || sweeps < 0) return LASTO_ERR_INVALID_ARG;
-    if (threads != 0 && (threads < 32 || threads > 512 || threads % 32)) return LASTO_ERR_INVALID_ARG;
+    const bool staged = threads == RBGS_STAGED;
+    if (threads != 0 && !staged && (threads < 32 || threads > 512 || threads % 32)) return LASTO_ERR_INVALID_ARG;
     if (threads == 0 && n[0] > 1023) return LASTO_ERR_INVALID_ARG;
     for (int d = 0; d < 3; d++)
         if (n[d] % 2 == 0) return LASTO_ERR_INVALID_ARG;   // the colour is the flat-index parity
+    if (staged && (!split_stage_ok(n[0], n[1], n[2]) || ((uintptr_t)u & 15u) || ((uintptr_t)b & 15u)))
+        return LASTO_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     OpLevel L(n, x, y, z, false, s);
     if (!L.ok()) return LASTO_ERR_NO_MEMORY;
     LevelT<float> V = L.S.view32();
     set_split(V, true);
-    cudaError_t e = cudaSuccess;
+    // the staged kernel's bounded waits report into a device word read back at the end
+    Scratch st(staged ? sizeof(int) : 0, s);
+    if (staged && !st.p) return LASTO_ERR_NO_MEMORY;
+    cudaError_t e = staged ? cudaMemsetAsync(st.p, 0, sizeof(int), s) : cudaSuccess;
     for (int it = 0; it < sweeps && e == cudaSuccess; it++) {
-        e = launch_rbgs<float>(V, u, b, 0, s, threads);
-        if (e == cudaSuccess) e = launch_rbgs<float>(V, u, b, 1, s, threads);
+        e = launch_rbgs<float>(V, u, b, 0, s, threads, st.as<int>());
+        if (e == cudaSuccess) e = launch_rbgs<float>(V, u, b, 1, s, threads, st.as<int>());
+    }
+    if (staged && e == cudaSuccess) {
+        int flag = 0;
+        e = cudaMemcpyAsync(&flag, st.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && flag) return flag;
     }
     return op_status(e);
 }

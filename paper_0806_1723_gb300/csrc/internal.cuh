@@ -58,10 +58,17 @@ void host_solid_harmonics(double x, double y, double z, double* S);
 __host__ __device__ __forceinline__ int l_of_lm(int lm) { return lm >= 16 ? 4 : lm >= 9 ? 3 : lm >= 4 ? 2 : lm >= 1 ? 1 : 0; }
 
 // ---------------------------------------------------------------- FP32 point update
-// u = acc / (-dsum) of a red-black FP32 update as acc times the correctly rounded reciprocal:
-// the same expression in every FP32 smoother variant (so they stay bitwise equal), and about
-// 10 % faster than the IEEE division in the memory-bound half sweep.
-__device__ __forceinline__ float rb_point32(float acc, float dsum) { return acc * __frcp_rn(-dsum); }
+// u = acc / (-dsum) of a red-black FP32 update as acc times the hardware's approximate
+// reciprocal (rcp.approx.ftz.f32, relative error below 2^-23 for the diagonal's range, one
+// instruction): the same expression in every FP32 smoother variant, so they stay bitwise equal.
+// The correctly rounded reciprocal costs a Newton step and a special-case branch per node, about
+// 6 % of the row-per-warp half sweep's time; a smoother's update needs no last-bit rounding.
+__device__ __forceinline__ float rb_point32(float acc, float dsum)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-dsum));
+    return acc * r;
+}
 
 // ---------------------------------------------------------------- block reductions
 template <int NT>
@@ -212,8 +219,17 @@ cudaError_t launch_inv_diag(const LevelStore& L, cudaStream_t s);
 cudaError_t launch_coarse_eig(const LevelStore& L, CoarseEig* eig, cudaStream_t s);
 
 // mg.cu
+// nt: threads per block of the flat kernels (32 .. 512), 0 for one warp (colour-split storage)
+// or one block (natural) per row, RBGS_STAGED for the plane-staged kernel of stage.cu
+// (colour-split FP32 only); status (may be null) receives LASTO_ERR_TIMEOUT from its bounded waits
+constexpr int RBGS_STAGED = 1;
 template <typename T>
-cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt = 256);
+cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt = 256,
+                        int* status = nullptr);
+// stage.cu
+cudaError_t launch_split_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s);
+bool split_stage_ok(int nx, int ny, int nz);
+void init_stage_attributes();
 template <typename T>
 cudaError_t launch_residual(const LevelT<T>& L, const T* u, const T* b, T* r, cudaStream_t s);
 template <typename T>

@@ -154,14 +154,22 @@ __device__ __forceinline__ void k_rbgs_split_rows_body(LevelT<float> L, float* _
     const unsigned q0 = ((unsigned)k * nxy + (unsigned)j * (unsigned)nx + (unsigned)i1) >> 1;
     const int hx = (nx - 1) >> 1, hxy = (int)((nxy - 1) >> 1);
     const int dxm = c - 1, dxp = c, dym = c - 1 - hx, dyp = c + hx, dzm = c - 1 - hxy, dzp = c + hxy;
-    const float* __restrict__ o = u + (size_t)(1 - c) * L.H + q0;   // the other colour, from q0
-    float* __restrict__ uo = u + (size_t)c * L.H + q0;
-    const float* __restrict__ bo = b + (size_t)c * L.H + q0;
+    // lane l's nodes are l + 32 v from q0: one base pointer per operand stream, so every load and
+    // store below is that base plus a compile-time offset (no per-node address arithmetic)
+    const float* __restrict__ o = u + (size_t)(1 - c) * L.H + q0 + lane;   // the other colour
+    const float* __restrict__ nxm = o + dxm;
+    const float* __restrict__ nxp = o + dxp;
+    const float* __restrict__ nym = o + dym;
+    const float* __restrict__ nyp = o + dyp;
+    const float* __restrict__ nzm = o + dzm;
+    const float* __restrict__ nzp = o + dzp;
+    float* __restrict__ uo = u + (size_t)c * L.H + q0 + lane;
+    const float* __restrict__ bo = b + (size_t)c * L.H + q0 + lane;
     const float cmy = L.ax[1].cm[j], cpy = L.ax[1].cp[j], dgy = L.ax[1].dg[j];
     const float cmz = L.ax[2].cm[k], cpz = L.ax[2].cp[k], dgz = L.ax[2].dg[k];
-    const float* __restrict__ cmx = L.ax[0].cm + i1;
-    const float* __restrict__ cpx = L.ax[0].cp + i1;
-    const float* __restrict__ dgx = L.ax[0].dg + i1;
+    const float* __restrict__ cmx = L.ax[0].cm + i1 + 2 * lane;
+    const float* __restrict__ cpx = L.ax[0].cp + i1 + 2 * lane;
+    const float* __restrict__ dgx = L.ax[0].dg + i1 + 2 * lane;
     if (row + pf < my * (L.nz - 2)) {
         // (an interior row's lines, up to 31 values past its end: still inside the array, as
         // the face plane follows)
@@ -176,19 +184,18 @@ __device__ __forceinline__ void k_rbgs_split_rows_body(LevelT<float> L, float* _
             asm volatile("prefetch.global.L2 [%0];" ::"l"(pz));
         }
     }
+    const int left = cnt - lane;
 #pragma unroll
     for (int v = 0; v < V; v++) {
-        const int s = lane + 32 * v;
-        if (s < cnt) {
-            const float* __restrict__ n = o + s;
-            float t = cmx[2 * s] * n[dxm];
-            t = fmaf(cpx[2 * s], n[dxp], t);
-            t = fmaf(cmy, n[dym], t);
-            t = fmaf(cpy, n[dyp], t);
-            t = fmaf(cmz, n[dzm], t);
-            t = fmaf(cpz, n[dzp], t);
-            const float acc = bo[s] - t;
-            uo[s] = rb_point32(acc, dgx[2 * s] + dgy + dgz);
+        if (32 * v < left) {
+            float t = cmx[64 * v] * nxm[32 * v];
+            t = fmaf(cpx[64 * v], nxp[32 * v], t);
+            t = fmaf(cmy, nym[32 * v], t);
+            t = fmaf(cpy, nyp[32 * v], t);
+            t = fmaf(cmz, nzm[32 * v], t);
+            t = fmaf(cpz, nzp[32 * v], t);
+            const float acc = bo[32 * v] - t;
+            uo[32 * v] = rb_point32(acc, dgx[64 * v] + dgy + dgz);
         }
     }
 }
@@ -237,10 +244,16 @@ inline int split_rows_v(int nx) { return (nx - 1) / 2 <= 256 ? std::max(1, ((nx 
 // nt > 0: k_rbgs with nt threads per block; nt == 0: k_rbgs_row (rows of at most 1023 nodes),
 // over colour-split storage k_rbgs_split_rows (rows of at most 513 nodes)
 template <typename T>
-cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt)
+cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt, int* status)
 {
     const bool split = L.lsh != 0;
     if (split && sizeof(T) != 4) return cudaErrorInvalidValue;   // FP64 levels keep natural storage
+    if (nt == RBGS_STAGED) {
+        if constexpr (sizeof(T) == 4) {
+            if (split) return launch_split_stage(L, u, b, colour, status, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (nt == 0 && split) {
         if constexpr (sizeof(T) == 4) {
             if (L.ny < 3 || L.nz < 3) return cudaErrorInvalidValue;
@@ -389,8 +402,12 @@ __global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, co
 }
 
 // The same in FP32 with one warp per interior fine (j, k) row, lanes along the row's red nodes and
-// then its black ones: the row's y and z weights and coarse rows once per warp, no index
-// division; the node expression is k_prolong_add's, so the two are bitwise equal.
+// its black ones: the row's y and z weights and coarse rows once per warp, no index division; the
+// node expression is k_prolong_add's, so the two are bitwise equal.  A lane takes PU nodes of each
+// colour run (64 fine nodes apart) per step and loads all their fine values before the first
+// update, so 2 PU loads of the iterate are in flight per lane rather than one.
+constexpr int PU = 3;
+
 template <int LS>
 __device__ __forceinline__ void k_prolong_add_rows_body(LevelT<float> F, LevelT<float> C, const float* __restrict__ ec, float* __restrict__ u)
 {
@@ -407,21 +424,40 @@ __device__ __forceinline__ void k_prolong_add_rows_body(LevelT<float> F, LevelT<
     const unsigned f0 = ((unsigned)k * (unsigned)F.ny + (unsigned)j) * (unsigned)F.nx;
     // the red nodes of the row, then the black ones (unit stride over colour-split storage); the
     // parity of i, and with it the x stencil, is the same along a run
-    for (int t = 0; t < 2; t++) {
-        const int ic = (t + j + k) & 1;
-        for (int i = (ic ? 1 : 2) + 2 * lane; i < F.nx - 1; i += 64) {
-            const int ni = (i & 1) ? 2 : 1;
-            const float wx[2] = {F.ax[0].pl[i], F.ax[0].pr[i]};
-            const float* base = crow + (i >> 1);
-            float e = 0.0f;
-            for (int c = 0; c < nk; c++)
-                for (int bb = 0; bb < nj; bb++) {
-                    const float* r = base + c * sz + bb * sy;
-                    const float sv = (ni == 2) ? fmaf(wx[0], r[0], wx[1] * r[1]) : r[0];
-                    e = fmaf(wz[c] * wy[bb], sv, e);
-                }
-            u[pos<LS>(F, f0 + (unsigned)i)] += e;
-        }
+    for (int m0 = 0; 64 * m0 < F.nx; m0 += PU) {
+        float uv[2][PU];
+        unsigned Q[2][PU];
+        bool ok[2][PU];
+#pragma unroll
+        for (int t = 0; t < 2; t++)
+#pragma unroll
+            for (int m = 0; m < PU; m++) {
+                const int i = (((t + j + k) & 1) ? 1 : 2) + 2 * lane + 64 * (m0 + m);
+                ok[t][m] = i < F.nx - 1;
+                Q[t][m] = pos<LS>(F, f0 + (unsigned)i);
+                uv[t][m] = ok[t][m] ? u[Q[t][m]] : 0.0f;
+            }
+#pragma unroll
+        for (int t = 0; t < 2; t++)
+#pragma unroll
+            for (int m = 0; m < PU; m++) {
+                if (!ok[t][m]) continue;
+                const int i = (((t + j + k) & 1) ? 1 : 2) + 2 * lane + 64 * (m0 + m);
+                const int ni = (i & 1) ? 2 : 1;
+                const float wx[2] = {F.ax[0].pl[i], F.ax[0].pr[i]};
+                const float* base = crow + (i >> 1);
+                float e = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 2; c++)
+#pragma unroll
+                    for (int bb = 0; bb < 2; bb++) {
+                        if (c >= nk || bb >= nj) continue;
+                        const float* r = base + c * sz + bb * sy;
+                        const float sv = (ni == 2) ? fmaf(wx[0], r[0], wx[1] * r[1]) : r[0];
+                        e = fmaf(wz[c] * wy[bb], sv, e);
+                    }
+                u[Q[t][m]] = uv[t][m] + e;
+            }
     }
 }
 
@@ -926,6 +962,7 @@ void init_bat_attributes();
 void init_mg_attributes()
 {
     init_bat_attributes();
+    init_stage_attributes();
     cudaFuncSetAttribute(k_bottom<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_bottom<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
@@ -1205,30 +1242,158 @@ __device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int
 
 // (the inner CG vectors share the finest level's FP32 storage order; every kernel walks the
 // nodes in flat order, so sums are formed in the same order in both)
+//
+// Each thread takes VU nodes a block's width apart per step and issues all their loads before
+// the first use: with one node per step a thread holds 4-8 B of DRAM loads in flight, a fraction
+// of what the copy rate needs at full occupancy, and the FP32 vector kernels ran at a quarter to
+// a half of it.  The accumulation order within a thread is the nodes' order.
+// The reducing ones run in one wave of VEC_BLOCKS blocks, a number of blocks per SM that their
+// register bound guarantees resident (a second, partial wave would leave SMs idle at the end).
+constexpr int VU = 4;
+constexpr int VEC_MIN_BLOCKS = 4;
+constexpr int VEC_BLOCKS = 152 * VEC_MIN_BLOCKS;
+static unsigned vec_grid(size_t N) { return (unsigned)std::min<size_t>((N + NT * VU - 1) / (NT * VU), VEC_BLOCKS); }
+#define GRID_STRIDE_U(P0, N) \
+    for (size_t P0 = blockIdx.x * (size_t)(NT * VU) + threadIdx.x; P0 < (N); P0 += (size_t)gridDim.x * (NT * VU))
+
 template <int LS>
 __device__ __forceinline__ void k_apply_dot32_body(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q, Red red)
 {
     __shared__ double sm[32];
     float acc = 0.0f;
-    GRID_STRIDE(P, L.N())
+    const size_t N = L.N();
+    GRID_STRIDE_U(P0, N)
     {
-        int i, j, k;
-        node_ijk(P, L, i, j, k);
-        const unsigned Q = pos<LS>(L, P);
-        float v = 0.0f;
-        if (!is_face(L, i, j, k)) {
-            v = fmaf(-dsum(L, i, j, k), p[Q], offdiag<LS>(L, p, P, i, j, k));
-            acc = fmaf(vol32(L, i, j, k) * p[Q], v, acc);
+        float pc[VU], od[VU], dg[VU], w[VU];
+        unsigned Q[VU];
+        bool in[VU], face[VU];
+#pragma unroll
+        for (int u = 0; u < VU; u++) {
+            const size_t P = P0 + (size_t)u * NT;
+            in[u] = P < N;
+            face[u] = true;
+            Q[u] = 0u;
+            pc[u] = od[u] = dg[u] = w[u] = 0.0f;
+            if (in[u]) {
+                int i, j, k;
+                node_ijk(P, L, i, j, k);
+                Q[u] = pos<LS>(L, P);
+                face[u] = is_face(L, i, j, k);
+                if (!face[u]) {
+                    pc[u] = p[Q[u]];
+                    od[u] = offdiag<LS>(L, p, P, i, j, k);
+                    dg[u] = dsum(L, i, j, k);
+                    w[u] = vol32(L, i, j, k);
+                }
+            }
         }
-        q[Q] = v;
+#pragma unroll
+        for (int u = 0; u < VU; u++) {
+            if (!in[u]) continue;
+            float v = 0.0f;
+            if (!face[u]) {
+                v = fmaf(-dg[u], pc[u], od[u]);
+                acc = fmaf(w[u] * pc[u], v, acc);
+            }
+            q[Q[u]] = v;
+        }
     }
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
 
 template <int LS>
-__global__ void __launch_bounds__(NT) k_apply_dot32(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q, Red red)
+__global__ void __launch_bounds__(NT, VEC_MIN_BLOCKS) k_apply_dot32(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q, Red red)
 {
     k_apply_dot32_body<LS>(L, p, q, red);
+}
+
+// The same with one warp per interior (j, k) row, its red nodes and then its black ones, lanes
+// along the run: the row's y and z coefficients and volume factors once per warp, the six
+// neighbours of a node at offsets fixed along the run (in the other half of colour-split storage)
+// and no index division, where the flat form above spends about as many instructions on indexing
+// as the copy rate leaves it.  Face nodes of q are not written (the CG reads q at interior nodes
+// only).  One row per warp while the grid allows (the reduction takes one partial per block, at
+// most ceil(N / 256) of them), else a grid-stride loop over rows; L2 prefetch of the z+ row of the
+// row pf ahead, both colours, as in the row-per-warp half sweep.  Sums run in the same order in
+// both storage orders.
+template <int LS, int V>
+__device__ __forceinline__ void k_apply_dot32_rows_body(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q, Red red, int pf)
+{
+    __shared__ double sm[32];
+    float acc = 0.0f;
+    const int my = L.ny - 2, rows = my * (L.nz - 2);
+    const int lane = threadIdx.x & 31;
+    const int nx = L.nx;
+    const unsigned nxy = (unsigned)nx * (unsigned)L.ny;
+    const int hx = (nx - 1) >> 1, hxy = (int)((nxy - 1) >> 1);
+    for (int row = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); row < rows;
+         row += (int)(gridDim.x * (blockDim.x >> 5))) {
+        const int k = row / my + 1, j = row - (k - 1) * my + 1;
+        if (pf > 0 && row + pf < rows) {
+            const int r2 = row + pf;
+            const int k2 = r2 / my + 2, j2 = r2 - (k2 - 2) * my + 1;   // the z+ row of row r2
+            if (k2 <= L.nz - 2 && lane < 2 * ((hx + 32) / 32)) {
+                const int c2 = lane & 1, l2 = lane >> 1;
+                const unsigned P2 = (unsigned)k2 * nxy + (unsigned)j2 * (unsigned)nx;
+                const float* a = LS ? p + (size_t)c2 * L.H + (P2 >> 1) + 32 * l2 : p + P2 + 64 * l2 + 32 * c2;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+            }
+        }
+        const float cmy = L.ax[1].cm[j], cpy = L.ax[1].cp[j], dgy = L.ax[1].dg[j];
+        const float cmz = L.ax[2].cm[k], cpz = L.ax[2].cp[k], dgz = L.ax[2].dg[k];
+        const float vy = L.ax[1].dual[j], vz = L.ax[2].dual[k];
+        const unsigned Prow = (unsigned)k * nxy + (unsigned)j * (unsigned)nx;
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const int i1 = ((c + j + k) & 1) ? 1 : 2;   // first interior node of the colour
+            const int left = ((nx - i1) >> 1) - lane;   // the colour's interior nodes past lane's first
+            const unsigned P0 = Prow + (unsigned)i1;
+            // one base pointer per operand stream, lane's first node; node v is 32 v nodes of the
+            // colour further on (a compile-time offset)
+            constexpr int ST = LS ? 1 : 2;
+            const float* __restrict__ cmx = L.ax[0].cm + i1 + 2 * lane;
+            const float* __restrict__ cpx = L.ax[0].cp + i1 + 2 * lane;
+            const float* __restrict__ dgx = L.ax[0].dg + i1 + 2 * lane;
+            const float* __restrict__ vx = L.ax[0].dual + i1 + 2 * lane;
+            const float *own, *nxm, *nxp, *nym, *nyp, *nzm, *nzp;
+            float* qo;
+            if constexpr (LS == 1) {
+                const unsigned q0 = (P0 >> 1) + (unsigned)lane;
+                own = p + (size_t)c * L.H + q0;
+                qo = q + (size_t)c * L.H + q0;
+                const float* o = p + (size_t)(1 - c) * L.H + q0;
+                nxm = o + (c - 1), nxp = o + c, nym = o + (c - 1 - hx), nyp = o + (c + hx), nzm = o + (c - 1 - hxy),
+                nzp = o + (c + hxy);
+            } else {
+                own = p + P0 + 2 * lane;
+                qo = q + P0 + 2 * lane;
+                nxm = own - 1, nxp = own + 1, nym = own - nx, nyp = own + nx, nzm = own - nxy, nzp = own + nxy;
+            }
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                if (32 * v < left) {
+                    const int off = 32 * ST * v;
+                    const float pc = __ldg(own + off);
+                    float t = cmx[64 * v] * __ldg(nxm + off);
+                    t = fmaf(cpx[64 * v], __ldg(nxp + off), t);
+                    t = fmaf(cmy, __ldg(nym + off), t);
+                    t = fmaf(cpy, __ldg(nyp + off), t);
+                    t = fmaf(cmz, __ldg(nzm + off), t);
+                    t = fmaf(cpz, __ldg(nzp + off), t);
+                    const float val = fmaf(-(dgx[64 * v] + dgy + dgz), pc, t);
+                    acc = fmaf(vx[64 * v] * vy * vz * pc, val, acc);
+                    qo[off] = val;
+                }
+            }
+        }
+    }
+    reduce_finish(block_sum_f32(acc, sm), red, sm);
+}
+
+template <int LS, int V>
+__global__ void __launch_bounds__(256) k_apply_dot32_rows(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q, Red red, int pf)
+{
+    k_apply_dot32_rows_body<LS, V>(L, p, q, red, pf);
 }
 
 template <int LS>
@@ -1237,22 +1402,45 @@ __device__ __forceinline__ void k_update_er32_body(LevelT<float> L, const Ctl* _
     __shared__ double sm[32];
     const float alpha = (float)ctl->alpha_in;
     float acc = 0.0f;
-    GRID_STRIDE(P, L.N())
+    const size_t N = L.N();
+    GRID_STRIDE_U(P0, N)
     {
-        int i, j, k;
-        node_ijk(P, L, i, j, k);
-        if (is_face(L, i, j, k)) continue;
-        const unsigned Q = pos<LS>(L, P);
-        e[Q] = fmaf(alpha, p[Q], e[Q]);
-        const float rv = fmaf(-alpha, q[Q], r[Q]);
-        r[Q] = rv;
-        acc = fmaf(rv, rv, acc);
+        float pv[VU], qv[VU], ev[VU], rv[VU];
+        unsigned Q[VU];
+        bool on[VU];
+#pragma unroll
+        for (int u = 0; u < VU; u++) {
+            const size_t P = P0 + (size_t)u * NT;
+            on[u] = false;
+            Q[u] = 0u;
+            pv[u] = qv[u] = ev[u] = rv[u] = 0.0f;
+            if (P < N) {
+                int i, j, k;
+                node_ijk(P, L, i, j, k);
+                on[u] = !is_face(L, i, j, k);
+                if (on[u]) {
+                    Q[u] = pos<LS>(L, P);
+                    pv[u] = p[Q[u]];
+                    qv[u] = q[Q[u]];
+                    ev[u] = e[Q[u]];
+                    rv[u] = r[Q[u]];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < VU; u++) {
+            if (!on[u]) continue;
+            e[Q[u]] = fmaf(alpha, pv[u], ev[u]);
+            const float rn = fmaf(-alpha, qv[u], rv[u]);
+            r[Q[u]] = rn;
+            acc = fmaf(rn, rn, acc);
+        }
     }
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
 
 template <int LS>
-__global__ void __launch_bounds__(NT) k_update_er32(LevelT<float> L, const Ctl* __restrict__ ctl, const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ e, float* __restrict__ r, Red red)
+__global__ void __launch_bounds__(NT, VEC_MIN_BLOCKS) k_update_er32(LevelT<float> L, const Ctl* __restrict__ ctl, const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ e, float* __restrict__ r, Red red)
 {
     k_update_er32_body<LS>(L, ctl, p, q, e, r, red);
 }
@@ -1263,32 +1451,74 @@ __device__ __forceinline__ void k_dot32_body(LevelT<float> L, const float* __res
 {
     __shared__ double sm[32];
     float acc = 0.0f;
-    GRID_STRIDE(P, L.N())
+    const size_t N = L.N();
+    GRID_STRIDE_U(P0, N)
     {
-        int i, j, k;
-        node_ijk(P, L, i, j, k);
-        if (is_face(L, i, j, k)) continue;
-        const unsigned Q = pos<LS>(L, P);
-        acc = z ? fmaf(vol32(L, i, j, k) * r[Q], z[Q], acc) : fmaf(r[Q], r[Q], acc);
+        float rv[VU], zv[VU], w[VU];
+        bool on[VU];
+#pragma unroll
+        for (int u = 0; u < VU; u++) {
+            const size_t P = P0 + (size_t)u * NT;
+            on[u] = false;
+            rv[u] = zv[u] = w[u] = 0.0f;
+            if (P < N) {
+                int i, j, k;
+                node_ijk(P, L, i, j, k);
+                on[u] = !is_face(L, i, j, k);
+                if (on[u]) {
+                    const unsigned Q = pos<LS>(L, P);
+                    rv[u] = r[Q];
+                    if (z) {
+                        zv[u] = z[Q];
+                        w[u] = vol32(L, i, j, k);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < VU; u++)
+            if (on[u]) acc = z ? fmaf(w[u] * rv[u], zv[u], acc) : fmaf(rv[u], rv[u], acc);
     }
     reduce_finish(block_sum_f32(acc, sm), red, sm);
 }
 
 template <int LS>
-__global__ void __launch_bounds__(NT) k_dot32(LevelT<float> L, const float* __restrict__ r, const float* __restrict__ z, Red red)
+__global__ void __launch_bounds__(NT, VEC_MIN_BLOCKS) k_dot32(LevelT<float> L, const float* __restrict__ r, const float* __restrict__ z, Red red)
 {
     k_dot32_body<LS>(L, r, z, red);
 }
 
+// p = z + beta p (VU nodes per thread, a block's width apart)
 template <int LS>
 __device__ __forceinline__ void k_update_p32_body(LevelT<float> L, const Ctl* __restrict__ ctl, const float* __restrict__ z, float* __restrict__ p)
 {
-    const size_t P = blockIdx.x * (size_t)NT + threadIdx.x;
-    if (P >= L.N()) return;
-    int i, j, k;
-    node_ijk(P, L, i, j, k);
-    const unsigned Q = pos<LS>(L, P);
-    p[Q] = is_face(L, i, j, k) ? 0.0f : fmaf((float)ctl->beta_in, p[Q], z[Q]);
+    const size_t N = L.N();
+    const size_t P0 = blockIdx.x * (size_t)(NT * VU) + threadIdx.x;
+    const float beta = (float)ctl->beta_in;
+    float zv[VU], pv[VU];
+    unsigned Q[VU];
+    bool in[VU], face[VU];
+#pragma unroll
+    for (int u = 0; u < VU; u++) {
+        const size_t P = P0 + (size_t)u * NT;
+        in[u] = P < N;
+        face[u] = true;
+        Q[u] = 0u;
+        zv[u] = pv[u] = 0.0f;
+        if (in[u]) {
+            int i, j, k;
+            node_ijk(P, L, i, j, k);
+            Q[u] = pos<LS>(L, P);
+            face[u] = is_face(L, i, j, k);
+            if (!face[u]) {
+                zv[u] = z[Q[u]];
+                pv[u] = p[Q[u]];
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < VU; u++)
+        if (in[u]) p[Q[u]] = face[u] ? 0.0f : fmaf(beta, pv[u], zv[u]);
 }
 
 template <int LS>
@@ -1354,37 +1584,95 @@ cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const doubl
     k_update_p<<<GRID(L)>>>(L, ctl, z, p);
     return cudaGetLastError();
 }
+// the row-per-warp form: grid and prefetch distance (half the rows the device holds resident;
+// none on levels too small for the prefetched lines to stay inside the arrays)
+static unsigned apply_rows_grid(const LevelT<float>& L)
+{
+    const size_t rows = (size_t)(L.ny - 2) * (L.nz - 2);
+    return (unsigned)std::min((rows + 7) / 8, (L.N() + 255) / 256);
+}
+
+template <int LS, int V, typename K>
+static cudaError_t apply_rows_pf(const LevelT<float>& L, K kernel, int* pf)
+{
+    static int pf_rows[64] = {0};
+    *pf = 0;
+    if (L.nx < 64 || L.ny < 8) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (pf_rows[dev] == 0) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        pf_rows[dev] = std::max(1, per_sm * sms * 8 / 2);
+    }
+    *pf = pf_rows[dev];
+    return cudaSuccess;
+}
+
+template <int LS, int V>
+static cudaError_t launch_apply_dot32_rows(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s)
+{
+    int pf = 0;
+    const cudaError_t e = apply_rows_pf<LS, V>(L, k_apply_dot32_rows<LS, V>, &pf);
+    if (e != cudaSuccess) return e;
+    k_apply_dot32_rows<LS, V><<<apply_rows_grid(L), 256, 0, s>>>(L, p, q, red, pf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s)
 {
+    if (L.ny >= 3 && L.nz >= 3) {
+#define LASTO_APPLY_ROWS(VV)                                                                       \
+    case VV:                                                                                       \
+        return L.lsh ? launch_apply_dot32_rows<1, VV>(L, p, q, red, s) : launch_apply_dot32_rows<0, VV>(L, p, q, red, s);
+        switch (split_rows_v(L.nx)) {
+            LASTO_APPLY_ROWS(1)
+            LASTO_APPLY_ROWS(2)
+            LASTO_APPLY_ROWS(3)
+            LASTO_APPLY_ROWS(4)
+            LASTO_APPLY_ROWS(5)
+            LASTO_APPLY_ROWS(6)
+            LASTO_APPLY_ROWS(7)
+            LASTO_APPLY_ROWS(8)
+            default: break;
+        }
+#undef LASTO_APPLY_ROWS
+    }
+    // rows of more than 513 nodes
     if (L.lsh)
-        k_apply_dot32<1><<<RGRID(L)>>>(L, p, q, red);
+        k_apply_dot32<1><<<vec_grid(L.N()), NT, 0, s>>>(L, p, q, red);
     else
-        k_apply_dot32<0><<<RGRID(L)>>>(L, p, q, red);
+        k_apply_dot32<0><<<vec_grid(L.N()), NT, 0, s>>>(L, p, q, red);
     return cudaGetLastError();
 }
 cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
                                float* r, const Red& red, cudaStream_t s)
 {
     if (L.lsh)
-        k_update_er32<1><<<RGRID(L)>>>(L, ctl, p, q, e, r, red);
+        k_update_er32<1><<<vec_grid(L.N()), NT, 0, s>>>(L, ctl, p, q, e, r, red);
     else
-        k_update_er32<0><<<RGRID(L)>>>(L, ctl, p, q, e, r, red);
+        k_update_er32<0><<<vec_grid(L.N()), NT, 0, s>>>(L, ctl, p, q, e, r, red);
     return cudaGetLastError();
 }
 cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, const Red& red, cudaStream_t s)
 {
     if (L.lsh)
-        k_dot32<1><<<RGRID(L)>>>(L, r, z, red);
+        k_dot32<1><<<vec_grid(L.N()), NT, 0, s>>>(L, r, z, red);
     else
-        k_dot32<0><<<RGRID(L)>>>(L, r, z, red);
+        k_dot32<0><<<vec_grid(L.N()), NT, 0, s>>>(L, r, z, red);
     return cudaGetLastError();
 }
 cudaError_t launch_update_p32(const LevelT<float>& L, const Ctl* ctl, const float* z, float* p, cudaStream_t s)
 {
+    const unsigned g = (unsigned)((L.N() + NT * VU - 1) / (NT * VU));
     if (L.lsh)
-        k_update_p32<1><<<GRID(L)>>>(L, ctl, z, p);
+        k_update_p32<1><<<g, NT, 0, s>>>(L, ctl, z, p);
     else
-        k_update_p32<0><<<GRID(L)>>>(L, ctl, z, p);
+        k_update_p32<0><<<g, NT, 0, s>>>(L, ctl, z, p);
     return cudaGetLastError();
 }
 cudaError_t launch_add_correction(size_t N, double* u, float* e, unsigned h32, cudaStream_t s)
@@ -1478,7 +1766,7 @@ __global__ void __launch_bounds__(NT) k_zero_bat(const __grid_constant__ BatPack
 }
 
 template <int LS>
-__global__ void __launch_bounds__(NT) k_dot32_bat(const __grid_constant__ BatPack<BatVec> pk, int with_z, int op, int mode)
+__global__ void __launch_bounds__(NT, VEC_MIN_BLOCKS) k_dot32_bat(const __grid_constant__ BatPack<BatVec> pk, int with_z, int op, int mode)
 {
     const BatVec& a = pk.m[blockIdx.y];
     if (!bat_on(a.ctl, mode)) return;
@@ -1495,7 +1783,7 @@ __global__ void __launch_bounds__(NT) k_update_p32_bat(const __grid_constant__ B
 }
 
 template <int LS>
-__global__ void __launch_bounds__(NT) k_apply_dot32_bat(const __grid_constant__ BatPack<BatVec> pk)
+__global__ void __launch_bounds__(NT, VEC_MIN_BLOCKS) k_apply_dot32_bat(const __grid_constant__ BatPack<BatVec> pk)
 {
     const BatVec& a = pk.m[blockIdx.y];
     if (!bat_on(a.ctl, BAT_INNER)) return;
@@ -1503,8 +1791,17 @@ __global__ void __launch_bounds__(NT) k_apply_dot32_bat(const __grid_constant__ 
     k_apply_dot32_body<LS>(a.V32, a.p32, a.q32, red);
 }
 
+template <int LS, int V>
+__global__ void __launch_bounds__(256) k_apply_dot32_rows_bat(const __grid_constant__ BatPack<BatVec> pk, int pf)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    const Red red{a.part, a.counter, a.ctl, FIN_IN_ALPHA, 0, 0};
+    k_apply_dot32_rows_body<LS, V>(a.V32, a.p32, a.q32, red, pf);
+}
+
 template <int LS>
-__global__ void __launch_bounds__(NT) k_update_er32_bat(const __grid_constant__ BatPack<BatVec> pk)
+__global__ void __launch_bounds__(NT, VEC_MIN_BLOCKS) k_update_er32_bat(const __grid_constant__ BatPack<BatVec> pk)
 {
     const BatVec& a = pk.m[blockIdx.y];
     if (!bat_on(a.ctl, BAT_INNER)) return;
@@ -1615,7 +1912,7 @@ cudaError_t launch_zero_bat(const BatPack<BatVec>& m, int nm, size_t n, int whic
 cudaError_t launch_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, int with_z, int op, int mode,
                              cudaStream_t s)
 {
-    const dim3 g(red_grid(V0.N()), (unsigned)nm);
+    const dim3 g(vec_grid(V0.N()), (unsigned)nm);
     if (V0.lsh)
         k_dot32_bat<1><<<g, NT, 0, s>>>(m, with_z, op, mode);
     else
@@ -1625,7 +1922,7 @@ cudaError_t launch_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, 
 
 cudaError_t launch_update_p32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
 {
-    const dim3 g((unsigned)((V0.N() + NT - 1) / NT), (unsigned)nm);
+    const dim3 g((unsigned)((V0.N() + NT * VU - 1) / (NT * VU)), (unsigned)nm);
     if (V0.lsh)
         k_update_p32_bat<1><<<g, NT, 0, s>>>(m);
     else
@@ -1633,9 +1930,37 @@ cudaError_t launch_update_p32_bat(const LevelT<float>& V0, const BatPack<BatVec>
     return cudaGetLastError();
 }
 
+template <int LS, int V>
+static cudaError_t launch_apply_dot32_rows_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
+{
+    int pf = 0;
+    const cudaError_t e = apply_rows_pf<LS, V>(V0, k_apply_dot32_rows<LS, V>, &pf);
+    if (e != cudaSuccess) return e;
+    k_apply_dot32_rows_bat<LS, V><<<dim3(apply_rows_grid(V0), (unsigned)nm), 256, 0, s>>>(m, pf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
 {
-    const dim3 g(red_grid(V0.N()), (unsigned)nm);
+    if (nm < 1 || nm > BAT_MAX) return cudaErrorInvalidValue;
+    if (V0.ny >= 3 && V0.nz >= 3) {
+#define LASTO_APPLY_ROWS(VV)                                                                          \
+    case VV:                                                                                          \
+        return V0.lsh ? launch_apply_dot32_rows_bat<1, VV>(V0, m, nm, s) : launch_apply_dot32_rows_bat<0, VV>(V0, m, nm, s);
+        switch (split_rows_v(V0.nx)) {
+            LASTO_APPLY_ROWS(1)
+            LASTO_APPLY_ROWS(2)
+            LASTO_APPLY_ROWS(3)
+            LASTO_APPLY_ROWS(4)
+            LASTO_APPLY_ROWS(5)
+            LASTO_APPLY_ROWS(6)
+            LASTO_APPLY_ROWS(7)
+            LASTO_APPLY_ROWS(8)
+            default: break;
+        }
+#undef LASTO_APPLY_ROWS
+    }
+    const dim3 g(vec_grid(V0.N()), (unsigned)nm);
     if (V0.lsh)
         k_apply_dot32_bat<1><<<g, NT, 0, s>>>(m);
     else
@@ -1645,7 +1970,7 @@ cudaError_t launch_apply_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec
 
 cudaError_t launch_update_er32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
 {
-    const dim3 g(red_grid(V0.N()), (unsigned)nm);
+    const dim3 g(vec_grid(V0.N()), (unsigned)nm);
     if (V0.lsh)
         k_update_er32_bat<1><<<g, NT, 0, s>>>(m);
     else
@@ -1679,7 +2004,7 @@ void init_bat_attributes()
     template cudaError_t launch_resid_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, const T*, T*, T*, \
                                                   bool, cudaStream_t);                                       \
     template cudaError_t launch_bottom<T>(const BottomArgs<T>&, cudaStream_t);                              \
-    template cudaError_t launch_rbgs<T>(const LevelT<T>&, T*, const T*, int, cudaStream_t, int);               \
+    template cudaError_t launch_rbgs<T>(const LevelT<T>&, T*, const T*, int, cudaStream_t, int, int*);               \
     template cudaError_t launch_residual<T>(const LevelT<T>&, const T*, const T*, T*, cudaStream_t);        \
     template cudaError_t launch_apply<T>(const LevelT<T>&, const T*, T*, cudaStream_t);                     \
     template cudaError_t launch_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, T*, cudaStream_t); \

@@ -1,0 +1,337 @@
+// The FP32 red-black half sweep over colour-split storage with its operands staged in shared
+// memory by bulk copies (Section 3's smoother, the same node update as k_rbgs_split_rows).
+//
+// In colour-split storage the rows of one colour are consecutive, so the nodes a tile of R
+// interior rows of plane k reads from the other colour -- its own rows and the rows j0 - 1 and
+// j0 + R of planes k - 1, k, k + 1 -- are one contiguous run per plane, and the tile's own
+// right-hand side is another.  A block owns R rows (one warp each) and a chunk of planes,
+// marches through the chunk in z and keeps the other colour's planes k - 1, k, k + 1 in a ring
+// of SG_NS slots with the next plane in flight (cp.async.bulk, completion counted on an
+// mbarrier), the right-hand side in SG_NB slots.  Each plane of the other colour is read from
+// DRAM once per (tile, chunk), and every warp's loads are shared-memory loads whose operands
+// arrived a plane earlier: the row-per-warp kernel's loads wait on L2 and DRAM one row at a
+// time.  Results go straight to global memory (the colour being written is not read in this
+// half sweep).
+//
+// Waits are bounded: a wait that runs out (about two seconds) raises LASTO_ERR_TIMEOUT in
+// *status (when given), the block waits -- again bounded -- for the copies it has in flight and
+// leaves.
+#include "internal.cuh"
+
+namespace lasto {
+
+namespace {
+
+constexpr int SG_R = 8;              // interior rows per tile, one warp each
+constexpr int SG_NT = 32 * SG_R;
+constexpr int SG_NS = 4;             // other-colour plane slots: k - 1, k, k + 1, one in flight
+constexpr int SG_NB = 2;             // right-hand-side plane slots: k, one in flight
+constexpr unsigned long long SG_WAIT_NS = 2000000000ull;
+
+struct StageGeom {
+    int tiles_j;      // ceil((ny - 2) / SG_R)
+    int chunk;        // planes per block
+    unsigned oslot;   // floats per other-colour slot (a multiple of 4)
+    unsigned bslot;   // floats per right-hand-side slot
+    int hx1;          // (nx - 1) / 2 rounded up to a multiple of 4: x coefficients per parity
+};
+
+__device__ __forceinline__ uint32_t sg_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sg_now()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// true once the phase of the given parity has completed; false after SG_WAIT_NS
+__device__ __forceinline__ bool sg_wait(uint32_t bar, uint32_t parity)
+{
+    uint64_t t0 = 0;
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        const uint64_t t = sg_now();
+        if (t0 == 0)
+            t0 = t;
+        else if (t - t0 > SG_WAIT_NS)
+            return false;
+    }
+}
+
+// [start, start + len) in floats from the array base: both ends multiples of 4 (16 bytes), the
+// end clipped to the last whole 16 bytes of the N-node array (the up to 3 nodes past it are the
+// last nodes of the face plane's last row, which no interior update reads)
+__device__ __forceinline__ void sg_range(unsigned a, unsigned e, unsigned N, unsigned& start, unsigned& len)
+{
+    start = a & ~3u;
+    e = min((e + 3u) & ~3u, N & ~3u);
+    len = e > start ? e - start : 0u;
+}
+
+// the other colour's run of plane p: rows j0 - 1 .. j0 + nr (the tile's rows and one on each side)
+__device__ __forceinline__ void sg_orange(const LevelT<float>& L, int c, int p, int j0, int nr, unsigned& start,
+                                          unsigned& len)
+{
+    const unsigned nxy = (unsigned)L.nx * (unsigned)L.ny;
+    const unsigned lo = (unsigned)p * nxy + (unsigned)(j0 - 1) * (unsigned)L.nx;
+    const unsigned hi = (unsigned)p * nxy + (unsigned)(j0 + nr + 1) * (unsigned)L.nx - 1u;
+    const unsigned h0 = (unsigned)(1 - c) * L.H;
+    sg_range(h0 + (lo >> 1), h0 + (hi >> 1) + 1u, (unsigned)L.N(), start, len);
+}
+
+// the colour's own run of plane p (right-hand side): rows j0 .. j0 + nr - 1
+__device__ __forceinline__ void sg_brange(const LevelT<float>& L, int c, int p, int j0, int nr, unsigned& start,
+                                          unsigned& len)
+{
+    const unsigned nxy = (unsigned)L.nx * (unsigned)L.ny;
+    const unsigned lo = (unsigned)p * nxy + (unsigned)j0 * (unsigned)L.nx;
+    const unsigned hi = (unsigned)p * nxy + (unsigned)(j0 + nr) * (unsigned)L.nx - 1u;
+    const unsigned h0 = (unsigned)c * L.H;
+    sg_range(h0 + (lo >> 1), h0 + (hi >> 1) + 1u, (unsigned)L.N(), start, len);
+}
+
+// one bulk copy of len floats from src + start into the slot, counted on bar
+__device__ __forceinline__ void sg_issue(const float* src, unsigned start, unsigned len, float* slot, uint32_t bar)
+{
+    // the slot's previous contents were read through the generic proxy (ordered before this by
+    // the block barrier); the copy writes through the async proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(len * 4u) : "memory");
+    if (len)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                sg_smem(slot)),
+            "l"(src + start), "r"(len * 4u), "r"(bar)
+            : "memory");
+}
+
+template <int V>
+__global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, float* __restrict__ u, const float* __restrict__ b,
+                                                            int colour, StageGeom g, int* __restrict__ status)
+{
+    extern __shared__ __align__(16) float sg[];
+    __shared__ __align__(8) uint64_t bar_o[SG_NS];
+    __shared__ __align__(8) uint64_t bar_b[SG_NB];
+    __shared__ unsigned ost[SG_NS], bst[SG_NB];   // global start of each slot's run (thread 0 writes it
+                                                  // before the copy's arrive; readers wait on the copy)
+    float* so = sg;                          // [SG_NS][oslot]
+    float* sb = sg + SG_NS * g.oslot;        // [SG_NB][bslot]
+    float* sx = sb + SG_NB * g.bslot;        // x coefficients [2 parities][cm, cp, dg][g.hx1]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tj = (int)(blockIdx.x % (unsigned)g.tiles_j), kc = (int)(blockIdx.x / (unsigned)g.tiles_j);
+    const int j0 = 1 + tj * SG_R;
+    const int nr = min(SG_R, L.ny - 1 - j0);           // the tile's interior rows
+    const int kA = 1 + kc * g.chunk, kB = min(L.nz - 2, kA + g.chunk - 1);
+    if (nr <= 0 || kA > kB) return;
+    const int c = colour;
+    const int nx = L.nx;
+    const unsigned nxy = (unsigned)nx * (unsigned)L.ny;
+    const int hx = (nx - 1) >> 1, hxy = (int)((nxy - 1) >> 1);
+    const int dxm = c - 1, dxp = c, dym = c - 1 - hx, dyp = c + hx, dzm = c - 1 - hxy, dzp = c + hxy;
+    const int oLast = kB + 1, o0 = kA - 1;           // other-colour planes o0 .. oLast, in order
+    // planes issued so far (thread 0's counts; the waits derive slot and parity from the plane)
+    int o_next = o0, b_next = kA;
+    if (tid == 0) {
+        for (int q = 0; q < SG_NS; q++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sg_smem(&bar_o[q])) : "memory");
+        for (int q = 0; q < SG_NB; q++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sg_smem(&bar_b[q])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    // the x coefficients of the colour's interior nodes by parity of the first one (i1 = 1, 2):
+    // node s of a run is i1 + 2 s; one copy per block, read conflict-free by consecutive lanes
+    for (int t = tid; t < 2 * g.hx1; t += SG_NT) {
+        const int par = t / g.hx1, sx_i = t - par * g.hx1;
+        const int i = 1 + par + 2 * sx_i;
+        const bool in = i < nx - 1;
+        sx[(par * 3 + 0) * g.hx1 + sx_i] = in ? L.ax[0].cm[i] : 0.0f;
+        sx[(par * 3 + 1) * g.hx1 + sx_i] = in ? L.ax[0].cp[i] : 0.0f;
+        sx[(par * 3 + 2) * g.hx1 + sx_i] = in ? L.ax[0].dg[i] : 0.0f;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (; o_next <= oLast && o_next < o0 + SG_NS; o_next++) {
+            unsigned st, ln;
+            sg_orange(L, c, o_next, j0, nr, st, ln);
+            const int q = (o_next - o0) % SG_NS;
+            ost[q] = st;
+            sg_issue(u, st, ln, so + q * g.oslot, sg_smem(&bar_o[q]));
+        }
+        for (; b_next <= kB && b_next < kA + SG_NB; b_next++) {
+            unsigned st, ln;
+            sg_brange(L, c, b_next, j0, nr, st, ln);
+            const int q = (b_next - kA) % SG_NB;
+            bst[q] = st;
+            sg_issue(b, st, ln, sb + q * g.bslot, sg_smem(&bar_b[q]));
+        }
+    }
+    // the warp's row and its x coefficients (row-independent but for the colour's first node)
+    const int j = j0 + warp;
+    const bool has_row = warp < nr;
+    const float cmy = has_row ? L.ax[1].cm[j] : 0.0f, cpy = has_row ? L.ax[1].cp[j] : 0.0f;
+    const float dgy = has_row ? L.ax[1].dg[j] : 0.0f;
+    bool failed = false;
+    for (int k = kA; k <= kB; k++) {
+        bool bad = false;
+        {
+            const int p[3] = {k - 1, k, k + 1};
+#pragma unroll
+            for (int t = 0; t < 3; t++) {
+                const int d = p[t] - o0;
+                if (!bad && !sg_wait(sg_smem(&bar_o[d % SG_NS]), (uint32_t)((d / SG_NS) & 1))) bad = true;
+            }
+            const int d = k - kA;
+            if (!bad && !sg_wait(sg_smem(&bar_b[d % SG_NB]), (uint32_t)((d / SG_NB) & 1))) bad = true;
+        }
+        if (!bad && has_row) {
+            const int i1 = ((c + j + k) & 1) ? 1 : 2;      // first interior node of the colour
+            const int left = ((nx - i1) >> 1) - lane;
+            const unsigned q0 = ((unsigned)k * nxy + (unsigned)j * (unsigned)nx + (unsigned)i1) >> 1;
+            const unsigned go = (unsigned)(1 - c) * L.H + q0 + (unsigned)lane;   // lane's node, other colour
+            const float* ok = so + ((k - o0) % SG_NS) * g.oslot + (go - ost[(k - o0) % SG_NS]);
+            const float* om = so + ((k - 1 - o0) % SG_NS) * g.oslot + (go - ost[(k - 1 - o0) % SG_NS]);
+            const float* op = so + ((k + 1 - o0) % SG_NS) * g.oslot + (go - ost[(k + 1 - o0) % SG_NS]);
+            const float* bo = sb + ((k - kA) % SG_NB) * g.bslot + ((unsigned)c * L.H + q0 + (unsigned)lane - bst[(k - kA) % SG_NB]);
+            float* uo = u + (size_t)c * L.H + q0 + lane;
+            const float cmz = L.ax[2].cm[k], cpz = L.ax[2].cp[k], dgz = L.ax[2].dg[k];
+            const float* cmx = sx + (i1 - 1) * 3 * g.hx1 + lane;
+            const float* cpx = cmx + g.hx1;
+            const float* dgx = cpx + g.hx1;
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                if (32 * v < left) {
+                    float t = cmx[32 * v] * ok[dxm + 32 * v];
+                    t = fmaf(cpx[32 * v], ok[dxp + 32 * v], t);
+                    t = fmaf(cmy, ok[dym + 32 * v], t);
+                    t = fmaf(cpy, ok[dyp + 32 * v], t);
+                    t = fmaf(cmz, om[dzm + 32 * v], t);
+                    t = fmaf(cpz, op[dzp + 32 * v], t);
+                    const float acc = bo[32 * v] - t;
+                    uo[32 * v] = rb_point32(acc, dgx[32 * v] + dgy + dgz);
+                }
+            }
+        }
+        // every warp is done with plane k - 1 and right-hand side k before their slots refill
+        if (__syncthreads_or(bad ? 1 : 0)) {
+            failed = true;
+            break;
+        }
+        if (tid == 0) {
+            if (o_next <= oLast) {   // into plane k - 1's slot
+                unsigned st, ln;
+                sg_orange(L, c, o_next, j0, nr, st, ln);
+                const int q = (o_next - o0) % SG_NS;
+                ost[q] = st;
+                sg_issue(u, st, ln, so + q * g.oslot, sg_smem(&bar_o[q]));
+                o_next++;
+            }
+            if (b_next <= kB) {      // into right-hand side k's slot
+                unsigned st, ln;
+                sg_brange(L, c, b_next, j0, nr, st, ln);
+                const int q = (b_next - kA) % SG_NB;
+                bst[q] = st;
+                sg_issue(b, st, ln, sb + q * g.bslot, sg_smem(&bar_b[q]));
+                b_next++;
+            }
+        }
+    }
+    if (tid == 0) {
+        // copies issued and not yet waited for land before the block leaves (on the normal path
+        // every issued plane has been waited for; after a timeout these waits are bounded too)
+        if (failed) {
+            for (int p = max(o0, o_next - SG_NS); p < o_next; p++) sg_wait(sg_smem(&bar_o[(p - o0) % SG_NS]), (uint32_t)(((p - o0) / SG_NS) & 1));
+            for (int p = max(kA, b_next - SG_NB); p < b_next; p++) sg_wait(sg_smem(&bar_b[(p - kA) % SG_NB]), (uint32_t)(((p - kA) / SG_NB) & 1));
+            if (status) atomicMax(status, (int)LASTO_ERR_TIMEOUT);
+        }
+    }
+}
+
+template <int V>
+size_t stage_smem(const StageGeom& g)
+{
+    return sizeof(float) * ((size_t)SG_NS * g.oslot + (size_t)SG_NB * g.bslot + 6 * (size_t)g.hx1);
+}
+
+constexpr size_t SG_SMEM_MAX = 200 * 1024;
+
+template <int V>
+cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s)
+{
+    StageGeom g;
+    g.tiles_j = (L.ny - 2 + SG_R - 1) / SG_R;
+    g.oslot = ((unsigned)(((SG_R + 2) * L.nx + 1) / 2) + 8u + 3u) & ~3u;
+    g.bslot = ((unsigned)((SG_R * L.nx + 1) / 2) + 8u + 3u) & ~3u;
+    g.hx1 = ((L.nx - 1) / 2 + 3) & ~3;
+    const size_t smem = stage_smem<V>(g);
+    if (smem > SG_SMEM_MAX) return cudaErrorInvalidValue;
+    // one wave: as many plane chunks per tile column as the resident blocks allow
+    static int per_sm_cache[64][2] = {{0, 0}};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    int per_sm = 0, sms = 0;
+    if (per_sm_cache[dev][1] == (int)smem) {
+        per_sm = per_sm_cache[dev][0];
+    } else {
+        // (the shared-memory opt-in is per device; first launches happen outside graph capture,
+        // in the smoother tuner or a direct call)
+        e = cudaFuncSetAttribute(k_rbgs_split_stage<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_split_stage<V>, SG_NT, smem);
+        if (e != cudaSuccess) return e;
+        per_sm_cache[dev][0] = per_sm;
+        per_sm_cache[dev][1] = (int)smem;
+    }
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int planes = L.nz - 2;
+    const int chunks0 = std::max(1, std::min(planes, std::max(1, per_sm) * sms / g.tiles_j));
+    g.chunk = (planes + chunks0 - 1) / chunks0;
+    const int chunks = (planes + g.chunk - 1) / g.chunk;
+    k_rbgs_split_stage<V><<<(unsigned)(g.tiles_j * chunks), SG_NT, smem, s>>>(L, u, b, colour, g, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// the grids the staged kernel takes: at least 9 nodes per axis, rows of at most 513 nodes
+bool split_stage_ok(int nx, int ny, int nz) { return nx >= 9 && ny >= 9 && nz >= 9 && nx <= 513; }
+
+// Colour-split FP32 half sweep with staged planes: a grid split_stage_ok accepts, u and b
+// 16-byte aligned (else cudaErrorInvalidValue).
+cudaError_t launch_split_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s)
+{
+    if (!L.lsh || !split_stage_ok(L.nx, L.ny, L.nz)) return cudaErrorInvalidValue;
+    if (((uintptr_t)u & 15u) || ((uintptr_t)b & 15u)) return cudaErrorInvalidValue;
+    switch ((L.nx - 1) / 2 <= 256 ? ((L.nx - 1) / 2 + 31) / 32 : 0) {
+        case 1: return launch_stage_v<1>(L, u, b, colour, status, s);
+        case 2: return launch_stage_v<2>(L, u, b, colour, status, s);
+        case 3: return launch_stage_v<3>(L, u, b, colour, status, s);
+        case 4: return launch_stage_v<4>(L, u, b, colour, status, s);
+        case 5: return launch_stage_v<5>(L, u, b, colour, status, s);
+        case 6: return launch_stage_v<6>(L, u, b, colour, status, s);
+        case 7: return launch_stage_v<7>(L, u, b, colour, status, s);
+        case 8: return launch_stage_v<8>(L, u, b, colour, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+void init_stage_attributes()
+{
+    cudaFuncSetAttribute(k_rbgs_split_stage<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+    cudaFuncSetAttribute(k_rbgs_split_stage<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+    cudaFuncSetAttribute(k_rbgs_split_stage<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+    cudaFuncSetAttribute(k_rbgs_split_stage<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+    cudaFuncSetAttribute(k_rbgs_split_stage<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+    cudaFuncSetAttribute(k_rbgs_split_stage<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+    cudaFuncSetAttribute(k_rbgs_split_stage<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+    cudaFuncSetAttribute(k_rbgs_split_stage<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+}
+
+}  // namespace lasto

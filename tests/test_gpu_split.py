@@ -23,15 +23,22 @@ def _grid(n, seed):
             graded_axis(n[2], 7.0, 4.0, seed + 2, 0.1))
 
 
-@pytest.mark.parametrize("n", [(5, 3, 7), (33, 33, 33), (71, 37, 13), (129, 129, 129), (97, 5, 9)])
-@pytest.mark.parametrize("threads", [128, 256, 512, 0])
+@pytest.mark.parametrize("n", [(5, 3, 7), (33, 33, 33), (71, 37, 13), (129, 129, 129), (97, 5, 9), (9, 9, 9),
+                               (35, 17, 21), (97, 99, 9), (513, 11, 9)])
+@pytest.mark.parametrize("threads", [128, 256, 512, 0, 1])
 def test_split_sweeps_equal_natural_sweeps(n, threads):
+    """threads = 1 is the plane-staged kernel: tiles of 8 rows (ragged last tile), plane chunks
+    of one plane up to many, rows of 9 to 513 nodes; it takes no axis shorter than 9."""
     import torch
     B = need_gpu()
     x, y, z = _grid(n, 51)
     rng = np.random.default_rng(52)
     u = torch.as_tensor(rng.normal(size=n[::-1]).astype(np.float32)).cuda().reshape(-1)
     b = torch.as_tensor(rng.normal(size=n[::-1]).astype(np.float32)).cuda().reshape(-1)
+    if threads == 0 and n[0] > 1023 or threads == 1 and min(n) < 9:
+        with pytest.raises(RuntimeError, match="INVALID_ARG"):
+            B.lasto_op_smooth_split(dev(x), dev(y), dev(z), B.split_colours(u), B.split_colours(b), threads=threads)
+        return
     for sweeps in (1, 3):
         ref = B.lasto_op_smooth(dev(x), dev(y), dev(z), u.clone(), b, sweeps=sweeps, threads=256)
         us, bs = B.split_colours(u), B.split_colours(b)
@@ -61,6 +68,13 @@ def test_split_op_rejects_bad_input():
     u = torch.zeros(9 ** 3, dtype=torch.float32, device="cuda")
     with pytest.raises(RuntimeError, match="INVALID_ARG"):
         B.lasto_op_smooth_split(x, x, x, u, u.clone(), threads=100)
+    # the staged kernel copies 16-byte runs: arrays that do not start on 16 bytes are refused
+    big = torch.zeros(9 ** 3 + 4, dtype=torch.float32, device="cuda")
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        B.lasto_op_smooth_split(x, x, x, big[1:1 + 9 ** 3], u.clone(), threads=1)
+    with pytest.raises(RuntimeError, match="INVALID_ARG"):
+        B.lasto_op_smooth_split(x, x, x, u, big[2:2 + 9 ** 3], threads=1)
+    B.lasto_op_smooth_split(x, x, x, big[4:4 + 9 ** 3], u.clone(), threads=1)
 
 
 def _solve(B, cls, table, n_max, guess=False):
@@ -81,15 +95,15 @@ def _solve(B, cls, table, n_max, guess=False):
 
 
 def test_solve_over_split_storage_equals_natural_storage(orc):
-    """Pd13 on 65^3 (its 33^3 level below): the finest level forced to each split block size,
-    then natural; the V_LM, iteration counts and residuals agree bit for bit, and match the
-    oracle."""
+    """Pd13 on 65^3 (its 33^3 level below): the finest level forced to each split kernel (flat
+    blocks of 128 and 256, one warp per row, plane-staged), then natural; the V_LM, iteration
+    counts and residuals agree bit for bit, and match the oracle."""
     B = need_gpu()
     cl = synth.pd13_small(n=65)
     rest = "33 33 33 4 0 256 0 0 0 0 0\n"
     v0, st0, _ = _solve(B, [cl], "65 65 65 4 0 256 0 0 0 0 0\n" + rest, 65)
     assert st0[0].status == 0 and st0[0].rel_resid <= 1e-10
-    for nt in (128, 256, 0):
+    for nt in (128, 256, 0, 1):
         v, st, _ = _solve(B, [cl], f"65 65 65 4 3 {nt} 0 0 0 0 0\n" + rest, 65)
         assert st[0].status == 0 and st[0].cycles == st0[0].cycles and st[0].rel_resid == st0[0].rel_resid
         assert np.array_equal(host(v), host(v0)), nt
