@@ -68,6 +68,9 @@ DRAM_BYTES_257_F64 = 537.7e6
 # 385^3 itself (third launch of `bench.py --profile smoother --n 385 --split --threads 0
 # --sweeps 2`, ncu --set full: caches flushed before the launch): 230.9 MB read + 87.2 MB written
 DRAM_BYTES_385_SPLIT_ROWS = 318.1e6
+# the plane-staged half sweep over colour-split storage (k_rbgs_split_stage<6>), captured the same
+# way (`--threads 1`): DRAM_BYTES_385_SPLIT_STAGE, read + written per launch
+DRAM_BYTES_385_SPLIT_STAGE = None
 
 
 def parse():
@@ -668,8 +671,8 @@ def run_profile(args, B):
         seq = synth.pd561_graded385(n_densities=2)
         solver = B.Poisson(n_max=385, max_atoms=561, precision=B.LASTO_PREC_MIXED, launch=1)
         # under a profiler the tuner's timings mean nothing; take the choices it makes without one
-        # (the finest level in colour-split storage, one warp per row; in-place half sweeps below)
-        solver.set_tune_table("385 385 385 4 3 0 0 0 0 0 0\n" +
+        # (the finest level in colour-split storage, plane-staged; in-place half sweeps below)
+        solver.set_tune_table("385 385 385 4 3 1 0 0 0 0 0\n" +
                               "".join(f"{m} {m} {m} 4 0 128 0 0 0 0 0\n" for m in (193, 97, 49, 25)))
         v = torch.empty((561, 25), dtype=torch.float64, device="cuda")
         pot = torch.empty(385 ** 3, dtype=torch.float64, device="cuda")
@@ -956,11 +959,12 @@ def smoother_roofline(B, stream, flush, dev, tuned, probes):
         return statistics.median(ts) / 1e3
 
     shapes = {}
-    for th in (0, 128):   # half sweeps over colour-split storage (the layout's data is irrelevant here)
+    names = {0: "rows", B.SPLIT_STAGED: "staged"}
+    for th in (B.SPLIT_STAGED, 0, 128):   # half sweeps over colour-split storage (its data is irrelevant here)
         t = (timed(lambda: B.lasto_op_smooth_split(*axes, u, b, sweeps=3, threads=th)) -
              timed(lambda: B.lasto_op_smooth_split(*axes, u, b, sweeps=1, threads=th))) / 4
-        shapes[f"split_{th if th else 'rows'}"] = {"us_per_launch": t * 1e6, "bytes_per_launch": 6.0 * n ** 3,
-                                                   "launches_per_sweep": 2, "nt": th}
+        shapes[f"split_{names.get(th, th)}"] = {"us_per_launch": t * 1e6, "bytes_per_launch": 6.0 * n ** 3,
+                                                "launches_per_sweep": 2, "nt": th}
     for th in (0, 128, 256):   # in-place half sweeps: per launch (2 launches per sweep)
         t = (timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=3, threads=th)) -
              timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=1, threads=th))) / 4
@@ -986,15 +990,19 @@ def smoother_roofline(B, stream, flush, dev, tuned, probes):
         if f[:4] == [str(n), str(n), str(n), "4"]:
             fused, nt, tx, ty = int(f[4]), int(f[5]), int(f[6]), int(f[7])
             pick = (f"wave_{tx}x{ty}" if fused == 2 else f"inplace_{nt if nt else 'rows'}" if fused == 0
-                    else f"split_{nt if nt else 'rows'}" if fused == 3 else None)
+                    else f"split_{names.get(nt, nt)}" if fused == 3 else None)
     if pick not in shapes:
         pick = min(shapes, key=lambda k: shapes[k]["us_per_sweep"])
     c = shapes[pick]
     traffic = None
     if pick.startswith("split"):
-        traffic = DRAM_BYTES_385_SPLIT_ROWS if (c["nt"] == 0 and n == 385) else None
+        traffic = (DRAM_BYTES_385_SPLIT_ROWS if c["nt"] == 0 else
+                   DRAM_BYTES_385_SPLIT_STAGE if c["nt"] == B.SPLIT_STAGED else None) if n == 385 else None
         kernel = ("k_rbgs_split_rows<6> (red-black half sweep over colour-split storage, one warp per row, "
                   "385^3 graded)" if c["nt"] == 0 else
+                  "k_rbgs_split_stage<6> (red-black half sweep over colour-split storage, tiles of 8 rows marching "
+                  "through plane chunks, the other colour's planes bulk-copied into shared memory one plane ahead, "
+                  "385^3 graded)" if c["nt"] == B.SPLIT_STAGED else
                   f"k_rbgs<float,split> (red-black half sweep over colour-split storage, {c['nt']} threads per "
                   "block, 385^3 graded)")
     elif pick.startswith("inplace"):

@@ -509,7 +509,9 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
     if (sizeof(T) == 4) {
         // FP32: form the 27 fine residuals inside the restriction (cheaper than a pass)
         // after nu1 >= 1 sweeps that end on the black half sweep the black residuals are zero
-        TRY(launch_resid_restrict<T>(V, VC, cur, b, Arr<T>::b(C), Arr<T>::u(C), nu1 > 0, s));
+        // (over colour-split storage the red residuals may go through the free r array first)
+        TRY(launch_resid_restrict<T>(V, VC, cur, b, Arr<T>::b(C), Arr<T>::u(C), nu1 > 0, s, V.lsh ? r : nullptr,
+                                     P.status));
     } else {
         // FP64: each residual once (FP64 arithmetic, not bandwidth, bounds this chip)
         TRY(launch_residual<T>(V, cur, b, r, s));

@@ -228,6 +228,8 @@ cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaSt
                         int* status = nullptr);
 // stage.cu
 cudaError_t launch_split_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s);
+cudaError_t launch_split_stage_resid(const LevelT<float>& L, const float* u, const float* b, float* r, int* status,
+                                     cudaStream_t s);
 bool split_stage_ok(int nx, int ny, int nz);
 void init_stage_attributes();
 template <typename T>
@@ -242,10 +244,12 @@ template <typename T>
 cudaError_t launch_coarse_apply(const LevelT<T>& L, const CoarseEig* eig, const T* b, T* e, bool add, cudaStream_t s);
 
 // red_only (FP32): the fine iterate's last half sweep was black, so only the red residuals are
-// formed (the black ones are zero)
+// formed (the black ones are zero).  scratch (optional, FP32, a free fine-level array, 16-byte
+// aligned): over colour-split storage on a grid the staged kernels take, the red residuals are
+// formed once into it by the plane-staged kernel and then restricted (status: its bounded waits)
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelT<T>& fine, const LevelT<T>& coarse, const T* u, const T* b, T* bc, T* uc,
-                                  bool red_only, cudaStream_t s);
+                                  bool red_only, cudaStream_t s, T* scratch = nullptr, int* status = nullptr);
 
 // slab.cu: fused red-black smoother.  One pass = ns full sweeps (colour `first`, then the
 // other), u_in -> u_out (distinct arrays; every node of u_out written).  A CTA owns a

@@ -707,14 +707,79 @@ __global__ void __launch_bounds__(256) k_resid_restrict_rows(LevelT<float> F, Le
     k_resid_restrict_rows_body<LS, RED_ONLY>(F, C, u, b, bc, uc);
 }
 
+// The restriction alone from the red residuals rr of a colour-split fine level (the black ones
+// zero), one warp per coarse (J, K) row, lanes along I: the weighted sum of k_resid_restrict_rows
+// <1, 1> over the same residual values in the same order, so the two are bitwise equal.  uc = 0.
+__global__ void __launch_bounds__(256) k_restrict_red_rows(LevelT<float> F, LevelT<float> C, const float* __restrict__ rr,
+                                                           float* __restrict__ bc, float* __restrict__ uc)
+{
+    const int row = (int)(blockIdx.x * 8 + (threadIdx.x >> 5));
+    if (row >= C.ny * C.nz) return;
+    const int lane = threadIdx.x & 31;
+    const int K = row / C.ny, J = row - K * C.ny;
+    const size_t cb = (size_t)row * C.nx;
+    const bool face_row = J == 0 || K == 0 || J == C.ny - 1 || K == C.nz - 1;
+    if (face_row) {
+        for (int I = lane; I < C.nx; I += 32) {
+            uc[cb + I] = 0.0f;
+            bc[cb + I] = 0.0f;
+        }
+        return;
+    }
+    const float* wy = F.ax[1].rw + 3 * J;
+    const float* wz = F.ax[2].rw + 3 * K;
+    const unsigned sy = (unsigned)F.nx, sz = (unsigned)F.nx * (unsigned)F.ny;
+    for (int I0 = 0; I0 < C.nx; I0 += 32) {
+        const int I = I0 + lane;
+        if (I >= C.nx) break;
+        uc[cb + I] = 0.0f;
+        if (I < 1 || I > C.nx - 2) {
+            bc[cb + I] = 0.0f;
+            continue;
+        }
+        const float* wx = F.ax[0].rw + 3 * I;
+        float r0[9], r1[9], r2[9];
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int bb = 0; bb < 3; bb++) {
+                const unsigned P = (unsigned)(2 * K - 1 + c) * sz + (unsigned)(2 * J - 1 + bb) * sy + (unsigned)(2 * I - 1);
+                const int q = 3 * c + bb;
+                r0[q] = r1[q] = r2[q] = 0.0f;
+                if ((c + bb) & 1) {   // (fj + fk) odd: the red nodes of the row are at odd fi
+                    r0[q] = __ldg(rr + (P >> 1));
+                    r2[q] = __ldg(rr + ((P + 2u) >> 1));
+                } else {
+                    r1[q] = __ldg(rr + ((P + 1u) >> 1));
+                }
+            }
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+#pragma unroll
+            for (int bb = 0; bb < 3; bb++) {
+                const int q = 3 * c + bb;
+                acc = fmaf(wz[c] * wy[bb], fmaf(wx[0], r0[q], fmaf(wx[1], r1[q], wx[2] * r2[q])), acc);
+            }
+        bc[cb + I] = acc;
+    }
+}
+
 // (the fine level in either storage order, the coarse one natural; red_only: the fine iterate's
 // last half sweep was black, FP32 only)
 template <typename T>
 cudaError_t launch_resid_restrict(const LevelT<T>& F, const LevelT<T>& C, const T* u, const T* b, T* bc, T* uc,
-                                  bool red_only, cudaStream_t s)
+                                  bool red_only, cudaStream_t s, T* scratch, int* status)
 {
     if (C.lsh) return cudaErrorInvalidValue;
     if constexpr (sizeof(T) == 4) {
+        if (F.lsh && red_only && scratch && split_stage_ok(F.nx, F.ny, F.nz) && !((uintptr_t)scratch & 15u) &&
+            !((uintptr_t)u & 15u) && !((uintptr_t)b & 15u)) {
+            cudaError_t e = launch_split_stage_resid(F, u, b, scratch, status, s);
+            if (e != cudaSuccess) return e;
+            k_restrict_red_rows<<<(unsigned)(((size_t)C.ny * C.nz + 7) / 8), 256, 0, s>>>(F, C, scratch, bc, uc);
+            return cudaGetLastError();
+        }
         const unsigned g = (unsigned)(((size_t)C.ny * C.nz + 7) / 8);
         if (F.lsh && red_only)
             k_resid_restrict_rows<1, 1><<<g, 256, 0, s>>>(F, C, u, b, bc, uc);
@@ -2002,7 +2067,7 @@ void init_bat_attributes()
 // ---------------------------------------------------------------- instantiations
 #define INST(T)                                                                                              \
     template cudaError_t launch_resid_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, const T*, T*, T*, \
-                                                  bool, cudaStream_t);                                       \
+                                                  bool, cudaStream_t, T*, int*);                            \
     template cudaError_t launch_bottom<T>(const BottomArgs<T>&, cudaStream_t);                              \
     template cudaError_t launch_rbgs<T>(const LevelT<T>&, T*, const T*, int, cudaStream_t, int, int*);               \
     template cudaError_t launch_residual<T>(const LevelT<T>&, const T*, const T*, T*, cudaStream_t);        \

@@ -112,9 +112,13 @@ __device__ __forceinline__ void sg_issue(const float* src, unsigned start, unsig
             : "memory");
 }
 
-template <int V>
+// RESID = 0: the half sweep of `colour` in place on u.  RESID = 1: no update; the residuals
+// b - A u of the colour's nodes go to r at the nodes' own storage positions (the restriction
+// after a black half sweep reads those of the red nodes: the black ones are then zero).
+template <int V, int RESID>
 __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, float* __restrict__ u, const float* __restrict__ b,
-                                                            int colour, StageGeom g, int* __restrict__ status)
+                                                            int colour, StageGeom g, int* __restrict__ status,
+                                                            float* __restrict__ r)
 {
     extern __shared__ __align__(16) float sg[];
     __shared__ __align__(8) uint64_t bar_o[SG_NS];
@@ -179,10 +183,9 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
     for (int k = kA; k <= kB; k++) {
         bool bad = false;
         {
-            const int p[3] = {k - 1, k, k + 1};
-#pragma unroll
-            for (int t = 0; t < 3; t++) {
-                const int d = p[t] - o0;
+            // planes k - 1 and k were waited for at the previous step (or here, at the first)
+            for (int p = (k == kA ? k - 1 : k + 1); p <= k + 1; p++) {
+                const int d = p - o0;
                 if (!bad && !sg_wait(sg_smem(&bar_o[d % SG_NS]), (uint32_t)((d / SG_NS) & 1))) bad = true;
             }
             const int d = k - kA;
@@ -197,7 +200,8 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
             const float* om = so + ((k - 1 - o0) % SG_NS) * g.oslot + (go - ost[(k - 1 - o0) % SG_NS]);
             const float* op = so + ((k + 1 - o0) % SG_NS) * g.oslot + (go - ost[(k + 1 - o0) % SG_NS]);
             const float* bo = sb + ((k - kA) % SG_NB) * g.bslot + ((unsigned)c * L.H + q0 + (unsigned)lane - bst[(k - kA) % SG_NB]);
-            float* uo = u + (size_t)c * L.H + q0 + lane;
+            float* uo = (RESID ? r : u) + (size_t)c * L.H + q0 + lane;
+            const float* uc = u + (size_t)c * L.H + q0 + lane;   // the colour's own values (RESID)
             const float cmz = L.ax[2].cm[k], cpz = L.ax[2].cp[k], dgz = L.ax[2].dg[k];
             const float* cmx = sx + (i1 - 1) * 3 * g.hx1 + lane;
             const float* cpx = cmx + g.hx1;
@@ -211,8 +215,12 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
                     t = fmaf(cpy, ok[dyp + 32 * v], t);
                     t = fmaf(cmz, om[dzm + 32 * v], t);
                     t = fmaf(cpz, op[dzp + 32 * v], t);
-                    const float acc = bo[32 * v] - t;
-                    uo[32 * v] = rb_point32(acc, dgx[32 * v] + dgy + dgz);
+                    if constexpr (RESID) {
+                        uo[32 * v] = bo[32 * v] - fmaf(-(dgx[32 * v] + dgy + dgz), __ldg(uc + 32 * v), t);
+                    } else {
+                        const float acc = bo[32 * v] - t;
+                        uo[32 * v] = rb_point32(acc, dgx[32 * v] + dgy + dgz);
+                    }
                 }
             }
         }
@@ -251,7 +259,6 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
     }
 }
 
-template <int V>
 size_t stage_smem(const StageGeom& g)
 {
     return sizeof(float) * ((size_t)SG_NS * g.oslot + (size_t)SG_NB * g.bslot + 6 * (size_t)g.hx1);
@@ -259,15 +266,30 @@ size_t stage_smem(const StageGeom& g)
 
 constexpr size_t SG_SMEM_MAX = 200 * 1024;
 
-template <int V>
-cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s)
+// the shared-memory opt-in of one instantiation on the current device (done once per device;
+// init_stage_attributes does it for all before any graph capture)
+template <int V, int RESID>
+cudaError_t stage_attr(int dev)
+{
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done[dev]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k_rbgs_split_stage<V, RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)SG_SMEM_MAX);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+template <int V, int RESID>
+cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int colour, int* status, float* r,
+                           cudaStream_t s)
 {
     StageGeom g;
     g.tiles_j = (L.ny - 2 + SG_R - 1) / SG_R;
     g.oslot = ((unsigned)(((SG_R + 2) * L.nx + 1) / 2) + 8u + 3u) & ~3u;
     g.bslot = ((unsigned)((SG_R * L.nx + 1) / 2) + 8u + 3u) & ~3u;
     g.hx1 = ((L.nx - 1) / 2 + 3) & ~3;
-    const size_t smem = stage_smem<V>(g);
+    const size_t smem = stage_smem(g);
     if (smem > SG_SMEM_MAX) return cudaErrorInvalidValue;
     // one wave: as many plane chunks per tile column as the resident blocks allow
     static int per_sm_cache[64][2] = {{0, 0}};
@@ -279,11 +301,9 @@ cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int
     if (per_sm_cache[dev][1] == (int)smem) {
         per_sm = per_sm_cache[dev][0];
     } else {
-        // (the shared-memory opt-in is per device; first launches happen outside graph capture,
-        // in the smoother tuner or a direct call)
-        e = cudaFuncSetAttribute(k_rbgs_split_stage<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+        e = stage_attr<V, RESID>(dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_split_stage<V>, SG_NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_split_stage<V, RESID>, SG_NT, smem);
         if (e != cudaSuccess) return e;
         per_sm_cache[dev][0] = per_sm;
         per_sm_cache[dev][1] = (int)smem;
@@ -294,7 +314,7 @@ cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int
     const int chunks0 = std::max(1, std::min(planes, std::max(1, per_sm) * sms / g.tiles_j));
     g.chunk = (planes + chunks0 - 1) / chunks0;
     const int chunks = (planes + g.chunk - 1) / g.chunk;
-    k_rbgs_split_stage<V><<<(unsigned)(g.tiles_j * chunks), SG_NT, smem, s>>>(L, u, b, colour, g, status);
+    k_rbgs_split_stage<V, RESID><<<(unsigned)(g.tiles_j * chunks), SG_NT, smem, s>>>(L, u, b, colour, g, status, r);
     return cudaGetLastError();
 }
 
@@ -303,35 +323,49 @@ cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int
 // the grids the staged kernel takes: at least 9 nodes per axis, rows of at most 513 nodes
 bool split_stage_ok(int nx, int ny, int nz) { return nx >= 9 && ny >= 9 && nz >= 9 && nx <= 513; }
 
-// Colour-split FP32 half sweep with staged planes: a grid split_stage_ok accepts, u and b
-// 16-byte aligned (else cudaErrorInvalidValue).
-cudaError_t launch_split_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s)
+template <int RESID>
+static cudaError_t launch_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, float* r,
+                                cudaStream_t s)
 {
     if (!L.lsh || !split_stage_ok(L.nx, L.ny, L.nz)) return cudaErrorInvalidValue;
     if (((uintptr_t)u & 15u) || ((uintptr_t)b & 15u)) return cudaErrorInvalidValue;
     switch ((L.nx - 1) / 2 <= 256 ? ((L.nx - 1) / 2 + 31) / 32 : 0) {
-        case 1: return launch_stage_v<1>(L, u, b, colour, status, s);
-        case 2: return launch_stage_v<2>(L, u, b, colour, status, s);
-        case 3: return launch_stage_v<3>(L, u, b, colour, status, s);
-        case 4: return launch_stage_v<4>(L, u, b, colour, status, s);
-        case 5: return launch_stage_v<5>(L, u, b, colour, status, s);
-        case 6: return launch_stage_v<6>(L, u, b, colour, status, s);
-        case 7: return launch_stage_v<7>(L, u, b, colour, status, s);
-        case 8: return launch_stage_v<8>(L, u, b, colour, status, s);
+        case 1: return launch_stage_v<1, RESID>(L, u, b, colour, status, r, s);
+        case 2: return launch_stage_v<2, RESID>(L, u, b, colour, status, r, s);
+        case 3: return launch_stage_v<3, RESID>(L, u, b, colour, status, r, s);
+        case 4: return launch_stage_v<4, RESID>(L, u, b, colour, status, r, s);
+        case 5: return launch_stage_v<5, RESID>(L, u, b, colour, status, r, s);
+        case 6: return launch_stage_v<6, RESID>(L, u, b, colour, status, r, s);
+        case 7: return launch_stage_v<7, RESID>(L, u, b, colour, status, r, s);
+        case 8: return launch_stage_v<8, RESID>(L, u, b, colour, status, r, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
+// Colour-split FP32 half sweep with staged planes: a grid split_stage_ok accepts, u and b
+// 16-byte aligned (else cudaErrorInvalidValue).
+cudaError_t launch_split_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s)
+{
+    return launch_stage<0>(L, u, b, colour, status, nullptr, s);
+}
+
+// The residuals b - A u of the red nodes into r (colour-split storage, red half), staged the
+// same way (u, b and r as for launch_split_stage).
+cudaError_t launch_split_stage_resid(const LevelT<float>& L, const float* u, const float* b, float* r, int* status,
+                                     cudaStream_t s)
+{
+    if ((uintptr_t)r & 15u) return cudaErrorInvalidValue;
+    return launch_stage<1>(L, const_cast<float*>(u), b, 0, status, r, s);
+}
+
 void init_stage_attributes()
 {
-    cudaFuncSetAttribute(k_rbgs_split_stage<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
-    cudaFuncSetAttribute(k_rbgs_split_stage<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
-    cudaFuncSetAttribute(k_rbgs_split_stage<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
-    cudaFuncSetAttribute(k_rbgs_split_stage<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
-    cudaFuncSetAttribute(k_rbgs_split_stage<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
-    cudaFuncSetAttribute(k_rbgs_split_stage<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
-    cudaFuncSetAttribute(k_rbgs_split_stage<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
-    cudaFuncSetAttribute(k_rbgs_split_stage<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SG_SMEM_MAX);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    stage_attr<1, 0>(dev), stage_attr<2, 0>(dev), stage_attr<3, 0>(dev), stage_attr<4, 0>(dev);
+    stage_attr<5, 0>(dev), stage_attr<6, 0>(dev), stage_attr<7, 0>(dev), stage_attr<8, 0>(dev);
+    stage_attr<1, 1>(dev), stage_attr<2, 1>(dev), stage_attr<3, 1>(dev), stage_attr<4, 1>(dev);
+    stage_attr<5, 1>(dev), stage_attr<6, 1>(dev), stage_attr<7, 1>(dev), stage_attr<8, 1>(dev);
 }
 
 }  // namespace lasto
