@@ -806,7 +806,7 @@ int enqueue_inner_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphCondition
     if (st) return st;
     TRY(launch_dot32(V, F.b32, F.u32, P.red(FIN_IN_BETA), s));
     TRY(launch_update_p32(V, P.ctl, F.u32, P.p32, s));
-    TRY(launch_apply_dot32(V, P.p32, P.q32, P.red(FIN_IN_ALPHA), s));
+    TRY(launch_apply_dot32(V, P.p32, P.q32, P.red(FIN_IN_ALPHA), s, P.status));
     TRY(launch_update_er32(V, P.ctl, P.p32, P.q32, P.e32, F.b32, P.red(FIN_IN_CHECK, cond, use_cond), s));
     return LASTO_OK;
 }
@@ -999,6 +999,7 @@ int upload_bat_args(lasto_poisson* h, const std::vector<std::vector<int>>& group
             a.part = P.part;
             a.counter = reinterpret_cast<unsigned int*>(P.status + 1);
             a.ctl = P.ctl;
+            a.status = P.status;
             cc[q] = P.ctl;
         }
         L.bot = put(bb.data(), sizeof(BatBottom) * nm);

@@ -318,7 +318,8 @@ cudaError_t launch_update_ur(const LevelT<double>& L, const Ctl* ctl, const doub
                              double* r, const Red& red, cudaStream_t s);
 cudaError_t launch_dot_rz(const LevelT<double>& L, const double* r, const double* z, const Red& red, cudaStream_t s);
 cudaError_t launch_update_p(const LevelT<double>& L, const Ctl* ctl, const double* z, double* p, cudaStream_t s);
-cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s);
+cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s,
+                               int* status = nullptr);
 cudaError_t launch_update_er32(const LevelT<float>& L, const Ctl* ctl, const float* p, const float* q, float* e,
                                float* r, const Red& red, cudaStream_t s);
 cudaError_t launch_dot32(const LevelT<float>& L, const float* r, const float* z, const Red& red, cudaStream_t s);
@@ -430,6 +431,7 @@ struct BatVec {              // one member's finest-level vectors, partials and 
     double* part;
     unsigned int* counter;
     Ctl* ctl;
+    int* status;             // the member's solve status (bounded waits of the staged kernels)
 };
 struct BatBottom {           // one member's one-block bottom levels
     BottomArgs<float> a;

@@ -11,6 +11,7 @@
 
 #include "internal.cuh"
 #include "ctl.cuh"
+#include "stage.cuh"
 
 namespace lasto {
 
@@ -408,13 +409,30 @@ __global__ void __launch_bounds__(NT) k_prolong_add(LevelT<T> F, LevelT<T> C, co
 // update, so 2 PU loads of the iterate are in flight per lane rather than one.
 constexpr int PU = 3;
 
+// L2 bulk prefetch of the fine row `row` of a row-per-warp kernel (both colours), by one lane:
+// the run is widened to whole 16-byte units inside the array
 template <int LS>
-__device__ __forceinline__ void k_prolong_add_rows_body(LevelT<float> F, LevelT<float> C, const float* __restrict__ ec, float* __restrict__ u)
+__device__ __forceinline__ void prefetch_row(const LevelT<float>& F, const float* a, int row)
+{
+    const int my = F.ny - 2;
+    const int k = row / my + 1, j = row - (k - 1) * my + 1;
+    const unsigned P = ((unsigned)k * (unsigned)F.ny + (unsigned)j) * (unsigned)F.nx, N = (unsigned)F.N();
+    for (int t = 0; t < (LS ? 2 : 1); t++) {
+        const unsigned lo = LS ? (unsigned)t * F.H + (P >> 1) : P;
+        const unsigned hi = LS ? (unsigned)t * F.H + ((P + (unsigned)F.nx) >> 1) + 1u : P + (unsigned)F.nx;
+        const unsigned a0 = lo & ~3u, a1 = min((hi + 3u) & ~3u, N & ~3u);
+        if (a1 > a0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a + a0), "r"((a1 - a0) * 4u) : "memory");
+    }
+}
+
+template <int LS>
+__device__ __forceinline__ void k_prolong_add_rows_body(LevelT<float> F, LevelT<float> C, const float* __restrict__ ec, float* __restrict__ u, int pf)
 {
     const int my = F.ny - 2;
     const int row = (int)(blockIdx.x * 8 + (threadIdx.x >> 5));
     if (row >= my * (F.nz - 2)) return;
     const int lane = threadIdx.x & 31;
+    if (pf > 0 && lane == 0 && row + pf < my * (F.nz - 2)) prefetch_row<LS>(F, u, row + pf);
     const int k = row / my + 1, j = row - (k - 1) * my + 1;
     const int nj = (j & 1) ? 2 : 1, nk = (k & 1) ? 2 : 1;
     const float wy[2] = {F.ax[1].pl[j], F.ax[1].pr[j]};
@@ -462,9 +480,32 @@ __device__ __forceinline__ void k_prolong_add_rows_body(LevelT<float> F, LevelT<
 }
 
 template <int LS>
-__global__ void __launch_bounds__(256) k_prolong_add_rows(LevelT<float> F, LevelT<float> C, const float* __restrict__ ec, float* __restrict__ u)
+__global__ void __launch_bounds__(256) k_prolong_add_rows(LevelT<float> F, LevelT<float> C, const float* __restrict__ ec, float* __restrict__ u, int pf)
 {
-    k_prolong_add_rows_body<LS>(F, C, ec, u);
+    k_prolong_add_rows_body<LS>(F, C, ec, u, pf);
+}
+
+// prefetch distance of the row-per-warp prolongation: half the rows the device holds resident
+// (none on small levels, whose rows stay in L2 anyway)
+template <int LS>
+static cudaError_t prolong_rows_pf(const LevelT<float>& F, int* pf)
+{
+    static int pf_rows[64] = {0};
+    *pf = 0;
+    if (F.N() < (size_t(1) << 22)) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (pf_rows[dev] == 0) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prolong_add_rows<LS>, 256, 0);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        pf_rows[dev] = std::max(1, per_sm * sms * 8 / 2);
+    }
+    *pf = pf_rows[dev];
+    return cudaSuccess;
 }
 
 // (the fine level in either storage order, the coarse one natural)
@@ -475,10 +516,14 @@ cudaError_t launch_prolong_add(const LevelT<T>& F, const LevelT<T>& C, const T* 
     if constexpr (sizeof(T) == 4) {
         if (F.ny >= 3 && F.nz >= 3) {
             const unsigned g = (unsigned)(((size_t)(F.ny - 2) * (F.nz - 2) + 7) / 8);
+            int pf = 0;
+            const cudaError_t e = F.lsh ? prolong_rows_pf<1>(F, &pf) : prolong_rows_pf<0>(F, &pf);
+            if (e != cudaSuccess) return e;
+            if ((uintptr_t)u & 15u) pf = 0;
             if (F.lsh)
-                k_prolong_add_rows<1><<<g, 256, 0, s>>>(F, C, ec, u);
+                k_prolong_add_rows<1><<<g, 256, 0, s>>>(F, C, ec, u, pf);
             else
-                k_prolong_add_rows<0><<<g, 256, 0, s>>>(F, C, ec, u);
+                k_prolong_add_rows<0><<<g, 256, 0, s>>>(F, C, ec, u, pf);
             return cudaGetLastError();
         }
     }
@@ -1461,6 +1506,179 @@ __global__ void __launch_bounds__(256) k_apply_dot32_rows(LevelT<float> L, const
     k_apply_dot32_rows_body<LS, V>(L, p, q, red, pf);
 }
 
+// The same, plane-staged (the arrangement of the staged half sweep, stage.cu): a block owns 8
+// interior rows (one warp each) and a chunk of planes, and keeps planes k - 1, k, k + 1 of p --
+// rows j0 - 1 .. j0 + 8, both colours: one run per colour half in colour-split storage, one run
+// in natural storage -- in a ring of AS_NS slots with the next plane in flight.  Both storage
+// orders run this kernel with the same node-to-thread map and accumulation order, so their sums
+// agree bit for bit; so do a lockstep batch and its members run alone.
+constexpr int AS_R = 8;
+constexpr int AS_NS = 4;
+
+struct ApplyGeom {
+    int tiles_j, chunk;
+    unsigned slot;   // floats per run slot (a multiple of 4)
+    int hx1;         // x coefficients per parity (a multiple of 4)
+};
+
+// run t (colour half t in colour-split storage; t = 0 the whole plane rows in natural) of plane pl
+template <int LS>
+__device__ __forceinline__ void as_range(const LevelT<float>& L, int t, int pl, int j0, int nr, unsigned& st, unsigned& len)
+{
+    const unsigned nxy = (unsigned)L.nx * (unsigned)L.ny;
+    const unsigned lo = (unsigned)pl * nxy + (unsigned)(j0 - 1) * (unsigned)L.nx;
+    const unsigned hi = (unsigned)pl * nxy + (unsigned)(j0 + nr + 1) * (unsigned)L.nx - 1u;
+    if constexpr (LS == 1)
+        stage::sg_range((unsigned)t * L.H + (lo >> 1), (unsigned)t * L.H + (hi >> 1) + 1u, (unsigned)L.N(), st, len);
+    else
+        stage::sg_range(lo, hi + 1u, (unsigned)L.N(), st, len);
+}
+
+template <int V, int LS>
+__device__ __forceinline__ void k_apply_stage_body(const LevelT<float>& L, const float* __restrict__ p, float* __restrict__ q,
+                                                   const Red& red, const ApplyGeom& g, int* __restrict__ status)
+{
+    using namespace stage;
+    constexpr int NH = LS ? 2 : 1;
+    extern __shared__ __align__(16) float sg[];
+    __shared__ __align__(8) uint64_t bar[AS_NS];
+    __shared__ unsigned st_of[NH][AS_NS];
+    __shared__ double sm[32];
+    float* ring = sg;                                // [NH][AS_NS][slot]
+    float* sx = sg + NH * AS_NS * g.slot;            // [2 parities][cm, cp, dg, dual][hx1]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tj = (int)(blockIdx.x % (unsigned)g.tiles_j), kc = (int)(blockIdx.x / (unsigned)g.tiles_j);
+    const int j0 = 1 + tj * AS_R;
+    const int nr = min(AS_R, L.ny - 1 - j0);
+    const int kA = 1 + kc * g.chunk, kB = min(L.nz - 2, kA + g.chunk - 1);
+    float acc = 0.0f;
+    bool failed = false;
+    if (nr > 0 && kA <= kB) {   // (block-uniform)
+        const int nx = L.nx;
+        const unsigned nxy = (unsigned)nx * (unsigned)L.ny;
+        const int hx = (nx - 1) >> 1, hxy = (int)((nxy - 1) >> 1);
+        const int o0 = kA - 1, oLast = kB + 1;
+        int o_next = o0;
+        auto issue = [&](int pl) {   // thread 0: plane pl into its slot, all runs on one barrier
+            const int qs = (pl - o0) % AS_NS;
+            unsigned st[NH], ln[NH], bytes = 0;
+            for (int t = 0; t < NH; t++) {
+                as_range<LS>(L, t, pl, j0, nr, st[t], ln[t]);
+                st_of[t][qs] = st[t];
+                bytes += ln[t] * 4u;
+            }
+            const uint32_t b = sg_smem(&bar[qs]);
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(bytes) : "memory");
+            for (int t = 0; t < NH; t++)
+                if (ln[t])
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                            sg_smem(ring + (t * AS_NS + qs) * g.slot)),
+                        "l"(p + st[t]), "r"(ln[t] * 4u), "r"(b)
+                        : "memory");
+        };
+        if (tid == 0) {
+            for (int qq = 0; qq < AS_NS; qq++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sg_smem(&bar[qq])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
+        for (int t = tid; t < 2 * g.hx1; t += blockDim.x) {
+            const int par = t / g.hx1, si = t - par * g.hx1;
+            const int i = 1 + par + 2 * si;
+            const bool in = i < nx - 1;
+            sx[(par * 4 + 0) * g.hx1 + si] = in ? L.ax[0].cm[i] : 0.0f;
+            sx[(par * 4 + 1) * g.hx1 + si] = in ? L.ax[0].cp[i] : 0.0f;
+            sx[(par * 4 + 2) * g.hx1 + si] = in ? L.ax[0].dg[i] : 0.0f;
+            sx[(par * 4 + 3) * g.hx1 + si] = in ? L.ax[0].dual[i] : 0.0f;
+        }
+        __syncthreads();
+        if (tid == 0)
+            for (; o_next <= oLast && o_next < o0 + AS_NS; o_next++) issue(o_next);
+        const int j = j0 + warp;
+        const bool has_row = warp < nr;
+        const float cmy = has_row ? L.ax[1].cm[j] : 0.0f, cpy = has_row ? L.ax[1].cp[j] : 0.0f;
+        const float dgy = has_row ? L.ax[1].dg[j] : 0.0f, vy = has_row ? L.ax[1].dual[j] : 0.0f;
+        for (int k = kA; k <= kB; k++) {
+            bool bad = false;
+            for (int pl = (k == kA ? k - 1 : k + 1); pl <= k + 1; pl++) {
+                const int d = pl - o0;
+                if (!bad && !sg_wait(sg_smem(&bar[d % AS_NS]), (uint32_t)((d / AS_NS) & 1))) bad = true;
+            }
+            if (!bad && has_row) {
+                const int sk = (k - o0) % AS_NS, skm = (k - 1 - o0) % AS_NS, skp = (k + 1 - o0) % AS_NS;
+                const float cmz = L.ax[2].cm[k], cpz = L.ax[2].cp[k], dgz = L.ax[2].dg[k], vz = L.ax[2].dual[k];
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const int i1 = ((c + j + k) & 1) ? 1 : 2;
+                    const int left = ((nx - i1) >> 1) - lane;
+                    const unsigned P0 = (unsigned)k * nxy + (unsigned)j * (unsigned)nx + (unsigned)i1;
+                    const float* cmx = sx + (i1 - 1) * 4 * g.hx1 + lane;
+                    const float* cpx = cmx + g.hx1;
+                    const float* dgx = cpx + g.hx1;
+                    const float* vx = dgx + g.hx1;
+                    constexpr int ST = LS ? 1 : 2;
+                    const float *own, *ok, *om, *op;
+                    float* qo;
+                    int dxm, dxp, dym, dyp, dzm, dzp;
+                    if constexpr (LS == 1) {
+                        const unsigned gq = (P0 >> 1) + (unsigned)lane;
+                        own = ring + (c * AS_NS + sk) * g.slot + ((unsigned)c * L.H + gq - st_of[c][sk]);
+                        const int oc = 1 - c;
+                        ok = ring + (oc * AS_NS + sk) * g.slot + ((unsigned)oc * L.H + gq - st_of[oc][sk]);
+                        om = ring + (oc * AS_NS + skm) * g.slot + ((unsigned)oc * L.H + gq - st_of[oc][skm]);
+                        op = ring + (oc * AS_NS + skp) * g.slot + ((unsigned)oc * L.H + gq - st_of[oc][skp]);
+                        qo = q + (size_t)c * L.H + gq;
+                        dxm = c - 1, dxp = c, dym = c - 1 - hx, dyp = c + hx, dzm = c - 1 - hxy, dzp = c + hxy;
+                    } else {
+                        const unsigned gp = P0 + 2u * (unsigned)lane;
+                        own = ring + sk * g.slot + (gp - st_of[0][sk]);
+                        ok = own;
+                        om = ring + skm * g.slot + (gp - st_of[0][skm]);
+                        op = ring + skp * g.slot + (gp - st_of[0][skp]);
+                        qo = q + gp;
+                        dxm = -1, dxp = 1, dym = -nx, dyp = nx, dzm = -(int)nxy, dzp = (int)nxy;
+                    }
+#pragma unroll
+                    for (int v = 0; v < V; v++) {
+                        if (32 * v < left) {
+                            const int o = 32 * ST * v;
+                            const float pc = own[o];
+                            float t = cmx[32 * v] * ok[dxm + o];
+                            t = fmaf(cpx[32 * v], ok[dxp + o], t);
+                            t = fmaf(cmy, ok[dym + o], t);
+                            t = fmaf(cpy, ok[dyp + o], t);
+                            t = fmaf(cmz, om[dzm + o], t);
+                            t = fmaf(cpz, op[dzp + o], t);
+                            const float val = fmaf(-(dgx[32 * v] + dgy + dgz), pc, t);
+                            acc = fmaf(vx[32 * v] * vy * vz * pc, val, acc);
+                            qo[o] = val;
+                        }
+                    }
+                }
+            }
+            if (__syncthreads_or(bad ? 1 : 0)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0 && o_next <= oLast) issue(o_next++);   // into plane k - 1's slot
+        }
+        if (tid == 0 && failed) {
+            for (int pl = max(o0, o_next - AS_NS); pl < o_next; pl++)
+                sg_wait(sg_smem(&bar[(pl - o0) % AS_NS]), (uint32_t)(((pl - o0) / AS_NS) & 1));
+            if (status) atomicMax(status, (int)LASTO_ERR_TIMEOUT);
+        }
+    }
+    // every block takes part in the reduction (a timed-out one with its partial sum so far)
+    reduce_finish(block_sum_f32(acc, sm), red, sm);
+}
+
+template <int V, int LS>
+__global__ void __launch_bounds__(256) k_apply_stage(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q,
+                                                     Red red, ApplyGeom g, int* __restrict__ status)
+{
+    k_apply_stage_body<V, LS>(L, p, q, red, g, status);
+}
+
 template <int LS>
 __device__ __forceinline__ void k_update_er32_body(LevelT<float> L, const Ctl* __restrict__ ctl, const float* __restrict__ p, const float* __restrict__ q, float* __restrict__ e, float* __restrict__ r, Red red)
 {
@@ -1688,8 +1906,88 @@ static cudaError_t launch_apply_dot32_rows(const LevelT<float>& L, const float* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s)
+// the plane-staged form: geometry, dynamic shared memory and grid (one wave, at most one block
+// per ceil(N / 256) nodes: the reduction's partials)
+constexpr size_t AS_SMEM_MAX = 200 * 1024;
+
+template <int V, int LS, typename K>
+static cudaError_t apply_stage_setup(const LevelT<float>& L, K kernel, ApplyGeom& g, size_t& smem, unsigned& blocks)
 {
+    static bool attr[64] = {false};
+    static int per_sm_cache[64][2] = {{0, 0}};
+    const int nx = L.nx;
+    g.tiles_j = (L.ny - 2 + AS_R - 1) / AS_R;
+    const unsigned run = LS ? (unsigned)(((AS_R + 2) * nx + 1) / 2) : (unsigned)((AS_R + 2) * nx);
+    g.slot = (run + 8u + 3u) & ~3u;
+    g.hx1 = ((nx - 1) / 2 + 3) & ~3;
+    smem = sizeof(float) * ((size_t)(LS ? 2 : 1) * AS_NS * g.slot + 8 * (size_t)g.hx1);
+    if (smem > AS_SMEM_MAX) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    int per_sm = 0, sms = 0;
+    if (per_sm_cache[dev][1] == (int)smem) {
+        per_sm = per_sm_cache[dev][0];
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
+        if (e != cudaSuccess) return e;
+        per_sm_cache[dev][0] = per_sm;
+        per_sm_cache[dev][1] = (int)smem;
+    }
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int planes = L.nz - 2;
+    const size_t cap = std::min<size_t>((size_t)std::max(1, per_sm) * sms, (L.N() + 255) / 256);
+    const int chunks0 = (int)std::max<size_t>(1, std::min<size_t>(planes, cap / g.tiles_j));
+    g.chunk = (planes + chunks0 - 1) / chunks0;
+    blocks = (unsigned)(g.tiles_j * ((planes + g.chunk - 1) / g.chunk));
+    return cudaSuccess;
+}
+
+static bool apply_stage_ok(const LevelT<float>& L, const float* p)
+{
+    return split_stage_ok(L.nx, L.ny, L.nz) && !((uintptr_t)p & 15u);
+}
+
+template <int V, int LS>
+static cudaError_t launch_apply_stage(const LevelT<float>& L, const float* p, float* q, const Red& red, int* status,
+                                      cudaStream_t s)
+{
+    ApplyGeom g;
+    size_t smem = 0;
+    unsigned blocks = 0;
+    cudaError_t e = apply_stage_setup<V, LS>(L, k_apply_stage<V, LS>, g, smem, blocks);
+    if (e != cudaSuccess) return e;
+    k_apply_stage<V, LS><<<blocks, 256, smem, s>>>(L, p, q, red, g, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_dot32(const LevelT<float>& L, const float* p, float* q, const Red& red, cudaStream_t s,
+                               int* status)
+{
+    if (apply_stage_ok(L, p)) {
+#define LASTO_APPLY_STAGE(VV)                                                                                       \
+    case VV:                                                                                                        \
+        return L.lsh ? launch_apply_stage<VV, 1>(L, p, q, red, status, s) : launch_apply_stage<VV, 0>(L, p, q, red, status, s);
+        switch (split_rows_v(L.nx)) {
+            LASTO_APPLY_STAGE(1)
+            LASTO_APPLY_STAGE(2)
+            LASTO_APPLY_STAGE(3)
+            LASTO_APPLY_STAGE(4)
+            LASTO_APPLY_STAGE(5)
+            LASTO_APPLY_STAGE(6)
+            LASTO_APPLY_STAGE(7)
+            LASTO_APPLY_STAGE(8)
+            default: break;
+        }
+#undef LASTO_APPLY_STAGE
+    }
     if (L.ny >= 3 && L.nz >= 3) {
 #define LASTO_APPLY_ROWS(VV)                                                                       \
     case VV:                                                                                       \
@@ -1812,7 +2110,7 @@ __global__ void __launch_bounds__(256) k_prolong_add_rows_bat(const __grid_const
 {
     const BatLevel& a = pk.m[blockIdx.y];
     if (!bat_on(a.ctl, BAT_INNER)) return;
-    k_prolong_add_rows_body<LS>(a.V, a.VC, a.uc, a.u);
+    k_prolong_add_rows_body<LS>(a.V, a.VC, a.uc, a.u, 0);
 }
 
 __global__ void __launch_bounds__(BOT_NT) k_bottom_bat(const BatBottom* __restrict__ m)
@@ -1854,6 +2152,15 @@ __global__ void __launch_bounds__(NT, VEC_MIN_BLOCKS) k_apply_dot32_bat(const __
     if (!bat_on(a.ctl, BAT_INNER)) return;
     const Red red{a.part, a.counter, a.ctl, FIN_IN_ALPHA, 0, 0};
     k_apply_dot32_body<LS>(a.V32, a.p32, a.q32, red);
+}
+
+template <int V, int LS>
+__global__ void __launch_bounds__(256) k_apply_stage_bat(const __grid_constant__ BatPack<BatVec> pk, ApplyGeom g)
+{
+    const BatVec& a = pk.m[blockIdx.y];
+    if (!bat_on(a.ctl, BAT_INNER)) return;
+    const Red red{a.part, a.counter, a.ctl, FIN_IN_ALPHA, 0, 0};
+    k_apply_stage_body<V, LS>(a.V32, a.p32, a.q32, red, g, a.status);
 }
 
 template <int LS, int V>
@@ -2005,9 +2312,46 @@ static cudaError_t launch_apply_dot32_rows_bat(const LevelT<float>& V0, const Ba
     return cudaGetLastError();
 }
 
+template <int V, int LS>
+static cudaError_t launch_apply_stage_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
+{
+    ApplyGeom g;
+    size_t smem = 0;
+    unsigned blocks = 0;
+    cudaError_t e = apply_stage_setup<V, LS>(V0, k_apply_stage_bat<V, LS>, g, smem, blocks);
+    if (e != cudaSuccess) return e;
+    // (the member's own kernel sizes the grid the same way: same shape, same partials)
+    ApplyGeom g1;
+    size_t smem1 = 0;
+    unsigned blocks1 = 0;
+    e = apply_stage_setup<V, LS>(V0, k_apply_stage<V, LS>, g1, smem1, blocks1);
+    if (e != cudaSuccess) return e;
+    k_apply_stage_bat<V, LS><<<dim3(blocks1, (unsigned)nm), 256, smem, s>>>(m, g1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply_dot32_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
 {
     if (nm < 1 || nm > BAT_MAX) return cudaErrorInvalidValue;
+    bool aligned = true;
+    for (int q = 0; q < nm; q++) aligned = aligned && apply_stage_ok(m.m[q].V32, m.m[q].p32);
+    if (aligned) {
+#define LASTO_APPLY_STAGE(VV)                                                                                  \
+    case VV:                                                                                                   \
+        return V0.lsh ? launch_apply_stage_bat<VV, 1>(V0, m, nm, s) : launch_apply_stage_bat<VV, 0>(V0, m, nm, s);
+        switch (split_rows_v(V0.nx)) {
+            LASTO_APPLY_STAGE(1)
+            LASTO_APPLY_STAGE(2)
+            LASTO_APPLY_STAGE(3)
+            LASTO_APPLY_STAGE(4)
+            LASTO_APPLY_STAGE(5)
+            LASTO_APPLY_STAGE(6)
+            LASTO_APPLY_STAGE(7)
+            LASTO_APPLY_STAGE(8)
+            default: break;
+        }
+#undef LASTO_APPLY_STAGE
+    }
     if (V0.ny >= 3 && V0.nz >= 3) {
 #define LASTO_APPLY_ROWS(VV)                                                                          \
     case VV:                                                                                          \
