@@ -189,15 +189,22 @@ bool valid_n(const int n[3])
     return num_levels(nn) >= 1;
 }
 
-__global__ void k_copy_interior(const double* __restrict__ src, double* __restrict__ dst, int nx, int ny, int nz)
+// one block per interior (j, k) row, the row's interior nodes four per thread (loads first)
+__global__ void __launch_bounds__(128) k_copy_interior(const double* __restrict__ src, double* __restrict__ dst, int nx,
+                                                       int ny, int nz)
 {
-    const size_t P = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const size_t N = (size_t)nx * ny * nz;
-    if (P >= N) return;
-    const size_t nxy = (size_t)nx * ny;
-    const int k = (int)(P / nxy), j = (int)((P % nxy) / nx), i = (int)(P % nx);
-    if (i == 0 || j == 0 || k == 0 || i == nx - 1 || j == ny - 1 || k == nz - 1) return;
-    dst[P] = src[P];
+    const int my = ny - 2;
+    const int row = (int)blockIdx.x;
+    const int k = row / my + 1, j = row - (k - 1) * my + 1;
+    const size_t base = ((size_t)k * ny + j) * nx;
+    for (int i0 = 1 + (int)threadIdx.x; i0 < nx - 1; i0 += 4 * 128) {
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) v[q] = i0 + 128 * q < nx - 1 ? src[base + i0 + 128 * q] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (i0 + 128 * q < nx - 1) dst[base + i0 + 128 * q] = v[q];
+    }
 }
 
 // true_is_last: the loop's last residual is already the true FP64 residual of the final iterate
@@ -613,7 +620,7 @@ int enqueue_rhs(lasto_poisson* h, ClusterPlan& P, const lasto_cluster& cl, const
         TRY(launch_boundary_exact(cl, tabs, F.u, s));   // the multipole scratch holds the moments
     }   // LASTO_BC_ZERO: the faces stay 0 (Eq. 3.3)
     if (guess) {
-        k_copy_interior<<<(unsigned)((F.N() + 255) / 256), 256, 0, s>>>(guess, F.u, n[0], n[1], n[2]);
+        k_copy_interior<<<(unsigned)((n[1] - 2) * (n[2] - 2)), 128, 0, s>>>(guess, F.u, n[0], n[1], n[2]);
         TRY(cudaGetLastError());
     }
     return LASTO_OK;

@@ -1231,47 +1231,130 @@ __device__ void reduce_finish(double block_total, const Red& r, double* sm)
 
 #define GRID_STRIDE(P, N) for (size_t P = blockIdx.x * (size_t)NT + threadIdx.x; P < (N); P += (size_t)gridDim.x * NT)
 
-// ||b_eff||^2: b with the Dirichlet faces moved to the right-hand side.
-__global__ void __launch_bounds__(NT) k_bnorm(LevelT<double> L, const double* __restrict__ u,
-                                             const double* __restrict__ b, Red red)
+// Each thread of the vector kernels below takes VU nodes a block's width apart per step and issues all their loads before
+// the first use: with one node per step a thread holds 4-8 B of DRAM loads in flight, a fraction
+// of what the copy rate needs at full occupancy, and the vector kernels ran at a quarter to a
+// half of it.  The accumulation order within a thread is the nodes' order.
+// The reducing ones run in one wave of VEC_BLOCKS blocks, a number of blocks per SM that their
+// register bound guarantees resident (a second, partial wave would leave SMs idle at the end).
+constexpr int VU = 4;
+constexpr int VEC_MIN_BLOCKS = 4;
+constexpr int VEC_BLOCKS = 152 * VEC_MIN_BLOCKS;
+static unsigned vec_grid(size_t N) { return (unsigned)std::min<size_t>((N + NT * VU - 1) / (NT * VU), VEC_BLOCKS); }
+#define GRID_STRIDE_U(P0, N) \
+    for (size_t P0 = blockIdx.x * (size_t)(NT * VU) + threadIdx.x; P0 < (N); P0 += (size_t)gridDim.x * (NT * VU))
+
+// b at a node next to a face with the face values moved to the right-hand side.  Not inlined:
+// inlined, the compiler predicates the six FP64 updates into every node's path, and the FP64
+// pipe (about 1/64 of the FP32 rate here) then bounds the whole norm.
+__device__ __noinline__ double bnorm_face_adjust(const LevelT<double>& L, const double* __restrict__ u, double w,
+                                                 size_t P, int i, int j, int k)
+{
+    const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
+    if (i == 1) w -= L.ax[0].cm[i] * u[P - 1];
+    if (i == L.nx - 2) w -= L.ax[0].cp[i] * u[P + 1];
+    if (j == 1) w -= L.ax[1].cm[j] * u[P - sy];
+    if (j == L.ny - 2) w -= L.ax[1].cp[j] * u[P + sy];
+    if (k == 1) w -= L.ax[2].cm[k] * u[P - sz];
+    if (k == L.nz - 2) w -= L.ax[2].cp[k] * u[P + sz];
+    return w;
+}
+
+// ||b_eff||^2: b with the Dirichlet faces moved to the right-hand side (VU nodes per thread and
+// step, loads first)
+__global__ void __launch_bounds__(NT, VEC_MIN_BLOCKS) k_bnorm(LevelT<double> L, const double* __restrict__ u,
+                                                             const double* __restrict__ b, Red red)
 {
     __shared__ double sm[32];
     double acc = 0.0;
-    GRID_STRIDE(P, L.N())
+    const size_t N = L.N();
+    GRID_STRIDE_U(P0, N)
     {
-        int i, j, k;
-        node_ijk(P, L, i, j, k);
-        if (is_face(L, i, j, k)) continue;
-        const size_t sy = L.nx, sz = (size_t)L.nx * L.ny;
-        double v = b[P];
-        if (i == 1) v -= L.ax[0].cm[i] * u[P - 1];
-        if (i == L.nx - 2) v -= L.ax[0].cp[i] * u[P + 1];
-        if (j == 1) v -= L.ax[1].cm[j] * u[P - sy];
-        if (j == L.ny - 2) v -= L.ax[1].cp[j] * u[P + sy];
-        if (k == 1) v -= L.ax[2].cm[k] * u[P - sz];
-        if (k == L.nz - 2) v -= L.ax[2].cp[k] * u[P + sz];
-        acc = fma(v, v, acc);
+        double v[VU];
+        bool on[VU];
+#pragma unroll
+        for (int q = 0; q < VU; q++) {
+            const size_t P = P0 + (size_t)q * NT;
+            on[q] = false;
+            v[q] = 0.0;
+            if (P < N) {
+                int i, j, k;
+                node_ijk(P, L, i, j, k);
+                if (!is_face(L, i, j, k)) {
+                    on[q] = true;
+                    v[q] = b[P];
+                    if (i == 1 || i == L.nx - 2 || j == 1 || j == L.ny - 2 || k == 1 || k == L.nz - 2)
+                        v[q] = bnorm_face_adjust(L, u, v[q], P, i, j, k);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < VU; q++)
+            if (on[q]) acc = fma(v[q], v[q], acc);
     }
     reduce_finish(block_sum<NT>(acc, sm), red, sm);
 }
 
 // r = b - A u (written when r != nullptr, FP32 copy when r32 != nullptr, in colour-split
-// storage when h32 = ceil(N / 2) is nonzero) and ||r||^2
+// storage when h32 = ceil(N / 2) is nonzero) and ||r||^2.  One warp per (j, k) row (grid-stride
+// over rows), RN_V nodes per lane and step with their loads first: the FP64 pipe (about 1/64
+// of the FP32 rate here) bounds this kernel, and the row form spends one FP64 add per node on
+// the diagonal (dg_x + (dg_y + dg_z), the second sum once per row) where the flat form spends
+// two.  Face nodes get r = 0.
+constexpr int RN_V = 4;
+
 __device__ __forceinline__ void k_resid_norm_body(LevelT<double> L, const double* __restrict__ u, const double* __restrict__ b, double* __restrict__ r, float* __restrict__ r32, unsigned h32, Red red)
 {
     __shared__ double sm[32];
     double acc = 0.0;
-    GRID_STRIDE(P, L.N())
-    {
-        int i, j, k;
-        node_ijk(P, L, i, j, k);
-        double v = 0.0;
-        if (!is_face(L, i, j, k)) v = b[P] - fma(-dsum(L, i, j, k), u[P], offdiag(L, u, P, i, j, k));
-        if (r) r[P] = v;
-        if (r32) r32[h32 ? ((unsigned)P >> 1) + ((unsigned)P & 1u) * h32 : (unsigned)P] = (float)v;
-        acc = fma(v, v, acc);
+    const int nx = L.nx, rows = L.ny * L.nz;
+    const int lane = threadIdx.x & 31;
+    const size_t sy = (size_t)nx, sz = (size_t)nx * L.ny;
+    for (int row = (int)(blockIdx.x * (NT / 32) + (threadIdx.x >> 5)); row < rows; row += (int)(gridDim.x * (NT / 32))) {
+        const int k = row / L.ny, j = row - k * L.ny;
+        const bool frow = j == 0 || k == 0 || j == L.ny - 1 || k == L.nz - 1;
+        const size_t P0 = (size_t)row * nx;
+        double cmy = 0.0, cpy = 0.0, cmz = 0.0, cpz = 0.0, dyz = 0.0;
+        if (!frow) {
+            cmy = L.ax[1].cm[j], cpy = L.ax[1].cp[j], cmz = L.ax[2].cm[k], cpz = L.ax[2].cp[k];
+            dyz = L.ax[1].dg[j] + L.ax[2].dg[k];
+        }
+        for (int i0 = lane; i0 < nx; i0 += 32 * RN_V) {
+            double v[RN_V];
+#pragma unroll
+            for (int q = 0; q < RN_V; q++) {
+                const int i = i0 + 32 * q;
+                v[q] = 0.0;
+                if (!frow && i >= 1 && i <= nx - 2) {
+                    const double* c = u + P0 + i;
+                    double t = L.ax[0].cm[i] * c[-1];
+                    t = fma(L.ax[0].cp[i], c[1], t);
+                    t = fma(cmy, c[-(ptrdiff_t)sy], t);
+                    t = fma(cpy, c[sy], t);
+                    t = fma(cmz, c[-(ptrdiff_t)sz], t);
+                    t = fma(cpz, c[sz], t);
+                    v[q] = b[P0 + i] - fma(-(L.ax[0].dg[i] + dyz), c[0], t);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RN_V; q++) {
+                const int i = i0 + 32 * q;
+                if (i >= nx) continue;
+                const unsigned P = (unsigned)(P0 + i);
+                if (r) r[P] = v[q];
+                if (r32) r32[h32 ? (P >> 1) + (P & 1u) * h32 : P] = (float)v[q];
+                acc = fma(v[q], v[q], acc);
+            }
+        }
     }
     reduce_finish(block_sum<NT>(acc, sm), red, sm);
+}
+
+// rows kernels' grid: one warp per row while the partials allow (one per ceil(N / 256) nodes)
+static unsigned resid_rows_grid(const LevelT<double>& L)
+{
+    const size_t rows = (size_t)L.ny * L.nz;
+    return (unsigned)std::max<size_t>(1, std::min((rows + NT / 32 - 1) / (NT / 32), (L.N() + 255) / 256));
 }
 
 __global__ void __launch_bounds__(NT) k_resid_norm(LevelT<double> L, const double* __restrict__ u, const double* __restrict__ b, double* __restrict__ r, float* __restrict__ r32, unsigned h32, Red red)
@@ -1352,19 +1435,6 @@ __device__ __forceinline__ float vol32(const LevelT<float>& L, int i, int j, int
 
 // (the inner CG vectors share the finest level's FP32 storage order; every kernel walks the
 // nodes in flat order, so sums are formed in the same order in both)
-//
-// Each thread takes VU nodes a block's width apart per step and issues all their loads before
-// the first use: with one node per step a thread holds 4-8 B of DRAM loads in flight, a fraction
-// of what the copy rate needs at full occupancy, and the FP32 vector kernels ran at a quarter to
-// a half of it.  The accumulation order within a thread is the nodes' order.
-// The reducing ones run in one wave of VEC_BLOCKS blocks, a number of blocks per SM that their
-// register bound guarantees resident (a second, partial wave would leave SMs idle at the end).
-constexpr int VU = 4;
-constexpr int VEC_MIN_BLOCKS = 4;
-constexpr int VEC_BLOCKS = 152 * VEC_MIN_BLOCKS;
-static unsigned vec_grid(size_t N) { return (unsigned)std::min<size_t>((N + NT * VU - 1) / (NT * VU), VEC_BLOCKS); }
-#define GRID_STRIDE_U(P0, N) \
-    for (size_t P0 = blockIdx.x * (size_t)(NT * VU) + threadIdx.x; P0 < (N); P0 += (size_t)gridDim.x * (NT * VU))
 
 template <int LS>
 __device__ __forceinline__ void k_apply_dot32_body(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q, Red red)
@@ -1837,13 +1907,13 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, si
 
 cudaError_t launch_bnorm(const LevelT<double>& L, const double* u, const double* b, const Red& red, cudaStream_t s)
 {
-    k_bnorm<<<RGRID(L)>>>(L, u, b, red);
+    k_bnorm<<<vec_grid(L.N()), NT, 0, s>>>(L, u, b, red);
     return cudaGetLastError();
 }
 cudaError_t launch_resid_norm(const LevelT<double>& L, const double* u, const double* b, double* r, float* r32,
                               unsigned h32, const Red& red, cudaStream_t s)
 {
-    k_resid_norm<<<RGRID(L)>>>(L, u, b, r, r32, h32, red);
+    k_resid_norm<<<resid_rows_grid(L), NT, 0, s>>>(L, u, b, r, r32, h32, red);
     return cudaGetLastError();
 }
 cudaError_t launch_apply_dot(const LevelT<double>& L, const double* p, double* q, const Red& red, cudaStream_t s)
@@ -1910,43 +1980,64 @@ static cudaError_t launch_apply_dot32_rows(const LevelT<float>& L, const float* 
 // per ceil(N / 256) nodes: the reduction's partials)
 constexpr size_t AS_SMEM_MAX = 200 * 1024;
 
-template <int V, int LS, typename K>
-static cudaError_t apply_stage_setup(const LevelT<float>& L, K kernel, ApplyGeom& g, size_t& smem, unsigned& blocks)
+// geometry of one storage order on a level
+template <int LS>
+static void apply_stage_geom(const LevelT<float>& L, ApplyGeom& g, size_t& smem)
 {
-    static bool attr[64] = {false};
-    static int per_sm_cache[64][2] = {{0, 0}};
     const int nx = L.nx;
     g.tiles_j = (L.ny - 2 + AS_R - 1) / AS_R;
     const unsigned run = LS ? (unsigned)(((AS_R + 2) * nx + 1) / 2) : (unsigned)((AS_R + 2) * nx);
     g.slot = (run + 8u + 3u) & ~3u;
     g.hx1 = ((nx - 1) / 2 + 3) & ~3;
     smem = sizeof(float) * ((size_t)(LS ? 2 : 1) * AS_NS * g.slot + 8 * (size_t)g.hx1);
-    if (smem > AS_SMEM_MAX) return cudaErrorInvalidValue;
+}
+
+template <int V, int LS>
+__global__ void __launch_bounds__(256) k_apply_stage(LevelT<float> L, const float* __restrict__ p, float* __restrict__ q,
+                                                     Red red, ApplyGeom g, int* __restrict__ status);
+
+// The grid: one wave of the blocks both storage orders hold resident (the fewer of the two), at
+// most one block per ceil(N / 256) nodes (the reduction's partials).  The block-to-work map, and
+// with it the order of the sums, thus depends on the grid shape alone -- never on the storage
+// order or on a lockstep batch -- so every form of the solve forms the same dot products.
+template <int V>
+static cudaError_t apply_stage_plan(const LevelT<float>& L, int& chunk, unsigned& blocks)
+{
+    static int cache[64][3] = {{0, 0, 0}};   // nx, ny, blocks per SM
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr[dev]) {
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS_SMEM_MAX);
-        if (e != cudaSuccess) return e;
-        attr[dev] = true;
-    }
-    int per_sm = 0, sms = 0;
-    if (per_sm_cache[dev][1] == (int)smem) {
-        per_sm = per_sm_cache[dev][0];
+    int per_sm = 0;
+    if (cache[dev][0] == L.nx && cache[dev][1] == L.ny) {
+        per_sm = cache[dev][2];
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
+        ApplyGeom g0, g1;
+        size_t m0 = 0, m1 = 0;
+        apply_stage_geom<0>(L, g0, m0);
+        apply_stage_geom<1>(L, g1, m1);
+        if (m0 > AS_SMEM_MAX || m1 > AS_SMEM_MAX) return cudaErrorInvalidValue;
+        int a0 = 0, a1 = 0;
+        e = cudaFuncSetAttribute(k_apply_stage<V, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS_SMEM_MAX);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_apply_stage<V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS_SMEM_MAX);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a0, k_apply_stage<V, 0>, 256, m0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a1, k_apply_stage<V, 1>, 256, m1);
         if (e != cudaSuccess) return e;
-        per_sm_cache[dev][0] = per_sm;
-        per_sm_cache[dev][1] = (int)smem;
+        per_sm = std::max(1, std::min(a0, a1));
+        cache[dev][0] = L.nx;
+        cache[dev][1] = L.ny;
+        cache[dev][2] = per_sm;
     }
+    int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    const int tiles_j = (L.ny - 2 + AS_R - 1) / AS_R;
     const int planes = L.nz - 2;
-    const size_t cap = std::min<size_t>((size_t)std::max(1, per_sm) * sms, (L.N() + 255) / 256);
-    const int chunks0 = (int)std::max<size_t>(1, std::min<size_t>(planes, cap / g.tiles_j));
-    g.chunk = (planes + chunks0 - 1) / chunks0;
-    blocks = (unsigned)(g.tiles_j * ((planes + g.chunk - 1) / g.chunk));
+    const size_t cap = std::min<size_t>((size_t)per_sm * sms, (L.N() + 255) / 256);
+    const int chunks0 = (int)std::max<size_t>(1, std::min<size_t>(planes, cap / tiles_j));
+    chunk = (planes + chunks0 - 1) / chunks0;
+    blocks = (unsigned)(tiles_j * ((planes + chunk - 1) / chunk));
     return cudaSuccess;
 }
 
@@ -1962,7 +2053,8 @@ static cudaError_t launch_apply_stage(const LevelT<float>& L, const float* p, fl
     ApplyGeom g;
     size_t smem = 0;
     unsigned blocks = 0;
-    cudaError_t e = apply_stage_setup<V, LS>(L, k_apply_stage<V, LS>, g, smem, blocks);
+    apply_stage_geom<LS>(L, g, smem);
+    cudaError_t e = apply_stage_plan<V>(L, g.chunk, blocks);
     if (e != cudaSuccess) return e;
     k_apply_stage<V, LS><<<blocks, 256, smem, s>>>(L, p, q, red, g, status);
     return cudaGetLastError();
@@ -2315,18 +2407,23 @@ static cudaError_t launch_apply_dot32_rows_bat(const LevelT<float>& V0, const Ba
 template <int V, int LS>
 static cudaError_t launch_apply_stage_bat(const LevelT<float>& V0, const BatPack<BatVec>& m, int nm, cudaStream_t s)
 {
+    static bool attr[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(k_apply_stage_bat<V, LS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS_SMEM_MAX);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
     ApplyGeom g;
     size_t smem = 0;
     unsigned blocks = 0;
-    cudaError_t e = apply_stage_setup<V, LS>(V0, k_apply_stage_bat<V, LS>, g, smem, blocks);
+    apply_stage_geom<LS>(V0, g, smem);
+    e = apply_stage_plan<V>(V0, g.chunk, blocks);   // the members' own grid
     if (e != cudaSuccess) return e;
-    // (the member's own kernel sizes the grid the same way: same shape, same partials)
-    ApplyGeom g1;
-    size_t smem1 = 0;
-    unsigned blocks1 = 0;
-    e = apply_stage_setup<V, LS>(V0, k_apply_stage<V, LS>, g1, smem1, blocks1);
-    if (e != cudaSuccess) return e;
-    k_apply_stage_bat<V, LS><<<dim3(blocks1, (unsigned)nm), 256, smem, s>>>(m, g1);
+    k_apply_stage_bat<V, LS><<<dim3(blocks, (unsigned)nm), 256, smem, s>>>(m, g);
     return cudaGetLastError();
 }
 
@@ -2393,7 +2490,7 @@ cudaError_t launch_outer_bat(const LevelT<double>& V0, const BatPack<BatVec>& m,
     k_add_correction_bat<<<dim3((unsigned)((N + NT - 1) / NT), (unsigned)nm), NT, 0, s>>>(m, N, h32);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resid_norm_bat<<<dim3(red_grid(N), (unsigned)nm), NT, 0, s>>>(m, h32);
+    k_resid_norm_bat<<<dim3(resid_rows_grid(V0), (unsigned)nm), NT, 0, s>>>(m, h32);
     return cudaGetLastError();
 }
 
