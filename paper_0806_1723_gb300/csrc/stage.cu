@@ -28,6 +28,10 @@ constexpr int SG_R = 8;              // interior rows per tile, one warp each
 constexpr int SG_NT = 32 * SG_R;
 constexpr int SG_NS = 4;             // other-colour plane slots: k - 1, k, k + 1, one in flight
 constexpr int SG_NB = 2;             // right-hand-side plane slots: k, one in flight
+
+// RESID = 0: the half sweep of `colour` in place on u.  RESID = 1: no update; the residuals
+// b - A u of the colour's nodes go to r at the nodes' own storage positions (the restriction
+// after a black half sweep reads those of the red nodes: the black ones are then zero).
 template <int V, int RESID>
 __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, float* __restrict__ u, const float* __restrict__ b,
                                                             int colour, StageGeom g, int* __restrict__ status,

@@ -98,8 +98,5 @@ __device__ __forceinline__ void sg_issue(const float* src, unsigned start, unsig
             : "memory");
 }
 
-// RESID = 0: the half sweep of `colour` in place on u.  RESID = 1: no update; the residuals
-// b - A u of the colour's nodes go to r at the nodes' own storage positions (the restriction
-// after a black half sweep reads those of the red nodes: the black ones are then zero).
 }  // namespace stage
 }  // namespace lasto
