@@ -68,9 +68,9 @@ DRAM_BYTES_257_F64 = 537.7e6
 # 385^3 itself (third launch of `bench.py --profile smoother --n 385 --split --threads 0
 # --sweeps 2`, ncu --set full: caches flushed before the launch): 230.9 MB read + 87.2 MB written
 DRAM_BYTES_385_SPLIT_ROWS = 318.1e6
-# the plane-staged half sweep over colour-split storage (k_rbgs_split_stage<6>), captured the same
-# way (`--threads 1`): DRAM_BYTES_385_SPLIT_STAGE, read + written per launch
-DRAM_BYTES_385_SPLIT_STAGE = None
+# the plane-staged half sweep over colour-split storage (k_rbgs_split_stage<6, 0>), captured the
+# same way (`--threads 1`): 237.2 MB read + 76.6 MB written
+DRAM_BYTES_385_SPLIT_STAGE = 313.8e6
 
 
 def parse():
