@@ -930,9 +930,10 @@ def smoother_roofline(B, stream, flush, dev, tuned, probes):
     """The second kernel of the headline: the FP32 smoother at 385^3, in the launch shape the
     tuner chose for that level.  Algorithmic bytes (the smoother's compulsory traffic, 12 B per
     node per FP32 sweep: u read, b read, u written): 6 B per node for one half-sweep launch (one
-    colour; natural or colour-split storage), 12 B per node for one fused wavefront sweep.  Each shape is timed alone
-    with CUDA events (L2 flushed; the difference of a longer and a shorter call, so table set-up
-    cancels), and the line reports the tuner's choice; `traffic` is ncu's DRAM bytes per launch
+    colour; natural or colour-split storage), 12 B per node for one fused wavefront sweep.  Each
+    shape is timed alone with CUDA events (L2 flushed before each call; the difference of a 9-
+    and a 1-sweep call for the half sweeps, 16 launches back to back as in a cycle's smoothing,
+    so table set-up and the first, cold launch cancel), and the line reports the tuner's choice; `traffic` is ncu's DRAM bytes per launch
     (dram__bytes_read.sum + dram__bytes_write.sum at 257^3 in steady state, scaled by nodes)."""
     import torch
 
@@ -961,13 +962,13 @@ def smoother_roofline(B, stream, flush, dev, tuned, probes):
     shapes = {}
     names = {0: "rows", B.SPLIT_STAGED: "staged"}
     for th in (B.SPLIT_STAGED, 0, 128):   # half sweeps over colour-split storage (its data is irrelevant here)
-        t = (timed(lambda: B.lasto_op_smooth_split(*axes, u, b, sweeps=3, threads=th)) -
-             timed(lambda: B.lasto_op_smooth_split(*axes, u, b, sweeps=1, threads=th))) / 4
+        t = (timed(lambda: B.lasto_op_smooth_split(*axes, u, b, sweeps=9, threads=th)) -
+             timed(lambda: B.lasto_op_smooth_split(*axes, u, b, sweeps=1, threads=th))) / 16
         shapes[f"split_{names.get(th, th)}"] = {"us_per_launch": t * 1e6, "bytes_per_launch": 6.0 * n ** 3,
                                                 "launches_per_sweep": 2, "nt": th}
     for th in (0, 128, 256):   # in-place half sweeps: per launch (2 launches per sweep)
-        t = (timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=3, threads=th)) -
-             timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=1, threads=th))) / 4
+        t = (timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=9, threads=th)) -
+             timed(lambda: B.lasto_op_smooth(*axes, u, b, sweeps=1, threads=th))) / 16
         shapes[f"inplace_{th if th else 'rows'}"] = {"us_per_launch": t * 1e6, "bytes_per_launch": 6.0 * n ** 3,
                                                      "launches_per_sweep": 2, "nt": th}
     for tile in ((60, 16), (60, 12), (60, 8)):   # wavefront sweeps: per launch (1 per sweep)
