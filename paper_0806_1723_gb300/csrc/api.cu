@@ -531,7 +531,7 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
         st = enqueue_cycle<T>(h, P, l + 1, Arr<T>::u(C), Arr<T>::b(C), Arr<T>::r(C), false, sym, s);
         if (st) return st;
     }
-    TRY(launch_prolong_add<T>(V, VC, Arr<T>::u(C), cur, s));
+    TRY(launch_prolong_add<T>(V, VC, Arr<T>::u(C), cur, s, P.status));
     TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu2, sym ? 1 : 0, ch, P.status, s));
     if (cur != u) return fail(h, LASTO_ERR_INVALID_ARG, "smoother passes do not return to the level array");
     return LASTO_OK;

@@ -230,6 +230,8 @@ cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaSt
 cudaError_t launch_split_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s);
 cudaError_t launch_split_stage_resid(const LevelT<float>& L, const float* u, const float* b, float* r, int* status,
                                      cudaStream_t s);
+cudaError_t launch_prolong_stage(const LevelT<float>& F, const LevelT<float>& C, const float* ec, float* u, int* status,
+                                 cudaStream_t s);
 bool split_stage_ok(int nx, int ny, int nz);
 void init_stage_attributes();
 template <typename T>
@@ -239,7 +241,8 @@ cudaError_t launch_apply(const LevelT<T>& L, const T* u, T* Au, cudaStream_t s);
 template <typename T>
 cudaError_t launch_restrict(const LevelT<T>& fine, const LevelT<T>& coarse, const T* r, T* bc, cudaStream_t s);
 template <typename T>
-cudaError_t launch_prolong_add(const LevelT<T>& fine, const LevelT<T>& coarse, const T* ec, T* u, cudaStream_t s);
+cudaError_t launch_prolong_add(const LevelT<T>& fine, const LevelT<T>& coarse, const T* ec, T* u, cudaStream_t s,
+                               int* status = nullptr);
 template <typename T>
 cudaError_t launch_coarse_apply(const LevelT<T>& L, const CoarseEig* eig, const T* b, T* e, bool add, cudaStream_t s);
 

@@ -510,10 +510,14 @@ static cudaError_t prolong_rows_pf(const LevelT<float>& F, int* pf)
 
 // (the fine level in either storage order, the coarse one natural)
 template <typename T>
-cudaError_t launch_prolong_add(const LevelT<T>& F, const LevelT<T>& C, const T* ec, T* u, cudaStream_t s)
+cudaError_t launch_prolong_add(const LevelT<T>& F, const LevelT<T>& C, const T* ec, T* u, cudaStream_t s, int* status)
 {
     if (C.lsh) return cudaErrorInvalidValue;
     if constexpr (sizeof(T) == 4) {
+        // colour-split fine level: the plane-staged form (bitwise the same); the solver's arrays
+        // are padded to 256 bytes, so ec is readable to the next 16 bytes past its end
+        if (F.lsh && split_stage_ok(F.nx, F.ny, F.nz) && !((uintptr_t)u & 15u) && !((uintptr_t)ec & 15u))
+            return launch_prolong_stage(F, C, ec, u, status, s);
         if (F.ny >= 3 && F.nz >= 3) {
             const unsigned g = (unsigned)(((size_t)(F.ny - 2) * (F.nz - 2) + 7) / 8);
             int pf = 0;
@@ -2514,7 +2518,7 @@ void init_bat_attributes()
     template cudaError_t launch_residual<T>(const LevelT<T>&, const T*, const T*, T*, cudaStream_t);        \
     template cudaError_t launch_apply<T>(const LevelT<T>&, const T*, T*, cudaStream_t);                     \
     template cudaError_t launch_restrict<T>(const LevelT<T>&, const LevelT<T>&, const T*, T*, cudaStream_t); \
-    template cudaError_t launch_prolong_add<T>(const LevelT<T>&, const LevelT<T>&, const T*, T*, cudaStream_t); \
+    template cudaError_t launch_prolong_add<T>(const LevelT<T>&, const LevelT<T>&, const T*, T*, cudaStream_t, int*); \
     template cudaError_t launch_coarse_apply<T>(const LevelT<T>&, const CoarseEig*, const T*, T*, bool, cudaStream_t);
 INST(double)
 INST(float)

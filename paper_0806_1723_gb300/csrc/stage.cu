@@ -277,6 +277,228 @@ cudaError_t launch_split_stage_resid(const LevelT<float>& L, const float* u, con
     return launch_stage<1>(L, const_cast<float*>(u), b, 0, status, r, s);
 }
 
+// ---------------------------------------------------------------- staged prolongation
+// u += P ec on a colour-split fine level (the coarse level natural): the trilinear prolongation
+// of Section 3 with the coarse rows a tile reads staged in shared memory.  A block owns 8
+// interior fine rows (a warp each, both colours) and a chunk of fine planes; fine plane k reads
+// coarse planes k/2 and, for odd k, k/2 + 1 -- rows j0/2 .. (j0 + 7)/2 + 1 of each, one
+// contiguous run -- kept in a ring of PS_NS slots with the next plane in flight (a coarse plane
+// serves two fine planes).  The fine values are read and written in place, the next fine
+// plane's rows brought into L2 by a bulk prefetch one plane ahead.  The node expression is
+// k_prolong_add's, so the two are bitwise equal.  ec must be readable up to the next multiple
+// of 4 floats past its end (the solver's arrays are padded to 256 bytes).
+namespace {
+
+constexpr int PS_R = 8;
+constexpr int PS_NT = 32 * PS_R;
+constexpr int PS_NS = 3;
+
+struct ProlongGeom {
+    int tiles_j, chunk;
+    unsigned cslot;   // floats per coarse run slot (a multiple of 4)
+    int hx1;          // fine x weights per parity (a multiple of 4)
+};
+
+// coarse run of coarse plane K for the tile's fine rows j0 .. j0 + nr - 1
+__device__ __forceinline__ void ps_range(const LevelT<float>& C, int K, int j0, int nr, unsigned& st, unsigned& len)
+{
+    const int Ja = j0 >> 1, Jb = min((j0 + nr - 1) / 2 + 1, C.ny - 1);
+    const unsigned lo = ((unsigned)K * (unsigned)C.ny + (unsigned)Ja) * (unsigned)C.nx;
+    const unsigned hi = ((unsigned)K * (unsigned)C.ny + (unsigned)Jb + 1u) * (unsigned)C.nx;   // exclusive
+    st = lo & ~3u;
+    len = ((hi + 3u) & ~3u) - st;
+}
+
+template <int V>
+__global__ void __launch_bounds__(PS_NT) k_prolong_stage(LevelT<float> F, LevelT<float> C, const float* __restrict__ ec,
+                                                         float* __restrict__ u, ProlongGeom g, int* __restrict__ status)
+{
+    extern __shared__ __align__(16) float sg[];
+    __shared__ __align__(8) uint64_t bar[PS_NS];
+    __shared__ unsigned cst[PS_NS];
+    float* sc = sg;                          // [PS_NS][cslot]
+    float* sw = sg + PS_NS * g.cslot;        // fine x weights [2 parities][pl, pr][hx1]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tj = (int)(blockIdx.x % (unsigned)g.tiles_j), kc = (int)(blockIdx.x / (unsigned)g.tiles_j);
+    const int j0 = 1 + tj * PS_R;
+    const int nr = min(PS_R, F.ny - 1 - j0);
+    const int kA = 1 + kc * g.chunk, kB = min(F.nz - 2, kA + g.chunk - 1);
+    if (nr <= 0 || kA > kB) return;
+    const int nx = F.nx;
+    const unsigned nxy = (unsigned)nx * (unsigned)F.ny;
+    const int K0 = kA >> 1, KL = (kB >> 1) + 1;   // coarse planes K0 .. KL, in order
+    int k_next = K0;
+    auto issue = [&](int K) {   // thread 0
+        const int q = (K - K0) % PS_NS;
+        unsigned st, ln;
+        ps_range(C, K, j0, nr, st, ln);
+        cst[q] = st;
+        const uint32_t b = sg_smem(&bar[q]);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(b), "r"(ln * 4u) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                         sg_smem(sc + q * g.cslot)),
+                     "l"(ec + st), "r"(ln * 4u), "r"(b)
+                     : "memory");
+    };
+    auto fine_prefetch = [&](int k) {   // thread 0: plane k's tile rows, both colours, into L2
+        for (int t = 0; t < 2; t++) {
+            const unsigned lo = (unsigned)t * F.H + (((unsigned)k * nxy + (unsigned)j0 * (unsigned)nx) >> 1);
+            const unsigned hi = (unsigned)t * F.H + (((unsigned)k * nxy + (unsigned)(j0 + nr) * (unsigned)nx) >> 1) + 1u;
+            sg_prefetch(u, lo & ~3u, (((hi + 3u) & ~3u) - (lo & ~3u)));
+        }
+    };
+    if (tid == 0) {
+        for (int q = 0; q < PS_NS; q++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(sg_smem(&bar[q])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    for (int t = tid; t < 2 * g.hx1; t += PS_NT) {
+        const int par = t / g.hx1, si = t - par * g.hx1;
+        const int i = 1 + par + 2 * si;
+        const bool in = i < nx - 1;
+        sw[(par * 2 + 0) * g.hx1 + si] = in ? F.ax[0].pl[i] : 0.0f;
+        sw[(par * 2 + 1) * g.hx1 + si] = in ? F.ax[0].pr[i] : 0.0f;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (; k_next <= KL && k_next < K0 + PS_NS; k_next++) issue(k_next);
+        fine_prefetch(kA);
+    }
+    const int j = j0 + warp;
+    const bool has_row = warp < nr;
+    const int nj = (j & 1) ? 2 : 1;
+    const float wy0 = has_row ? F.ax[1].pl[j] : 0.0f, wy1 = has_row ? F.ax[1].pr[j] : 0.0f;
+    bool failed = false;
+    int waited = K0 - 1;   // coarse planes waited for so far
+    for (int k = kA; k <= kB; k++) {
+        const int K = k >> 1, nk = (k & 1) ? 2 : 1;
+        bool bad = false;
+        for (int Kw = waited + 1; Kw <= K + nk - 1; Kw++) {
+            const int d = Kw - K0;
+            if (!bad && !sg_wait(sg_smem(&bar[d % PS_NS]), (uint32_t)((d / PS_NS) & 1))) bad = true;
+        }
+        waited = max(waited, K + nk - 1);
+        if (tid == 0 && k < kB) fine_prefetch(k + 1);
+        if (!bad && has_row) {
+            const float wz0 = F.ax[2].pl[k], wz1 = F.ax[2].pr[k];
+            const float wz[2] = {wz0, wz1}, wy[2] = {wy0, wy1};
+            // the coarse row (K, j / 2) of each needed coarse plane, in its slot
+            const float* crow[2];
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int Kc = min(K + c, KL);
+                const int q = (Kc - K0) % PS_NS;
+                crow[c] = sc + q * g.cslot + ((((unsigned)Kc * (unsigned)C.ny + (unsigned)(j >> 1)) * (unsigned)C.nx) - cst[q]);
+            }
+#pragma unroll
+            for (int t = 0; t < 2; t++) {   // the row's red nodes, then its black ones
+                const int i1 = ((t + j + k) & 1) ? 1 : 2;
+                const int left = ((nx - i1) >> 1) - lane;
+                const int ni = (i1 & 1) ? 2 : 1;   // the parity of i is the run's
+                float* ur = u + (size_t)t * F.H + ((((unsigned)k * nxy + (unsigned)j * (unsigned)nx + (unsigned)i1) >> 1) + lane);
+                const float* wx0 = sw + (i1 - 1) * 2 * g.hx1 + lane;
+                const float* wx1 = wx0 + g.hx1;
+                float uv[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) uv[v] = 32 * v < left ? ur[32 * v] : 0.0f;
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    if (32 * v >= left) continue;
+                    const int i = i1 + 2 * (lane + 32 * v);
+                    const float wx[2] = {wx0[32 * v], wx1[32 * v]};
+                    float e = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 2; c++)
+#pragma unroll
+                        for (int bb = 0; bb < 2; bb++) {
+                            if (c >= nk || bb >= nj) continue;
+                            const float* r = crow[c] + bb * C.nx + (i >> 1);
+                            const float sv = (ni == 2) ? fmaf(wx[0], r[0], wx[1] * r[1]) : r[0];
+                            e = fmaf(wz[c] * wy[bb], sv, e);
+                        }
+                    ur[32 * v] = uv[v] + e;
+                }
+            }
+        }
+        if (__syncthreads_or(bad ? 1 : 0)) {
+            failed = true;
+            break;
+        }
+        // after an odd fine plane its lower coarse plane is done: its slot takes the next one
+        if (tid == 0 && (k & 1) && k_next <= KL) issue(k_next++);
+    }
+    if (tid == 0 && failed) {
+        for (int K = max(K0, k_next - PS_NS); K < k_next; K++)
+            sg_wait(sg_smem(&bar[(K - K0) % PS_NS]), (uint32_t)(((K - K0) / PS_NS) & 1));
+        if (status) atomicMax(status, (int)LASTO_ERR_TIMEOUT);
+    }
+}
+
+template <int V>
+cudaError_t launch_prolong_stage_v(const LevelT<float>& F, const LevelT<float>& C, const float* ec, float* u,
+                                   int* status, cudaStream_t s)
+{
+    static bool attr[64] = {false};
+    static int per_sm_cache[64][2] = {{0, 0}};
+    ProlongGeom g;
+    g.tiles_j = (F.ny - 2 + PS_R - 1) / PS_R;
+    g.cslot = (((unsigned)(PS_R / 2 + 2) * (unsigned)C.nx) + 8u + 3u) & ~3u;
+    g.hx1 = ((F.nx - 1) / 2 + 3) & ~3;
+    const size_t smem = sizeof(float) * ((size_t)PS_NS * g.cslot + 4 * (size_t)g.hx1);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(k_prolong_stage<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    int per_sm = 0, sms = 0;
+    if (per_sm_cache[dev][1] == (int)smem) {
+        per_sm = per_sm_cache[dev][0];
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_prolong_stage<V>, PS_NT, smem);
+        if (e != cudaSuccess) return e;
+        per_sm_cache[dev][0] = per_sm;
+        per_sm_cache[dev][1] = (int)smem;
+    }
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // chunks of an even number of fine planes (a coarse plane serves a pair)
+    const int planes = F.nz - 2;
+    const int chunks0 = std::max(1, std::min(planes, std::max(1, per_sm) * sms / g.tiles_j));
+    g.chunk = (planes + chunks0 - 1) / chunks0;
+    g.chunk += g.chunk & 1;
+    const int chunks = (planes + g.chunk - 1) / g.chunk;
+    k_prolong_stage<V><<<(unsigned)(g.tiles_j * chunks), PS_NT, smem, s>>>(F, C, ec, u, g, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// u += P ec, fine level colour-split (a grid split_stage_ok accepts, u 16-byte aligned), coarse
+// level natural with every axis (n + 1) / 2 of the fine one; ec readable to the next multiple of
+// 4 floats past its end
+cudaError_t launch_prolong_stage(const LevelT<float>& F, const LevelT<float>& C, const float* ec, float* u, int* status,
+                                 cudaStream_t s)
+{
+    if (!F.lsh || C.lsh || !split_stage_ok(F.nx, F.ny, F.nz) || ((uintptr_t)u & 15u) || ((uintptr_t)ec & 15u))
+        return cudaErrorInvalidValue;
+    if (C.nx != (F.nx + 1) / 2 || C.ny != (F.ny + 1) / 2 || C.nz != (F.nz + 1) / 2) return cudaErrorInvalidValue;
+    switch ((F.nx - 1) / 2 <= 256 ? ((F.nx - 1) / 2 + 31) / 32 : 0) {
+        case 1: return launch_prolong_stage_v<1>(F, C, ec, u, status, s);
+        case 2: return launch_prolong_stage_v<2>(F, C, ec, u, status, s);
+        case 3: return launch_prolong_stage_v<3>(F, C, ec, u, status, s);
+        case 4: return launch_prolong_stage_v<4>(F, C, ec, u, status, s);
+        case 5: return launch_prolong_stage_v<5>(F, C, ec, u, status, s);
+        case 6: return launch_prolong_stage_v<6>(F, C, ec, u, status, s);
+        case 7: return launch_prolong_stage_v<7>(F, C, ec, u, status, s);
+        case 8: return launch_prolong_stage_v<8>(F, C, ec, u, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 void init_stage_attributes()
 {
     int dev = 0;
