@@ -471,7 +471,8 @@ int bottom_level(const ClusterPlan& P)
 }
 
 template <typename T>
-int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, bool fcycle, bool sym, cudaStream_t s)
+int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, bool fcycle, bool sym, cudaStream_t s,
+                  bool zero_start = false)
 {
     LevelStore& S = P.lv[l];
     const LevelT<T> V = Arr<T>::view(S);
@@ -510,7 +511,19 @@ int enqueue_cycle(lasto_poisson* h, ClusterPlan& P, int l, T* u, T* b, T* r, boo
         if (ch.nt == RBGS_STAGED) ch.nt = 0;   // natural storage: one block per row
     }
     T* cur = u;   // fused passes move the iterate between u and the partner array
-    TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu1, 0, ch, P.status, s));
+    if (zero_start && sizeof(T) == 4 && nu1 >= 1 && (ch.fused == 0 || ch.fused == 3)) {
+        // from u = 0 (faces zero) the first red half sweep is a point update
+        if constexpr (sizeof(T) == 4) {
+            if (V.lsh && ch.nt == RBGS_STAGED)
+                TRY(launch_split_stage_first_red(V, u, b, P.status, s));
+            else
+                TRY(launch_first_red32(V, u, b, s));
+        }
+        TRY(launch_rbgs<T>(V, u, b, 1, s, ch.nt, P.status));
+        TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu1 - 1, 0, ch, P.status, s));
+    } else {
+        TRY(smooth<T>(V, cur, Arr<T>::partner(S), u, b, nu1, 0, ch, P.status, s));
+    }
     LevelStore& C = P.lv[l + 1];
     const LevelT<T> VC = Arr<T>::view(C);
     if (sizeof(T) == 4) {
@@ -808,8 +821,14 @@ int enqueue_inner_iteration(lasto_poisson* h, ClusterPlan& P, cudaGraphCondition
 {
     LevelStore& F = P.lv[0];
     const LevelT<float> V = F.view32();
-    TRY(cudaMemsetAsync(F.u32, 0, sizeof(float) * F.N(), s));
-    int st = enqueue_cycle<float>(h, P, 0, F.u32, F.b32, F.r32, false, true, s);
+    // the preconditioner starts from z = 0: with in-place sweeps on the finest level its first
+    // red half sweep is a point update that needs no zeroed z (the faces of z were zeroed at the
+    // inner solve's start, and nothing writes them); otherwise z is zeroed here
+    const SmoothChoice ch0 = smooth_choice<float>(h, F);
+    const int nu1_0 = h->cfg.nu_fine > 0 ? h->cfg.nu_fine : h->cfg.nu1;
+    const bool point_first = P.L >= 2 && bottom_level(P) != 0 && nu1_0 >= 1 && (ch0.fused == 0 || ch0.fused == 3);
+    if (!point_first) TRY(cudaMemsetAsync(F.u32, 0, sizeof(float) * F.N(), s));
+    int st = enqueue_cycle<float>(h, P, 0, F.u32, F.b32, F.r32, false, true, s, point_first);
     if (st) return st;
     TRY(launch_dot32(V, F.b32, F.u32, P.red(FIN_IN_BETA), s));
     TRY(launch_update_p32(V, P.ctl, F.u32, P.p32, s));
@@ -824,6 +843,7 @@ int enqueue_inner_start(lasto_poisson* h, ClusterPlan& P, cudaGraphConditionalHa
     LevelStore& F = P.lv[0];
     TRY(launch_dot32(F.view32(), F.b32, nullptr, P.red(FIN_IN_START, cond, use_cond), s));
     TRY(cudaMemsetAsync(P.p32, 0, sizeof(float) * F.N(), s));
+    TRY(cudaMemsetAsync(F.u32, 0, sizeof(float) * F.N(), s));   // z, faces included
     return LASTO_OK;
 }
 

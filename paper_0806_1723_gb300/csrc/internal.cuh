@@ -226,10 +226,13 @@ constexpr int RBGS_STAGED = 1;
 template <typename T>
 cudaError_t launch_rbgs(const LevelT<T>& L, T* u, const T* b, int colour, cudaStream_t s, int nt = 256,
                         int* status = nullptr);
+// the first red FP32 half sweep from u = 0 (either storage order; faces of u already zero)
+cudaError_t launch_first_red32(const LevelT<float>& L, float* u, const float* b, cudaStream_t s);
 // stage.cu
 cudaError_t launch_split_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, cudaStream_t s);
 cudaError_t launch_split_stage_resid(const LevelT<float>& L, const float* u, const float* b, float* r, int* status,
                                      cudaStream_t s);
+cudaError_t launch_split_stage_first_red(const LevelT<float>& L, float* u, const float* b, int* status, cudaStream_t s);
 cudaError_t launch_prolong_stage(const LevelT<float>& F, const LevelT<float>& C, const float* ec, float* u, int* status,
                                  cudaStream_t s);
 bool split_stage_ok(int nx, int ny, int nz);

@@ -104,6 +104,52 @@ __device__ __forceinline__ void k_rbgs_body(LevelT<T> L, T* __restrict__ u, cons
     }
 }
 
+// The first (red) FP32 half sweep from u = 0: every neighbour term is +0, so the update is the
+// point value rb_point32(b, diagonal) -- bitwise the half sweep's result -- and reads neither u
+// nor the black nodes, which the black half sweep after it overwrites without reading.  VU red
+// nodes per thread, loads first.  (The faces of u must already be zero.)
+template <int LS>
+__global__ void __launch_bounds__(256) k_first_red32(LevelT<float> L, float* __restrict__ u, const float* __restrict__ b,
+                                                     unsigned nred)
+{
+    constexpr int NV = 4;
+    const unsigned t0 = blockIdx.x * (256u * NV) + threadIdx.x;
+    float bv[NV];
+    unsigned Q[NV];
+    bool on[NV];
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+        const unsigned t = t0 + 256u * q;
+        on[q] = false;
+        bv[q] = 0.0f;
+        Q[q] = 0u;
+        if (t < nred) {
+            int i, j, k;
+            node_ijk(2 * (size_t)t, L, i, j, k);
+            if (!is_face(L, i, j, k)) {
+                on[q] = true;
+                Q[q] = LS ? t : 2u * t;
+                bv[q] = b[Q[q]];
+                bv[q] = rb_point32(bv[q], dsum(L, i, j, k));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NV; q++)
+        if (on[q]) u[Q[q]] = bv[q];
+}
+
+cudaError_t launch_first_red32(const LevelT<float>& L, float* u, const float* b, cudaStream_t s)
+{
+    const unsigned nred = (unsigned)((L.N() + 1) / 2);
+    const unsigned g = (nred + 256u * 4u - 1u) / (256u * 4u);
+    if (L.lsh)
+        k_first_red32<1><<<g, 256, 0, s>>>(L, u, b, nred);
+    else
+        k_first_red32<0><<<g, 256, 0, s>>>(L, u, b, nred);
+    return cudaGetLastError();
+}
+
 template <typename T, int LS>
 __global__ void __launch_bounds__(512) k_rbgs(LevelT<T> L, T* __restrict__ u, const T* __restrict__ b, int colour, size_t nhalf)
 {

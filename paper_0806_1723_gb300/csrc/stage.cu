@@ -29,14 +29,18 @@ constexpr int SG_NT = 32 * SG_R;
 constexpr int SG_NS = 4;             // other-colour plane slots: k - 1, k, k + 1, one in flight
 constexpr int SG_NB = 2;             // right-hand-side plane slots: k, one in flight
 
-// RESID = 0: the half sweep of `colour` in place on u.  RESID = 1: no update; the residuals
-// b - A u of the colour's nodes go to r at the nodes' own storage positions (the restriction
-// after a black half sweep reads those of the red nodes: the black ones are then zero).
-template <int V, int RESID>
+// MODE 0: the half sweep of `colour` in place on u.  MODE 1: no update; the residuals b - A u
+// of the colour's nodes go to r at the nodes' own storage positions (the restriction after a
+// black half sweep reads those of the red nodes: the black ones are then zero).  MODE 2: the
+// half sweep of `colour` from an other colour that is zero: every neighbour term is +0, so the
+// other colour is neither staged nor read (its stale values may be anything) and the result is
+// bitwise the half sweep's over zeros.
+template <int V, int MODE>
 __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, float* __restrict__ u, const float* __restrict__ b,
                                                             int colour, StageGeom g, int* __restrict__ status,
                                                             float* __restrict__ r)
 {
+    constexpr bool RESID = MODE == 1, ZO = MODE == 2;
     extern __shared__ __align__(16) float sg[];
     __shared__ __align__(8) uint64_t bar_o[SG_NS];
     __shared__ __align__(8) uint64_t bar_b[SG_NB];
@@ -76,7 +80,7 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
     }
     __syncthreads();
     if (tid == 0) {
-        for (; o_next <= oLast && o_next < o0 + SG_NS; o_next++) {
+        for (; !ZO && o_next <= oLast && o_next < o0 + SG_NS; o_next++) {
             unsigned st, ln;
             sg_orange(L, c, o_next, j0, nr, st, ln);
             const int q = (o_next - o0) % SG_NS;
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
         bool bad = false;
         {
             // planes k - 1 and k were waited for at the previous step (or here, at the first)
-            for (int p = (k == kA ? k - 1 : k + 1); p <= k + 1; p++) {
+            for (int p = (k == kA ? k - 1 : k + 1); p <= k + 1 && !ZO; p++) {
                 const int d = p - o0;
                 if (!bad && !sg_wait(sg_smem(&bar_o[d % SG_NS]), (uint32_t)((d / SG_NS) & 1))) bad = true;
             }
@@ -114,9 +118,9 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
             const int left = ((nx - i1) >> 1) - lane;
             const unsigned q0 = ((unsigned)k * nxy + (unsigned)j * (unsigned)nx + (unsigned)i1) >> 1;
             const unsigned go = (unsigned)(1 - c) * L.H + q0 + (unsigned)lane;   // lane's node, other colour
-            const float* ok = so + ((k - o0) % SG_NS) * g.oslot + (go - ost[(k - o0) % SG_NS]);
-            const float* om = so + ((k - 1 - o0) % SG_NS) * g.oslot + (go - ost[(k - 1 - o0) % SG_NS]);
-            const float* op = so + ((k + 1 - o0) % SG_NS) * g.oslot + (go - ost[(k + 1 - o0) % SG_NS]);
+            const float* ok = ZO ? so : so + ((k - o0) % SG_NS) * g.oslot + (go - ost[(k - o0) % SG_NS]);
+            const float* om = ZO ? so : so + ((k - 1 - o0) % SG_NS) * g.oslot + (go - ost[(k - 1 - o0) % SG_NS]);
+            const float* op = ZO ? so : so + ((k + 1 - o0) % SG_NS) * g.oslot + (go - ost[(k + 1 - o0) % SG_NS]);
             const float* bo = sb + ((k - kA) % SG_NB) * g.bslot + ((unsigned)c * L.H + q0 + (unsigned)lane - bst[(k - kA) % SG_NB]);
             float* uo = (RESID ? r : u) + (size_t)c * L.H + q0 + lane;
             const float* uc = u + (size_t)c * L.H + q0 + lane;   // the colour's own values (RESID)
@@ -127,12 +131,15 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 if (32 * v < left) {
-                    float t = cmx[32 * v] * ok[dxm + 32 * v];
-                    t = fmaf(cpx[32 * v], ok[dxp + 32 * v], t);
-                    t = fmaf(cmy, ok[dym + 32 * v], t);
-                    t = fmaf(cpy, ok[dyp + 32 * v], t);
-                    t = fmaf(cmz, om[dzm + 32 * v], t);
-                    t = fmaf(cpz, op[dzp + 32 * v], t);
+                    float t = 0.0f;   // ZO: the sum of the six terms over zero neighbours, +0
+                    if constexpr (!ZO) {
+                        t = cmx[32 * v] * ok[dxm + 32 * v];
+                        t = fmaf(cpx[32 * v], ok[dxp + 32 * v], t);
+                        t = fmaf(cmy, ok[dym + 32 * v], t);
+                        t = fmaf(cpy, ok[dyp + 32 * v], t);
+                        t = fmaf(cmz, om[dzm + 32 * v], t);
+                        t = fmaf(cpz, op[dzp + 32 * v], t);
+                    }
                     if constexpr (RESID) {
                         uo[32 * v] = bo[32 * v] - fmaf(-(dgx[32 * v] + dgy + dgz), __ldg(uc + 32 * v), t);
                     } else {
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(SG_NT) k_rbgs_split_stage(LevelT<float> L, flo
             break;
         }
         if (tid == 0) {
-            if (o_next <= oLast) {   // into plane k - 1's slot
+            if (!ZO && o_next <= oLast) {   // into plane k - 1's slot
                 unsigned st, ln;
                 sg_orange(L, c, o_next, j0, nr, st, ln);
                 const int q = (o_next - o0) % SG_NS;
@@ -187,19 +194,19 @@ constexpr size_t SG_SMEM_MAX = 200 * 1024;
 
 // the shared-memory opt-in of one instantiation on the current device (done once per device;
 // init_stage_attributes does it for all before any graph capture)
-template <int V, int RESID>
+template <int V, int MODE>
 cudaError_t stage_attr(int dev)
 {
     static bool done[64] = {false};
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (done[dev]) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(k_rbgs_split_stage<V, RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(k_rbgs_split_stage<V, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)SG_SMEM_MAX);
     if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
-template <int V, int RESID>
+template <int V, int MODE>
 cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int colour, int* status, float* r,
                            cudaStream_t s)
 {
@@ -220,9 +227,9 @@ cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int
     if (per_sm_cache[dev][1] == (int)smem) {
         per_sm = per_sm_cache[dev][0];
     } else {
-        e = stage_attr<V, RESID>(dev);
+        e = stage_attr<V, MODE>(dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_split_stage<V, RESID>, SG_NT, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rbgs_split_stage<V, MODE>, SG_NT, smem);
         if (e != cudaSuccess) return e;
         per_sm_cache[dev][0] = per_sm;
         per_sm_cache[dev][1] = (int)smem;
@@ -233,7 +240,7 @@ cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int
     const int chunks0 = std::max(1, std::min(planes, std::max(1, per_sm) * sms / g.tiles_j));
     g.chunk = (planes + chunks0 - 1) / chunks0;
     const int chunks = (planes + g.chunk - 1) / g.chunk;
-    k_rbgs_split_stage<V, RESID><<<(unsigned)(g.tiles_j * chunks), SG_NT, smem, s>>>(L, u, b, colour, g, status, r);
+    k_rbgs_split_stage<V, MODE><<<(unsigned)(g.tiles_j * chunks), SG_NT, smem, s>>>(L, u, b, colour, g, status, r);
     return cudaGetLastError();
 }
 
@@ -242,21 +249,21 @@ cudaError_t launch_stage_v(const LevelT<float>& L, float* u, const float* b, int
 // the grids the staged kernel takes: at least 9 nodes per axis, rows of at most 513 nodes
 bool split_stage_ok(int nx, int ny, int nz) { return nx >= 9 && ny >= 9 && nz >= 9 && nx <= 513; }
 
-template <int RESID>
+template <int MODE>
 static cudaError_t launch_stage(const LevelT<float>& L, float* u, const float* b, int colour, int* status, float* r,
                                 cudaStream_t s)
 {
     if (!L.lsh || !split_stage_ok(L.nx, L.ny, L.nz)) return cudaErrorInvalidValue;
     if (((uintptr_t)u & 15u) || ((uintptr_t)b & 15u)) return cudaErrorInvalidValue;
     switch ((L.nx - 1) / 2 <= 256 ? ((L.nx - 1) / 2 + 31) / 32 : 0) {
-        case 1: return launch_stage_v<1, RESID>(L, u, b, colour, status, r, s);
-        case 2: return launch_stage_v<2, RESID>(L, u, b, colour, status, r, s);
-        case 3: return launch_stage_v<3, RESID>(L, u, b, colour, status, r, s);
-        case 4: return launch_stage_v<4, RESID>(L, u, b, colour, status, r, s);
-        case 5: return launch_stage_v<5, RESID>(L, u, b, colour, status, r, s);
-        case 6: return launch_stage_v<6, RESID>(L, u, b, colour, status, r, s);
-        case 7: return launch_stage_v<7, RESID>(L, u, b, colour, status, r, s);
-        case 8: return launch_stage_v<8, RESID>(L, u, b, colour, status, r, s);
+        case 1: return launch_stage_v<1, MODE>(L, u, b, colour, status, r, s);
+        case 2: return launch_stage_v<2, MODE>(L, u, b, colour, status, r, s);
+        case 3: return launch_stage_v<3, MODE>(L, u, b, colour, status, r, s);
+        case 4: return launch_stage_v<4, MODE>(L, u, b, colour, status, r, s);
+        case 5: return launch_stage_v<5, MODE>(L, u, b, colour, status, r, s);
+        case 6: return launch_stage_v<6, MODE>(L, u, b, colour, status, r, s);
+        case 7: return launch_stage_v<7, MODE>(L, u, b, colour, status, r, s);
+        case 8: return launch_stage_v<8, MODE>(L, u, b, colour, status, r, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -275,6 +282,14 @@ cudaError_t launch_split_stage_resid(const LevelT<float>& L, const float* u, con
 {
     if ((uintptr_t)r & 15u) return cudaErrorInvalidValue;
     return launch_stage<1>(L, const_cast<float*>(u), b, 0, status, r, s);
+}
+
+// The red half sweep from a black colour that is zero (the first half sweep from u = 0; the
+// faces of u zero): neither reads nor stages the black nodes, bitwise the red half sweep over
+// zeros.  u and b as for launch_split_stage.
+cudaError_t launch_split_stage_first_red(const LevelT<float>& L, float* u, const float* b, int* status, cudaStream_t s)
+{
+    return launch_stage<2>(L, u, b, 0, status, nullptr, s);
 }
 
 // ---------------------------------------------------------------- staged prolongation
@@ -507,6 +522,8 @@ void init_stage_attributes()
     stage_attr<5, 0>(dev), stage_attr<6, 0>(dev), stage_attr<7, 0>(dev), stage_attr<8, 0>(dev);
     stage_attr<1, 1>(dev), stage_attr<2, 1>(dev), stage_attr<3, 1>(dev), stage_attr<4, 1>(dev);
     stage_attr<5, 1>(dev), stage_attr<6, 1>(dev), stage_attr<7, 1>(dev), stage_attr<8, 1>(dev);
+    stage_attr<1, 2>(dev), stage_attr<2, 2>(dev), stage_attr<3, 2>(dev), stage_attr<4, 2>(dev);
+    stage_attr<5, 2>(dev), stage_attr<6, 2>(dev), stage_attr<7, 2>(dev), stage_attr<8, 2>(dev);
 }
 
 }  // namespace lasto
