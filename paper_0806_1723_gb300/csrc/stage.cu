@@ -13,6 +13,10 @@
 // time.  Results go straight to global memory (the colour being written is not read in this
 // half sweep).
 //
+// The same kernel forms the red residuals for the restriction (MODE 1) and the first red half
+// sweep from a zero iterate (MODE 2); the file also holds the staged prolongation onto a
+// colour-split level (k_prolong_stage), which stages the coarse rows the same way.
+//
 // Waits are bounded: a wait that runs out (about two seconds) raises LASTO_ERR_TIMEOUT in
 // *status (when given), the block waits -- again bounded -- for the copies it has in flight and
 // leaves.
